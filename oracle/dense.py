@@ -1,0 +1,125 @@
+"""Dense (definition-level) oracle: the multivariate-normal log-density of each
+pulsar's residual vector.  TEST INFRASTRUCTURE ONLY.
+
+The Kalman filter's prediction-error decomposition reaches this exactly, up to
+rounding (paper, Statement of Need and Relation to Existing Work: the
+state-space likelihood is the time-domain form of the Gaussian-process
+likelihood that frequency-domain methods evaluate with full covariance
+matrices).  Here that covariance is written out and factorised by Cholesky,
+O(N^3): usable for N up to a few thousand.
+
+Model (paper, Functionality: linear SDEs for the pulsar's spin wandering,
+separated from EFAC/EQUAD white measurement noise): with tau = t - t_1,
+
+  C_ij = P0_rr + P0_ry (tau_i + tau_j) + P0_yy tau_i tau_j
+         + sigma_p^2 (m^2 M / 2 - m^3 / 6) + delta_ij R_i,
+  m = min(tau_i, tau_j),  M = max(tau_i, tau_j),  R_i = EFAC^2 sigma_i^2 + EQUAD^2
+
+(the covariance of a once-integrated Brownian motion plus the propagated
+prior), and ll_p = -1/2 [(r - s)^T C^-1 (r - s) + ln det C + N ln 2 pi].
+
+Gradients: d ll / d theta = (ds/dtheta)^T alpha for the signal parameters and
+1/2 tr[(alpha alpha^T - C^-1) dC/deta] for the noise parameters, with
+alpha = C^-1 (r - s).
+"""
+from __future__ import annotations
+
+import numpy as np
+from scipy.linalg import cho_factor, cho_solve
+
+LN10 = np.log(10.0)
+N_GW = 7
+
+
+def cw_project(theta_gw, pos):
+    """(A, B, Omega, Phi0) of the Earth-term continuous-wave residual.
+
+    Works for real or complex theta (complex-step derivatives).
+    """
+    th = np.asarray(theta_gw)
+    f = 10.0 ** th[0]
+    W = 2.0 * np.pi * f
+    phi0, psi, cosi, sind, al, h0 = th[1], th[2], th[3], th[4], th[5], 10.0 ** th[6]
+    cosd = np.sqrt(1.0 - sind * sind)
+    n = np.array([cosd * np.cos(al), cosd * np.sin(al), sind])
+    u = np.array([np.sin(al), -np.cos(al), 0.0 * al])
+    v = np.array([sind * np.cos(al), sind * np.sin(al), -cosd])
+    p = np.cos(psi) * u + np.sin(psi) * v
+    q = -np.sin(psi) * u + np.cos(psi) * v
+    c = np.asarray(pos, dtype=np.float64)
+    cp, cq = c @ p, c @ q
+    D = 1.0 - c @ n
+    if np.real(D) < 1e-12:
+        D = 1e-12 + 1j * np.imag(D) if np.iscomplexobj(D) else 1e-12
+    Fp = 0.5 * (cp * cp - cq * cq) / D
+    Fx = cp * cq / D
+    A = Fp * h0 * (1.0 + cosi * cosi) / W
+    B = -2.0 * Fx * h0 * cosi / W
+    return A, B, W, phi0
+
+
+def cw_signal(theta_gw, pos, t):
+    A, B, W, phi0 = cw_project(theta_gw, pos)
+    ph = W * np.asarray(t) + phi0
+    return A * np.sin(ph) + B * np.cos(ph)
+
+
+def ibm_covariance(t, sig2, p0, R):
+    """Dense covariance of the residual vector of one pulsar."""
+    tau = np.asarray(t, dtype=np.float64) - t[0]
+    mn = np.minimum.outer(tau, tau)
+    mx = np.maximum.outer(tau, tau)
+    C = (p0[0] + p0[1] * (tau[:, None] + tau[None, :]) + p0[2] * np.outer(tau, tau)
+         + sig2 * (mn * mn * mx / 2.0 - mn ** 3 / 6.0))
+    C[np.diag_indices_from(C)] += R
+    return C
+
+
+def _pulsar_parts(data, p, theta):
+    t, r, sig = data.pulsar(p)
+    ls, efac = theta[N_GW + 2 * p], theta[N_GW + 2 * p + 1]
+    sig2 = 10.0 ** (2.0 * ls)
+    R = efac ** 2 * sig ** 2 + data.equad[p] ** 2
+    C = ibm_covariance(t, sig2, data.p0[p], R)
+    s = cw_signal(theta[:N_GW], data.pos[p], t)
+    return t, r, sig, sig2, efac, C, s
+
+
+def pulsar_loglik(data, p, theta):
+    t, r, sig, sig2, efac, C, s = _pulsar_parts(data, p, theta)
+    cf = cho_factor(C, lower=True)
+    d = r - s
+    alpha = cho_solve(cf, d)
+    logdet = 2.0 * np.sum(np.log(np.diag(cf[0])))
+    return -0.5 * (d @ alpha + logdet + len(t) * np.log(2.0 * np.pi))
+
+
+def loglik(data, theta):
+    theta = np.atleast_2d(theta)
+    return np.array([sum(pulsar_loglik(data, p, th) for p in range(data.n_pulsars))
+                     for th in theta])
+
+
+def grad(data, theta, h=1e-20):
+    """Gradient by the dense formulas; ds/dtheta by complex step on cw_signal."""
+    theta = np.asarray(theta, dtype=np.float64)
+    P = data.n_pulsars
+    g = np.zeros(N_GW + 2 * P)
+    for p in range(P):
+        t, r, sig, sig2, efac, C, s = _pulsar_parts(data, p, theta)
+        cf = cho_factor(C, lower=True)
+        alpha = cho_solve(cf, r - s)
+        for j in range(N_GW):
+            thc = theta[:N_GW].astype(np.complex128)
+            thc[j] += 1j * h
+            ds = np.imag(cw_signal(thc, data.pos[p], t)) / h
+            g[j] += ds @ alpha
+        Cinv = cho_solve(cf, np.eye(len(t)))
+        M = np.outer(alpha, alpha) - Cinv
+        tau = t - t[0]
+        mn = np.minimum.outer(tau, tau)
+        mx = np.maximum.outer(tau, tau)
+        dC_ls = 2.0 * LN10 * sig2 * (mn * mn * mx / 2.0 - mn ** 3 / 6.0)
+        g[N_GW + 2 * p] = 0.5 * np.sum(M * dC_ls)
+        g[N_GW + 2 * p + 1] = 0.5 * np.sum(np.diag(M) * 2.0 * efac * sig ** 2)
+    return g

@@ -1,0 +1,252 @@
+/*
+ * CPU oracle: plain, slow FP64 Kalman-filter log-likelihood of a pulsar timing
+ * array and its gradient.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the CPU
+ * baseline leg of the benchmark load this library; the CUDA product path shares
+ * no code with it.
+ *
+ * What it computes (paper, Functionality: the likelihood of the TOA data
+ * evaluated by a Kalman filter in O(N); pulsars are independent given the
+ * parameters of a deterministic continuous-wave source, so the array
+ * log-likelihood is the sum of the pulsar log-likelihoods):
+ *
+ *   ll(theta) = sum_p ll_p(theta),  theta = [log10 f, Phi0, psi, cos iota,
+ *               sin delta, alpha, log10 h0, (log10 sigma_p, EFAC_p)_p]
+ *
+ * The continuous-wave residual is the Earth term of a monochromatic source
+ * (paper, Future Directions, and the prior work it cites):
+ *   n = (cos d cos a, cos d sin a, sin d), u = (sin a, -cos a, 0),
+ *   v = (sin d cos a, sin d sin a, -cos d), p = cos psi u + sin psi v,
+ *   q = -sin psi u + cos psi v,
+ *   F+ = ((c.p)^2 - (c.q)^2) / (2 (1 - n.c)),  Fx = (c.p)(c.q) / (1 - n.c),
+ *   s(t) = A sin(W t + Phi0) + B cos(W t + Phi0),
+ *   A = F+ h0 (1 + cos^2 i) / W,  B = -2 Fx h0 cos i / W,  W = 2 pi f.
+ *
+ * The gradient is taken by the complex-step method (Squire & Trapp 1998):
+ * d ll / d theta_j = Im ll(theta + i h e_j) / h with h = 1e-20, evaluated
+ * through the same filter code in complex arithmetic.  It shares nothing with
+ * the reverse-mode adjoint of the CUDA path.
+ *
+ * Out-of-domain parameter vectors (non-finite, EFAC <= 0, |cos i| > 1,
+ * |sin d| > 1) and filters that meet S_k <= 0 get ll = -inf and a zero
+ * gradient.
+ */
+#include <complex.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#define LOG2PI 1.8378770664093454836
+#define CS_H 1e-20
+#define N_GW 7
+
+typedef double complex cplx;
+
+/* ---- the filter, instantiated for double and for double complex ---- */
+#define KF_T double
+#define KF_NAME kf_real
+#define KF_SIN sin
+#define KF_COS cos
+#define KF_LOG log
+#define KF_RE(x) (x)
+#define KF_LOG2PI LOG2PI
+#include "kf_body.h"
+#undef KF_T
+#undef KF_NAME
+#undef KF_SIN
+#undef KF_COS
+#undef KF_LOG
+#undef KF_RE
+
+#define KF_T cplx
+#define KF_NAME kf_cplx
+#define KF_SIN csin
+#define KF_COS ccos
+#define KF_LOG clog
+#define KF_RE(x) creal(x)
+#include "kf_body.h"
+
+/* ---- continuous-wave projection, in complex arithmetic ---- */
+static void cw_project(const cplx th[N_GW], const double c[3],
+                       cplx* A, cplx* B, cplx* Om, cplx* Phi0)
+{
+    cplx f = cpow(10.0, th[0]);
+    cplx W = 2.0 * M_PI * f;
+    cplx psi = th[2], cosi = th[3], sind = th[4], al = th[5];
+    cplx h0 = cpow(10.0, th[6]);
+    cplx cosd = csqrt(1.0 - sind * sind);
+    cplx n[3] = {cosd * ccos(al), cosd * csin(al), sind};
+    cplx u[3] = {csin(al), -ccos(al), 0.0};
+    cplx v[3] = {sind * ccos(al), sind * csin(al), -cosd};
+    cplx p[3], q[3];
+    for (int i = 0; i < 3; ++i) {
+        p[i] = ccos(psi) * u[i] + csin(psi) * v[i];
+        q[i] = -csin(psi) * u[i] + ccos(psi) * v[i];
+    }
+    cplx cp = c[0] * p[0] + c[1] * p[1] + c[2] * p[2];
+    cplx cq = c[0] * q[0] + c[1] * q[1] + c[2] * q[2];
+    cplx D = 1.0 - (c[0] * n[0] + c[1] * n[1] + c[2] * n[2]);
+    if (creal(D) < 1e-12) D = 1e-12 + I * cimag(D);   /* source behind the pulsar */
+    cplx Fp = 0.5 * (cp * cp - cq * cq) / D;
+    cplx Fx = cp * cq / D;
+    *A = Fp * h0 * (1.0 + cosi * cosi) / W;
+    *B = -2.0 * Fx * h0 * cosi / W;
+    *Om = W;
+    *Phi0 = th[1];
+}
+
+static int theta_in_domain(const double* th, int P)
+{
+    int D = N_GW + 2 * P;
+    for (int j = 0; j < D; ++j)
+        if (!isfinite(th[j])) return 0;
+    if (fabs(th[3]) > 1.0 || fabs(th[4]) > 1.0) return 0;
+    for (int p = 0; p < P; ++p)
+        if (!(th[N_GW + 2 * p + 1] > 0.0)) return 0;
+    return 1;
+}
+
+typedef struct {
+    int P;
+    const int64_t* off;
+    const double *t, *r, *sigma, *pos, *equad, *p0;
+} array_view;
+
+/* one pulsar, complex parameters */
+static cplx pulsar_ll_c(const array_view* a, int p, const cplx thgw[N_GW],
+                        cplx log10sig, cplx efac, int* bad)
+{
+    cplx A, B, Om, Phi0;
+    cw_project(thgw, a->pos + 3 * p, &A, &B, &Om, &Phi0);
+    cplx sig2 = cpow(10.0, 2.0 * log10sig);
+    int64_t o = a->off[p], n = a->off[p + 1] - a->off[p];
+    return kf_cplx(n, a->t + o, a->r + o, a->sigma + o, a->equad[p], a->p0 + 3 * p,
+                   A, B, Om, Phi0, sig2, efac, bad, NULL, NULL);
+}
+
+/* one pulsar, real parameters */
+static double pulsar_ll_r(const array_view* a, int p, const double* th, int* bad)
+{
+    cplx thc[N_GW];
+    for (int j = 0; j < N_GW; ++j) thc[j] = th[j];
+    cplx A, B, Om, Phi0;
+    cw_project(thc, a->pos + 3 * p, &A, &B, &Om, &Phi0);
+    double sig2 = pow(10.0, 2.0 * th[N_GW + 2 * p]);
+    double efac = th[N_GW + 2 * p + 1];
+    int64_t o = a->off[p], n = a->off[p + 1] - a->off[p];
+    return kf_real(n, a->t + o, a->r + o, a->sigma + o, a->equad[p], a->p0 + 3 * p,
+                   creal(A), creal(B), creal(Om), creal(Phi0), sig2, efac, bad, NULL, NULL);
+}
+
+static double walker_ll(const array_view* a, const double* th, double* lane_ll)
+{
+    if (!theta_in_domain(th, a->P)) {
+        if (lane_ll) for (int p = 0; p < a->P; ++p) lane_ll[p] = -INFINITY;
+        return -INFINITY;
+    }
+    double ll = 0.0;
+    int bad = 0;
+    for (int p = 0; p < a->P; ++p) {
+        int b = 0;
+        double lp = pulsar_ll_r(a, p, th, &b);
+        if (b || isnan(lp)) lp = -INFINITY;
+        if (lane_ll) lane_ll[p] = lp;
+        bad |= b;
+        ll += lp;
+    }
+    if (bad || isnan(ll)) ll = -INFINITY;
+    return ll;
+}
+
+static void walker_grad(const array_view* a, const double* th, double* g)
+{
+    int P = a->P, D = N_GW + 2 * P;
+    memset(g, 0, sizeof(double) * D);
+    cplx thgw[N_GW];
+    for (int j = 0; j < N_GW; ++j) thgw[j] = th[j];
+    int bad = 0;
+    /* continuous-wave parameters: every pulsar depends on them */
+    for (int j = 0; j < N_GW; ++j) {
+        cplx tj[N_GW];
+        memcpy(tj, thgw, sizeof(tj));
+        tj[j] += I * CS_H;
+        double acc = 0.0;
+        for (int p = 0; p < P; ++p) {
+            cplx lp = pulsar_ll_c(a, p, tj, th[N_GW + 2 * p], th[N_GW + 2 * p + 1], &bad);
+            acc += cimag(lp) / CS_H;
+        }
+        g[j] = acc;
+    }
+    /* per-pulsar noise parameters: only their own pulsar depends on them */
+    for (int p = 0; p < P; ++p) {
+        double ls = th[N_GW + 2 * p], ef = th[N_GW + 2 * p + 1];
+        cplx l1 = pulsar_ll_c(a, p, thgw, ls + I * CS_H, ef, &bad);
+        cplx l2 = pulsar_ll_c(a, p, thgw, ls, ef + I * CS_H, &bad);
+        g[N_GW + 2 * p] = cimag(l1) / CS_H;
+        g[N_GW + 2 * p + 1] = cimag(l2) / CS_H;
+    }
+    if (bad) memset(g, 0, sizeof(double) * D);
+}
+
+/* ---------------------------- exported API ---------------------------- */
+
+/* Array log-likelihood for B parameter vectors theta[B][7+2P] -> out[B].
+   lane_out (optional, may be NULL): per-pulsar terms [B][P]. */
+int oracle_loglik(int P, const int64_t* off, const double* t, const double* r,
+                  const double* sigma, const double* pos, const double* equad,
+                  const double* p0, const double* theta, int64_t B,
+                  double* out, double* lane_out)
+{
+    array_view a = {P, off, t, r, sigma, pos, equad, p0};
+    int D = N_GW + 2 * P;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t b = 0; b < B; ++b)
+        out[b] = walker_ll(&a, theta + b * D, lane_out ? lane_out + b * P : NULL);
+    return 0;
+}
+
+/* Log-likelihood and gradient: out_ll[B], out_grad[B][7+2P]. */
+int oracle_loglik_grad(int P, const int64_t* off, const double* t, const double* r,
+                       const double* sigma, const double* pos, const double* equad,
+                       const double* p0, const double* theta, int64_t B,
+                       double* out_ll, double* out_grad)
+{
+    array_view a = {P, off, t, r, sigma, pos, equad, p0};
+    int D = N_GW + 2 * P;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t b = 0; b < B; ++b) {
+        const double* th = theta + b * D;
+        out_ll[b] = walker_ll(&a, th, NULL);
+        if (isinf(out_ll[b]) && out_ll[b] < 0)
+            memset(out_grad + b * D, 0, sizeof(double) * D);
+        else
+            walker_grad(&a, th, out_grad + b * D);
+    }
+    return 0;
+}
+
+/* Continuous-wave projection of one parameter vector onto one pulsar:
+   out = {A, B, Omega, Phi0}. */
+int oracle_cw_project(const double* theta_gw, const double* pos, double* out)
+{
+    cplx th[N_GW];
+    for (int j = 0; j < N_GW; ++j) th[j] = theta_gw[j];
+    cplx A, B, Om, Phi0;
+    cw_project(th, pos, &A, &B, &Om, &Phi0);
+    out[0] = creal(A); out[1] = creal(B); out[2] = creal(Om); out[3] = creal(Phi0);
+    return 0;
+}
+
+/* One pulsar's filter with explicit lane parameters lane = {A, B, Omega,
+   Phi0, sigma^2, EFAC}; optionally returns the innovations e_k and their
+   variances S_k (used by the calibration tests). */
+double oracle_pulsar_filter(int64_t n, const double* t, const double* r, const double* sigma,
+                            double equad, const double* p0, const double* lane,
+                            double* e_out, double* S_out)
+{
+    int bad = 0;
+    double ll = kf_real(n, t, r, sigma, equad, p0, lane[0], lane[1], lane[2], lane[3],
+                        lane[4], lane[5], &bad, e_out, S_out);
+    return bad ? -INFINITY : ll;
+}
