@@ -1,0 +1,134 @@
+/*
+ * argus.h -- C ABI of the GB300 (sm_103a) batched Kalman-filter likelihood of
+ * pulsar-timing-array data.
+ *
+ * The paper (Functionality: "Kalman filter likelihood evaluation" and
+ * "Sampler Integration") makes one call the core of the method: the
+ * log-likelihood of the TOA data under a linear Gaussian state-space model,
+ * evaluated by a Kalman filter in O(N), and its gradient, called by a
+ * gradient-based sampler at every step.  This library evaluates that call for
+ * a batch of B parameter vectors ("walkers") at once, one (walker, pulsar)
+ * lane per CUDA thread, in FP64.
+ *
+ * Model, per pulsar p (paper, Functionality: "State-space model
+ * construction"; the continuous-wave source of Future Directions):
+ *   state x = (rho, y): timing residual [s] and fractional frequency deviation;
+ *   d rho/dt = y,  dy/dt = xi(t),  <xi(t) xi(t')> = sigma_p^2 delta(t - t');
+ *   r_k = rho(t_k) + s_p(t_k) + eps_k,  eps_k ~ N(0, EFAC_p^2 sigma_k^2 + EQUAD_p^2);
+ *   x(t_1) ~ N(0, P0_p);
+ *   s_p(t) = A sin(W t + Phi0) + B cos(W t + Phi0), the Earth term of a
+ *   monochromatic gravitational wave projected on the pulsar direction.
+ * ll(theta) = sum_p sum_k -1/2 (ln 2 pi + ln S_k + e_k^2 / S_k).
+ *
+ * Parameter vector theta (D = 7 + 2P doubles, row-major [B][D]):
+ *   [log10 f_gw (Hz), Phi0 (rad), psi (rad), cos iota, sin delta, alpha (rad),
+ *    log10 h0, then per pulsar (log10 sigma_p, EFAC_p)].
+ * Out-of-domain vectors (a non-finite entry, EFAC <= 0, |cos iota| > 1,
+ * |sin delta| > 1) and filters that meet a non-positive or non-finite
+ * innovation variance give loglik = -inf and a zero gradient for that walker;
+ * the call still returns ARGUS_OK.
+ *
+ * Pointers: theta, loglik and grad may each be device memory or host memory
+ * (pinned or pageable); the library asks CUDA which.  With device pointers a
+ * call only enqueues work on `stream` and returns.  With any host pointer the
+ * call stages through device buffers owned by the handle, and returns after
+ * the stream has finished and the host outputs are written.  The caller owns
+ * theta and the outputs; the handle owns the staged TOA data and all scratch.
+ * Calls on one handle must not run concurrently from several host threads.
+ */
+#ifndef ARGUS_H
+#define ARGUS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum argus_status {
+    ARGUS_OK = 0,
+    ARGUS_ERR_INVALID_ARG = 1,   /* rejected on the host before any launch */
+    ARGUS_ERR_CUDA = 2,          /* a CUDA call failed; see argus_last_error() */
+    ARGUS_ERR_OOM = 3,           /* device allocation failed */
+    ARGUS_ERR_NONFINITE = 4,     /* reserved: reported through loglik = -inf instead */
+    ARGUS_ERR_TIMEOUT = 5,       /* a bounded device-side wait gave up */
+    ARGUS_ERR_UNSUPPORTED = 6    /* no sm_103a device, or a size beyond a documented limit */
+} argus_status;
+
+/* One pulsar as handed to argus_array_create (all host memory, copied). */
+typedef struct argus_pulsar {
+    int64_t n_toa;          /* >= 0 TOAs */
+    const double* t;        /* [n_toa] TOA times, s from the array epoch, non-decreasing */
+    const double* r;        /* [n_toa] timing residuals, s */
+    const double* sigma;    /* [n_toa] TOA errors, s, finite and > 0 */
+    double pos[3];          /* unit vector towards the pulsar (|pos| = 1 within 1e-6) */
+    double equad;           /* EQUAD, s, >= 0 */
+    double p0[3];           /* prior covariance of (rho, y): {rr, ry, yy}, positive semi-definite */
+} argus_pulsar;
+
+/* Opaque handle: device copies of the TOA data, scratch, plans, graphs. */
+typedef struct argus_array argus_array;
+
+/* How a batch is scheduled (paper: none -- this is the GPU's own choice).
+ * mode ARGUS_MODE_BATCHED: all B x P lanes in one persistent launch fed by an
+ *   atomic work counter over (pulsar, walker-tile) items sorted by TOA count,
+ *   largest first; optionally replayed from a captured CUDA graph.
+ * mode ARGUS_MODE_PLAIN: the same kernels launched once per parameter vector
+ *   (B launches of P lanes each); the comparison point. */
+enum { ARGUS_MODE_BATCHED = 0, ARGUS_MODE_PLAIN = 1 };
+typedef struct argus_plan {
+    int32_t mode;             /* ARGUS_MODE_BATCHED | ARGUS_MODE_PLAIN */
+    int32_t walkers_per_cta;  /* lanes of one pulsar per thread block: 32, 64, 128 or 256 */
+    int32_t ctas_per_sm;      /* resident blocks per SM of the persistent grid, 1..8 */
+    int32_t ckpt_stride;      /* adjoint checkpoint stride in TOAs; 0 = ceil(sqrt(N_p)) */
+    int32_t use_graph;        /* 1: capture each (theta, B, outputs) call once, then replay */
+    int32_t reserved[3];      /* must be 0 */
+} argus_plan;
+
+/* Copy n_pulsars pulsars to device `device` and build the handle.
+ * Precomputes per TOA: dt_k = t_k - t_{k-1} (dt_1 = 0), dt^2/2, dt^3/3,
+ * sigma_k^2.  Returns ARGUS_ERR_INVALID_ARG for unsorted times, non-positive
+ * or non-finite errors, a non-unit position, a negative EQUAD, a prior that is
+ * not positive semi-definite, or n_pulsars < 1; ARGUS_ERR_UNSUPPORTED if the
+ * device is not sm_103; *out is set only on success. */
+argus_status argus_array_create(const argus_pulsar* pulsars, int32_t n_pulsars, int32_t device,
+                                argus_array** out);
+
+/* Free everything the handle owns.  NULL is allowed.  Synchronises the device. */
+void argus_array_destroy(argus_array* array);
+
+/* D = 7 + 2P, the length of one parameter vector; -1 for NULL. */
+int32_t argus_array_dim(const argus_array* array);
+
+/* Replace / read the scheduling plan.  set_plan validates every field and
+ * drops captured graphs; get_plan copies the current plan into *plan. */
+argus_status argus_array_set_plan(argus_array* array, const argus_plan* plan);
+argus_status argus_array_get_plan(const argus_array* array, argus_plan* plan);
+
+/* Array log-likelihood of B parameter vectors.
+ * theta [B][D] doubles, loglik [B] doubles (device or host, see above).
+ * B = 0 is a no-op.  stream: a cudaStream_t, or NULL for the legacy stream. */
+argus_status argus_loglik(argus_array* array, const double* theta, int64_t B,
+                          double* loglik, void* stream);
+
+/* Log-likelihood and its gradient d loglik / d theta, [B][D] doubles, by a
+ * reverse-mode adjoint sweep through the filter with forward states
+ * checkpointed every ckpt_stride TOAs (default ceil(sqrt(N_p))). */
+argus_status argus_loglik_grad(argus_array* array, const double* theta, int64_t B,
+                               double* loglik, double* grad, void* stream);
+
+/* Per-(walker, pulsar) terms, for inspection: lane_ll [B][P] doubles (device
+ * or host) receives ll_p(theta_b).  Same rules as argus_loglik. */
+argus_status argus_lane_loglik(argus_array* array, const double* theta, int64_t B,
+                               double* lane_ll, void* stream);
+
+/* Human-readable name of a status, and the message of the last error raised
+ * on the calling host thread ("" if none). */
+const char* argus_status_string(argus_status status);
+const char* argus_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ARGUS_H */

@@ -1,0 +1,254 @@
+"""Thin Python binding of the C ABI in include/argus.h (ctypes).
+
+Argument marshalling only: every step of the likelihood runs in the CUDA
+library.  If libargus.so is missing or no sm_103 device is present the calls
+raise; there is no CPU fallback.
+
+Names follow the C ABI: ``argus_array_create``, ``argus_loglik``,
+``argus_loglik_grad``, ``argus_lane_loglik``; ``ArgusLoglik`` is the
+torch.autograd.Function a gradient-based sampler calls (paper, Functionality:
+"Sampler Integration" -- likelihood and gradient for HMC).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+ARGUS_MODE_BATCHED = 0
+ARGUS_MODE_PLAIN = 1
+STATUS = {0: "ARGUS_OK", 1: "ARGUS_ERR_INVALID_ARG", 2: "ARGUS_ERR_CUDA", 3: "ARGUS_ERR_OOM",
+          4: "ARGUS_ERR_NONFINITE", 5: "ARGUS_ERR_TIMEOUT", 6: "ARGUS_ERR_UNSUPPORTED"}
+
+
+class ArgusError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class ArgusPulsar(ctypes.Structure):
+    _fields_ = [("n_toa", ctypes.c_int64),
+                ("t", ctypes.POINTER(ctypes.c_double)),
+                ("r", ctypes.POINTER(ctypes.c_double)),
+                ("sigma", ctypes.POINTER(ctypes.c_double)),
+                ("pos", ctypes.c_double * 3),
+                ("equad", ctypes.c_double),
+                ("p0", ctypes.c_double * 3)]
+
+
+class ArgusPlan(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32),
+                ("walkers_per_cta", ctypes.c_int32),
+                ("ctas_per_sm", ctypes.c_int32),
+                ("ckpt_stride", ctypes.c_int32),
+                ("use_graph", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load libargus.so; raises if it is absent (no fallback path exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise ArgusError(6, f"{path} is not built; run __graft_entry__.build()")
+        _build.build()
+    lib = ctypes.CDLL(path)
+    vp, dp = ctypes.c_void_p, ctypes.c_void_p
+    lib.argus_array_create.argtypes = [ctypes.POINTER(ArgusPulsar), ctypes.c_int32, ctypes.c_int32,
+                                       ctypes.POINTER(vp)]
+    lib.argus_array_create.restype = ctypes.c_int
+    lib.argus_array_destroy.argtypes = [vp]
+    lib.argus_array_destroy.restype = None
+    lib.argus_array_dim.argtypes = [vp]
+    lib.argus_array_dim.restype = ctypes.c_int32
+    lib.argus_array_set_plan.argtypes = [vp, ctypes.POINTER(ArgusPlan)]
+    lib.argus_array_set_plan.restype = ctypes.c_int
+    lib.argus_array_get_plan.argtypes = [vp, ctypes.POINTER(ArgusPlan)]
+    lib.argus_array_get_plan.restype = ctypes.c_int
+    lib.argus_loglik.argtypes = [vp, dp, ctypes.c_int64, dp, vp]
+    lib.argus_loglik.restype = ctypes.c_int
+    lib.argus_loglik_grad.argtypes = [vp, dp, ctypes.c_int64, dp, dp, vp]
+    lib.argus_loglik_grad.restype = ctypes.c_int
+    lib.argus_lane_loglik.argtypes = [vp, dp, ctypes.c_int64, dp, vp]
+    lib.argus_lane_loglik.restype = ctypes.c_int
+    lib.argus_status_string.argtypes = [ctypes.c_int]
+    lib.argus_status_string.restype = ctypes.c_char_p
+    lib.argus_last_error.argtypes = []
+    lib.argus_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(st: int) -> None:
+    if st != 0:
+        raise ArgusError(st, _lib.argus_last_error().decode())
+
+
+def _ptr(x):
+    """Raw address of a torch tensor or numpy array (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return x.data_ptr()
+
+
+def _stream_of(*tensors):
+    import torch
+    for t in tensors:
+        if isinstance(t, torch.Tensor) and t.is_cuda:
+            return torch.cuda.current_stream(t.device).cuda_stream
+    return None
+
+
+class Array:
+    """Handle of one pulsar array on one device (argus_array_create)."""
+
+    def __init__(self, data, device: int = 0):
+        lib = load()
+        P = data.n_pulsars
+        self._keep = []
+        ps = (ArgusPulsar * P)()
+        for p in range(P):
+            t, r, s = (np.ascontiguousarray(a, dtype=np.float64) for a in data.pulsar(p))
+            self._keep += [t, r, s]
+            dp = ctypes.POINTER(ctypes.c_double)
+            ps[p].n_toa = len(t)
+            ps[p].t = t.ctypes.data_as(dp)
+            ps[p].r = r.ctypes.data_as(dp)
+            ps[p].sigma = s.ctypes.data_as(dp)
+            ps[p].pos[:] = [float(v) for v in data.pos[p]]
+            ps[p].equad = float(data.equad[p])
+            ps[p].p0[:] = [float(v) for v in data.p0[p]]
+        h = ctypes.c_void_p()
+        _check(lib.argus_array_create(ps, P, device, ctypes.byref(h)))
+        self._keep = None
+        self.handle = h
+        self.n_pulsars = P
+        self.dim = lib.argus_array_dim(h)
+        self.device = device
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib.argus_array_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_plan(self) -> dict:
+        p = ArgusPlan()
+        _check(_lib.argus_array_get_plan(self.handle, ctypes.byref(p)))
+        return dict(mode=p.mode, walkers_per_cta=p.walkers_per_cta, ctas_per_sm=p.ctas_per_sm,
+                    ckpt_stride=p.ckpt_stride, use_graph=p.use_graph)
+
+    def set_plan(self, **kw) -> None:
+        cur = self.get_plan()
+        cur.update(kw)
+        p = ArgusPlan(cur["mode"], cur["walkers_per_cta"], cur["ctas_per_sm"],
+                      cur["ckpt_stride"], cur["use_graph"])
+        _check(_lib.argus_array_set_plan(self.handle, ctypes.byref(p)))
+
+
+def argus_array_create(data, device: int = 0) -> Array:
+    return Array(data, device)
+
+
+def _new_like(theta, shape):
+    if isinstance(theta, np.ndarray):
+        return np.empty(shape, dtype=np.float64)
+    import torch
+    return torch.empty(shape, dtype=torch.float64, device=theta.device)
+
+
+def _prep(theta, dim):
+    if isinstance(theta, np.ndarray):
+        theta = np.ascontiguousarray(np.atleast_2d(theta), dtype=np.float64)
+    else:
+        if theta.dim() == 1:
+            theta = theta[None, :]
+        assert theta.dtype.is_floating_point and theta.element_size() == 8, "theta must be float64"
+        theta = theta.contiguous()
+    if theta.shape[1] != dim:
+        raise ArgusError(1, f"theta has {theta.shape[1]} columns, array needs {dim}")
+    return theta
+
+
+def argus_loglik(array: Array, theta, loglik=None, stream=None):
+    theta = _prep(theta, array.dim)
+    B = theta.shape[0]
+    if loglik is None:
+        loglik = _new_like(theta, (B,))
+    s = stream if stream is not None else _stream_of(theta, loglik)
+    _check(_lib.argus_loglik(array.handle, _ptr(theta), B, _ptr(loglik), s))
+    return loglik
+
+
+def argus_loglik_grad(array: Array, theta, loglik=None, grad=None, stream=None):
+    theta = _prep(theta, array.dim)
+    B = theta.shape[0]
+    if loglik is None:
+        loglik = _new_like(theta, (B,))
+    if grad is None:
+        grad = _new_like(theta, (B, array.dim))
+    s = stream if stream is not None else _stream_of(theta, loglik, grad)
+    _check(_lib.argus_loglik_grad(array.handle, _ptr(theta), B, _ptr(loglik), _ptr(grad), s))
+    return loglik, grad
+
+
+def argus_lane_loglik(array: Array, theta, lane=None, stream=None):
+    theta = _prep(theta, array.dim)
+    B = theta.shape[0]
+    if lane is None:
+        lane = _new_like(theta, (B, array.n_pulsars))
+    s = stream if stream is not None else _stream_of(theta, lane)
+    _check(_lib.argus_lane_loglik(array.handle, _ptr(theta), B, _ptr(lane), s))
+    return lane
+
+
+def _autograd_function():
+    import torch
+
+    class ArgusLoglik(torch.autograd.Function):
+        """loglik(theta) with the adjoint-kernel gradient as its backward."""
+
+        @staticmethod
+        def forward(ctx, theta, array):
+            ll, g = argus_loglik_grad(array, theta.detach())
+            ctx.save_for_backward(g)
+            return ll
+
+        @staticmethod
+        def backward(ctx, gout):
+            (g,) = ctx.saved_tensors
+            return gout[:, None] * g, None
+
+    return ArgusLoglik
+
+
+_ArgusLoglik = None
+
+
+def loglik_autograd(theta, array: Array):
+    """Differentiable array log-likelihood: ``ArgusLoglik.apply(theta, array)``."""
+    global _ArgusLoglik
+    if _ArgusLoglik is None:
+        _ArgusLoglik = _autograd_function()
+    return _ArgusLoglik.apply(theta, array)

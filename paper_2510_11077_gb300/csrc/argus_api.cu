@@ -1,0 +1,563 @@
+// C ABI of the batched Kalman-filter likelihood (declared in include/argus.h).
+//
+// Host side only: validation, the device copy of the TOA data (the per-TOA
+// pre-stage), the schedule (work items sorted by TOA count, persistent grid
+// size, scratch slots), CUDA-graph capture and replay, and host-pointer
+// staging.  Every arithmetic step of the likelihood runs in kf_kernels.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/argus.h"
+#include "kf_internal.cuh"
+
+using namespace argus;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+argus_status fail(argus_status st, const std::string& msg) {
+    g_last_error = msg;
+    return st;
+}
+
+argus_status cuda_fail(cudaError_t e, const char* what) {
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    return fail(e == cudaErrorMemoryAllocation ? ARGUS_ERR_OOM : ARGUS_ERR_CUDA, m);
+}
+
+#define CK(call)                                         \
+    do {                                                 \
+        cudaError_t _e = (call);                         \
+        if (_e != cudaSuccess) return cuda_fail(_e, #call); \
+    } while (0)
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+template <class T>
+argus_status grow(T** p, size_t* cap, size_t need) {
+    if (need <= *cap && *p) return ARGUS_OK;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+    if (need == 0) return ARGUS_OK;
+    CK(cudaMalloc(reinterpret_cast<void**>(p), need * sizeof(T)));
+    *cap = need;
+    return ARGUS_OK;
+}
+
+struct GraphKey {
+    const double* theta;
+    int64_t B;
+    double* ll;
+    double* grad;
+    double* lane;
+    bool operator==(const GraphKey& o) const {
+        return theta == o.theta && B == o.B && ll == o.ll && grad == o.grad && lane == o.lane;
+    }
+};
+
+struct GraphEntry {
+    GraphKey key;
+    cudaGraphExec_t exec;
+    uint64_t last_use;
+};
+
+constexpr int kMaxGraphs = 8;
+
+}  // namespace
+
+struct argus_array {
+    int device = 0;
+    int n_sm = 0;
+    int P = 0;
+    int64_t total_toa = 0;
+    int32_t stride_max = 1;   // for the current plan
+    int32_t nseg_max = 0;
+    std::vector<PulsarDev> h_psr;
+    std::vector<double> h_p0;     // not used after create; kept for clarity
+    PulsarDev* d_psr = nullptr;
+    double* d_rec = nullptr;
+    argus_plan plan{};
+    // per-batch buffers
+    double* d_lc = nullptr;        size_t cap_lc = 0;
+    double* d_lane = nullptr;      size_t cap_lane = 0;
+    WorkItem* d_items = nullptr;   size_t cap_items = 0;
+    int64_t items_B = -1;
+    int items_W = 0;
+    int n_items = 0;
+    // adjoint scratch, one slot per resident block of the persistent grid
+    double* d_ckpt = nullptr;      size_t cap_ckpt = 0;
+    double* d_tape = nullptr;      size_t cap_tape = 0;
+    int* d_counter = nullptr;
+    // host staging
+    double* d_stage = nullptr;     size_t cap_stage = 0;
+    // graphs
+    cudaStream_t cap_stream = nullptr;
+    std::vector<GraphEntry> graphs;
+    uint64_t use_clock = 0;
+};
+
+namespace {
+
+void drop_graphs(argus_array* h) {
+    for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
+    h->graphs.clear();
+}
+
+argus_plan default_plan() {
+    argus_plan p{};
+    p.mode = ARGUS_MODE_BATCHED;
+    p.walkers_per_cta = 128;
+    p.ctas_per_sm = 4;
+    p.ckpt_stride = 0;
+    p.use_graph = 1;
+    return p;
+}
+
+argus_status validate_plan(const argus_plan* p) {
+    if (!p) return fail(ARGUS_ERR_INVALID_ARG, "plan is NULL");
+    if (p->mode != ARGUS_MODE_BATCHED && p->mode != ARGUS_MODE_PLAIN)
+        return fail(ARGUS_ERR_INVALID_ARG, "plan.mode must be BATCHED or PLAIN");
+    const int w = p->walkers_per_cta;
+    if (w != 32 && w != 64 && w != 128 && w != 256)
+        return fail(ARGUS_ERR_INVALID_ARG, "plan.walkers_per_cta must be 32, 64, 128 or 256");
+    if (p->ctas_per_sm < 1 || p->ctas_per_sm > 8)
+        return fail(ARGUS_ERR_INVALID_ARG, "plan.ctas_per_sm must be in 1..8");
+    if (p->ckpt_stride < 0 || p->ckpt_stride > kMaxStride)
+        return fail(ARGUS_ERR_INVALID_ARG, "plan.ckpt_stride must be in 0..256");
+    if (p->use_graph != 0 && p->use_graph != 1)
+        return fail(ARGUS_ERR_INVALID_ARG, "plan.use_graph must be 0 or 1");
+    for (int i = 0; i < 3; ++i)
+        if (p->reserved[i] != 0) return fail(ARGUS_ERR_INVALID_ARG, "plan.reserved must be 0");
+    return ARGUS_OK;
+}
+
+// Segment length of the adjoint for a pulsar with n TOAs.
+int stride_for(int64_t n, int ckpt_stride) {
+    int c = ckpt_stride;
+    if (c == 0) c = int(std::ceil(std::sqrt(double(std::max<int64_t>(n, 1)))));
+    return std::max(1, std::min(c, kMaxStride));
+}
+
+// Re-derive per-pulsar strides for the plan and upload the pulsar table.
+argus_status apply_plan(argus_array* h) {
+    h->stride_max = 1;
+    h->nseg_max = 0;
+    for (auto& ps : h->h_psr) {
+        ps.stride = stride_for(ps.n, h->plan.ckpt_stride);
+        ps.nseg = int((ps.n + ps.stride - 1) / ps.stride);
+        h->stride_max = std::max(h->stride_max, ps.stride);
+        h->nseg_max = std::max(h->nseg_max, ps.nseg);
+    }
+    CK(cudaMemcpy(h->d_psr, h->h_psr.data(), sizeof(PulsarDev) * h->P, cudaMemcpyHostToDevice));
+    drop_graphs(h);
+    h->items_B = -1;
+    return ARGUS_OK;
+}
+
+// Work items (pulsar, walker tile), pulsars with the most TOAs first.
+argus_status ensure_items(argus_array* h, int64_t B, int W) {
+    if (h->items_B == B && h->items_W == W) return ARGUS_OK;
+    std::vector<int> order(h->P);
+    for (int p = 0; p < h->P; ++p) order[p] = p;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return h->h_psr[a].n > h->h_psr[b].n; });
+    std::vector<WorkItem> items;
+    const int64_t tiles = (B + W - 1) / W;
+    items.reserve(size_t(tiles) * h->P);
+    for (int p : order)
+        for (int64_t t = 0; t < tiles; ++t) items.push_back(WorkItem{p, int32_t(t * W)});
+    if (items.size() > size_t(INT32_MAX)) return fail(ARGUS_ERR_UNSUPPORTED, "too many work items");
+    argus_status st = grow(&h->d_items, &h->cap_items, items.size());
+    if (st) return st;
+    if (!items.empty())
+        CK(cudaMemcpy(h->d_items, items.data(), sizeof(WorkItem) * items.size(),
+                      cudaMemcpyHostToDevice));
+    h->n_items = int(items.size());
+    h->items_B = B;
+    h->items_W = W;
+    drop_graphs(h);
+    return ARGUS_OK;
+}
+
+int grid_for(const argus_array* h, int n_items) {
+    const int g = h->n_sm * h->plan.ctas_per_sm;
+    return std::max(1, std::min(g, n_items));
+}
+
+// Buffers for a batch of B walkers; reallocation invalidates captured graphs.
+argus_status ensure_batch(argus_array* h, int64_t B, int W, int grid, bool grad) {
+    const size_t lanes = size_t(B) * h->P;
+    void* before[4] = {h->d_lc, h->d_lane, h->d_ckpt, h->d_tape};
+    argus_status st;
+    if ((st = grow(&h->d_lc, &h->cap_lc, lanes * kLaneConsts))) return st;
+    if ((st = grow(&h->d_lane, &h->cap_lane, lanes * (1 + kLaneGrads)))) return st;
+    if (grad) {
+        const size_t ck = size_t(h->nseg_max) * kCkptDoubles * W * grid;
+        const size_t tp = size_t(h->stride_max) * kTapeDoubles * W * grid;
+        if ((st = grow(&h->d_ckpt, &h->cap_ckpt, std::max<size_t>(ck, 1)))) return st;
+        if ((st = grow(&h->d_tape, &h->cap_tape, std::max<size_t>(tp, 1)))) return st;
+    }
+    void* after[4] = {h->d_lc, h->d_lane, h->d_ckpt, h->d_tape};
+    if (memcmp(before, after, sizeof(before)) != 0) drop_graphs(h);
+    return ARGUS_OK;
+}
+
+FilterArgs make_args(argus_array* h, int64_t B, int W, int grid, bool persistent) {
+    FilterArgs a{};
+    a.rec = h->d_rec;
+    a.psr = h->d_psr;
+    a.items = h->d_items;
+    a.n_items = h->n_items;
+    a.P = h->P;
+    a.B = B;
+    a.lc = h->d_lc;
+    a.lane_out = h->d_lane;
+    a.ckpt = h->d_ckpt;
+    a.tape = h->d_tape;
+    a.ckpt_slot = int64_t(h->nseg_max) * kCkptDoubles * W;
+    a.tape_slot = int64_t(h->stride_max) * kTapeDoubles * W;
+    a.stride_max = h->stride_max;
+    a.counter = persistent ? h->d_counter : nullptr;
+    (void)grid;
+    return a;
+}
+
+// Enqueue one batched evaluation: K1 -> K2 or K3 -> K4.
+argus_status enqueue_batched(argus_array* h, const double* theta, int64_t B, double* ll,
+                             double* grad, double* lane, cudaStream_t s) {
+    const bool want_grad = grad != nullptr;
+    const int W = h->plan.walkers_per_cta;
+    const int grid = grid_for(h, h->n_items);
+    CK(cudaMemsetAsync(h->d_counter, 0, sizeof(int), s));
+    launch_project(theta, B, h->P, h->d_psr, h->d_lc, s);
+    FilterArgs a = make_args(h, B, W, grid, true);
+    if (want_grad) launch_filter_grad(a, W, grid, s);
+    else launch_filter_fwd(a, W, grid, s);
+    launch_reduce(theta, B, h->P, h->d_psr, h->d_lane, ll, grad, lane, s);
+    CK(cudaGetLastError());
+    return ARGUS_OK;
+}
+
+argus_status run_batched(argus_array* h, const double* theta, int64_t B, double* ll, double* grad,
+                         double* lane, cudaStream_t s) {
+    const int W = h->plan.walkers_per_cta;
+    argus_status st;
+    if ((st = ensure_items(h, B, W))) return st;
+    const int grid = grid_for(h, h->n_items);
+    if ((st = ensure_batch(h, B, W, grid, grad != nullptr))) return st;
+    if (!h->plan.use_graph) return enqueue_batched(h, theta, B, ll, grad, lane, s);
+
+    GraphKey key{theta, B, ll, grad, lane};
+    for (auto& g : h->graphs) {
+        if (g.key == key) {
+            g.last_use = ++h->use_clock;
+            CK(cudaGraphLaunch(g.exec, s));
+            return ARGUS_OK;
+        }
+    }
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    st = enqueue_batched(h, theta, B, ll, grad, lane, h->cap_stream);
+    cudaError_t ce = cudaStreamEndCapture(h->cap_stream, &graph);
+    if (st) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
+    cudaGraphExec_t exec = nullptr;
+    ce = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaGraphInstantiate");
+    if (int(h->graphs.size()) >= kMaxGraphs) {
+        auto old = std::min_element(h->graphs.begin(), h->graphs.end(),
+                                    [](const GraphEntry& a, const GraphEntry& b) {
+                                        return a.last_use < b.last_use;
+                                    });
+        cudaGraphExecDestroy(old->exec);
+        h->graphs.erase(old);
+    }
+    h->graphs.push_back(GraphEntry{key, exec, ++h->use_clock});
+    CK(cudaGraphLaunch(exec, s));
+    return ARGUS_OK;
+}
+
+// The comparison point: the same kernels, one parameter vector per launch.
+argus_status run_plain(argus_array* h, const double* theta, int64_t B, double* ll, double* grad,
+                       double* lane, cudaStream_t s) {
+    const int W = 32;
+    const int D = kNgw + 2 * h->P;
+    argus_status st;
+    if ((st = ensure_items(h, 1, W))) return st;
+    const int grid = h->n_items;
+    if ((st = ensure_batch(h, 1, W, grid, grad != nullptr))) return st;
+    FilterArgs a = make_args(h, 1, W, grid, false);
+    for (int64_t b = 0; b < B; ++b) {
+        const double* th = theta + b * D;
+        launch_project(th, 1, h->P, h->d_psr, h->d_lc, s);
+        if (grad) launch_filter_grad(a, W, grid, s);
+        else launch_filter_fwd(a, W, grid, s);
+        launch_reduce(th, 1, h->P, h->d_psr, h->d_lane, ll ? ll + b : nullptr,
+                      grad ? grad + b * D : nullptr, lane ? lane + b * h->P : nullptr, s);
+    }
+    CK(cudaGetLastError());
+    return ARGUS_OK;
+}
+
+bool is_device_ptr(const void* p) {
+    if (!p) return true;
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();   // clear the sticky-free error of an unknown pointer
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Evaluate with any mix of host and device pointers.
+argus_status evaluate(argus_array* h, const double* theta, int64_t B, double* ll, double* grad,
+                      double* lane, void* stream) {
+    if (!h) return fail(ARGUS_ERR_INVALID_ARG, "array handle is NULL");
+    if (B < 0) return fail(ARGUS_ERR_INVALID_ARG, "B must be >= 0");
+    if (B == 0) return ARGUS_OK;
+    if (!theta) return fail(ARGUS_ERR_INVALID_ARG, "theta is NULL");
+    if (B > (int64_t(1) << 31) / std::max(1, h->P))
+        return fail(ARGUS_ERR_UNSUPPORTED, "B x P exceeds 2^31 lanes");
+    DeviceGuard guard(h->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int D = kNgw + 2 * h->P;
+    const bool dev_in = is_device_ptr(theta);
+    const bool dev_ll = is_device_ptr(ll), dev_g = is_device_ptr(grad), dev_l = is_device_ptr(lane);
+    const bool staged = !(dev_in && dev_ll && dev_g && dev_l);
+    const double* th_d = theta;
+    double *ll_d = ll, *g_d = grad, *lane_d = lane;
+    if (staged) {
+        const size_t need = size_t(B) * (2 * D + 1 + h->P);
+        argus_status st = grow(&h->d_stage, &h->cap_stage, need);
+        if (st) return st;
+        double* base = h->d_stage;
+        if (!dev_in) {
+            CK(cudaMemcpyAsync(base, theta, sizeof(double) * B * D, cudaMemcpyHostToDevice, s));
+            th_d = base;
+        }
+        base += size_t(B) * D;
+        if (ll && !dev_ll) ll_d = base;
+        base += B;
+        if (grad && !dev_g) g_d = base;
+        base += size_t(B) * D;
+        if (lane && !dev_l) lane_d = base;
+    }
+    argus_status st = (h->plan.mode == ARGUS_MODE_PLAIN)
+                          ? run_plain(h, th_d, B, ll_d, g_d, lane_d, s)
+                          : run_batched(h, th_d, B, ll_d, g_d, lane_d, s);
+    if (st) return st;
+    if (staged) {
+        if (ll && !dev_ll)
+            CK(cudaMemcpyAsync(ll, ll_d, sizeof(double) * B, cudaMemcpyDeviceToHost, s));
+        if (grad && !dev_g)
+            CK(cudaMemcpyAsync(grad, g_d, sizeof(double) * B * D, cudaMemcpyDeviceToHost, s));
+        if (lane && !dev_l)
+            CK(cudaMemcpyAsync(lane, lane_d, sizeof(double) * B * h->P, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    return ARGUS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+argus_status argus_array_create(const argus_pulsar* psrs, int32_t n_pulsars, int32_t device,
+                                argus_array** out) {
+    if (!out) return fail(ARGUS_ERR_INVALID_ARG, "out is NULL");
+    if (!psrs || n_pulsars < 1) return fail(ARGUS_ERR_INVALID_ARG, "need at least one pulsar");
+    if (device < 0) return fail(ARGUS_ERR_INVALID_ARG, "device must be >= 0");
+    int64_t total = 0;
+    for (int p = 0; p < n_pulsars; ++p) {
+        const argus_pulsar& ps = psrs[p];
+        char buf[160];
+        if (ps.n_toa < 0 || ps.n_toa > INT32_MAX) {
+            snprintf(buf, sizeof buf, "pulsar %d: n_toa out of range", p);
+            return fail(ARGUS_ERR_INVALID_ARG, buf);
+        }
+        if (ps.n_toa > 0 && (!ps.t || !ps.r || !ps.sigma)) {
+            snprintf(buf, sizeof buf, "pulsar %d: NULL data", p);
+            return fail(ARGUS_ERR_INVALID_ARG, buf);
+        }
+        for (int64_t k = 0; k < ps.n_toa; ++k) {
+            if (!std::isfinite(ps.t[k]) || !std::isfinite(ps.r[k]) || !std::isfinite(ps.sigma[k]) ||
+                !(ps.sigma[k] > 0.0) || (k > 0 && ps.t[k] < ps.t[k - 1])) {
+                snprintf(buf, sizeof buf, "pulsar %d TOA %lld: non-finite, unsorted or sigma <= 0", p,
+                         (long long)k);
+                return fail(ARGUS_ERR_INVALID_ARG, buf);
+            }
+        }
+        const double nrm = std::sqrt(ps.pos[0] * ps.pos[0] + ps.pos[1] * ps.pos[1] + ps.pos[2] * ps.pos[2]);
+        if (!(std::fabs(nrm - 1.0) <= 1e-6)) {
+            snprintf(buf, sizeof buf, "pulsar %d: position is not a unit vector", p);
+            return fail(ARGUS_ERR_INVALID_ARG, buf);
+        }
+        if (!(ps.equad >= 0.0) || !std::isfinite(ps.equad)) {
+            snprintf(buf, sizeof buf, "pulsar %d: EQUAD must be finite and >= 0", p);
+            return fail(ARGUS_ERR_INVALID_ARG, buf);
+        }
+        if (!(ps.p0[0] >= 0.0 && ps.p0[2] >= 0.0 && ps.p0[0] * ps.p0[2] >= ps.p0[1] * ps.p0[1]) ||
+            !std::isfinite(ps.p0[1])) {
+            snprintf(buf, sizeof buf, "pulsar %d: prior covariance is not positive semi-definite", p);
+            return fail(ARGUS_ERR_INVALID_ARG, buf);
+        }
+        total += ps.n_toa;
+    }
+    // host validation is complete; now the device
+    int ndev = 0;
+    CK(cudaGetDeviceCount(&ndev));
+    if (device >= ndev) return fail(ARGUS_ERR_INVALID_ARG, "no such device");
+    cudaDeviceProp prop{};
+    CK(cudaGetDeviceProperties(&prop, device));
+    if (prop.major != 10 || prop.minor != 3)
+        return fail(ARGUS_ERR_UNSUPPORTED, std::string("built for sm_103a, device is ") + prop.name);
+
+    DeviceGuard guard(device);
+    argus_array* h = new argus_array();
+    h->device = device;
+    h->n_sm = prop.multiProcessorCount;
+    h->P = n_pulsars;
+    h->total_toa = total;
+    h->plan = default_plan();
+    h->h_psr.resize(n_pulsars);
+
+    // A0 pre-stage: per-TOA records [t, dt, dt^2/2, dt^3/3, r, sigma^2, dt^2, 0]
+    std::vector<double> rec(size_t(std::max<int64_t>(total, 1)) * kRecDoubles, 0.0);
+    int64_t off = 0;
+    for (int p = 0; p < n_pulsars; ++p) {
+        const argus_pulsar& ps = psrs[p];
+        PulsarDev& d = h->h_psr[p];
+        d.off = off;
+        d.n = int32_t(ps.n_toa);
+        for (int i = 0; i < 3; ++i) d.pos[i] = ps.pos[i];
+        d.equad2 = ps.equad * ps.equad;
+        for (int i = 0; i < 3; ++i) d.p0[i] = ps.p0[i];
+        for (int64_t k = 0; k < ps.n_toa; ++k) {
+            double* q = rec.data() + (off + k) * kRecDoubles;
+            const double dt = (k == 0) ? 0.0 : ps.t[k] - ps.t[k - 1];
+            q[0] = ps.t[k];
+            q[1] = dt;
+            q[2] = dt * dt / 2.0;
+            q[3] = dt * dt * dt / 3.0;
+            q[4] = ps.r[k];
+            q[5] = ps.sigma[k] * ps.sigma[k];
+            q[6] = dt * dt;
+            q[7] = 0.0;
+        }
+        off += ps.n_toa;
+    }
+    auto cleanup = [&](argus_status st) {
+        argus_array_destroy(h);
+        return st;
+    };
+    cudaError_t e;
+    if ((e = cudaMalloc(&h->d_rec, rec.size() * sizeof(double))) != cudaSuccess)
+        return cleanup(cuda_fail(e, "cudaMalloc(records)"));
+    if ((e = cudaMemcpy(h->d_rec, rec.data(), rec.size() * sizeof(double), cudaMemcpyHostToDevice)) !=
+        cudaSuccess)
+        return cleanup(cuda_fail(e, "cudaMemcpy(records)"));
+    if ((e = cudaMalloc(&h->d_psr, sizeof(PulsarDev) * n_pulsars)) != cudaSuccess)
+        return cleanup(cuda_fail(e, "cudaMalloc(pulsars)"));
+    if ((e = cudaMalloc(&h->d_counter, sizeof(int))) != cudaSuccess)
+        return cleanup(cuda_fail(e, "cudaMalloc(counter)"));
+    if ((e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
+        return cleanup(cuda_fail(e, "cudaStreamCreate"));
+    argus_status st = apply_plan(h);
+    if (st) return cleanup(st);
+    *out = h;
+    return ARGUS_OK;
+}
+
+void argus_array_destroy(argus_array* h) {
+    if (!h) return;
+    DeviceGuard guard(h->device);
+    cudaDeviceSynchronize();
+    drop_graphs(h);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    cudaFree(h->d_rec);
+    cudaFree(h->d_psr);
+    cudaFree(h->d_lc);
+    cudaFree(h->d_lane);
+    cudaFree(h->d_items);
+    cudaFree(h->d_ckpt);
+    cudaFree(h->d_tape);
+    cudaFree(h->d_counter);
+    cudaFree(h->d_stage);
+    delete h;
+}
+
+int32_t argus_array_dim(const argus_array* h) { return h ? kNgw + 2 * h->P : -1; }
+
+argus_status argus_array_set_plan(argus_array* h, const argus_plan* plan) {
+    if (!h) return fail(ARGUS_ERR_INVALID_ARG, "array handle is NULL");
+    argus_status st = validate_plan(plan);
+    if (st) return st;
+    DeviceGuard guard(h->device);
+    CK(cudaDeviceSynchronize());
+    h->plan = *plan;
+    return apply_plan(h);
+}
+
+argus_status argus_array_get_plan(const argus_array* h, argus_plan* plan) {
+    if (!h || !plan) return fail(ARGUS_ERR_INVALID_ARG, "NULL argument");
+    *plan = h->plan;
+    return ARGUS_OK;
+}
+
+argus_status argus_loglik(argus_array* h, const double* theta, int64_t B, double* loglik,
+                          void* stream) {
+    if (B > 0 && !loglik) return fail(ARGUS_ERR_INVALID_ARG, "loglik is NULL");
+    return evaluate(h, theta, B, loglik, nullptr, nullptr, stream);
+}
+
+argus_status argus_loglik_grad(argus_array* h, const double* theta, int64_t B, double* loglik,
+                               double* grad, void* stream) {
+    if (B > 0 && (!loglik || !grad)) return fail(ARGUS_ERR_INVALID_ARG, "loglik or grad is NULL");
+    return evaluate(h, theta, B, loglik, grad, nullptr, stream);
+}
+
+argus_status argus_lane_loglik(argus_array* h, const double* theta, int64_t B, double* lane_ll,
+                               void* stream) {
+    if (B > 0 && !lane_ll) return fail(ARGUS_ERR_INVALID_ARG, "lane_ll is NULL");
+    return evaluate(h, theta, B, nullptr, nullptr, lane_ll, stream);
+}
+
+const char* argus_status_string(argus_status s) {
+    switch (s) {
+        case ARGUS_OK: return "ARGUS_OK";
+        case ARGUS_ERR_INVALID_ARG: return "ARGUS_ERR_INVALID_ARG";
+        case ARGUS_ERR_CUDA: return "ARGUS_ERR_CUDA";
+        case ARGUS_ERR_OOM: return "ARGUS_ERR_OOM";
+        case ARGUS_ERR_NONFINITE: return "ARGUS_ERR_NONFINITE";
+        case ARGUS_ERR_TIMEOUT: return "ARGUS_ERR_TIMEOUT";
+        case ARGUS_ERR_UNSUPPORTED: return "ARGUS_ERR_UNSUPPORTED";
+    }
+    return "ARGUS_ERR_UNKNOWN";
+}
+
+const char* argus_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

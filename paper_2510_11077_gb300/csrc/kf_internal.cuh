@@ -1,0 +1,67 @@
+// Internal declarations shared by the C-ABI layer and the filter kernels.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace argus {
+
+constexpr int kNgw = 7;          // continuous-wave parameters at the head of theta
+constexpr int kRecDoubles = 8;   // doubles per staged TOA record
+constexpr int kCkptDoubles = 5;  // (m0, m1, p00, p01, p11) per checkpoint
+constexpr int kTapeDoubles = 6;  // (M00, M01, 1/S, e, sin, cos) per step of a segment
+constexpr int kMaxStride = 256;  // longest adjoint segment, in TOAs
+constexpr int kLaneConsts = 7;   // A, B, f, Phi0/(2 pi), sigma^2, EFAC^2, EFAC
+constexpr int kLaneGrads = 6;    // dll/dA, dB, dPhi0, dOmega, dsigma^2, EFAC term
+
+// One staged TOA record (8 doubles = 64 bytes, 16-byte aligned):
+//   [0] t  [1] dt  [2] dt^2/2  [3] dt^3/3  [4] r  [5] sigma^2  [6] dt^2  [7] 0
+struct PulsarDev {
+    int64_t off;      // first record of this pulsar
+    int32_t n;        // TOAs
+    int32_t stride;   // adjoint checkpoint stride (TOAs per segment)
+    int32_t nseg;     // ceil(n / stride)
+    int32_t pad;
+    double pos[3];    // unit vector
+    double equad2;    // EQUAD^2
+    double p0[3];     // prior covariance rr, ry, yy
+};
+
+struct WorkItem {
+    int32_t p;        // pulsar
+    int32_t b0;       // first walker of the tile
+};
+
+struct FilterArgs {
+    const double* rec;        // [sum N][8]
+    const PulsarDev* psr;     // [P]
+    const WorkItem* items;    // [n_items], largest pulsars first
+    int32_t n_items;
+    int32_t P;
+    int64_t B;
+    const double* lc;         // lane constants [7][P][B]
+    double* lane_out;         // [1 + 6][P][B]: ll, then the gradient terms
+    double* ckpt;             // per block slot: [nseg_max][5][W]
+    double* tape;             // per block slot: [stride_max][6][W]
+    int64_t ckpt_slot;        // doubles per block slot in ckpt
+    int64_t tape_slot;        // doubles per block slot in tape
+    int32_t stride_max;       // longest segment of any pulsar (shared-memory records)
+    int32_t pad;
+    int* counter;             // persistent work counter (nullptr: one item per block)
+};
+
+// K1: theta [B][D] -> lane constants [7][P][B].
+void launch_project(const double* theta, int64_t B, int32_t P, const PulsarDev* psr,
+                    double* lc, cudaStream_t s);
+// K2: forward filter, ll per lane -> lane_out[0][P][B].
+void launch_filter_fwd(const FilterArgs& a, int W, int grid, cudaStream_t s);
+// K3: forward with checkpoints + reverse sweep -> lane_out[0..6][P][B].
+void launch_filter_grad(const FilterArgs& a, int W, int grid, cudaStream_t s);
+// K4: deterministic sum over pulsars (and chain rule through K1 for grad).
+void launch_reduce(const double* theta, int64_t B, int32_t P, const PulsarDev* psr,
+                   const double* lane_out, double* loglik, double* grad, double* lane_ll,
+                   cudaStream_t s);
+// shared-memory bytes a filter block needs
+size_t filter_smem_bytes(bool grad, int stride_max);
+
+}  // namespace argus
