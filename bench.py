@@ -1,0 +1,332 @@
+#!/usr/bin/env python
+"""Benchmark of the batched FP64 Kalman-filter log-likelihood + gradient.
+
+One step = one evaluation of loglik and its full gradient for a whole batch of
+parameter vectors (K1 projection -> K3 checkpointed adjoint filter -> K4
+reduction), with the batch's inputs resident in HBM.  Metric: loglik+grad
+evaluations (parameter vectors) per second, whole job.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload NAME]
+
+Default workload: 100 pulsars, log-normal TOA counts (median 3000, clipped to
+[200, 20000], 449,398 TOAs), 16384 walkers, D = 207, FP64.  Multi-GPU runs
+(torchrun) give each rank its own 16384 walkers (weak scaling, no collective
+on the data path).  Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "loglik+grad evals/s on 1 GB300, batched vs plain filter; % FP64/HBM roofline"
+UNIT = "evals/s"
+DEFAULT_WORKLOAD = "psr100_toalognormal_w16384"
+# FP64 peak derived from the part's unit counts and clock: 2 FP64 FMA per
+# clock per SM x 2 flop x 152 SMs x 2.07 GHz = 1.2586 TFLOP/s (the nominal
+# 1.25 TFLOP/s of a GB300).
+FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.07e9 / 1e12
+# Algorithmic FP64 flops per lane-step of the gradient kernel: the forward
+# recursion counts 40 flops per TOA (predict 6 FMA + 2 add, signal and
+# innovation 4 FMA + 2 add, update 1 rcp + 2 mul + 5 FMA + 2 quad, FMA = 2
+# flops, transcendentals not counted); forward + recompute + adjoint = 3x.
+FLOPS_PER_LANE_STEP_GRAD = 120
+L2_FLUSH_BYTES = 256 << 20
+CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--plain-walkers", type=int, default=8)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={CLOCK_QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.idx)],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(f[1]), max=float(f[2]), reasons=f[4:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        seen = sorted({n for r in rows for n, v in zip(names, r["reasons"][1:]) if v == "Active"})
+        return {"sm_mhz": statistics.median(r["sm"] for r in rows),
+                "sm_max_mhz": max(r["max"] for r in rows),
+                "reasons": seen, "samples": len(rows)}
+
+
+def traffic_record(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel
+    source is unchanged since the counters were taken; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    rec = json.load(open(path)).get(kernel)
+    if not rec:
+        return None
+    src = os.path.join(ROOT, "paper_2510_11077_gb300", "csrc", "kf_kernels.cu")
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    return rec if rec.get("source_sha") == h else None
+
+
+def cpu_baseline(data, theta, seconds):
+    """The CPU oracle as it stands on this host's cores, on a bounded sample."""
+    from oracle import kalman
+    cores = os.cpu_count() or 1
+    kalman.set_threads(cores)
+    done, t0, i = 0, time.perf_counter(), 0
+    while time.perf_counter() - t0 < seconds:
+        rows = theta[i % len(theta): i % len(theta) + cores]
+        kalman.loglik_grad(data, rows)
+        done += len(rows)
+        i += cores
+    dt = time.perf_counter() - t0
+    return {"value": done / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{done} walkers of the same workload (complex-step gradient, OpenMP over "
+                      f"walkers), {dt:.1f} s"}
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from oracle import kalman
+    from paper_2510_11077_gb300 import inputs
+    w = inputs.WORKLOADS[args.workload]
+    data = inputs.make_workload_array(w.name)
+    theta = inputs.make_theta_batch(data, w.batch, seed=w.seed)
+    cores = os.cpu_count() or 1
+    kalman.set_threads(cores)
+    per_step = cores * 2
+    for i in range(args.warmup):
+        kalman.loglik_grad(data, theta[:per_step])
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        kalman.loglik_grad(data, theta[i * per_step:(i + 1) * per_step])
+    dt = time.perf_counter() - t0
+    value = args.steps * per_step / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "pulsars": data.n_pulsars, "toas": int(data.n_toa.sum()),
+                       "batch": w.batch, "dim": data.dim,
+                       "step": f"{per_step} walkers of the batch per step (bounded CPU sample)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{per_step} walkers per step, {args.steps} steps"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_2510_11077_gb300 import argus, inputs
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend="nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = inputs.WORKLOADS[args.workload]
+    data = inputs.make_workload_array(w.name)
+    B, D = w.batch, data.dim
+    theta_np = inputs.make_theta_batch(data, B, seed=w.seed + 7919 * rank)
+    theta = torch.from_numpy(theta_np).to(dev)
+    arr = argus.Array(data, device=local)
+    plan = arr.get_plan()
+    ll = torch.empty(B, dtype=torch.float64, device=dev)
+    g = torch.empty((B, D), dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        argus.argus_loglik_grad(arr, theta, ll, g)
+
+    arr.set_timing(True)
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize(dev)
+
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    gpu_index = vis.split(",")[local] if vis else str(local)
+    clocks = ClockSampler(gpu_index) if rank == 0 else None
+    if clocks:
+        clocks.start()
+        time.sleep(0.3)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    kern = []
+    for k in range(args.steps):
+        flush.zero_()                       # evict L2 between timed steps (not timed)
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+        kern.append(arr.get_timing())
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop() if clocks else None
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * B * args.steps / (total_ms / 1e3)
+    filt_ms = statistics.mean(k[1] for k in kern)
+
+    # end to end through the public call with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        th_h = torch.from_numpy(theta_np).pin_memory()
+        ll_h = torch.empty(B, dtype=torch.float64).pin_memory()
+        g_h = torch.empty((B, D), dtype=torch.float64).pin_memory()
+        arr.set_timing(False)
+        argus.argus_loglik_grad(arr, th_h, ll_h, g_h)      # capture the staged graph
+        if world > 1:
+            torch.distributed.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            argus.argus_loglik_grad(arr, th_h, ll_h, g_h)   # H2D, compute, D2H, sync
+        e2e_s = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = {"value": world * B * args.steps / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": B * D * 8, "d2h_bytes_per_step": B * 8 + B * D * 8}
+        if not np.allclose(ll_h.numpy(), ll.cpu().numpy(), rtol=0, atol=0, equal_nan=True):
+            raise RuntimeError("host-buffer path disagrees with the device path")
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return 0
+
+    # the same math launched once per parameter vector, on a sample of walkers
+    n_plain = min(args.plain_walkers, B)
+    arr_p = argus.Array(data, device=local)
+    arr_p.set_plan(mode=argus.ARGUS_MODE_PLAIN)
+    th_p = theta[:n_plain].contiguous()
+    llp = torch.empty(n_plain, dtype=torch.float64, device=dev)
+    gp = torch.empty((n_plain, D), dtype=torch.float64, device=dev)
+    argus.argus_loglik_grad(arr_p, th_p[:2].contiguous(), llp[:2], gp[:2])
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    argus.argus_loglik_grad(arr_p, th_p, llp, gp)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    plain = {"value": n_plain / (e0.elapsed_time(e1) / 1e3), "unit": UNIT,
+             "sample_walkers": n_plain, "launches_per_walker": 3}
+    if not torch.equal(llp, ll[:n_plain]):
+        raise RuntimeError("plain and batched filters disagree")
+    arr_p.close()
+
+    lane_steps = B * int(data.n_toa.sum())
+    achieved = FLOPS_PER_LANE_STEP_GRAD * lane_steps / (filt_ms * 1e-3) / 1e12
+    tr = traffic_record("k_filter_grad")
+    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS,
+                "traffic": tr["dram_bytes_per_launch"] if tr else None,
+                "kernel": "k_filter_grad", "kernel_ms": filt_ms,
+                "peak_source": "derived: 2 FP64 FMA/clk/SM x 152 SMs x 2.07 GHz",
+                "algorithmic": f"{FLOPS_PER_LANE_STEP_GRAD} FP64 flop per lane-step x "
+                               f"{lane_steps} lane-steps per launch"}
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(data, theta_np, args.cpu_seconds)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": w.name, "pulsars": data.n_pulsars,
+                       "toas": int(data.n_toa.sum()), "batch_per_gpu": B, "dim": D,
+                       "lane_steps_per_gpu": lane_steps, "plan": plan,
+                       "l2": "flushed between timed steps (256 MiB write, untimed)"},
+            "e2e": e2e, "gpu_launches": 3 * args.steps, "roofline": roofline,
+            "plain_filter": plain, "batched_over_plain": value / world / plain["value"],
+            "stage_ms": {"project": statistics.mean(k[0] for k in kern), "filter": filt_ms,
+                         "reduce": statistics.mean(k[2] for k in kern)},
+            "clocks": clk, "cpu_baseline": cpu}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

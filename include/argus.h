@@ -122,6 +122,16 @@ argus_status argus_loglik_grad(argus_array* array, const double* theta, int64_t 
 argus_status argus_lane_loglik(argus_array* array, const double* theta, int64_t B,
                                double* lane_ll, void* stream);
 
+/* Kernel timing, for measurement.  With timing enabled (default off) every
+ * batched call records CUDA events around its three stages on its stream
+ * (captured graphs include them); argus_array_get_timing waits for the last
+ * call and writes its stage durations in milliseconds to ms[3] =
+ * {projection (K1), filter (K2 or K3), reduction (K4)}.  Enabling or
+ * disabling drops captured graphs.  ARGUS_ERR_INVALID_ARG if no timed call
+ * has run since timing was enabled. */
+argus_status argus_array_set_timing(argus_array* array, int32_t enable);
+argus_status argus_array_get_timing(argus_array* array, float* ms);
+
 /* Human-readable name of a status, and the message of the last error raised
  * on the calling host thread ("" if none). */
 const char* argus_status_string(argus_status status);

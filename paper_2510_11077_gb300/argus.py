@@ -85,6 +85,10 @@ def load(build_if_missing: bool = False):
     lib.argus_loglik_grad.restype = ctypes.c_int
     lib.argus_lane_loglik.argtypes = [vp, dp, ctypes.c_int64, dp, vp]
     lib.argus_lane_loglik.restype = ctypes.c_int
+    lib.argus_array_set_timing.argtypes = [vp, ctypes.c_int32]
+    lib.argus_array_set_timing.restype = ctypes.c_int
+    lib.argus_array_get_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
+    lib.argus_array_get_timing.restype = ctypes.c_int
     lib.argus_status_string.argtypes = [ctypes.c_int]
     lib.argus_status_string.restype = ctypes.c_char_p
     lib.argus_last_error.argtypes = []
@@ -152,6 +156,15 @@ class Array:
             self.close()
         except Exception:
             pass
+
+    def set_timing(self, enable: bool) -> None:
+        _check(_lib.argus_array_set_timing(self.handle, int(bool(enable))))
+
+    def get_timing(self):
+        """(K1, filter, K4) durations of the last timed call, milliseconds."""
+        ms = (ctypes.c_float * 3)()
+        _check(_lib.argus_array_get_timing(self.handle, ms))
+        return tuple(ms)
 
     def get_plan(self) -> dict:
         p = ArgusPlan()

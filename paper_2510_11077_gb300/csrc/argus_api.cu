@@ -92,7 +92,6 @@ struct argus_array {
     int32_t stride_max = 1;   // for the current plan
     int32_t nseg_max = 0;
     std::vector<PulsarDev> h_psr;
-    std::vector<double> h_p0;     // not used after create; kept for clarity
     PulsarDev* d_psr = nullptr;
     double* d_rec = nullptr;
     argus_plan plan{};
@@ -113,6 +112,10 @@ struct argus_array {
     cudaStream_t cap_stream = nullptr;
     std::vector<GraphEntry> graphs;
     uint64_t use_clock = 0;
+    // stage timing (argus_array_set_timing)
+    bool timing = false;
+    bool timed_once = false;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
 };
 
 namespace {
@@ -248,11 +251,18 @@ argus_status enqueue_batched(argus_array* h, const double* theta, int64_t B, dou
     const int W = h->plan.walkers_per_cta;
     const int grid = grid_for(h, h->n_items);
     CK(cudaMemsetAsync(h->d_counter, 0, sizeof(int), s));
+    if (h->timing) CK(cudaEventRecordWithFlags(h->ev[0], s, cudaEventRecordExternal));
     launch_project(theta, B, h->P, h->d_psr, h->d_lc, s);
+    if (h->timing) CK(cudaEventRecordWithFlags(h->ev[1], s, cudaEventRecordExternal));
     FilterArgs a = make_args(h, B, W, grid, true);
     if (want_grad) launch_filter_grad(a, W, grid, s);
     else launch_filter_fwd(a, W, grid, s);
+    if (h->timing) CK(cudaEventRecordWithFlags(h->ev[2], s, cudaEventRecordExternal));
     launch_reduce(theta, B, h->P, h->d_psr, h->d_lane, ll, grad, lane, s);
+    if (h->timing) {
+        CK(cudaEventRecordWithFlags(h->ev[3], s, cudaEventRecordExternal));
+        h->timed_once = true;
+    }
     CK(cudaGetLastError());
     return ARGUS_OK;
 }
@@ -496,6 +506,8 @@ void argus_array_destroy(argus_array* h) {
     DeviceGuard guard(h->device);
     cudaDeviceSynchronize();
     drop_graphs(h);
+    for (auto& e : h->ev)
+        if (e) cudaEventDestroy(e);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     cudaFree(h->d_rec);
     cudaFree(h->d_psr);
@@ -543,6 +555,27 @@ argus_status argus_lane_loglik(argus_array* h, const double* theta, int64_t B, d
                                void* stream) {
     if (B > 0 && !lane_ll) return fail(ARGUS_ERR_INVALID_ARG, "lane_ll is NULL");
     return evaluate(h, theta, B, nullptr, nullptr, lane_ll, stream);
+}
+
+argus_status argus_array_set_timing(argus_array* h, int32_t enable) {
+    if (!h) return fail(ARGUS_ERR_INVALID_ARG, "array handle is NULL");
+    DeviceGuard guard(h->device);
+    if (enable && !h->ev[0])
+        for (auto& e : h->ev) CK(cudaEventCreate(&e));
+    h->timing = enable != 0;
+    h->timed_once = false;
+    drop_graphs(h);
+    return ARGUS_OK;
+}
+
+argus_status argus_array_get_timing(argus_array* h, float* ms) {
+    if (!h || !ms) return fail(ARGUS_ERR_INVALID_ARG, "NULL argument");
+    if (!h->timing || !h->timed_once)
+        return fail(ARGUS_ERR_INVALID_ARG, "no timed call since timing was enabled");
+    DeviceGuard guard(h->device);
+    CK(cudaEventSynchronize(h->ev[3]));
+    for (int i = 0; i < 3; ++i) CK(cudaEventElapsedTime(&ms[i], h->ev[i], h->ev[i + 1]));
+    return ARGUS_OK;
 }
 
 const char* argus_status_string(argus_status s) {

@@ -152,6 +152,8 @@ def make_array(n_toa: np.ndarray, seed: int, with_signal: bool = True,
         a, b = off[p], off[p + 1]
         n = b - a
         tp = np.sort(rng.uniform(0.0, t_obs, n))
+        if n == 0:
+            continue
         log10_sig, efac = theta[7 + 2 * p], theta[8 + 2 * p]
         sp = 10.0 ** log10_sig
         # integrated random walk of the fractional frequency y

@@ -30,7 +30,8 @@ def argus():
 def ll_err(ll, ref):
     ll, ref = np.asarray(ll), np.asarray(ref)
     both_inf = np.isneginf(ll) & np.isneginf(ref)
-    d = np.where(both_inf, 0.0, np.abs(ll - ref) / np.maximum(np.abs(ref), 1.0))
+    with np.errstate(invalid="ignore"):
+        d = np.where(both_inf, 0.0, np.abs(ll - ref) / np.maximum(np.abs(ref), 1.0))
     return np.nan_to_num(d, nan=np.inf).max()
 
 
