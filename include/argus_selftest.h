@@ -1,0 +1,39 @@
+/*
+ * argus_selftest.h -- self-checks of the device arithmetic helpers used by
+ * the filter kernels.  The paper has no counterpart: these expose, for tests
+ * only, the GPU routines that replace FP64 transcendentals on the hot path so
+ * that their accuracy can be measured against CUDA's own functions and
+ * high-precision references.  All pointers are HOST memory; each call
+ * allocates its own device buffers, runs on the legacy stream and
+ * synchronises.  Errors: ARGUS_ERR_INVALID_ARG for NULL or n < 0,
+ * ARGUS_ERR_CUDA / ARGUS_ERR_OOM from CUDA.
+ */
+#ifndef ARGUS_SELFTEST_H
+#define ARGUS_SELFTEST_H
+
+#include <stdint.h>
+
+#include "argus.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* For each phase x[i] (cycles): the table + double-float sin/cos of 2 pi x
+ * (sin_out, cos_out) and CUDA's sincospi(2 x) (ref_sin, ref_cos), all [n]. */
+argus_status argus_selftest_phase(const double* x, int64_t n, double* sin_out, double* cos_out,
+                                  double* ref_sin, double* ref_cos);
+
+/* out[i] = 1 / S[i] by the approximate reciprocal + two Newton-Raphson steps;
+ * S[i] must be positive and normal. */
+argus_status argus_selftest_rcp(const double* S, int64_t n, double* out);
+
+/* *out = sum_i ln S[i] by the running mantissa product; *bad = 1 if some S[i]
+ * is not a positive, normal, finite number. */
+argus_status argus_selftest_logsum(const double* S, int64_t n, double* out, int32_t* bad);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ARGUS_SELFTEST_H */

@@ -9,6 +9,7 @@
 #include <cstdint>
 
 #include "kf_internal.cuh"
+#include "kf_math.cuh"
 
 namespace argus {
 
@@ -151,6 +152,8 @@ __global__ void k_project(const double* __restrict__ theta, int64_t B, int32_t P
 //   update:   m += M[:,0] e / S,  P = M - M[:,0] M[0,:] / S
 // The covariance update is written as P00 = M00 R/S, P01 = M01 R/S,
 // P11 = M11 - M01^2/S, algebraically equal to M - K S K^T.
+// The signal's sin/cos run on the FP32/integer pipes (phase_sincos); the
+// log-determinant is a running mantissa product (LogProd).
 // ---------------------------------------------------------------------------
 struct Lane {
     double A, B, f, phc, sig2, efac2, equad2;
@@ -161,11 +164,13 @@ struct State {
 };
 
 struct StepOut {   // what the adjoint needs from the forward step
-    double M00, M01, rS, e, sn, cs;
+    double K0, K1, rS, e, sn, cs;
 };
 
+template <bool kTape>
 __device__ __forceinline__ void kf_step(State& x, const double* __restrict__ rec, const Lane& L,
-                                        double& quad, double& logS, StepOut& so) {
+                                        PhaseTable tab, double& quad, LogProd& lp,
+                                        StepOut& so) {
     const double t = rec[0], dt = rec[1], h2 = rec[2], h3 = rec[3], r = rec[4], s2k = rec[5];
     // predict
     const double m0 = fma(dt, x.m1, x.m0);
@@ -173,61 +178,67 @@ __device__ __forceinline__ void kf_step(State& x, const double* __restrict__ rec
     const double M00 = fma(L.sig2, h3, fma(dt, x.p01 + t1, x.p00));
     const double M01 = fma(L.sig2, h2, t1);
     const double M11 = fma(L.sig2, dt, x.p11);
-    // signal: phase in cycles, sin/cos of 2 pi x
+    // signal at phase f t + Phi0/(2 pi) cycles
     double sn, cs;
-    sincospi(2.0 * fma(L.f, t, L.phc), &sn, &cs);
+    phase_sincos(fma(L.f, t, L.phc), tab, sn, cs);
     const double s = fma(L.A, sn, L.B * cs);
     // innovation
     const double e = (r - s) - m0;
     const double R = fma(L.efac2, s2k, L.equad2);
     const double S = M00 + R;
-    const double rS = 1.0 / S;
+    const double rS = rcp_nr(S);
     const double g = e * rS;
     const double w = R * rS;
+    const double K1 = M01 * rS;
     // update
     x.m0 = fma(M00, g, m0);
     x.m1 = fma(M01, g, x.m1);
     x.p00 = M00 * w;
     x.p01 = M01 * w;
-    x.p11 = fma(-M01 * rS, M01, M11);
-    quad = fma(e, g, quad);
-    logS += log(S);
-    so.M00 = M00; so.M01 = M01; so.rS = rS; so.e = e; so.sn = sn; so.cs = cs;
+    x.p11 = fma(-K1, M01, M11);
+    if (kTape) {
+        so.K0 = M00 * rS; so.K1 = K1; so.rS = rS; so.e = e; so.sn = sn; so.cs = cs;
+    } else {
+        quad = fma(e, g, quad);
+        lp.add(S);
+    }
 }
 
 struct Adjoint {
     double mu0, mu1, pi00, pi01, pi11;   // adjoints of the post-update state
 };
 
+// Per-lane gradient accumulators: dll/dA, dll/dB, sum sbar t sin, sum sbar t
+// cos, dll/dsigma^2, and sum Sbar sigma_k^2 (= dll/dEFAC / (2 EFAC)).  The
+// Phi0 and Omega derivatives follow as A gB - B gA and A gBt - B gAt.
 struct LaneGrad {
-    double A, B, Ph, W, s2, E;
+    double A, B, At, Bt, s2, E;
 };
 
 // Reverse of kf_step: consumes the adjoint of the step's output state and the
 // step's own loglik term, produces the adjoint of its input state and adds the
 // step's contribution to the lane gradient.
 __device__ __forceinline__ void kf_step_adjoint(Adjoint& a, const StepOut& so,
-                                                const double* __restrict__ rec, const Lane& L,
-                                                double t_k, LaneGrad& g) {
-    const double dt = rec[1], h2 = rec[2], h3 = rec[3], s2k = rec[5], dt2 = rec[6];
-    const double K0 = so.M00 * so.rS, K1 = so.M01 * so.rS, gg = so.e * so.rS;
+                                                const double* __restrict__ rec, LaneGrad& g) {
+    const double t = rec[0], dt = rec[1], h2 = rec[2], h3 = rec[3], s2k = rec[5], dt2 = rec[6];
+    const double K0 = so.K0, K1 = so.K1, gg = so.e * so.rS;
     const double t1 = fma(a.mu0, K0, a.mu1 * K1);
     const double ebar = t1 - gg;                                // dL/de
     const double u = fma(a.pi01, K1, a.pi00 * K0);
-    const double Sbar = fma(-0.5 * so.rS, 1.0 - so.e * gg, fma(-gg, t1, fma(K0, u, a.pi11 * K1 * K1)));
+    const double v = a.pi11 * K1;
+    const double Sbar = fma(-0.5 * so.rS, fma(-so.e, gg, 1.0), fma(-gg, t1, fma(K0, u, v * K1)));
     const double a0 = a.mu0 - ebar;                             // dL/d(predicted m0)
-    const double M00b = fma(a.mu0, gg, fma(a.pi00, 1.0 - 2.0 * K0, fma(-a.pi01, K1, Sbar)));
-    const double M01b = fma(a.mu1, gg, fma(a.pi01, 1.0 - K0, -2.0 * a.pi11 * K1));
+    const double M00b = fma(a.mu0, gg, fma(a.pi00, fma(-2.0, K0, 1.0), fma(-a.pi01, K1, Sbar)));
+    const double M01b = fma(a.mu1, gg, fma(a.pi01, 1.0 - K0, -2.0 * v));
     const double M11b = a.pi11;
     g.s2 = fma(M00b, h3, fma(M01b, h2, fma(M11b, dt, g.s2)));
     g.E = fma(Sbar, s2k, g.E);
-    const double sbar = -ebar;                                  // dL/ds_k
-    g.A = fma(sbar, so.sn, g.A);
-    g.B = fma(sbar, so.cs, g.B);
-    const double dph = fma(L.A, so.cs, -L.B * so.sn);           // ds/dPhi
-    const double sd = sbar * dph;
-    g.Ph += sd;
-    g.W = fma(sd, t_k, g.W);
+    // dL/ds_k = -ebar
+    g.A = fma(-ebar, so.sn, g.A);
+    g.B = fma(-ebar, so.cs, g.B);
+    const double st = -ebar * t;
+    g.At = fma(st, so.sn, g.At);
+    g.Bt = fma(st, so.cs, g.Bt);
     // back through the prediction m = F m, M = F P F^T + Q
     a.mu0 = a0;
     a.mu1 = fma(dt, a0, a.mu1);
@@ -265,17 +276,34 @@ __device__ __forceinline__ int next_item(const FilterArgs& a, int iter, int* s_i
     return *s_item;
 }
 
-__device__ __forceinline__ double finish_ll(int n, double quad, double logS) {
-    const double ll = -0.5 * (double(n) * kLog2Pi + logS + quad);
-    return isfinite(ll) ? ll : -INFINITY;
+__device__ __forceinline__ double finish_ll(int n, double quad, const LogProd& lp) {
+    if (n == 0) return 0.0;
+    const double ll = -0.5 * (double(n) * kLog2Pi + lp.value() + quad);
+    return (lp.bad || !isfinite(ll)) ? -INFINITY : ll;
+}
+
+// shared memory of a filter block: phase table, then the staged TOA records
+struct FilterSmem {
+    PhaseTable tab;
+    double* rec;
+};
+
+__device__ __forceinline__ FilterSmem filter_smem() {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    FilterSmem s;
+    s.tab.d = reinterpret_cast<double2*>(smem_raw);
+    s.tab.f = reinterpret_cast<float4*>(smem_raw + kPhaseTable * sizeof(double2));
+    s.rec = reinterpret_cast<double*>(smem_raw + kPhaseTableBytes);
+    return s;
 }
 
 // ---------------------------------------------------------------------------
 // K2: forward filter, one lane per thread.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_filter_fwd(FilterArgs a) {
-    extern __shared__ __align__(16) double smem[];
+    const FilterSmem sm = filter_smem();
     __shared__ int s_item;
+    fill_phase_table(sm.tab);
     for (int iter = 0;; ++iter) {
         const int it = next_item(a, iter, &s_item);
         if (it >= a.n_items) break;
@@ -287,18 +315,20 @@ __global__ void __launch_bounds__(256) k_filter_fwd(FilterArgs a) {
         Lane L;
         State x{0.0, 0.0, ps.p0[0], ps.p0[1], ps.p0[2]};
         if (active) load_lane(a, wi.p, b, ps.equad2, L);
-        double quad = 0.0, logS = 0.0;
+        double quad = 0.0;
+        LogProd lp;
         StepOut so;
         for (int k0 = 0; k0 < n; k0 += kChunk) {
             const int cnt = min(kChunk, n - k0);
             __syncthreads();
-            stage_records(smem, a.rec + (ps.off + k0) * kRecDoubles, cnt);
+            stage_records(sm.rec, a.rec + (ps.off + k0) * kRecDoubles, cnt);
             __syncthreads();
             if (active) {
-                for (int k = 0; k < cnt; ++k) kf_step(x, smem + k * kRecDoubles, L, quad, logS, so);
+                for (int k = 0; k < cnt; ++k)
+                    kf_step<false>(x, sm.rec + k * kRecDoubles, L, sm.tab, quad, lp, so);
             }
         }
-        if (active) a.lane_out[int64_t(wi.p) * a.B + b] = finish_ll(n, quad, logS);
+        if (active) a.lane_out[int64_t(wi.p) * a.B + b] = finish_ll(n, quad, lp);
         __syncthreads();
     }
 }
@@ -308,17 +338,18 @@ __global__ void __launch_bounds__(256) k_filter_fwd(FilterArgs a) {
 // Pass 1 runs the filter forward segment by segment (stride TOAs each) and
 // checkpoints the state at the start of every segment.  Pass 2 walks the
 // segments backwards: restore the checkpoint, re-run the segment forward
-// recording (M00, M01, 1/S, e, sin, cos) per step in the block's tape, then
+// recording (K0, K1, 1/S, e, sin, cos) per step in the block's tape, then
 // run the adjoint steps in reverse.  Checkpoints and tape live in the block's
 // own slot of global scratch ([..][field][W], so a warp's accesses coalesce).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_filter_grad(FilterArgs a) {
-    extern __shared__ __align__(16) double smem[];
+    const FilterSmem sm = filter_smem();
     __shared__ int s_item;
     const int W = blockDim.x;
     const int tid = threadIdx.x;
     double* ck = a.ckpt + int64_t(blockIdx.x) * a.ckpt_slot + tid;
     double* tp = a.tape + int64_t(blockIdx.x) * a.tape_slot + tid;
+    fill_phase_table(sm.tab);
     for (int iter = 0;; ++iter) {
         const int it = next_item(a, iter, &s_item);
         if (it >= a.n_items) break;
@@ -330,44 +361,46 @@ __global__ void __launch_bounds__(256) k_filter_grad(FilterArgs a) {
         Lane L;
         if (active) load_lane(a, wi.p, b, ps.equad2, L);
         State x{0.0, 0.0, ps.p0[0], ps.p0[1], ps.p0[2]};
-        double quad = 0.0, logS = 0.0;
+        double quad = 0.0;
+        LogProd lp;
         StepOut so;
         // pass 1: forward with checkpoints
         for (int seg = 0; seg < nseg; ++seg) {
             const int k0 = seg * c, cnt = min(c, n - k0);
             __syncthreads();
-            stage_records(smem, a.rec + (ps.off + k0) * kRecDoubles, cnt);
+            stage_records(sm.rec, a.rec + (ps.off + k0) * kRecDoubles, cnt);
             __syncthreads();
             if (active) {
                 double* cp = ck + int64_t(seg) * kCkptDoubles * W;
                 cp[0 * W] = x.m0; cp[1 * W] = x.m1; cp[2 * W] = x.p00; cp[3 * W] = x.p01; cp[4 * W] = x.p11;
-                for (int k = 0; k < cnt; ++k) kf_step(x, smem + k * kRecDoubles, L, quad, logS, so);
+                for (int k = 0; k < cnt; ++k)
+                    kf_step<false>(x, sm.rec + k * kRecDoubles, L, sm.tab, quad, lp, so);
             }
         }
-        const double ll = finish_ll(n, quad, logS);
+        const double ll = finish_ll(n, quad, lp);
         // pass 2: reverse sweep
         Adjoint adj{0.0, 0.0, 0.0, 0.0, 0.0};
         LaneGrad g{0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
         for (int seg = nseg - 1; seg >= 0; --seg) {
             const int k0 = seg * c, cnt = min(c, n - k0);
             __syncthreads();
-            stage_records(smem, a.rec + (ps.off + k0) * kRecDoubles, cnt);
+            stage_records(sm.rec, a.rec + (ps.off + k0) * kRecDoubles, cnt);
             __syncthreads();
             if (active) {
                 const double* cp = ck + int64_t(seg) * kCkptDoubles * W;
                 State y{cp[0 * W], cp[1 * W], cp[2 * W], cp[3 * W], cp[4 * W]};
-                double q2 = 0.0, l2 = 0.0;
+                double q2 = 0.0;
+                LogProd l2;
                 for (int k = 0; k < cnt; ++k) {
-                    kf_step(y, smem + k * kRecDoubles, L, q2, l2, so);
+                    kf_step<true>(y, sm.rec + k * kRecDoubles, L, sm.tab, q2, l2, so);
                     double* tk = tp + int64_t(k) * kTapeDoubles * W;
-                    tk[0 * W] = so.M00; tk[1 * W] = so.M01; tk[2 * W] = so.rS;
+                    tk[0 * W] = so.K0; tk[1 * W] = so.K1; tk[2 * W] = so.rS;
                     tk[3 * W] = so.e; tk[4 * W] = so.sn; tk[5 * W] = so.cs;
                 }
                 for (int k = cnt - 1; k >= 0; --k) {
                     const double* tk = tp + int64_t(k) * kTapeDoubles * W;
                     StepOut sk{tk[0 * W], tk[1 * W], tk[2 * W], tk[3 * W], tk[4 * W], tk[5 * W]};
-                    const double* rk = smem + k * kRecDoubles;
-                    kf_step_adjoint(adj, sk, rk, L, rk[0], g);
+                    kf_step_adjoint(adj, sk, sm.rec + k * kRecDoubles, g);
                 }
             }
         }
@@ -377,8 +410,8 @@ __global__ void __launch_bounds__(256) k_filter_grad(FilterArgs a) {
             o[0] = ll;
             o[1 * lanes] = g.A;
             o[2 * lanes] = g.B;
-            o[3 * lanes] = g.Ph;
-            o[4 * lanes] = g.W;
+            o[3 * lanes] = g.At;
+            o[4 * lanes] = g.Bt;
             o[5 * lanes] = g.s2;
             o[6 * lanes] = g.E;
         }
@@ -421,11 +454,14 @@ __global__ void k_reduce(const double* __restrict__ theta, int64_t B, int32_t P,
     double gw[kNgw] = {0, 0, 0, 0, 0, 0, 0};
     for (int p = 0; p < P; ++p) {
         const double* o = lane_out + int64_t(p) * B + b;
-        const double gA = o[1 * lanes], gB = o[2 * lanes], gP = o[3 * lanes];
-        const double gW = o[4 * lanes], gs2 = o[5 * lanes], gE = o[6 * lanes];
+        const double gA = o[1 * lanes], gB = o[2 * lanes], gAt = o[3 * lanes];
+        const double gBt = o[4 * lanes], gs2 = o[5 * lanes], gE = o[6 * lanes];
         Antenna R;
         antenna(F, psr[p].pos, true, R);
         const double A = R.Fp * F.ampP, Bc = R.Fx * F.ampX;
+        // ds/dPhi0 = A cos - B sin, ds/dOmega = t (A cos - B sin)
+        const double gP = fma(A, gB, -Bc * gA);
+        const double gW = fma(A, gBt, -Bc * gAt);
         const double gAB = fma(gA, A, gB * Bc);
         gw[0] += fma(gW, F.W * kLn10, -gAB * kLn10);
         gw[1] += gP;
@@ -448,7 +484,7 @@ __global__ void k_reduce(const double* __restrict__ theta, int64_t B, int32_t P,
 // ---------------------------------------------------------------------------
 size_t filter_smem_bytes(bool grad, int stride_max) {
     const int recs = grad ? stride_max : kChunk;
-    return size_t(recs) * kRecDoubles * sizeof(double);
+    return kPhaseTableBytes + size_t(recs) * kRecDoubles * sizeof(double);
 }
 
 void launch_project(const double* theta, int64_t B, int32_t P, const PulsarDev* psr, double* lc,

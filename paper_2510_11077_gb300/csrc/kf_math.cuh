@@ -1,0 +1,173 @@
+// Arithmetic helpers of the filter kernels, written for a part whose FP64
+// pipe issues 2 FMA per clock per SM while its FP32 and integer pipes issue
+// 64-128: everything that does not need FP64 runs on the other pipes.
+//
+//  * phase_sincos: sin and cos of 2 pi x for a phase x in cycles.  The
+//    fraction of x is taken exactly as a 64-bit fixed-point number with
+//    integer instructions; its top 8 bits index a 256-entry table of
+//    sin/cos(2 pi j / 256); the remainder (|a| <= pi/256 rad) goes through
+//    Taylor polynomials in double-float arithmetic (a value as an unevaluated
+//    sum of two floats, ~48-bit significand), then the angle-addition formula.
+//    Error-free transformations: Knuth's two-sum, Dekker's fast two-sum and
+//    the FMA two-product (as in the double-float arithmetic of Hida, Li &
+//    Bailey 2001).  Only the final hi+lo sums run on the FP64 pipe.
+//  * rcp_nr: 1/S by the FP64 approximate-reciprocal instruction refined by
+//    two Newton-Raphson steps r <- r + r (1 - S r).
+//  * LogProd: sum of ln S_k as a running product kept in [1, 2) with its
+//    binary exponent accumulated in an integer (one log per lane at the end).
+#pragma once
+
+#include <cstdint>
+
+namespace argus {
+
+struct df {
+    float hi, lo;
+};
+
+__device__ __forceinline__ df two_sum(float a, float b) {
+    const float s = a + b;
+    const float bb = s - a;
+    const float e = (a - (s - bb)) + (b - bb);
+    return {s, e};
+}
+
+__device__ __forceinline__ df fast_two_sum(float a, float b) {   // needs |a| >= |b|
+    const float s = a + b;
+    return {s, b - (s - a)};
+}
+
+__device__ __forceinline__ df df_mul(df a, df b) {
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
+    return fast_two_sum(p, e);
+}
+
+__device__ __forceinline__ df df_add(df a, df b) {
+    df s = two_sum(a.hi, b.hi);
+    const df t = two_sum(a.lo, b.lo);
+    s = fast_two_sum(s.hi, s.lo + t.hi);
+    return fast_two_sum(s.hi, s.lo + t.lo);
+}
+
+__device__ __forceinline__ df df_add_f(df a, float b) {          // a + b, b a float
+    const df s = two_sum(a.hi, b);
+    return fast_two_sum(s.hi, s.lo + a.lo);
+}
+
+__device__ __forceinline__ df df_neg(df a) { return {-a.hi, -a.lo}; }
+
+// Exact float -> double by re-packing the bits (integer instructions only).
+// Zero and subnormal floats map to a signed zero.
+__device__ __forceinline__ double f2d_bits(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned e = (u >> 23) & 0xffu;
+    unsigned hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u >> 3) & 0xfffffu);
+    unsigned lo = u << 29;
+    hi = e ? hi : (u & 0x80000000u);
+    lo = e ? lo : 0u;
+    return __hiloint2double(int(hi), int(lo));
+}
+
+__device__ __forceinline__ double df_to_double(df a) { return f2d_bits(a.hi) + f2d_bits(a.lo); }
+
+// frac(x) * 2^64 for a finite double x (exact, integer instructions only).
+__device__ __forceinline__ uint64_t frac_cycles_u64(double x) {
+    const long long b = __double_as_longlong(x);
+    const int ef = int((b >> 52) & 0x7ff);
+    const unsigned long long m =
+        (static_cast<unsigned long long>(b) & 0xFFFFFFFFFFFFFull) | (ef ? (1ull << 52) : 0ull);
+    const int s = ef - 1075 + 64;   // x = m 2^(ef - 1075)
+    unsigned long long F = 0ull;
+    if (s >= 0 && s < 64) F = m << s;
+    else if (s < 0 && s > -64) F = m >> (-s);
+    return (b < 0) ? (0ull - F) : F;
+}
+
+// Table of sin/cos(2 pi j / 256): FP64 values (for the final sums) and the
+// same values as double-float pairs (for the small corrections).
+constexpr int kPhaseTable = 256;
+
+struct PhaseTable {
+    double2* d;   // {sin, cos}
+    float4* f;    // {sin.hi, sin.lo, cos.hi, cos.lo}
+};
+
+constexpr size_t kPhaseTableBytes = kPhaseTable * (sizeof(double2) + sizeof(float4));
+
+__device__ __forceinline__ void fill_phase_table(PhaseTable tab) {
+    for (int j = threadIdx.x; j < kPhaseTable; j += blockDim.x) {
+        double s, c;
+        sincospi(double(j) / (kPhaseTable / 2), &s, &c);
+        const float sh = __double2float_rn(s), ch = __double2float_rn(c);
+        tab.d[j] = make_double2(s, c);
+        tab.f[j] = make_float4(sh, __double2float_rn(s - double(sh)), ch,
+                               __double2float_rn(c - double(ch)));
+    }
+}
+
+// sin(2 pi x), cos(2 pi x) for x in cycles.  With x = j/256 + a/(2 pi):
+//   sin = S_j + [S_j (cos a - 1) + C_j sin a],  cos = C_j + [C_j (cos a - 1) - S_j sin a],
+// the brackets (|.| <= 0.013) in double-float, the two sums in FP64.
+__device__ __forceinline__ void phase_sincos(double x, PhaseTable tab, double& sn, double& cs) {
+    const uint64_t F = frac_cycles_u64(x);
+    const uint64_t j = (F + (1ull << 55)) >> 56;                 // nearest table node
+    const long long d = static_cast<long long>(F - (j << 56));   // |d| <= 2^55
+    // d exactly as a sum of three floats, then to radians: a = 2 pi 2^-64 d
+    const float d2 = float(int(d >> 32)) * 4294967296.0f;        // exact (|d>>32| <= 2^23)
+    const unsigned dl = unsigned(d & 0xffffffffll);
+    df dd = two_sum(d2, float(dl >> 8) * 256.0f);
+    dd = df_add_f(dd, float(dl & 0xffu));
+    const df k2pi = {6.28318548202514648e+00f * 5.42101086242752217e-20f,
+                     -1.7484556025237907e-07f * 5.42101086242752217e-20f};   // 2 pi * 2^-64
+    const df a = df_mul(dd, k2pi);
+    const df a2 = df_mul(a, a);
+    const float q = a2.hi;
+    // sin a = a + a c,  c = -a^2/6 + a^4/120 - a^6/5040
+    const df m6 = {-1.66666671633720398e-01f, 4.967053740534411e-09f};             // -1/6
+    df c = df_mul(a2, m6);
+    c = df_add_f(c, q * q * fmaf(-q, 1.0f / 5040.0f, 1.0f / 120.0f));
+    const df sa = df_add(a, df_mul(a, c));
+    // cos a - 1 = -a^2/2 + a^4/24 - a^6/720
+    const df cm1 = df_add_f(df{-0.5f * a2.hi, -0.5f * a2.lo},
+                            q * q * fmaf(-q, 1.0f / 720.0f, 1.0f / 24.0f));
+    const int jj = int(j & (kPhaseTable - 1));
+    const float4 t = tab.f[jj];
+    const double2 td = tab.d[jj];
+    const df S = {t.x, t.y}, C = {t.z, t.w};
+    const df corr_s = df_add(df_mul(S, cm1), df_mul(C, sa));
+    const df corr_c = df_add(df_mul(C, cm1), df_neg(df_mul(S, sa)));
+    sn = (td.x + f2d_bits(corr_s.hi)) + f2d_bits(corr_s.lo);
+    cs = (td.y + f2d_bits(corr_c.hi)) + f2d_bits(corr_c.lo);
+}
+
+// 1/S for a positive normal S: approximate reciprocal + 2 Newton-Raphson steps.
+__device__ __forceinline__ double rcp_nr(double S) {
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(S));
+    double e = fma(-S, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-S, r, 1.0);
+    return fma(r, e, r);
+}
+
+// Running sum of ln S_k: mantissa product in [1, 2) and an integer exponent.
+struct LogProd {
+    double pr = 1.0;
+    int ex = 0;
+    unsigned bad = 0u;   // set if some S_k was not a positive, normal, finite number
+    __device__ __forceinline__ void add(double S) {
+        const unsigned hs = unsigned(__double2hiint(S));
+        bad |= (hs - 0x00100000u) >= (0x7ff00000u - 0x00100000u) ? 1u : 0u;
+        const double p = pr * S;
+        const int hi = __double2hiint(p);
+        ex += ((hi >> 20) & 0x7ff) - 1023;
+        pr = __hiloint2double((hi & 0x800fffff) | 0x3ff00000, __double2loint(p));
+    }
+    __device__ __forceinline__ double value() const {
+        return log(pr) + double(ex) * 0.69314718055994530942;
+    }
+};
+
+}  // namespace argus

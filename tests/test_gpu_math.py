@@ -1,0 +1,80 @@
+"""Accuracy of the device arithmetic that replaces FP64 transcendentals on the
+filter's hot path, against CUDA's own functions and high-precision references."""
+from __future__ import annotations
+
+import ctypes
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+try:
+    import mpmath
+except ImportError:   # not installed on every box; the numpy reference still runs
+    mpmath = None
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2510_11077_gb300 import argus
+    lib = argus.load()
+    dp = ctypes.c_void_p
+    lib.argus_selftest_phase.argtypes = [dp, ctypes.c_int64, dp, dp, dp, dp]
+    lib.argus_selftest_rcp.argtypes = [dp, ctypes.c_int64, dp]
+    lib.argus_selftest_logsum.argtypes = [dp, ctypes.c_int64, dp, dp]
+    return lib
+
+
+def _p(a):
+    return a.ctypes.data
+
+
+def test_phase_sincos_accuracy(lib):
+    rng = np.random.default_rng(0)
+    # phases a pulsar filter meets: f t + Phi0/2pi up to ~35 cycles, both signs,
+    # plus table nodes, half-nodes, tiny and integer phases
+    x = np.concatenate([rng.uniform(-40, 40, 20000), rng.uniform(0, 1, 5000),
+                        np.arange(0, 3, 1 / 512), [0.0, -0.0, 1e-300, 5e-17, 1.0, -3.0, 33.25],
+                        rng.uniform(0, 1e-6, 100)])
+    n = len(x)
+    s, c, rs, rc = (np.empty(n) for _ in range(4))
+    assert lib.argus_selftest_phase(_p(x), n, _p(s), _p(c), _p(rs), _p(rc)) == 0
+    # against CUDA's sincospi
+    assert np.max(np.abs(s - rs)) < 6e-16 and np.max(np.abs(c - rc)) < 6e-16
+    # against numpy on the exact fraction (argument error <= 1 ulp of pi)
+    fr = x - np.rint(x)
+    assert np.max(np.abs(s - np.sin(2 * np.pi * fr))) < 1.5e-15
+    assert np.max(np.abs(c - np.cos(2 * np.pi * fr))) < 1.5e-15
+    if mpmath is not None:   # 40-digit reference on a subsample
+        mpmath.mp.dps = 40
+        idx = rng.choice(n, 1500, replace=False)
+        es = max(abs(float(mpmath.sinpi(2 * mpmath.mpf(x[i]))) - s[i]) for i in idx)
+        ec = max(abs(float(mpmath.cospi(2 * mpmath.mpf(x[i]))) - c[i]) for i in idx)
+        assert es < 5e-16 and ec < 5e-16, (es, ec)
+    assert np.all(np.abs(s) <= 1.0 + 1e-15) and np.all(np.abs(c) <= 1.0 + 1e-15)
+
+
+def test_newton_reciprocal_is_within_one_ulp(lib):
+    rng = np.random.default_rng(1)
+    S = np.concatenate([10.0 ** rng.uniform(-300, 300, 20000), 1e-14 * rng.uniform(0.5, 4, 20000),
+                        [1.0, 2.0, 3.0, 0.1, 2.2250738585072014e-308 * 4]])
+    out = np.empty_like(S)
+    assert lib.argus_selftest_rcp(_p(S), len(S), _p(out)) == 0
+    ref = 1.0 / S
+    ulps = np.abs(out - ref) / np.spacing(np.abs(ref))
+    assert ulps.max() <= 1.0
+
+
+def test_log_product_matches_sum_of_logs(lib):
+    rng = np.random.default_rng(2)
+    S = 1e-14 * rng.uniform(0.3, 3.0, 20000)
+    out = np.empty(1); bad = np.zeros(1, dtype=np.int32)
+    assert lib.argus_selftest_logsum(_p(S), len(S), _p(out), _p(bad)) == 0
+    ref = math.fsum(np.log(S))
+    assert bad[0] == 0
+    assert abs(out[0] - ref) <= 1e-14 * abs(ref)
+    for badval in (0.0, -1e-14, np.inf, np.nan, 1e-320):
+        T = S[:50].copy(); T[17] = badval
+        assert lib.argus_selftest_logsum(_p(T), len(T), _p(out), _p(bad)) == 0
+        assert bad[0] == 1, badval
