@@ -117,6 +117,31 @@ argus_status argus_loglik(argus_array* array, const double* theta, int64_t B,
 argus_status argus_loglik_grad(argus_array* array, const double* theta, int64_t B,
                                double* loglik, double* grad, void* stream);
 
+/* Allocation-free variant of argus_loglik_grad.  The paper has no
+ * counterpart: this exists for callers that must not allocate device memory
+ * while they run -- e.g. code inside a framework that has already reserved
+ * (nearly) all GPU memory for its own pool, where a cudaMalloc from this
+ * library would fail or fragment that pool, or a sampler's hot loop where a
+ * cudaMalloc/cudaFree (which may synchronise the device) is unacceptable.
+ * Create the handle beforehand with argus_array_create (which does allocate);
+ * this call then allocates nothing: all of its scratch (work counter and
+ * items, lane constants, per-lane results, adjoint checkpoints and tape)
+ * comes from one file-scope device array of 64 MiB that every GPU which
+ * loads the library holds until the process exits.
+ * theta [B][D], loglik [B] and grad [B][D] must be device memory (otherwise
+ * ARGUS_ERR_INVALID_ARG); results equal argus_loglik_grad's.  A batch whose
+ * scratch does not fit in 64 MiB (about 112 bytes per walker x pulsar lane,
+ * plus at least one block's checkpoint and tape slot) is rejected with
+ * ARGUS_ERR_UNSUPPORTED and a message giving the bytes needed.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  Every call shares the one array and leaves its contents behind;
+ * calls whose work overlaps on the GPU (other streams, other host threads,
+ * other handles on the same device) race on it and must be serialised by
+ * the caller. */
+argus_status argus_loglik_grad_noalloc(argus_array* array, const double* theta, int64_t B,
+                                       double* loglik, double* grad, void* stream);
+
 /* Per-(walker, pulsar) terms, for inspection: lane_ll [B][P] doubles (device
  * or host) receives ll_p(theta_b).  Same rules as argus_loglik. */
 argus_status argus_lane_loglik(argus_array* array, const double* theta, int64_t B,

@@ -85,6 +85,8 @@ def load(build_if_missing: bool = False):
     lib.argus_loglik_grad.restype = ctypes.c_int
     lib.argus_lane_loglik.argtypes = [vp, dp, ctypes.c_int64, dp, vp]
     lib.argus_lane_loglik.restype = ctypes.c_int
+    lib.argus_loglik_grad_noalloc.argtypes = [vp, dp, ctypes.c_int64, dp, dp, vp]
+    lib.argus_loglik_grad_noalloc.restype = ctypes.c_int
     lib.argus_array_set_timing.argtypes = [vp, ctypes.c_int32]
     lib.argus_array_set_timing.restype = ctypes.c_int
     lib.argus_array_get_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
@@ -223,6 +225,17 @@ def argus_loglik_grad(array: Array, theta, loglik=None, grad=None, stream=None):
         grad = _new_like(theta, (B, array.dim))
     s = stream if stream is not None else _stream_of(theta, loglik, grad)
     _check(_lib.argus_loglik_grad(array.handle, _ptr(theta), B, _ptr(loglik), _ptr(grad), s))
+    return loglik, grad
+
+
+def argus_loglik_grad_noalloc(array: Array, theta, loglik, grad, stream=None):
+    """Allocation-free loglik + gradient: all three tensors must already be on
+    the device; the library takes its scratch from a fixed 64 MiB device
+    array instead of allocating (see include/argus.h)."""
+    theta = _prep(theta, array.dim)
+    s = stream if stream is not None else _stream_of(theta, loglik, grad)
+    _check(_lib.argus_loglik_grad_noalloc(array.handle, _ptr(theta), theta.shape[0],
+                                          _ptr(loglik), _ptr(grad), s))
     return loglik, grad
 
 

@@ -594,3 +594,123 @@ const char* argus_status_string(argus_status s) {
 const char* argus_last_error(void) { return g_last_error.c_str(); }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free log-likelihood + gradient (argus_loglik_grad_noalloc).
+//
+// For callers that must not allocate device memory while they run: code
+// embedded in a framework that has already reserved (nearly) all of the GPU's
+// memory for its own pool, so a cudaMalloc from this library would fail or
+// fragment that pool, and code in a hot loop where a cudaMalloc/cudaFree (which
+// can synchronise the device) is not acceptable.  The handle is still created
+// once, up front, by argus_array_create.  Each call then takes all of its
+// scratch -- work counter, work items, lane constants, per-lane results,
+// adjoint checkpoints and tape -- from one file-scope device array of
+// kNoAllocBytes, and allocates nothing.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace {
+
+constexpr size_t kNoAllocBytes = size_t(64) << 20;   // 64 MiB, held by every GPU that loads the library
+constexpr int kNoAllocW = 64;                        // walkers per block in this variant
+constexpr int kNoAllocMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+__global__ void k_noalloc_items(WorkItem* items, int n_items, int64_t tiles, int W) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_items) return;
+    items[i] = WorkItem{int32_t(i / tiles), int32_t((i % tiles) * W)};
+}
+
+size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
+
+// Device address of the scratch array on the current device; looked up once
+// per device (the array's name in host code is only a host-side stand-in).
+argus_status noalloc_scratch(int dev, unsigned char** out) {
+    if (dev < 0 || dev >= kNoAllocMaxDevices)
+        return fail(ARGUS_ERR_UNSUPPORTED, "device ordinal beyond the no-alloc table");
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(no-alloc scratch)");
+        g_noalloc_addr[dev] = p;
+    }
+    *out = static_cast<unsigned char*>(g_noalloc_addr[dev]);
+    return ARGUS_OK;
+}
+
+}  // namespace
+
+extern "C" argus_status argus_loglik_grad_noalloc(argus_array* h, const double* theta, int64_t B,
+                                                  double* loglik, double* grad, void* stream) {
+    if (!h) return fail(ARGUS_ERR_INVALID_ARG, "array handle is NULL");
+    if (B < 0) return fail(ARGUS_ERR_INVALID_ARG, "B must be >= 0");
+    if (B == 0) return ARGUS_OK;
+    if (!theta || !loglik || !grad) return fail(ARGUS_ERR_INVALID_ARG, "NULL theta, loglik or grad");
+    DeviceGuard guard(h->device);
+    if (!is_device_ptr(theta) || !is_device_ptr(loglik) || !is_device_ptr(grad))
+        return fail(ARGUS_ERR_INVALID_ARG, "argus_loglik_grad_noalloc needs device pointers");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int W = kNoAllocW;
+    const int64_t tiles = (B + W - 1) / W;
+    const int64_t n_items64 = tiles * h->P;
+    if (n_items64 > INT32_MAX) return fail(ARGUS_ERR_UNSUPPORTED, "too many work items");
+    const int n_items = int(n_items64);
+    const size_t lanes = size_t(B) * h->P;
+    // carve the array: counter | items | lane constants | lane results | slots
+    const size_t off_items = 256;
+    const size_t off_lc = off_items + align256(size_t(n_items) * sizeof(WorkItem));
+    const size_t off_lane = off_lc + align256(lanes * kLaneConsts * sizeof(double));
+    const size_t off_slots = off_lane + align256(lanes * (1 + kLaneGrads) * sizeof(double));
+    const size_t ck_slot = size_t(h->nseg_max) * kCkptDoubles * W;     // doubles
+    const size_t tp_slot = size_t(h->stride_max) * kTapeDoubles * W;   // doubles
+    const size_t slot_bytes = align256(ck_slot * sizeof(double)) + align256(tp_slot * sizeof(double));
+    if (off_slots + slot_bytes > kNoAllocBytes) {
+        char buf[200];
+        snprintf(buf, sizeof buf,
+                 "argus_loglik_grad_noalloc: B x P = %zu lanes with %d-TOA segments needs %zu bytes "
+                 "of static scratch; the maximum is %zu",
+                 lanes, h->stride_max, off_slots + slot_bytes, kNoAllocBytes);
+        return fail(ARGUS_ERR_UNSUPPORTED, buf);
+    }
+    const int fit = int(std::min<size_t>((kNoAllocBytes - off_slots) / slot_bytes, INT32_MAX));
+    const int grid = std::max(1, std::min({n_items, 4 * h->n_sm, fit}));
+    unsigned char* base = nullptr;
+    argus_status st = noalloc_scratch(h->device, &base);
+    if (st) return st;
+    int* counter = reinterpret_cast<int*>(base);
+    WorkItem* items = reinterpret_cast<WorkItem*>(base + off_items);
+    double* lc = reinterpret_cast<double*>(base + off_lc);
+    double* lane = reinterpret_cast<double*>(base + off_lane);
+    double* ckpt = reinterpret_cast<double*>(base + off_slots);
+    double* tape = reinterpret_cast<double*>(base + off_slots + align256(ck_slot * sizeof(double)) * grid);
+    // the work counter must start at zero; everything else is written before it is read
+    CK(cudaMemsetAsync(counter, 0, sizeof(int), s));
+    k_noalloc_items<<<(n_items + 255) / 256, 256, 0, s>>>(items, n_items, tiles, W);
+    launch_project(theta, B, h->P, h->d_psr, lc, s);
+    FilterArgs a{};
+    a.rec = h->d_rec;
+    a.psr = h->d_psr;
+    a.items = items;
+    a.n_items = n_items;
+    a.P = h->P;
+    a.B = B;
+    a.lc = lc;
+    a.lane_out = lane;
+    a.ckpt = ckpt;
+    a.tape = tape;
+    a.ckpt_slot = int64_t(align256(ck_slot * sizeof(double)) / sizeof(double));
+    a.tape_slot = int64_t(align256(tp_slot * sizeof(double)) / sizeof(double));
+    a.stride_max = h->stride_max;
+    a.counter = counter;
+    launch_filter_grad(a, W, grid, s);
+    launch_reduce(theta, B, h->P, h->d_psr, lane, loglik, grad, nullptr, s);
+    CK(cudaGetLastError());
+    return ARGUS_OK;
+}
