@@ -58,6 +58,11 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--autotune", choices=["cache", "off", "force"], default="cache",
+                    help="cache: use the tuned-plan cache, tuning on a miss; force: retune")
+    ap.add_argument("--tune-batch", type=int, default=4096)
+    ap.add_argument("--plan", default="",
+                    help="fixed plan, e.g. tape_cache=1,walkers_per_cta=128 (disables autotune)")
     return ap.parse_args()
 
 
@@ -196,6 +201,20 @@ def run_ours(args):
     theta_np = inputs.make_theta_batch(data, B, seed=w.seed + 7919 * rank)
     theta = torch.from_numpy(theta_np).to(dev)
     arr = argus.Array(data, device=local)
+    tuned = None
+    if args.plan:
+        arr.set_plan(**{k: int(v) for k, v in (kv.split("=") for kv in args.plan.split(","))})
+    elif args.autotune != "off":
+        from paper_2510_11077_gb300 import autotune
+        cache = autotune.DEFAULT_CACHE
+        if args.autotune == "force" and os.path.exists(cache):
+            c = autotune.load_cache(cache)
+            c.pop(autotune.plan_key(data.n_toa, B, True, torch.cuda.get_device_name(dev)), None)
+            autotune.save_cache(c, cache)
+        res = autotune.autotune(arr, theta, data.n_toa, grad=True, tune_batch=args.tune_batch,
+                                batch_for_key=B)
+        tuned = {"cached": res["cached"], "tune_batch": res.get("tune_batch"),
+                 "candidates": len(res.get("tried", []))}
     plan = arr.get_plan()
     ll = torch.empty(B, dtype=torch.float64, device=dev)
     g = torch.empty((B, D), dtype=torch.float64, device=dev)
@@ -308,7 +327,7 @@ def run_ours(args):
             "data": "synthetic",
             "config": {"workload": w.name, "pulsars": data.n_pulsars,
                        "toas": int(data.n_toa.sum()), "batch_per_gpu": B, "dim": D,
-                       "lane_steps_per_gpu": lane_steps, "plan": plan,
+                       "lane_steps_per_gpu": lane_steps, "plan": plan, "autotune": tuned,
                        "l2": "flushed between timed steps (256 MiB write, untimed)"},
             "e2e": e2e, "gpu_launches": 3 * args.steps, "roofline": roofline,
             "plain_filter": plain, "batched_over_plain": value / world / plain["value"],

@@ -82,7 +82,11 @@ typedef struct argus_plan {
     int32_t ctas_per_sm;      /* resident blocks per SM of the persistent grid, 1..8 */
     int32_t ckpt_stride;      /* adjoint checkpoint stride in TOAs; 0 = ceil(sqrt(N_p)) */
     int32_t use_graph;        /* 1: capture each (theta, B, outputs) call once, then replay */
-    int32_t reserved[3];      /* must be 0 */
+    int32_t tape_cache;       /* adjoint: 0 = re-run each segment from its checkpoint (memory
+                                 O(sqrt N) per lane); 1 = also keep every segment's tape in HBM
+                                 during the forward pass and skip the re-run (memory O(N) per
+                                 lane: 48 B per TOA per resident lane) */
+    int32_t reserved[2];      /* must be 0 */
 } argus_plan;
 
 /* Copy n_pulsars pulsars to device `device` and build the handle.

@@ -46,7 +46,8 @@ class ArgusPlan(ctypes.Structure):
                 ("ctas_per_sm", ctypes.c_int32),
                 ("ckpt_stride", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 3)]
+                ("tape_cache", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 _lib = None
@@ -172,13 +173,13 @@ class Array:
         p = ArgusPlan()
         _check(_lib.argus_array_get_plan(self.handle, ctypes.byref(p)))
         return dict(mode=p.mode, walkers_per_cta=p.walkers_per_cta, ctas_per_sm=p.ctas_per_sm,
-                    ckpt_stride=p.ckpt_stride, use_graph=p.use_graph)
+                    ckpt_stride=p.ckpt_stride, use_graph=p.use_graph, tape_cache=p.tape_cache)
 
     def set_plan(self, **kw) -> None:
         cur = self.get_plan()
         cur.update(kw)
         p = ArgusPlan(cur["mode"], cur["walkers_per_cta"], cur["ctas_per_sm"],
-                      cur["ckpt_stride"], cur["use_graph"])
+                      cur["ckpt_stride"], cur["use_graph"], cur["tape_cache"])
         _check(_lib.argus_array_set_plan(self.handle, ctypes.byref(p)))
 
 

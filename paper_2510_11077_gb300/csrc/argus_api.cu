@@ -91,6 +91,7 @@ struct argus_array {
     int64_t total_toa = 0;
     int32_t stride_max = 1;   // for the current plan
     int32_t nseg_max = 0;
+    int32_t n_max = 0;        // most TOAs of any pulsar
     std::vector<PulsarDev> h_psr;
     PulsarDev* d_psr = nullptr;
     double* d_rec = nullptr;
@@ -148,7 +149,9 @@ argus_status validate_plan(const argus_plan* p) {
         return fail(ARGUS_ERR_INVALID_ARG, "plan.ckpt_stride must be in 0..256");
     if (p->use_graph != 0 && p->use_graph != 1)
         return fail(ARGUS_ERR_INVALID_ARG, "plan.use_graph must be 0 or 1");
-    for (int i = 0; i < 3; ++i)
+    if (p->tape_cache != 0 && p->tape_cache != 1)
+        return fail(ARGUS_ERR_INVALID_ARG, "plan.tape_cache must be 0 or 1");
+    for (int i = 0; i < 2; ++i)
         if (p->reserved[i] != 0) return fail(ARGUS_ERR_INVALID_ARG, "plan.reserved must be 0");
     return ARGUS_OK;
 }
@@ -164,7 +167,9 @@ int stride_for(int64_t n, int ckpt_stride) {
 argus_status apply_plan(argus_array* h) {
     h->stride_max = 1;
     h->nseg_max = 0;
+    h->n_max = 0;
     for (auto& ps : h->h_psr) {
+        h->n_max = std::max(h->n_max, ps.n);
         ps.stride = stride_for(ps.n, h->plan.ckpt_stride);
         ps.nseg = int((ps.n + ps.stride - 1) / ps.stride);
         h->stride_max = std::max(h->stride_max, ps.stride);
@@ -215,7 +220,8 @@ argus_status ensure_batch(argus_array* h, int64_t B, int W, int grid, bool grad)
     if ((st = grow(&h->d_lane, &h->cap_lane, lanes * (1 + kLaneGrads)))) return st;
     if (grad) {
         const size_t ck = size_t(h->nseg_max) * kCkptDoubles * W * grid;
-        const size_t tp = size_t(h->stride_max) * kTapeDoubles * W * grid;
+        const size_t tp_len = h->plan.tape_cache ? size_t(std::max(h->n_max, 1)) : size_t(h->stride_max);
+        const size_t tp = tp_len * kTapeDoubles * W * grid;
         if ((st = grow(&h->d_ckpt, &h->cap_ckpt, std::max<size_t>(ck, 1)))) return st;
         if ((st = grow(&h->d_tape, &h->cap_tape, std::max<size_t>(tp, 1)))) return st;
     }
@@ -237,8 +243,10 @@ FilterArgs make_args(argus_array* h, int64_t B, int W, int grid, bool persistent
     a.ckpt = h->d_ckpt;
     a.tape = h->d_tape;
     a.ckpt_slot = int64_t(h->nseg_max) * kCkptDoubles * W;
-    a.tape_slot = int64_t(h->stride_max) * kTapeDoubles * W;
+    const int64_t tp_len = h->plan.tape_cache ? std::max(h->n_max, 1) : h->stride_max;
+    a.tape_slot = tp_len * kTapeDoubles * W;
     a.stride_max = h->stride_max;
+    a.tape_cache = h->plan.tape_cache;
     a.counter = persistent ? h->d_counter : nullptr;
     (void)grid;
     return a;

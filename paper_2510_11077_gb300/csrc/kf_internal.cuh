@@ -42,11 +42,11 @@ struct FilterArgs {
     const double* lc;         // lane constants [7][P][B]
     double* lane_out;         // [1 + 6][P][B]: ll, then the gradient terms
     double* ckpt;             // per block slot: [nseg_max][5][W]
-    double* tape;             // per block slot: [stride_max][6][W]
+    double* tape;             // per block slot: [stride_max or N_max][6][W]
     int64_t ckpt_slot;        // doubles per block slot in ckpt
     int64_t tape_slot;        // doubles per block slot in tape
     int32_t stride_max;       // longest segment of any pulsar (shared-memory records)
-    int32_t pad;
+    int32_t tape_cache;       // 1: tape slot holds every segment of the pulsar (no re-run)
     int* counter;             // persistent work counter (nullptr: one item per block)
 };
 

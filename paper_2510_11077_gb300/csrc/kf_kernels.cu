@@ -167,7 +167,8 @@ struct StepOut {   // what the adjoint needs from the forward step
     double K0, K1, rS, e, sn, cs;
 };
 
-template <bool kTape>
+// kTape: produce what the adjoint needs; kLL: accumulate the log-likelihood.
+template <bool kTape, bool kLL>
 __device__ __forceinline__ void kf_step(State& x, const double* __restrict__ rec, const Lane& L,
                                         PhaseTable tab, double& quad, LogProd& lp,
                                         StepOut& so) {
@@ -198,7 +199,8 @@ __device__ __forceinline__ void kf_step(State& x, const double* __restrict__ rec
     x.p11 = fma(-K1, M01, M11);
     if (kTape) {
         so.K0 = M00 * rS; so.K1 = K1; so.rS = rS; so.e = e; so.sn = sn; so.cs = cs;
-    } else {
+    }
+    if (kLL) {
         quad = fma(e, g, quad);
         lp.add(S);
     }
@@ -325,7 +327,7 @@ __global__ void __launch_bounds__(256) k_filter_fwd(FilterArgs a) {
             __syncthreads();
             if (active) {
                 for (int k = 0; k < cnt; ++k)
-                    kf_step<false>(x, sm.rec + k * kRecDoubles, L, sm.tab, quad, lp, so);
+                    kf_step<false, true>(x, sm.rec + k * kRecDoubles, L, sm.tab, quad, lp, so);
             }
         }
         if (active) a.lane_out[int64_t(wi.p) * a.B + b] = finish_ll(n, quad, lp);
@@ -341,7 +343,11 @@ __global__ void __launch_bounds__(256) k_filter_fwd(FilterArgs a) {
 // recording (K0, K1, 1/S, e, sin, cos) per step in the block's tape, then
 // run the adjoint steps in reverse.  Checkpoints and tape live in the block's
 // own slot of global scratch ([..][field][W], so a warp's accesses coalesce).
+// With kCache the tape of every segment is written during pass 1 and kept in
+// HBM (the slot holds the whole pulsar), so pass 2 skips the re-run: HBM
+// traffic is traded for FP64 work, which is the scarce resource here.
 // ---------------------------------------------------------------------------
+template <bool kCache>
 __global__ void __launch_bounds__(256) k_filter_grad(FilterArgs a) {
     const FilterSmem sm = filter_smem();
     __shared__ int s_item;
@@ -364,7 +370,7 @@ __global__ void __launch_bounds__(256) k_filter_grad(FilterArgs a) {
         double quad = 0.0;
         LogProd lp;
         StepOut so;
-        // pass 1: forward with checkpoints
+        // pass 1: forward with checkpoints (and, with kCache, the whole tape)
         for (int seg = 0; seg < nseg; ++seg) {
             const int k0 = seg * c, cnt = min(c, n - k0);
             __syncthreads();
@@ -373,8 +379,14 @@ __global__ void __launch_bounds__(256) k_filter_grad(FilterArgs a) {
             if (active) {
                 double* cp = ck + int64_t(seg) * kCkptDoubles * W;
                 cp[0 * W] = x.m0; cp[1 * W] = x.m1; cp[2 * W] = x.p00; cp[3 * W] = x.p01; cp[4 * W] = x.p11;
-                for (int k = 0; k < cnt; ++k)
-                    kf_step<false>(x, sm.rec + k * kRecDoubles, L, sm.tab, quad, lp, so);
+                for (int k = 0; k < cnt; ++k) {
+                    kf_step<kCache, true>(x, sm.rec + k * kRecDoubles, L, sm.tab, quad, lp, so);
+                    if (kCache) {
+                        double* tk = tp + int64_t(k0 + k) * kTapeDoubles * W;
+                        tk[0 * W] = so.K0; tk[1 * W] = so.K1; tk[2 * W] = so.rS;
+                        tk[3 * W] = so.e; tk[4 * W] = so.sn; tk[5 * W] = so.cs;
+                    }
+                }
             }
         }
         const double ll = finish_ll(n, quad, lp);
@@ -387,18 +399,21 @@ __global__ void __launch_bounds__(256) k_filter_grad(FilterArgs a) {
             stage_records(sm.rec, a.rec + (ps.off + k0) * kRecDoubles, cnt);
             __syncthreads();
             if (active) {
-                const double* cp = ck + int64_t(seg) * kCkptDoubles * W;
-                State y{cp[0 * W], cp[1 * W], cp[2 * W], cp[3 * W], cp[4 * W]};
-                double q2 = 0.0;
-                LogProd l2;
-                for (int k = 0; k < cnt; ++k) {
-                    kf_step<true>(y, sm.rec + k * kRecDoubles, L, sm.tab, q2, l2, so);
-                    double* tk = tp + int64_t(k) * kTapeDoubles * W;
-                    tk[0 * W] = so.K0; tk[1 * W] = so.K1; tk[2 * W] = so.rS;
-                    tk[3 * W] = so.e; tk[4 * W] = so.sn; tk[5 * W] = so.cs;
+                const double* ts = tp + int64_t(kCache ? k0 : 0) * kTapeDoubles * W;
+                if (!kCache) {
+                    const double* cp = ck + int64_t(seg) * kCkptDoubles * W;
+                    State y{cp[0 * W], cp[1 * W], cp[2 * W], cp[3 * W], cp[4 * W]};
+                    double q2 = 0.0;
+                    LogProd l2;
+                    for (int k = 0; k < cnt; ++k) {
+                        kf_step<true, false>(y, sm.rec + k * kRecDoubles, L, sm.tab, q2, l2, so);
+                        double* tk = tp + int64_t(k) * kTapeDoubles * W;
+                        tk[0 * W] = so.K0; tk[1 * W] = so.K1; tk[2 * W] = so.rS;
+                        tk[3 * W] = so.e; tk[4 * W] = so.sn; tk[5 * W] = so.cs;
+                    }
                 }
                 for (int k = cnt - 1; k >= 0; --k) {
-                    const double* tk = tp + int64_t(k) * kTapeDoubles * W;
+                    const double* tk = ts + int64_t(k) * kTapeDoubles * W;
                     StepOut sk{tk[0 * W], tk[1 * W], tk[2 * W], tk[3 * W], tk[4 * W], tk[5 * W]};
                     kf_step_adjoint(adj, sk, sm.rec + k * kRecDoubles, g);
                 }
@@ -500,7 +515,9 @@ void launch_filter_fwd(const FilterArgs& a, int W, int grid, cudaStream_t s) {
 }
 
 void launch_filter_grad(const FilterArgs& a, int W, int grid, cudaStream_t s) {
-    k_filter_grad<<<grid, W, filter_smem_bytes(true, a.stride_max), s>>>(a);
+    const size_t smem = filter_smem_bytes(true, a.stride_max);
+    if (a.tape_cache) k_filter_grad<true><<<grid, W, smem, s>>>(a);
+    else k_filter_grad<false><<<grid, W, smem, s>>>(a);
 }
 
 void launch_reduce(const double* theta, int64_t B, int32_t P, const PulsarDev* psr,

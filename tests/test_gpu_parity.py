@@ -231,3 +231,35 @@ def test_repeat_runs_are_deterministic(argus):
     a = run(argus, arr, theta, grad=True)
     b = run(argus, arr, theta, grad=True)
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_tape_cache_mode_matches_oracle_and_recompute_mode(argus):
+    data = inputs.make_array(np.array([1, 37, 200, 513, 129, 0]), seed=113, equad=1e-8)
+    theta = inputs.make_theta_batch(data, 150, seed=15)
+    arr = argus.argus_array_create(data)
+    ll0, g0 = run(argus, arr, theta, grad=True)
+    arr.set_plan(tape_cache=1)
+    ll1, g1 = run(argus, arr, theta, grad=True)
+    assert ll_err(ll1, ll0) <= 1e-13 and g_err(g1, g0) <= 1e-12
+    idx = np.array([0, 77, 149])
+    ll_ref, g_ref = kalman.loglik_grad(data, theta[idx])
+    assert ll_err(ll1[idx], ll_ref) <= LL_TOL and g_err(g1[idx], g_ref) <= G_TOL
+
+
+def test_autotuner_picks_and_caches_a_plan(argus, tmp_path):
+    from paper_2510_11077_gb300 import autotune
+    data = inputs.make_array(np.array([300, 120, 700]), seed=114)
+    theta = torch.from_numpy(inputs.make_theta_batch(data, 300, seed=16)).cuda()
+    arr = argus.argus_array_create(data)
+    cache = str(tmp_path / "plans.json")
+    space = {"walkers_per_cta": (64, 128), "ctas_per_sm": (2, 4), "tape_cache": (0, 1)}
+    res = autotune.autotune(arr, theta, data.n_toa, grad=True, space=space, cache_path=cache)
+    assert not res["cached"] and len(res["tried"]) == 8
+    assert arr.get_plan()["walkers_per_cta"] == res["plan"]["walkers_per_cta"]
+    arr2 = argus.argus_array_create(data)
+    res2 = autotune.autotune(arr2, theta, data.n_toa, grad=True, space=space, cache_path=cache)
+    assert res2["cached"] and res2["plan"] == res["plan"]
+    ll, g = argus.argus_loglik_grad(arr2, theta)
+    ll_ref, g_ref = kalman.loglik_grad(data, theta[:3].cpu().numpy())
+    assert ll_err(ll[:3].cpu().numpy(), ll_ref) <= LL_TOL
+    assert g_err(g[:3].cpu().numpy(), g_ref) <= G_TOL
