@@ -188,6 +188,7 @@ def run_ours(args):
     import torch
 
     from paper_2510_11077_gb300 import argus, inputs
+    from paper_2510_11077_gb300 import dist as pdist
 
     world, rank, local = dist_env()
     if world > 1:
@@ -198,7 +199,7 @@ def run_ours(args):
     w = inputs.WORKLOADS[args.workload]
     data = inputs.make_workload_array(w.name)
     B, D = w.batch, data.dim
-    theta_np = inputs.make_theta_batch(data, B, seed=w.seed + 7919 * rank)
+    theta_np = inputs.make_theta_batch(data, B, seed=pdist.rank_seed(w.seed, rank))
     theta = torch.from_numpy(theta_np).to(dev)
     arr = argus.Array(data, device=local)
     tuned = None
@@ -252,12 +253,8 @@ def run_ours(args):
         torch.distributed.barrier()
     clk = clocks.stop() if clocks else None
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * B * args.steps / (total_ms / 1e3)
+    total_ms = pdist.max_over_ranks(sum(step_ms), device=dev)
+    value = pdist.job_throughput(B * args.steps, world, total_ms / 1e3)
     filt_ms = statistics.mean(k[1] for k in kern)
 
     # end to end through the public call with pinned host buffers
@@ -273,12 +270,8 @@ def run_ours(args):
         t0 = time.perf_counter()
         for _ in range(args.steps):
             argus.argus_loglik_grad(arr, th_h, ll_h, g_h)   # H2D, compute, D2H, sync
-        e2e_s = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e2e_s = float(t.item())
-        e2e = {"value": world * B * args.steps / e2e_s, "unit": UNIT,
+        e2e_s = pdist.max_over_ranks(time.perf_counter() - t0, device=dev)
+        e2e = {"value": pdist.job_throughput(B * args.steps, world, e2e_s), "unit": UNIT,
                "h2d_bytes_per_step": B * D * 8, "d2h_bytes_per_step": B * 8 + B * D * 8}
         if not np.allclose(ll_h.numpy(), ll.cpu().numpy(), rtol=0, atol=0, equal_nan=True):
             raise RuntimeError("host-buffer path disagrees with the device path")
