@@ -32,6 +32,22 @@ argus_status argus_selftest_rcp(const double* S, int64_t n, double* out);
  * is not a positive, normal, finite number. */
 argus_status argus_selftest_logsum(const double* S, int64_t n, double* out, int32_t* bad);
 
+/* The tensor-core GEMM of the surrogate network, plain FP32 epilogue:
+ * for each K-chunk z < chunks, C[z][m][n] = sum_k A[m][zK + k] B[n][zK + k]
+ * with K = k_total / chunks.  A [M][k_total], B [N][k_total] as BF16 bit
+ * patterns (uint16), C [chunks][M][N] FP32; M a multiple of 128, K a multiple
+ * of 64 and <= 256, bn (64 or 128) divides N.  Returns ARGUS_ERR_TIMEOUT if a
+ * bounded device-side wait gave up. */
+argus_status argus_selftest_gemm(const uint16_t* A, const uint16_t* B, int32_t M, int32_t N,
+                                 int32_t k_total, int32_t bn, int32_t chunks, float* C);
+
+/* Gradient of the loss of the last argus_surrogate_train_step, in the flat
+ * parameter layout of argus_surrogate.h (host array of
+ * argus_surrogate_param_count() floats): the fixed-order sum of the split-K
+ * weight partials and the bias column sums that the Adam update consumed. */
+struct argus_surrogate;
+argus_status argus_selftest_surrogate_grads(struct argus_surrogate* s, float* grads);
+
 #ifdef __cplusplus
 }
 #endif

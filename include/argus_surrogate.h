@@ -1,0 +1,88 @@
+/*
+ * argus_surrogate.h -- C ABI of the learned surrogate of the array
+ * log-likelihood and its gradient.
+ *
+ * The target path pairs the exact filter with a small network trained on the
+ * exact filter's own evaluations and used as the first stage of a
+ * delayed-acceptance sampler whose second stage, fallback and judge is the
+ * exact FP64 filter (argus.h).  The paper's own sampler integration
+ * (Functionality, "Sampler Integration") calls a likelihood and its gradient
+ * at every step; the surrogate supplies a cheap approximation of both.
+ *
+ * Network: 47 -> 256 -> 256 -> 256 -> 256 -> 48, GELU (exact erf form) after
+ * each hidden layer; BF16 weights and activations, FP32 accumulation on the
+ * tensor cores (tcgen05, TMA-staged operands), FP32 master weights and Adam
+ * (beta1 0.9, beta2 0.999, eps 1e-8).  The 47 inputs are a 20-pulsar array's
+ * parameter vector (7 source + 2 x 20 noise); the 48 outputs are the
+ * log-likelihood and its 47 derivatives.  Inputs are standardized by
+ * (x - x_mean) / x_std; the value output is (ll - y_mean) / y_std and output
+ * 1 + k is dll/dx_k * x_std_k / y_std (the gradient in standardized units).
+ *
+ * Parameters, as one flat FP32 array of argus_surrogate_param_count() values:
+ * for each layer l = 0..4, W_l row-major [N_l][K_l] then b_l [N_l], with
+ * (K_l, N_l) = (64, 256), (256, 256), (256, 256), (256, 256), (256, 64); the
+ * padding (input columns 47..63 of W_0, output rows 48..63 of W_4 and b_4) is
+ * zero and stays zero.
+ *
+ * Device pointers throughout (ARGUS_ERR_INVALID_ARG otherwise); calls are
+ * asynchronous on `stream` except create/destroy/set/get, which synchronise.
+ */
+#ifndef ARGUS_SURROGATE_H
+#define ARGUS_SURROGATE_H
+
+#include <stdint.h>
+
+#include "argus.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct argus_surrogate argus_surrogate;
+
+/* Number of FP32 parameters in the flat layout above. */
+int64_t argus_surrogate_param_count(void);
+
+/* Allocate a network on `device` for batches of up to max_rows rows (rounded
+ * up to a multiple of 256) with fan-in scaled normal weights drawn from
+ * `seed`, zero biases, and identity normalizers.  ARGUS_ERR_UNSUPPORTED if
+ * the device is not sm_103. */
+argus_status argus_surrogate_create(int32_t device, int32_t max_rows, uint64_t seed,
+                                    argus_surrogate** out);
+void argus_surrogate_destroy(argus_surrogate* s);
+
+/* Host arrays x_mean[47], x_std[47] (> 0); value mean/std (> 0); loss
+ * weights of the value output and of each gradient output (>= 0). */
+argus_status argus_surrogate_set_normalizers(argus_surrogate* s, const float* x_mean,
+                                             const float* x_std, float y_mean, float y_std,
+                                             float value_weight, float grad_weight);
+
+/* Copy all parameters from / to a host array in the flat layout.  set_weights
+ * also resets the Adam state and step count. */
+argus_status argus_surrogate_set_weights(argus_surrogate* s, const float* params);
+argus_status argus_surrogate_get_weights(argus_surrogate* s, float* params);
+
+/* Surrogate log-likelihood and gradient of B parameter vectors:
+ * theta [B][47], loglik [B], grad [B][47] or NULL (FP32, device). */
+argus_status argus_surrogate_eval(argus_surrogate* s, const float* theta, int64_t B, float* loglik,
+                                  float* grad, void* stream);
+
+/* One Adam step on a minibatch of n <= max_rows exact evaluations:
+ * theta [n][47], loglik [n], grad [n][47] (FP32, device).  The loss is the
+ * weighted mean squared error of the standardized outputs; *loss (device
+ * FP32) receives its value before the step. */
+argus_status argus_surrogate_train_step(argus_surrogate* s, const float* theta, const float* loglik,
+                                        const float* grad, int64_t n, float lr, float* loss,
+                                        void* stream);
+
+/* Synchronise and report whether a bounded device-side wait of the tensor-core
+ * kernels gave up since the last check (ARGUS_ERR_TIMEOUT; the flag is then
+ * cleared).  Message of the last surrogate error on this host thread. */
+argus_status argus_surrogate_check(argus_surrogate* s);
+const char* argus_surrogate_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ARGUS_SURROGATE_H */

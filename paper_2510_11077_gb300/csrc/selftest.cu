@@ -5,6 +5,7 @@
 
 #include "../../include/argus_selftest.h"
 #include "kf_math.cuh"
+#include "mlp_internal.cuh"
 
 namespace {
 
@@ -109,6 +110,39 @@ argus_status argus_selftest_logsum(const double* S, int64_t n, double* out, int3
     TRY(cudaMemcpy(&hb, dbad, sizeof(int), cudaMemcpyDeviceToHost));
     *bad = hb;
     return ARGUS_OK;
+}
+
+argus_status argus_selftest_gemm(const uint16_t* A, const uint16_t* B, int32_t M, int32_t N,
+                                 int32_t k_total, int32_t bn, int32_t chunks, float* C) {
+    if (!A || !B || !C || M <= 0 || N <= 0 || chunks < 1 || k_total <= 0 || k_total % chunks ||
+        M % 128 || (bn != 64 && bn != 128) || N % bn)
+        return ARGUS_ERR_INVALID_ARG;
+    const int K = k_total / chunks;
+    if (K % 64 || K > 256) return ARGUS_ERR_INVALID_ARG;
+    const size_t na = size_t(M) * k_total, nb = size_t(N) * k_total, nc = size_t(chunks) * M * N;
+    DevBuf bufA, bufB, bufC, bufE;
+    TRY(cudaMalloc(&bufA.p, na * 2));
+    TRY(cudaMalloc(&bufB.p, nb * 2));
+    TRY(cudaMalloc(&bufC.p, nc * 4));
+    TRY(cudaMalloc(&bufE.p, sizeof(int)));
+    TRY(cudaMemcpy(bufA.p, A, na * 2, cudaMemcpyHostToDevice));
+    TRY(cudaMemcpy(bufB.p, B, nb * 2, cudaMemcpyHostToDevice));
+    TRY(cudaMemset(bufC.p, 0, nc * 4));
+    TRY(cudaMemset(bufE.p, 0, sizeof(int)));
+    CUtensorMap ta, tb;
+    if (!make_tmap_bf16(&ta, bufA.p, uint64_t(M), uint64_t(k_total), 128) ||
+        !make_tmap_bf16(&tb, bufB.p, uint64_t(N), uint64_t(k_total), uint32_t(bn)))
+        return ARGUS_ERR_CUDA;
+    GemmEpiArgs e{};
+    e.out_f32 = static_cast<float*>(bufC.p);
+    e.ldo = N;
+    e.chunk_stride = int64_t(M) * N;
+    TRY(launch_gemm_tc(&ta, &tb, M, N, K, bn, chunks, kEpiF32, e, static_cast<int*>(bufE.p), nullptr));
+    TRY(cudaDeviceSynchronize());
+    int err = 0;
+    TRY(cudaMemcpy(&err, bufE.p, sizeof(int), cudaMemcpyDeviceToHost));
+    TRY(cudaMemcpy(C, bufC.p, nc * 4, cudaMemcpyDeviceToHost));
+    return err ? ARGUS_ERR_TIMEOUT : ARGUS_OK;
 }
 
 }  // extern "C"

@@ -1,0 +1,637 @@
+// Surrogate network of the array log-likelihood and its gradient:
+// MLP 47 -> 256 -> 256 -> 256 -> 256 -> 48 (GELU), BF16 weights and
+// activations, FP32 accumulation on the tensor cores (mlp_gemm.cu), FP32
+// master weights and Adam.  C ABI in include/argus_surrogate.h.
+//
+// Layer l computes z = x W_l^T + b_l.  Shapes are padded for the tensor
+// cores: the input has 64 columns (47 used), the output 64 (48 used); padding
+// weights are zero and get zero gradient.  Inputs are standardized
+// (x_k - mean_k) / std_k; the value head predicts (ll - y_mean) / y_std and
+// the gradient head predicts dll/dx_k * std_k / y_std.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/argus_selftest.h"
+#include "../../include/argus_surrogate.h"
+#include "mlp_internal.cuh"
+
+using namespace argus;
+
+namespace {
+
+thread_local std::string g_sur_error;
+
+argus_status sfail(argus_status st, const std::string& m) {
+    g_sur_error = m;
+    return st;
+}
+
+argus_status scuda(cudaError_t e, const char* what) {
+    return sfail(e == cudaErrorMemoryAllocation ? ARGUS_ERR_OOM : ARGUS_ERR_CUDA,
+                 std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define SCK(call)                                          \
+    do {                                                   \
+        cudaError_t _e = (call);                           \
+        if (_e != cudaSuccess) return scuda(_e, #call);    \
+    } while (0)
+
+constexpr int kIn[kMlpLayers] = {kMlpInPad, kMlpHidden, kMlpHidden, kMlpHidden, kMlpHidden};
+constexpr int kOut[kMlpLayers] = {kMlpHidden, kMlpHidden, kMlpHidden, kMlpHidden, kMlpOutPad};
+
+struct DeviceGuardS {
+    int prev = -1;
+    explicit DeviceGuardS(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuardS() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+// ---------------------------------------------------------------------------
+// small kernels
+// ---------------------------------------------------------------------------
+struct Norm {
+    float xm[kMlpInPad], xs[kMlpInPad];   // input mean / std (pad: 0 / 1)
+    float ym, ys;                          // value mean / std
+    float w[kMlpOut];                      // loss weights (value, then gradient components)
+};
+
+// X0[r][k] = bf16((theta[r][k] - xm_k) / xs_k) for k < 47, 0 otherwise; rows >= n are 0.
+// xt (optional) is the transposed copy [64][pitch].
+__global__ void k_standardize(const float* __restrict__ theta, int64_t n, int rows, Norm nm,
+                              __nv_bfloat16* __restrict__ x, __nv_bfloat16* __restrict__ xt,
+                              int pitch) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= rows) return;
+    for (int k = 0; k < kMlpInPad; ++k) {
+        float v = 0.0f;
+        if (r < n && k < kMlpIn) v = (theta[int64_t(r) * kMlpIn + k] - nm.xm[k]) / nm.xs[k];
+        const __nv_bfloat16 b = __float2bfloat16_rn(v);
+        x[int64_t(r) * kMlpInPad + k] = b;
+        if (xt) xt[int64_t(k) * pitch + r] = b;
+    }
+}
+
+// Standardized targets, weighted squared error per row, and
+// dY = bf16(2 w_j (y - t) / n) (+ its transpose); padding rows and columns get 0.
+__global__ void k_loss(const float* __restrict__ y, const float* __restrict__ ll,
+                       const float* __restrict__ grad, int64_t n, int rows, Norm nm,
+                       __nv_bfloat16* __restrict__ dy, __nv_bfloat16* __restrict__ dyt, int pitch,
+                       float* __restrict__ row_loss) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= rows) return;
+    float acc = 0.0f;
+    for (int j = 0; j < kMlpOutPad; ++j) {
+        float d = 0.0f;
+        if (r < n && j < kMlpOut) {
+            const float t = (j == 0) ? (ll[r] - nm.ym) / nm.ys
+                                     : grad[int64_t(r) * kMlpIn + (j - 1)] * nm.xs[j - 1] / nm.ys;
+            const float e = y[int64_t(r) * kMlpOutPad + j] - t;
+            acc += nm.w[j] * e * e;
+            d = 2.0f * nm.w[j] * e / float(n);
+        }
+        const __nv_bfloat16 b = __float2bfloat16_rn(d);
+        dy[int64_t(r) * kMlpOutPad + j] = b;
+        dyt[int64_t(j) * pitch + r] = b;
+    }
+    row_loss[r] = (r < n) ? acc : 0.0f;
+}
+
+// loss = sum_r row_loss[r] / n (fixed order)
+__global__ void k_loss_sum(const float* __restrict__ row_loss, int rows, int64_t n,
+                           float* __restrict__ out) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    float s = 0.0f;
+    for (int r = 0; r < rows; ++r) s += row_loss[r];
+    *out = s / float(n);
+}
+
+// Column sums (bias gradients), fixed row order: out[c] = sum_r m[r][c].
+__global__ void k_colsum_f32(const float* __restrict__ m, int rows, int cols, float* __restrict__ out) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= cols) return;
+    float s = 0.0f;
+    for (int r = 0; r < rows; ++r) s += m[int64_t(r) * cols + c];
+    out[c] = s;
+}
+
+__global__ void k_colsum_bf16(const __nv_bfloat16* __restrict__ m, int rows, int cols,
+                              float* __restrict__ out) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= cols) return;
+    float s = 0.0f;
+    for (int r = 0; r < rows; ++r) s += __bfloat162float(m[int64_t(r) * cols + c]);
+    out[c] = s;
+}
+
+// Adam on one weight matrix W [N][K] (FP32 master) with its gradient as the
+// fixed-order sum of split-K partials; transposed partials for the last layer.
+__global__ void k_adam_w(float* __restrict__ W, float* __restrict__ m, float* __restrict__ v,
+                         const float* __restrict__ part, int chunks, int64_t chunk_stride, int N,
+                         int K, int transposed, float lr, float c1, float c2,
+                         __nv_bfloat16* __restrict__ w16, __nv_bfloat16* __restrict__ w16t) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= N * K) return;
+    const int o = idx / K, i = idx % K;
+    const int pidx = transposed ? (i * N + o) : idx;
+    float g = 0.0f;
+    for (int c = 0; c < chunks; ++c) g += part[int64_t(c) * chunk_stride + pidx];
+    const float mm = 0.9f * m[idx] + 0.1f * g;
+    const float vv = 0.999f * v[idx] + 0.001f * g * g;
+    m[idx] = mm;
+    v[idx] = vv;
+    const float w = W[idx] - lr * (mm / c1) / (sqrtf(vv / c2) + 1e-8f);
+    W[idx] = w;
+    const __nv_bfloat16 b = __float2bfloat16_rn(w);
+    w16[idx] = b;
+    w16t[int64_t(i) * N + o] = b;
+}
+
+__global__ void k_adam_b(float* __restrict__ b, float* __restrict__ m, float* __restrict__ v,
+                         const float* __restrict__ g, int N, float lr, float c1, float c2) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const float mm = 0.9f * m[i] + 0.1f * g[i];
+    const float vv = 0.999f * v[i] + 0.001f * g[i] * g[i];
+    m[i] = mm;
+    v[i] = vv;
+    b[i] = b[i] - lr * (mm / c1) / (sqrtf(vv / c2) + 1e-8f);
+}
+
+// BF16 copies (and transposes) of the FP32 master weights.
+__global__ void k_cast_w(const float* __restrict__ W, int N, int K, __nv_bfloat16* __restrict__ w16,
+                         __nv_bfloat16* __restrict__ w16t) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= N * K) return;
+    const int o = idx / K, i = idx % K;
+    const __nv_bfloat16 b = __float2bfloat16_rn(W[idx]);
+    w16[idx] = b;
+    w16t[int64_t(i) * N + o] = b;
+}
+
+// De-standardize: ll = y0 ys + ym, grad_k = y_{1+k} ys / xs_k.
+__global__ void k_destandardize(const float* __restrict__ y, int64_t n, Norm nm,
+                                float* __restrict__ ll, float* __restrict__ grad) {
+    const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const float* yr = y + r * kMlpOutPad;
+    ll[r] = yr[0] * nm.ys + nm.ym;
+    if (grad)
+        for (int k = 0; k < kMlpIn; ++k) grad[r * kMlpIn + k] = yr[1 + k] * nm.ys / nm.xs[k];
+}
+
+template <class T>
+argus_status dalloc(T** p, size_t n) {
+    SCK(cudaMalloc(reinterpret_cast<void**>(p), std::max<size_t>(n, 1) * sizeof(T)));
+    return ARGUS_OK;
+}
+
+}  // namespace
+
+struct argus_surrogate {
+    int device = 0;
+    int rows = 0;          // capacity (multiple of 128)
+    int step = 0;
+    Norm norm{};
+    float* W[kMlpLayers] = {};
+    float* b[kMlpLayers] = {};
+    float* mW[kMlpLayers] = {};
+    float* vW[kMlpLayers] = {};
+    float* mb[kMlpLayers] = {};
+    float* vb[kMlpLayers] = {};
+    float* gb[kMlpLayers] = {};
+    float* part[kMlpLayers] = {};
+    __nv_bfloat16* W16[kMlpLayers] = {};
+    __nv_bfloat16* W16T[kMlpLayers] = {};
+    // activations: H[0] = standardized input [rows][64], H[l] [rows][256]
+    __nv_bfloat16* H[kMlpLayers] = {};
+    __nv_bfloat16* HT[kMlpLayers] = {};
+    float* Z[kMlpLayers] = {};      // Z[l] = pre-activation feeding H[l] (l = 1..4)
+    float* Y = nullptr;
+    __nv_bfloat16* dY = nullptr;
+    __nv_bfloat16* dYT = nullptr;
+    float* dZ32[2] = {};
+    __nv_bfloat16* dZ16[2] = {};
+    __nv_bfloat16* dZT[2] = {};
+    float* row_loss = nullptr;
+    int* err = nullptr;
+    int last_chunks = 0;   // split-K chunks of the last training step
+    // tensor maps
+    CUtensorMap tmW[kMlpLayers], tmWT[kMlpLayers], tmH[kMlpLayers], tmHT[kMlpLayers];
+    CUtensorMap tmdY, tmdYT, tmdZ16[2], tmdZT[2];
+};
+
+namespace {
+
+void free_all(argus_surrogate* s) {
+    for (int l = 0; l < kMlpLayers; ++l) {
+        cudaFree(s->W[l]); cudaFree(s->b[l]); cudaFree(s->mW[l]); cudaFree(s->vW[l]);
+        cudaFree(s->mb[l]); cudaFree(s->vb[l]); cudaFree(s->gb[l]); cudaFree(s->part[l]);
+        cudaFree(s->W16[l]); cudaFree(s->W16T[l]); cudaFree(s->H[l]); cudaFree(s->HT[l]);
+        cudaFree(s->Z[l]);
+    }
+    cudaFree(s->Y); cudaFree(s->dY); cudaFree(s->dYT); cudaFree(s->row_loss); cudaFree(s->err);
+    for (int i = 0; i < 2; ++i) {
+        cudaFree(s->dZ32[i]); cudaFree(s->dZ16[i]); cudaFree(s->dZT[i]);
+    }
+}
+
+argus_status build_maps(argus_surrogate* s) {
+    const uint64_t R = uint64_t(s->rows);
+    bool ok = true;
+    for (int l = 0; l < kMlpLayers; ++l) {
+        ok &= make_tmap_bf16(&s->tmW[l], s->W16[l], kOut[l], kIn[l], kOut[l] == 64 ? 64 : 128);
+        ok &= make_tmap_bf16(&s->tmWT[l], s->W16T[l], kIn[l], kOut[l], 128);
+        ok &= make_tmap_bf16(&s->tmH[l], s->H[l], R, kIn[l], 128);
+        ok &= make_tmap_bf16(&s->tmHT[l], s->HT[l], kIn[l], R, kIn[l] == 64 ? 64 : 128);
+    }
+    ok &= make_tmap_bf16(&s->tmdY, s->dY, R, kMlpOutPad, 128);
+    ok &= make_tmap_bf16(&s->tmdYT, s->dYT, kMlpOutPad, R, 64);
+    for (int i = 0; i < 2; ++i) {
+        ok &= make_tmap_bf16(&s->tmdZ16[i], s->dZ16[i], R, kMlpHidden, 128);
+        ok &= make_tmap_bf16(&s->tmdZT[i], s->dZT[i], kMlpHidden, R, 128);
+    }
+    return ok ? ARGUS_OK : sfail(ARGUS_ERR_CUDA, "cuTensorMapEncodeTiled refused a tensor map");
+}
+
+// Refresh BF16 copies from the FP32 master weights.
+argus_status cast_weights(argus_surrogate* s, cudaStream_t st) {
+    for (int l = 0; l < kMlpLayers; ++l) {
+        const int n = kOut[l] * kIn[l];
+        k_cast_w<<<(n + 255) / 256, 256, 0, st>>>(s->W[l], kOut[l], kIn[l], s->W16[l], s->W16T[l]);
+    }
+    SCK(cudaGetLastError());
+    return ARGUS_OK;
+}
+
+GemmEpiArgs epi_none() {
+    GemmEpiArgs e{};
+    return e;
+}
+
+// Forward over `rows` rows already standardized in H[0].  train: also save
+// pre-activations and transposed activations for the backward pass.
+argus_status forward(argus_surrogate* s, int rows, bool train, cudaStream_t st) {
+    for (int l = 0; l < kMlpLayers; ++l) {
+        GemmEpiArgs e = epi_none();
+        e.bias = s->b[l];
+        const int N = kOut[l], K = kIn[l];
+        const int bn = N == 64 ? 64 : 128;
+        cudaError_t ce;
+        if (l < kMlpLayers - 1) {
+            e.out_f32 = train ? s->Z[l + 1] : nullptr;
+            e.ldo = N;
+            e.out_bf16 = s->H[l + 1];
+            e.ldb = N;
+            e.out_bf16_t = train ? s->HT[l + 1] : nullptr;
+            e.ldt = s->rows;
+            ce = launch_gemm_tc(&s->tmH[l], &s->tmW[l], rows, N, K, bn, 1, kEpiGelu, e, s->err, st);
+        } else {
+            e.out_f32 = s->Y;
+            e.ldo = N;
+            ce = launch_gemm_tc(&s->tmH[l], &s->tmW[l], rows, N, K, bn, 1, kEpiF32, e, s->err, st);
+        }
+        if (ce != cudaSuccess) return scuda(ce, "forward GEMM");
+    }
+    return ARGUS_OK;
+}
+
+argus_status check_err(argus_surrogate* s) {
+    int e = 0;
+    SCK(cudaMemcpy(&e, s->err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e) {
+        cudaMemset(s->err, 0, sizeof(int));
+        return sfail(ARGUS_ERR_TIMEOUT, "a tensor-core GEMM wait timed out (code " + std::to_string(e) + ")");
+    }
+    return ARGUS_OK;
+}
+
+bool dev_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+extern "C" {
+
+int64_t argus_surrogate_param_count(void) {
+    int64_t n = 0;
+    for (int l = 0; l < kMlpLayers; ++l) n += int64_t(kOut[l]) * kIn[l] + kOut[l];
+    return n;
+}
+
+argus_status argus_surrogate_create(int32_t device, int32_t max_rows, uint64_t seed,
+                                    argus_surrogate** out) {
+    if (!out) return sfail(ARGUS_ERR_INVALID_ARG, "out is NULL");
+    if (max_rows < 1 || max_rows > (1 << 20)) return sfail(ARGUS_ERR_INVALID_ARG, "max_rows out of range");
+    int ndev = 0;
+    SCK(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) return sfail(ARGUS_ERR_INVALID_ARG, "no such device");
+    cudaDeviceProp prop{};
+    SCK(cudaGetDeviceProperties(&prop, device));
+    if (prop.major != 10 || prop.minor != 3)
+        return sfail(ARGUS_ERR_UNSUPPORTED, std::string("built for sm_103a, device is ") + prop.name);
+    DeviceGuardS guard(device);
+    argus_surrogate* s = new argus_surrogate();
+    s->device = device;
+    s->rows = ((max_rows + 255) / 256) * 256;
+    const size_t R = size_t(s->rows);
+    const int max_chunks = s->rows / 128;
+    argus_status st = ARGUS_OK;
+    auto A = [&](argus_status x) { if (x && !st) st = x; };
+    for (int l = 0; l < kMlpLayers; ++l) {
+        const size_t nw = size_t(kOut[l]) * kIn[l];
+        A(dalloc(&s->W[l], nw)); A(dalloc(&s->b[l], kOut[l]));
+        A(dalloc(&s->mW[l], nw)); A(dalloc(&s->vW[l], nw));
+        A(dalloc(&s->mb[l], kOut[l])); A(dalloc(&s->vb[l], kOut[l])); A(dalloc(&s->gb[l], kOut[l]));
+        A(dalloc(&s->part[l], nw * max_chunks));
+        A(dalloc(&s->W16[l], nw)); A(dalloc(&s->W16T[l], nw));
+        A(dalloc(&s->H[l], R * kIn[l])); A(dalloc(&s->HT[l], R * kIn[l]));
+        A(dalloc(&s->Z[l], R * kMlpHidden));
+    }
+    A(dalloc(&s->Y, R * kMlpOutPad));
+    A(dalloc(&s->dY, R * kMlpOutPad)); A(dalloc(&s->dYT, R * kMlpOutPad));
+    for (int i = 0; i < 2; ++i) {
+        A(dalloc(&s->dZ32[i], R * kMlpHidden)); A(dalloc(&s->dZ16[i], R * kMlpHidden));
+        A(dalloc(&s->dZT[i], R * kMlpHidden));
+    }
+    A(dalloc(&s->row_loss, R));
+    A(dalloc(&s->err, 1));
+    if (!st) {
+        // fan-in scaled normal weights from a seeded host generator (Box-Muller on splitmix64)
+        std::vector<float> w;
+        uint64_t x = seed ? seed : 0x9E3779B97F4A7C15ull;
+        auto next = [&]() {
+            x += 0x9E3779B97F4A7C15ull;
+            uint64_t z = x;
+            z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+            z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+            return double((z ^ (z >> 31)) >> 11) * (1.0 / 9007199254740992.0);
+        };
+        for (int l = 0; l < kMlpLayers && !st; ++l) {
+            const int N = kOut[l], K = kIn[l];
+            const int fan_in = (l == 0) ? kMlpIn : K;
+            const double sd = std::sqrt(2.0 / fan_in) * (l == kMlpLayers - 1 ? 0.5 : 1.0);
+            w.assign(size_t(N) * K, 0.0f);
+            for (int o = 0; o < N; ++o)
+                for (int i = 0; i < K; ++i) {
+                    const double u1 = std::max(next(), 1e-300), u2 = next();
+                    const double g = std::sqrt(-2.0 * std::log(u1)) * std::cos(6.283185307179586 * u2);
+                    const bool pad = (l == 0 && i >= kMlpIn) || (l == kMlpLayers - 1 && o >= kMlpOut);
+                    w[size_t(o) * K + i] = pad ? 0.0f : float(g * sd);
+                }
+            if (cudaMemcpy(s->W[l], w.data(), w.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+                cudaMemset(s->b[l], 0, N * 4) != cudaSuccess)
+                st = sfail(ARGUS_ERR_CUDA, "initial weights");
+        }
+        for (int l = 0; l < kMlpLayers && !st; ++l) {
+            const size_t nw = size_t(kOut[l]) * kIn[l];
+            if (cudaMemset(s->mW[l], 0, nw * 4) || cudaMemset(s->vW[l], 0, nw * 4) ||
+                cudaMemset(s->mb[l], 0, kOut[l] * 4) || cudaMemset(s->vb[l], 0, kOut[l] * 4))
+                st = sfail(ARGUS_ERR_CUDA, "optimizer state");
+        }
+        if (!st && cudaMemset(s->err, 0, sizeof(int)) != cudaSuccess) st = sfail(ARGUS_ERR_CUDA, "err");
+    }
+    if (!st) st = build_maps(s);
+    if (!st) st = cast_weights(s, nullptr);
+    if (!st && cudaDeviceSynchronize() != cudaSuccess) st = sfail(ARGUS_ERR_CUDA, "create sync");
+    if (st) {
+        free_all(s);
+        delete s;
+        return st;
+    }
+    for (int k = 0; k < kMlpInPad; ++k) { s->norm.xm[k] = 0.0f; s->norm.xs[k] = 1.0f; }
+    s->norm.ym = 0.0f; s->norm.ys = 1.0f;
+    for (int j = 0; j < kMlpOut; ++j) s->norm.w[j] = 1.0f;
+    *out = s;
+    return ARGUS_OK;
+}
+
+void argus_surrogate_destroy(argus_surrogate* s) {
+    if (!s) return;
+    DeviceGuardS guard(s->device);
+    cudaDeviceSynchronize();
+    free_all(s);
+    delete s;
+}
+
+argus_status argus_surrogate_set_normalizers(argus_surrogate* s, const float* x_mean,
+                                             const float* x_std, float y_mean, float y_std,
+                                             float value_weight, float grad_weight) {
+    if (!s || !x_mean || !x_std) return sfail(ARGUS_ERR_INVALID_ARG, "NULL argument");
+    for (int k = 0; k < kMlpIn; ++k)
+        if (!(x_std[k] > 0.0f) || !std::isfinite(x_mean[k]))
+            return sfail(ARGUS_ERR_INVALID_ARG, "x_std must be > 0 and x_mean finite");
+    if (!(y_std > 0.0f) || !std::isfinite(y_mean) || !(value_weight >= 0.0f) || !(grad_weight >= 0.0f))
+        return sfail(ARGUS_ERR_INVALID_ARG, "bad value normalizer or loss weights");
+    for (int k = 0; k < kMlpInPad; ++k) {
+        s->norm.xm[k] = k < kMlpIn ? x_mean[k] : 0.0f;
+        s->norm.xs[k] = k < kMlpIn ? x_std[k] : 1.0f;
+    }
+    s->norm.ym = y_mean;
+    s->norm.ys = y_std;
+    s->norm.w[0] = value_weight;
+    for (int j = 1; j < kMlpOut; ++j) s->norm.w[j] = grad_weight;
+    return ARGUS_OK;
+}
+
+argus_status argus_surrogate_set_weights(argus_surrogate* s, const float* params) {
+    if (!s || !params) return sfail(ARGUS_ERR_INVALID_ARG, "NULL argument");
+    DeviceGuardS guard(s->device);
+    const float* p = params;
+    for (int l = 0; l < kMlpLayers; ++l) {
+        const size_t nw = size_t(kOut[l]) * kIn[l];
+        SCK(cudaMemcpy(s->W[l], p, nw * 4, cudaMemcpyHostToDevice));
+        p += nw;
+        SCK(cudaMemcpy(s->b[l], p, kOut[l] * 4, cudaMemcpyHostToDevice));
+        p += kOut[l];
+        SCK(cudaMemset(s->mW[l], 0, nw * 4));
+        SCK(cudaMemset(s->vW[l], 0, nw * 4));
+        SCK(cudaMemset(s->mb[l], 0, kOut[l] * 4));
+        SCK(cudaMemset(s->vb[l], 0, kOut[l] * 4));
+    }
+    s->step = 0;
+    argus_status st = cast_weights(s, nullptr);
+    if (st) return st;
+    SCK(cudaDeviceSynchronize());
+    return ARGUS_OK;
+}
+
+argus_status argus_surrogate_get_weights(argus_surrogate* s, float* params) {
+    if (!s || !params) return sfail(ARGUS_ERR_INVALID_ARG, "NULL argument");
+    DeviceGuardS guard(s->device);
+    SCK(cudaDeviceSynchronize());
+    float* p = params;
+    for (int l = 0; l < kMlpLayers; ++l) {
+        const size_t nw = size_t(kOut[l]) * kIn[l];
+        SCK(cudaMemcpy(p, s->W[l], nw * 4, cudaMemcpyDeviceToHost));
+        p += nw;
+        SCK(cudaMemcpy(p, s->b[l], kOut[l] * 4, cudaMemcpyDeviceToHost));
+        p += kOut[l];
+    }
+    return ARGUS_OK;
+}
+
+argus_status argus_surrogate_eval(argus_surrogate* s, const float* theta, int64_t B, float* loglik,
+                                  float* grad, void* stream) {
+    if (!s) return sfail(ARGUS_ERR_INVALID_ARG, "surrogate handle is NULL");
+    if (B < 0) return sfail(ARGUS_ERR_INVALID_ARG, "B must be >= 0");
+    if (B == 0) return ARGUS_OK;
+    if (!theta || !loglik) return sfail(ARGUS_ERR_INVALID_ARG, "NULL theta or loglik");
+    DeviceGuardS guard(s->device);
+    if (!dev_ptr(theta) || !dev_ptr(loglik) || (grad && !dev_ptr(grad)))
+        return sfail(ARGUS_ERR_INVALID_ARG, "argus_surrogate_eval needs device pointers");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    for (int64_t r0 = 0; r0 < B; r0 += s->rows) {
+        const int64_t n = std::min<int64_t>(s->rows, B - r0);
+        const int rows = int(((n + 127) / 128) * 128);
+        k_standardize<<<(rows + 127) / 128, 128, 0, st>>>(theta + r0 * kMlpIn, n, rows, s->norm,
+                                                          s->H[0], nullptr, s->rows);
+        argus_status e = forward(s, rows, false, st);
+        if (e) return e;
+        k_destandardize<<<unsigned((n + 127) / 128), 128, 0, st>>>(s->Y, n, s->norm, loglik + r0,
+                                                                  grad ? grad + r0 * kMlpIn : nullptr);
+        SCK(cudaGetLastError());
+    }
+    return ARGUS_OK;
+}
+
+argus_status argus_surrogate_train_step(argus_surrogate* s, const float* theta, const float* loglik,
+                                        const float* grad, int64_t n, float lr, float* loss,
+                                        void* stream) {
+    if (!s) return sfail(ARGUS_ERR_INVALID_ARG, "surrogate handle is NULL");
+    if (n < 1 || n > s->rows)
+        return sfail(ARGUS_ERR_INVALID_ARG, "n must be in 1..max_rows (rounded up to 256)");
+    if (!theta || !loglik || !grad || !loss) return sfail(ARGUS_ERR_INVALID_ARG, "NULL argument");
+    if (!(lr > 0.0f) || !std::isfinite(lr)) return sfail(ARGUS_ERR_INVALID_ARG, "lr must be > 0");
+    DeviceGuardS guard(s->device);
+    if (!dev_ptr(theta) || !dev_ptr(loglik) || !dev_ptr(grad) || !dev_ptr(loss))
+        return sfail(ARGUS_ERR_INVALID_ARG, "argus_surrogate_train_step needs device pointers");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const int rows = int(((n + 127) / 128) * 128);
+    const int ck = (rows % 256 == 0) ? 256 : 128;   // K per split-K chunk over the batch
+    const int chunks = rows / ck;
+    k_standardize<<<(rows + 127) / 128, 128, 0, st>>>(theta, n, rows, s->norm, s->H[0], s->HT[0],
+                                                      s->rows);
+    argus_status e = forward(s, rows, true, st);
+    if (e) return e;
+    k_loss<<<(rows + 127) / 128, 128, 0, st>>>(s->Y, loglik, grad, n, rows, s->norm, s->dY, s->dYT,
+                                               s->rows, s->row_loss);
+    k_loss_sum<<<1, 32, 0, st>>>(s->row_loss, rows, n, loss);
+    // output layer: dW4^T = H4^T dY (split-K over rows), db4 = sum_r dY, dH4 = dY W4 -> dZ4
+    {
+        GemmEpiArgs g = epi_none();
+        g.out_f32 = s->part[4];
+        g.ldo = kMlpOutPad;
+        g.chunk_stride = int64_t(kMlpHidden) * kMlpOutPad;
+        cudaError_t ce = launch_gemm_tc(&s->tmHT[4], &s->tmdYT, kMlpHidden, kMlpOutPad, ck, 64, chunks,
+                                        kEpiF32, g, s->err, st);
+        if (ce != cudaSuccess) return scuda(ce, "dW4 GEMM");
+        k_colsum_bf16<<<1, kMlpOutPad, 0, st>>>(s->dY, rows, kMlpOutPad, s->gb[4]);
+        GemmEpiArgs d = epi_none();
+        d.zin = s->Z[4];
+        d.ldz = kMlpHidden;
+        d.out_f32 = s->dZ32[0];
+        d.ldo = kMlpHidden;
+        d.out_bf16 = s->dZ16[0];
+        d.ldb = kMlpHidden;
+        d.out_bf16_t = s->dZT[0];
+        d.ldt = s->rows;
+        ce = launch_gemm_tc(&s->tmdY, &s->tmWT[4], rows, kMlpHidden, kMlpOutPad, 128, 1, kEpiGeluBwd, d,
+                            s->err, st);
+        if (ce != cudaSuccess) return scuda(ce, "dH4 GEMM");
+    }
+    // hidden layers l = 3..0: cur holds dZ_{l+1}
+    int cur = 0;
+    for (int l = kMlpLayers - 2; l >= 0; --l) {
+        const int K = kIn[l];
+        GemmEpiArgs g = epi_none();
+        g.out_f32 = s->part[l];
+        g.ldo = K;
+        g.chunk_stride = int64_t(kMlpHidden) * K;
+        cudaError_t ce = launch_gemm_tc(&s->tmdZT[cur], &s->tmHT[l], kMlpHidden, K, ck, K == 64 ? 64 : 128,
+                                        chunks, kEpiF32, g, s->err, st);
+        if (ce != cudaSuccess) return scuda(ce, "dW GEMM");
+        k_colsum_f32<<<1, kMlpHidden, 0, st>>>(s->dZ32[cur], rows, kMlpHidden, s->gb[l]);
+        if (l > 0) {
+            GemmEpiArgs d = epi_none();
+            d.zin = s->Z[l];
+            d.ldz = kMlpHidden;
+            d.out_f32 = s->dZ32[cur ^ 1];
+            d.ldo = kMlpHidden;
+            d.out_bf16 = s->dZ16[cur ^ 1];
+            d.ldb = kMlpHidden;
+            d.out_bf16_t = s->dZT[cur ^ 1];
+            d.ldt = s->rows;
+            ce = launch_gemm_tc(&s->tmdZ16[cur], &s->tmWT[l], rows, kMlpHidden, kMlpHidden, 128, 1,
+                                kEpiGeluBwd, d, s->err, st);
+            if (ce != cudaSuccess) return scuda(ce, "dH GEMM");
+            cur ^= 1;
+        }
+    }
+    s->last_chunks = chunks;
+    // Adam
+    s->step += 1;
+    const float c1 = float(1.0 - std::pow(0.9, s->step));
+    const float c2 = float(1.0 - std::pow(0.999, s->step));
+    for (int l = 0; l < kMlpLayers; ++l) {
+        const int N = kOut[l], K = kIn[l];
+        const int64_t stride = int64_t(N) * K;
+        k_adam_w<<<(N * K + 255) / 256, 256, 0, st>>>(s->W[l], s->mW[l], s->vW[l], s->part[l], chunks,
+                                                      stride, N, K, l == kMlpLayers - 1 ? 1 : 0, lr, c1,
+                                                      c2, s->W16[l], s->W16T[l]);
+        k_adam_b<<<(N + 255) / 256, 256, 0, st>>>(s->b[l], s->mb[l], s->vb[l], s->gb[l], N, lr, c1, c2);
+    }
+    SCK(cudaGetLastError());
+    return ARGUS_OK;
+}
+
+argus_status argus_surrogate_check(argus_surrogate* s) {
+    if (!s) return sfail(ARGUS_ERR_INVALID_ARG, "surrogate handle is NULL");
+    DeviceGuardS guard(s->device);
+    SCK(cudaDeviceSynchronize());
+    return check_err(s);
+}
+
+const char* argus_surrogate_last_error(void) { return g_sur_error.c_str(); }
+
+argus_status argus_selftest_surrogate_grads(argus_surrogate* s, float* grads) {
+    if (!s || !grads || s->last_chunks < 1) return sfail(ARGUS_ERR_INVALID_ARG, "no training step yet");
+    DeviceGuardS guard(s->device);
+    SCK(cudaDeviceSynchronize());
+    float* p = grads;
+    for (int l = 0; l < kMlpLayers; ++l) {
+        const int N = kOut[l], K = kIn[l];
+        const size_t nw = size_t(N) * K;
+        std::vector<float> part(nw * s->last_chunks);
+        SCK(cudaMemcpy(part.data(), s->part[l], part.size() * 4, cudaMemcpyDeviceToHost));
+        for (int o = 0; o < N; ++o)
+            for (int i = 0; i < K; ++i) {
+                const size_t pidx = (l == kMlpLayers - 1) ? size_t(i) * N + o : size_t(o) * K + i;
+                float g = 0.0f;
+                for (int c = 0; c < s->last_chunks; ++c) g += part[size_t(c) * nw + pidx];
+                p[size_t(o) * K + i] = g;
+            }
+        p += nw;
+        SCK(cudaMemcpy(p, s->gb[l], N * 4, cudaMemcpyDeviceToHost));
+        p += N;
+    }
+    return ARGUS_OK;
+}
+
+}  // extern "C"

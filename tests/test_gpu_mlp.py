@@ -1,0 +1,148 @@
+"""Surrogate network on the GPU against its oracle (oracle/mlp.py).
+
+The BF16 rounding points match the oracle's; the remaining differences come
+from FP32 summation order inside the tensor cores, which can move an
+activation across a BF16 rounding boundary.  Tolerances below are stated
+relative to the largest magnitude of each compared array.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import pytest
+
+from oracle import mlp
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2510_11077_gb300 import argus
+    lib = argus.load()
+    vp = ctypes.c_void_p
+    lib.argus_selftest_gemm.argtypes = [vp, vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                        ctypes.c_int32, ctypes.c_int32, vp]
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    return lib
+
+
+def _bf16_bits(x):
+    r = mlp.bf16_round(x)
+    return (r.view(np.uint32) >> 16).astype(np.uint16), r
+
+
+@pytest.mark.parametrize("M,N,K,bn,chunks", [(128, 64, 64, 64, 1), (128, 128, 256, 128, 1),
+                                             (256, 256, 256, 128, 1), (256, 64, 512, 64, 2),
+                                             (384, 128, 256, 128, 2)])
+def test_tensor_core_gemm(lib, M, N, K, bn, chunks):
+    rng = np.random.default_rng(M + N + K)
+    A16, A = _bf16_bits(rng.standard_normal((M, K)).astype(np.float32))
+    B16, B = _bf16_bits(rng.standard_normal((N, K)).astype(np.float32))
+    C = np.empty((chunks, M, N), np.float32)
+    st = lib.argus_selftest_gemm(A16.ctypes.data, B16.ctypes.data, M, N, K, bn, chunks, C.ctypes.data)
+    assert st == 0, st
+    kc = K // chunks
+    for z in range(chunks):
+        ref = A[:, z * kc:(z + 1) * kc].astype(np.float64) @ B[:, z * kc:(z + 1) * kc].astype(np.float64).T
+        assert np.max(np.abs(C[z] - ref)) <= 1e-5 * np.max(np.abs(ref)), z
+
+
+def _oracle_io(params, theta, xm, xs, ym, ys):
+    x = np.zeros((theta.shape[0], mlp.IN_PAD), np.float32)
+    x[:, :mlp.IN_DIM] = (theta.astype(np.float32) - xm) / xs
+    y, cache = mlp.forward(params, x)
+    ll = y[:, 0] * np.float32(ys) + np.float32(ym)
+    g = y[:, 1:mlp.OUT_DIM] * np.float32(ys) / xs
+    return x, y, cache, ll, g
+
+
+def _setup(seed, n):
+    from paper_2510_11077_gb300 import surrogate
+    rng = np.random.default_rng(seed)
+    params = mlp.init_params(seed)
+    for l in range(5):   # non-zero biases so the bias path is exercised
+        params[l][1] = (0.1 * rng.standard_normal(params[l][1].shape)).astype(np.float32)
+        if l == 4:
+            params[l][1][mlp.OUT_DIM:] = 0.0
+    theta = rng.uniform(-3, 3, (n, mlp.IN_DIM)).astype(np.float32)
+    xm = rng.uniform(-0.5, 0.5, mlp.IN_DIM).astype(np.float32)
+    xs = rng.uniform(0.5, 2.0, mlp.IN_DIM).astype(np.float32)
+    ym, ys = 1234.5, 17.0
+    s = surrogate.Surrogate(device=0, max_rows=1024, seed=seed)
+    s.set_normalizers(xm, xs, ym, ys, value_weight=2.0, grad_weight=1.0)
+    s.set_weights(surrogate.flatten(params))
+    return s, params, theta, xm, xs, ym, ys
+
+
+def test_surrogate_weights_roundtrip(lib):
+    s, params, *_ = _setup(11, 8)
+    from paper_2510_11077_gb300 import surrogate
+    assert np.array_equal(s.get_weights(), surrogate.flatten(params))
+
+
+@pytest.mark.parametrize("n", [1, 130, 1000, 2500])
+def test_surrogate_eval_matches_oracle(lib, n):
+    s, params, theta, xm, xs, ym, ys = _setup(12, n)
+    ll, g = s.eval(torch.from_numpy(theta).cuda())
+    s.check()
+    ll, g = ll.cpu().numpy(), g.cpu().numpy()
+    _, y, _, ll_ref, g_ref = _oracle_io(params, theta, xm, xs, ym, ys)
+    dv = np.abs(ll - ll_ref) / ys
+    assert dv.max() <= 2e-2 * max(np.abs(y[:, 0]).max(), 1e-3), dv.max()
+    dg = np.abs(g - g_ref)
+    assert dg.max() <= 2e-2 * np.abs(g_ref).max(), (dg.max(), np.abs(g_ref).max())
+    # the bulk agrees far more tightly than the worst element
+    assert np.median(dg) <= 1e-3 * np.abs(g_ref).max()
+
+
+def test_surrogate_train_step_gradients_match_oracle(lib):
+    from paper_2510_11077_gb300 import surrogate
+    n = 512
+    s, params, theta, xm, xs, ym, ys = _setup(13, n)
+    rng = np.random.default_rng(5)
+    ll_t = (ym + ys * rng.standard_normal(n)).astype(np.float32)
+    g_t = (rng.standard_normal((n, mlp.IN_DIM)) * ys / xs).astype(np.float32)
+    loss = s.train_step(torch.from_numpy(theta).cuda(), torch.from_numpy(ll_t).cuda(),
+                        torch.from_numpy(g_t).cuda(), lr=1e-3)
+    s.check()
+    gpu = surrogate.unflatten(s.last_grads(), mlp.LAYERS)
+    x, y, cache, _, _ = _oracle_io(params, theta, xm, xs, ym, ys)
+    t = np.zeros((n, mlp.OUT_DIM), np.float32)
+    t[:, 0] = (ll_t - np.float32(ym)) / np.float32(ys)
+    t[:, 1:] = g_t * xs / np.float32(ys)
+    w = np.concatenate([[2.0], np.ones(mlp.OUT_DIM - 1)]).astype(np.float32)
+    loss_ref, dy = mlp.loss_and_dy(y, t, w)
+    assert abs(float(loss.item()) - loss_ref) <= 1e-3 * loss_ref
+    ref = mlp.backward(params, cache, dy)
+    for l in range(5):
+        for i in range(2):
+            a, b = gpu[l][i], ref[l][i]
+            assert np.max(np.abs(a - b)) <= 3e-2 * np.max(np.abs(b)), (l, i)
+            cos = float(np.sum(a * b) / (np.linalg.norm(a) * np.linalg.norm(b)))
+            assert cos > 0.999, (l, i, cos)
+    # padding stays zero after the Adam step
+    wts = surrogate.unflatten(s.get_weights(), mlp.LAYERS)
+    assert np.all(wts[0][0][:, mlp.IN_DIM:] == 0) and np.all(wts[4][0][mlp.OUT_DIM:] == 0)
+    assert np.all(wts[4][1][mlp.OUT_DIM:] == 0)
+
+
+def test_surrogate_training_fits_a_smooth_function(lib):
+    """Adam on the GPU drives the loss of a smooth target well down (as the
+    oracle does on the same problem)."""
+    from paper_2510_11077_gb300 import surrogate
+    rng = np.random.default_rng(7)
+    n = 1024
+    theta = rng.standard_normal((n, mlp.IN_DIM)).astype(np.float32)
+    A = rng.standard_normal((mlp.IN_DIM, mlp.IN_DIM)).astype(np.float32) / mlp.IN_DIM
+    ll = -0.5 * np.einsum("ni,ij,nj->n", theta, A @ A.T + np.eye(mlp.IN_DIM), theta).astype(np.float32)
+    g = -(theta @ (A @ A.T + np.eye(mlp.IN_DIM))).astype(np.float32)
+    s = surrogate.Surrogate(device=0, max_rows=1024, seed=3)
+    s.set_normalizers(np.zeros(mlp.IN_DIM), np.ones(mlp.IN_DIM), float(ll.mean()), float(ll.std()))
+    th, l_, g_ = (torch.from_numpy(a).cuda() for a in (theta, ll, g))
+    losses = [float(s.train_step(th, l_, g_, lr=2e-3).item()) for _ in range(150)]
+    s.check()
+    assert losses[-1] < 0.1 * losses[0], (losses[0], losses[-1])
