@@ -146,6 +146,13 @@ argus_status argus_loglik_grad(argus_array* array, const double* theta, int64_t 
 argus_status argus_loglik_grad_noalloc(argus_array* array, const double* theta, int64_t B,
                                        double* loglik, double* grad, void* stream);
 
+/* The model's continuous-wave timing residual s_p(t_k) = A sin(W t_k + Phi0)
+ * + B cos(W t_k + Phi0) at every TOA of the array, for one set of source
+ * parameters theta_gw = [log10 f_gw, Phi0, psi, cos iota, sin delta, alpha,
+ * log10 h0] (host, 7 doubles).  s: host array of sum_p N_p doubles in the
+ * pulsars' order.  Synchronous.  For simulating or subtracting a source. */
+argus_status argus_cw_signal(argus_array* array, const double* theta_gw, double* s);
+
 /* Per-(walker, pulsar) terms, for inspection: lane_ll [B][P] doubles (device
  * or host) receives ll_p(theta_b).  Same rules as argus_loglik. */
 argus_status argus_lane_loglik(argus_array* array, const double* theta, int64_t B,

@@ -57,6 +57,14 @@ argus_status argus_surrogate_set_normalizers(argus_surrogate* s, const float* x_
                                              const float* x_std, float y_mean, float y_std,
                                              float value_weight, float grad_weight);
 
+/* Optional quadratic baseline in the network's input coordinates x:
+ * ll(x) ~ net(x) - 1/2 x^T H x, grad ~ net_grad(x) - H x, with H a host
+ * [47][47] row-major FP32 matrix (e.g. the inverse posterior covariance of a
+ * Gaussian approximation, with x the offset from its mean).  The network then
+ * only learns the residual: training targets have the baseline subtracted and
+ * eval adds it back.  NULL removes the baseline. */
+argus_status argus_surrogate_set_baseline(argus_surrogate* s, const float* H);
+
 /* Copy all parameters from / to a host array in the flat layout.  set_weights
  * also resets the Adam state and step count. */
 argus_status argus_surrogate_set_weights(argus_surrogate* s, const float* params);

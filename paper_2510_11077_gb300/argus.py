@@ -88,6 +88,8 @@ def load(build_if_missing: bool = False):
     lib.argus_lane_loglik.restype = ctypes.c_int
     lib.argus_loglik_grad_noalloc.argtypes = [vp, dp, ctypes.c_int64, dp, dp, vp]
     lib.argus_loglik_grad_noalloc.restype = ctypes.c_int
+    lib.argus_cw_signal.argtypes = [vp, dp, dp]
+    lib.argus_cw_signal.restype = ctypes.c_int
     lib.argus_array_set_timing.argtypes = [vp, ctypes.c_int32]
     lib.argus_array_set_timing.restype = ctypes.c_int
     lib.argus_array_get_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
@@ -238,6 +240,14 @@ def argus_loglik_grad_noalloc(array: Array, theta, loglik, grad, stream=None):
     _check(_lib.argus_loglik_grad_noalloc(array.handle, _ptr(theta), theta.shape[0],
                                           _ptr(loglik), _ptr(grad), s))
     return loglik, grad
+
+
+def argus_cw_signal(array: Array, theta_gw, n_total: int) -> np.ndarray:
+    """The model's continuous-wave residual at every TOA (host arrays)."""
+    th = np.ascontiguousarray(theta_gw[:7], dtype=np.float64)
+    out = np.empty(int(n_total), dtype=np.float64)
+    _check(_lib.argus_cw_signal(array.handle, th.ctypes.data, out.ctypes.data))
+    return out
 
 
 def argus_lane_loglik(array: Array, theta, lane=None, stream=None):

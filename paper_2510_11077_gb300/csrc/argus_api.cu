@@ -586,6 +586,27 @@ argus_status argus_array_get_timing(argus_array* h, float* ms) {
     return ARGUS_OK;
 }
 
+argus_status argus_cw_signal(argus_array* h, const double* theta_gw, double* s) {
+    if (!h || !theta_gw || !s) return fail(ARGUS_ERR_INVALID_ARG, "NULL argument");
+    for (int j = 0; j < kNgw; ++j)
+        if (!std::isfinite(theta_gw[j])) return fail(ARGUS_ERR_INVALID_ARG, "non-finite theta_gw");
+    if (h->total_toa == 0) return ARGUS_OK;
+    DeviceGuard guard(h->device);
+    double* d = nullptr;
+    CK(cudaMalloc(&d, sizeof(double) * (kNgw + h->total_toa)));
+    cudaError_t e = cudaMemcpy(d, theta_gw, sizeof(double) * kNgw, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        launch_cw_signal(d, h->P, h->d_psr, h->d_rec, h->n_max, d + kNgw, nullptr);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess)
+        e = cudaMemcpy(s, d + kNgw, sizeof(double) * h->total_toa, cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return cuda_fail(e, "argus_cw_signal");
+    return ARGUS_OK;
+}
+
 const char* argus_status_string(argus_status s) {
     switch (s) {
         case ARGUS_OK: return "ARGUS_OK";

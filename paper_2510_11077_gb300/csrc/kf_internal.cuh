@@ -61,6 +61,9 @@ void launch_filter_grad(const FilterArgs& a, int W, int grid, cudaStream_t s);
 void launch_reduce(const double* theta, int64_t B, int32_t P, const PulsarDev* psr,
                    const double* lane_out, double* loglik, double* grad, double* lane_ll,
                    cudaStream_t s);
+// The model's continuous-wave residual at every TOA for one theta_gw [7] (device).
+void launch_cw_signal(const double* theta_gw, int32_t P, const PulsarDev* psr, const double* rec,
+                      int max_n, double* s, cudaStream_t st);
 // shared-memory bytes a filter block needs
 size_t filter_smem_bytes(bool grad, int stride_max);
 

@@ -492,6 +492,25 @@ __global__ void k_reduce(const double* __restrict__ theta, int64_t B, int32_t P,
     for (int j = 0; j < kNgw; ++j) gout[j] = gw[j];
 }
 
+// s[off_p + k] = A_p sin(W t_k + Phi0) + B_p cos(W t_k + Phi0); grid (TOA blocks, P)
+__global__ void k_cw_signal(const double* __restrict__ thg, const PulsarDev* __restrict__ psr,
+                            const double* __restrict__ rec, double* __restrict__ s) {
+    const int p = blockIdx.y;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const PulsarDev& ps = psr[p];
+    if (k >= ps.n) return;
+    double th[kNgw];
+    for (int j = 0; j < kNgw; ++j) th[j] = thg[j];
+    SourceFrame F;
+    source_frame(th, false, F);
+    Antenna R;
+    antenna(F, ps.pos, false, R);
+    const double t = rec[(ps.off + k) * kRecDoubles];
+    double sn, cs;
+    sincospi(2.0 * fma(F.f, t, th[1] / kTwoPi), &sn, &cs);
+    s[ps.off + k] = fma(R.Fp * F.ampP, sn, R.Fx * F.ampX * cs);
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -518,6 +537,13 @@ void launch_filter_grad(const FilterArgs& a, int W, int grid, cudaStream_t s) {
     const size_t smem = filter_smem_bytes(true, a.stride_max);
     if (a.tape_cache) k_filter_grad<true><<<grid, W, smem, s>>>(a);
     else k_filter_grad<false><<<grid, W, smem, s>>>(a);
+}
+
+void launch_cw_signal(const double* theta_gw, int32_t P, const PulsarDev* psr, const double* rec,
+                      int max_n, double* s, cudaStream_t st) {
+    if (max_n <= 0) return;
+    dim3 grid((max_n + 127) / 128, P);
+    k_cw_signal<<<grid, 128, 0, st>>>(theta_gw, psr, rec, s);
 }
 
 void launch_reduce(const double* theta, int64_t B, int32_t P, const PulsarDev* psr,

@@ -84,7 +84,8 @@ __global__ void k_standardize(const float* __restrict__ theta, int64_t n, int ro
 // Standardized targets, weighted squared error per row, and
 // dY = bf16(2 w_j (y - t) / n) (+ its transpose); padding rows and columns get 0.
 __global__ void k_loss(const float* __restrict__ y, const float* __restrict__ ll,
-                       const float* __restrict__ grad, int64_t n, int rows, Norm nm,
+                       const float* __restrict__ grad, const float* __restrict__ base,
+                       const float* __restrict__ gbase, int64_t n, int rows, Norm nm,
                        __nv_bfloat16* __restrict__ dy, __nv_bfloat16* __restrict__ dyt, int pitch,
                        float* __restrict__ row_loss) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
@@ -93,8 +94,10 @@ __global__ void k_loss(const float* __restrict__ y, const float* __restrict__ ll
     for (int j = 0; j < kMlpOutPad; ++j) {
         float d = 0.0f;
         if (r < n && j < kMlpOut) {
-            const float t = (j == 0) ? (ll[r] - nm.ym) / nm.ys
-                                     : grad[int64_t(r) * kMlpIn + (j - 1)] * nm.xs[j - 1] / nm.ys;
+            const float b0 = base ? base[r] : 0.0f;
+            const float bj = (gbase && j > 0) ? gbase[int64_t(r) * kMlpIn + (j - 1)] : 0.0f;
+            const float t = (j == 0) ? (ll[r] - b0 - nm.ym) / nm.ys
+                                     : (grad[int64_t(r) * kMlpIn + (j - 1)] - bj) * nm.xs[j - 1] / nm.ys;
             const float e = y[int64_t(r) * kMlpOutPad + j] - t;
             acc += nm.w[j] * e * e;
             d = 2.0f * nm.w[j] * e / float(n);
@@ -178,15 +181,35 @@ __global__ void k_cast_w(const float* __restrict__ W, int N, int K, __nv_bfloat1
     w16t[int64_t(i) * N + o] = b;
 }
 
+// Quadratic baseline of the log-likelihood in the network's input coordinates:
+// base = -1/2 u^T H u, gbase = -H u (H symmetric [47][47]; all zero = no baseline).
+__global__ void k_baseline(const float* __restrict__ u, int64_t n, const float* __restrict__ H,
+                           float* __restrict__ base, float* __restrict__ gbase) {
+    const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const float* ur = u + r * kMlpIn;
+    float q = 0.0f;
+    for (int i = 0; i < kMlpIn; ++i) {
+        float hu = 0.0f;
+        for (int j = 0; j < kMlpIn; ++j) hu = fmaf(H[i * kMlpIn + j], ur[j], hu);
+        gbase[r * kMlpIn + i] = -hu;
+        q = fmaf(ur[i], hu, q);
+    }
+    base[r] = -0.5f * q;
+}
+
 // De-standardize: ll = y0 ys + ym, grad_k = y_{1+k} ys / xs_k.
+// (plus the baseline, if any: base [n], gbase [n][47]).
 __global__ void k_destandardize(const float* __restrict__ y, int64_t n, Norm nm,
+                                const float* __restrict__ base, const float* __restrict__ gbase,
                                 float* __restrict__ ll, float* __restrict__ grad) {
     const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (r >= n) return;
     const float* yr = y + r * kMlpOutPad;
-    ll[r] = yr[0] * nm.ys + nm.ym;
+    ll[r] = yr[0] * nm.ys + nm.ym + (base ? base[r] : 0.0f);
     if (grad)
-        for (int k = 0; k < kMlpIn; ++k) grad[r * kMlpIn + k] = yr[1 + k] * nm.ys / nm.xs[k];
+        for (int k = 0; k < kMlpIn; ++k)
+            grad[r * kMlpIn + k] = yr[1 + k] * nm.ys / nm.xs[k] + (gbase ? gbase[r * kMlpIn + k] : 0.0f);
 }
 
 template <class T>
@@ -223,6 +246,10 @@ struct argus_surrogate {
     __nv_bfloat16* dZ16[2] = {};
     __nv_bfloat16* dZT[2] = {};
     float* row_loss = nullptr;
+    float* Hq = nullptr;        // baseline precision matrix [47][47] (device)
+    bool has_baseline = false;
+    float* base = nullptr;      // [rows] baseline values of the current batch
+    float* gbase = nullptr;     // [rows][47]
     int* err = nullptr;
     int last_chunks = 0;   // split-K chunks of the last training step
     // tensor maps
@@ -240,6 +267,7 @@ void free_all(argus_surrogate* s) {
         cudaFree(s->Z[l]);
     }
     cudaFree(s->Y); cudaFree(s->dY); cudaFree(s->dYT); cudaFree(s->row_loss); cudaFree(s->err);
+    cudaFree(s->Hq); cudaFree(s->base); cudaFree(s->gbase);
     for (int i = 0; i < 2; ++i) {
         cudaFree(s->dZ32[i]); cudaFree(s->dZ16[i]); cudaFree(s->dZT[i]);
     }
@@ -371,6 +399,9 @@ argus_status argus_surrogate_create(int32_t device, int32_t max_rows, uint64_t s
         A(dalloc(&s->dZT[i], R * kMlpHidden));
     }
     A(dalloc(&s->row_loss, R));
+    A(dalloc(&s->Hq, size_t(kMlpIn) * kMlpIn));
+    A(dalloc(&s->base, R));
+    A(dalloc(&s->gbase, R * kMlpIn));
     A(dalloc(&s->err, 1));
     if (!st) {
         // fan-in scaled normal weights from a seeded host generator (Box-Muller on splitmix64)
@@ -450,6 +481,20 @@ argus_status argus_surrogate_set_normalizers(argus_surrogate* s, const float* x_
     return ARGUS_OK;
 }
 
+argus_status argus_surrogate_set_baseline(argus_surrogate* s, const float* H) {
+    if (!s) return sfail(ARGUS_ERR_INVALID_ARG, "surrogate handle is NULL");
+    DeviceGuardS guard(s->device);
+    if (!H) {
+        s->has_baseline = false;
+        return ARGUS_OK;
+    }
+    for (int i = 0; i < kMlpIn * kMlpIn; ++i)
+        if (!std::isfinite(H[i])) return sfail(ARGUS_ERR_INVALID_ARG, "non-finite baseline matrix");
+    SCK(cudaMemcpy(s->Hq, H, sizeof(float) * kMlpIn * kMlpIn, cudaMemcpyHostToDevice));
+    s->has_baseline = true;
+    return ARGUS_OK;
+}
+
 argus_status argus_surrogate_set_weights(argus_surrogate* s, const float* params) {
     if (!s || !params) return sfail(ARGUS_ERR_INVALID_ARG, "NULL argument");
     DeviceGuardS guard(s->device);
@@ -504,8 +549,12 @@ argus_status argus_surrogate_eval(argus_surrogate* s, const float* theta, int64_
                                                           s->H[0], nullptr, s->rows);
         argus_status e = forward(s, rows, false, st);
         if (e) return e;
-        k_destandardize<<<unsigned((n + 127) / 128), 128, 0, st>>>(s->Y, n, s->norm, loglik + r0,
-                                                                  grad ? grad + r0 * kMlpIn : nullptr);
+        if (s->has_baseline)
+            k_baseline<<<unsigned((n + 127) / 128), 128, 0, st>>>(theta + r0 * kMlpIn, n, s->Hq,
+                                                                 s->base, s->gbase);
+        k_destandardize<<<unsigned((n + 127) / 128), 128, 0, st>>>(
+            s->Y, n, s->norm, s->has_baseline ? s->base : nullptr,
+            s->has_baseline ? s->gbase : nullptr, loglik + r0, grad ? grad + r0 * kMlpIn : nullptr);
         SCK(cudaGetLastError());
     }
     return ARGUS_OK;
@@ -530,8 +579,11 @@ argus_status argus_surrogate_train_step(argus_surrogate* s, const float* theta, 
                                                       s->rows);
     argus_status e = forward(s, rows, true, st);
     if (e) return e;
-    k_loss<<<(rows + 127) / 128, 128, 0, st>>>(s->Y, loglik, grad, n, rows, s->norm, s->dY, s->dYT,
-                                               s->rows, s->row_loss);
+    if (s->has_baseline)
+        k_baseline<<<unsigned((n + 127) / 128), 128, 0, st>>>(theta, n, s->Hq, s->base, s->gbase);
+    k_loss<<<(rows + 127) / 128, 128, 0, st>>>(s->Y, loglik, grad, s->has_baseline ? s->base : nullptr,
+                                               s->has_baseline ? s->gbase : nullptr, n, rows, s->norm,
+                                               s->dY, s->dYT, s->rows, s->row_loss);
     k_loss_sum<<<1, 32, 0, st>>>(s->row_loss, rows, n, loss);
     // output layer: dW4^T = H4^T dY (split-K over rows), db4 = sum_r dY, dH4 = dY W4 -> dZ4
     {

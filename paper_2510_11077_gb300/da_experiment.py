@@ -1,0 +1,306 @@
+"""Surrogate-accelerated delayed-acceptance HMC on a 20-pulsar array.
+
+1. Exact HMC warm-up (all chains in lock-step) with dual-averaging step size
+   and a diagonal mass matrix from the warm-up draws.
+2. Training set: parameter vectors drawn around the warm-up posterior
+   (Gaussian, `spread` x the posterior standard deviation, inside the prior
+   box), each evaluated by the exact FP64 filter (loglik + gradient).
+3. Surrogate training on the GPU (BF16 tensor-core MLP, Adam).
+4. From the same warmed-up state: plain exact HMC and delayed-acceptance HMC
+   (surrogate trajectory and stage 1, exact filter as stage 2), both with the
+   same step size, mass matrix and trajectory length.
+5. ESS/s (minimum over parameters) of both, with and without the surrogate's
+   data-generation and training time, and a check that the two posteriors
+   agree (means within Monte Carlo error).
+
+The network sees FP32 inputs; to keep their precision it is fed parameter
+offsets from a fixed FP64 centre and log-likelihood offsets from a fixed FP64
+reference value.
+"""
+from __future__ import annotations
+
+import math
+import time
+
+import numpy as np
+import torch
+
+from . import argus, inputs, sampler
+from .surrogate import Surrogate
+
+N_GW = inputs.N_GW
+
+
+def prior_box(P):
+    lo = np.concatenate([inputs.PRIOR_GW[:, 0], np.tile(inputs.PRIOR_NOISE[:, 0], P)])
+    hi = np.concatenate([inputs.PRIOR_GW[:, 1], np.tile(inputs.PRIOR_NOISE[:, 1], P)])
+    return lo, hi
+
+
+class ExactTarget:
+    """log posterior = exact FP64 filter log-likelihood inside the prior box."""
+
+    def __init__(self, data, device):
+        self.arr = argus.Array(data, device=device)      # loglik + grad, graph replay
+        self.arr_ll = argus.Array(data, device=device)   # loglik of varying batch sizes
+        self.arr_ll.set_plan(use_graph=0)
+        lo, hi = prior_box(data.n_pulsars)
+        self.lo = torch.tensor(lo, dtype=torch.float64, device=device)
+        self.hi = torch.tensor(hi, dtype=torch.float64, device=device)
+        self.calls_grad = 0
+        self.calls_ll = 0
+        self._bufs = {}
+
+    def inside(self, x):
+        return torch.all((x >= self.lo) & (x <= self.hi), dim=1)
+
+    def loglik_grad(self, x):
+        """Exact loglik + gradient through fixed buffers (one captured graph per
+        batch size is replayed instead of re-captured)."""
+        B, D = x.shape
+        if B not in self._bufs:
+            dev = x.device
+            self._bufs[B] = (torch.empty((B, D), dtype=torch.float64, device=dev),
+                             torch.empty(B, dtype=torch.float64, device=dev),
+                             torch.empty((B, D), dtype=torch.float64, device=dev))
+        th, ll, g = self._bufs[B]
+        th.copy_(x)
+        argus.argus_loglik_grad(self.arr, th, ll, g)
+        return ll.clone(), g.clone()
+
+    def logp_grad(self, x):
+        ll, g = self.loglik_grad(x)
+        self.calls_grad += x.shape[0]
+        m = self.inside(x)
+        ll = torch.where(m, ll, torch.full_like(ll, -math.inf))
+        return ll, torch.where(m[:, None], g, torch.zeros_like(g))
+
+    def logp(self, x):
+        ll = argus.argus_loglik(self.arr_ll, x.contiguous())
+        self.calls_ll += x.shape[0]
+        return torch.where(self.inside(x), ll, torch.full_like(ll, -math.inf))
+
+
+class SurrogateTarget:
+    """log posterior approximated by the trained network, same prior box."""
+
+    def __init__(self, net, exact, centre, ll_ref):
+        self.net, self.exact = net, exact
+        self.centre = centre
+        self.ll_ref = ll_ref
+
+    def logp_grad(self, x):
+        u = (x - self.centre).float().contiguous()
+        ll, g = self.net.eval(u)
+        ll = ll.double() + self.ll_ref
+        m = self.exact.inside(x)
+        ll = torch.where(m, ll, torch.full_like(ll, -math.inf))
+        return ll, torch.where(m[:, None], g.double(), torch.zeros_like(x))
+
+
+def _sync():
+    torch.cuda.synchronize()
+
+
+def model_array(seed, log10_h0=-13.7, device=0):
+    """The 20-pulsar workload's TOAs and noise, plus the model's own
+    continuous-wave residual at a detectable strain, so that the posterior is
+    centred on known parameters.  Returns (data, theta_true)."""
+    w = inputs.WORKLOADS["psr20_toa500-2000_w4096"]
+    rng = np.random.Generator(np.random.PCG64(w.seed))
+    n_toa = inputs.draw_toa_counts(rng, w.n_pulsars, w.toa_law)
+    data = inputs.make_array(n_toa, seed, with_signal=False)
+    theta = data.theta_true.copy()
+    theta[6] = log10_h0
+    arr = argus.Array(data, device=device)
+    data.r = data.r + argus.argus_cw_signal(arr, theta[:N_GW], int(data.off[-1]))
+    arr.close()
+    data.theta_true = theta
+    return data, theta
+
+
+def warmup(target, x0, n_iter, n_steps, gen, log=None):
+    """Exact HMC warm-up: dual averaging of the step size; diagonal mass from the
+    second half of the draws (re-estimated once at 60%)."""
+    C, D = x0.shape
+    inv_mass = x0.var(dim=0, keepdim=True).clamp_min(1e-30)   # initial scales from the starts
+    st = sampler.ChainState(x0, *target.logp_grad(x0))
+    da = sampler.DualAveraging(0.05, target=0.8)
+    eps = 0.05
+    keep = []
+    tail = []
+    for it in range(n_iter):
+        st, a = sampler.hmc_step(st, target.logp_grad, torch.full((C, 1), eps, dtype=torch.float64,
+                                                                  device=x0.device),
+                                 n_steps, inv_mass, gen)
+        eps = da.update(float(a.mean()))
+        if it >= n_iter // 3:
+            keep.append(st.x)
+        if it >= int(0.75 * n_iter):
+            tail.append(st.x)
+        if it == int(0.6 * n_iter) and keep:
+            xs = torch.stack(keep)
+            inv_mass = xs.reshape(-1, D).var(dim=0, keepdim=True).clamp_min(1e-30)
+            keep = []
+            da = sampler.DualAveraging(eps, target=0.8)
+        if log and it % 25 == 0:
+            log(f"warmup {it}: eps {eps:.3g} acc {float(a.mean()):.3f}")
+    return st, da.final(), inv_mass, torch.cat(tail)
+
+
+def make_training_set(target, centre, chol, n, batch, gen):
+    """n exact (loglik, grad) evaluations at centre + chol N(0, I), inside the box."""
+    D = centre.shape[0]
+    xs, lls, gs = [], [], []
+    done = 0
+    while done < n:
+        b = min(batch, n - done)
+        z = torch.randn((b, D), generator=gen, dtype=torch.float64, device=centre.device)
+        x = centre[None, :] + z @ chol.T
+        x = torch.maximum(torch.minimum(x, target.hi), target.lo)
+        ll, g = target.loglik_grad(x)
+        ok = torch.isfinite(ll)
+        xs.append(x[ok]); lls.append(ll[ok]); gs.append(g[ok])
+        done += b
+    return torch.cat(xs), torch.cat(lls), torch.cat(gs)
+
+
+def train(net, x, ll, g, centre, ll_ref, epochs, batch, lr, gen, log=None):
+    n = x.shape[0]
+    u = (x - centre).float()
+    llc = (ll - ll_ref).float()
+    gf = g.float()
+    losses = []
+    steps = epochs * (n // batch)
+    for name, a in (("inputs", u), ("loglik", llc), ("grad", gf)):
+        if not bool(torch.isfinite(a).all()):
+            raise FloatingPointError(f"non-finite training {name}")
+    k = 0
+    for ep in range(epochs):
+        perm = torch.randperm(n, generator=gen, device=x.device)
+        for i in range(n // batch):
+            idx = perm[i * batch:(i + 1) * batch]
+            lr_k = lr * 0.5 * (1 + math.cos(math.pi * k / steps))    # cosine decay
+            loss = net.train_step(u[idx].contiguous(), llc[idx].contiguous(), gf[idx].contiguous(),
+                                  lr_k)
+            k += 1
+        losses.append(float(loss.item()))
+        if not math.isfinite(losses[-1]):
+            raise FloatingPointError(f"training loss became {losses[-1]} in epoch {ep}")
+        if log:
+            log(f"epoch {ep}: loss {losses[-1]:.4g}")
+    net.check()
+    return losses
+
+
+def holdout_error(net, target, centre, ll_ref, x, ll, g):
+    st = SurrogateTarget(net, target, centre, ll_ref)
+    lp, gp = st.logp_grad(x)
+    err = (lp - ll).abs()
+    gerr = (gp - g).norm(dim=1) / g.norm(dim=1).clamp_min(1e-30)
+    return float(err.median()), float(err.quantile(0.9)), float(gerr.median())
+
+
+def run(n_chains=4096, n_train=1_000_000, warmup_iter=200, sample_iter=100, n_steps=16,
+        spread=2.0, epochs=40, batch=4096, lr=2e-3, seed=20251017, device=0, log=None):
+    torch.cuda.set_device(device)
+    dev = torch.device("cuda", device)
+    gen = torch.Generator(device=dev).manual_seed(seed)
+    data, theta_true = model_array(seed, device=device)
+    target = ExactTarget(data, device)
+    D = data.dim
+    assert D == 47
+    x0 = torch.from_numpy(inputs.make_theta_batch(data, n_chains, seed=seed)).to(dev)
+    x0 = torch.maximum(torch.minimum(x0, target.hi), target.lo)
+    t0 = time.perf_counter()
+    st, eps, inv_mass, draws_w = warmup(target, x0, warmup_iter, n_steps, gen, log)
+    _sync()
+    t_warm = time.perf_counter() - t0
+    # Gaussian approximation of the posterior from the last warm-up draws
+    centre = draws_w.mean(dim=0)
+    cov = torch.cov(draws_w.T) + torch.diag(1e-12 * torch.diag(torch.cov(draws_w.T)).clamp_min(1e-300))
+    chol = torch.linalg.cholesky(cov)
+    H = torch.linalg.inv(cov)
+    ll_ref = float(st.lp.max())
+
+    # training data from the exact filter
+    t0 = time.perf_counter()
+    xt, llt, gt = make_training_set(target, centre, spread * chol, n_train, 16384, gen)
+    _sync()
+    t_data = time.perf_counter() - t0
+    n_hold = min(20000, xt.shape[0] // 10)
+    xh, llh, gh = xt[:n_hold], llt[:n_hold], gt[:n_hold]
+    xt, llt, gt = xt[n_hold:], llt[n_hold:], gt[n_hold:]
+    net = Surrogate(device=device, max_rows=max(batch, n_chains), seed=seed)
+    net.set_baseline(H.float().cpu().numpy())
+    u = (xt - centre)
+    resid = (llt - ll_ref) + 0.5 * torch.einsum("ni,ij,nj->n", u, H, u)   # target minus baseline
+    net.set_normalizers(np.zeros(D, np.float32), u.std(dim=0).cpu().numpy().astype(np.float32),
+                        float(resid.mean()), float(resid.std()), value_weight=1.0, grad_weight=1.0)
+    t0 = time.perf_counter()
+    losses = train(net, xt, llt, gt, centre, ll_ref, epochs, batch, lr, gen, log)
+    _sync()
+    t_train = time.perf_counter() - t0
+    med, p90, gmed = holdout_error(net, target, centre, ll_ref, xh, llh, gh)
+
+    eps_t = torch.full((n_chains, 1), eps, dtype=torch.float64, device=dev)
+    # plain exact HMC
+    st_h = sampler.ChainState(st.x.clone(), st.lp.clone(), st.g.clone())
+    draws_h, acc_h = [], []
+    _sync(); t0 = time.perf_counter()
+    for _ in range(sample_iter):
+        st_h, a = sampler.hmc_step(st_h, target.logp_grad, eps_t, n_steps, inv_mass, gen)
+        draws_h.append(st_h.x)
+        acc_h.append(a.mean())
+    _sync(); t_hmc = time.perf_counter() - t0
+    # delayed acceptance
+    sur = SurrogateTarget(net, target, centre, ll_ref)
+    lps, gs = sur.logp_grad(st.x)
+    st_d = sampler.DAState(st.x.clone(), lps, gs, st.lp.clone())
+    draws_d, acc1_d, acc_d, n_exact = [], [], [], 0
+    _sync(); t0 = time.perf_counter()
+    for _ in range(sample_iter):
+        st_d, a1, a, ne = sampler.da_hmc_step(st_d, sur.logp_grad, target.logp, eps_t, n_steps,
+                                              inv_mass, gen)
+        draws_d.append(st_d.x)
+        acc1_d.append(a1.mean()); acc_d.append(a.mean())
+        n_exact += ne
+    _sync(); t_da = time.perf_counter() - t0
+
+    dh = torch.stack(draws_h, dim=1).cpu().numpy()
+    dd = torch.stack(draws_d, dim=1).cpu().numpy()
+    ess_h = sampler.ess(dh)
+    ess_d = sampler.ess(dd)
+    # posterior agreement: difference of means in units of the combined MC error
+    var = dh.reshape(-1, D).var(axis=0)
+    se = np.sqrt(var / np.minimum(ess_h, dh.shape[0] * dh.shape[1]) +
+                 dd.reshape(-1, D).var(axis=0) / np.minimum(ess_d, dd.shape[0] * dd.shape[1]))
+    z = np.abs(dh.reshape(-1, D).mean(0) - dd.reshape(-1, D).mean(0)) / np.maximum(se, 1e-300)
+    sd_ratio = np.sqrt(dd.reshape(-1, D).var(axis=0) / var)
+    res = {
+        "chains": n_chains, "dim": D, "leapfrog_steps": n_steps, "step_size": eps,
+        "sample_iters": sample_iter, "warmup_iters": warmup_iter, "warmup_s": t_warm,
+        "train_rows": int(xt.shape[0]), "holdout_rows": int(n_hold), "epochs": epochs,
+        "baseline": "Gaussian from the warm-up draws (network fits the residual)",
+        "data_gen_s": t_data, "train_s": t_train, "final_loss": losses[-1],
+        "holdout_abs_err_nats_median": med, "holdout_abs_err_nats_p90": p90,
+        "holdout_grad_rel_err_median": gmed,
+        "hmc": {"seconds": t_hmc, "accept": float(torch.stack(acc_h).mean()),
+                "ess_min": float(ess_h.min()), "ess_median": float(np.median(ess_h)),
+                "ess_per_s": float(ess_h.min() / t_hmc),
+                "exact_grad_evals": sample_iter * n_steps * n_chains},
+        "da_hmc": {"seconds": t_da, "accept_stage1": float(torch.stack(acc1_d).mean()),
+                   "accept": float(torch.stack(acc_d).mean()),
+                   "ess_min": float(ess_d.min()), "ess_median": float(np.median(ess_d)),
+                   "ess_per_s": float(ess_d.min() / t_da),
+                   "ess_per_s_incl_training": float(ess_d.min() / (t_da + t_data + t_train)),
+                   "exact_ll_evals": n_exact,
+                   "surrogate_evals": sample_iter * n_steps * n_chains},
+        "posterior_mean_z_max": float(z.max()),
+        "posterior_sd_ratio_range": [float(sd_ratio.min()), float(sd_ratio.max())],
+    }
+    res["ess_per_s_gain"] = res["da_hmc"]["ess_per_s"] / max(res["hmc"]["ess_per_s"], 1e-300)
+    res["ess_per_s_gain_incl_training"] = (res["da_hmc"]["ess_per_s_incl_training"] /
+                                           max(res["hmc"]["ess_per_s"], 1e-300))
+    net.close()
+    return res

@@ -30,6 +30,7 @@ def _lib():
         lib.argus_surrogate_set_normalizers.argtypes = [vp, vp, vp, ctypes.c_float, ctypes.c_float,
                                                         ctypes.c_float, ctypes.c_float]
         lib.argus_surrogate_set_weights.argtypes = [vp, vp]
+        lib.argus_surrogate_set_baseline.argtypes = [vp, vp]
         lib.argus_surrogate_get_weights.argtypes = [vp, vp]
         lib.argus_surrogate_eval.argtypes = [vp, vp, ctypes.c_int64, vp, vp, vp]
         lib.argus_surrogate_train_step.argtypes = [vp, vp, vp, vp, ctypes.c_int64, ctypes.c_float,
@@ -78,6 +79,15 @@ class Surrogate:
         _check(_lib().argus_surrogate_set_normalizers(self.handle, xm.ctypes.data, xs.ctypes.data,
                                                       float(y_mean), float(y_std),
                                                       float(value_weight), float(grad_weight)))
+
+    def set_baseline(self, H):
+        """ll ~ net(x) - x^T H x / 2 (H: [47, 47]); None removes it."""
+        if H is None:
+            _check(_lib().argus_surrogate_set_baseline(self.handle, None))
+            return
+        Hf = np.ascontiguousarray(H, dtype=np.float32)
+        assert Hf.shape == (N_IN, N_IN)
+        _check(_lib().argus_surrogate_set_baseline(self.handle, Hf.ctypes.data))
 
     def set_weights(self, flat):
         flat = np.ascontiguousarray(flat, dtype=np.float32)

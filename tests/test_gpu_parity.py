@@ -263,3 +263,14 @@ def test_autotuner_picks_and_caches_a_plan(argus, tmp_path):
     ll_ref, g_ref = kalman.loglik_grad(data, theta[:3].cpu().numpy())
     assert ll_err(ll[:3].cpu().numpy(), ll_ref) <= LL_TOL
     assert g_err(g[:3].cpu().numpy(), g_ref) <= G_TOL
+
+
+def test_cw_signal_matches_oracle(argus):
+    from oracle import dense
+    data = inputs.make_array(np.array([300, 0, 57, 1000]), seed=115)
+    arr = argus.argus_array_create(data)
+    for th in inputs.make_theta_batch(data, 3, seed=19, kind="prior"):
+        s = argus.argus_cw_signal(arr, th, int(data.off[-1]))
+        ref = np.concatenate([dense.cw_signal(th[:7], data.pos[p], data.pulsar(p)[0])
+                              for p in range(data.n_pulsars)])
+        assert np.max(np.abs(s - ref)) <= 1e-12 * np.max(np.abs(ref))
