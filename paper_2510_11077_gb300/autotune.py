@@ -29,10 +29,14 @@ DEFAULT_SPACE = {
 }
 
 
+FILTER_SOURCES = ("kf_kernels.cu", "kf_math.cuh", "kf_internal.cuh")
+
+
 def _source_hash() -> str:
+    """Hash of the filter kernels' sources: a tuned plan is stale once they change."""
     h = hashlib.sha256()
     csrc = os.path.join(HERE, "csrc")
-    for f in sorted(os.listdir(csrc)):
+    for f in FILTER_SOURCES:
         h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 

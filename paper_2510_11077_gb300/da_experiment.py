@@ -42,6 +42,7 @@ class ExactTarget:
 
     def __init__(self, data, device):
         self.arr = argus.Array(data, device=device)      # loglik + grad, graph replay
+        self.arr.set_plan(tape_cache=1, walkers_per_cta=64, ctas_per_sm=8)
         self.arr_ll = argus.Array(data, device=device)   # loglik of varying batch sizes
         self.arr_ll.set_plan(use_graph=0)
         lo, hi = prior_box(data.n_pulsars)
@@ -202,7 +203,8 @@ def holdout_error(net, target, centre, ll_ref, x, ll, g):
 
 
 def run(n_chains=4096, n_train=1_000_000, warmup_iter=200, sample_iter=100, n_steps=16,
-        spread=2.0, epochs=40, batch=4096, lr=2e-3, seed=20251017, device=0, log=None):
+        spread=2.0, epochs=40, batch=4096, lr=1e-3, value_weight=10.0, seed=20251017, device=0,
+        retune_iter=40, log=None):
     torch.cuda.set_device(device)
     dev = torch.device("cuda", device)
     gen = torch.Generator(device=dev).manual_seed(seed)
@@ -222,6 +224,17 @@ def run(n_chains=4096, n_train=1_000_000, warmup_iter=200, sample_iter=100, n_st
     chol = torch.linalg.cholesky(cov)
     H = torch.linalg.inv(cov)
     ll_ref = float(st.lp.max())
+    # dense mass from the same covariance; re-tune the step size under it
+    mass = sampler.DenseMass(cov)
+    da_eps = sampler.DualAveraging(eps, target=0.8)
+    for it in range(retune_iter):
+        st, a = sampler.hmc_step(st, target.logp_grad, torch.full((n_chains, 1), eps,
+                                                                  dtype=torch.float64, device=dev),
+                                 n_steps, mass, gen)
+        eps = da_eps.update(float(a.mean()))
+    if retune_iter:
+        eps = da_eps.final()
+    inv_mass = mass
 
     # training data from the exact filter
     t0 = time.perf_counter()
@@ -236,7 +249,8 @@ def run(n_chains=4096, n_train=1_000_000, warmup_iter=200, sample_iter=100, n_st
     u = (xt - centre)
     resid = (llt - ll_ref) + 0.5 * torch.einsum("ni,ij,nj->n", u, H, u)   # target minus baseline
     net.set_normalizers(np.zeros(D, np.float32), u.std(dim=0).cpu().numpy().astype(np.float32),
-                        float(resid.mean()), float(resid.std()), value_weight=1.0, grad_weight=1.0)
+                        float(resid.mean()), float(resid.std()), value_weight=value_weight,
+                        grad_weight=1.0)
     t0 = time.perf_counter()
     losses = train(net, xt, llt, gt, centre, ll_ref, epochs, batch, lr, gen, log)
     _sync()
@@ -279,6 +293,7 @@ def run(n_chains=4096, n_train=1_000_000, warmup_iter=200, sample_iter=100, n_st
     sd_ratio = np.sqrt(dd.reshape(-1, D).var(axis=0) / var)
     res = {
         "chains": n_chains, "dim": D, "leapfrog_steps": n_steps, "step_size": eps,
+        "mass": "dense (warm-up covariance)",
         "sample_iters": sample_iter, "warmup_iters": warmup_iter, "warmup_s": t_warm,
         "train_rows": int(xt.shape[0]), "holdout_rows": int(n_hold), "epochs": epochs,
         "baseline": "Gaussian from the warm-up draws (network fits the residual)",

@@ -30,15 +30,47 @@ import numpy as np
 import torch
 
 
+class DenseMass:
+    """Kinetic energy p^T S p / 2 with S = inverse mass (e.g. a posterior
+    covariance); momenta p ~ N(0, S^-1) drawn as z L^-1 with S = L L^T."""
+
+    def __init__(self, S):
+        self.S = S
+        self.Linv = torch.linalg.inv(torch.linalg.cholesky(S))
+
+    def sample(self, shape, gen, dtype, device):
+        z = torch.randn(shape, generator=gen, dtype=dtype, device=device)
+        return z @ self.Linv
+
+    def kinetic(self, p):
+        return 0.5 * torch.sum((p @ self.S) * p, dim=1)
+
+    def velocity(self, p):
+        return p @ self.S
+
+
+def _sample_p(x, inv_mass, gen):
+    if isinstance(inv_mass, DenseMass):
+        return inv_mass.sample(x.shape, gen, x.dtype, x.device)
+    return torch.randn(x.shape, generator=gen, dtype=x.dtype, device=x.device) / torch.sqrt(inv_mass)
+
+
 def _kinetic(p, inv_mass):
+    if isinstance(inv_mass, DenseMass):
+        return inv_mass.kinetic(p)
     return 0.5 * torch.sum(p * p * inv_mass, dim=1)
 
 
+def _velocity(p, inv_mass):
+    return inv_mass.velocity(p) if isinstance(inv_mass, DenseMass) else inv_mass * p
+
+
 def leapfrog(x, p, lp, g, logp_grad, eps, n_steps, inv_mass):
-    """L leapfrog steps from (x, p) with cached (lp, g) at x; eps [C, 1]."""
+    """L leapfrog steps from (x, p) with cached (lp, g) at x; eps [C, 1];
+    inv_mass a [1, D] diagonal or a DenseMass."""
     p = p + 0.5 * eps * g
     for i in range(n_steps):
-        x = x + eps * inv_mass * p
+        x = x + eps * _velocity(p, inv_mass)
         lp, g = logp_grad(x)
         if i < n_steps - 1:
             p = p + eps * g
@@ -61,7 +93,7 @@ def hmc_step(state, logp_grad, eps, n_steps, inv_mass, gen):
     """One exact HMC transition for every chain.  Returns (state, accept_prob)."""
     x, lp, g = state.x, state.lp, state.g
     C = x.shape[0]
-    p = torch.randn(x.shape, generator=gen, dtype=x.dtype, device=x.device) / torch.sqrt(inv_mass)
+    p = _sample_p(x, inv_mass, gen)
     h0 = -lp + _kinetic(p, inv_mass)
     x1, p1, lp1, g1 = leapfrog(x, p, lp, g, logp_grad, eps, n_steps, inv_mass)
     lp1 = _finite(lp1)
@@ -91,7 +123,7 @@ def da_hmc_step(state, approx_logp_grad, exact_logp, eps, n_steps, inv_mass, gen
     """
     x = state.x
     C = x.shape[0]
-    p = torch.randn(x.shape, generator=gen, dtype=x.dtype, device=x.device) / torch.sqrt(inv_mass)
+    p = _sample_p(x, inv_mass, gen)
     k0 = _kinetic(p, inv_mass)
     x1, p1, lps1, gs1 = leapfrog(x, p, state.lp_s, state.g_s, approx_logp_grad, eps, n_steps, inv_mass)
     lps1 = _finite(lps1)

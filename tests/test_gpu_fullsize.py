@@ -79,11 +79,20 @@ def test_array67_grad_1024_walkers(argus):
     assert _err_g(g[idx[1]][None, :], fd[None, :]) <= 1e-4
 
 
-def test_array100_grad_16384_walkers(argus):
+def test_array100_grad_16384_walkers(argus, tmp_path):
+    """In the benchmark's own launch configuration: the autotuner's plan for this
+    array and batch (from the committed cache, else tuned here)."""
+    from paper_2510_11077_gb300 import autotune
     w = inputs.WORKLOADS["psr100_toalognormal_w16384"]
     data = inputs.make_workload_array(w.name)
     theta = inputs.make_theta_batch(data, w.batch, seed=w.seed)
     arr = argus.argus_array_create(data)
+    cache = autotune.load_cache()
+    key = autotune.plan_key(data.n_toa, w.batch, True, torch.cuda.get_device_name(0))
+    if key in cache:
+        arr.set_plan(**cache[key]["plan"])
+    else:
+        arr.set_plan(tape_cache=1, walkers_per_cta=64, ctas_per_sm=8)
     ll, g = argus.argus_loglik_grad(arr, torch.from_numpy(theta).cuda())
     ll, g = ll.cpu().numpy(), g.cpu().numpy()
     assert np.all(np.isfinite(ll)) and np.all(np.isfinite(g))
