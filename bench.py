@@ -356,8 +356,8 @@ def run_da_hmc(args):
                           if os.environ.get("CUDA_VISIBLE_DEVICES") else str(local))
     clocks.start()
     res = da_experiment.run(n_chains=4096, n_train=1_000_000, warmup_iter=200, sample_iter=100,
-                            n_steps=16, epochs=40, batch=4096, lr=1e-3, value_weight=10.0,
-                            device=local)
+                            da_iter=400, n_steps=16, epochs=60, batch=4096, lr=1e-3,
+                            value_weight=10.0, device=local)
     # tensor-core throughput of the surrogate: eval of 4096 rows, and a train step
     dev = torch.device("cuda", local)
     net = surrogate.Surrogate(device=local, max_rows=4096, seed=1)

@@ -83,6 +83,14 @@ argus_status argus_surrogate_train_step(argus_surrogate* s, const float* theta, 
                                         const float* grad, int64_t n, float lr, float* loss,
                                         void* stream);
 
+/* Which gradient argus_surrogate_eval returns: mode 0 (default) = the 47
+ * gradient outputs of the network; mode 1 = the exact input gradient of the
+ * value output, by back-propagation through the network (one backward pass
+ * per eval).  Mode 1 makes the surrogate a conservative field -- the gradient
+ * of the density it reports -- which a Hamiltonian integrator needs to
+ * conserve the surrogate's energy. */
+argus_status argus_surrogate_set_grad_mode(argus_surrogate* s, int32_t mode);
+
 /* Synchronise and report whether a bounded device-side wait of the tensor-core
  * kernels gave up since the last check (ARGUS_ERR_TIMEOUT; the flag is then
  * cleared).  Message of the last surrogate error on this host thread. */

@@ -111,6 +111,22 @@ def backward(params, cache, dy, rnd: bool = True):
     return grads
 
 
+def value_input_grad(params, x, rnd: bool = True):
+    """d y_0 / d x: the value output's gradient with respect to the (standardized,
+    padded) input, by back-propagating dY = e_0 with the same rounding points as
+    the weight gradients (BF16 operands, FP32 accumulation)."""
+    y, (xs, zs) = forward(params, x, rnd)
+    dt = y.dtype
+    dz_bf = np.zeros_like(y)
+    dz_bf[:, 0] = 1.0
+    for l in reversed(range(len(params))):
+        W, _ = params[l]
+        dx = (dz_bf @ _r(W.astype(dt), rnd)).astype(dt)
+        if l == 0:
+            return y, dx
+        dz_bf = _r((dx * gelu_grad(zs[l - 1])).astype(dt), rnd)
+
+
 class Adam:
     """Adam on FP32 master weights (Kingma & Ba 2015), bias-corrected."""
 

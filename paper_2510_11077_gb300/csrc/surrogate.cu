@@ -181,6 +181,29 @@ __global__ void k_cast_w(const float* __restrict__ W, int N, int K, __nv_bfloat1
     w16t[int64_t(i) * N + o] = b;
 }
 
+// dY = one-hot on the value output (1 in column 0 of real rows), for
+// back-propagating the value head to the inputs.
+__global__ void k_seed_value(int64_t n, int rows, __nv_bfloat16* __restrict__ dy) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= rows) return;
+    for (int j = 0; j < kMlpOutPad; ++j)
+        dy[int64_t(r) * kMlpOutPad + j] = __float2bfloat16_rn((j == 0 && r < n) ? 1.0f : 0.0f);
+}
+
+// Value and its exact input gradient: ll = y0 ys + ym (+ base),
+// grad_k = dx0_k ys / xs_k (+ gbase), dx0 = d y0 / d(standardized input).
+__global__ void k_destandardize_bp(const float* __restrict__ y, const float* __restrict__ dx0,
+                                   int64_t n, Norm nm, const float* __restrict__ base,
+                                   const float* __restrict__ gbase, float* __restrict__ ll,
+                                   float* __restrict__ grad) {
+    const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    ll[r] = y[r * kMlpOutPad] * nm.ys + nm.ym + (base ? base[r] : 0.0f);
+    for (int k = 0; k < kMlpIn; ++k)
+        grad[r * kMlpIn + k] = dx0[r * kMlpInPad + k] * nm.ys / nm.xs[k] +
+                               (gbase ? gbase[r * kMlpIn + k] : 0.0f);
+}
+
 // Quadratic baseline of the log-likelihood in the network's input coordinates:
 // base = -1/2 u^T H u, gbase = -H u (H symmetric [47][47]; all zero = no baseline).
 __global__ void k_baseline(const float* __restrict__ u, int64_t n, const float* __restrict__ H,
@@ -254,6 +277,8 @@ struct argus_surrogate {
     int last_chunks = 0;   // split-K chunks of the last training step
     // tensor maps
     CUtensorMap tmW[kMlpLayers], tmWT[kMlpLayers], tmH[kMlpLayers], tmHT[kMlpLayers];
+    CUtensorMap tmWT0_b64;   // W_0^T [64][256] with a 64-row box (B operand of dX0 = dZ1 W0)
+    int grad_mode = 0;       // 0: gradient head; 1: back-propagated value head
     CUtensorMap tmdY, tmdYT, tmdZ16[2], tmdZT[2];
 };
 
@@ -282,6 +307,7 @@ argus_status build_maps(argus_surrogate* s) {
         ok &= make_tmap_bf16(&s->tmH[l], s->H[l], R, kIn[l], 128);
         ok &= make_tmap_bf16(&s->tmHT[l], s->HT[l], kIn[l], R, kIn[l] == 64 ? 64 : 128);
     }
+    ok &= make_tmap_bf16(&s->tmWT0_b64, s->W16T[0], kIn[0], kOut[0], 64);
     ok &= make_tmap_bf16(&s->tmdY, s->dY, R, kMlpOutPad, 128);
     ok &= make_tmap_bf16(&s->tmdYT, s->dYT, kMlpOutPad, R, 64);
     for (int i = 0; i < 2; ++i) {
@@ -330,6 +356,40 @@ argus_status forward(argus_surrogate* s, int rows, bool train, cudaStream_t st) 
         }
         if (ce != cudaSuccess) return scuda(ce, "forward GEMM");
     }
+    return ARGUS_OK;
+}
+
+// d y0 / d(standardized input) for the rows of the last forward pass (which
+// saved its pre-activations): back-propagate a one-hot dY on the value output
+// through the four GELU layers and W_0.  Result in dZ32[1] as [rows][64].
+argus_status value_input_grad(argus_surrogate* s, int64_t n, int rows, cudaStream_t st) {
+    k_seed_value<<<(rows + 127) / 128, 128, 0, st>>>(n, rows, s->dY);
+    GemmEpiArgs d = epi_none();
+    d.zin = s->Z[4];
+    d.ldz = kMlpHidden;
+    d.out_bf16 = s->dZ16[0];
+    d.ldb = kMlpHidden;
+    cudaError_t ce = launch_gemm_tc(&s->tmdY, &s->tmWT[4], rows, kMlpHidden, kMlpOutPad, 128, 1,
+                                    kEpiGeluBwd, d, s->err, st);
+    if (ce != cudaSuccess) return scuda(ce, "value backprop GEMM");
+    int cur = 0;
+    for (int l = kMlpLayers - 2; l >= 1; --l) {
+        GemmEpiArgs g = epi_none();
+        g.zin = s->Z[l];
+        g.ldz = kMlpHidden;
+        g.out_bf16 = s->dZ16[cur ^ 1];
+        g.ldb = kMlpHidden;
+        ce = launch_gemm_tc(&s->tmdZ16[cur], &s->tmWT[l], rows, kMlpHidden, kMlpHidden, 128, 1,
+                            kEpiGeluBwd, g, s->err, st);
+        if (ce != cudaSuccess) return scuda(ce, "value backprop GEMM");
+        cur ^= 1;
+    }
+    GemmEpiArgs x = epi_none();
+    x.out_f32 = s->dZ32[1];
+    x.ldo = kMlpInPad;
+    ce = launch_gemm_tc(&s->tmdZ16[cur], &s->tmWT0_b64, rows, kMlpInPad, kMlpHidden, 64, 1, kEpiF32,
+                        x, s->err, st);
+    if (ce != cudaSuccess) return scuda(ce, "value backprop GEMM");
     return ARGUS_OK;
 }
 
@@ -547,14 +607,23 @@ argus_status argus_surrogate_eval(argus_surrogate* s, const float* theta, int64_
         const int rows = int(((n + 127) / 128) * 128);
         k_standardize<<<(rows + 127) / 128, 128, 0, st>>>(theta + r0 * kMlpIn, n, rows, s->norm,
                                                           s->H[0], nullptr, s->rows);
-        argus_status e = forward(s, rows, false, st);
+        const bool bp = grad && s->grad_mode == 1;
+        argus_status e = forward(s, rows, bp, st);
         if (e) return e;
         if (s->has_baseline)
             k_baseline<<<unsigned((n + 127) / 128), 128, 0, st>>>(theta + r0 * kMlpIn, n, s->Hq,
                                                                  s->base, s->gbase);
-        k_destandardize<<<unsigned((n + 127) / 128), 128, 0, st>>>(
-            s->Y, n, s->norm, s->has_baseline ? s->base : nullptr,
-            s->has_baseline ? s->gbase : nullptr, loglik + r0, grad ? grad + r0 * kMlpIn : nullptr);
+        if (!bp) {
+            k_destandardize<<<unsigned((n + 127) / 128), 128, 0, st>>>(
+                s->Y, n, s->norm, s->has_baseline ? s->base : nullptr,
+                s->has_baseline ? s->gbase : nullptr, loglik + r0, grad ? grad + r0 * kMlpIn : nullptr);
+        } else {
+            e = value_input_grad(s, n, rows, st);
+            if (e) return e;
+            k_destandardize_bp<<<unsigned((n + 127) / 128), 128, 0, st>>>(
+                s->Y, s->dZ32[1], n, s->norm, s->has_baseline ? s->base : nullptr,
+                s->has_baseline ? s->gbase : nullptr, loglik + r0, grad + r0 * kMlpIn);
+        }
         SCK(cudaGetLastError());
     }
     return ARGUS_OK;
@@ -650,6 +719,13 @@ argus_status argus_surrogate_train_step(argus_surrogate* s, const float* theta, 
         k_adam_b<<<(N + 255) / 256, 256, 0, st>>>(s->b[l], s->mb[l], s->vb[l], s->gb[l], N, lr, c1, c2);
     }
     SCK(cudaGetLastError());
+    return ARGUS_OK;
+}
+
+argus_status argus_surrogate_set_grad_mode(argus_surrogate* s, int32_t mode) {
+    if (!s) return sfail(ARGUS_ERR_INVALID_ARG, "surrogate handle is NULL");
+    if (mode != 0 && mode != 1) return sfail(ARGUS_ERR_INVALID_ARG, "mode must be 0 or 1");
+    s->grad_mode = mode;
     return ARGUS_OK;
 }
 

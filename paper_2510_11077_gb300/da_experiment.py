@@ -2,9 +2,11 @@
 
 1. Exact HMC warm-up (all chains in lock-step) with dual-averaging step size
    and a diagonal mass matrix from the warm-up draws.
-2. Training set: parameter vectors drawn around the warm-up posterior
-   (Gaussian, `spread` x the posterior standard deviation, inside the prior
-   box), each evaluated by the exact FP64 filter (loglik + gradient).
+2. Training set: points drawn around the warm-up posterior (Gaussian with
+   `spread` x its covariance), each evaluated by the exact FP64 filter
+   (loglik + gradient).
+   Sampling, training and the surrogate all work in unconstrained
+   coordinates z (theta = lo + (hi - lo) sigmoid(z) for the uniform prior box).
 3. Surrogate training on the GPU (BF16 tensor-core MLP, Adam).
 4. From the same warmed-up state: plain exact HMC and delayed-acceptance HMC
    (surrogate trajectory and stage 1, exact filter as stage 2), both with the
@@ -38,7 +40,13 @@ def prior_box(P):
 
 
 class ExactTarget:
-    """log posterior = exact FP64 filter log-likelihood inside the prior box."""
+    """Exact FP64 filter posterior in unconstrained coordinates z.
+
+    Every parameter has a uniform prior on a box [lo, hi]; sampling runs in
+    z with theta = lo + (hi - lo) sigmoid(z), so the target is
+    log p(z) = ll(theta(z)) + sum log(dtheta/dz) and no trajectory meets a
+    wall.
+    """
 
     def __init__(self, data, device):
         self.arr = argus.Array(data, device=device)      # loglik + grad, graph replay
@@ -52,51 +60,62 @@ class ExactTarget:
         self.calls_ll = 0
         self._bufs = {}
 
-    def inside(self, x):
-        return torch.all((x >= self.lo) & (x <= self.hi), dim=1)
+    def to_theta(self, z):
+        return self.lo + (self.hi - self.lo) * torch.sigmoid(z)
 
-    def loglik_grad(self, x):
-        """Exact loglik + gradient through fixed buffers (one captured graph per
-        batch size is replayed instead of re-captured)."""
-        B, D = x.shape
+    def to_z(self, theta):
+        u = ((theta - self.lo) / (self.hi - self.lo)).clamp(1e-12, 1 - 1e-12)
+        return torch.log(u) - torch.log1p(-u)
+
+    def _jac(self, z):
+        sg = torch.sigmoid(z)
+        dtdz = (self.hi - self.lo) * sg * (1 - sg)
+        return torch.log(dtdz).sum(dim=1), dtdz, 1 - 2 * sg
+
+    def loglik_grad(self, theta):
+        """Exact loglik + gradient in theta, through fixed buffers (one captured
+        graph per batch size is replayed instead of re-captured)."""
+        B, D = theta.shape
         if B not in self._bufs:
-            dev = x.device
+            dev = theta.device
             self._bufs[B] = (torch.empty((B, D), dtype=torch.float64, device=dev),
                              torch.empty(B, dtype=torch.float64, device=dev),
                              torch.empty((B, D), dtype=torch.float64, device=dev))
         th, ll, g = self._bufs[B]
-        th.copy_(x)
+        th.copy_(theta)
         argus.argus_loglik_grad(self.arr, th, ll, g)
         return ll.clone(), g.clone()
 
-    def logp_grad(self, x):
-        ll, g = self.loglik_grad(x)
-        self.calls_grad += x.shape[0]
-        m = self.inside(x)
-        ll = torch.where(m, ll, torch.full_like(ll, -math.inf))
-        return ll, torch.where(m[:, None], g, torch.zeros_like(g))
+    def logp_grad(self, z):
+        ll, g = self.loglik_grad(self.to_theta(z))
+        self.calls_grad += z.shape[0]
+        lj, dtdz, glj = self._jac(z)
+        lp = ll + lj
+        lp = torch.where(torch.isfinite(lp), lp, torch.full_like(lp, -math.inf))
+        return lp, g * dtdz + glj
 
-    def logp(self, x):
-        ll = argus.argus_loglik(self.arr_ll, x.contiguous())
-        self.calls_ll += x.shape[0]
-        return torch.where(self.inside(x), ll, torch.full_like(ll, -math.inf))
+    def logp(self, z):
+        ll = argus.argus_loglik(self.arr_ll, self.to_theta(z).contiguous())
+        self.calls_ll += z.shape[0]
+        lp = ll + self._jac(z)[0]
+        return torch.where(torch.isfinite(lp), lp, torch.full_like(lp, -math.inf))
 
 
 class SurrogateTarget:
-    """log posterior approximated by the trained network, same prior box."""
+    """The same log posterior in z approximated by the trained network (fed the
+    offset from a fixed FP64 centre, and returning the offset from ll_ref)."""
 
     def __init__(self, net, exact, centre, ll_ref):
         self.net, self.exact = net, exact
         self.centre = centre
         self.ll_ref = ll_ref
 
-    def logp_grad(self, x):
-        u = (x - self.centre).float().contiguous()
-        ll, g = self.net.eval(u)
-        ll = ll.double() + self.ll_ref
-        m = self.exact.inside(x)
-        ll = torch.where(m, ll, torch.full_like(ll, -math.inf))
-        return ll, torch.where(m[:, None], g.double(), torch.zeros_like(x))
+    def logp_grad(self, z):
+        u = (z - self.centre).float().contiguous()
+        lp, g = self.net.eval(u)
+        lp = lp.double() + self.ll_ref
+        lp = torch.where(torch.isfinite(lp), lp, torch.full_like(lp, -math.inf))
+        return lp, g.double()
 
 
 def _sync():
@@ -150,7 +169,7 @@ def warmup(target, x0, n_iter, n_steps, gen, log=None):
 
 
 def make_training_set(target, centre, chol, n, batch, gen):
-    """n exact (loglik, grad) evaluations at centre + chol N(0, I), inside the box."""
+    """n exact (log posterior, gradient) evaluations at centre + chol N(0, I) in z."""
     D = centre.shape[0]
     xs, lls, gs = [], [], []
     done = 0
@@ -158,8 +177,7 @@ def make_training_set(target, centre, chol, n, batch, gen):
         b = min(batch, n - done)
         z = torch.randn((b, D), generator=gen, dtype=torch.float64, device=centre.device)
         x = centre[None, :] + z @ chol.T
-        x = torch.maximum(torch.minimum(x, target.hi), target.lo)
-        ll, g = target.loglik_grad(x)
+        ll, g = target.logp_grad(x)
         ok = torch.isfinite(ll)
         xs.append(x[ok]); lls.append(ll[ok]); gs.append(g[ok])
         done += b
@@ -202,9 +220,10 @@ def holdout_error(net, target, centre, ll_ref, x, ll, g):
     return float(err.median()), float(err.quantile(0.9)), float(gerr.median())
 
 
-def run(n_chains=4096, n_train=1_000_000, warmup_iter=200, sample_iter=100, n_steps=16,
-        spread=2.0, epochs=40, batch=4096, lr=1e-3, value_weight=10.0, seed=20251017, device=0,
-        retune_iter=40, log=None):
+def run(n_chains=4096, n_train=1_000_000, warmup_iter=200, sample_iter=100, da_iter=None,
+        n_steps=16,
+        spread=1.0, epochs=40, batch=4096, lr=1e-3, value_weight=10.0, seed=20251017, device=0,
+        retune_iter=40, grad_mode=1, log=None):
     torch.cuda.set_device(device)
     dev = torch.device("cuda", device)
     gen = torch.Generator(device=dev).manual_seed(seed)
@@ -212,8 +231,8 @@ def run(n_chains=4096, n_train=1_000_000, warmup_iter=200, sample_iter=100, n_st
     target = ExactTarget(data, device)
     D = data.dim
     assert D == 47
-    x0 = torch.from_numpy(inputs.make_theta_batch(data, n_chains, seed=seed)).to(dev)
-    x0 = torch.maximum(torch.minimum(x0, target.hi), target.lo)
+    th0 = torch.from_numpy(inputs.make_theta_batch(data, n_chains, seed=seed)).to(dev)
+    x0 = target.to_z(torch.maximum(torch.minimum(th0, target.hi), target.lo))
     t0 = time.perf_counter()
     st, eps, inv_mass, draws_w = warmup(target, x0, warmup_iter, n_steps, gen, log)
     _sync()
@@ -267,13 +286,16 @@ def run(n_chains=4096, n_train=1_000_000, warmup_iter=200, sample_iter=100, n_st
         draws_h.append(st_h.x)
         acc_h.append(a.mean())
     _sync(); t_hmc = time.perf_counter() - t0
-    # delayed acceptance
+    # delayed acceptance (grad_mode 1: trajectories follow the gradient of the
+    # surrogate's own value output, so they conserve its energy)
+    net.set_grad_mode(grad_mode)
     sur = SurrogateTarget(net, target, centre, ll_ref)
     lps, gs = sur.logp_grad(st.x)
     st_d = sampler.DAState(st.x.clone(), lps, gs, st.lp.clone())
     draws_d, acc1_d, acc_d, n_exact = [], [], [], 0
+    da_iter = da_iter or sample_iter
     _sync(); t0 = time.perf_counter()
-    for _ in range(sample_iter):
+    for _ in range(da_iter):
         st_d, a1, a, ne = sampler.da_hmc_step(st_d, sur.logp_grad, target.logp, eps_t, n_steps,
                                               inv_mass, gen)
         draws_d.append(st_d.x)
@@ -281,8 +303,8 @@ def run(n_chains=4096, n_train=1_000_000, warmup_iter=200, sample_iter=100, n_st
         n_exact += ne
     _sync(); t_da = time.perf_counter() - t0
 
-    dh = torch.stack(draws_h, dim=1).cpu().numpy()
-    dd = torch.stack(draws_d, dim=1).cpu().numpy()
+    dh = target.to_theta(torch.stack(draws_h, dim=1)).cpu().numpy()
+    dd = target.to_theta(torch.stack(draws_d, dim=1)).cpu().numpy()
     ess_h = sampler.ess(dh)
     ess_d = sampler.ess(dd)
     # posterior agreement: difference of means in units of the combined MC error
@@ -294,7 +316,9 @@ def run(n_chains=4096, n_train=1_000_000, warmup_iter=200, sample_iter=100, n_st
     res = {
         "chains": n_chains, "dim": D, "leapfrog_steps": n_steps, "step_size": eps,
         "mass": "dense (warm-up covariance)",
-        "sample_iters": sample_iter, "warmup_iters": warmup_iter, "warmup_s": t_warm,
+        "surrogate_gradient": "back-propagated value output" if grad_mode == 1 else "gradient outputs",
+        "sample_iters": sample_iter, "da_iters": da_iter, "warmup_iters": warmup_iter,
+        "warmup_s": t_warm,
         "train_rows": int(xt.shape[0]), "holdout_rows": int(n_hold), "epochs": epochs,
         "baseline": "Gaussian from the warm-up draws (network fits the residual)",
         "data_gen_s": t_data, "train_s": t_train, "final_loss": losses[-1],
@@ -310,7 +334,7 @@ def run(n_chains=4096, n_train=1_000_000, warmup_iter=200, sample_iter=100, n_st
                    "ess_per_s": float(ess_d.min() / t_da),
                    "ess_per_s_incl_training": float(ess_d.min() / (t_da + t_data + t_train)),
                    "exact_ll_evals": n_exact,
-                   "surrogate_evals": sample_iter * n_steps * n_chains},
+                   "surrogate_evals": da_iter * n_steps * n_chains},
         "posterior_mean_z_max": float(z.max()),
         "posterior_sd_ratio_range": [float(sd_ratio.min()), float(sd_ratio.max())],
     }

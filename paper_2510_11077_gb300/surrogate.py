@@ -31,6 +31,7 @@ def _lib():
                                                         ctypes.c_float, ctypes.c_float]
         lib.argus_surrogate_set_weights.argtypes = [vp, vp]
         lib.argus_surrogate_set_baseline.argtypes = [vp, vp]
+        lib.argus_surrogate_set_grad_mode.argtypes = [vp, ctypes.c_int32]
         lib.argus_surrogate_get_weights.argtypes = [vp, vp]
         lib.argus_surrogate_eval.argtypes = [vp, vp, ctypes.c_int64, vp, vp, vp]
         lib.argus_surrogate_train_step.argtypes = [vp, vp, vp, vp, ctypes.c_int64, ctypes.c_float,
@@ -88,6 +89,10 @@ class Surrogate:
         Hf = np.ascontiguousarray(H, dtype=np.float32)
         assert Hf.shape == (N_IN, N_IN)
         _check(_lib().argus_surrogate_set_baseline(self.handle, Hf.ctypes.data))
+
+    def set_grad_mode(self, mode: int):
+        """0: gradient outputs of the network; 1: back-propagated value output."""
+        _check(_lib().argus_surrogate_set_grad_mode(self.handle, int(mode)))
 
     def set_weights(self, flat):
         flat = np.ascontiguousarray(flat, dtype=np.float32)

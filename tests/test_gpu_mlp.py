@@ -146,3 +146,20 @@ def test_surrogate_training_fits_a_smooth_function(lib):
     losses = [float(s.train_step(th, l_, g_, lr=2e-3).item()) for _ in range(150)]
     s.check()
     assert losses[-1] < 0.1 * losses[0], (losses[0], losses[-1])
+
+
+def test_surrogate_value_backprop_gradient_matches_oracle(lib):
+    n = 700
+    s, params, theta, xm, xs, ym, ys = _setup(14, n)
+    s.set_grad_mode(1)
+    ll, g = s.eval(torch.from_numpy(theta).cuda())
+    s.check()
+    ll, g = ll.cpu().numpy(), g.cpu().numpy()
+    x = np.zeros((n, mlp.IN_PAD), np.float32)
+    x[:, :mlp.IN_DIM] = (theta.astype(np.float32) - xm) / xs
+    y, dx = mlp.value_input_grad(params, x)
+    g_ref = dx[:, :mlp.IN_DIM] * np.float32(ys) / xs
+    assert np.max(np.abs(ll - (y[:, 0] * ys + ym))) <= 2e-2 * ys * max(np.abs(y[:, 0]).max(), 1e-3)
+    dg = np.abs(g - g_ref)
+    assert dg.max() <= 3e-2 * np.abs(g_ref).max(), (dg.max(), np.abs(g_ref).max())
+    assert np.median(dg) <= 2e-3 * np.abs(g_ref).max()

@@ -122,3 +122,15 @@ def test_training_reduces_loss_and_keeps_padding_zero():
     assert losses[-1] < 0.5 * losses[0]
     assert np.all(params[0][0][:, mlp.IN_DIM:] == 0) and np.all(params[4][0][mlp.OUT_DIM:] == 0)
     assert np.all(params[4][1][mlp.OUT_DIM:] == 0)
+
+
+def test_value_input_gradient_matches_finite_differences():
+    rng = np.random.default_rng(8)
+    params = _tiny_params(9)
+    x = np.zeros((3, mlp.IN_PAD)); x[:, :mlp.IN_DIM] = rng.standard_normal((3, mlp.IN_DIM))
+    _, g = mlp.value_input_grad(params, x, rnd=False)
+    h = 1e-6
+    for k in rng.choice(mlp.IN_DIM, 8, replace=False):
+        xp, xm = x.copy(), x.copy(); xp[:, k] += h; xm[:, k] -= h
+        fd = (mlp.forward(params, xp, rnd=False)[0][:, 0] - mlp.forward(params, xm, rnd=False)[0][:, 0]) / (2 * h)
+        assert np.allclose(g[:, k], fd, rtol=1e-5, atol=1e-7)
