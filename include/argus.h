@@ -79,7 +79,7 @@ enum { ARGUS_MODE_BATCHED = 0, ARGUS_MODE_PLAIN = 1 };
 typedef struct argus_plan {
     int32_t mode;             /* ARGUS_MODE_BATCHED | ARGUS_MODE_PLAIN */
     int32_t walkers_per_cta;  /* lanes of one pulsar per thread block: 32, 64, 128 or 256 */
-    int32_t ctas_per_sm;      /* resident blocks per SM of the persistent grid, 1..8 */
+    int32_t ctas_per_sm;      /* resident blocks per SM of the persistent grid, 1..16 */
     int32_t ckpt_stride;      /* adjoint checkpoint stride in TOAs; 0 = ceil(sqrt(N_p)) */
     int32_t use_graph;        /* 1: capture each (theta, B, outputs) call once, then replay */
     int32_t tape_cache;       /* adjoint: 0 = re-run each segment from its checkpoint (memory

@@ -22,8 +22,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 DEFAULT_CACHE = os.path.join(HERE, "tuned_plans.json")
 
 DEFAULT_SPACE = {
-    "walkers_per_cta": (64, 128, 256),
-    "ctas_per_sm": (2, 4, 8),
+    "walkers_per_cta": (32, 64, 128),
+    "ctas_per_sm": (4, 8, 16),
     "tape_cache": (0, 1),
     "ckpt_stride": (0,),
 }

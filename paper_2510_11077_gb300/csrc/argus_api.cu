@@ -143,8 +143,8 @@ argus_status validate_plan(const argus_plan* p) {
     const int w = p->walkers_per_cta;
     if (w != 32 && w != 64 && w != 128 && w != 256)
         return fail(ARGUS_ERR_INVALID_ARG, "plan.walkers_per_cta must be 32, 64, 128 or 256");
-    if (p->ctas_per_sm < 1 || p->ctas_per_sm > 8)
-        return fail(ARGUS_ERR_INVALID_ARG, "plan.ctas_per_sm must be in 1..8");
+    if (p->ctas_per_sm < 1 || p->ctas_per_sm > 16)
+        return fail(ARGUS_ERR_INVALID_ARG, "plan.ctas_per_sm must be in 1..16");
     if (p->ckpt_stride < 0 || p->ckpt_stride > kMaxStride)
         return fail(ARGUS_ERR_INVALID_ARG, "plan.ckpt_stride must be in 0..256");
     if (p->use_graph != 0 && p->use_graph != 1)
@@ -462,7 +462,7 @@ argus_status argus_array_create(const argus_pulsar* psrs, int32_t n_pulsars, int
     h->plan = default_plan();
     h->h_psr.resize(n_pulsars);
 
-    // A0 pre-stage: per-TOA records [t, dt, dt^2/2, dt^3/3, r, sigma^2, dt^2, 0]
+    // A0 pre-stage: per-TOA records [t, dt, dt^2/2, dt^3/3, r, sigma^2, dt^2, 2 dt]
     std::vector<double> rec(size_t(std::max<int64_t>(total, 1)) * kRecDoubles, 0.0);
     int64_t off = 0;
     for (int p = 0; p < n_pulsars; ++p) {
@@ -483,7 +483,7 @@ argus_status argus_array_create(const argus_pulsar* psrs, int32_t n_pulsars, int
             q[4] = ps.r[k];
             q[5] = ps.sigma[k] * ps.sigma[k];
             q[6] = dt * dt;
-            q[7] = 0.0;
+            q[7] = 2.0 * dt;
         }
         off += ps.n_toa;
     }

@@ -9,13 +9,13 @@ namespace argus {
 constexpr int kNgw = 7;          // continuous-wave parameters at the head of theta
 constexpr int kRecDoubles = 8;   // doubles per staged TOA record
 constexpr int kCkptDoubles = 5;  // (m0, m1, p00, p01, p11) per checkpoint
-constexpr int kTapeDoubles = 6;  // (K0, K1, 1/S, e, sin, cos) per step of a segment
+constexpr int kTapeDoubles = 6;  // (R/S, K1, 1/S, e, sin, cos) per step of a segment
 constexpr int kMaxStride = 256;  // longest adjoint segment, in TOAs
 constexpr int kLaneConsts = 7;   // A, B, f, Phi0/(2 pi), sigma^2, EFAC^2, EFAC
 constexpr int kLaneGrads = 6;    // dll/dA, dB, t-weighted sin and cos sums, dsigma^2, EFAC term
 
 // One staged TOA record (8 doubles = 64 bytes, 16-byte aligned):
-//   [0] t  [1] dt  [2] dt^2/2  [3] dt^3/3  [4] r  [5] sigma^2  [6] dt^2  [7] 0
+//   [0] t  [1] dt  [2] dt^2/2  [3] dt^3/3  [4] r  [5] sigma^2  [6] dt^2  [7] 2 dt
 struct PulsarDev {
     int64_t off;      // first record of this pulsar
     int32_t n;        // TOAs

@@ -163,8 +163,8 @@ struct State {
     double m0, m1, p00, p01, p11;
 };
 
-struct StepOut {   // what the adjoint needs from the forward step
-    double K0, K1, rS, e, sn, cs;
+struct StepOut {   // what the adjoint needs from the forward step (w = R/S = 1 - K0)
+    double w, K1, rS, e, sn, cs;
 };
 
 // kTape: produce what the adjoint needs; kLL: accumulate the log-likelihood.
@@ -198,7 +198,7 @@ __device__ __forceinline__ void kf_step(State& x, const double* __restrict__ rec
     x.p01 = M01 * w;
     x.p11 = fma(-K1, M01, M11);
     if (kTape) {
-        so.K0 = M00 * rS; so.K1 = K1; so.rS = rS; so.e = e; so.sn = sn; so.cs = cs;
+        so.w = w; so.K1 = K1; so.rS = rS; so.e = e; so.sn = sn; so.cs = cs;
     }
     if (kLL) {
         quad = fma(e, g, quad);
@@ -223,15 +223,18 @@ struct LaneGrad {
 __device__ __forceinline__ void kf_step_adjoint(Adjoint& a, const StepOut& so,
                                                 const double* __restrict__ rec, LaneGrad& g) {
     const double t = rec[0], dt = rec[1], h2 = rec[2], h3 = rec[3], s2k = rec[5], dt2 = rec[6];
-    const double K0 = so.K0, K1 = so.K1, gg = so.e * so.rS;
-    const double t1 = fma(a.mu0, K0, a.mu1 * K1);
+    const double twodt = rec[7];
+    // K0 = M00/S = 1 - w
+    const double w = so.w, K1 = so.K1, gg = so.e * so.rS;
+    const double t1 = fma(-a.mu0, w, fma(a.mu1, K1, a.mu0));    // mu0 K0 + mu1 K1
     const double ebar = t1 - gg;                                // dL/de
-    const double u = fma(a.pi01, K1, a.pi00 * K0);
+    const double u = fma(-a.pi00, w, fma(a.pi01, K1, a.pi00));  // pi00 K0 + pi01 K1
     const double v = a.pi11 * K1;
-    const double Sbar = fma(-0.5 * so.rS, fma(-so.e, gg, 1.0), fma(-gg, t1, fma(K0, u, v * K1)));
+    const double ku = fma(-w, u, fma(v, K1, u));                // K0 u + K1 v
+    const double Sbar = fma(-0.5 * so.rS, fma(-so.e, gg, 1.0), fma(-gg, t1, ku));
     const double a0 = a.mu0 - ebar;                             // dL/d(predicted m0)
-    const double M00b = fma(a.mu0, gg, fma(a.pi00, fma(-2.0, K0, 1.0), fma(-a.pi01, K1, Sbar)));
-    const double M01b = fma(a.mu1, gg, fma(a.pi01, 1.0 - K0, -2.0 * v));
+    const double M00b = fma(a.mu0, gg, fma(a.pi00, fma(2.0, w, -1.0), fma(-a.pi01, K1, Sbar)));
+    const double M01b = fma(a.mu1, gg, fma(a.pi01, w, -2.0 * v));
     const double M11b = a.pi11;
     g.s2 = fma(M00b, h3, fma(M01b, h2, fma(M11b, dt, g.s2)));
     g.E = fma(Sbar, s2k, g.E);
@@ -245,7 +248,7 @@ __device__ __forceinline__ void kf_step_adjoint(Adjoint& a, const StepOut& so,
     a.mu0 = a0;
     a.mu1 = fma(dt, a0, a.mu1);
     a.pi00 = M00b;
-    a.pi01 = fma(2.0 * dt, M00b, M01b);
+    a.pi01 = fma(twodt, M00b, M01b);
     a.pi11 = fma(dt2, M00b, fma(dt, M01b, M11b));
 }
 
@@ -340,7 +343,7 @@ __global__ void __launch_bounds__(256) k_filter_fwd(FilterArgs a) {
 // Pass 1 runs the filter forward segment by segment (stride TOAs each) and
 // checkpoints the state at the start of every segment.  Pass 2 walks the
 // segments backwards: restore the checkpoint, re-run the segment forward
-// recording (K0, K1, 1/S, e, sin, cos) per step in the block's tape, then
+// recording (R/S, K1, 1/S, e, sin, cos) per step in the block's tape, then
 // run the adjoint steps in reverse.  Checkpoints and tape live in the block's
 // own slot of global scratch ([..][field][W], so a warp's accesses coalesce).
 // With kCache the tape of every segment is written during pass 1 and kept in
@@ -383,7 +386,7 @@ __global__ void __launch_bounds__(256) k_filter_grad(FilterArgs a) {
                     kf_step<kCache, true>(x, sm.rec + k * kRecDoubles, L, sm.tab, quad, lp, so);
                     if (kCache) {
                         double* tk = tp + int64_t(k0 + k) * kTapeDoubles * W;
-                        tk[0 * W] = so.K0; tk[1 * W] = so.K1; tk[2 * W] = so.rS;
+                        tk[0 * W] = so.w; tk[1 * W] = so.K1; tk[2 * W] = so.rS;
                         tk[3 * W] = so.e; tk[4 * W] = so.sn; tk[5 * W] = so.cs;
                     }
                 }
@@ -408,7 +411,7 @@ __global__ void __launch_bounds__(256) k_filter_grad(FilterArgs a) {
                     for (int k = 0; k < cnt; ++k) {
                         kf_step<true, false>(y, sm.rec + k * kRecDoubles, L, sm.tab, q2, l2, so);
                         double* tk = tp + int64_t(k) * kTapeDoubles * W;
-                        tk[0 * W] = so.K0; tk[1 * W] = so.K1; tk[2 * W] = so.rS;
+                        tk[0 * W] = so.w; tk[1 * W] = so.K1; tk[2 * W] = so.rS;
                         tk[3 * W] = so.e; tk[4 * W] = so.sn; tk[5 * W] = so.cs;
                     }
                 }
