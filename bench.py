@@ -40,7 +40,9 @@ FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.07e9 / 1e12
 # recursion counts 40 flops per TOA (predict 6 FMA + 2 add, signal and
 # innovation 4 FMA + 2 add, update 1 rcp + 2 mul + 5 FMA + 2 quad, FMA = 2
 # flops, transcendentals not counted); forward + recompute + adjoint = 3x.
+FLOPS_PER_LANE_STEP_FWD = 40
 FLOPS_PER_LANE_STEP_GRAD = 120
+LOGLIK_WORKLOAD = "psr20_toa500-2000_w4096"
 L2_FLUSH_BYTES = 256 << 20
 CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -58,6 +60,8 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-loglik", action="store_true",
+                    help="skip the loglik-only leg (20 pulsars x 4096 walkers)")
     ap.add_argument("--autotune", choices=["cache", "off", "force"], default="cache",
                     help="cache: use the tuned-plan cache, tuning on a miss; force: retune")
     ap.add_argument("--tune-batch", type=int, default=4096)
@@ -185,6 +189,50 @@ def run_reference(args):
     return 0
 
 
+def loglik_only(args, dev, local):
+    """Forward filter alone (K1 -> K2 -> K4) on the 20-pulsar, 4096-walker array:
+    loglik evals/s with the forward kernel timed live and its FP64 roofline."""
+    import torch
+
+    from paper_2510_11077_gb300 import argus, autotune, inputs
+    w = inputs.WORKLOADS[LOGLIK_WORKLOAD]
+    data = inputs.make_workload_array(w.name)
+    theta = torch.from_numpy(inputs.make_theta_batch(data, w.batch, seed=w.seed)).to(dev)
+    arr = argus.Array(data, device=local)
+    res = autotune.autotune(arr, theta, data.n_toa, grad=False, batch_for_key=w.batch,
+                            space={"tape_cache": (0,)})
+    ll = torch.empty(w.batch, dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    arr.set_timing(True)
+    for _ in range(3):
+        argus.argus_loglik(arr, theta, ll)
+    torch.cuda.synchronize(dev)
+    reps = 20
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(reps)]
+    kern = []
+    for k in range(reps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        argus.argus_loglik(arr, theta, ll)
+        ev[k][1].record(stream)
+        kern.append(arr.get_timing()[1])
+    torch.cuda.synchronize(dev)
+    step_ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    k_ms = statistics.mean(kern)
+    lane_steps = w.batch * int(data.n_toa.sum())
+    achieved = FLOPS_PER_LANE_STEP_FWD * lane_steps / (k_ms * 1e-3) / 1e12
+    arr.close()
+    return {"workload": w.name, "metric": "loglik evals/s", "value": w.batch / (step_ms * 1e-3),
+            "ms_per_step": step_ms, "plan": res["plan"], "autotune_cached": res["cached"],
+            "roofline": {"bound": "alu", "kernel": "k_filter_fwd", "kernel_ms": k_ms,
+                         "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved / FP64_PEAK_TFLOPS,
+                         "algorithmic": f"{FLOPS_PER_LANE_STEP_FWD} FP64 flop per lane-step x "
+                                        f"{lane_steps} lane-steps per launch"}}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -303,6 +351,7 @@ def run_ours(args):
         raise RuntimeError("plain and batched filters disagree")
     arr_p.close()
 
+    loglik_leg = None if args.no_loglik else loglik_only(args, dev, local)
     lane_steps = B * int(data.n_toa.sum())
     achieved = FLOPS_PER_LANE_STEP_GRAD * lane_steps / (filt_ms * 1e-3) / 1e12
     tr = traffic_record("k_filter_grad")
@@ -328,7 +377,7 @@ def run_ours(args):
             "plain_filter": plain, "batched_over_plain": value / world / plain["value"],
             "stage_ms": {"project": statistics.mean(k[0] for k in kern), "filter": filt_ms,
                          "reduce": statistics.mean(k[2] for k in kern)},
-            "clocks": clk, "cpu_baseline": cpu}
+            "clocks": clk, "cpu_baseline": cpu, "loglik_only": loglik_leg}
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -223,7 +223,7 @@ def holdout_error(net, target, centre, ll_ref, x, ll, g):
 def run(n_chains=4096, n_train=1_000_000, warmup_iter=200, sample_iter=100, da_iter=None,
         n_steps=16,
         spread=1.0, epochs=40, batch=4096, lr=1e-3, value_weight=10.0, seed=20251017, device=0,
-        retune_iter=40, grad_mode=1, log=None):
+        retune_iter=40, grad_mode=1, graph_leapfrog=True, log=None):
     torch.cuda.set_device(device)
     dev = torch.device("cuda", device)
     gen = torch.Generator(device=dev).manual_seed(seed)
@@ -290,6 +290,8 @@ def run(n_chains=4096, n_train=1_000_000, warmup_iter=200, sample_iter=100, da_i
     # surrogate's own value output, so they conserve its energy)
     net.set_grad_mode(grad_mode)
     sur = SurrogateTarget(net, target, centre, ll_ref)
+    lf = (sampler.GraphedLeapfrog(sur.logp_grad, n_steps, inv_mass, tuple(st.x.shape), st.x.dtype, dev)
+          if graph_leapfrog else None)
     lps, gs = sur.logp_grad(st.x)
     st_d = sampler.DAState(st.x.clone(), lps, gs, st.lp.clone())
     draws_d, acc1_d, acc_d, n_exact = [], [], [], 0
@@ -297,7 +299,7 @@ def run(n_chains=4096, n_train=1_000_000, warmup_iter=200, sample_iter=100, da_i
     _sync(); t0 = time.perf_counter()
     for _ in range(da_iter):
         st_d, a1, a, ne = sampler.da_hmc_step(st_d, sur.logp_grad, target.logp, eps_t, n_steps,
-                                              inv_mass, gen)
+                                              inv_mass, gen, leapfrog_fn=lf)
         draws_d.append(st_d.x)
         acc1_d.append(a1.mean()); acc_d.append(a.mean())
         n_exact += ne
@@ -317,6 +319,7 @@ def run(n_chains=4096, n_train=1_000_000, warmup_iter=200, sample_iter=100, da_i
         "chains": n_chains, "dim": D, "leapfrog_steps": n_steps, "step_size": eps,
         "mass": "dense (warm-up covariance)",
         "surrogate_gradient": "back-propagated value output" if grad_mode == 1 else "gradient outputs",
+        "da_leapfrog": "CUDA graph" if graph_leapfrog else "eager",
         "sample_iters": sample_iter, "da_iters": da_iter, "warmup_iters": warmup_iter,
         "warmup_s": t_warm,
         "train_rows": int(xt.shape[0]), "holdout_rows": int(n_hold), "epochs": epochs,

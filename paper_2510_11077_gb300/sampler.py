@@ -113,7 +113,39 @@ class DAState:
         self.x, self.lp_s, self.g_s, self.lp_e = x, lp_s, g_s, lp_e
 
 
-def da_hmc_step(state, approx_logp_grad, exact_logp, eps, n_steps, inv_mass, gen):
+class GraphedLeapfrog:
+    """`leapfrog` for a fixed batch shape, captured once in a CUDA graph and
+    replayed (the trajectory's kernels launch without per-step host work).
+    The captured target must run only stream-ordered GPU work."""
+
+    def __init__(self, logp_grad, n_steps, inv_mass, shape, dtype, device, warmup=2):
+        C, D = shape
+        self.inp = [torch.zeros((C, D), dtype=dtype, device=device),      # x
+                    torch.zeros((C, D), dtype=dtype, device=device),      # p
+                    torch.zeros(C, dtype=dtype, device=device),           # lp
+                    torch.zeros((C, D), dtype=dtype, device=device),      # g
+                    torch.zeros((C, 1), dtype=dtype, device=device)]      # eps
+        self.n_steps, self.inv_mass, self.logp_grad = n_steps, inv_mass, logp_grad
+        side = torch.cuda.Stream(device)
+        side.wait_stream(torch.cuda.current_stream(device))
+        with torch.cuda.stream(side):
+            for _ in range(warmup):
+                leapfrog(*self.inp[:4], logp_grad, self.inp[4], n_steps, inv_mass)
+        torch.cuda.current_stream(device).wait_stream(side)
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph, capture_error_mode="relaxed"):
+            self.out = leapfrog(*self.inp[:4], logp_grad, self.inp[4], n_steps, inv_mass)
+
+    def __call__(self, x, p, lp, g, logp_grad, eps, n_steps, inv_mass):
+        assert logp_grad == self.logp_grad and n_steps == self.n_steps
+        for dst, src in zip(self.inp, (x, p, lp, g, eps)):
+            dst.copy_(src)
+        self.graph.replay()
+        return tuple(t.clone() for t in self.out)
+
+
+def da_hmc_step(state, approx_logp_grad, exact_logp, eps, n_steps, inv_mass, gen,
+                leapfrog_fn=None):
     """One delayed-acceptance HMC transition.
 
     approx_logp_grad(x) -> (lp, g): the cheap approximation (drives the
@@ -125,7 +157,8 @@ def da_hmc_step(state, approx_logp_grad, exact_logp, eps, n_steps, inv_mass, gen
     C = x.shape[0]
     p = _sample_p(x, inv_mass, gen)
     k0 = _kinetic(p, inv_mass)
-    x1, p1, lps1, gs1 = leapfrog(x, p, state.lp_s, state.g_s, approx_logp_grad, eps, n_steps, inv_mass)
+    lf = leapfrog_fn or leapfrog
+    x1, p1, lps1, gs1 = lf(x, p, state.lp_s, state.g_s, approx_logp_grad, eps, n_steps, inv_mass)
     lps1 = _finite(lps1)
     k1 = _kinetic(p1, inv_mass)
     dhs = (-state.lp_s + k0) - (-lps1 + k1)          # H_s(x, p) - H_s(x', p')
