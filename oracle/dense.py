@@ -18,6 +18,20 @@ separated from EFAC/EQUAD white measurement noise): with tau = t - t_1,
 (the covariance of a once-integrated Brownian motion plus the propagated
 prior), and ll_p = -1/2 [(r - s)^T C^-1 (r - s) + ln det C + N ln 2 pi].
 
+With Ornstein-Uhlenbeck red noise (paper, Functionality: OU processes for
+pulsar-intrinsic red noise), dy = -gam y dt + sigma_p dW, so y(tau) =
+e^{-gam tau} y_1 + eta(tau) and rho(tau) = rho_1 + g(tau) y_1 + int_0^tau eta,
+g(tau) = (1 - e^{-gam tau}) / gam.  Then
+
+  C_ij = P0_rr + P0_ry (g_i + g_j) + P0_yy g_i g_j
+         + sigma_p^2 int_0^m g(v) g(v + M - m) dv + delta_ij R_i,
+
+  int_0^m g(v) g(v + d) dv
+    = [m - g(m) - e^{-gam d} g(m) + e^{-gam d} (1 - e^{-2 gam m}) / (2 gam)] / gam^2
+
+(the covariance of the integral of an OU process started at zero), which
+tends to the integrated-Brownian-motion kernel as gam -> 0.
+
 Gradients: d ll / d theta = (ds/dtheta)^T alpha for the signal parameters and
 1/2 tr[(alpha alpha^T - C^-1) dC/deta] for the noise parameters, with
 alpha = C^-1 (r - s).
@@ -75,12 +89,37 @@ def ibm_covariance(t, sig2, p0, R):
     return C
 
 
+def ou_covariance(t, sig2, gam, p0, R):
+    """Dense covariance of one pulsar's residuals under OU red noise (gam may be
+    complex, for complex-step derivatives in gam)."""
+    tau = np.asarray(t, dtype=np.float64) - t[0]
+    mn = np.minimum.outer(tau, tau)
+    d = np.maximum.outer(tau, tau) - mn
+    g = -np.expm1(-gam * tau) / gam
+    gm = -np.expm1(-gam * mn) / gam
+    ed = np.exp(-gam * d)
+    K = (mn - gm - ed * gm - ed * np.expm1(-2.0 * gam * mn) / (2.0 * gam)) / (gam * gam)
+    C = p0[0] + p0[1] * (g[:, None] + g[None, :]) + p0[2] * np.outer(g, g) + sig2 * K
+    C[np.diag_indices_from(C)] += R
+    return C
+
+
+def _noise(data, p, theta):
+    """(sig2, gam or None, efac) of pulsar p."""
+    k = 3 if getattr(data, "model", "rw") == "ou" else 2
+    nz = theta[N_GW + k * p:N_GW + k * (p + 1)]
+    gam = 10.0 ** nz[1] if k == 3 else None
+    return 10.0 ** (2.0 * nz[0]), gam, nz[-1], k
+
+
 def _pulsar_parts(data, p, theta):
     t, r, sig = data.pulsar(p)
-    ls, efac = theta[N_GW + 2 * p], theta[N_GW + 2 * p + 1]
-    sig2 = 10.0 ** (2.0 * ls)
+    sig2, gam, efac, _ = _noise(data, p, theta)
     R = efac ** 2 * sig ** 2 + data.equad[p] ** 2
-    C = ibm_covariance(t, sig2, data.p0[p], R)
+    if gam is None:
+        C = ibm_covariance(t, sig2, data.p0[p], R)
+    else:
+        C = ou_covariance(t, sig2, gam, data.p0[p], R)
     s = cw_signal(theta[:N_GW], data.pos[p], t)
     return t, r, sig, sig2, efac, C, s
 
@@ -104,7 +143,8 @@ def grad(data, theta, h=1e-20):
     """Gradient by the dense formulas; ds/dtheta by complex step on cw_signal."""
     theta = np.asarray(theta, dtype=np.float64)
     P = data.n_pulsars
-    g = np.zeros(N_GW + 2 * P)
+    k = 3 if getattr(data, "model", "rw") == "ou" else 2
+    g = np.zeros(N_GW + k * P)
     for p in range(P):
         t, r, sig, sig2, efac, C, s = _pulsar_parts(data, p, theta)
         cf = cho_factor(C, lower=True)
@@ -116,10 +156,20 @@ def grad(data, theta, h=1e-20):
             g[j] += ds @ alpha
         Cinv = cho_solve(cf, np.eye(len(t)))
         M = np.outer(alpha, alpha) - Cinv
-        tau = t - t[0]
-        mn = np.minimum.outer(tau, tau)
-        mx = np.maximum.outer(tau, tau)
-        dC_ls = 2.0 * LN10 * sig2 * (mn * mn * mx / 2.0 - mn ** 3 / 6.0)
-        g[N_GW + 2 * p] = 0.5 * np.sum(M * dC_ls)
-        g[N_GW + 2 * p + 1] = 0.5 * np.sum(np.diag(M) * 2.0 * efac * sig ** 2)
+        R = efac ** 2 * sig ** 2 + data.equad[p] ** 2
+        if k == 2:
+            tau = t - t[0]
+            mn = np.minimum.outer(tau, tau)
+            mx = np.maximum.outer(tau, tau)
+            dC_ls = 2.0 * LN10 * sig2 * (mn * mn * mx / 2.0 - mn ** 3 / 6.0)
+        else:
+            # the red-noise part is proportional to sigma_p^2
+            lg = theta[N_GW + k * p + 1]
+            zero = np.zeros(3)
+            dC_ls = 2.0 * LN10 * (ou_covariance(t, sig2, 10.0 ** lg, zero, 0.0))
+            thc = 10.0 ** (lg + 1j * h)
+            dC_lg = np.imag(ou_covariance(t, sig2, thc, data.p0[p], R)) / h
+            g[N_GW + k * p + 1] = 0.5 * np.sum(M * dC_lg)
+        g[N_GW + k * p] = 0.5 * np.sum(M * dC_ls)
+        g[N_GW + k * p + k - 1] = 0.5 * np.sum(np.diag(M) * 2.0 * efac * sig ** 2)
     return g

@@ -46,6 +46,8 @@ typedef double complex cplx;
 /* ---- the filter, instantiated for double and for double complex ---- */
 #define KF_T double
 #define KF_NAME kf_real
+#define KF_PHI ou_phi_real
+#define KF_EXP exp
 #define KF_SIN sin
 #define KF_COS cos
 #define KF_LOG log
@@ -54,6 +56,8 @@ typedef double complex cplx;
 #include "kf_body.h"
 #undef KF_T
 #undef KF_NAME
+#undef KF_PHI
+#undef KF_EXP
 #undef KF_SIN
 #undef KF_COS
 #undef KF_LOG
@@ -61,6 +65,8 @@ typedef double complex cplx;
 
 #define KF_T cplx
 #define KF_NAME kf_cplx
+#define KF_PHI ou_phi_cplx
+#define KF_EXP cexp
 #define KF_SIN csin
 #define KF_COS ccos
 #define KF_LOG clog
@@ -96,33 +102,39 @@ static void cw_project(const cplx th[N_GW], const double c[3],
     *Phi0 = th[1];
 }
 
-static int theta_in_domain(const double* th, int P)
-{
-    int D = N_GW + 2 * P;
-    for (int j = 0; j < D; ++j)
-        if (!isfinite(th[j])) return 0;
-    if (fabs(th[3]) > 1.0 || fabs(th[4]) > 1.0) return 0;
-    for (int p = 0; p < P; ++p)
-        if (!(th[N_GW + 2 * p + 1] > 0.0)) return 0;
-    return 1;
-}
-
 typedef struct {
     int P;
     const int64_t* off;
     const double *t, *r, *sigma, *pos, *equad, *p0;
+    int ou;    /* 0: random walk, (log10 sigma, EFAC) per pulsar;
+                  1: OU, (log10 sigma, log10 gamma, EFAC) per pulsar */
 } array_view;
 
-/* one pulsar, complex parameters */
-static cplx pulsar_ll_c(const array_view* a, int p, const cplx thgw[N_GW],
-                        cplx log10sig, cplx efac, int* bad)
+static int n_noise(const array_view* a) { return a->ou ? 3 : 2; }
+
+static int theta_in_domain(const array_view* a, const double* th)
+{
+    int np = n_noise(a), D = N_GW + np * a->P;
+    for (int j = 0; j < D; ++j)
+        if (!isfinite(th[j])) return 0;
+    if (fabs(th[3]) > 1.0 || fabs(th[4]) > 1.0) return 0;
+    for (int p = 0; p < a->P; ++p)
+        if (!(th[N_GW + np * p + np - 1] > 0.0)) return 0;
+    return 1;
+}
+
+/* one pulsar, complex parameters; nz = its noise parameters (n_noise of them) */
+static cplx pulsar_ll_c(const array_view* a, int p, const cplx thgw[N_GW], const cplx* nz,
+                        int* bad)
 {
     cplx A, B, Om, Phi0;
     cw_project(thgw, a->pos + 3 * p, &A, &B, &Om, &Phi0);
-    cplx sig2 = cpow(10.0, 2.0 * log10sig);
+    cplx sig2 = cpow(10.0, 2.0 * nz[0]);
+    cplx gam = a->ou ? cpow(10.0, nz[1]) : 0.0;
+    cplx efac = nz[n_noise(a) - 1];
     int64_t o = a->off[p], n = a->off[p + 1] - a->off[p];
     return kf_cplx(n, a->t + o, a->r + o, a->sigma + o, a->equad[p], a->p0 + 3 * p,
-                   A, B, Om, Phi0, sig2, efac, bad, NULL, NULL);
+                   A, B, Om, Phi0, sig2, efac, a->ou, gam, bad, NULL, NULL);
 }
 
 /* one pulsar, real parameters */
@@ -132,16 +144,20 @@ static double pulsar_ll_r(const array_view* a, int p, const double* th, int* bad
     for (int j = 0; j < N_GW; ++j) thc[j] = th[j];
     cplx A, B, Om, Phi0;
     cw_project(thc, a->pos + 3 * p, &A, &B, &Om, &Phi0);
-    double sig2 = pow(10.0, 2.0 * th[N_GW + 2 * p]);
-    double efac = th[N_GW + 2 * p + 1];
+    int np = n_noise(a);
+    const double* nz = th + N_GW + np * p;
+    double sig2 = pow(10.0, 2.0 * nz[0]);
+    double gam = a->ou ? pow(10.0, nz[1]) : 0.0;
+    double efac = nz[np - 1];
     int64_t o = a->off[p], n = a->off[p + 1] - a->off[p];
     return kf_real(n, a->t + o, a->r + o, a->sigma + o, a->equad[p], a->p0 + 3 * p,
-                   creal(A), creal(B), creal(Om), creal(Phi0), sig2, efac, bad, NULL, NULL);
+                   creal(A), creal(B), creal(Om), creal(Phi0), sig2, efac, a->ou, gam, bad,
+                   NULL, NULL);
 }
 
 static double walker_ll(const array_view* a, const double* th, double* lane_ll)
 {
-    if (!theta_in_domain(th, a->P)) {
+    if (!theta_in_domain(a, th)) {
         if (lane_ll) for (int p = 0; p < a->P; ++p) lane_ll[p] = -INFINITY;
         return -INFINITY;
     }
@@ -161,7 +177,7 @@ static double walker_ll(const array_view* a, const double* th, double* lane_ll)
 
 static void walker_grad(const array_view* a, const double* th, double* g)
 {
-    int P = a->P, D = N_GW + 2 * P;
+    int P = a->P, np = n_noise(a), D = N_GW + np * P;
     memset(g, 0, sizeof(double) * D);
     cplx thgw[N_GW];
     for (int j = 0; j < N_GW; ++j) thgw[j] = th[j];
@@ -173,33 +189,38 @@ static void walker_grad(const array_view* a, const double* th, double* g)
         tj[j] += I * CS_H;
         double acc = 0.0;
         for (int p = 0; p < P; ++p) {
-            cplx lp = pulsar_ll_c(a, p, tj, th[N_GW + 2 * p], th[N_GW + 2 * p + 1], &bad);
+            cplx nz[3];
+            for (int i = 0; i < np; ++i) nz[i] = th[N_GW + np * p + i];
+            cplx lp = pulsar_ll_c(a, p, tj, nz, &bad);
             acc += cimag(lp) / CS_H;
         }
         g[j] = acc;
     }
     /* per-pulsar noise parameters: only their own pulsar depends on them */
     for (int p = 0; p < P; ++p) {
-        double ls = th[N_GW + 2 * p], ef = th[N_GW + 2 * p + 1];
-        cplx l1 = pulsar_ll_c(a, p, thgw, ls + I * CS_H, ef, &bad);
-        cplx l2 = pulsar_ll_c(a, p, thgw, ls, ef + I * CS_H, &bad);
-        g[N_GW + 2 * p] = cimag(l1) / CS_H;
-        g[N_GW + 2 * p + 1] = cimag(l2) / CS_H;
+        for (int i = 0; i < np; ++i) {
+            cplx nz[3];
+            for (int k = 0; k < np; ++k) nz[k] = th[N_GW + np * p + k];
+            nz[i] += I * CS_H;
+            cplx lp = pulsar_ll_c(a, p, thgw, nz, &bad);
+            g[N_GW + np * p + i] = cimag(lp) / CS_H;
+        }
     }
     if (bad) memset(g, 0, sizeof(double) * D);
 }
 
 /* ---------------------------- exported API ---------------------------- */
 
-/* Array log-likelihood for B parameter vectors theta[B][7+2P] -> out[B].
+/* Array log-likelihood for B parameter vectors theta[B][D] -> out[B],
+   D = 7 + 2P (model 0, random walk) or 7 + 3P (model 1, Ornstein-Uhlenbeck).
    lane_out (optional, may be NULL): per-pulsar terms [B][P]. */
 int oracle_loglik(int P, const int64_t* off, const double* t, const double* r,
                   const double* sigma, const double* pos, const double* equad,
-                  const double* p0, const double* theta, int64_t B,
+                  const double* p0, int model, const double* theta, int64_t B,
                   double* out, double* lane_out)
 {
-    array_view a = {P, off, t, r, sigma, pos, equad, p0};
-    int D = N_GW + 2 * P;
+    array_view a = {P, off, t, r, sigma, pos, equad, p0, model};
+    int D = N_GW + n_noise(&a) * P;
 #pragma omp parallel for schedule(dynamic, 1)
     for (int64_t b = 0; b < B; ++b)
         out[b] = walker_ll(&a, theta + b * D, lane_out ? lane_out + b * P : NULL);
@@ -209,11 +230,11 @@ int oracle_loglik(int P, const int64_t* off, const double* t, const double* r,
 /* Log-likelihood and gradient: out_ll[B], out_grad[B][7+2P]. */
 int oracle_loglik_grad(int P, const int64_t* off, const double* t, const double* r,
                        const double* sigma, const double* pos, const double* equad,
-                       const double* p0, const double* theta, int64_t B,
+                       const double* p0, int model, const double* theta, int64_t B,
                        double* out_ll, double* out_grad)
 {
-    array_view a = {P, off, t, r, sigma, pos, equad, p0};
-    int D = N_GW + 2 * P;
+    array_view a = {P, off, t, r, sigma, pos, equad, p0, model};
+    int D = N_GW + n_noise(&a) * P;
 #pragma omp parallel for schedule(dynamic, 1)
     for (int64_t b = 0; b < B; ++b) {
         const double* th = theta + b * D;
@@ -239,7 +260,8 @@ int oracle_cw_project(const double* theta_gw, const double* pos, double* out)
 }
 
 /* One pulsar's filter with explicit lane parameters lane = {A, B, Omega,
-   Phi0, sigma^2, EFAC}; optionally returns the innovations e_k and their
+   Phi0, sigma^2, EFAC, gamma}; gamma > 0 selects the Ornstein-Uhlenbeck
+   model, 0 the random walk; optionally returns the innovations e_k and their
    variances S_k (used by the calibration tests). */
 double oracle_pulsar_filter(int64_t n, const double* t, const double* r, const double* sigma,
                             double equad, const double* p0, const double* lane,
@@ -247,6 +269,6 @@ double oracle_pulsar_filter(int64_t n, const double* t, const double* r, const d
 {
     int bad = 0;
     double ll = kf_real(n, t, r, sigma, equad, p0, lane[0], lane[1], lane[2], lane[3],
-                        lane[4], lane[5], &bad, e_out, S_out);
+                        lane[4], lane[5], lane[6] > 0.0, lane[6], &bad, e_out, S_out);
     return bad ? -INFINITY : ll;
 }

@@ -18,7 +18,7 @@ def _load(path: str | None = None):
     path = path or _build.build()
     if path not in _libs:
         lib = ctypes.CDLL(path)
-        arr = [ctypes.c_int, _ip, _dp, _dp, _dp, _dp, _dp, _dp, _dp, ctypes.c_int64]
+        arr = [ctypes.c_int, _ip, _dp, _dp, _dp, _dp, _dp, _dp, ctypes.c_int, _dp, ctypes.c_int64]
         lib.oracle_loglik.argtypes = arr + [_dp, _dp]
         lib.oracle_loglik.restype = ctypes.c_int
         lib.oracle_loglik_grad.argtypes = arr + [_dp, _dp]
@@ -43,7 +43,9 @@ def _ptr(a):
 def _array_args(data):
     off = np.ascontiguousarray(data.off, dtype=np.int64)
     keep = [off, _d(data.t), _d(data.r), _d(data.sigma), _d(data.pos), _d(data.equad), _d(data.p0)]
-    args = [ctypes.c_int(data.n_pulsars), off.ctypes.data_as(_ip)] + [_ptr(a) for a in keep[1:]]
+    model = 1 if getattr(data, "model", "rw") == "ou" else 0
+    args = ([ctypes.c_int(data.n_pulsars), off.ctypes.data_as(_ip)] + [_ptr(a) for a in keep[1:]]
+            + [ctypes.c_int(model)])
     return keep, args
 
 
@@ -89,11 +91,13 @@ def cw_project(theta_gw, pos, lib_path: str | None = None):
 
 def pulsar_filter(t, r, sigma, equad, p0, lane, trace: bool = False,
                   lib_path: str | None = None):
-    """One pulsar's log-likelihood for lane = (A, B, Omega, Phi0, sigma^2, EFAC).
+    """One pulsar's log-likelihood for lane = (A, B, Omega, Phi0, sigma^2, EFAC
+    [, gamma]); gamma > 0 selects the Ornstein-Uhlenbeck red noise.
 
     With trace=True also returns the innovations e_k and variances S_k.
     """
     lib = _load(lib_path)
+    lane = np.concatenate([np.asarray(lane, dtype=np.float64), np.zeros(7 - len(lane))])
     t, r, sigma, p0, lane = _d(t), _d(r), _d(sigma), _d(p0), _d(lane)
     n = len(t)
     e = np.empty(n) if trace else None

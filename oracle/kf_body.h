@@ -15,32 +15,76 @@
  * Prior x(t_1) ~ N(0, P0).  The log-likelihood is the prediction-error
  * decomposition: sum_k -1/2 (ln 2 pi + ln S_k + e_k^2 / S_k).
  *
+ * With ou != 0 the frequency deviation is an Ornstein-Uhlenbeck process
+ * instead (paper, Functionality: pulsar-intrinsic red noise as an OU
+ * process): dy/dt = -gam y + xi(t).  Over dt, with x = gam dt,
+ *   F = [[1, dt phi1(x)], [0, exp(-x)]],
+ *   Q = sigma^2 [[dt^3/3 phi4(x), dt^2/2 phi1(x)^2], [., dt phi1(2x)]],
+ *   phi1(x) = (1 - e^-x)/x,  phi4(x) = 3 (x - 2 (1 - e^-x) + (1 - e^-2x)/2) / x^3,
+ * (both -> 1 as gam -> 0, the random walk), by their Taylor series below
+ * x = 0.5 and the closed forms above.
+ *
  * Steps per TOA in textbook order: predict the mean (m = F m) and covariance
  * (P = F P F^T + Q), form the signal and the innovation e = r - s - H m with
  * H = (1, 0) and its variance S = H P H^T + R, gain K = P H^T / S, update
  * m = m + K e and P = P - K S K^T, accumulate the likelihood term.
  */
+static void KF_PHI(KF_T x, KF_T* p1, KF_T* p2, KF_T* p4)
+{
+    if (KF_RE(x) < 0.5) {
+        /* Taylor series, 22 terms: phi1 = sum (-x)^m/(m+1)!,
+           phi4 = sum 3 (-1)^(m+3) (2 - 2^(m+2)) / (m+3)! x^m */
+        KF_T s1 = 0.0, s2 = 0.0, s4 = 0.0;
+        for (int m = 21; m >= 0; --m) {
+            double f1 = 1.0, f4 = 1.0;
+            for (int i = 2; i <= m + 1; ++i) f1 *= i;
+            for (int i = 2; i <= m + 3; ++i) f4 *= i;
+            double c1 = ((m & 1) ? -1.0 : 1.0) / f1;
+            double c4 = 3.0 * (((m + 3) & 1) ? -1.0 : 1.0) * (2.0 - pow(2.0, m + 2)) / f4;
+            s1 = s1 * x + c1;
+            s2 = s2 * (2.0 * x) + c1;
+            s4 = s4 * x + c4;
+        }
+        *p1 = s1; *p2 = s2; *p4 = s4;
+    } else {
+        KF_T e1 = KF_EXP(-x), e2 = KF_EXP(-2.0 * x);
+        *p1 = (1.0 - e1) / x;
+        *p2 = (1.0 - e2) / (2.0 * x);
+        *p4 = 3.0 * (x - 2.0 * (1.0 - e1) + 0.5 * (1.0 - e2)) / (x * x * x);
+    }
+}
+
 static KF_T KF_NAME(int64_t n, const double* t, const double* r, const double* sigma,
                     double equad, const double p0[3],
                     KF_T A, KF_T B, KF_T Om, KF_T Phi0, KF_T sig2, KF_T efac,
-                    int* bad, double* e_out, double* S_out)
+                    int ou, KF_T gam, int* bad, double* e_out, double* S_out)
 {
     KF_T m0 = 0.0, m1 = 0.0;
     KF_T p00 = p0[0], p01 = p0[1], p11 = p0[2];
     KF_T ll = 0.0;
     for (int64_t k = 0; k < n; ++k) {
         double dt = (k == 0) ? 0.0 : t[k] - t[k - 1];
-        /* transition F = [[1, dt], [0, 1]] and process noise
-           Q = sigma^2 [[dt^3/3, dt^2/2], [dt^2/2, dt]] */
+        /* transition F = [[1, b], [0, a]] and process noise Q; for the
+           random walk b = dt, a = 1, Q = sigma^2 [[dt^3/3, dt^2/2], [dt^2/2, dt]] */
+        KF_T b = dt, a = 1.0;
         KF_T q00 = sig2 * (dt * dt * dt / 3.0);
         KF_T q01 = sig2 * (dt * dt / 2.0);
         KF_T q11 = sig2 * dt;
+        if (ou) {
+            KF_T p1, p2, p4;
+            KF_PHI(gam * dt, &p1, &p2, &p4);
+            b = dt * p1;
+            a = 1.0 - gam * dt * p1;
+            q00 = q00 * p4;
+            q01 = q01 * p1 * p1;
+            q11 = q11 * p2;
+        }
         /* predict */
-        KF_T mp0 = m0 + dt * m1;
-        KF_T mp1 = m1;
-        KF_T a00 = p00 + dt * p01 + dt * p01 + dt * dt * p11 + q00;
-        KF_T a01 = p01 + dt * p11 + q01;
-        KF_T a11 = p11 + q11;
+        KF_T mp0 = m0 + b * m1;
+        KF_T mp1 = a * m1;
+        KF_T a00 = p00 + b * p01 + b * p01 + b * b * p11 + q00;
+        KF_T a01 = a * (p01 + b * p11) + q01;
+        KF_T a11 = a * a * p11 + q11;
         /* continuous-wave timing residual at this TOA */
         KF_T phase = Om * t[k] + Phi0;
         KF_T s = A * KF_SIN(phase) + B * KF_COS(phase);

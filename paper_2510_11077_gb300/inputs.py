@@ -21,9 +21,11 @@ for a continuous gravitational wave: random per-pulsar amplitude and phase).
 They carry the value distributions of real timing residuals; the likelihood
 does not assume they were drawn from its own model.
 
-Parameter vector layout (D = 7 + 2P):
+Parameter vector layout (D = 7 + 2P for the random-walk red noise):
 ``[log10 f_gw, Phi0, psi, cos iota, sin delta, alpha, log10 h0,
-   (log10 sigma_p, EFAC_p) for p in 0..P-1]``
+   (log10 sigma_p, EFAC_p) for p in 0..P-1]``; with Ornstein-Uhlenbeck red
+noise (model "ou") each pulsar has ``(log10 sigma_p, log10 gamma_p, EFAC_p)``
+and D = 7 + 3P.
 """
 from __future__ import annotations
 
@@ -51,6 +53,15 @@ PRIOR_NOISE = np.array([
     [-21.0, -19.0],          # log10 sigma_p [s^-1/2]
     [0.8, 1.2],              # EFAC
 ])
+PRIOR_NOISE_OU = np.array([
+    [-21.0, -19.0],          # log10 sigma_p [s^-1/2]
+    [-10.0, -7.0],           # log10 gamma_p [s^-1] (mean reversion 0.3 - 300 yr)
+    [0.8, 1.2],              # EFAC
+])
+
+
+def noise_prior(model: str) -> np.ndarray:
+    return PRIOR_NOISE_OU if model == "ou" else PRIOR_NOISE
 
 
 @dataclasses.dataclass
@@ -64,14 +75,19 @@ class ArrayData:
     equad: np.ndarray    # float64 [P], s
     p0: np.ndarray       # float64 [P, 3], prior covariance (rr, ry, yy)
     theta_true: np.ndarray  # float64 [D], parameters used to draw the residuals
+    model: str = "rw"    # red noise: "rw" random walk, "ou" Ornstein-Uhlenbeck
 
     @property
     def n_pulsars(self) -> int:
         return len(self.off) - 1
 
     @property
+    def n_noise(self) -> int:
+        return 3 if self.model == "ou" else 2
+
+    @property
     def dim(self) -> int:
-        return N_GW + 2 * self.n_pulsars
+        return N_GW + self.n_noise * self.n_pulsars
 
     @property
     def n_toa(self) -> np.ndarray:
@@ -119,11 +135,13 @@ def draw_toa_counts(rng: np.random.Generator, n_pulsars: int, law: tuple) -> np.
     raise ValueError(f"unknown TOA-count law {law!r}")
 
 
-def draw_prior(rng: np.random.Generator, n_pulsars: int, n: int) -> np.ndarray:
+def draw_prior(rng: np.random.Generator, n_pulsars: int, n: int, model: str = "rw") -> np.ndarray:
     """n parameter vectors drawn uniformly from the prior box, float64 [n, D]."""
+    pr = noise_prior(model)
+    k = len(pr)
     gw = PRIOR_GW[:, 0] + (PRIOR_GW[:, 1] - PRIOR_GW[:, 0]) * rng.random((n, N_GW))
-    nz = PRIOR_NOISE[:, 0] + (PRIOR_NOISE[:, 1] - PRIOR_NOISE[:, 0]) * rng.random((n, n_pulsars, 2))
-    return np.concatenate([gw, nz.reshape(n, 2 * n_pulsars)], axis=1)
+    nz = pr[:, 0] + (pr[:, 1] - pr[:, 0]) * rng.random((n, n_pulsars, k))
+    return np.concatenate([gw, nz.reshape(n, k * n_pulsars)], axis=1)
 
 
 def isotropic_positions(rng: np.random.Generator, n: int) -> np.ndarray:
@@ -134,12 +152,13 @@ def isotropic_positions(rng: np.random.Generator, n: int) -> np.ndarray:
 
 
 def make_array(n_toa: np.ndarray, seed: int, with_signal: bool = True,
-               t_obs: float = T_OBS, equad: float = 0.0) -> ArrayData:
+               t_obs: float = T_OBS, equad: float = 0.0, model: str = "rw") -> ArrayData:
     """Draw TOAs, errors, positions, a true parameter vector and residuals."""
     rng = np.random.Generator(np.random.PCG64(seed))
     n_toa = np.asarray(n_toa, dtype=np.int64)
     P = len(n_toa)
-    theta = draw_prior(rng, P, 1)[0]
+    theta = draw_prior(rng, P, 1, model)[0]
+    k = 3 if model == "ou" else 2
     if not with_signal:
         theta[6] = -30.0   # negligible strain
     pos = isotropic_positions(rng, P)
@@ -154,11 +173,21 @@ def make_array(n_toa: np.ndarray, seed: int, with_signal: bool = True,
         tp = np.sort(rng.uniform(0.0, t_obs, n))
         if n == 0:
             continue
-        log10_sig, efac = theta[7 + 2 * p], theta[8 + 2 * p]
+        log10_sig, efac = theta[7 + k * p], theta[7 + k * p + k - 1]
         sp = 10.0 ** log10_sig
-        # integrated random walk of the fractional frequency y
         dt = np.diff(tp, prepend=tp[0])
-        y = np.sqrt(P0_DEFAULT[2]) * rng.standard_normal() + np.cumsum(sp * np.sqrt(dt) * rng.standard_normal(n))
+        if model == "ou":
+            # Ornstein-Uhlenbeck fractional frequency, exact AR(1) steps
+            gam = 10.0 ** theta[7 + k * p + 1]
+            z = rng.standard_normal(n)
+            y = np.empty(n)
+            y[0] = np.sqrt(P0_DEFAULT[2]) * rng.standard_normal()
+            for i in range(1, n):
+                decay = np.exp(-gam * dt[i])
+                y[i] = decay * y[i - 1] + sp * np.sqrt(-np.expm1(-2 * gam * dt[i]) / (2 * gam)) * z[i]
+        else:
+            # integrated random walk of the fractional frequency y
+            y = np.sqrt(P0_DEFAULT[2]) * rng.standard_normal() + np.cumsum(sp * np.sqrt(dt) * rng.standard_normal(n))
         y_prev = np.concatenate([[y[0]], y[:-1]])
         rho = np.sqrt(P0_DEFAULT[0]) * rng.standard_normal() + np.cumsum(0.5 * dt * (y + y_prev))
         white = efac * sig[a:b] * rng.standard_normal(n)
@@ -171,7 +200,7 @@ def make_array(n_toa: np.ndarray, seed: int, with_signal: bool = True,
     t -= t.min()
     return ArrayData(off=off, t=t, r=r, sigma=sig, pos=pos,
                      equad=np.full(P, equad), p0=np.tile(np.array(P0_DEFAULT), (P, 1)),
-                     theta_true=theta)
+                     theta_true=theta, model=model)
 
 
 def make_workload_array(name: str) -> ArrayData:
@@ -189,14 +218,15 @@ def make_theta_batch(data: ArrayData, batch: int, seed: int, kind: str = "poster
     """
     rng = np.random.Generator(np.random.PCG64(seed))
     P = data.n_pulsars
+    k = data.n_noise
     if kind == "prior":
-        return draw_prior(rng, P, batch)
+        return draw_prior(rng, P, batch, data.model)
     width = np.concatenate([
         np.array([1e-4, 1e-2, 1e-2, 1e-2, 1e-2, 1e-2, 1e-2]),
-        np.tile(np.array([1e-2, 1e-2]), P)])
+        np.tile(np.full(k, 1e-2), P)])
     th = data.theta_true[None, :] + width[None, :] * rng.standard_normal((batch, data.dim))
     # keep the bounded coordinates inside their domain
     th[:, 3] = np.clip(th[:, 3], -1.0, 1.0)
     th[:, 4] = np.clip(th[:, 4], -0.999, 0.999)
-    th[:, 8::2] = np.abs(th[:, 8::2])
+    th[:, 7 + k - 1::k] = np.abs(th[:, 7 + k - 1::k])
     return th

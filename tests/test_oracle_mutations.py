@@ -22,15 +22,15 @@ from paper_2510_11077_gb300 import inputs
 ORACLE_DIR = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "oracle")
 
 MUTATIONS = {
-    "drop_q01": ("kf_body.h", "KF_T a01 = p01 + dt * p11 + q01;", "KF_T a01 = p01 + dt * p11;"),
+    "drop_q01": ("kf_body.h", "KF_T a01 = a * (p01 + b * p11) + q01;", "KF_T a01 = a * (p01 + b * p11);"),
     "q00_factor": ("kf_body.h", "dt * dt * dt / 3.0", "dt * dt * dt / 2.0"),
     "innovation_sign": ("kf_body.h", "r[k] - s - mp0", "r[k] - s + mp0"),
     "gain_transposed": ("kf_body.h", "K0 = a00 / S, K1 = a01 / S", "K0 = a01 / S, K1 = a00 / S"),
     "p11_index": ("kf_body.h", "p11 = a11 - K1 * S * K1", "p11 = a11 - K0 * S * K1"),
     "p01_index": ("kf_body.h", "p01 = a01 - K0 * S * K1", "p01 = a01 - K0 * S * K0"),
     "drop_log2pi": ("kf_body.h", "KF_LOG2PI + KF_LOG(S)", "KF_LOG(S)"),
-    "mean_predict": ("kf_body.h", "KF_T mp0 = m0 + dt * m1;", "KF_T mp0 = m0;"),
-    "a00_cross_term": ("kf_body.h", "p00 + dt * p01 + dt * p01", "p00 + dt * p01"),
+    "mean_predict": ("kf_body.h", "KF_T mp0 = m0 + b * m1;", "KF_T mp0 = m0;"),
+    "a00_cross_term": ("kf_body.h", "p00 + b * p01 + b * p01", "p00 + b * p01"),
     "efac_not_squared": ("kf_body.h", "efac * efac * (sigma[k] * sigma[k])", "efac * (sigma[k] * sigma[k])"),
     "dt_from_first": ("kf_body.h", "t[k] - t[k - 1]", "t[k] - t[0]"),
     "phase_sign": ("kf_body.h", "Om * t[k] + Phi0", "Om * t[k] - Phi0"),
@@ -41,9 +41,21 @@ MUTATIONS = {
     "q_basis_sign": ("kalman.c", "q[i] = -csin(psi) * u[i]", "q[i] = csin(psi) * u[i]"),
     "v_basis_sign": ("kalman.c", "sind * csin(al), -cosd}", "sind * csin(al), cosd}"),
     "h0_index": ("kalman.c", "cplx h0 = cpow(10.0, th[6]);", "cplx h0 = cpow(10.0, th[5]);"),
-    "noise_grads_swapped": ("kalman.c", "g[N_GW + 2 * p] = cimag(l1) / CS_H;",
-                            "g[N_GW + 2 * p] = cimag(l2) / CS_H;"),
+    "noise_grads_swapped": ("kalman.c", "g[N_GW + np * p + i] = cimag(lp) / CS_H;",
+                            "g[N_GW + np * p + (i + 1) % np] = cimag(lp) / CS_H;"),
     "omega_no_2pi": ("kalman.c", "cplx W = 2.0 * M_PI * f;", "cplx W = M_PI * f;"),
+    # Ornstein-Uhlenbeck red noise
+    "ou_decay_first_order": ("kf_body.h", "a = 1.0 - gam * dt * p1;", "a = 1.0 - gam * dt;"),
+    "ou_q01_phi": ("kf_body.h", "q01 = q01 * p1 * p1;", "q01 = q01 * p1;"),
+    "ou_q11_phi": ("kf_body.h", "q11 = q11 * p2;", "q11 = q11 * p1;"),
+    "ou_a01_no_decay": ("kf_body.h", "KF_T a01 = a * (p01 + b * p11) + q01;", "KF_T a01 = p01 + b * p11 + q01;"),
+    "ou_a11_decay_once": ("kf_body.h", "KF_T a11 = a * a * p11 + q11;", "KF_T a11 = a * p11 + q11;"),
+    "ou_phi4_series": ("kf_body.h", "(2.0 - pow(2.0, m + 2))", "(2.0 - pow(2.0, m + 1))"),
+    "ou_phi1_series_sign": ("kf_body.h", "double c1 = ((m & 1) ? -1.0 : 1.0) / f1;", "double c1 = 1.0 / f1;"),
+    "ou_phi2_closed": ("kf_body.h", "*p2 = (1.0 - e2) / (2.0 * x);", "*p2 = (1.0 - e2) / x;"),
+    "ou_phi4_closed": ("kf_body.h", "0.5 * (1.0 - e2)) / (x * x * x)", "(1.0 - e2)) / (x * x * x)"),
+    "ou_gamma_index": ("kalman.c", "cplx gam = a->ou ? cpow(10.0, nz[1]) : 0.0;",
+                       "cplx gam = a->ou ? cpow(10.0, nz[0]) : 0.0;"),
 }
 
 
@@ -98,6 +110,22 @@ def _pins(lib):
     fd = np.array(fd)
     if not np.all(np.abs(g[0] - fd) <= 1e-4 * np.maximum(np.abs(fd), 1e-3 * np.abs(fd).max())):
         failed.append("fd")
+    # Ornstein-Uhlenbeck red noise: dense likelihood (steps on both sides of
+    # the series / closed-form switch) and the dense gradient
+    rng = np.random.default_rng(3)
+    tt = np.cumsum(np.concatenate([rng.uniform(1e5, 4e6, 25), rng.uniform(5e6, 3e7, 20)]))
+    do = inputs.ArrayData(off=np.array([0, 45]), t=tt, r=1e-6 * rng.standard_normal(45),
+                          sigma=np.full(45, 1e-7), pos=np.array([[0.6, 0.0, 0.8]]),
+                          equad=np.array([1e-8]), p0=np.array([inputs.P0_DEFAULT]),
+                          theta_true=np.zeros(10), model="ou")
+    tho = np.array([-8.3, 0.5, 0.4, 0.2, 0.1, 1.0, -13.5, -19.5, -7.0, 1.05])
+    llo = kalman.loglik(do, tho, lib_path=lib)[0]
+    if not abs(llo - dense.loglik(do, tho)[0]) <= 1e-10 * abs(llo):
+        failed.append("dense_ou")
+    _, go = kalman.loglik_grad(do, tho, lib_path=lib)
+    gd = dense.grad(do, tho)
+    if not np.all(np.abs(go[0] - gd) <= 1e-6 * np.maximum(np.abs(gd), 1e-3 * np.abs(gd).max())):
+        failed.append("grad_ou")
     # antenna pattern: textbook case (source at the pole, pulsar on the equator)
     thp = np.array([-8.0, 0.0, 0.0, 0.5, 1.0, 0.0, -14.0])
     A, B, W, _ = kalman.cw_project(thp, np.array([1.0, 0.0, 0.0]), lib_path=lib)
