@@ -19,10 +19,15 @@
  *   s_p(t) = A sin(W t + Phi0) + B cos(W t + Phi0), the Earth term of a
  *   monochromatic gravitational wave projected on the pulsar direction.
  * ll(theta) = sum_p sum_k -1/2 (ln 2 pi + ln S_k + e_k^2 / S_k).
+ * With Ornstein-Uhlenbeck red noise (ARGUS_NOISE_OU; paper, Functionality:
+ * OU processes for pulsar-intrinsic red noise) the frequency deviation obeys
+ * dy/dt = -gamma_p y + xi(t) instead, with one more parameter per pulsar.
  *
- * Parameter vector theta (D = 7 + 2P doubles, row-major [B][D]):
+ * Parameter vector theta (row-major [B][D]):
  *   [log10 f_gw (Hz), Phi0 (rad), psi (rad), cos iota, sin delta, alpha (rad),
- *    log10 h0, then per pulsar (log10 sigma_p, EFAC_p)].
+ *    log10 h0, then per pulsar (log10 sigma_p, EFAC_p)]  (D = 7 + 2P), or
+ *   per pulsar (log10 sigma_p, log10 gamma_p [1/s], EFAC_p) with
+ *   ARGUS_NOISE_OU (D = 7 + 3P).
  * Out-of-domain vectors (a non-finite entry, EFAC <= 0, |cos iota| > 1,
  * |sin delta| > 1) and filters that meet a non-positive or non-finite
  * innovation variance give loglik = -inf and a zero gradient for that walker;
@@ -85,7 +90,8 @@ typedef struct argus_plan {
     int32_t tape_cache;       /* adjoint: 0 = re-run each segment from its checkpoint (memory
                                  O(sqrt N) per lane); 1 = also keep every segment's tape in HBM
                                  during the forward pass and skip the re-run (memory O(N) per
-                                 lane: 48 B per TOA per resident lane) */
+                                 lane: 48 B per TOA per resident lane, 72 B with
+                                 ARGUS_NOISE_OU) */
     int32_t reserved[2];      /* must be 0 */
 } argus_plan;
 
@@ -98,11 +104,26 @@ typedef struct argus_plan {
 argus_status argus_array_create(const argus_pulsar* pulsars, int32_t n_pulsars, int32_t device,
                                 argus_array** out);
 
+/* Red-noise model of the frequency deviation y. */
+enum { ARGUS_NOISE_RANDOM_WALK = 0, ARGUS_NOISE_OU = 1 };
+
+/* argus_array_create with a choice of red-noise model: ARGUS_NOISE_RANDOM_WALK
+ * (what argus_array_create builds) or ARGUS_NOISE_OU, where over a step dt
+ * the state transition is F = [[1, (1 - e^{-gamma dt})/gamma], [0, e^{-gamma dt}]]
+ * and the process noise the exact covariance of the integrated OU increment.
+ * ARGUS_ERR_INVALID_ARG for any other value; otherwise as argus_array_create. */
+argus_status argus_array_create_ex(const argus_pulsar* pulsars, int32_t n_pulsars, int32_t device,
+                                   int32_t noise_model, argus_array** out);
+
 /* Free everything the handle owns.  NULL is allowed.  Synchronises the device. */
 void argus_array_destroy(argus_array* array);
 
-/* D = 7 + 2P, the length of one parameter vector; -1 for NULL. */
+/* D = 7 + 2P (random walk) or 7 + 3P (OU), the length of one parameter
+ * vector; -1 for NULL. */
 int32_t argus_array_dim(const argus_array* array);
+
+/* The handle's ARGUS_NOISE_* model; -1 for NULL. */
+int32_t argus_array_noise_model(const argus_array* array);
 
 /* Replace / read the scheduling plan.  set_plan validates every field and
  * drops captured graphs; get_plan copies the current plan into *plan. */
@@ -134,7 +155,7 @@ argus_status argus_loglik_grad(argus_array* array, const double* theta, int64_t 
  * loads the library holds until the process exits.
  * theta [B][D], loglik [B] and grad [B][D] must be device memory (otherwise
  * ARGUS_ERR_INVALID_ARG); results equal argus_loglik_grad's.  A batch whose
- * scratch does not fit in 64 MiB (about 112 bytes per walker x pulsar lane,
+ * scratch does not fit in 64 MiB (about 128 bytes per walker x pulsar lane,
  * plus at least one block's checkpoint and tape slot) is rejected with
  * ARGUS_ERR_UNSUPPORTED and a message giving the bytes needed.
  * The first call on a device looks up the array's device address (once per

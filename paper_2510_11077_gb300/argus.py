@@ -20,6 +20,9 @@ from . import build as _build
 
 ARGUS_MODE_BATCHED = 0
 ARGUS_MODE_PLAIN = 1
+ARGUS_NOISE_RANDOM_WALK = 0
+ARGUS_NOISE_OU = 1
+NOISE_MODELS = {"rw": ARGUS_NOISE_RANDOM_WALK, "ou": ARGUS_NOISE_OU}
 STATUS = {0: "ARGUS_OK", 1: "ARGUS_ERR_INVALID_ARG", 2: "ARGUS_ERR_CUDA", 3: "ARGUS_ERR_OOM",
           4: "ARGUS_ERR_NONFINITE", 5: "ARGUS_ERR_TIMEOUT", 6: "ARGUS_ERR_UNSUPPORTED"}
 
@@ -72,6 +75,11 @@ def load(build_if_missing: bool = False):
     lib.argus_array_create.argtypes = [ctypes.POINTER(ArgusPulsar), ctypes.c_int32, ctypes.c_int32,
                                        ctypes.POINTER(vp)]
     lib.argus_array_create.restype = ctypes.c_int
+    lib.argus_array_create_ex.argtypes = [ctypes.POINTER(ArgusPulsar), ctypes.c_int32, ctypes.c_int32,
+                                          ctypes.c_int32, ctypes.POINTER(vp)]
+    lib.argus_array_create_ex.restype = ctypes.c_int
+    lib.argus_array_noise_model.argtypes = [vp]
+    lib.argus_array_noise_model.restype = ctypes.c_int32
     lib.argus_array_destroy.argtypes = [vp]
     lib.argus_array_destroy.restype = None
     lib.argus_array_dim.argtypes = [vp]
@@ -125,10 +133,12 @@ def _stream_of(*tensors):
 
 
 class Array:
-    """Handle of one pulsar array on one device (argus_array_create)."""
+    """Handle of one pulsar array on one device (argus_array_create_ex; the
+    red-noise model is ``data.model``, "rw" or "ou")."""
 
     def __init__(self, data, device: int = 0):
         lib = load()
+        model = NOISE_MODELS[getattr(data, "model", "rw")]
         P = data.n_pulsars
         self._keep = []
         ps = (ArgusPulsar * P)()
@@ -144,11 +154,12 @@ class Array:
             ps[p].equad = float(data.equad[p])
             ps[p].p0[:] = [float(v) for v in data.p0[p]]
         h = ctypes.c_void_p()
-        _check(lib.argus_array_create(ps, P, device, ctypes.byref(h)))
+        _check(lib.argus_array_create_ex(ps, P, device, model, ctypes.byref(h)))
         self._keep = None
         self.handle = h
         self.n_pulsars = P
         self.dim = lib.argus_array_dim(h)
+        self.noise_model = lib.argus_array_noise_model(h)
         self.device = device
 
     def close(self):

@@ -41,9 +41,10 @@ def _source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def plan_key(n_toa, batch: int, grad: bool, gpu_name: str) -> str:
+def plan_key(n_toa, batch: int, grad: bool, gpu_name: str, model: str = "rw") -> str:
     shape = hashlib.sha256(",".join(str(int(n)) for n in n_toa).encode()).hexdigest()[:16]
-    return f"{gpu_name}|P{len(n_toa)}|toa{shape}|B{batch}|{'grad' if grad else 'll'}|src{_source_hash()}"
+    return (f"{gpu_name}|P{len(n_toa)}|toa{shape}|B{batch}|{'grad' if grad else 'll'}|{model}"
+            f"|src{_source_hash()}")
 
 
 def load_cache(path: str = DEFAULT_CACHE) -> dict:
@@ -91,7 +92,8 @@ def autotune(arr, theta, n_toa, grad: bool = True, space: dict | None = None,
     import torch
     space = dict(DEFAULT_SPACE, **(space or {}))
     B = theta.shape[0] if batch_for_key is None else batch_for_key
-    key = plan_key(n_toa, B, grad, torch.cuda.get_device_name(theta.device))
+    model = {v: k for k, v in argus.NOISE_MODELS.items()}[getattr(arr, "noise_model", 0)]
+    key = plan_key(n_toa, B, grad, torch.cuda.get_device_name(theta.device), model)
     cache = load_cache(cache_path) if cache_path else {}
     if key in cache:
         arr.set_plan(**cache[key]["plan"])

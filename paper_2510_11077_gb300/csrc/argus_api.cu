@@ -88,6 +88,8 @@ struct argus_array {
     int device = 0;
     int n_sm = 0;
     int P = 0;
+    int32_t model = kRandomWalk;   // red-noise model (argus.h: ARGUS_NOISE_*)
+    int32_t nq = 2;                // noise parameters per pulsar
     int64_t total_toa = 0;
     int32_t stride_max = 1;   // for the current plan
     int32_t nseg_max = 0;
@@ -221,7 +223,7 @@ argus_status ensure_batch(argus_array* h, int64_t B, int W, int grid, bool grad)
     if (grad) {
         const size_t ck = size_t(h->nseg_max) * kCkptDoubles * W * grid;
         const size_t tp_len = h->plan.tape_cache ? size_t(std::max(h->n_max, 1)) : size_t(h->stride_max);
-        const size_t tp = tp_len * kTapeDoubles * W * grid;
+        const size_t tp = tp_len * tape_doubles(h->model) * W * grid;
         if ((st = grow(&h->d_ckpt, &h->cap_ckpt, std::max<size_t>(ck, 1)))) return st;
         if ((st = grow(&h->d_tape, &h->cap_tape, std::max<size_t>(tp, 1)))) return st;
     }
@@ -244,10 +246,11 @@ FilterArgs make_args(argus_array* h, int64_t B, int W, int grid, bool persistent
     a.tape = h->d_tape;
     a.ckpt_slot = int64_t(h->nseg_max) * kCkptDoubles * W;
     const int64_t tp_len = h->plan.tape_cache ? std::max(h->n_max, 1) : h->stride_max;
-    a.tape_slot = tp_len * kTapeDoubles * W;
+    a.tape_slot = tp_len * tape_doubles(h->model) * W;
     a.stride_max = h->stride_max;
     a.tape_cache = h->plan.tape_cache;
     a.counter = persistent ? h->d_counter : nullptr;
+    a.model = h->model;
     (void)grid;
     return a;
 }
@@ -260,13 +263,13 @@ argus_status enqueue_batched(argus_array* h, const double* theta, int64_t B, dou
     const int grid = grid_for(h, h->n_items);
     CK(cudaMemsetAsync(h->d_counter, 0, sizeof(int), s));
     if (h->timing) CK(cudaEventRecordWithFlags(h->ev[0], s, cudaEventRecordExternal));
-    launch_project(theta, B, h->P, h->d_psr, h->d_lc, s);
+    launch_project(theta, B, h->P, h->model, h->d_psr, h->d_lc, s);
     if (h->timing) CK(cudaEventRecordWithFlags(h->ev[1], s, cudaEventRecordExternal));
     FilterArgs a = make_args(h, B, W, grid, true);
     if (want_grad) launch_filter_grad(a, W, grid, s);
     else launch_filter_fwd(a, W, grid, s);
     if (h->timing) CK(cudaEventRecordWithFlags(h->ev[2], s, cudaEventRecordExternal));
-    launch_reduce(theta, B, h->P, h->d_psr, h->d_lane, ll, grad, lane, s);
+    launch_reduce(theta, B, h->P, h->model, h->d_psr, h->d_lane, ll, grad, lane, s);
     if (h->timing) {
         CK(cudaEventRecordWithFlags(h->ev[3], s, cudaEventRecordExternal));
         h->timed_once = true;
@@ -322,7 +325,7 @@ argus_status run_batched(argus_array* h, const double* theta, int64_t B, double*
 argus_status run_plain(argus_array* h, const double* theta, int64_t B, double* ll, double* grad,
                        double* lane, cudaStream_t s) {
     const int W = 32;
-    const int D = kNgw + 2 * h->P;
+    const int D = kNgw + h->nq * h->P;
     argus_status st;
     if ((st = ensure_items(h, 1, W))) return st;
     const int grid = h->n_items;
@@ -330,10 +333,10 @@ argus_status run_plain(argus_array* h, const double* theta, int64_t B, double* l
     FilterArgs a = make_args(h, 1, W, grid, false);
     for (int64_t b = 0; b < B; ++b) {
         const double* th = theta + b * D;
-        launch_project(th, 1, h->P, h->d_psr, h->d_lc, s);
+        launch_project(th, 1, h->P, h->model, h->d_psr, h->d_lc, s);
         if (grad) launch_filter_grad(a, W, grid, s);
         else launch_filter_fwd(a, W, grid, s);
-        launch_reduce(th, 1, h->P, h->d_psr, h->d_lane, ll ? ll + b : nullptr,
+        launch_reduce(th, 1, h->P, h->model, h->d_psr, h->d_lane, ll ? ll + b : nullptr,
                       grad ? grad + b * D : nullptr, lane ? lane + b * h->P : nullptr, s);
     }
     CK(cudaGetLastError());
@@ -361,7 +364,7 @@ argus_status evaluate(argus_array* h, const double* theta, int64_t B, double* ll
         return fail(ARGUS_ERR_UNSUPPORTED, "B x P exceeds 2^31 lanes");
     DeviceGuard guard(h->device);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    const int D = kNgw + 2 * h->P;
+    const int D = kNgw + h->nq * h->P;
     const bool dev_in = is_device_ptr(theta);
     const bool dev_ll = is_device_ptr(ll), dev_g = is_device_ptr(grad), dev_l = is_device_ptr(lane);
     const bool staged = !(dev_in && dev_ll && dev_g && dev_l);
@@ -405,7 +408,14 @@ extern "C" {
 
 argus_status argus_array_create(const argus_pulsar* psrs, int32_t n_pulsars, int32_t device,
                                 argus_array** out) {
+    return argus_array_create_ex(psrs, n_pulsars, device, ARGUS_NOISE_RANDOM_WALK, out);
+}
+
+argus_status argus_array_create_ex(const argus_pulsar* psrs, int32_t n_pulsars, int32_t device,
+                                   int32_t noise_model, argus_array** out) {
     if (!out) return fail(ARGUS_ERR_INVALID_ARG, "out is NULL");
+    if (noise_model != ARGUS_NOISE_RANDOM_WALK && noise_model != ARGUS_NOISE_OU)
+        return fail(ARGUS_ERR_INVALID_ARG, "noise_model must be ARGUS_NOISE_RANDOM_WALK or ARGUS_NOISE_OU");
     if (!psrs || n_pulsars < 1) return fail(ARGUS_ERR_INVALID_ARG, "need at least one pulsar");
     if (device < 0) return fail(ARGUS_ERR_INVALID_ARG, "device must be >= 0");
     int64_t total = 0;
@@ -458,6 +468,8 @@ argus_status argus_array_create(const argus_pulsar* psrs, int32_t n_pulsars, int
     h->device = device;
     h->n_sm = prop.multiProcessorCount;
     h->P = n_pulsars;
+    h->model = noise_model == ARGUS_NOISE_OU ? kOrnsteinUhlenbeck : kRandomWalk;
+    h->nq = noise_params(h->model);
     h->total_toa = total;
     h->plan = default_plan();
     h->h_psr.resize(n_pulsars);
@@ -529,7 +541,12 @@ void argus_array_destroy(argus_array* h) {
     delete h;
 }
 
-int32_t argus_array_dim(const argus_array* h) { return h ? kNgw + 2 * h->P : -1; }
+int32_t argus_array_dim(const argus_array* h) { return h ? kNgw + h->nq * h->P : -1; }
+
+int32_t argus_array_noise_model(const argus_array* h) {
+    if (!h) return -1;
+    return h->model == kOrnsteinUhlenbeck ? ARGUS_NOISE_OU : ARGUS_NOISE_RANDOM_WALK;
+}
 
 argus_status argus_array_set_plan(argus_array* h, const argus_plan* plan) {
     if (!h) return fail(ARGUS_ERR_INVALID_ARG, "array handle is NULL");
@@ -698,7 +715,7 @@ extern "C" argus_status argus_loglik_grad_noalloc(argus_array* h, const double* 
     const size_t off_lane = off_lc + align256(lanes * kLaneConsts * sizeof(double));
     const size_t off_slots = off_lane + align256(lanes * (1 + kLaneGrads) * sizeof(double));
     const size_t ck_slot = size_t(h->nseg_max) * kCkptDoubles * W;     // doubles
-    const size_t tp_slot = size_t(h->stride_max) * kTapeDoubles * W;   // doubles
+    const size_t tp_slot = size_t(h->stride_max) * tape_doubles(h->model) * W;   // doubles
     const size_t slot_bytes = align256(ck_slot * sizeof(double)) + align256(tp_slot * sizeof(double));
     if (off_slots + slot_bytes > kNoAllocBytes) {
         char buf[200];
@@ -722,7 +739,7 @@ extern "C" argus_status argus_loglik_grad_noalloc(argus_array* h, const double* 
     // the work counter must start at zero; everything else is written before it is read
     CK(cudaMemsetAsync(counter, 0, sizeof(int), s));
     k_noalloc_items<<<(n_items + 255) / 256, 256, 0, s>>>(items, n_items, tiles, W);
-    launch_project(theta, B, h->P, h->d_psr, lc, s);
+    launch_project(theta, B, h->P, h->model, h->d_psr, lc, s);
     FilterArgs a{};
     a.rec = h->d_rec;
     a.psr = h->d_psr;
@@ -738,8 +755,9 @@ extern "C" argus_status argus_loglik_grad_noalloc(argus_array* h, const double* 
     a.tape_slot = int64_t(align256(tp_slot * sizeof(double)) / sizeof(double));
     a.stride_max = h->stride_max;
     a.counter = counter;
+    a.model = h->model;
     launch_filter_grad(a, W, grid, s);
-    launch_reduce(theta, B, h->P, h->d_psr, lane, loglik, grad, nullptr, s);
+    launch_reduce(theta, B, h->P, h->model, h->d_psr, lane, loglik, grad, nullptr, s);
     CK(cudaGetLastError());
     return ARGUS_OK;
 }

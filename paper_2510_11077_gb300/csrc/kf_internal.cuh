@@ -10,9 +10,19 @@ constexpr int kNgw = 7;          // continuous-wave parameters at the head of th
 constexpr int kRecDoubles = 8;   // doubles per staged TOA record
 constexpr int kCkptDoubles = 5;  // (m0, m1, p00, p01, p11) per checkpoint
 constexpr int kTapeDoubles = 6;  // (R/S, K1, 1/S, e, sin, cos) per step of a segment
+constexpr int kTapeDoublesOU = 9; // ... plus (m1, p01 + b p11, p11) before the step
 constexpr int kMaxStride = 256;  // longest adjoint segment, in TOAs
-constexpr int kLaneConsts = 7;   // A, B, f, Phi0/(2 pi), sigma^2, EFAC^2, EFAC
-constexpr int kLaneGrads = 6;    // dll/dA, dB, t-weighted sin and cos sums, dsigma^2, EFAC term
+constexpr int kLaneConsts = 8;   // A, B, f, Phi0/(2 pi), sigma^2, EFAC^2, EFAC, gamma
+constexpr int kLaneGrads = 7;    // dll/dA, dB, t-weighted sin and cos sums, dsigma^2, EFAC term,
+                                 // dll/dgamma
+
+// Red-noise model of the frequency deviation y (argus.h: ARGUS_NOISE_*).
+enum NoiseModel : int32_t { kRandomWalk = 0, kOrnsteinUhlenbeck = 1 };
+
+inline int noise_params(int32_t model) { return model == kOrnsteinUhlenbeck ? 3 : 2; }
+inline int tape_doubles(int32_t model) {
+    return model == kOrnsteinUhlenbeck ? kTapeDoublesOU : kTapeDoubles;
+}
 
 // One staged TOA record (8 doubles = 64 bytes, 16-byte aligned):
 //   [0] t  [1] dt  [2] dt^2/2  [3] dt^3/3  [4] r  [5] sigma^2  [6] dt^2  [7] 2 dt
@@ -40,7 +50,7 @@ struct FilterArgs {
     int32_t P;
     int64_t B;
     const double* lc;         // lane constants [7][P][B]
-    double* lane_out;         // [1 + 6][P][B]: ll, then the gradient terms
+    double* lane_out;         // [1 + 7][P][B]: ll, then the gradient terms
     double* ckpt;             // per block slot: [nseg_max][5][W]
     double* tape;             // per block slot: [stride_max or N_max][6][W]
     int64_t ckpt_slot;        // doubles per block slot in ckpt
@@ -48,17 +58,19 @@ struct FilterArgs {
     int32_t stride_max;       // longest segment of any pulsar (shared-memory records)
     int32_t tape_cache;       // 1: tape slot holds every segment of the pulsar (no re-run)
     int* counter;             // persistent work counter (nullptr: one item per block)
+    int32_t model;            // NoiseModel
+    int32_t pad;
 };
 
-// K1: theta [B][D] -> lane constants [7][P][B].
-void launch_project(const double* theta, int64_t B, int32_t P, const PulsarDev* psr,
+// K1: theta [B][D] -> lane constants [8][P][B].
+void launch_project(const double* theta, int64_t B, int32_t P, int32_t model, const PulsarDev* psr,
                     double* lc, cudaStream_t s);
 // K2: forward filter, ll per lane -> lane_out[0][P][B].
 void launch_filter_fwd(const FilterArgs& a, int W, int grid, cudaStream_t s);
-// K3: forward with checkpoints + reverse sweep -> lane_out[0..6][P][B].
+// K3: forward with checkpoints + reverse sweep -> lane_out[0..7][P][B].
 void launch_filter_grad(const FilterArgs& a, int W, int grid, cudaStream_t s);
 // K4: deterministic sum over pulsars (and chain rule through K1 for grad).
-void launch_reduce(const double* theta, int64_t B, int32_t P, const PulsarDev* psr,
+void launch_reduce(const double* theta, int64_t B, int32_t P, int32_t model, const PulsarDev* psr,
                    const double* lane_out, double* loglik, double* grad, double* lane_ll,
                    cudaStream_t s);
 // The model's continuous-wave residual at every TOA for one theta_gw [7] (device).

@@ -106,26 +106,28 @@ __device__ void antenna(const SourceFrame& F, const double* c, bool with_derivs,
     }
 }
 
-__device__ __forceinline__ bool theta_in_domain(const double* th, int P) {
-    const int D = kNgw + 2 * P;
+// nq noise parameters per pulsar: (log10 sigma, EFAC) or (log10 sigma, log10 gamma, EFAC)
+__device__ __forceinline__ bool theta_in_domain(const double* th, int P, int nq) {
+    const int D = kNgw + nq * P;
     bool ok = true;
     for (int j = 0; j < D; ++j) ok = ok && isfinite(th[j]);
     ok = ok && fabs(th[3]) <= 1.0 && fabs(th[4]) <= 1.0;
-    for (int p = 0; p < P; ++p) ok = ok && th[kNgw + 2 * p + 1] > 0.0;
+    for (int p = 0; p < P; ++p) ok = ok && th[kNgw + nq * p + nq - 1] > 0.0;
     return ok;
 }
 
 // ---------------------------------------------------------------------------
-// K1: lane constants.  lc[k][p][b], k = A, B, f, Phi0/(2 pi), sigma^2, EFAC^2, EFAC
+// K1: lane constants.  lc[k][p][b], k = A, B, f, Phi0/(2 pi), sigma^2, EFAC^2,
+// EFAC, gamma (the last only for Ornstein-Uhlenbeck red noise)
 // ---------------------------------------------------------------------------
-__global__ void k_project(const double* __restrict__ theta, int64_t B, int32_t P,
+__global__ void k_project(const double* __restrict__ theta, int64_t B, int32_t P, int32_t nq,
                           const PulsarDev* __restrict__ psr, double* __restrict__ lc) {
     const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     const int64_t lanes = B * P;
     if (idx >= lanes) return;
     const int p = int(idx / B);
     const int64_t b = idx - int64_t(p) * B;
-    const int D = kNgw + 2 * P;
+    const int D = kNgw + nq * P;
     const double* th = theta + b * D;
     double thg[kNgw];
     for (int j = 0; j < kNgw; ++j) thg[j] = th[j];
@@ -133,8 +135,9 @@ __global__ void k_project(const double* __restrict__ theta, int64_t B, int32_t P
     source_frame(thg, false, F);
     Antenna R;
     antenna(F, psr[p].pos, false, R);
-    const double efac = th[kNgw + 2 * p + 1];
-    const double sig2 = exp10(2.0 * th[kNgw + 2 * p]);
+    const double* nz = th + kNgw + nq * p;
+    const double efac = nz[nq - 1];
+    const double sig2 = exp10(2.0 * nz[0]);
     double* o = lc + idx;
     o[0 * lanes] = R.Fp * F.ampP;
     o[1 * lanes] = R.Fx * F.ampX;
@@ -143,6 +146,7 @@ __global__ void k_project(const double* __restrict__ theta, int64_t B, int32_t P
     o[4 * lanes] = sig2;
     o[5 * lanes] = efac * efac;
     o[6 * lanes] = efac;
+    if (nq == 3) o[7 * lanes] = exp10(nz[1]);
 }
 
 // ---------------------------------------------------------------------------
@@ -156,7 +160,7 @@ __global__ void k_project(const double* __restrict__ theta, int64_t B, int32_t P
 // log-determinant is a running mantissa product (LogProd).
 // ---------------------------------------------------------------------------
 struct Lane {
-    double A, B, f, phc, sig2, efac2, equad2;
+    double A, B, f, phc, sig2, efac2, equad2, gam;
 };
 
 struct State {
@@ -165,20 +169,110 @@ struct State {
 
 struct StepOut {   // what the adjoint needs from the forward step (w = R/S = 1 - K0)
     double w, K1, rS, e, sn, cs;
+    double m1, t1, p11;   // Ornstein-Uhlenbeck only: m1, p01 + b p11 and p11 before the step
 };
 
-// kTape: produce what the adjoint needs; kLL: accumulate the log-likelihood.
-template <bool kTape, bool kLL>
+// ---------------------------------------------------------------------------
+// Ornstein-Uhlenbeck red noise, dy = -gamma y dt + sigma dW.  Over one step,
+// with x = gamma dt:
+//   F = [[1, b], [0, a]],  a = e^-x,  b = dt psi1(x),
+//   Q / sigma^2 = [[dt^3/3 phi4(x), dt^2/2 psi1(x)^2], [., dt psi1(2x)]],
+// where psi_k(x) = sum_m (-x)^m / (m + k)! are the exponential-integrator
+// phi-functions at -x (psi_{k-1} = 1/(k-1)! - x psi_k), so that
+//   psi1(2x) = psi1 (1 - x psi1 / 2),   phi4 = 3 (psi2 - psi3 - x psi2^2 / 2),
+// and their x-derivatives, for the adjoint, follow from psi_k' = k psi_{k+1} - psi_k:
+//   a' = -a,  psi1' = psi2 - psi1,  psi1(2x)' = a (psi2 - psi1) - psi1^2 / 2,
+//   phi4' = 3 ((2 psi3 - psi2)(1 - x psi2) - (3 psi4 - psi3) - psi2^2 / 2).
+// Below x = 0.5 psi4 is its Taylor series, cut where the next term falls
+// below 2^-56 of the sum (7, 10 or 14 terms for x below 1/64, 1/8, 1/2), and
+// psi3, psi2, psi1, a follow by the recurrence without cancellation.  Above,
+// a = exp(-x) and closed forms with u = 1 - a:
+//   psi1 = u / x,  psi2 = (1 - psi1) / x,  phi4 = 3 (x - u (1 + u/2)) / x^3,
+//   phi4' = 3 u^2 / x^3 - 3 phi4 / x.
+// As gamma -> 0 every factor tends to the random walk's (a = 1, b = dt,
+// Q = sigma^2 [[dt^3/3, dt^2/2], [., dt]]).
+// ---------------------------------------------------------------------------
+struct OuCoef {
+    double a, b, c00, c01, c11;        // F entries and Q / sigma^2
+    double da, db, dc00, dc01, dc11;   // their derivatives in x (with kDeriv)
+};
+
+constexpr double factorial(int n) { return n <= 1 ? 1.0 : double(n) * factorial(n - 1); }
+constexpr double psi4_coef(int m) { return ((m & 1) ? -1.0 : 1.0) / factorial(m + 4); }
+
+template <int N>
+__device__ __forceinline__ double psi4_series(double x) {
+    double s = psi4_coef(N - 1);
+#pragma unroll
+    for (int m = N - 2; m >= 0; --m) s = fma(s, x, psi4_coef(m));
+    return s;
+}
+
+template <bool kDeriv>
+__device__ __forceinline__ void ou_coef(double x, double dt, double h2, double h3, OuCoef& c) {
+    double p1, p2, phi4, dphi4 = 0.0;
+    if (x < 0.5) {
+        double p4;
+        if (x < 0.015625) p4 = psi4_series<7>(x);
+        else if (x < 0.125) p4 = psi4_series<10>(x);
+        else p4 = psi4_series<14>(x);
+        const double p3 = fma(-x, p4, 1.0 / 6.0);
+        p2 = fma(-x, p3, 0.5);
+        p1 = fma(-x, p2, 1.0);
+        c.a = fma(-x, p1, 1.0);
+        phi4 = 3.0 * fma(-0.5 * x * p2, p2, p2 - p3);
+        if (kDeriv)
+            dphi4 = 3.0 * fma(-0.5 * p2, p2, fma(2.0 * p3 - p2, fma(-x, p2, 1.0), fma(-3.0, p4, p3)));
+    } else {
+        c.a = exp(-x);
+        const double r = 1.0 / x;
+        const double u = 1.0 - c.a;
+        p1 = u * r;
+        p2 = (1.0 - p1) * r;
+        phi4 = 3.0 * (x - u * fma(0.5, u, 1.0)) * (r * r * r);
+        if (kDeriv) dphi4 = 3.0 * r * fma(u * u, r * r, -phi4);
+    }
+    c.b = dt * p1;
+    c.c00 = h3 * phi4;
+    c.c01 = h2 * (p1 * p1);
+    c.c11 = dt * (p1 * fma(-0.5 * x, p1, 1.0));
+    if (kDeriv) {
+        const double dp1 = p2 - p1;
+        c.da = -c.a;
+        c.db = dt * dp1;
+        c.dc00 = h3 * dphi4;
+        c.dc01 = h2 * (2.0 * p1 * dp1);
+        c.dc11 = dt * fma(c.a, dp1, -0.5 * p1 * p1);
+    }
+}
+
+// kTape: produce what the adjoint needs; kLL: accumulate the log-likelihood;
+// kOU: Ornstein-Uhlenbeck red noise (else the random walk).
+template <bool kTape, bool kLL, bool kOU>
 __device__ __forceinline__ void kf_step(State& x, const double* __restrict__ rec, const Lane& L,
                                         PhaseTable tab, double& quad, LogProd& lp,
                                         StepOut& so) {
     const double t = rec[0], dt = rec[1], h2 = rec[2], h3 = rec[3], r = rec[4], s2k = rec[5];
     // predict
-    const double m0 = fma(dt, x.m1, x.m0);
-    const double t1 = fma(dt, x.p11, x.p01);
-    const double M00 = fma(L.sig2, h3, fma(dt, x.p01 + t1, x.p00));
-    const double M01 = fma(L.sig2, h2, t1);
-    const double M11 = fma(L.sig2, dt, x.p11);
+    double m0, mp1, t1, M00, M01, M11;
+    if (kOU) {
+        OuCoef c;
+        ou_coef<false>(L.gam * dt, dt, h2, h3, c);
+        m0 = fma(c.b, x.m1, x.m0);
+        mp1 = c.a * x.m1;
+        t1 = fma(c.b, x.p11, x.p01);
+        M00 = fma(L.sig2, c.c00, fma(c.b, x.p01 + t1, x.p00));
+        M01 = fma(L.sig2, c.c01, c.a * t1);
+        M11 = fma(L.sig2, c.c11, c.a * c.a * x.p11);
+        if (kTape) { so.m1 = x.m1; so.t1 = t1; so.p11 = x.p11; }
+    } else {
+        m0 = fma(dt, x.m1, x.m0);
+        mp1 = x.m1;
+        t1 = fma(dt, x.p11, x.p01);
+        M00 = fma(L.sig2, h3, fma(dt, x.p01 + t1, x.p00));
+        M01 = fma(L.sig2, h2, t1);
+        M11 = fma(L.sig2, dt, x.p11);
+    }
     // signal at phase f t + Phi0/(2 pi) cycles
     double sn, cs;
     phase_sincos(fma(L.f, t, L.phc), tab, sn, cs);
@@ -193,7 +287,7 @@ __device__ __forceinline__ void kf_step(State& x, const double* __restrict__ rec
     const double K1 = M01 * rS;
     // update
     x.m0 = fma(M00, g, m0);
-    x.m1 = fma(M01, g, x.m1);
+    x.m1 = fma(M01, g, mp1);
     x.p00 = M00 * w;
     x.p01 = M01 * w;
     x.p11 = fma(-K1, M01, M11);
@@ -211,17 +305,20 @@ struct Adjoint {
 };
 
 // Per-lane gradient accumulators: dll/dA, dll/dB, sum sbar t sin, sum sbar t
-// cos, dll/dsigma^2, and sum Sbar sigma_k^2 (= dll/dEFAC / (2 EFAC)).  The
-// Phi0 and Omega derivatives follow as A gB - B gA and A gBt - B gAt.
+// cos, dll/dsigma^2, sum Sbar sigma_k^2 (= dll/dEFAC / (2 EFAC)) and, for
+// Ornstein-Uhlenbeck red noise, dll/dgamma.  The Phi0 and Omega derivatives
+// follow as A gB - B gA and A gBt - B gAt.
 struct LaneGrad {
-    double A, B, At, Bt, s2, E;
+    double A, B, At, Bt, s2, E, G;
 };
 
 // Reverse of kf_step: consumes the adjoint of the step's output state and the
 // step's own loglik term, produces the adjoint of its input state and adds the
 // step's contribution to the lane gradient.
+template <bool kOU>
 __device__ __forceinline__ void kf_step_adjoint(Adjoint& a, const StepOut& so,
-                                                const double* __restrict__ rec, LaneGrad& g) {
+                                                const double* __restrict__ rec, const Lane& L,
+                                                LaneGrad& g) {
     const double t = rec[0], dt = rec[1], h2 = rec[2], h3 = rec[3], s2k = rec[5], dt2 = rec[6];
     const double twodt = rec[7];
     // K0 = M00/S = 1 - w
@@ -236,7 +333,6 @@ __device__ __forceinline__ void kf_step_adjoint(Adjoint& a, const StepOut& so,
     const double M00b = fma(a.mu0, gg, fma(a.pi00, fma(2.0, w, -1.0), fma(-a.pi01, K1, Sbar)));
     const double M01b = fma(a.mu1, gg, fma(a.pi01, w, -2.0 * v));
     const double M11b = a.pi11;
-    g.s2 = fma(M00b, h3, fma(M01b, h2, fma(M11b, dt, g.s2)));
     g.E = fma(Sbar, s2k, g.E);
     // dL/ds_k = -ebar
     g.A = fma(-ebar, so.sn, g.A);
@@ -245,13 +341,46 @@ __device__ __forceinline__ void kf_step_adjoint(Adjoint& a, const StepOut& so,
     g.At = fma(st, so.sn, g.At);
     g.Bt = fma(st, so.cs, g.Bt);
     // back through the prediction m = F m, M = F P F^T + Q
-    a.mu0 = a0;
-    a.mu1 = fma(dt, a0, a.mu1);
-    a.pi00 = M00b;
-    a.pi01 = fma(twodt, M00b, M01b);
-    a.pi11 = fma(dt2, M00b, fma(dt, M01b, M11b));
+    if (kOU) {
+        OuCoef c;
+        ou_coef<true>(L.gam * dt, dt, h2, h3, c);
+        g.s2 = fma(M00b, c.c00, fma(M01b, c.c01, fma(M11b, c.c11, g.s2)));
+        // adjoints of a and b, then d/dgamma = dt d/dx
+        const double abar = fma(a.mu1, so.m1, fma(M01b, so.t1, 2.0 * c.a * M11b * so.p11));
+        const double bbar = fma(a0, so.m1, fma(2.0 * M00b, so.t1, c.a * M01b * so.p11));
+        const double qx = fma(M00b, c.dc00, fma(M01b, c.dc01, M11b * c.dc11));
+        g.G = fma(dt, fma(abar, c.da, fma(bbar, c.db, L.sig2 * qx)), g.G);
+        a.mu0 = a0;
+        a.mu1 = fma(c.b, a0, c.a * a.mu1);
+        a.pi00 = M00b;
+        a.pi01 = fma(2.0 * c.b, M00b, c.a * M01b);
+        a.pi11 = fma(c.b * c.b, M00b, c.a * fma(c.b, M01b, c.a * M11b));
+    } else {
+        g.s2 = fma(M00b, h3, fma(M01b, h2, fma(M11b, dt, g.s2)));
+        a.mu0 = a0;
+        a.mu1 = fma(dt, a0, a.mu1);
+        a.pi00 = M00b;
+        a.pi01 = fma(twodt, M00b, M01b);
+        a.pi11 = fma(dt2, M00b, fma(dt, M01b, M11b));
+    }
 }
 
+// One step's tape record, field-major within the step: [field][W].
+template <bool kOU>
+__device__ __forceinline__ void tape_put(double* tk, int W, const StepOut& so) {
+    tk[0 * W] = so.w; tk[1 * W] = so.K1; tk[2 * W] = so.rS;
+    tk[3 * W] = so.e; tk[4 * W] = so.sn; tk[5 * W] = so.cs;
+    if (kOU) { tk[6 * W] = so.m1; tk[7 * W] = so.t1; tk[8 * W] = so.p11; }
+}
+
+template <bool kOU>
+__device__ __forceinline__ StepOut tape_get(const double* tk, int W) {
+    StepOut so{tk[0 * W], tk[1 * W], tk[2 * W], tk[3 * W], tk[4 * W], tk[5 * W], 0.0, 0.0, 0.0};
+    if (kOU) { so.m1 = tk[6 * W]; so.t1 = tk[7 * W]; so.p11 = tk[8 * W]; }
+    return so;
+}
+
+template <bool kOU>
 __device__ __forceinline__ void load_lane(const FilterArgs& a, int p, int64_t b, double equad2,
                                           Lane& L) {
     const int64_t lanes = a.B * a.P;
@@ -263,6 +392,7 @@ __device__ __forceinline__ void load_lane(const FilterArgs& a, int p, int64_t b,
     L.sig2 = o[4 * lanes];
     L.efac2 = o[5 * lanes];
     L.equad2 = equad2;
+    L.gam = kOU ? o[7 * lanes] : 0.0;
 }
 
 // Cooperative copy of `cnt` records into shared memory (16-byte vector loads).
@@ -305,6 +435,7 @@ __device__ __forceinline__ FilterSmem filter_smem() {
 // ---------------------------------------------------------------------------
 // K2: forward filter, one lane per thread.
 // ---------------------------------------------------------------------------
+template <bool kOU>
 __global__ void __launch_bounds__(256) k_filter_fwd(FilterArgs a) {
     const FilterSmem sm = filter_smem();
     __shared__ int s_item;
@@ -319,7 +450,7 @@ __global__ void __launch_bounds__(256) k_filter_fwd(FilterArgs a) {
         const bool active = b < a.B;
         Lane L;
         State x{0.0, 0.0, ps.p0[0], ps.p0[1], ps.p0[2]};
-        if (active) load_lane(a, wi.p, b, ps.equad2, L);
+        if (active) load_lane<kOU>(a, wi.p, b, ps.equad2, L);
         double quad = 0.0;
         LogProd lp;
         StepOut so;
@@ -330,7 +461,7 @@ __global__ void __launch_bounds__(256) k_filter_fwd(FilterArgs a) {
             __syncthreads();
             if (active) {
                 for (int k = 0; k < cnt; ++k)
-                    kf_step<false, true>(x, sm.rec + k * kRecDoubles, L, sm.tab, quad, lp, so);
+                    kf_step<false, true, kOU>(x, sm.rec + k * kRecDoubles, L, sm.tab, quad, lp, so);
             }
         }
         if (active) a.lane_out[int64_t(wi.p) * a.B + b] = finish_ll(n, quad, lp);
@@ -350,8 +481,9 @@ __global__ void __launch_bounds__(256) k_filter_fwd(FilterArgs a) {
 // HBM (the slot holds the whole pulsar), so pass 2 skips the re-run: HBM
 // traffic is traded for FP64 work, which is the scarce resource here.
 // ---------------------------------------------------------------------------
-template <bool kCache>
+template <bool kCache, bool kOU>
 __global__ void __launch_bounds__(256) k_filter_grad(FilterArgs a) {
+    constexpr int kTd = kOU ? kTapeDoublesOU : kTapeDoubles;
     const FilterSmem sm = filter_smem();
     __shared__ int s_item;
     const int W = blockDim.x;
@@ -368,7 +500,7 @@ __global__ void __launch_bounds__(256) k_filter_grad(FilterArgs a) {
         const int64_t b = int64_t(wi.b0) + tid;
         const bool active = b < a.B;
         Lane L;
-        if (active) load_lane(a, wi.p, b, ps.equad2, L);
+        if (active) load_lane<kOU>(a, wi.p, b, ps.equad2, L);
         State x{0.0, 0.0, ps.p0[0], ps.p0[1], ps.p0[2]};
         double quad = 0.0;
         LogProd lp;
@@ -383,42 +515,35 @@ __global__ void __launch_bounds__(256) k_filter_grad(FilterArgs a) {
                 double* cp = ck + int64_t(seg) * kCkptDoubles * W;
                 cp[0 * W] = x.m0; cp[1 * W] = x.m1; cp[2 * W] = x.p00; cp[3 * W] = x.p01; cp[4 * W] = x.p11;
                 for (int k = 0; k < cnt; ++k) {
-                    kf_step<kCache, true>(x, sm.rec + k * kRecDoubles, L, sm.tab, quad, lp, so);
-                    if (kCache) {
-                        double* tk = tp + int64_t(k0 + k) * kTapeDoubles * W;
-                        tk[0 * W] = so.w; tk[1 * W] = so.K1; tk[2 * W] = so.rS;
-                        tk[3 * W] = so.e; tk[4 * W] = so.sn; tk[5 * W] = so.cs;
-                    }
+                    kf_step<kCache, true, kOU>(x, sm.rec + k * kRecDoubles, L, sm.tab, quad, lp, so);
+                    if (kCache) tape_put<kOU>(tp + int64_t(k0 + k) * kTd * W, W, so);
                 }
             }
         }
         const double ll = finish_ll(n, quad, lp);
         // pass 2: reverse sweep
         Adjoint adj{0.0, 0.0, 0.0, 0.0, 0.0};
-        LaneGrad g{0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        LaneGrad g{0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
         for (int seg = nseg - 1; seg >= 0; --seg) {
             const int k0 = seg * c, cnt = min(c, n - k0);
             __syncthreads();
             stage_records(sm.rec, a.rec + (ps.off + k0) * kRecDoubles, cnt);
             __syncthreads();
             if (active) {
-                const double* ts = tp + int64_t(kCache ? k0 : 0) * kTapeDoubles * W;
+                const double* ts = tp + int64_t(kCache ? k0 : 0) * kTd * W;
                 if (!kCache) {
                     const double* cp = ck + int64_t(seg) * kCkptDoubles * W;
                     State y{cp[0 * W], cp[1 * W], cp[2 * W], cp[3 * W], cp[4 * W]};
                     double q2 = 0.0;
                     LogProd l2;
                     for (int k = 0; k < cnt; ++k) {
-                        kf_step<true, false>(y, sm.rec + k * kRecDoubles, L, sm.tab, q2, l2, so);
-                        double* tk = tp + int64_t(k) * kTapeDoubles * W;
-                        tk[0 * W] = so.w; tk[1 * W] = so.K1; tk[2 * W] = so.rS;
-                        tk[3 * W] = so.e; tk[4 * W] = so.sn; tk[5 * W] = so.cs;
+                        kf_step<true, false, kOU>(y, sm.rec + k * kRecDoubles, L, sm.tab, q2, l2, so);
+                        tape_put<kOU>(tp + int64_t(k) * kTd * W, W, so);
                     }
                 }
                 for (int k = cnt - 1; k >= 0; --k) {
-                    const double* tk = ts + int64_t(k) * kTapeDoubles * W;
-                    StepOut sk{tk[0 * W], tk[1 * W], tk[2 * W], tk[3 * W], tk[4 * W], tk[5 * W]};
-                    kf_step_adjoint(adj, sk, sm.rec + k * kRecDoubles, g);
+                    const StepOut sk = tape_get<kOU>(ts + int64_t(k) * kTd * W, W);
+                    kf_step_adjoint<kOU>(adj, sk, sm.rec + k * kRecDoubles, L, g);
                 }
             }
         }
@@ -432,6 +557,7 @@ __global__ void __launch_bounds__(256) k_filter_grad(FilterArgs a) {
             o[4 * lanes] = g.Bt;
             o[5 * lanes] = g.s2;
             o[6 * lanes] = g.E;
+            if (kOU) o[7 * lanes] = g.G;
         }
         __syncthreads();
     }
@@ -441,16 +567,16 @@ __global__ void __launch_bounds__(256) k_filter_grad(FilterArgs a) {
 // K4: per walker, fixed-order sum over pulsars; for the gradient, the chain
 // rule through K1 for the 7 source parameters and the two noise terms.
 // ---------------------------------------------------------------------------
-__global__ void k_reduce(const double* __restrict__ theta, int64_t B, int32_t P,
+__global__ void k_reduce(const double* __restrict__ theta, int64_t B, int32_t P, int32_t nq,
                          const PulsarDev* __restrict__ psr, const double* __restrict__ lane_out,
                          double* __restrict__ loglik, double* __restrict__ grad,
                          double* __restrict__ lane_ll) {
     const int64_t b = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (b >= B) return;
-    const int D = kNgw + 2 * P;
+    const int D = kNgw + nq * P;
     const int64_t lanes = B * P;
     const double* th = theta + b * D;
-    const bool ok = theta_in_domain(th, P);
+    const bool ok = theta_in_domain(th, P, nq);
     double ll = 0.0;
     for (int p = 0; p < P; ++p) {
         const double lp = lane_out[int64_t(p) * B + b];
@@ -488,9 +614,11 @@ __global__ void k_reduce(const double* __restrict__ theta, int64_t B, int32_t P,
         gw[4] += fma(gA, R.Fp_x * F.ampP, gB * R.Fx_x * F.ampX);
         gw[5] += fma(gA, R.Fp_a * F.ampP, gB * R.Fx_a * F.ampX);
         gw[6] += gAB * kLn10;
-        const double ls = th[kNgw + 2 * p], efac = th[kNgw + 2 * p + 1];
-        gout[kNgw + 2 * p] = gs2 * 2.0 * kLn10 * exp10(2.0 * ls);
-        gout[kNgw + 2 * p + 1] = gE * 2.0 * efac;
+        const double* nz = th + kNgw + nq * p;
+        double* gz = gout + kNgw + nq * p;
+        gz[0] = gs2 * 2.0 * kLn10 * exp10(2.0 * nz[0]);
+        gz[nq - 1] = gE * 2.0 * nz[nq - 1];
+        if (nq == 3) gz[1] = o[7 * lanes] * kLn10 * exp10(nz[1]);
     }
     for (int j = 0; j < kNgw; ++j) gout[j] = gw[j];
 }
@@ -524,22 +652,30 @@ size_t filter_smem_bytes(bool grad, int stride_max) {
     return kPhaseTableBytes + size_t(recs) * kRecDoubles * sizeof(double);
 }
 
-void launch_project(const double* theta, int64_t B, int32_t P, const PulsarDev* psr, double* lc,
-                    cudaStream_t s) {
+void launch_project(const double* theta, int64_t B, int32_t P, int32_t model, const PulsarDev* psr,
+                    double* lc, cudaStream_t s) {
     const int64_t lanes = B * P;
     const int threads = 128;
     const int64_t blocks = (lanes + threads - 1) / threads;
-    k_project<<<unsigned(blocks), threads, 0, s>>>(theta, B, P, psr, lc);
+    k_project<<<unsigned(blocks), threads, 0, s>>>(theta, B, P, noise_params(model), psr, lc);
 }
 
 void launch_filter_fwd(const FilterArgs& a, int W, int grid, cudaStream_t s) {
-    k_filter_fwd<<<grid, W, filter_smem_bytes(false, 0), s>>>(a);
+    const size_t smem = filter_smem_bytes(false, 0);
+    if (a.model == kOrnsteinUhlenbeck) k_filter_fwd<true><<<grid, W, smem, s>>>(a);
+    else k_filter_fwd<false><<<grid, W, smem, s>>>(a);
 }
 
 void launch_filter_grad(const FilterArgs& a, int W, int grid, cudaStream_t s) {
     const size_t smem = filter_smem_bytes(true, a.stride_max);
-    if (a.tape_cache) k_filter_grad<true><<<grid, W, smem, s>>>(a);
-    else k_filter_grad<false><<<grid, W, smem, s>>>(a);
+    const bool ou = a.model == kOrnsteinUhlenbeck;
+    if (a.tape_cache) {
+        if (ou) k_filter_grad<true, true><<<grid, W, smem, s>>>(a);
+        else k_filter_grad<true, false><<<grid, W, smem, s>>>(a);
+    } else {
+        if (ou) k_filter_grad<false, true><<<grid, W, smem, s>>>(a);
+        else k_filter_grad<false, false><<<grid, W, smem, s>>>(a);
+    }
 }
 
 void launch_cw_signal(const double* theta_gw, int32_t P, const PulsarDev* psr, const double* rec,
@@ -549,13 +685,13 @@ void launch_cw_signal(const double* theta_gw, int32_t P, const PulsarDev* psr, c
     k_cw_signal<<<grid, 128, 0, st>>>(theta_gw, psr, rec, s);
 }
 
-void launch_reduce(const double* theta, int64_t B, int32_t P, const PulsarDev* psr,
+void launch_reduce(const double* theta, int64_t B, int32_t P, int32_t model, const PulsarDev* psr,
                    const double* lane_out, double* loglik, double* grad, double* lane_ll,
                    cudaStream_t s) {
     const int threads = 128;
     const int64_t blocks = (B + threads - 1) / threads;
-    k_reduce<<<unsigned(blocks), threads, 0, s>>>(theta, B, P, psr, lane_out, loglik, grad,
-                                                  lane_ll);
+    k_reduce<<<unsigned(blocks), threads, 0, s>>>(theta, B, P, noise_params(model), psr, lane_out,
+                                                  loglik, grad, lane_ll);
 }
 
 }  // namespace argus

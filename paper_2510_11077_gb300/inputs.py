@@ -203,11 +203,11 @@ def make_array(n_toa: np.ndarray, seed: int, with_signal: bool = True,
                      theta_true=theta, model=model)
 
 
-def make_workload_array(name: str) -> ArrayData:
+def make_workload_array(name: str, model: str = "rw") -> ArrayData:
     w = WORKLOADS[name]
     rng = np.random.Generator(np.random.PCG64(w.seed))
     n_toa = draw_toa_counts(rng, w.n_pulsars, w.toa_law)
-    return make_array(n_toa, w.seed + 1000, with_signal=w.with_signal)
+    return make_array(n_toa, w.seed + 1000, with_signal=w.with_signal, model=model)
 
 
 def make_theta_batch(data: ArrayData, batch: int, seed: int, kind: str = "posterior") -> np.ndarray:

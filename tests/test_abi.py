@@ -88,6 +88,16 @@ def test_create_rejects_bad_input_before_any_device_call(lib, bad):
     assert lib.argus_last_error() != b""
 
 
+def test_create_ex_rejects_unknown_noise_model(lib):
+    data = inputs.make_array(np.array([20, 30]), seed=1)
+    ps, keep = _pulsars(data)
+    h = ctypes.c_void_p()
+    st = lib.argus_array_create_ex(ps, data.n_pulsars, 0, 7, ctypes.byref(h))
+    assert st == 1 and h.value is None
+    assert b"noise_model" in lib.argus_last_error()
+    assert lib.argus_array_noise_model(None) == -1
+
+
 def test_calls_on_null_handle_are_rejected(lib):
     assert lib.argus_loglik(None, None, 1, None, None) == 1
     assert lib.argus_array_set_plan(None, None) == 1
