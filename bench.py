@@ -42,7 +42,15 @@ FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.07e9 / 1e12
 # flops, transcendentals not counted); forward + recompute + adjoint = 3x.
 FLOPS_PER_LANE_STEP_FWD = 40
 FLOPS_PER_LANE_STEP_GRAD = 120
+# With Ornstein-Uhlenbeck red noise the forward step also builds F and Q from
+# gamma dt: 1 mul for x, a 7-term Horner series (6 FMA, the shortest of the
+# kernel's three), 4 FMA of recurrence, 6 flops for phi4, 8 for the
+# coefficients and 4 more in the prediction = 39 flops; 79 per lane-step, and
+# the gradient counted, as above, as 3x the forward.
+FLOPS_PER_LANE_STEP_FWD_OU = 79
+FLOPS_PER_LANE_STEP_GRAD_OU = 3 * FLOPS_PER_LANE_STEP_FWD_OU
 LOGLIK_WORKLOAD = "psr20_toa500-2000_w4096"
+OU_WORKLOAD = "psr20_toa500-2000_w4096"
 L2_FLUSH_BYTES = 256 << 20
 CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -62,6 +70,10 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-loglik", action="store_true",
                     help="skip the loglik-only leg (20 pulsars x 4096 walkers)")
+    ap.add_argument("--no-ou", action="store_true",
+                    help="skip the Ornstein-Uhlenbeck red-noise leg (20 pulsars x 4096 walkers)")
+    ap.add_argument("--noise", choices=["rw", "ou"], default="rw",
+                    help="red-noise model of the main step (rw: random walk; ou: Ornstein-Uhlenbeck)")
     ap.add_argument("--autotune", choices=["cache", "off", "force"], default="cache",
                     help="cache: use the tuned-plan cache, tuning on a miss; force: retune")
     ap.add_argument("--tune-batch", type=int, default=4096)
@@ -163,7 +175,7 @@ def run_reference(args):
     from oracle import kalman
     from paper_2510_11077_gb300 import inputs
     w = inputs.WORKLOADS[args.workload]
-    data = inputs.make_workload_array(w.name)
+    data = inputs.make_workload_array(w.name, model=args.noise)
     theta = inputs.make_theta_batch(data, w.batch, seed=w.seed)
     cores = os.cpu_count() or 1
     kalman.set_threads(cores)
@@ -179,7 +191,8 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": w.name, "pulsars": data.n_pulsars, "toas": int(data.n_toa.sum()),
+            "config": {"workload": w.name + ("" if args.noise == "rw" else " (OU red noise)"),
+                       "pulsars": data.n_pulsars, "toas": int(data.n_toa.sum()),
                        "batch": w.batch, "dim": data.dim,
                        "step": f"{per_step} walkers of the batch per step (bounded CPU sample)"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -233,6 +246,54 @@ def loglik_only(args, dev, local):
                                         f"{lane_steps} lane-steps per launch"}}
 
 
+def ou_leg(args, dev, local):
+    """Loglik + gradient with Ornstein-Uhlenbeck red noise (D = 7 + 3P) on the
+    20-pulsar, 4096-walker array: evals/s, the adjoint kernel timed live and
+    its FP64 roofline."""
+    import torch
+
+    from paper_2510_11077_gb300 import argus, autotune, inputs
+    w = inputs.WORKLOADS[OU_WORKLOAD]
+    data = inputs.make_workload_array(w.name, model="ou")
+    theta = torch.from_numpy(inputs.make_theta_batch(data, w.batch, seed=w.seed)).to(dev)
+    arr = argus.Array(data, device=local)
+    res = autotune.autotune(arr, theta, data.n_toa, grad=True, batch_for_key=w.batch)
+    ll = torch.empty(w.batch, dtype=torch.float64, device=dev)
+    g = torch.empty((w.batch, data.dim), dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    arr.set_timing(True)
+    for _ in range(3):
+        argus.argus_loglik_grad(arr, theta, ll, g)
+    torch.cuda.synchronize(dev)
+    reps = 10
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(reps)]
+    kern = []
+    for k in range(reps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        argus.argus_loglik_grad(arr, theta, ll, g)
+        ev[k][1].record(stream)
+        kern.append(arr.get_timing()[1])
+    torch.cuda.synchronize(dev)
+    step_ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    k_ms = statistics.mean(kern)
+    lane_steps = w.batch * int(data.n_toa.sum())
+    achieved = FLOPS_PER_LANE_STEP_GRAD_OU * lane_steps / (k_ms * 1e-3) / 1e12
+    tr = traffic_record("k_filter_grad_ou")
+    arr.close()
+    return {"workload": w.name + " (Ornstein-Uhlenbeck red noise)", "dim": data.dim,
+            "metric": "loglik+grad evals/s", "value": w.batch / (step_ms * 1e-3),
+            "ms_per_step": step_ms, "plan": res["plan"], "autotune_cached": res["cached"],
+            "roofline": {"bound": "alu", "kernel": "k_filter_grad<OU>", "kernel_ms": k_ms,
+                         "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved / FP64_PEAK_TFLOPS,
+                         "traffic": tr["dram_bytes_per_launch"] if tr else None,
+                         "algorithmic": f"{FLOPS_PER_LANE_STEP_GRAD_OU} FP64 flop per lane-step x "
+                                        f"{lane_steps} lane-steps per launch"}}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -247,7 +308,7 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     w = inputs.WORKLOADS[args.workload]
-    data = inputs.make_workload_array(w.name)
+    data = inputs.make_workload_array(w.name, model=args.noise)
     B, D = w.batch, data.dim
     theta_np = inputs.make_theta_batch(data, B, seed=pdist.rank_seed(w.seed, rank))
     theta = torch.from_numpy(theta_np).to(dev)
@@ -260,7 +321,8 @@ def run_ours(args):
         cache = autotune.DEFAULT_CACHE
         if args.autotune == "force" and os.path.exists(cache):
             c = autotune.load_cache(cache)
-            c.pop(autotune.plan_key(data.n_toa, B, True, torch.cuda.get_device_name(dev)), None)
+            c.pop(autotune.plan_key(data.n_toa, B, True, torch.cuda.get_device_name(dev), args.noise),
+                  None)
             autotune.save_cache(c, cache)
         res = autotune.autotune(arr, theta, data.n_toa, grad=True, tune_batch=args.tune_batch,
                                 batch_for_key=B)
@@ -326,6 +388,7 @@ def run_ours(args):
         if not np.allclose(ll_h.numpy(), ll.cpu().numpy(), rtol=0, atol=0, equal_nan=True):
             raise RuntimeError("host-buffer path disagrees with the device path")
 
+    arr.close()                   # frees the adjoint tape before the other legs
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
@@ -352,15 +415,17 @@ def run_ours(args):
     arr_p.close()
 
     loglik_leg = None if args.no_loglik else loglik_only(args, dev, local)
+    ou = None if args.no_ou else ou_leg(args, dev, local)
     lane_steps = B * int(data.n_toa.sum())
-    achieved = FLOPS_PER_LANE_STEP_GRAD * lane_steps / (filt_ms * 1e-3) / 1e12
-    tr = traffic_record("k_filter_grad")
+    flops = FLOPS_PER_LANE_STEP_GRAD_OU if args.noise == "ou" else FLOPS_PER_LANE_STEP_GRAD
+    achieved = flops * lane_steps / (filt_ms * 1e-3) / 1e12
+    tr = traffic_record("k_filter_grad") if args.noise == "rw" else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS,
                 "traffic": tr["dram_bytes_per_launch"] if tr else None,
                 "kernel": "k_filter_grad", "kernel_ms": filt_ms,
                 "peak_source": "derived: 2 FP64 FMA/clk/SM x 152 SMs x 2.07 GHz",
-                "algorithmic": f"{FLOPS_PER_LANE_STEP_GRAD} FP64 flop per lane-step x "
+                "algorithmic": f"{flops} FP64 flop per lane-step x "
                                f"{lane_steps} lane-steps per launch"}
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
@@ -369,7 +434,8 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": w.name, "pulsars": data.n_pulsars,
+            "config": {"workload": w.name + ("" if args.noise == "rw" else " (OU red noise)"),
+                       "pulsars": data.n_pulsars,
                        "toas": int(data.n_toa.sum()), "batch_per_gpu": B, "dim": D,
                        "lane_steps_per_gpu": lane_steps, "plan": plan, "autotune": tuned,
                        "l2": "flushed between timed steps (256 MiB write, untimed)"},
@@ -377,7 +443,8 @@ def run_ours(args):
             "plain_filter": plain, "batched_over_plain": value / world / plain["value"],
             "stage_ms": {"project": statistics.mean(k[0] for k in kern), "filter": filt_ms,
                          "reduce": statistics.mean(k[2] for k in kern)},
-            "clocks": clk, "cpu_baseline": cpu, "loglik_only": loglik_leg}
+            "clocks": clk, "cpu_baseline": cpu, "loglik_only": loglik_leg,
+            "ou_red_noise": ou}
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

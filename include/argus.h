@@ -90,7 +90,7 @@ typedef struct argus_plan {
     int32_t tape_cache;       /* adjoint: 0 = re-run each segment from its checkpoint (memory
                                  O(sqrt N) per lane); 1 = also keep every segment's tape in HBM
                                  during the forward pass and skip the re-run (memory O(N) per
-                                 lane: 48 B per TOA per resident lane, 72 B with
+                                 lane: 48 B per TOA per resident lane, 144 B with
                                  ARGUS_NOISE_OU) */
     int32_t reserved[2];      /* must be 0 */
 } argus_plan;

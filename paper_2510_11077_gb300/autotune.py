@@ -6,8 +6,12 @@ resident per SM in the persistent grid, the adjoint checkpoint stride and
 whether the adjoint keeps its tape in HBM.  The tuner times every candidate
 with CUDA events on a sub-batch of the caller's walkers, skips candidates
 that do not fit in device memory, applies the fastest and records it in a
-JSON cache keyed by the array's shape, the batch size, the GPU and the
-library source, so later runs reuse it without timing.
+JSON cache keyed by the array's shape, the batch size, the noise model, the
+GPU and the library source, so later runs reuse it without timing.
+Candidates within `tie` (relative) of the fastest count as equally fast; of
+those the tuner takes the one with the fewest resident lanes (walkers per
+block x blocks per SM), whose scratch -- the adjoint tape above all -- takes
+the least device memory.
 """
 from __future__ import annotations
 
@@ -20,6 +24,8 @@ from . import argus
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 DEFAULT_CACHE = os.path.join(HERE, "tuned_plans.json")
+
+TIE = 0.01
 
 DEFAULT_SPACE = {
     "walkers_per_cta": (32, 64, 128),
@@ -81,9 +87,17 @@ def _time_plan(arr, theta, grad: bool, reps: int) -> float:
     return e0.elapsed_time(e1) / reps
 
 
+def pick(tried: list, tie: float = TIE) -> dict:
+    """The chosen entry of a list of timed candidates (see the module note)."""
+    ok = [t for t in tried if t.get("ms") is not None]
+    fastest = min(t["ms"] for t in ok)
+    near = [t for t in ok if t["ms"] <= fastest * (1.0 + tie)]
+    return min(near, key=lambda t: (t["plan"]["walkers_per_cta"] * t["plan"]["ctas_per_sm"], t["ms"]))
+
+
 def autotune(arr, theta, n_toa, grad: bool = True, space: dict | None = None,
              tune_batch: int | None = None, reps: int = 2, cache_path: str | None = DEFAULT_CACHE,
-             batch_for_key: int | None = None, log=None) -> dict:
+             batch_for_key: int | None = None, log=None, tie: float = TIE) -> dict:
     """Pick the fastest plan for `arr` on walkers `theta` (a CUDA tensor).
 
     tune_batch: time on the first tune_batch walkers only (default: all).
@@ -100,7 +114,6 @@ def autotune(arr, theta, n_toa, grad: bool = True, space: dict | None = None,
         return dict(cache[key], cached=True)
     th = theta[:tune_batch].contiguous() if tune_batch else theta
     tried = []
-    best = None
     names = list(space)
     for values in itertools.product(*(space[k] for k in names)):
         plan = dict(zip(names, values), mode=argus.ARGUS_MODE_BATCHED, use_graph=1)
@@ -115,13 +128,14 @@ def autotune(arr, theta, n_toa, grad: bool = True, space: dict | None = None,
         tried.append(dict(plan=plan, ms=ms))
         if log:
             log(f"autotune {plan} -> {ms:.2f} ms")
-        if best is None or ms < best[1]:
-            best = (plan, ms)
-    if best is None:
+    if not any(t["ms"] is not None for t in tried):
         raise argus.ArgusError(3, "no candidate plan fits in device memory")
-    arr.set_plan(**best[0])
-    rec = {"plan": best[0], "ms": best[1], "tune_batch": th.shape[0], "tried": tried}
+    best = pick(tried, tie)
+    arr.set_plan(**best["plan"])
+    rec = {"plan": best["plan"], "ms": best["ms"], "tune_batch": th.shape[0], "tried": tried}
     if cache_path:
+        src = f"|src{_source_hash()}"
+        cache = {k: v for k, v in cache.items() if k.endswith(src)}   # drop stale plans
         cache[key] = rec
         save_cache(cache, cache_path)
     return dict(rec, cached=False)

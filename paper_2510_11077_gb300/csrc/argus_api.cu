@@ -180,6 +180,15 @@ argus_status apply_plan(argus_array* h) {
     CK(cudaMemcpy(h->d_psr, h->h_psr.data(), sizeof(PulsarDev) * h->P, cudaMemcpyHostToDevice));
     drop_graphs(h);
     h->items_B = -1;
+    // the adjoint scratch is sized by the plan (blocks x walkers x segment or
+    // tape length): release it so a new plan allocates what it needs rather
+    // than keeping the largest buffer any earlier plan used
+    cudaFree(h->d_ckpt);
+    cudaFree(h->d_tape);
+    h->d_ckpt = nullptr;
+    h->d_tape = nullptr;
+    h->cap_ckpt = 0;
+    h->cap_tape = 0;
     return ARGUS_OK;
 }
 

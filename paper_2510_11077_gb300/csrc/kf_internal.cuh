@@ -10,7 +10,8 @@ constexpr int kNgw = 7;          // continuous-wave parameters at the head of th
 constexpr int kRecDoubles = 8;   // doubles per staged TOA record
 constexpr int kCkptDoubles = 5;  // (m0, m1, p00, p01, p11) per checkpoint
 constexpr int kTapeDoubles = 6;  // (R/S, K1, 1/S, e, sin, cos) per step of a segment
-constexpr int kTapeDoublesOU = 9; // ... plus (m1, p01 + b p11, p11) before the step
+constexpr int kTapeDoublesOU = 18; // ... plus (m1, p01 + b p11, a p11) before the step, the
+                                   // transition a, b, Q / sigma^2 (3) and d/dgamma of b, Q (4)
 constexpr int kMaxStride = 256;  // longest adjoint segment, in TOAs
 constexpr int kLaneConsts = 8;   // A, B, f, Phi0/(2 pi), sigma^2, EFAC^2, EFAC, gamma
 constexpr int kLaneGrads = 7;    // dll/dA, dB, t-weighted sin and cos sums, dsigma^2, EFAC term,

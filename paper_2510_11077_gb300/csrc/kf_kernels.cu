@@ -169,7 +169,10 @@ struct State {
 
 struct StepOut {   // what the adjoint needs from the forward step (w = R/S = 1 - K0)
     double w, K1, rS, e, sn, cs;
-    double m1, t1, p11;   // Ornstein-Uhlenbeck only: m1, p01 + b p11 and p11 before the step
+    // Ornstein-Uhlenbeck only: m1, p01 + b p11 and a p11 before the step, the
+    // transition a, b, Q / sigma^2 and the gamma-derivatives of b and Q / sigma^2
+    double m1, t1, ap11;
+    double a, b, c00, c01, c11, db, dc00, dc01, dc11;
 };
 
 // ---------------------------------------------------------------------------
@@ -184,37 +187,57 @@ struct StepOut {   // what the adjoint needs from the forward step (w = R/S = 1 
 //   a' = -a,  psi1' = psi2 - psi1,  psi1(2x)' = a (psi2 - psi1) - psi1^2 / 2,
 //   phi4' = 3 ((2 psi3 - psi2)(1 - x psi2) - (3 psi4 - psi3) - psi2^2 / 2).
 // Below x = 0.5 psi4 is its Taylor series, cut where the next term falls
-// below 2^-56 of the sum (7, 10 or 14 terms for x below 1/64, 1/8, 1/2), and
-// psi3, psi2, psi1, a follow by the recurrence without cancellation.  Above,
-// a = exp(-x) and closed forms with u = 1 - a:
+// below 2^-54 of the sum (5, 7, 10 or 14 terms for x below 2^-8, 2^-6, 2^-3,
+// 2^-1; psi4 enters everything else multiplied by x or, in phi4', beside
+// terms 8x larger), and psi3, psi2, psi1, a follow by the recurrence without
+// cancellation.  Above, a = exp(-x) and closed forms with u = 1 - a:
 //   psi1 = u / x,  psi2 = (1 - psi1) / x,  phi4 = 3 (x - u (1 + u/2)) / x^3,
 //   phi4' = 3 u^2 / x^3 - 3 phi4 / x.
-// As gamma -> 0 every factor tends to the random walk's (a = 1, b = dt,
-// Q = sigma^2 [[dt^3/3, dt^2/2], [., dt]]).
+// The range tests compare the high word of x (x >= 0, thresholds powers of
+// two) on the integer pipe.  As gamma -> 0 every factor tends to the random
+// walk's (a = 1, b = dt, Q = sigma^2 [[dt^3/3, dt^2/2], [., dt]]).
+// With kDeriv the gamma-derivatives (d/dgamma = dt d/dx) of b and of the
+// three Q / sigma^2 entries are formed here too, in the forward step, so that
+// the reverse sweep reads them from the tape instead of re-deriving them.
 // ---------------------------------------------------------------------------
 struct OuCoef {
     double a, b, c00, c01, c11;        // F entries and Q / sigma^2
-    double da, db, dc00, dc01, dc11;   // their derivatives in x (with kDeriv)
+    double db, dc00, dc01, dc11;       // their derivatives in gamma (with kDeriv)
 };
 
+// Taylor coefficients (-1)^m / (m + 4)!, each fixed at compile time (a static
+// constexpr member must be a constant expression; (m + 4)! <= 17! is exact
+// in a double, so each coefficient is one correctly rounded division).
 constexpr double factorial(int n) { return n <= 1 ? 1.0 : double(n) * factorial(n - 1); }
-constexpr double psi4_coef(int m) { return ((m & 1) ? -1.0 : 1.0) / factorial(m + 4); }
+template <int M>
+struct Psi4Coef {
+    static constexpr double value = ((M & 1) ? -1.0 : 1.0) / factorial(M + 4);
+};
+
+template <int M>
+__device__ __forceinline__ double psi4_horner(double x, double s) {
+    if constexpr (M < 0) {
+        return s;
+    } else {
+        return psi4_horner<M - 1>(x, fma(s, x, Psi4Coef<M>::value));
+    }
+}
 
 template <int N>
 __device__ __forceinline__ double psi4_series(double x) {
-    double s = psi4_coef(N - 1);
-#pragma unroll
-    for (int m = N - 2; m >= 0; --m) s = fma(s, x, psi4_coef(m));
-    return s;
+    return psi4_horner<N - 2>(x, Psi4Coef<N - 1>::value);
 }
 
 template <bool kDeriv>
-__device__ __forceinline__ void ou_coef(double x, double dt, double h2, double h3, OuCoef& c) {
+__device__ __forceinline__ void ou_coef(double x, double dt, double h2, double h3, double dt2,
+                                        OuCoef& c) {
     double p1, p2, phi4, dphi4 = 0.0;
-    if (x < 0.5) {
+    const int hx = __double2hiint(x);
+    if (hx < 0x3FE00000) {                       // x < 2^-1
         double p4;
-        if (x < 0.015625) p4 = psi4_series<7>(x);
-        else if (x < 0.125) p4 = psi4_series<10>(x);
+        if (hx < 0x3F700000) p4 = psi4_series<5>(x);          // x < 2^-8
+        else if (hx < 0x3F900000) p4 = psi4_series<7>(x);     // x < 2^-6
+        else if (hx < 0x3FC00000) p4 = psi4_series<10>(x);    // x < 2^-3
         else p4 = psi4_series<14>(x);
         const double p3 = fma(-x, p4, 1.0 / 6.0);
         p2 = fma(-x, p3, 0.5);
@@ -232,17 +255,17 @@ __device__ __forceinline__ void ou_coef(double x, double dt, double h2, double h
         phi4 = 3.0 * (x - u * fma(0.5, u, 1.0)) * (r * r * r);
         if (kDeriv) dphi4 = 3.0 * r * fma(u * u, r * r, -phi4);
     }
+    const double p1sq = p1 * p1;
     c.b = dt * p1;
     c.c00 = h3 * phi4;
-    c.c01 = h2 * (p1 * p1);
-    c.c11 = dt * (p1 * fma(-0.5 * x, p1, 1.0));
+    c.c01 = h2 * p1sq;
+    c.c11 = dt * fma(-0.5 * x, p1sq, p1);
     if (kDeriv) {
         const double dp1 = p2 - p1;
-        c.da = -c.a;
-        c.db = dt * dp1;
-        c.dc00 = h3 * dphi4;
-        c.dc01 = h2 * (2.0 * p1 * dp1);
-        c.dc11 = dt * fma(c.a, dp1, -0.5 * p1 * p1);
+        c.db = dt2 * dp1;                          // dt^2 psi1'
+        c.dc00 = (h3 * dt) * dphi4;                // dt^4/3 phi4'
+        c.dc01 = (3.0 * h3) * (p1 * dp1);          // dt^3 psi1 psi1'
+        c.dc11 = dt2 * fma(c.a, dp1, -0.5 * p1sq); // dt^2 (a psi1' - psi1^2 / 2)
     }
 }
 
@@ -257,14 +280,19 @@ __device__ __forceinline__ void kf_step(State& x, const double* __restrict__ rec
     double m0, mp1, t1, M00, M01, M11;
     if (kOU) {
         OuCoef c;
-        ou_coef<false>(L.gam * dt, dt, h2, h3, c);
+        ou_coef<kTape>(L.gam * dt, dt, h2, h3, rec[6], c);
         m0 = fma(c.b, x.m1, x.m0);
         mp1 = c.a * x.m1;
         t1 = fma(c.b, x.p11, x.p01);
+        const double ap11 = c.a * x.p11;
         M00 = fma(L.sig2, c.c00, fma(c.b, x.p01 + t1, x.p00));
         M01 = fma(L.sig2, c.c01, c.a * t1);
-        M11 = fma(L.sig2, c.c11, c.a * c.a * x.p11);
-        if (kTape) { so.m1 = x.m1; so.t1 = t1; so.p11 = x.p11; }
+        M11 = fma(L.sig2, c.c11, c.a * ap11);
+        if (kTape) {
+            so.m1 = x.m1; so.t1 = t1; so.ap11 = ap11;
+            so.a = c.a; so.b = c.b; so.c00 = c.c00; so.c01 = c.c01; so.c11 = c.c11;
+            so.db = c.db; so.dc00 = c.dc00; so.dc01 = c.dc01; so.dc11 = c.dc11;
+        }
     } else {
         m0 = fma(dt, x.m1, x.m0);
         mp1 = x.m1;
@@ -342,19 +370,17 @@ __device__ __forceinline__ void kf_step_adjoint(Adjoint& a, const StepOut& so,
     g.Bt = fma(st, so.cs, g.Bt);
     // back through the prediction m = F m, M = F P F^T + Q
     if (kOU) {
-        OuCoef c;
-        ou_coef<true>(L.gam * dt, dt, h2, h3, c);
-        g.s2 = fma(M00b, c.c00, fma(M01b, c.c01, fma(M11b, c.c11, g.s2)));
-        // adjoints of a and b, then d/dgamma = dt d/dx
-        const double abar = fma(a.mu1, so.m1, fma(M01b, so.t1, 2.0 * c.a * M11b * so.p11));
-        const double bbar = fma(a0, so.m1, fma(2.0 * M00b, so.t1, c.a * M01b * so.p11));
-        const double qx = fma(M00b, c.dc00, fma(M01b, c.dc01, M11b * c.dc11));
-        g.G = fma(dt, fma(abar, c.da, fma(bbar, c.db, L.sig2 * qx)), g.G);
+        g.s2 = fma(M00b, so.c00, fma(M01b, so.c01, fma(M11b, so.c11, g.s2)));
+        // adjoints of a and b; da/dgamma = -dt a
+        const double abar = fma(a.mu1, so.m1, fma(M01b, so.t1, 2.0 * M11b * so.ap11));
+        const double bbar = fma(a0, so.m1, fma(2.0 * M00b, so.t1, M01b * so.ap11));
+        const double qg = fma(M00b, so.dc00, fma(M01b, so.dc01, M11b * so.dc11));
+        g.G = fma(-dt * so.a, abar, fma(bbar, so.db, fma(L.sig2, qg, g.G)));
         a.mu0 = a0;
-        a.mu1 = fma(c.b, a0, c.a * a.mu1);
+        a.mu1 = fma(so.b, a0, so.a * a.mu1);
         a.pi00 = M00b;
-        a.pi01 = fma(2.0 * c.b, M00b, c.a * M01b);
-        a.pi11 = fma(c.b * c.b, M00b, c.a * fma(c.b, M01b, c.a * M11b));
+        a.pi01 = fma(2.0 * so.b, M00b, so.a * M01b);
+        a.pi11 = fma(so.b * so.b, M00b, so.a * fma(so.b, M01b, so.a * M11b));
     } else {
         g.s2 = fma(M00b, h3, fma(M01b, h2, fma(M11b, dt, g.s2)));
         a.mu0 = a0;
@@ -370,13 +396,25 @@ template <bool kOU>
 __device__ __forceinline__ void tape_put(double* tk, int W, const StepOut& so) {
     tk[0 * W] = so.w; tk[1 * W] = so.K1; tk[2 * W] = so.rS;
     tk[3 * W] = so.e; tk[4 * W] = so.sn; tk[5 * W] = so.cs;
-    if (kOU) { tk[6 * W] = so.m1; tk[7 * W] = so.t1; tk[8 * W] = so.p11; }
+    if (kOU) {
+        tk[6 * W] = so.m1; tk[7 * W] = so.t1; tk[8 * W] = so.ap11;
+        tk[9 * W] = so.a; tk[10 * W] = so.b; tk[11 * W] = so.c00; tk[12 * W] = so.c01;
+        tk[13 * W] = so.c11; tk[14 * W] = so.db; tk[15 * W] = so.dc00; tk[16 * W] = so.dc01;
+        tk[17 * W] = so.dc11;
+    }
 }
 
 template <bool kOU>
 __device__ __forceinline__ StepOut tape_get(const double* tk, int W) {
-    StepOut so{tk[0 * W], tk[1 * W], tk[2 * W], tk[3 * W], tk[4 * W], tk[5 * W], 0.0, 0.0, 0.0};
-    if (kOU) { so.m1 = tk[6 * W]; so.t1 = tk[7 * W]; so.p11 = tk[8 * W]; }
+    StepOut so{};
+    so.w = tk[0 * W]; so.K1 = tk[1 * W]; so.rS = tk[2 * W];
+    so.e = tk[3 * W]; so.sn = tk[4 * W]; so.cs = tk[5 * W];
+    if (kOU) {
+        so.m1 = tk[6 * W]; so.t1 = tk[7 * W]; so.ap11 = tk[8 * W];
+        so.a = tk[9 * W]; so.b = tk[10 * W]; so.c00 = tk[11 * W]; so.c01 = tk[12 * W];
+        so.c11 = tk[13 * W]; so.db = tk[14 * W]; so.dc00 = tk[15 * W]; so.dc01 = tk[16 * W];
+        so.dc11 = tk[17 * W];
+    }
     return so;
 }
 
