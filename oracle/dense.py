@@ -32,6 +32,10 @@ g(tau) = (1 - e^{-gam tau}) / gam.  Then
 (the covariance of the integral of an OU process started at zero), which
 tends to the integrated-Brownian-motion kernel as gam -> 0.
 
+With the wave's pulsar term the residual is the Earth term minus the same
+Earth-term residual at the retarded time t - tau_p, tau_p = d_p (1 - n.c)/c
+(d_p the pulsar's distance): s(t) = s_E(t) - s_E(t - tau_p).
+
 Gradients: d ll / d theta = (ds/dtheta)^T alpha for the signal parameters and
 1/2 tr[(alpha alpha^T - C^-1) dC/deta] for the noise parameters, with
 alpha = C^-1 (r - s).
@@ -43,6 +47,8 @@ from scipy.linalg import cho_factor, cho_solve
 
 LN10 = np.log(10.0)
 N_GW = 7
+# light-travel time over one kiloparsec, s (IAU: 1 pc = 648000/pi au, au and c exact)
+KPC_LIGHT_S = 1e3 * (648000.0 / np.pi) * 149597870700.0 / 299792458.0
 
 
 def cw_project(theta_gw, pos):
@@ -72,10 +78,28 @@ def cw_project(theta_gw, pos):
     return A, B, W, phi0
 
 
-def cw_signal(theta_gw, pos, t):
+def _delay_factor(theta_gw, pos):
+    """1 - n.c, clamped as in the antenna pattern."""
+    th = np.asarray(theta_gw)
+    sind, al = th[4], th[5]
+    cosd = np.sqrt(1.0 - sind * sind)
+    n = np.array([cosd * np.cos(al), cosd * np.sin(al), sind])
+    D = 1.0 - np.asarray(pos, dtype=np.float64) @ n
+    if np.real(D) < 1e-12:
+        D = 1e-12 + 1j * np.imag(D) if np.iscomplexobj(D) else 1e-12
+    return D
+
+
+def cw_signal(theta_gw, pos, t, d_kpc=None):
+    """The continuous-wave residual; with a distance d_kpc, Earth minus pulsar term."""
     A, B, W, phi0 = cw_project(theta_gw, pos)
-    ph = W * np.asarray(t) + phi0
-    return A * np.sin(ph) + B * np.cos(ph)
+    t = np.asarray(t)
+    s_earth = lambda tt: A * np.sin(W * tt + phi0) + B * np.cos(W * tt + phi0)
+    s = s_earth(t)
+    if d_kpc is not None:
+        tau = d_kpc * KPC_LIGHT_S * _delay_factor(theta_gw, pos)
+        s = s - s_earth(t - tau)
+    return s
 
 
 def ibm_covariance(t, sig2, p0, R):
@@ -104,23 +128,31 @@ def ou_covariance(t, sig2, gam, p0, R):
     return C
 
 
+def _layout(data):
+    """(parameters per pulsar, OU?, pulsar term?)"""
+    ou = getattr(data, "model", "rw") == "ou"
+    pt = bool(getattr(data, "pulsar_term", False))
+    return 2 + int(ou) + int(pt), ou, pt
+
+
 def _noise(data, p, theta):
-    """(sig2, gam or None, efac) of pulsar p."""
-    k = 3 if getattr(data, "model", "rw") == "ou" else 2
+    """(sig2, gam or None, efac, parameters per pulsar, d or None) of pulsar p."""
+    k, ou, pt = _layout(data)
     nz = theta[N_GW + k * p:N_GW + k * (p + 1)]
-    gam = 10.0 ** nz[1] if k == 3 else None
-    return 10.0 ** (2.0 * nz[0]), gam, nz[-1], k
+    gam = 10.0 ** nz[1] if ou else None
+    efac = nz[2] if ou else nz[1]
+    return 10.0 ** (2.0 * nz[0]), gam, efac, k, (nz[-1] if pt else None)
 
 
 def _pulsar_parts(data, p, theta):
     t, r, sig = data.pulsar(p)
-    sig2, gam, efac, _ = _noise(data, p, theta)
+    sig2, gam, efac, _, d = _noise(data, p, theta)
     R = efac ** 2 * sig ** 2 + data.equad[p] ** 2
     if gam is None:
         C = ibm_covariance(t, sig2, data.p0[p], R)
     else:
         C = ou_covariance(t, sig2, gam, data.p0[p], R)
-    s = cw_signal(theta[:N_GW], data.pos[p], t)
+    s = cw_signal(theta[:N_GW], data.pos[p], t, d)
     return t, r, sig, sig2, efac, C, s
 
 
@@ -143,21 +175,25 @@ def grad(data, theta, h=1e-20):
     """Gradient by the dense formulas; ds/dtheta by complex step on cw_signal."""
     theta = np.asarray(theta, dtype=np.float64)
     P = data.n_pulsars
-    k = 3 if getattr(data, "model", "rw") == "ou" else 2
+    k, ou, pt = _layout(data)
     g = np.zeros(N_GW + k * P)
     for p in range(P):
         t, r, sig, sig2, efac, C, s = _pulsar_parts(data, p, theta)
+        d = theta[N_GW + k * p + k - 1] if pt else None
         cf = cho_factor(C, lower=True)
         alpha = cho_solve(cf, r - s)
         for j in range(N_GW):
             thc = theta[:N_GW].astype(np.complex128)
             thc[j] += 1j * h
-            ds = np.imag(cw_signal(thc, data.pos[p], t)) / h
+            ds = np.imag(cw_signal(thc, data.pos[p], t, d)) / h
             g[j] += ds @ alpha
+        if pt:
+            ds = np.imag(cw_signal(theta[:N_GW], data.pos[p], t, d + 1j * h)) / h
+            g[N_GW + k * p + k - 1] = ds @ alpha
         Cinv = cho_solve(cf, np.eye(len(t)))
         M = np.outer(alpha, alpha) - Cinv
         R = efac ** 2 * sig ** 2 + data.equad[p] ** 2
-        if k == 2:
+        if not ou:
             tau = t - t[0]
             mn = np.minimum.outer(tau, tau)
             mx = np.maximum.outer(tau, tau)
@@ -171,5 +207,5 @@ def grad(data, theta, h=1e-20):
             dC_lg = np.imag(ou_covariance(t, sig2, thc, data.p0[p], R)) / h
             g[N_GW + k * p + 1] = 0.5 * np.sum(M * dC_lg)
         g[N_GW + k * p] = 0.5 * np.sum(M * dC_ls)
-        g[N_GW + k * p + k - 1] = 0.5 * np.sum(np.diag(M) * 2.0 * efac * sig ** 2)
+        g[N_GW + k * p + (2 if ou else 1)] = 0.5 * np.sum(np.diag(M) * 2.0 * efac * sig ** 2)
     return g

@@ -43,7 +43,8 @@ def _ptr(a):
 def _array_args(data):
     off = np.ascontiguousarray(data.off, dtype=np.int64)
     keep = [off, _d(data.t), _d(data.r), _d(data.sigma), _d(data.pos), _d(data.equad), _d(data.p0)]
-    model = 1 if getattr(data, "model", "rw") == "ou" else 0
+    model = (1 if getattr(data, "model", "rw") == "ou" else 0) | \
+        (2 if getattr(data, "pulsar_term", False) else 0)
     args = ([ctypes.c_int(data.n_pulsars), off.ctypes.data_as(_ip)] + [_ptr(a) for a in keep[1:]]
             + [ctypes.c_int(model)])
     return keep, args
@@ -81,23 +82,25 @@ def loglik_grad(data, theta, lib_path: str | None = None):
     return ll, g
 
 
-def cw_project(theta_gw, pos, lib_path: str | None = None):
-    """(A, B, Omega, Phi0) of one parameter vector on one pulsar."""
+def cw_project(theta_gw, pos, lib_path: str | None = None, with_delay: bool = False):
+    """(A, B, Omega, Phi0) of one parameter vector on one pulsar; with
+    with_delay also 1 - n.c (clamped), the pulsar term's geometric factor."""
     lib = _load(lib_path)
-    th = _d(theta_gw[:7]); c = _d(pos); out = np.empty(4)
+    th = _d(theta_gw[:7]); c = _d(pos); out = np.empty(5)
     lib.oracle_cw_project(_ptr(th), _ptr(c), _ptr(out))
-    return out
+    return out if with_delay else out[:4]
 
 
 def pulsar_filter(t, r, sigma, equad, p0, lane, trace: bool = False,
                   lib_path: str | None = None):
     """One pulsar's log-likelihood for lane = (A, B, Omega, Phi0, sigma^2, EFAC
-    [, gamma]); gamma > 0 selects the Ornstein-Uhlenbeck red noise.
+    [, gamma [, Dp]]); gamma > 0 selects the Ornstein-Uhlenbeck red noise and
+    Dp != 0 adds the pulsar term with phase lag Dp (rad).
 
     With trace=True also returns the innovations e_k and variances S_k.
     """
     lib = _load(lib_path)
-    lane = np.concatenate([np.asarray(lane, dtype=np.float64), np.zeros(7 - len(lane))])
+    lane = np.concatenate([np.asarray(lane, dtype=np.float64), np.zeros(8 - len(lane))])
     t, r, sigma, p0, lane = _d(t), _d(r), _d(sigma), _d(p0), _d(lane)
     n = len(t)
     e = np.empty(n) if trace else None

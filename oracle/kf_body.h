@@ -24,6 +24,11 @@
  * (both -> 1 as gam -> 0, the random walk), by their Taylor series below
  * x = 0.5 and the closed forms above.
  *
+ * With pt != 0 the continuous-wave residual also carries its pulsar term:
+ * the wave that passed the pulsar a time tau_p earlier, with the opposite
+ * sign; for a monochromatic source that is the Earth-term sinusoid with its
+ * phase lagging by Dp = Om tau_p (the caller forms Dp).
+ *
  * Steps per TOA in textbook order: predict the mean (m = F m) and covariance
  * (P = F P F^T + Q), form the signal and the innovation e = r - s - H m with
  * H = (1, 0) and its variance S = H P H^T + R, gain K = P H^T / S, update
@@ -57,7 +62,7 @@ static void KF_PHI(KF_T x, KF_T* p1, KF_T* p2, KF_T* p4)
 static KF_T KF_NAME(int64_t n, const double* t, const double* r, const double* sigma,
                     double equad, const double p0[3],
                     KF_T A, KF_T B, KF_T Om, KF_T Phi0, KF_T sig2, KF_T efac,
-                    int ou, KF_T gam, int* bad, double* e_out, double* S_out)
+                    int ou, KF_T gam, int pt, KF_T Dp, int* bad, double* e_out, double* S_out)
 {
     KF_T m0 = 0.0, m1 = 0.0;
     KF_T p00 = p0[0], p01 = p0[1], p11 = p0[2];
@@ -88,6 +93,7 @@ static KF_T KF_NAME(int64_t n, const double* t, const double* r, const double* s
         /* continuous-wave timing residual at this TOA */
         KF_T phase = Om * t[k] + Phi0;
         KF_T s = A * KF_SIN(phase) + B * KF_COS(phase);
+        if (pt) s -= A * KF_SIN(phase - Dp) + B * KF_COS(phase - Dp);
         /* innovation and its variance */
         KF_T R = efac * efac * (sigma[k] * sigma[k]) + equad * equad;
         KF_T e = r[k] - s - mp0;

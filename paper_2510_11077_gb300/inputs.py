@@ -25,7 +25,8 @@ Parameter vector layout (D = 7 + 2P for the random-walk red noise):
 ``[log10 f_gw, Phi0, psi, cos iota, sin delta, alpha, log10 h0,
    (log10 sigma_p, EFAC_p) for p in 0..P-1]``; with Ornstein-Uhlenbeck red
 noise (model "ou") each pulsar has ``(log10 sigma_p, log10 gamma_p, EFAC_p)``
-and D = 7 + 3P.
+and D = 7 + 3P.  With the wave's pulsar term (``pulsar_term=True``) each
+pulsar's block ends with its distance d_p in kpc.
 """
 from __future__ import annotations
 
@@ -60,8 +61,13 @@ PRIOR_NOISE_OU = np.array([
 ])
 
 
-def noise_prior(model: str) -> np.ndarray:
-    return PRIOR_NOISE_OU if model == "ou" else PRIOR_NOISE
+PRIOR_DIST = np.array([[0.2, 3.0]])   # pulsar distance d_p [kpc]
+
+
+def noise_prior(model: str, pulsar_term: bool = False) -> np.ndarray:
+    """Prior box of one pulsar's own parameters, in theta order."""
+    pr = PRIOR_NOISE_OU if model == "ou" else PRIOR_NOISE
+    return np.concatenate([pr, PRIOR_DIST]) if pulsar_term else pr
 
 
 @dataclasses.dataclass
@@ -76,6 +82,7 @@ class ArrayData:
     p0: np.ndarray       # float64 [P, 3], prior covariance (rr, ry, yy)
     theta_true: np.ndarray  # float64 [D], parameters used to draw the residuals
     model: str = "rw"    # red noise: "rw" random walk, "ou" Ornstein-Uhlenbeck
+    pulsar_term: bool = False   # the wave's pulsar term (distance d_p per pulsar)
 
     @property
     def n_pulsars(self) -> int:
@@ -86,8 +93,17 @@ class ArrayData:
         return 3 if self.model == "ou" else 2
 
     @property
+    def n_per_pulsar(self) -> int:
+        """Parameters per pulsar: the noise parameters, then d_p with the pulsar term."""
+        return self.n_noise + (1 if self.pulsar_term else 0)
+
+    @property
+    def efac_slot(self) -> int:
+        return self.n_noise - 1
+
+    @property
     def dim(self) -> int:
-        return N_GW + self.n_noise * self.n_pulsars
+        return N_GW + self.n_per_pulsar * self.n_pulsars
 
     @property
     def n_toa(self) -> np.ndarray:
@@ -135,9 +151,10 @@ def draw_toa_counts(rng: np.random.Generator, n_pulsars: int, law: tuple) -> np.
     raise ValueError(f"unknown TOA-count law {law!r}")
 
 
-def draw_prior(rng: np.random.Generator, n_pulsars: int, n: int, model: str = "rw") -> np.ndarray:
+def draw_prior(rng: np.random.Generator, n_pulsars: int, n: int, model: str = "rw",
+               pulsar_term: bool = False) -> np.ndarray:
     """n parameter vectors drawn uniformly from the prior box, float64 [n, D]."""
-    pr = noise_prior(model)
+    pr = noise_prior(model, pulsar_term)
     k = len(pr)
     gw = PRIOR_GW[:, 0] + (PRIOR_GW[:, 1] - PRIOR_GW[:, 0]) * rng.random((n, N_GW))
     nz = pr[:, 0] + (pr[:, 1] - pr[:, 0]) * rng.random((n, n_pulsars, k))
@@ -152,7 +169,8 @@ def isotropic_positions(rng: np.random.Generator, n: int) -> np.ndarray:
 
 
 def make_array(n_toa: np.ndarray, seed: int, with_signal: bool = True,
-               t_obs: float = T_OBS, equad: float = 0.0, model: str = "rw") -> ArrayData:
+               t_obs: float = T_OBS, equad: float = 0.0, model: str = "rw",
+               pulsar_term: bool = False) -> ArrayData:
     """Draw TOAs, errors, positions, a true parameter vector and residuals."""
     rng = np.random.Generator(np.random.PCG64(seed))
     n_toa = np.asarray(n_toa, dtype=np.int64)
@@ -198,16 +216,23 @@ def make_array(n_toa: np.ndarray, seed: int, with_signal: bool = True,
         t[a:b] = tp; r[a:b] = rho + white + sinus
     # array epoch: earliest TOA of the whole array is t = 0
     t -= t.min()
+    if pulsar_term:
+        # distances drawn after everything else, so the residuals do not
+        # depend on the flag
+        d = PRIOR_DIST[0, 0] + (PRIOR_DIST[0, 1] - PRIOR_DIST[0, 0]) * rng.random(P)
+        blocks = theta[N_GW:].reshape(P, k)
+        theta = np.concatenate([theta[:N_GW], np.concatenate([blocks, d[:, None]], axis=1).ravel()])
     return ArrayData(off=off, t=t, r=r, sigma=sig, pos=pos,
                      equad=np.full(P, equad), p0=np.tile(np.array(P0_DEFAULT), (P, 1)),
-                     theta_true=theta, model=model)
+                     theta_true=theta, model=model, pulsar_term=pulsar_term)
 
 
-def make_workload_array(name: str, model: str = "rw") -> ArrayData:
+def make_workload_array(name: str, model: str = "rw", pulsar_term: bool = False) -> ArrayData:
     w = WORKLOADS[name]
     rng = np.random.Generator(np.random.PCG64(w.seed))
     n_toa = draw_toa_counts(rng, w.n_pulsars, w.toa_law)
-    return make_array(n_toa, w.seed + 1000, with_signal=w.with_signal, model=model)
+    return make_array(n_toa, w.seed + 1000, with_signal=w.with_signal, model=model,
+                      pulsar_term=pulsar_term)
 
 
 def make_theta_batch(data: ArrayData, batch: int, seed: int, kind: str = "posterior") -> np.ndarray:
@@ -218,9 +243,9 @@ def make_theta_batch(data: ArrayData, batch: int, seed: int, kind: str = "poster
     """
     rng = np.random.Generator(np.random.PCG64(seed))
     P = data.n_pulsars
-    k = data.n_noise
+    k = data.n_per_pulsar
     if kind == "prior":
-        return draw_prior(rng, P, batch, data.model)
+        return draw_prior(rng, P, batch, data.model, data.pulsar_term)
     width = np.concatenate([
         np.array([1e-4, 1e-2, 1e-2, 1e-2, 1e-2, 1e-2, 1e-2]),
         np.tile(np.full(k, 1e-2), P)])
@@ -228,5 +253,7 @@ def make_theta_batch(data: ArrayData, batch: int, seed: int, kind: str = "poster
     # keep the bounded coordinates inside their domain
     th[:, 3] = np.clip(th[:, 3], -1.0, 1.0)
     th[:, 4] = np.clip(th[:, 4], -0.999, 0.999)
-    th[:, 7 + k - 1::k] = np.abs(th[:, 7 + k - 1::k])
+    th[:, 7 + data.efac_slot::k] = np.abs(th[:, 7 + data.efac_slot::k])
+    if data.pulsar_term:
+        th[:, 7 + k - 1::k] = np.abs(th[:, 7 + k - 1::k])
     return th

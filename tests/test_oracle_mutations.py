@@ -56,6 +56,17 @@ MUTATIONS = {
     "ou_phi4_closed": ("kf_body.h", "0.5 * (1.0 - e2)) / (x * x * x)", "(1.0 - e2)) / (x * x * x)"),
     "ou_gamma_index": ("kalman.c", "cplx gam = a->ou ? cpow(10.0, nz[1]) : 0.0;",
                        "cplx gam = a->ou ? cpow(10.0, nz[0]) : 0.0;"),
+    # the wave's pulsar term
+    "pt_sign": ("kf_body.h", "if (pt) s -= A", "if (pt) s += A"),
+    "pt_lag_sign": ("kf_body.h", "KF_SIN(phase - Dp) + B * KF_COS(phase - Dp)",
+                    "KF_SIN(phase + Dp) + B * KF_COS(phase + Dp)"),
+    "pt_no_geometry": ("kalman.c", "Om * (nz[n_noise(a) - 1] * KPC_LIGHT_S * Dn)",
+                       "Om * (nz[n_noise(a) - 1] * KPC_LIGHT_S)"),
+    "pt_light_speed_km": ("kalman.c", "149597870700.0 / 299792458.0)", "149597870700.0 / 299792.458)"),
+    "pt_efac_slot": ("kalman.c", "static int efac_slot(const array_view* a) { return 1 + a->ou; }",
+                     "static int efac_slot(const array_view* a) { return n_noise(a) - 1; }"),
+    "pt_real_distance_index": ("kalman.c", "creal(Om) * (nz[np - 1] * KPC_LIGHT_S",
+                               "creal(Om) * (nz[np - 2] * KPC_LIGHT_S"),
 }
 
 
@@ -126,6 +137,16 @@ def _pins(lib):
     gd = dense.grad(do, tho)
     if not np.all(np.abs(go[0] - gd) <= 1e-6 * np.maximum(np.abs(gd), 1e-3 * np.abs(gd).max())):
         failed.append("grad_ou")
+    # the wave's pulsar term with OU red noise: dense likelihood and gradient
+    dp = inputs.make_array(np.array([70, 45]), seed=5, equad=1e-8, model="ou", pulsar_term=True)
+    thp = inputs.make_theta_batch(dp, 1, seed=2)[0]
+    llp = kalman.loglik(dp, thp, lib_path=lib)[0]
+    if not abs(llp - dense.loglik(dp, thp)[0]) <= 1e-10 * abs(llp):
+        failed.append("dense_pt")
+    _, gp = kalman.loglik_grad(dp, thp, lib_path=lib)
+    gdp = dense.grad(dp, thp)
+    if not np.all(np.abs(gp[0] - gdp) <= 1e-6 * np.maximum(np.abs(gdp), 1e-3 * np.abs(gdp).max())):
+        failed.append("grad_pt")
     # antenna pattern: textbook case (source at the pole, pulsar on the equator)
     thp = np.array([-8.0, 0.0, 0.0, 0.5, 1.0, 0.0, -14.0])
     A, B, W, _ = kalman.cw_project(thp, np.array([1.0, 0.0, 0.0]), lib_path=lib)
