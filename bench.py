@@ -74,6 +74,10 @@ def parse_args():
                     help="skip the Ornstein-Uhlenbeck red-noise leg (20 pulsars x 4096 walkers)")
     ap.add_argument("--noise", choices=["rw", "ou"], default="rw",
                     help="red-noise model of the main step (rw: random walk; ou: Ornstein-Uhlenbeck)")
+    ap.add_argument("--pulsar-term", action="store_true",
+                    help="main step with the wave's pulsar term (distance d_p per pulsar)")
+    ap.add_argument("--no-pt", action="store_true",
+                    help="skip the pulsar-term leg (20 pulsars x 4096 walkers)")
     ap.add_argument("--autotune", choices=["cache", "off", "force"], default="cache",
                     help="cache: use the tuned-plan cache, tuning on a miss; force: retune")
     ap.add_argument("--tune-batch", type=int, default=4096)
@@ -175,7 +179,7 @@ def run_reference(args):
     from oracle import kalman
     from paper_2510_11077_gb300 import inputs
     w = inputs.WORKLOADS[args.workload]
-    data = inputs.make_workload_array(w.name, model=args.noise)
+    data = inputs.make_workload_array(w.name, model=args.noise, pulsar_term=args.pulsar_term)
     theta = inputs.make_theta_batch(data, w.batch, seed=w.seed)
     cores = os.cpu_count() or 1
     kalman.set_threads(cores)
@@ -191,7 +195,8 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": w.name + ("" if args.noise == "rw" else " (OU red noise)"),
+            "config": {"workload": w.name + ("" if args.noise == "rw" else " (OU red noise)")
+                                   + (" (with pulsar term)" if args.pulsar_term else ""),
                        "pulsars": data.n_pulsars, "toas": int(data.n_toa.sum()),
                        "batch": w.batch, "dim": data.dim,
                        "step": f"{per_step} walkers of the batch per step (bounded CPU sample)"},
@@ -294,6 +299,53 @@ def ou_leg(args, dev, local):
                                         f"{lane_steps} lane-steps per launch"}}
 
 
+def pulsar_term_leg(args, dev, local):
+    """Loglik + gradient with the wave's pulsar term on the 20-pulsar,
+    4096-walker array, against the same array without it: the filter kernels
+    are shared, so the leg reports the stage times of K1 (projection, where the
+    pulsar term is folded in) and K4 (reduction, its chain rule)."""
+    import torch
+
+    from paper_2510_11077_gb300 import argus, autotune, inputs
+    w = inputs.WORKLOADS[OU_WORKLOAD]
+    out = {}
+    for pt in (False, True):
+        data = inputs.make_workload_array(w.name, pulsar_term=pt)
+        theta = torch.from_numpy(inputs.make_theta_batch(data, w.batch, seed=w.seed)).to(dev)
+        arr = argus.Array(data, device=local)
+        res = autotune.autotune(arr, theta, data.n_toa, grad=True, batch_for_key=w.batch)
+        ll = torch.empty(w.batch, dtype=torch.float64, device=dev)
+        g = torch.empty((w.batch, data.dim), dtype=torch.float64, device=dev)
+        flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+        stream = torch.cuda.current_stream(dev)
+        arr.set_timing(True)
+        for _ in range(3):
+            argus.argus_loglik_grad(arr, theta, ll, g)
+        torch.cuda.synchronize(dev)
+        reps = 10
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(reps)]
+        stages = []
+        for k in range(reps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            argus.argus_loglik_grad(arr, theta, ll, g)
+            ev[k][1].record(stream)
+            stages.append(arr.get_timing())
+        torch.cuda.synchronize(dev)
+        step_ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+        arr.close()
+        out["with_pulsar_term" if pt else "earth_term_only"] = {
+            "dim": data.dim, "value": w.batch / (step_ms * 1e-3), "unit": UNIT,
+            "ms_per_step": step_ms, "plan": res["plan"],
+            "stage_ms": {"project": statistics.mean(x[0] for x in stages),
+                         "filter": statistics.mean(x[1] for x in stages),
+                         "reduce": statistics.mean(x[2] for x in stages)}}
+    out["workload"] = w.name
+    out["metric"] = "loglik+grad evals/s"
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -308,7 +360,7 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     w = inputs.WORKLOADS[args.workload]
-    data = inputs.make_workload_array(w.name, model=args.noise)
+    data = inputs.make_workload_array(w.name, model=args.noise, pulsar_term=args.pulsar_term)
     B, D = w.batch, data.dim
     theta_np = inputs.make_theta_batch(data, B, seed=pdist.rank_seed(w.seed, rank))
     theta = torch.from_numpy(theta_np).to(dev)
@@ -321,8 +373,8 @@ def run_ours(args):
         cache = autotune.DEFAULT_CACHE
         if args.autotune == "force" and os.path.exists(cache):
             c = autotune.load_cache(cache)
-            c.pop(autotune.plan_key(data.n_toa, B, True, torch.cuda.get_device_name(dev), args.noise),
-                  None)
+            name = args.noise + ("+pt" if args.pulsar_term else "")
+            c.pop(autotune.plan_key(data.n_toa, B, True, torch.cuda.get_device_name(dev), name), None)
             autotune.save_cache(c, cache)
         res = autotune.autotune(arr, theta, data.n_toa, grad=True, tune_batch=args.tune_batch,
                                 batch_for_key=B)
@@ -416,6 +468,7 @@ def run_ours(args):
 
     loglik_leg = None if args.no_loglik else loglik_only(args, dev, local)
     ou = None if args.no_ou else ou_leg(args, dev, local)
+    pt_leg = None if args.no_pt else pulsar_term_leg(args, dev, local)
     lane_steps = B * int(data.n_toa.sum())
     flops = FLOPS_PER_LANE_STEP_GRAD_OU if args.noise == "ou" else FLOPS_PER_LANE_STEP_GRAD
     achieved = flops * lane_steps / (filt_ms * 1e-3) / 1e12
@@ -434,7 +487,8 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": w.name + ("" if args.noise == "rw" else " (OU red noise)"),
+            "config": {"workload": w.name + ("" if args.noise == "rw" else " (OU red noise)")
+                                   + (" (with pulsar term)" if args.pulsar_term else ""),
                        "pulsars": data.n_pulsars,
                        "toas": int(data.n_toa.sum()), "batch_per_gpu": B, "dim": D,
                        "lane_steps_per_gpu": lane_steps, "plan": plan, "autotune": tuned,
@@ -444,7 +498,7 @@ def run_ours(args):
             "stage_ms": {"project": statistics.mean(k[0] for k in kern), "filter": filt_ms,
                          "reduce": statistics.mean(k[2] for k in kern)},
             "clocks": clk, "cpu_baseline": cpu, "loglik_only": loglik_leg,
-            "ou_red_noise": ou}
+            "ou_red_noise": ou, "pulsar_term": pt_leg}
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -22,13 +22,19 @@
  * With Ornstein-Uhlenbeck red noise (ARGUS_NOISE_OU; paper, Functionality:
  * OU processes for pulsar-intrinsic red noise) the frequency deviation obeys
  * dy/dt = -gamma_p y + xi(t) instead, with one more parameter per pulsar.
+ * With the wave's pulsar term (ARGUS_PULSAR_TERM; the source model of the
+ * paper's cited prior work on pulsar terms) s_p(t) also subtracts the same
+ * wave at the retarded time t - d_p (1 - n.c)/c, d_p the pulsar's distance:
+ *   s_p(t) = A sin Phi + B cos Phi - A sin(Phi - L_p) - B cos(Phi - L_p),
+ *   L_p = W d_p (1 - n.c) / c,  1 kpc / c = 1e3 (648000/pi) au / c.
  *
  * Parameter vector theta (row-major [B][D]):
  *   [log10 f_gw (Hz), Phi0 (rad), psi (rad), cos iota, sin delta, alpha (rad),
  *    log10 h0, then per pulsar (log10 sigma_p, EFAC_p)]  (D = 7 + 2P), or
  *   per pulsar (log10 sigma_p, log10 gamma_p [1/s], EFAC_p) with
- *   ARGUS_NOISE_OU (D = 7 + 3P).
- * Out-of-domain vectors (a non-finite entry, EFAC <= 0, |cos iota| > 1,
+ *   ARGUS_NOISE_OU (D = 7 + 3P); ARGUS_PULSAR_TERM appends d_p [kpc] to each
+ *   pulsar's block (D = 7 + 3P or 7 + 4P).
+ * Out-of-domain vectors (a non-finite entry, EFAC <= 0, d_p <= 0, |cos iota| > 1,
  * |sin delta| > 1) and filters that meet a non-positive or non-finite
  * innovation variance give loglik = -inf and a zero gradient for that walker;
  * the call still returns ARGUS_OK.
@@ -104,26 +110,28 @@ typedef struct argus_plan {
 argus_status argus_array_create(const argus_pulsar* pulsars, int32_t n_pulsars, int32_t device,
                                 argus_array** out);
 
-/* Red-noise model of the frequency deviation y. */
-enum { ARGUS_NOISE_RANDOM_WALK = 0, ARGUS_NOISE_OU = 1 };
+/* Model flags: the red-noise model of the frequency deviation y, optionally
+ * OR-ed with the wave's pulsar term. */
+enum { ARGUS_NOISE_RANDOM_WALK = 0, ARGUS_NOISE_OU = 1, ARGUS_PULSAR_TERM = 2 };
 
-/* argus_array_create with a choice of red-noise model: ARGUS_NOISE_RANDOM_WALK
- * (what argus_array_create builds) or ARGUS_NOISE_OU, where over a step dt
- * the state transition is F = [[1, (1 - e^{-gamma dt})/gamma], [0, e^{-gamma dt}]]
- * and the process noise the exact covariance of the integrated OU increment.
- * ARGUS_ERR_INVALID_ARG for any other value; otherwise as argus_array_create. */
+/* argus_array_create with a choice of model.  ARGUS_NOISE_RANDOM_WALK is what
+ * argus_array_create builds; with ARGUS_NOISE_OU the state transition over a
+ * step dt is F = [[1, (1 - e^{-gamma dt})/gamma], [0, e^{-gamma dt}]] and the
+ * process noise the exact covariance of the integrated OU increment;
+ * | ARGUS_PULSAR_TERM adds the pulsar term.  ARGUS_ERR_INVALID_ARG for any
+ * other bit; otherwise as argus_array_create. */
 argus_status argus_array_create_ex(const argus_pulsar* pulsars, int32_t n_pulsars, int32_t device,
-                                   int32_t noise_model, argus_array** out);
+                                   int32_t model, argus_array** out);
 
 /* Free everything the handle owns.  NULL is allowed.  Synchronises the device. */
 void argus_array_destroy(argus_array* array);
 
-/* D = 7 + 2P (random walk) or 7 + 3P (OU), the length of one parameter
- * vector; -1 for NULL. */
+/* D = 7 + kP, k = 2 (random walk) or 3 (OU), plus 1 with the pulsar term:
+ * the length of one parameter vector; -1 for NULL. */
 int32_t argus_array_dim(const argus_array* array);
 
-/* The handle's ARGUS_NOISE_* model; -1 for NULL. */
-int32_t argus_array_noise_model(const argus_array* array);
+/* The handle's model flags (ARGUS_NOISE_* | ARGUS_PULSAR_TERM); -1 for NULL. */
+int32_t argus_array_model(const argus_array* array);
 
 /* Replace / read the scheduling plan.  set_plan validates every field and
  * drops captured graphs; get_plan copies the current plan into *plan. */
@@ -167,8 +175,9 @@ argus_status argus_loglik_grad(argus_array* array, const double* theta, int64_t 
 argus_status argus_loglik_grad_noalloc(argus_array* array, const double* theta, int64_t B,
                                        double* loglik, double* grad, void* stream);
 
-/* The model's continuous-wave timing residual s_p(t_k) = A sin(W t_k + Phi0)
- * + B cos(W t_k + Phi0) at every TOA of the array, for one set of source
+/* The model's continuous-wave timing residual, Earth term only,
+ * s_p(t_k) = A sin(W t_k + Phi0) + B cos(W t_k + Phi0), at every TOA of the
+ * array (whatever the handle's model flags), for one set of source
  * parameters theta_gw = [log10 f_gw, Phi0, psi, cos iota, sin delta, alpha,
  * log10 h0] (host, 7 doubles).  s: host array of sum_p N_p doubles in the
  * pulsars' order.  Synchronous.  For simulating or subtracting a source. */

@@ -22,7 +22,19 @@ ARGUS_MODE_BATCHED = 0
 ARGUS_MODE_PLAIN = 1
 ARGUS_NOISE_RANDOM_WALK = 0
 ARGUS_NOISE_OU = 1
+ARGUS_PULSAR_TERM = 2
 NOISE_MODELS = {"rw": ARGUS_NOISE_RANDOM_WALK, "ou": ARGUS_NOISE_OU}
+
+
+def model_flags(data) -> int:
+    """argus.h model flags of an ArrayData (red-noise model, pulsar term)."""
+    return NOISE_MODELS[getattr(data, "model", "rw")] | \
+        (ARGUS_PULSAR_TERM if getattr(data, "pulsar_term", False) else 0)
+
+
+def model_name(flags: int) -> str:
+    """'rw' or 'ou', with '+pt' for the pulsar term."""
+    return ("ou" if flags & ARGUS_NOISE_OU else "rw") + ("+pt" if flags & ARGUS_PULSAR_TERM else "")
 STATUS = {0: "ARGUS_OK", 1: "ARGUS_ERR_INVALID_ARG", 2: "ARGUS_ERR_CUDA", 3: "ARGUS_ERR_OOM",
           4: "ARGUS_ERR_NONFINITE", 5: "ARGUS_ERR_TIMEOUT", 6: "ARGUS_ERR_UNSUPPORTED"}
 
@@ -78,8 +90,8 @@ def load(build_if_missing: bool = False):
     lib.argus_array_create_ex.argtypes = [ctypes.POINTER(ArgusPulsar), ctypes.c_int32, ctypes.c_int32,
                                           ctypes.c_int32, ctypes.POINTER(vp)]
     lib.argus_array_create_ex.restype = ctypes.c_int
-    lib.argus_array_noise_model.argtypes = [vp]
-    lib.argus_array_noise_model.restype = ctypes.c_int32
+    lib.argus_array_model.argtypes = [vp]
+    lib.argus_array_model.restype = ctypes.c_int32
     lib.argus_array_destroy.argtypes = [vp]
     lib.argus_array_destroy.restype = None
     lib.argus_array_dim.argtypes = [vp]
@@ -134,11 +146,12 @@ def _stream_of(*tensors):
 
 class Array:
     """Handle of one pulsar array on one device (argus_array_create_ex; the
-    red-noise model is ``data.model``, "rw" or "ou")."""
+    red-noise model is ``data.model``, "rw" or "ou", and ``data.pulsar_term``
+    adds the wave's pulsar term)."""
 
     def __init__(self, data, device: int = 0):
         lib = load()
-        model = NOISE_MODELS[getattr(data, "model", "rw")]
+        model = model_flags(data)
         P = data.n_pulsars
         self._keep = []
         ps = (ArgusPulsar * P)()
@@ -159,7 +172,8 @@ class Array:
         self.handle = h
         self.n_pulsars = P
         self.dim = lib.argus_array_dim(h)
-        self.noise_model = lib.argus_array_noise_model(h)
+        self.model = lib.argus_array_model(h)
+        self.noise_model = self.model & ARGUS_NOISE_OU
         self.device = device
 
     def close(self):

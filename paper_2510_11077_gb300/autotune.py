@@ -106,7 +106,7 @@ def autotune(arr, theta, n_toa, grad: bool = True, space: dict | None = None,
     import torch
     space = dict(DEFAULT_SPACE, **(space or {}))
     B = theta.shape[0] if batch_for_key is None else batch_for_key
-    model = {v: k for k, v in argus.NOISE_MODELS.items()}[getattr(arr, "noise_model", 0)]
+    model = argus.model_name(getattr(arr, "model", 0))
     key = plan_key(n_toa, B, grad, torch.cuda.get_device_name(theta.device), model)
     cache = load_cache(cache_path) if cache_path else {}
     if key in cache:

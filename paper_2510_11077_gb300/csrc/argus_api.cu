@@ -89,7 +89,8 @@ struct argus_array {
     int n_sm = 0;
     int P = 0;
     int32_t model = kRandomWalk;   // red-noise model (argus.h: ARGUS_NOISE_*)
-    int32_t nq = 2;                // noise parameters per pulsar
+    int32_t flags = 0;             // kFlagOU | kFlagPulsarTerm (argus.h model flags)
+    int32_t nq = 2;                // parameters per pulsar
     int64_t total_toa = 0;
     int32_t stride_max = 1;   // for the current plan
     int32_t nseg_max = 0;
@@ -272,13 +273,13 @@ argus_status enqueue_batched(argus_array* h, const double* theta, int64_t B, dou
     const int grid = grid_for(h, h->n_items);
     CK(cudaMemsetAsync(h->d_counter, 0, sizeof(int), s));
     if (h->timing) CK(cudaEventRecordWithFlags(h->ev[0], s, cudaEventRecordExternal));
-    launch_project(theta, B, h->P, h->model, h->d_psr, h->d_lc, s);
+    launch_project(theta, B, h->P, h->flags, h->d_psr, h->d_lc, s);
     if (h->timing) CK(cudaEventRecordWithFlags(h->ev[1], s, cudaEventRecordExternal));
     FilterArgs a = make_args(h, B, W, grid, true);
     if (want_grad) launch_filter_grad(a, W, grid, s);
     else launch_filter_fwd(a, W, grid, s);
     if (h->timing) CK(cudaEventRecordWithFlags(h->ev[2], s, cudaEventRecordExternal));
-    launch_reduce(theta, B, h->P, h->model, h->d_psr, h->d_lane, ll, grad, lane, s);
+    launch_reduce(theta, B, h->P, h->flags, h->d_psr, h->d_lane, ll, grad, lane, s);
     if (h->timing) {
         CK(cudaEventRecordWithFlags(h->ev[3], s, cudaEventRecordExternal));
         h->timed_once = true;
@@ -342,10 +343,10 @@ argus_status run_plain(argus_array* h, const double* theta, int64_t B, double* l
     FilterArgs a = make_args(h, 1, W, grid, false);
     for (int64_t b = 0; b < B; ++b) {
         const double* th = theta + b * D;
-        launch_project(th, 1, h->P, h->model, h->d_psr, h->d_lc, s);
+        launch_project(th, 1, h->P, h->flags, h->d_psr, h->d_lc, s);
         if (grad) launch_filter_grad(a, W, grid, s);
         else launch_filter_fwd(a, W, grid, s);
-        launch_reduce(th, 1, h->P, h->model, h->d_psr, h->d_lane, ll ? ll + b : nullptr,
+        launch_reduce(th, 1, h->P, h->flags, h->d_psr, h->d_lane, ll ? ll + b : nullptr,
                       grad ? grad + b * D : nullptr, lane ? lane + b * h->P : nullptr, s);
     }
     CK(cudaGetLastError());
@@ -421,10 +422,11 @@ argus_status argus_array_create(const argus_pulsar* psrs, int32_t n_pulsars, int
 }
 
 argus_status argus_array_create_ex(const argus_pulsar* psrs, int32_t n_pulsars, int32_t device,
-                                   int32_t noise_model, argus_array** out) {
+                                   int32_t model, argus_array** out) {
     if (!out) return fail(ARGUS_ERR_INVALID_ARG, "out is NULL");
-    if (noise_model != ARGUS_NOISE_RANDOM_WALK && noise_model != ARGUS_NOISE_OU)
-        return fail(ARGUS_ERR_INVALID_ARG, "noise_model must be ARGUS_NOISE_RANDOM_WALK or ARGUS_NOISE_OU");
+    if ((model & ~int32_t(ARGUS_NOISE_OU | ARGUS_PULSAR_TERM)) != 0)
+        return fail(ARGUS_ERR_INVALID_ARG,
+                    "model must be ARGUS_NOISE_RANDOM_WALK or ARGUS_NOISE_OU, optionally | ARGUS_PULSAR_TERM");
     if (!psrs || n_pulsars < 1) return fail(ARGUS_ERR_INVALID_ARG, "need at least one pulsar");
     if (device < 0) return fail(ARGUS_ERR_INVALID_ARG, "device must be >= 0");
     int64_t total = 0;
@@ -477,8 +479,9 @@ argus_status argus_array_create_ex(const argus_pulsar* psrs, int32_t n_pulsars, 
     h->device = device;
     h->n_sm = prop.multiProcessorCount;
     h->P = n_pulsars;
-    h->model = noise_model == ARGUS_NOISE_OU ? kOrnsteinUhlenbeck : kRandomWalk;
-    h->nq = noise_params(h->model);
+    h->model = (model & ARGUS_NOISE_OU) ? kOrnsteinUhlenbeck : kRandomWalk;
+    h->flags = ((model & ARGUS_NOISE_OU) ? kFlagOU : 0) | ((model & ARGUS_PULSAR_TERM) ? kFlagPulsarTerm : 0);
+    h->nq = params_per_pulsar(h->flags);
     h->total_toa = total;
     h->plan = default_plan();
     h->h_psr.resize(n_pulsars);
@@ -552,9 +555,10 @@ void argus_array_destroy(argus_array* h) {
 
 int32_t argus_array_dim(const argus_array* h) { return h ? kNgw + h->nq * h->P : -1; }
 
-int32_t argus_array_noise_model(const argus_array* h) {
+int32_t argus_array_model(const argus_array* h) {
     if (!h) return -1;
-    return h->model == kOrnsteinUhlenbeck ? ARGUS_NOISE_OU : ARGUS_NOISE_RANDOM_WALK;
+    return ((h->flags & kFlagOU) ? ARGUS_NOISE_OU : ARGUS_NOISE_RANDOM_WALK) |
+           ((h->flags & kFlagPulsarTerm) ? ARGUS_PULSAR_TERM : 0);
 }
 
 argus_status argus_array_set_plan(argus_array* h, const argus_plan* plan) {
@@ -748,7 +752,7 @@ extern "C" argus_status argus_loglik_grad_noalloc(argus_array* h, const double* 
     // the work counter must start at zero; everything else is written before it is read
     CK(cudaMemsetAsync(counter, 0, sizeof(int), s));
     k_noalloc_items<<<(n_items + 255) / 256, 256, 0, s>>>(items, n_items, tiles, W);
-    launch_project(theta, B, h->P, h->model, h->d_psr, lc, s);
+    launch_project(theta, B, h->P, h->flags, h->d_psr, lc, s);
     FilterArgs a{};
     a.rec = h->d_rec;
     a.psr = h->d_psr;
@@ -766,7 +770,7 @@ extern "C" argus_status argus_loglik_grad_noalloc(argus_array* h, const double* 
     a.counter = counter;
     a.model = h->model;
     launch_filter_grad(a, W, grid, s);
-    launch_reduce(theta, B, h->P, h->model, h->d_psr, lane, loglik, grad, nullptr, s);
+    launch_reduce(theta, B, h->P, h->flags, h->d_psr, lane, loglik, grad, nullptr, s);
     CK(cudaGetLastError());
     return ARGUS_OK;
 }

@@ -20,9 +20,15 @@ constexpr int kLaneGrads = 7;    // dll/dA, dB, t-weighted sin and cos sums, dsi
 // Red-noise model of the frequency deviation y (argus.h: ARGUS_NOISE_*).
 enum NoiseModel : int32_t { kRandomWalk = 0, kOrnsteinUhlenbeck = 1 };
 
-inline int noise_params(int32_t model) { return model == kOrnsteinUhlenbeck ? 3 : 2; }
-inline int tape_doubles(int32_t model) {
-    return model == kOrnsteinUhlenbeck ? kTapeDoublesOU : kTapeDoubles;
+// Model flags as in argus.h: bit 0 the noise model, bit 1 the wave's pulsar
+// term.  Per pulsar theta holds (log10 sigma, [log10 gamma], EFAC, [d_kpc]).
+constexpr int32_t kFlagOU = 1;
+constexpr int32_t kFlagPulsarTerm = 2;
+__host__ __device__ inline int params_per_pulsar(int32_t flags) {
+    return 2 + (flags & kFlagOU) + ((flags & kFlagPulsarTerm) >> 1);
+}
+inline int tape_doubles(int32_t noise_model) {
+    return noise_model == kOrnsteinUhlenbeck ? kTapeDoublesOU : kTapeDoubles;
 }
 
 // One staged TOA record (8 doubles = 64 bytes, 16-byte aligned):
@@ -59,19 +65,19 @@ struct FilterArgs {
     int32_t stride_max;       // longest segment of any pulsar (shared-memory records)
     int32_t tape_cache;       // 1: tape slot holds every segment of the pulsar (no re-run)
     int* counter;             // persistent work counter (nullptr: one item per block)
-    int32_t model;            // NoiseModel
+    int32_t model;            // NoiseModel (the pulsar term only changes K1 and K4)
     int32_t pad;
 };
 
-// K1: theta [B][D] -> lane constants [8][P][B].
-void launch_project(const double* theta, int64_t B, int32_t P, int32_t model, const PulsarDev* psr,
+// K1: theta [B][D] -> lane constants [8][P][B] (flags: kFlagOU | kFlagPulsarTerm).
+void launch_project(const double* theta, int64_t B, int32_t P, int32_t flags, const PulsarDev* psr,
                     double* lc, cudaStream_t s);
 // K2: forward filter, ll per lane -> lane_out[0][P][B].
 void launch_filter_fwd(const FilterArgs& a, int W, int grid, cudaStream_t s);
 // K3: forward with checkpoints + reverse sweep -> lane_out[0..7][P][B].
 void launch_filter_grad(const FilterArgs& a, int W, int grid, cudaStream_t s);
 // K4: deterministic sum over pulsars (and chain rule through K1 for grad).
-void launch_reduce(const double* theta, int64_t B, int32_t P, int32_t model, const PulsarDev* psr,
+void launch_reduce(const double* theta, int64_t B, int32_t P, int32_t flags, const PulsarDev* psr,
                    const double* lane_out, double* loglik, double* grad, double* lane_ll,
                    cudaStream_t s);
 // The model's continuous-wave residual at every TOA for one theta_gw [7] (device).

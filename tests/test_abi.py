@@ -88,14 +88,21 @@ def test_create_rejects_bad_input_before_any_device_call(lib, bad):
     assert lib.argus_last_error() != b""
 
 
-def test_create_ex_rejects_unknown_noise_model(lib):
+def test_create_ex_rejects_unknown_model_flags(lib):
     data = inputs.make_array(np.array([20, 30]), seed=1)
     ps, keep = _pulsars(data)
     h = ctypes.c_void_p()
-    st = lib.argus_array_create_ex(ps, data.n_pulsars, 0, 7, ctypes.byref(h))
-    assert st == 1 and h.value is None
-    assert b"noise_model" in lib.argus_last_error()
-    assert lib.argus_array_noise_model(None) == -1
+    for bad in (4, 7, -1):
+        st = lib.argus_array_create_ex(ps, data.n_pulsars, 0, bad, ctypes.byref(h))
+        assert st == 1 and h.value is None
+        assert b"model must be" in lib.argus_last_error()
+    assert lib.argus_array_model(None) == -1
+
+
+def test_model_flags_of_array_data():
+    d = inputs.make_array(np.array([5, 6]), seed=1, model="ou", pulsar_term=True)
+    assert argus.model_flags(d) == argus.ARGUS_NOISE_OU | argus.ARGUS_PULSAR_TERM
+    assert argus.model_name(argus.model_flags(d)) == "ou+pt" and d.dim == 7 + 4 * 2
 
 
 def test_calls_on_null_handle_are_rejected(lib):
