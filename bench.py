@@ -78,6 +78,8 @@ def parse_args():
                     help="main step with the wave's pulsar term (distance d_p per pulsar)")
     ap.add_argument("--no-pt", action="store_true",
                     help="skip the pulsar-term leg (20 pulsars x 4096 walkers)")
+    ap.add_argument("--no-latency", action="store_true",
+                    help="skip the single-walker latency leg (1 pulsar x 1000 TOAs)")
     ap.add_argument("--autotune", choices=["cache", "off", "force"], default="cache",
                     help="cache: use the tuned-plan cache, tuning on a miss; force: retune")
     ap.add_argument("--tune-batch", type=int, default=4096)
@@ -346,6 +348,54 @@ def pulsar_term_leg(args, dev, local):
     return out
 
 
+LATENCY_WORKLOAD = "psr1_toa1000"
+
+
+def latency_leg(args, dev, local):
+    """Latency of one loglik evaluation of one parameter vector on the
+    1-pulsar, 1000-TOA array: the sequential filter (one lane, one thread
+    stepping through the TOAs) against the time-parallel filter (plan mode
+    SCAN).  Each call is a CUDA-graph replay; L2 is flushed before each call,
+    outside the events."""
+    import torch
+
+    from paper_2510_11077_gb300 import argus, inputs
+    w = inputs.WORKLOADS[LATENCY_WORKLOAD]
+    data = inputs.make_workload_array(w.name)
+    theta = torch.from_numpy(inputs.make_theta_batch(data, 1, seed=w.seed)).to(dev)
+    ll = torch.empty(1, dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    out = {"workload": w.name, "metric": "loglik latency", "unit": "us", "walkers": 1}
+    vals = {}
+    for name, plan in (("sequential", dict(mode=argus.ARGUS_MODE_BATCHED, walkers_per_cta=32)),
+                       ("scan", dict(mode=argus.ARGUS_MODE_SCAN))):
+        arr = argus.Array(data, device=local)
+        arr.set_plan(**plan)
+        for _ in range(5):
+            argus.argus_loglik(arr, theta, ll)
+        torch.cuda.synchronize(dev)
+        reps = 200
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(reps)]
+        for k in range(reps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            argus.argus_loglik(arr, theta, ll)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize(dev)
+        us = sorted(a.elapsed_time(b) * 1e3 for a, b in ev)
+        vals[name] = float(ll.item())
+        out[name] = {"median_us": us[reps // 2], "p10_us": us[reps // 10], "p90_us": us[9 * reps // 10],
+                     "plan": arr.get_plan()}
+        arr.close()
+    if vals["sequential"] != vals["scan"] and abs(vals["sequential"] - vals["scan"]) > \
+            1e-12 * abs(vals["sequential"]):
+        raise RuntimeError("scan and sequential filters disagree")
+    out["speedup"] = out["sequential"]["median_us"] / out["scan"]["median_us"]
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -469,6 +519,7 @@ def run_ours(args):
     loglik_leg = None if args.no_loglik else loglik_only(args, dev, local)
     ou = None if args.no_ou else ou_leg(args, dev, local)
     pt_leg = None if args.no_pt else pulsar_term_leg(args, dev, local)
+    lat = None if args.no_latency else latency_leg(args, dev, local)
     lane_steps = B * int(data.n_toa.sum())
     flops = FLOPS_PER_LANE_STEP_GRAD_OU if args.noise == "ou" else FLOPS_PER_LANE_STEP_GRAD
     achieved = flops * lane_steps / (filt_ms * 1e-3) / 1e12
@@ -498,7 +549,7 @@ def run_ours(args):
             "stage_ms": {"project": statistics.mean(k[0] for k in kern), "filter": filt_ms,
                          "reduce": statistics.mean(k[2] for k in kern)},
             "clocks": clk, "cpu_baseline": cpu, "loglik_only": loglik_leg,
-            "ou_red_noise": ou, "pulsar_term": pt_leg}
+            "ou_red_noise": ou, "pulsar_term": pt_leg, "latency_1psr": lat}
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

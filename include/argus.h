@@ -85,8 +85,16 @@ typedef struct argus_array argus_array;
  *   atomic work counter over (pulsar, walker-tile) items sorted by TOA count,
  *   largest first; optionally replayed from a captured CUDA graph.
  * mode ARGUS_MODE_PLAIN: the same kernels launched once per parameter vector
- *   (B launches of P lanes each); the comparison point. */
-enum { ARGUS_MODE_BATCHED = 0, ARGUS_MODE_PLAIN = 1 };
+ *   (B launches of P lanes each); the comparison point.
+ * mode ARGUS_MODE_SCAN: for few lanes (a single parameter vector, a few
+ *   pulsars), argus_loglik and argus_lane_loglik run the time-parallel
+ *   filter: each lane's TOAs are cut into chunks of 32 x scan_elems, one warp
+ *   per chunk, combined by an associative scan (Sarkka & Garcia-Fernandez
+ *   2021) and finished by ordinary Kalman steps; O(N) work, O(scan_elems +
+ *   log N) depth.  It costs ~10x the sequential filter's FP64 work, so it
+ *   pays only while the sequential filter leaves the GPU idle.
+ *   argus_loglik_grad in this mode runs the batched adjoint. */
+enum { ARGUS_MODE_BATCHED = 0, ARGUS_MODE_PLAIN = 1, ARGUS_MODE_SCAN = 2 };
 typedef struct argus_plan {
     int32_t mode;             /* ARGUS_MODE_BATCHED | ARGUS_MODE_PLAIN */
     int32_t walkers_per_cta;  /* lanes of one pulsar per thread block: 32, 64, 128 or 256 */
@@ -98,7 +106,9 @@ typedef struct argus_plan {
                                  during the forward pass and skip the re-run (memory O(N) per
                                  lane: 48 B per TOA per resident lane, 144 B with
                                  ARGUS_NOISE_OU) */
-    int32_t reserved[2];      /* must be 0 */
+    int32_t scan_elems;       /* ARGUS_MODE_SCAN: TOAs per thread, 1..4096; 0 = chosen from the
+                                 batch (about 4 warps per SM) */
+    int32_t reserved;         /* must be 0 */
 } argus_plan;
 
 /* Copy n_pulsars pulsars to device `device` and build the handle.

@@ -20,6 +20,7 @@ from . import build as _build
 
 ARGUS_MODE_BATCHED = 0
 ARGUS_MODE_PLAIN = 1
+ARGUS_MODE_SCAN = 2
 ARGUS_NOISE_RANDOM_WALK = 0
 ARGUS_NOISE_OU = 1
 ARGUS_PULSAR_TERM = 2
@@ -62,7 +63,8 @@ class ArgusPlan(ctypes.Structure):
                 ("ckpt_stride", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32),
                 ("tape_cache", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("scan_elems", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 _lib = None
@@ -200,13 +202,14 @@ class Array:
         p = ArgusPlan()
         _check(_lib.argus_array_get_plan(self.handle, ctypes.byref(p)))
         return dict(mode=p.mode, walkers_per_cta=p.walkers_per_cta, ctas_per_sm=p.ctas_per_sm,
-                    ckpt_stride=p.ckpt_stride, use_graph=p.use_graph, tape_cache=p.tape_cache)
+                    ckpt_stride=p.ckpt_stride, use_graph=p.use_graph, tape_cache=p.tape_cache,
+                    scan_elems=p.scan_elems)
 
     def set_plan(self, **kw) -> None:
         cur = self.get_plan()
         cur.update(kw)
         p = ArgusPlan(cur["mode"], cur["walkers_per_cta"], cur["ctas_per_sm"],
-                      cur["ckpt_stride"], cur["use_graph"], cur["tape_cache"])
+                      cur["ckpt_stride"], cur["use_graph"], cur["tape_cache"], cur["scan_elems"], 0)
         _check(_lib.argus_array_set_plan(self.handle, ctypes.byref(p)))
 
 

@@ -110,6 +110,16 @@ struct argus_array {
     double* d_ckpt = nullptr;      size_t cap_ckpt = 0;
     double* d_tape = nullptr;      size_t cap_tape = 0;
     int* d_counter = nullptr;
+    // time-parallel filter (ARGUS_MODE_SCAN)
+    ScanItem* d_sitems = nullptr;  size_t cap_sitems = 0;
+    int32_t* d_lane_first = nullptr; size_t cap_lane_first = 0;
+    double* d_tpre = nullptr;      size_t cap_tpre = 0;
+    double* d_bagg = nullptr;      size_t cap_bagg = 0;
+    double* d_bpre = nullptr;      size_t cap_bpre = 0;
+    double* d_part = nullptr;      size_t cap_part = 0;
+    int64_t scan_B = -1;
+    int32_t scan_E = 0;
+    int32_t n_sitems = 0;
     // host staging
     double* d_stage = nullptr;     size_t cap_stage = 0;
     // graphs
@@ -141,8 +151,8 @@ argus_plan default_plan() {
 
 argus_status validate_plan(const argus_plan* p) {
     if (!p) return fail(ARGUS_ERR_INVALID_ARG, "plan is NULL");
-    if (p->mode != ARGUS_MODE_BATCHED && p->mode != ARGUS_MODE_PLAIN)
-        return fail(ARGUS_ERR_INVALID_ARG, "plan.mode must be BATCHED or PLAIN");
+    if (p->mode != ARGUS_MODE_BATCHED && p->mode != ARGUS_MODE_PLAIN && p->mode != ARGUS_MODE_SCAN)
+        return fail(ARGUS_ERR_INVALID_ARG, "plan.mode must be BATCHED, PLAIN or SCAN");
     const int w = p->walkers_per_cta;
     if (w != 32 && w != 64 && w != 128 && w != 256)
         return fail(ARGUS_ERR_INVALID_ARG, "plan.walkers_per_cta must be 32, 64, 128 or 256");
@@ -154,8 +164,9 @@ argus_status validate_plan(const argus_plan* p) {
         return fail(ARGUS_ERR_INVALID_ARG, "plan.use_graph must be 0 or 1");
     if (p->tape_cache != 0 && p->tape_cache != 1)
         return fail(ARGUS_ERR_INVALID_ARG, "plan.tape_cache must be 0 or 1");
-    for (int i = 0; i < 2; ++i)
-        if (p->reserved[i] != 0) return fail(ARGUS_ERR_INVALID_ARG, "plan.reserved must be 0");
+    if (p->scan_elems < 0 || p->scan_elems > 4096)
+        return fail(ARGUS_ERR_INVALID_ARG, "plan.scan_elems must be in 0..4096");
+    if (p->reserved != 0) return fail(ARGUS_ERR_INVALID_ARG, "plan.reserved must be 0");
     return ARGUS_OK;
 }
 
@@ -181,6 +192,7 @@ argus_status apply_plan(argus_array* h) {
     CK(cudaMemcpy(h->d_psr, h->h_psr.data(), sizeof(PulsarDev) * h->P, cudaMemcpyHostToDevice));
     drop_graphs(h);
     h->items_B = -1;
+    h->scan_B = -1;
     // the adjoint scratch is sized by the plan (blocks x walkers x segment or
     // tape length): release it so a new plan allocates what it needs rather
     // than keeping the largest buffer any earlier plan used
@@ -265,6 +277,87 @@ FilterArgs make_args(argus_array* h, int64_t B, int W, int grid, bool persistent
     return a;
 }
 
+// Chunks of the time-parallel filter for a batch of B walkers: lanes in
+// lane_out order (p * B + b), each cut into chunks of 32 E TOAs.
+argus_status ensure_scan(argus_array* h, int64_t B) {
+    int64_t E = h->plan.scan_elems;
+    if (E == 0) {
+        const int64_t work = B * h->total_toa;
+        const int64_t warps = int64_t(std::max(h->n_sm, 1)) * 4;
+        E = std::max<int64_t>(1, (work + 32 * warps - 1) / (32 * warps));
+        E = std::min<int64_t>(E, 4096);
+    }
+    if (h->scan_B == B && h->scan_E == E) return ARGUS_OK;
+    const int64_t lanes = B * h->P;
+    std::vector<ScanItem> items;
+    std::vector<int32_t> first(size_t(lanes) + 1, 0);
+    const int64_t chunk = 32 * E;
+    for (int p = 0; p < h->P; ++p) {
+        const int64_t n = h->h_psr[p].n;
+        for (int64_t b = 0; b < B; ++b) {
+            const int64_t lane = int64_t(p) * B + b;
+            first[lane] = int32_t(items.size());
+            for (int64_t k0 = 0; k0 < n; k0 += chunk) {
+                if (items.size() >= size_t(INT32_MAX / 32))
+                    return fail(ARGUS_ERR_UNSUPPORTED, "too many scan chunks: use a batched plan");
+                items.push_back(ScanItem{int32_t(lane), int32_t(k0)});
+            }
+        }
+    }
+    first[lanes] = int32_t(items.size());
+    const size_t ni = std::max<size_t>(items.size(), 1);
+    argus_status st;
+    if ((st = grow(&h->d_sitems, &h->cap_sitems, ni))) return st;
+    if ((st = grow(&h->d_lane_first, &h->cap_lane_first, first.size()))) return st;
+    if ((st = grow(&h->d_tpre, &h->cap_tpre, ni * 32 * kScanElem))) return st;
+    if ((st = grow(&h->d_bagg, &h->cap_bagg, ni * kScanElem))) return st;
+    if ((st = grow(&h->d_bpre, &h->cap_bpre, ni * kScanElem))) return st;
+    if ((st = grow(&h->d_part, &h->cap_part, ni * 2))) return st;
+    if (!items.empty())
+        CK(cudaMemcpy(h->d_sitems, items.data(), sizeof(ScanItem) * items.size(),
+                      cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h->d_lane_first, first.data(), sizeof(int32_t) * first.size(),
+                  cudaMemcpyHostToDevice));
+    h->n_sitems = int32_t(items.size());
+    h->scan_B = B;
+    h->scan_E = int32_t(E);
+    drop_graphs(h);
+    return ARGUS_OK;
+}
+
+// Enqueue one time-parallel loglik evaluation: K1 -> S1..S4 -> K4.
+argus_status enqueue_scan(argus_array* h, const double* theta, int64_t B, double* ll, double* lane,
+                          cudaStream_t s) {
+    if (h->timing) CK(cudaEventRecordWithFlags(h->ev[0], s, cudaEventRecordExternal));
+    launch_project(theta, B, h->P, h->flags, h->d_psr, h->d_lc, s);
+    if (h->timing) CK(cudaEventRecordWithFlags(h->ev[1], s, cudaEventRecordExternal));
+    ScanArgs a{};
+    a.rec = h->d_rec;
+    a.psr = h->d_psr;
+    a.lc = h->d_lc;
+    a.P = h->P;
+    a.B = B;
+    a.items = h->d_sitems;
+    a.n_items = h->n_sitems;
+    a.E = h->scan_E;
+    a.lane_first = h->d_lane_first;
+    a.tpre = h->d_tpre;
+    a.bagg = h->d_bagg;
+    a.bpre = h->d_bpre;
+    a.part = h->d_part;
+    a.lane_out = h->d_lane;
+    a.model = h->model;
+    launch_filter_scan(a, s);
+    if (h->timing) CK(cudaEventRecordWithFlags(h->ev[2], s, cudaEventRecordExternal));
+    launch_reduce(theta, B, h->P, h->flags, h->d_psr, h->d_lane, ll, nullptr, lane, s);
+    if (h->timing) {
+        CK(cudaEventRecordWithFlags(h->ev[3], s, cudaEventRecordExternal));
+        h->timed_once = true;
+    }
+    CK(cudaGetLastError());
+    return ARGUS_OK;
+}
+
 // Enqueue one batched evaluation: K1 -> K2 or K3 -> K4.
 argus_status enqueue_batched(argus_array* h, const double* theta, int64_t B, double* ll,
                              double* grad, double* lane, cudaStream_t s) {
@@ -291,11 +384,21 @@ argus_status enqueue_batched(argus_array* h, const double* theta, int64_t B, dou
 argus_status run_batched(argus_array* h, const double* theta, int64_t B, double* ll, double* grad,
                          double* lane, cudaStream_t s) {
     const int W = h->plan.walkers_per_cta;
+    const bool scan = h->plan.mode == ARGUS_MODE_SCAN && grad == nullptr;
     argus_status st;
-    if ((st = ensure_items(h, B, W))) return st;
-    const int grid = grid_for(h, h->n_items);
-    if ((st = ensure_batch(h, B, W, grid, grad != nullptr))) return st;
-    if (!h->plan.use_graph) return enqueue_batched(h, theta, B, ll, grad, lane, s);
+    if (scan) {
+        if ((st = ensure_batch(h, B, W, 1, false))) return st;
+        if ((st = ensure_scan(h, B))) return st;
+    } else {
+        if ((st = ensure_items(h, B, W))) return st;
+        const int grid = grid_for(h, h->n_items);
+        if ((st = ensure_batch(h, B, W, grid, grad != nullptr))) return st;
+    }
+    auto enqueue = [&](cudaStream_t st_) {
+        return scan ? enqueue_scan(h, theta, B, ll, lane, st_)
+                    : enqueue_batched(h, theta, B, ll, grad, lane, st_);
+    };
+    if (!h->plan.use_graph) return enqueue(s);
 
     GraphKey key{theta, B, ll, grad, lane};
     for (auto& g : h->graphs) {
@@ -307,7 +410,7 @@ argus_status run_batched(argus_array* h, const double* theta, int64_t B, double*
     }
     cudaGraph_t graph = nullptr;
     CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
-    st = enqueue_batched(h, theta, B, ll, grad, lane, h->cap_stream);
+    st = enqueue(h->cap_stream);
     cudaError_t ce = cudaStreamEndCapture(h->cap_stream, &graph);
     if (st) {
         if (graph) cudaGraphDestroy(graph);
@@ -550,6 +653,12 @@ void argus_array_destroy(argus_array* h) {
     cudaFree(h->d_tape);
     cudaFree(h->d_counter);
     cudaFree(h->d_stage);
+    cudaFree(h->d_sitems);
+    cudaFree(h->d_lane_first);
+    cudaFree(h->d_tpre);
+    cudaFree(h->d_bagg);
+    cudaFree(h->d_bpre);
+    cudaFree(h->d_part);
     delete h;
 }
 

@@ -76,6 +76,32 @@ void launch_project(const double* theta, int64_t B, int32_t P, int32_t flags, co
 void launch_filter_fwd(const FilterArgs& a, int W, int grid, cudaStream_t s);
 // K3: forward with checkpoints + reverse sweep -> lane_out[0..7][P][B].
 void launch_filter_grad(const FilterArgs& a, int W, int grid, cudaStream_t s);
+// Time-parallel (associative-scan) forward filter, for few lanes.  A lane's
+// TOAs are cut into chunks of 32 x E; one warp per chunk.
+constexpr int kScanElem = 14;   // doubles per scan element (A 4, b 2, C 3, eta 2, J 3)
+struct ScanItem {
+    int32_t lane;     // p * B + b
+    int32_t k0;       // first TOA of the chunk
+};
+struct ScanArgs {
+    const double* rec;
+    const PulsarDev* psr;
+    const double* lc;         // lane constants [8][P][B]
+    int32_t P;
+    int64_t B;
+    const ScanItem* items;    // [n_items], lanes in order, chunks in order
+    int32_t n_items;
+    int32_t E;                // TOAs per thread
+    const int32_t* lane_first;   // [B P + 1]: items of lane l are lane_first[l] .. [l + 1] - 1
+    double* tpre;             // [n_items * 32][14]: inclusive prefix of each thread in its chunk
+    double* bagg;             // [n_items][14]: chunk aggregates
+    double* bpre;             // [n_items][14]: exclusive prefix of each chunk in its lane
+    double* part;             // [n_items][2]: (sum e^2/S, sum ln S) of the chunk, NaN if invalid
+    double* lane_out;         // [P][B]: ll per lane
+    int32_t model;            // NoiseModel
+};
+void launch_filter_scan(const ScanArgs& a, cudaStream_t s);
+
 // K4: deterministic sum over pulsars (and chain rule through K1 for grad).
 void launch_reduce(const double* theta, int64_t B, int32_t P, int32_t flags, const PulsarDev* psr,
                    const double* lane_out, double* loglik, double* grad, double* lane_ll,

@@ -1,0 +1,115 @@
+"""GPU parity of the time-parallel (associative-scan) filter, plan mode
+ARGUS_MODE_SCAN, against the CPU oracle and against the sequential filter.
+Log-likelihood tolerance as everywhere: |d| <= 1e-9 max(|ll|, 1)."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+from oracle import kalman
+from paper_2510_11077_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+LL_TOL = 1e-9
+
+
+@pytest.fixture(scope="module")
+def argus():
+    from paper_2510_11077_gb300 import argus as a
+    a.load()
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    return a
+
+
+def ll_err(ll, ref):
+    ll, ref = np.asarray(ll), np.asarray(ref)
+    both_inf = np.isneginf(ll) & np.isneginf(ref)
+    with np.errstate(invalid="ignore"):
+        d = np.where(both_inf, 0.0, np.abs(ll - ref) / np.maximum(np.abs(ref), 1.0))
+    return np.nan_to_num(d, nan=np.inf).max()
+
+
+def run_ll(argus, arr, theta):
+    return argus.argus_loglik(arr, torch.from_numpy(np.ascontiguousarray(theta)).cuda()).cpu().numpy()
+
+
+def test_single_pulsar_1000_toas_one_walker(argus):
+    """The few-lane workload the scan is for: 1 pulsar, 1000 TOAs, 1 walker."""
+    w = inputs.WORKLOADS["psr1_toa1000"]
+    data = inputs.make_workload_array(w.name)
+    theta = inputs.make_theta_batch(data, 1, seed=w.seed)
+    arr = argus.argus_array_create(data)
+    ll_seq = run_ll(argus, arr, theta)
+    arr.set_plan(mode=argus.ARGUS_MODE_SCAN)
+    ll = run_ll(argus, arr, theta)
+    assert ll_err(ll, kalman.loglik(data, theta)) <= LL_TOL
+    assert ll_err(ll, ll_seq) <= 1e-12
+
+
+@pytest.mark.parametrize("n", [1, 2, 31, 32, 33, 95, 1000, 4099])
+@pytest.mark.parametrize("elems", [0, 1, 3])
+def test_chunk_edges(argus, n, elems):
+    data = inputs.make_array(np.array([n]), seed=400 + n, equad=1e-8)
+    theta = inputs.make_theta_batch(data, 2, seed=1)
+    arr = argus.argus_array_create(data)
+    arr.set_plan(mode=argus.ARGUS_MODE_SCAN, scan_elems=elems)
+    assert ll_err(run_ll(argus, arr, theta), kalman.loglik(data, theta)) <= LL_TOL
+
+
+@pytest.mark.parametrize("model,pt", [("rw", False), ("ou", False), ("rw", True), ("ou", True)])
+def test_ragged_array_all_models(argus, model, pt):
+    data = inputs.make_array(np.array([0, 1, 37, 200, 513, 1290]), seed=401, equad=2e-8,
+                             model=model, pulsar_term=pt)
+    for kind in ("posterior", "prior"):
+        theta = inputs.make_theta_batch(data, 5, seed=3, kind=kind)
+        arr = argus.argus_array_create(data)
+        arr.set_plan(mode=argus.ARGUS_MODE_SCAN)
+        ll = run_ll(argus, arr, theta)
+        assert ll_err(ll, kalman.loglik(data, theta)) <= LL_TOL
+        lane = argus.argus_lane_loglik(arr, torch.from_numpy(theta).cuda()).cpu().numpy()
+        _, ref = kalman.loglik(data, theta, lanes=True)
+        assert ll_err(lane.ravel(), ref.ravel()) <= LL_TOL
+        assert np.all(lane[:, 0] == 0.0)                   # the empty pulsar
+
+
+def test_long_pulsar_and_equal_times(argus):
+    data = inputs.make_array(np.array([20000, 3]), seed=402, model="ou")
+    a = data.off[0]
+    data.t[a + 100:a + 104] = data.t[a + 100]              # dt = 0 inside a chunk
+    data.t[a + 63:a + 66] = data.t[a + 63]                 # ... and across a chunk edge
+    data.t[a:data.off[1]] = np.sort(data.t[a:data.off[1]])
+    theta = inputs.make_theta_batch(data, 1, seed=4)
+    arr = argus.argus_array_create(data)
+    arr.set_plan(mode=argus.ARGUS_MODE_SCAN, scan_elems=2)
+    assert ll_err(run_ll(argus, arr, theta), kalman.loglik(data, theta)) <= LL_TOL
+
+
+def test_out_of_domain_and_graph_replay(argus):
+    data = inputs.make_array(np.array([300, 700]), seed=403)
+    theta = inputs.make_theta_batch(data, 4, seed=5)
+    theta[1, 8] = -1.0                                     # EFAC < 0
+    theta[2, 0] = np.nan
+    arr = argus.argus_array_create(data)
+    arr.set_plan(mode=argus.ARGUS_MODE_SCAN)
+    th = torch.from_numpy(theta).cuda()
+    out = torch.empty(4, dtype=torch.float64, device="cuda")
+    argus.argus_loglik(arr, th, out)                       # capture
+    first = out.cpu().numpy().copy()
+    for _ in range(3):
+        argus.argus_loglik(arr, th, out)                   # replay
+        assert np.array_equal(out.cpu().numpy(), first)
+    assert np.all(np.isneginf(first[1:3])) and np.all(np.isfinite(first[[0, 3]]))
+    assert ll_err(first, kalman.loglik(data, theta)) <= LL_TOL
+
+
+def test_gradient_in_scan_mode_is_the_adjoints(argus):
+    data = inputs.make_array(np.array([150, 90]), seed=404)
+    theta = inputs.make_theta_batch(data, 3, seed=6)
+    arr = argus.argus_array_create(data)
+    ll0, g0 = argus.argus_loglik_grad(arr, torch.from_numpy(theta).cuda())
+    arr.set_plan(mode=argus.ARGUS_MODE_SCAN)
+    ll1, g1 = argus.argus_loglik_grad(arr, torch.from_numpy(theta).cuda())
+    assert torch.equal(ll0, ll1) and torch.equal(g0, g1)
