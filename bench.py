@@ -17,7 +17,6 @@ on the data path).  Prints one JSON line on rank 0.
 from __future__ import annotations
 
 import argparse
-import hashlib
 import json
 import os
 import statistics
@@ -152,9 +151,8 @@ def traffic_record(kernel: str):
     rec = json.load(open(path)).get(kernel)
     if not rec:
         return None
-    src = os.path.join(ROOT, "paper_2510_11077_gb300", "csrc", "kf_kernels.cu")
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    return rec if rec.get("source_sha") == h else None
+    from paper_2510_11077_gb300 import autotune
+    return rec if rec.get("source_sha") == autotune.source_hash() else None
 
 
 def cpu_baseline(data, theta, seconds):
@@ -372,8 +370,14 @@ def latency_leg(args, dev, local):
                        ("scan", dict(mode=argus.ARGUS_MODE_SCAN))):
         arr = argus.Array(data, device=local)
         arr.set_plan(**plan)
+        arr.set_timing(True)
         for _ in range(5):
             argus.argus_loglik(arr, theta, ll)
+        torch.cuda.synchronize(dev)
+        stages = arr.get_timing()
+        arr.set_timing(False)
+        for _ in range(3):
+            argus.argus_loglik(arr, theta, ll)     # re-capture without the stage events
         torch.cuda.synchronize(dev)
         reps = 200
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -387,7 +391,9 @@ def latency_leg(args, dev, local):
         us = sorted(a.elapsed_time(b) * 1e3 for a, b in ev)
         vals[name] = float(ll.item())
         out[name] = {"median_us": us[reps // 2], "p10_us": us[reps // 10], "p90_us": us[9 * reps // 10],
-                     "plan": arr.get_plan()}
+                     "plan": arr.get_plan(),
+                     "stage_us": {"project": stages[0] * 1e3, "filter": stages[1] * 1e3,
+                                  "reduce": stages[2] * 1e3}}
         arr.close()
     if vals["sequential"] != vals["scan"] and abs(vals["sequential"] - vals["scan"]) > \
             1e-12 * abs(vals["sequential"]):

@@ -35,11 +35,16 @@ DEFAULT_SPACE = {
 }
 
 
-FILTER_SOURCES = ("kf_kernels.cu", "kf_math.cuh", "kf_internal.cuh")
+FILTER_SOURCES = ("kf_kernels.cu", "kf_model.cuh", "kf_math.cuh", "kf_internal.cuh")
+
+
+def source_hash() -> str:
+    return _source_hash()
 
 
 def _source_hash() -> str:
-    """Hash of the filter kernels' sources: a tuned plan is stale once they change."""
+    """Hash of the batched filter kernels' sources: a tuned plan (and a recorded
+    ncu traffic figure) is stale once they change."""
     h = hashlib.sha256()
     csrc = os.path.join(HERE, "csrc")
     for f in FILTER_SOURCES:

@@ -120,6 +120,7 @@ struct argus_array {
     int64_t scan_B = -1;
     int32_t scan_E = 0;
     int32_t n_sitems = 0;
+    double* d_phase_tab = nullptr;
     // host staging
     double* d_stage = nullptr;     size_t cap_stage = 0;
     // graphs
@@ -346,6 +347,7 @@ argus_status enqueue_scan(argus_array* h, const double* theta, int64_t B, double
     a.bpre = h->d_bpre;
     a.part = h->d_part;
     a.lane_out = h->d_lane;
+    a.phase_table = h->d_phase_tab;
     a.model = h->model;
     launch_filter_scan(a, s);
     if (h->timing) CK(cudaEventRecordWithFlags(h->ev[2], s, cudaEventRecordExternal));
@@ -628,6 +630,11 @@ argus_status argus_array_create_ex(const argus_pulsar* psrs, int32_t n_pulsars, 
         return cleanup(cuda_fail(e, "cudaMalloc(pulsars)"));
     if ((e = cudaMalloc(&h->d_counter, sizeof(int))) != cudaSuccess)
         return cleanup(cuda_fail(e, "cudaMalloc(counter)"));
+    if ((e = cudaMalloc(&h->d_phase_tab, sizeof(double) * kPhaseTableDoubles)) != cudaSuccess)
+        return cleanup(cuda_fail(e, "cudaMalloc(phase table)"));
+    launch_fill_phase_table(h->d_phase_tab, nullptr);
+    if ((e = cudaGetLastError()) != cudaSuccess || (e = cudaDeviceSynchronize()) != cudaSuccess)
+        return cleanup(cuda_fail(e, "phase table"));
     if ((e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
         return cleanup(cuda_fail(e, "cudaStreamCreate"));
     argus_status st = apply_plan(h);
@@ -659,6 +666,7 @@ void argus_array_destroy(argus_array* h) {
     cudaFree(h->d_bagg);
     cudaFree(h->d_bpre);
     cudaFree(h->d_part);
+    cudaFree(h->d_phase_tab);
     delete h;
 }
 

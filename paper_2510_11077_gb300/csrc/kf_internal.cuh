@@ -98,9 +98,13 @@ struct ScanArgs {
     double* bpre;             // [n_items][14]: exclusive prefix of each chunk in its lane
     double* part;             // [n_items][2]: (sum e^2/S, sum ln S) of the chunk, NaN if invalid
     double* lane_out;         // [P][B]: ll per lane
+    const double* phase_table;   // the handle's sin/cos(2 pi j / 256) table (kPhaseTableDoubles)
     int32_t model;            // NoiseModel
 };
 void launch_filter_scan(const ScanArgs& a, cudaStream_t s);
+// the sin/cos table of phase_sincos in global memory: 256 double2 then 256 float4
+constexpr int kPhaseTableDoubles = 256 * 4;
+void launch_fill_phase_table(double* tab, cudaStream_t s);
 
 // K4: deterministic sum over pulsars (and chain rule through K1 for grad).
 void launch_reduce(const double* theta, int64_t B, int32_t P, int32_t flags, const PulsarDev* psr,

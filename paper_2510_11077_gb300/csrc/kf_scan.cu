@@ -37,6 +37,13 @@
 
 namespace argus {
 
+__global__ void k_fill_phase_table(double* tab) {
+    fill_phase_table(PhaseTable{reinterpret_cast<double2*>(tab),
+                                reinterpret_cast<float4*>(tab + 2 * kPhaseTable)});
+}
+
+void launch_fill_phase_table(double* tab, cudaStream_t s) { k_fill_phase_table<<<1, 256, 0, s>>>(tab); }
+
 namespace {
 
 constexpr double kLog2PiScan = 1.8378770664093454836;
@@ -55,7 +62,8 @@ __device__ __forceinline__ SElem scan_combine(const SElem& i, const SElem& j) {
     const double M01 = fma(i.C00, j.J01, i.C01 * j.J11);
     const double M10 = fma(i.C01, j.J00, i.C11 * j.J01);
     const double M11 = 1.0 + fma(i.C01, j.J01, i.C11 * j.J11);
-    const double rdet = 1.0 / fma(M00, M11, -M01 * M10);
+    // C_i, J_j are positive semi-definite, so det(I + C_i J_j) >= 1
+    const double rdet = rcp_nr(fma(M00, M11, -M01 * M10));
     const double X00 = M11 * rdet, X01 = -M01 * rdet, X10 = -M10 * rdet, X11 = M00 * rdet;
     // G = A_j X
     const double G00 = fma(j.A00, X00, j.A01 * X10), G01 = fma(j.A00, X01, j.A01 * X11);
@@ -172,20 +180,21 @@ __device__ __forceinline__ Lane scan_lane(const ScanArgs& a, int lane, bool ou, 
     return L;
 }
 
-__device__ __forceinline__ PhaseTable scan_table() {
-    extern __shared__ __align__(16) unsigned char smem_scan[];
+// the handle's sin/cos table in global memory (filled once when the handle is
+// built): a one-warp block would spend longer filling a shared copy than
+// using it
+__device__ __forceinline__ PhaseTable scan_table(const ScanArgs& a) {
+    double* t = const_cast<double*>(a.phase_table);   // read only
     PhaseTable tab;
-    tab.d = reinterpret_cast<double2*>(smem_scan);
-    tab.f = reinterpret_cast<float4*>(smem_scan + kPhaseTable * sizeof(double2));
+    tab.d = reinterpret_cast<double2*>(t);
+    tab.f = reinterpret_cast<float4*>(t + 2 * kPhaseTable);
     return tab;
 }
 
 // S1
 template <bool kOU>
 __global__ void __launch_bounds__(32) k_scan_local(ScanArgs a) {
-    const PhaseTable tab = scan_table();
-    fill_phase_table(tab);
-    __syncwarp();
+    const PhaseTable tab = scan_table(a);
     const ScanItem it = a.items[blockIdx.x];
     const int p = int(it.lane / a.B);
     const PulsarDev& ps = a.psr[p];
@@ -193,7 +202,8 @@ __global__ void __launch_bounds__(32) k_scan_local(ScanArgs a) {
     const int k_lo = it.k0 + int(threadIdx.x) * a.E;
     const int k_hi = min(k_lo + a.E, ps.n);
     SElem agg = scan_identity();
-    for (int k = k_lo; k < k_hi; ++k)
+    if (k_lo < k_hi) agg = scan_element<kOU>(k_lo, a.rec + (ps.off + k_lo) * kRecDoubles, L, tab, ps);
+    for (int k = k_lo + 1; k < k_hi; ++k)
         agg = scan_combine(agg, scan_element<kOU>(k, a.rec + (ps.off + k) * kRecDoubles, L, tab, ps));
     agg = warp_scan(agg);
     store_elem(a.tpre + (int64_t(blockIdx.x) * 32 + threadIdx.x) * kScanElem, agg);
@@ -208,7 +218,8 @@ __global__ void __launch_bounds__(32) k_scan_chunks(ScanArgs a) {
     const int q = (cnt + 31) / 32;
     const int c_lo = int(threadIdx.x) * q, c_hi = min(c_lo + q, cnt);
     SElem agg = scan_identity();
-    for (int c = c_lo; c < c_hi; ++c)
+    if (c_lo < c_hi) agg = load_elem(a.bagg + int64_t(first + c_lo) * kScanElem);
+    for (int c = c_lo + 1; c < c_hi; ++c)
         agg = scan_combine(agg, load_elem(a.bagg + int64_t(first + c) * kScanElem));
     const SElem inc = warp_scan(agg);
     SElem pre = shfl_up_elem(inc, 1);
@@ -222,9 +233,7 @@ __global__ void __launch_bounds__(32) k_scan_chunks(ScanArgs a) {
 // S3
 template <bool kOU>
 __global__ void __launch_bounds__(32) k_scan_finish(ScanArgs a) {
-    const PhaseTable tab = scan_table();
-    fill_phase_table(tab);
-    __syncwarp();
+    const PhaseTable tab = scan_table(a);
     const ScanItem it = a.items[blockIdx.x];
     const int p = int(it.lane / a.B);
     const PulsarDev& ps = a.psr[p];
@@ -236,11 +245,15 @@ __global__ void __launch_bounds__(32) k_scan_finish(ScanArgs a) {
     if (k_lo < k_hi) {
         State x{0.0, 0.0, ps.p0[0], ps.p0[1], ps.p0[2]};
         if (k_lo > 0) {
-            // filtered state at TOA k_lo - 1: chunk prefix x earlier threads of the chunk
-            SElem pre = load_elem(a.bpre + int64_t(blockIdx.x) * kScanElem);
-            if (threadIdx.x > 0)
-                pre = scan_combine(pre, load_elem(a.tpre + (int64_t(blockIdx.x) * 32 + threadIdx.x - 1) *
-                                                               kScanElem));
+            // filtered state at TOA k_lo - 1: chunk prefix x earlier threads of
+            // the chunk (the lane's first chunk has no prefix)
+            SElem pre;
+            if (threadIdx.x == 0) {
+                pre = load_elem(a.bpre + int64_t(blockIdx.x) * kScanElem);
+            } else {
+                pre = load_elem(a.tpre + (int64_t(blockIdx.x) * 32 + threadIdx.x - 1) * kScanElem);
+                if (it.k0 > 0) pre = scan_combine(load_elem(a.bpre + int64_t(blockIdx.x) * kScanElem), pre);
+            }
             x = State{pre.b0, pre.b1, pre.C00, pre.C01, pre.C11};
         }
         StepOut so;
@@ -280,7 +293,7 @@ __global__ void k_scan_sum(ScanArgs a) {
 }  // namespace
 
 void launch_filter_scan(const ScanArgs& a, cudaStream_t s) {
-    const size_t smem = kPhaseTableBytes;
+    const size_t smem = 0;
     const bool ou = a.model == kOrnsteinUhlenbeck;
     const int lanes = int(a.B * a.P);
     if (a.n_items > 0) {
