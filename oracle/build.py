@@ -8,8 +8,8 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libargus_oracle.so")
-SOURCES = ["kalman.c"]
-HEADERS = ["kf_body.h"]
+SOURCES = ["kalman.c", "gwb.c"]
+HEADERS = ["kf_body.h", "ou_phi.h", "gwb_body.h"]
 
 
 def _stale() -> bool:

@@ -209,3 +209,87 @@ def grad(data, theta, h=1e-20):
         g[N_GW + k * p] = 0.5 * np.sum(M * dC_ls)
         g[N_GW + k * p + (2 if ou else 1)] = 0.5 * np.sum(np.diag(M) * 2.0 * efac * sig ** 2)
     return g
+
+
+# ---------------------------------------------------------------------------
+# Joint likelihood with a Hellings-Downs correlated GW background (the model
+# stated in gwb_body.h): per pulsar rho integrates its own OU red noise y and
+# the GW redshift a; the a_n are stationary OU processes (damping gamma_a)
+# whose driving noises are correlated across pulsars by the HD matrix G, with
+# amplitude h_a.  The residual covariance, all TOAs of all pulsars, is
+#   C = blockdiag_n(C_int,n + R_n) + h_a^2 (G_nm K(t_i, t_j))_{(n,i),(m,j)},
+# C_int,n the OU-integrated covariance from the prior P0_n at the array's
+# earliest TOA t_0, and K the covariance of the time integrals from t_0 of a
+# stationary unit-noise OU process:
+#   K(u, v) = int_0^u int_0^v e^{-gamma |s - s'|} ds ds' / (2 gamma)
+#           = [2 E(gamma m) + g(gamma m) g(gamma |u - v|)] / (2 gamma^3),
+#   m = min(u, v),  g(x) = 1 - e^-x,  E(x) = x - g(x)   (both terms >= 0).
+# ---------------------------------------------------------------------------
+def hellings_downs(pos):
+    pos = np.asarray(pos, dtype=np.float64)
+    c = np.clip(pos @ pos.T, -1.0, 1.0)
+    x = 0.5 * (1.0 - c)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        G = np.where(x > 0, 1.5 * x * np.log(np.where(x > 0, x, 1.0)), 0.0) - 0.25 * x + 0.5
+    np.fill_diagonal(G, 1.0)
+    return G
+
+
+def _E(x):
+    """x - (1 - e^-x), without cancellation."""
+    x = np.asarray(x, dtype=np.float64)
+    small = x < 0.1
+    xs = np.where(small, x, 0.0)
+    ser = np.zeros_like(x)
+    term = xs * xs / 2.0
+    for k in range(2, 20):
+        ser = ser + term
+        term = -term * xs / (k + 1)
+    return np.where(small, ser, x + np.expm1(-np.where(small, 1.0, x)))
+
+
+def gw_integrated_kernel(u, v, gam):
+    """K(u, v) for arrays u [n], v [m] (seconds since t_0)."""
+    u = np.asarray(u, dtype=np.float64)[:, None]
+    v = np.asarray(v, dtype=np.float64)[None, :]
+    mn = np.minimum(u, v)
+    d = np.abs(u - v)
+    g = lambda z: -np.expm1(-z)
+    return (2.0 * _E(gam * mn) + g(gam * mn) * g(gam * d)) / (2.0 * gam ** 3)
+
+
+def gwb_covariance(data, theta):
+    P = data.n_pulsars
+    t0 = data.t.min() if len(data.t) else 0.0
+    G = hellings_downs(data.pos)
+    ha2, ga = 10.0 ** (2.0 * theta[0]), 10.0 ** theta[1]
+    blocks = []
+    for p in range(P):
+        t, r, sig = data.pulsar(p)
+        ls, lg, efac = theta[2 + 3 * p: 5 + 3 * p]
+        R = efac ** 2 * sig ** 2 + data.equad[p] ** 2
+        Ci = ou_covariance(np.concatenate([[t0], t]), 10.0 ** (2 * ls), 10.0 ** lg, data.p0[p], 0.0)[1:, 1:]
+        blocks.append(Ci + np.diag(R))
+    n = len(data.t)
+    C = np.zeros((n, n))
+    for a in range(P):
+        ta = data.pulsar(a)[0] - t0
+        sa = slice(data.off[a], data.off[a + 1])
+        C[sa, sa] += blocks[a]
+        for b in range(P):
+            tb = data.pulsar(b)[0] - t0
+            sb = slice(data.off[b], data.off[b + 1])
+            C[sa, sb] += ha2 * G[a, b] * gw_integrated_kernel(ta, tb, ga)
+    return C
+
+
+def gwb_loglik(data, theta):
+    theta = np.atleast_2d(theta)
+    out = []
+    for th in theta:
+        C = gwb_covariance(data, th)
+        cf = cho_factor(C, lower=True)
+        alpha = cho_solve(cf, data.r)
+        logdet = 2.0 * np.sum(np.log(np.diag(cf[0])))
+        out.append(-0.5 * (data.r @ alpha + logdet + len(data.r) * np.log(2.0 * np.pi)))
+    return np.array(out)

@@ -50,10 +50,10 @@ MUTATIONS = {
     "ou_q11_phi": ("kf_body.h", "q11 = q11 * p2;", "q11 = q11 * p1;"),
     "ou_a01_no_decay": ("kf_body.h", "KF_T a01 = a * (p01 + b * p11) + q01;", "KF_T a01 = p01 + b * p11 + q01;"),
     "ou_a11_decay_once": ("kf_body.h", "KF_T a11 = a * a * p11 + q11;", "KF_T a11 = a * p11 + q11;"),
-    "ou_phi4_series": ("kf_body.h", "(2.0 - pow(2.0, m + 2))", "(2.0 - pow(2.0, m + 1))"),
-    "ou_phi1_series_sign": ("kf_body.h", "double c1 = ((m & 1) ? -1.0 : 1.0) / f1;", "double c1 = 1.0 / f1;"),
-    "ou_phi2_closed": ("kf_body.h", "*p2 = (1.0 - e2) / (2.0 * x);", "*p2 = (1.0 - e2) / x;"),
-    "ou_phi4_closed": ("kf_body.h", "0.5 * (1.0 - e2)) / (x * x * x)", "(1.0 - e2)) / (x * x * x)"),
+    "ou_phi4_series": ("ou_phi.h", "(2.0 - pow(2.0, m + 2))", "(2.0 - pow(2.0, m + 1))"),
+    "ou_phi1_series_sign": ("ou_phi.h", "double c1 = ((m & 1) ? -1.0 : 1.0) / f1;", "double c1 = 1.0 / f1;"),
+    "ou_phi2_closed": ("ou_phi.h", "*p2 = (1.0 - e2) / (2.0 * x);", "*p2 = (1.0 - e2) / x;"),
+    "ou_phi4_closed": ("ou_phi.h", "0.5 * (1.0 - e2)) / (x * x * x)", "(1.0 - e2)) / (x * x * x)"),
     "ou_gamma_index": ("kalman.c", "cplx gam = a->ou ? cpow(10.0, nz[1]) : 0.0;",
                        "cplx gam = a->ou ? cpow(10.0, nz[0]) : 0.0;"),
     # the wave's pulsar term
@@ -73,7 +73,7 @@ MUTATIONS = {
 def _build_variant(tmp, name, mut):
     d = os.path.join(tmp, name)
     os.makedirs(d)
-    for f in ("kalman.c", "kf_body.h"):
+    for f in ("kalman.c", "kf_body.h", "ou_phi.h"):
         shutil.copy(os.path.join(ORACLE_DIR, f), d)
     if mut is not None:
         fname, old, new = mut
