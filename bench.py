@@ -79,6 +79,8 @@ def parse_args():
                     help="skip the pulsar-term leg (20 pulsars x 4096 walkers)")
     ap.add_argument("--no-latency", action="store_true",
                     help="skip the single-walker latency leg (1 pulsar x 1000 TOAs)")
+    ap.add_argument("--no-gwb", action="store_true",
+                    help="skip the Hellings-Downs GW-background leg (20 pulsars, joint filter)")
     ap.add_argument("--autotune", choices=["cache", "off", "force"], default="cache",
                     help="cache: use the tuned-plan cache, tuning on a miss; force: retune")
     ap.add_argument("--tune-batch", type=int, default=4096)
@@ -347,6 +349,67 @@ def pulsar_term_leg(args, dev, local):
 
 
 LATENCY_WORKLOAD = "psr1_toa1000"
+GWB_BATCH = 1216
+
+
+def gwb_flops_per_toa(P: int) -> int:
+    """Algorithmic FP64 flops of one TOA of the joint filter (FMA = 2): the
+    predict of each upper 3x3 block (F_I X: 18, (F_I X) F_J^T: 18, Q: 8), the
+    symmetric rank-1 update of the 3P x 3P covariance (3 per upper entry) and
+    the mean (10 per pulsar)."""
+    n = 3 * P
+    return 44 * P * (P + 1) // 2 + 3 * n * (n + 1) // 2 + 10 * P
+
+
+def gwb_leg(args, dev, local):
+    """Joint likelihood with a Hellings-Downs correlated GW background on the
+    20-pulsar array (26,182 TOAs, 60-dimensional joint state): evals/s with
+    GWB_BATCH parameter vectors, and the FP64 roofline of the joint filter."""
+    import numpy as np
+    import torch
+
+    from paper_2510_11077_gb300 import argus, inputs
+    w = inputs.WORKLOADS[LOGLIK_WORKLOAD]
+    data = inputs.make_workload_array(w.name)
+    P = data.n_pulsars
+    rng = np.random.default_rng(w.seed)
+    th = np.empty((GWB_BATCH, 2 + 3 * P))
+    th[:, 0] = rng.uniform(-20.0, -18.5, GWB_BATCH)
+    th[:, 1] = rng.uniform(-9.5, -7.5, GWB_BATCH)
+    th[:, 2::3] = rng.uniform(-20.8, -19.2, (GWB_BATCH, P))
+    th[:, 3::3] = rng.uniform(-9.8, -7.2, (GWB_BATCH, P))
+    th[:, 4::3] = rng.uniform(0.85, 1.15, (GWB_BATCH, P))
+    theta = torch.from_numpy(th).to(dev)
+    arr = argus.GwbArray(data, device=local)
+    ll = torch.empty(GWB_BATCH, dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    argus.argus_gwb_loglik(arr, theta, ll)
+    torch.cuda.synchronize(dev)
+    reps = 3
+    ms = []
+    for _ in range(reps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        argus.argus_gwb_loglik(arr, theta, ll)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms.append(e0.elapsed_time(e1))
+    arr.close()
+    step_ms = statistics.mean(ms)
+    n_toa = int(data.n_toa.sum())
+    flops = gwb_flops_per_toa(P) * n_toa * GWB_BATCH
+    achieved = flops / (step_ms * 1e-3) / 1e12
+    return {"workload": w.name + " (joint filter, Hellings-Downs GW background)", "dim": 2 + 3 * P,
+            "state_dim": 3 * P, "batch": GWB_BATCH, "metric": "loglik evals/s",
+            "value": GWB_BATCH / (step_ms * 1e-3), "ms_per_step": step_ms,
+            "finite": bool(torch.isfinite(ll).all().item()),
+            "roofline": {"bound": "alu", "kernel": "k_gwb_filter", "kernel_ms": step_ms,
+                         "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved / FP64_PEAK_TFLOPS,
+                         "algorithmic": f"{gwb_flops_per_toa(P)} FP64 flop per TOA per parameter vector x "
+                                        f"{n_toa} TOAs x {GWB_BATCH}"}}
 
 
 def latency_leg(args, dev, local):
@@ -526,6 +589,7 @@ def run_ours(args):
     ou = None if args.no_ou else ou_leg(args, dev, local)
     pt_leg = None if args.no_pt else pulsar_term_leg(args, dev, local)
     lat = None if args.no_latency else latency_leg(args, dev, local)
+    gwb_l = None if args.no_gwb else gwb_leg(args, dev, local)
     lane_steps = B * int(data.n_toa.sum())
     flops = FLOPS_PER_LANE_STEP_GRAD_OU if args.noise == "ou" else FLOPS_PER_LANE_STEP_GRAD
     achieved = flops * lane_steps / (filt_ms * 1e-3) / 1e12
@@ -555,7 +619,7 @@ def run_ours(args):
             "stage_ms": {"project": statistics.mean(k[0] for k in kern), "filter": filt_ms,
                          "reduce": statistics.mean(k[2] for k in kern)},
             "clocks": clk, "cpu_baseline": cpu, "loglik_only": loglik_leg,
-            "ou_red_noise": ou, "pulsar_term": pt_leg, "latency_1psr": lat}
+            "ou_red_noise": ou, "pulsar_term": pt_leg, "latency_1psr": lat, "gwb_hd": gwb_l}
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -116,6 +116,15 @@ def load(build_if_missing: bool = False):
     lib.argus_array_set_timing.restype = ctypes.c_int
     lib.argus_array_get_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
     lib.argus_array_get_timing.restype = ctypes.c_int
+    lib.argus_gwb_create.argtypes = [ctypes.POINTER(ArgusPulsar), ctypes.c_int32, ctypes.c_int32,
+                                     ctypes.POINTER(vp)]
+    lib.argus_gwb_create.restype = ctypes.c_int
+    lib.argus_gwb_destroy.argtypes = [vp]
+    lib.argus_gwb_destroy.restype = None
+    lib.argus_gwb_dim.argtypes = [vp]
+    lib.argus_gwb_dim.restype = ctypes.c_int32
+    lib.argus_gwb_loglik.argtypes = [vp, dp, ctypes.c_int64, dp, vp]
+    lib.argus_gwb_loglik.restype = ctypes.c_int
     lib.argus_status_string.argtypes = [ctypes.c_int]
     lib.argus_status_string.restype = ctypes.c_char_p
     lib.argus_last_error.argtypes = []
@@ -144,6 +153,61 @@ def _stream_of(*tensors):
         if isinstance(t, torch.Tensor) and t.is_cuda:
             return torch.cuda.current_stream(t.device).cuda_stream
     return None
+
+
+def _pulsar_structs(data):
+    P = data.n_pulsars
+    keep = []
+    ps = (ArgusPulsar * P)()
+    dp = ctypes.POINTER(ctypes.c_double)
+    for p in range(P):
+        t, r, s = (np.ascontiguousarray(a, dtype=np.float64) for a in data.pulsar(p))
+        keep += [t, r, s]
+        ps[p].n_toa = len(t)
+        ps[p].t = t.ctypes.data_as(dp)
+        ps[p].r = r.ctypes.data_as(dp)
+        ps[p].sigma = s.ctypes.data_as(dp)
+        ps[p].pos[:] = [float(v) for v in data.pos[p]]
+        ps[p].equad = float(data.equad[p])
+        ps[p].p0[:] = [float(v) for v in data.p0[p]]
+    return ps, keep
+
+
+class GwbArray:
+    """Handle of the joint likelihood with a Hellings-Downs correlated GW
+    background (argus_gwb_create, include/argus_gwb.h); theta = [log10 h_a,
+    log10 gamma_a, (log10 sigma_p, log10 gamma_p, EFAC_p) per pulsar]."""
+
+    def __init__(self, data, device: int = 0):
+        lib = load()
+        ps, keep = _pulsar_structs(data)
+        h = ctypes.c_void_p()
+        _check(lib.argus_gwb_create(ps, data.n_pulsars, device, ctypes.byref(h)))
+        self.handle = h
+        self.n_pulsars = data.n_pulsars
+        self.dim = lib.argus_gwb_dim(h)
+        self.device = device
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib.argus_gwb_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def argus_gwb_loglik(array: GwbArray, theta, loglik=None, stream=None):
+    theta = _prep(theta, array.dim)
+    B = theta.shape[0]
+    if loglik is None:
+        loglik = _new_like(theta, (B,))
+    s = stream if stream is not None else _stream_of(theta, loglik)
+    _check(_lib.argus_gwb_loglik(array.handle, _ptr(theta), B, _ptr(loglik), s))
+    return loglik
 
 
 class Array:

@@ -27,6 +27,60 @@ argus_status fail(argus_status st, const std::string& msg) {
     return st;
 }
 
+}  // namespace
+
+// the last-error record shared by every entry point of the library
+int argus::record_error(int status, const char* msg) {
+    g_last_error = msg ? msg : "";
+    return status;
+}
+
+// Host validation of pulsar data shared by every handle constructor: sorted
+// finite TOAs, positive errors, unit positions, EQUAD >= 0, a positive
+// semi-definite prior.  Returns ARGUS_OK and the TOA count, or the status.
+int argus::validate_pulsars(const argus_pulsar* psrs, int32_t n_pulsars, int64_t* total_out) {
+    int64_t total = 0;
+    for (int p = 0; p < n_pulsars; ++p) {
+        const argus_pulsar& ps = psrs[p];
+        char buf[160];
+        if (ps.n_toa < 0 || ps.n_toa > INT32_MAX) {
+            snprintf(buf, sizeof buf, "pulsar %d: n_toa out of range", p);
+            return fail(ARGUS_ERR_INVALID_ARG, buf);
+        }
+        if (ps.n_toa > 0 && (!ps.t || !ps.r || !ps.sigma)) {
+            snprintf(buf, sizeof buf, "pulsar %d: NULL data", p);
+            return fail(ARGUS_ERR_INVALID_ARG, buf);
+        }
+        for (int64_t k = 0; k < ps.n_toa; ++k) {
+            if (!std::isfinite(ps.t[k]) || !std::isfinite(ps.r[k]) || !std::isfinite(ps.sigma[k]) ||
+                !(ps.sigma[k] > 0.0) || (k > 0 && ps.t[k] < ps.t[k - 1])) {
+                snprintf(buf, sizeof buf, "pulsar %d TOA %lld: non-finite, unsorted or sigma <= 0", p,
+                         (long long)k);
+                return fail(ARGUS_ERR_INVALID_ARG, buf);
+            }
+        }
+        const double nrm = std::sqrt(ps.pos[0] * ps.pos[0] + ps.pos[1] * ps.pos[1] + ps.pos[2] * ps.pos[2]);
+        if (!(std::fabs(nrm - 1.0) <= 1e-6)) {
+            snprintf(buf, sizeof buf, "pulsar %d: position is not a unit vector", p);
+            return fail(ARGUS_ERR_INVALID_ARG, buf);
+        }
+        if (!(ps.equad >= 0.0) || !std::isfinite(ps.equad)) {
+            snprintf(buf, sizeof buf, "pulsar %d: EQUAD must be finite and >= 0", p);
+            return fail(ARGUS_ERR_INVALID_ARG, buf);
+        }
+        if (!(ps.p0[0] >= 0.0 && ps.p0[2] >= 0.0 && ps.p0[0] * ps.p0[2] >= ps.p0[1] * ps.p0[1]) ||
+            !std::isfinite(ps.p0[1])) {
+            snprintf(buf, sizeof buf, "pulsar %d: prior covariance is not positive semi-definite", p);
+            return fail(ARGUS_ERR_INVALID_ARG, buf);
+        }
+        total += ps.n_toa;
+    }
+    *total_out = total;
+    return ARGUS_OK;
+}
+
+namespace {
+
 argus_status cuda_fail(cudaError_t e, const char* what) {
     std::string m = std::string(what) + ": " + cudaGetErrorString(e);
     return fail(e == cudaErrorMemoryAllocation ? ARGUS_ERR_OOM : ARGUS_ERR_CUDA, m);
@@ -535,41 +589,7 @@ argus_status argus_array_create_ex(const argus_pulsar* psrs, int32_t n_pulsars, 
     if (!psrs || n_pulsars < 1) return fail(ARGUS_ERR_INVALID_ARG, "need at least one pulsar");
     if (device < 0) return fail(ARGUS_ERR_INVALID_ARG, "device must be >= 0");
     int64_t total = 0;
-    for (int p = 0; p < n_pulsars; ++p) {
-        const argus_pulsar& ps = psrs[p];
-        char buf[160];
-        if (ps.n_toa < 0 || ps.n_toa > INT32_MAX) {
-            snprintf(buf, sizeof buf, "pulsar %d: n_toa out of range", p);
-            return fail(ARGUS_ERR_INVALID_ARG, buf);
-        }
-        if (ps.n_toa > 0 && (!ps.t || !ps.r || !ps.sigma)) {
-            snprintf(buf, sizeof buf, "pulsar %d: NULL data", p);
-            return fail(ARGUS_ERR_INVALID_ARG, buf);
-        }
-        for (int64_t k = 0; k < ps.n_toa; ++k) {
-            if (!std::isfinite(ps.t[k]) || !std::isfinite(ps.r[k]) || !std::isfinite(ps.sigma[k]) ||
-                !(ps.sigma[k] > 0.0) || (k > 0 && ps.t[k] < ps.t[k - 1])) {
-                snprintf(buf, sizeof buf, "pulsar %d TOA %lld: non-finite, unsorted or sigma <= 0", p,
-                         (long long)k);
-                return fail(ARGUS_ERR_INVALID_ARG, buf);
-            }
-        }
-        const double nrm = std::sqrt(ps.pos[0] * ps.pos[0] + ps.pos[1] * ps.pos[1] + ps.pos[2] * ps.pos[2]);
-        if (!(std::fabs(nrm - 1.0) <= 1e-6)) {
-            snprintf(buf, sizeof buf, "pulsar %d: position is not a unit vector", p);
-            return fail(ARGUS_ERR_INVALID_ARG, buf);
-        }
-        if (!(ps.equad >= 0.0) || !std::isfinite(ps.equad)) {
-            snprintf(buf, sizeof buf, "pulsar %d: EQUAD must be finite and >= 0", p);
-            return fail(ARGUS_ERR_INVALID_ARG, buf);
-        }
-        if (!(ps.p0[0] >= 0.0 && ps.p0[2] >= 0.0 && ps.p0[0] * ps.p0[2] >= ps.p0[1] * ps.p0[1]) ||
-            !std::isfinite(ps.p0[1])) {
-            snprintf(buf, sizeof buf, "pulsar %d: prior covariance is not positive semi-definite", p);
-            return fail(ARGUS_ERR_INVALID_ARG, buf);
-        }
-        total += ps.n_toa;
-    }
+    if (argus_status st = argus_status(validate_pulsars(psrs, n_pulsars, &total))) return st;
     // host validation is complete; now the device
     int ndev = 0;
     CK(cudaGetDeviceCount(&ndev));

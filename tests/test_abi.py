@@ -105,6 +105,20 @@ def test_model_flags_of_array_data():
     assert argus.model_name(argus.model_flags(d)) == "ou+pt" and d.dim == 7 + 4 * 2
 
 
+def test_gwb_create_rejects_too_many_pulsars_and_bad_data(lib):
+    data = inputs.make_array(np.full(49, 3), seed=2)
+    ps, keep = _pulsars(data)
+    h = ctypes.c_void_p()
+    assert lib.argus_gwb_create(ps, 49, 0, ctypes.byref(h)) == 6 and h.value is None
+    assert b"48" in lib.argus_last_error()
+    data = inputs.make_array(np.array([10, 10]), seed=3)
+    data.sigma[4] = -1.0
+    ps, keep = _pulsars(data)
+    assert lib.argus_gwb_create(ps, 2, 0, ctypes.byref(h)) == 1 and h.value is None
+    assert lib.argus_gwb_dim(None) == -1
+    assert lib.argus_gwb_loglik(None, None, 1, None, None) == 1
+
+
 def test_calls_on_null_handle_are_rejected(lib):
     assert lib.argus_loglik(None, None, 1, None, None) == 1
     assert lib.argus_array_set_plan(None, None) == 1

@@ -1,0 +1,106 @@
+"""GPU parity of the joint likelihood with a Hellings-Downs correlated GW
+background (include/argus_gwb.h) against the CPU oracle (oracle/gwb.c).
+Tolerance as everywhere: |d| <= 1e-9 max(|ll|, 1)."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+from oracle import gwb
+from paper_2510_11077_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+LL_TOL = 1e-9
+
+
+@pytest.fixture(scope="module")
+def argus():
+    from paper_2510_11077_gb300 import argus as a
+    a.load()
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    return a
+
+
+def ll_err(ll, ref):
+    ll, ref = np.asarray(ll), np.asarray(ref)
+    both_inf = np.isneginf(ll) & np.isneginf(ref)
+    with np.errstate(invalid="ignore"):
+        d = np.where(both_inf, 0.0, np.abs(ll - ref) / np.maximum(np.abs(ref), 1.0))
+    return np.nan_to_num(d, nan=np.inf).max()
+
+
+def thetas(P, B, rng, lh=(-20.5, -18.0), lg=(-10.0, -7.0)):
+    th = np.empty((B, 2 + 3 * P))
+    th[:, 0] = rng.uniform(*lh, B)
+    th[:, 1] = rng.uniform(*lg, B)
+    th[:, 2::3] = rng.uniform(-20.8, -19.2, (B, P))
+    th[:, 3::3] = rng.uniform(-9.8, -7.2, (B, P))
+    th[:, 4::3] = rng.uniform(0.85, 1.15, (B, P))
+    return th
+
+
+def run(argus, arr, theta):
+    return argus.argus_gwb_loglik(arr, torch.from_numpy(np.ascontiguousarray(theta)).cuda()).cpu().numpy()
+
+
+@pytest.mark.parametrize("sizes", [[40], [30, 50, 20], [0, 25, 1, 60], [15] * 8])
+def test_parity_small_arrays(argus, sizes):
+    data = inputs.make_array(np.array(sizes), seed=500 + len(sizes), equad=1e-8)
+    theta = thetas(len(sizes), 24, np.random.default_rng(len(sizes)))
+    arr = argus.GwbArray(data)
+    assert arr.dim == 2 + 3 * len(sizes)
+    assert ll_err(run(argus, arr, theta), gwb.loglik(data, theta)) <= LL_TOL
+
+
+def test_equal_times_across_pulsars(argus):
+    data = inputs.make_array(np.array([40, 35, 25]), seed=501)
+    a, b = data.off[1], data.off[2]
+    data.t[a:a + 10] = data.t[3:13]                      # pulsar 1 shares ten TOA times with pulsar 0
+    data.t[a:b] = np.sort(data.t[a:b])
+    data.t[b + 2:b + 5] = data.t[b + 2]                  # and pulsar 2 repeats one of its own
+    theta = thetas(3, 16, np.random.default_rng(2))
+    arr = argus.GwbArray(data)
+    assert ll_err(run(argus, arr, theta), gwb.loglik(data, theta)) <= LL_TOL
+
+
+def test_twenty_pulsars(argus):
+    """20 pulsars (the 60-dimensional joint state of the 20-pulsar workload),
+    100 TOAs each so that the oracle's dense algebra finishes in seconds."""
+    rng = np.random.default_rng(3)
+    data = inputs.make_array(np.full(20, 100), seed=502, equad=1e-8)
+    theta = thetas(20, 6, rng)
+    arr = argus.GwbArray(data)
+    assert ll_err(run(argus, arr, theta), gwb.loglik(data, theta)) <= LL_TOL
+
+
+def test_largest_supported_array(argus):
+    data = inputs.make_array(np.full(48, 6), seed=503)
+    theta = thetas(48, 3, np.random.default_rng(4))
+    arr = argus.GwbArray(data)
+    assert ll_err(run(argus, arr, theta), gwb.loglik(data, theta)) <= LL_TOL
+
+
+def test_out_of_domain_and_host_pointers(argus):
+    data = inputs.make_array(np.array([30, 40]), seed=504)
+    theta = thetas(2, 5, np.random.default_rng(5))
+    theta[0, 4] = 0.0           # EFAC of pulsar 0
+    theta[1, 0] = np.inf
+    arr = argus.GwbArray(data)
+    ll_dev = run(argus, arr, theta)
+    ll_host = argus.argus_gwb_loglik(arr, theta)        # numpy in, numpy out (staged)
+    assert np.array_equal(ll_dev, ll_host)
+    assert np.all(np.isneginf(ll_dev[:2])) and np.all(np.isfinite(ll_dev[2:]))
+    assert ll_err(ll_dev, gwb.loglik(data, theta)) <= LL_TOL
+
+
+def test_batch_larger_than_the_grid(argus):
+    """More parameter vectors than resident blocks: the grid-stride loop."""
+    data = inputs.make_array(np.array([12, 9]), seed=505)
+    theta = thetas(2, 3000, np.random.default_rng(6))
+    arr = argus.GwbArray(data)
+    ll = run(argus, arr, theta)
+    idx = np.array([0, 1, 1215, 1216, 2999])
+    assert ll_err(ll[idx], gwb.loglik(data, theta[idx])) <= LL_TOL
