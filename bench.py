@@ -81,6 +81,8 @@ def parse_args():
                     help="skip the single-walker latency leg (1 pulsar x 1000 TOAs)")
     ap.add_argument("--no-gwb", action="store_true",
                     help="skip the Hellings-Downs GW-background leg (20 pulsars, joint filter)")
+    ap.add_argument("--gwb-batch", type=int, default=1216,
+                    help="parameter vectors of the GW-background leg")
     ap.add_argument("--autotune", choices=["cache", "off", "force"], default="cache",
                     help="cache: use the tuned-plan cache, tuning on a miss; force: retune")
     ap.add_argument("--tune-batch", type=int, default=4096)
@@ -349,7 +351,6 @@ def pulsar_term_leg(args, dev, local):
 
 
 LATENCY_WORKLOAD = "psr1_toa1000"
-GWB_BATCH = 1216
 
 
 def gwb_flops_per_toa(P: int) -> int:
@@ -364,7 +365,7 @@ def gwb_flops_per_toa(P: int) -> int:
 def gwb_leg(args, dev, local):
     """Joint likelihood with a Hellings-Downs correlated GW background on the
     20-pulsar array (26,182 TOAs, 60-dimensional joint state): evals/s with
-    GWB_BATCH parameter vectors, and the FP64 roofline of the joint filter."""
+    --gwb-batch parameter vectors, and the FP64 roofline of the joint filter."""
     import numpy as np
     import torch
 
@@ -372,6 +373,7 @@ def gwb_leg(args, dev, local):
     w = inputs.WORKLOADS[LOGLIK_WORKLOAD]
     data = inputs.make_workload_array(w.name)
     P = data.n_pulsars
+    GWB_BATCH = args.gwb_batch
     rng = np.random.default_rng(w.seed)
     th = np.empty((GWB_BATCH, 2 + 3 * P))
     th[:, 0] = rng.uniform(-20.0, -18.5, GWB_BATCH)

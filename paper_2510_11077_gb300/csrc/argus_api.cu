@@ -15,6 +15,7 @@
 
 #include "../../include/argus.h"
 #include "kf_internal.cuh"
+#include "lib_internal.cuh"
 
 using namespace argus;
 

@@ -9,15 +9,15 @@
 //      (a_p, b_p, Q_p / sigma_p^2 by ou_coef) and the GW process's;
 //   2. predict: F is block diagonal (3 x 3 per pulsar,
 //      F_n = [[1, b_p, b_a], [0, a_p, 0], [0, 0, a_a]]), so each 3 x 3 block
-//      of P becomes F_I P_IJ F_J^T + Q_IJ on its own; only blocks I <= J are
-//      computed and mirrored, keeping P exactly symmetric.  Q_IJ holds the
-//      intrinsic noise (I = J) and h_a^2 G_IJ times the integrated-OU
-//      increment covariance of the GW process in the (rho, a) slots;
+//      of P becomes F_I P_IJ F_J^T + Q_IJ on its own.  P is symmetric and
+//      only its upper triangle is stored: blocks I <= J are computed, the
+//      diagonal blocks read symmetrically.  Q_IJ holds the intrinsic noise
+//      (I = J) and h_a^2 G_IJ times the integrated-OU increment covariance of
+//      the GW process in the (rho, a) slots;
 //   3. innovate on rho_q of the TOA's pulsar q: c = P e_{3q}, S = c_{3q} + R,
-//      e = r - m_{3q};
-//   4. update: m += c e / S, P_ij -= (c_i c_j) / S (the product c_i c_j is the
-//      same whichever way round, so P stays symmetric), and accumulate
-//      -1/2 (ln 2 pi + ln S + e^2 / S).
+//      e = r - m_{3q} (thread 0 forms 1/S once);
+//   4. update: m += c e / S and, over the upper triangle only,
+//      P_ij -= (c_i c_j) / S; accumulate -1/2 (ln 2 pi + ln S + e^2 / S).
 // Steps 2-4 are spread over the block's threads with a barrier between them;
 // a TOA at the same time as the previous one skips the predict (F = I, Q = 0).
 #include <algorithm>
@@ -33,6 +33,7 @@
 #include "../../include/argus.h"
 #include "../../include/argus_gwb.h"
 #include "kf_internal.cuh"
+#include "lib_internal.cuh"
 #include "kf_math.cuh"
 #include "kf_model.cuh"
 
@@ -68,6 +69,14 @@ __host__ __device__ inline size_t gwb_smem_doubles(int P) {
     return size_t(n) * n + 2 * n + 5 * P + size_t(P) * P + 3 * P + 16;
 }
 
+// dynamic shared memory of a block: the doubles, the (I, J) pairs of the
+// upper 3x3 blocks (uint16) and the (i, j) pairs of the upper entries (uint8)
+__host__ __device__ inline size_t gwb_smem_bytes(int P) {
+    const size_t n = 3 * size_t(P);
+    return gwb_smem_doubles(P) * sizeof(double) + size_t(P) * (P + 1) * sizeof(uint16_t) +
+           n * (n + 1) * sizeof(uint8_t);
+}
+
 __global__ void __launch_bounds__(kGwbThreads) k_gwb_filter(GwbArgs a) {
     extern __shared__ __align__(16) double gsm[];
     const int P = a.P, n = 3 * P, D = 2 + 3 * P;
@@ -80,12 +89,17 @@ __global__ void __launch_bounds__(kGwbThreads) k_gwb_filter(GwbArgs a) {
     double* gw = par + 3 * P;                // a_a, b_a, h_a^2 (q00, q01, q11), h_a^2, gamma_a, e, S, ok
     uint16_t* pairs = reinterpret_cast<uint16_t*>(gw + 16);   // upper 3x3 blocks (I, J)
     const int nb = P * (P + 1) / 2;
+    uint8_t* ent = reinterpret_cast<uint8_t*>(pairs + 2 * nb);   // upper entries (i, j), i <= j
+    const int ne = n * (n + 1) / 2;
     const int tid = threadIdx.x;
     for (int i = tid; i < P * P; i += blockDim.x) G[i] = a.G[i];
     if (tid == 0) {
         int k = 0;
         for (int I = 0; I < P; ++I)
             for (int J = I; J < P; ++J) { pairs[2 * k] = uint16_t(I); pairs[2 * k + 1] = uint16_t(J); ++k; }
+        k = 0;
+        for (int i = 0; i < n; ++i)
+            for (int j = i; j < n; ++j) { ent[2 * k] = uint8_t(i); ent[2 * k + 1] = uint8_t(j); ++k; }
     }
     for (int64_t b = blockIdx.x; b < a.B; b += gridDim.x) {
         const double* th = a.theta + b * D;
@@ -157,7 +171,9 @@ __global__ void __launch_bounds__(kGwbThreads) k_gwb_filter(GwbArgs a) {
                     const double apJ = co[5 * J], bpJ = co[5 * J + 1];
                     double X[3][3];
                     for (int u = 0; u < 3; ++u)
-                        for (int v = 0; v < 3; ++v) X[u][v] = Pm[(3 * I + u) * n + 3 * J + v];
+                        for (int v = 0; v < 3; ++v)
+                            X[u][v] = (I < J || u <= v) ? Pm[(3 * I + u) * n + 3 * J + v]
+                                                        : Pm[(3 * I + v) * n + 3 * J + u];
                     double Y[3][3];   // F_I X
                     for (int v = 0; v < 3; ++v) {
                         Y[0][v] = fma(bpI, X[1][v], fma(ba, X[2][v], X[0][v]));
@@ -182,34 +198,32 @@ __global__ void __launch_bounds__(kGwbThreads) k_gwb_filter(GwbArgs a) {
                         Z[1][1] += co[5 * I + 4];
                     }
                     for (int u = 0; u < 3; ++u)
-                        for (int v = 0; v < 3; ++v) {
-                            Pm[(3 * I + u) * n + 3 * J + v] = Z[u][v];
-                            Pm[(3 * J + v) * n + 3 * I + u] = Z[u][v];
-                        }
+                        for (int v = 0; v < 3; ++v)
+                            if (I < J || u <= v) Pm[(3 * I + u) * n + 3 * J + v] = Z[u][v];
                 }
                 __syncthreads();
             }
             // 3. innovate on rho of pulsar q
             const int i0 = 3 * rk.q;
-            for (int i = tid; i < n; i += blockDim.x) c[i] = Pm[i * n + i0];
+            for (int i = tid; i < n; i += blockDim.x) c[i] = Pm[min(i, i0) * n + max(i, i0)];
             if (tid == 0) {
                 const double R = fma(par[3 * rk.q + 2], rk.s2, a.equad2[rk.q]);
-                gw[7] = rk.r - m[i0];
-                gw[8] = Pm[i0 * n + i0] + R;
-            }
-            __syncthreads();
-            // 4. update
-            const double e = gw[7], S = gw[8];
-            const double rS = rcp_nr(S), g = e * rS;
-            for (int i = tid; i < n * n; i += blockDim.x) {
-                const int r = i / n, col = i - r * n;
-                Pm[i] = fma(-(c[r] * c[col]), rS, Pm[i]);
-            }
-            for (int i = tid; i < n; i += blockDim.x) m[i] = fma(c[i], g, m[i]);
-            if (tid == 0) {
-                quad = fma(e, g, quad);
+                const double e = rk.r - m[i0];
+                const double S = Pm[i0 * n + i0] + R;
+                const double rS = rcp_nr(S);
+                gw[7] = rS;
+                gw[8] = e * rS;
+                quad = fma(e, gw[8], quad);
                 lp.add(S);
             }
+            __syncthreads();
+            // 4. update (upper triangle)
+            const double rS = gw[7], g = gw[8];
+            for (int q = tid; q < ne; q += blockDim.x) {
+                const int r = ent[2 * q], col = ent[2 * q + 1];
+                Pm[r * n + col] = fma(-(c[r] * c[col]), rS, Pm[r * n + col]);
+            }
+            for (int i = tid; i < n; i += blockDim.x) m[i] = fma(c[i], g, m[i]);
             __syncthreads();
         }
         if (tid == 0) {
@@ -343,8 +357,7 @@ argus_status argus_gwb_create(const argus_pulsar* psrs, int32_t n_pulsars, int32
         return bail(e, "cudaMemcpy");
     // the kernel's dynamic shared memory limit, set for the largest array any
     // handle may hold (a per-function setting shared by all handles)
-    const size_t smem_max = gwb_smem_doubles(kGwbMaxPulsars) * sizeof(double) +
-                            size_t(kGwbMaxPulsars) * (kGwbMaxPulsars + 1) * sizeof(uint16_t);
+    const size_t smem_max = gwb_smem_bytes(kGwbMaxPulsars);
     if ((e = cudaFuncSetAttribute(k_gwb_filter, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_max))) !=
         cudaSuccess)
         return bail(e, "cudaFuncSetAttribute");
@@ -410,7 +423,7 @@ argus_status argus_gwb_loglik(argus_gwb* h, const double* theta, int64_t B, doub
     }
     {
         GwbArgs a{h->d_rec, h->N, h->P, h->d_p0, h->d_equad2, h->d_G, th_d, B, ll_d};
-        const size_t smem = gwb_smem_doubles(h->P) * sizeof(double) + size_t(h->P) * (h->P + 1) * sizeof(uint16_t);
+        const size_t smem = gwb_smem_bytes(h->P);
         const int grid = int(std::min<int64_t>(B, int64_t(h->n_sm) * 8));
         k_gwb_filter<<<grid, kGwbThreads, smem, s>>>(a);
         if ((e = cudaGetLastError()) != cudaSuccess) {

@@ -106,19 +106,6 @@ void launch_filter_scan(const ScanArgs& a, cudaStream_t s);
 constexpr int kPhaseTableDoubles = 256 * 4;
 void launch_fill_phase_table(double* tab, cudaStream_t s);
 
-// Stores msg as the calling thread's argus_last_error() and returns status.
-int record_error(int status, const char* msg);
-}  // namespace argus
-struct argus_pulsar;
-namespace argus {
-// Host validation of argus_pulsar data (argus_array_create's rules); returns
-// an argus_status and the total TOA count.
-int validate_pulsars(const argus_pulsar* psrs, int32_t n_pulsars, int64_t* total);
-
-// Joint filter with a Hellings-Downs correlated GW background (gwb.cu):
-// pulsars at most kGwbMaxPulsars (the 3P x 3P covariance lives in shared memory).
-constexpr int kGwbMaxPulsars = 48;
-
 // K4: deterministic sum over pulsars (and chain rule through K1 for grad).
 void launch_reduce(const double* theta, int64_t B, int32_t P, int32_t flags, const PulsarDev* psr,
                    const double* lane_out, double* loglik, double* grad, double* lane_ll,
