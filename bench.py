@@ -159,19 +159,53 @@ def traffic_record(kernel: str):
     return rec if rec.get("source_sha") == autotune.source_hash() else None
 
 
-def cpu_baseline(data, theta, seconds):
-    """The CPU oracle as it stands on this host's cores, on a bounded sample."""
+def _oracle_rate(data, theta, threads, seconds):
     from oracle import kalman
-    cores = os.cpu_count() or 1
-    kalman.set_threads(cores)
+    used = kalman.set_threads(threads)
     done, t0, i = 0, time.perf_counter(), 0
     while time.perf_counter() - t0 < seconds:
-        rows = theta[i % len(theta): i % len(theta) + cores]
+        rows = theta[i % len(theta): i % len(theta) + used]
         kalman.loglik_grad(data, rows)
         done += len(rows)
-        i += cores
+        i += used
     dt = time.perf_counter() - t0
-    return {"value": done / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+    return done / dt, done, dt, used
+
+
+def dense_vs_kalman():
+    """The O(N^3) dense multivariate normal (Cholesky) against the O(N)
+    filter, one pulsar, one parameter vector, on this host (the oracle's own
+    implementations of each)."""
+    import numpy as np
+
+    from oracle import dense, kalman
+    from paper_2510_11077_gb300 import inputs
+    kalman.set_threads(1)
+    out = []
+    for n in (250, 500, 1000, 2000):
+        d = inputs.make_array(np.array([n]), seed=n)
+        th = inputs.make_theta_batch(d, 1, seed=1)
+        row = {"toas": n}
+        for name, f in (("dense_s", lambda: dense.loglik(d, th)), ("kalman_s", lambda: kalman.loglik(d, th))):
+            f()
+            t0 = time.perf_counter()
+            reps = 0
+            while time.perf_counter() - t0 < 0.3:
+                f(); reps += 1
+            row[name] = (time.perf_counter() - t0) / reps
+        out.append(row)
+    return out
+
+
+def cpu_baseline(data, theta, seconds):
+    """The CPU oracle as it stands on this host's cores, on a bounded sample:
+    all cores (OpenMP over walkers) and one core."""
+    cores = os.cpu_count() or 1
+    v_all, done, dt, used = _oracle_rate(data, theta, cores, seconds)
+    v_one, done1, dt1, _ = _oracle_rate(data, theta, 1, max(2.0, seconds / 3))
+    return {"value": v_all, "unit": UNIT, "cores": used, "kind": "oracle",
+            "single_core": {"value": v_one, "unit": UNIT, "sample": f"{done1} walkers, {dt1:.1f} s"},
+            "dense_vs_kalman_1psr": dense_vs_kalman(),
             "sample": f"{done} walkers of the same workload (complex-step gradient, OpenMP over "
                       f"walkers), {dt:.1f} s"}
 
@@ -220,6 +254,8 @@ def loglik_only(args, dev, local):
     w = inputs.WORKLOADS[LOGLIK_WORKLOAD]
     data = inputs.make_workload_array(w.name)
     theta = torch.from_numpy(inputs.make_theta_batch(data, w.batch, seed=w.seed)).to(dev)
+    theta_prior = torch.from_numpy(inputs.make_theta_batch(data, w.batch, seed=w.seed + 7,
+                                                           kind="prior")).to(dev)
     arr = argus.Array(data, device=local)
     res = autotune.autotune(arr, theta, data.n_toa, grad=False, batch_for_key=w.batch,
                             space={"tape_cache": (0,)})
@@ -243,11 +279,25 @@ def loglik_only(args, dev, local):
     torch.cuda.synchronize(dev)
     step_ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
     k_ms = statistics.mean(kern)
+    # the same batch size drawn from the prior: the path does not depend on the values
+    llp = torch.empty(w.batch, dtype=torch.float64, device=dev)
+    argus.argus_loglik(arr, theta_prior, llp)
+    torch.cuda.synchronize(dev)
+    evp = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for k in range(reps):
+        flush.zero_()
+        evp[k][0].record(stream)
+        argus.argus_loglik(arr, theta_prior, llp)
+        evp[k][1].record(stream)
+    torch.cuda.synchronize(dev)
+    prior_ms = statistics.mean(a.elapsed_time(b) for a, b in evp)
     lane_steps = w.batch * int(data.n_toa.sum())
     achieved = FLOPS_PER_LANE_STEP_FWD * lane_steps / (k_ms * 1e-3) / 1e12
     arr.close()
     return {"workload": w.name, "metric": "loglik evals/s", "value": w.batch / (step_ms * 1e-3),
-            "ms_per_step": step_ms, "plan": res["plan"], "autotune_cached": res["cached"],
+            "ms_per_step": step_ms, "prior_draws_ms_per_step": prior_ms,
+            "lane_steps_per_s": lane_steps / (step_ms * 1e-3),
+            "plan": res["plan"], "autotune_cached": res["cached"],
             "roofline": {"bound": "alu", "kernel": "k_filter_fwd", "kernel_ms": k_ms,
                          "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": achieved / FP64_PEAK_TFLOPS,
@@ -582,6 +632,7 @@ def run_ours(args):
     e1.record(stream)
     torch.cuda.synchronize(dev)
     plain = {"value": n_plain / (e0.elapsed_time(e1) / 1e3), "unit": UNIT,
+             "lane_steps_per_s": n_plain * int(data.n_toa.sum()) / (e0.elapsed_time(e1) / 1e3),
              "sample_walkers": n_plain, "launches_per_walker": 3}
     if not torch.equal(llp, ll[:n_plain]):
         raise RuntimeError("plain and batched filters disagree")
@@ -596,9 +647,15 @@ def run_ours(args):
     flops = FLOPS_PER_LANE_STEP_GRAD_OU if args.noise == "ou" else FLOPS_PER_LANE_STEP_GRAD
     achieved = flops * lane_steps / (filt_ms * 1e-3) / 1e12
     tr = traffic_record("k_filter_grad") if args.noise == "rw" else None
+    peaks, _ = _measured_peaks()
+    hbm = peaks.get("hbm_gbs") if peaks else None
+    dram_gbs = tr["dram_bytes_per_launch"] / (filt_ms * 1e-3) / 1e9 if tr else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS,
                 "traffic": tr["dram_bytes_per_launch"] if tr else None,
+                "dram": {"achieved_gbs": dram_gbs, "peak_gbs": hbm,
+                         "frac": (dram_gbs / hbm) if (dram_gbs and hbm) else None,
+                         "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"},
                 "kernel": "k_filter_grad", "kernel_ms": filt_ms,
                 "peak_source": "derived: 2 FP64 FMA/clk/SM x 152 SMs x 2.07 GHz",
                 "algorithmic": f"{flops} FP64 flop per lane-step x "
@@ -617,6 +674,7 @@ def run_ours(args):
                        "lane_steps_per_gpu": lane_steps, "plan": plan, "autotune": tuned,
                        "l2": "flushed between timed steps (256 MiB write, untimed)"},
             "e2e": e2e, "gpu_launches": 3 * args.steps, "roofline": roofline,
+            "lane_steps_per_s": lane_steps * world * args.steps / (total_ms * 1e-3),
             "plain_filter": plain, "batched_over_plain": value / world / plain["value"],
             "stage_ms": {"project": statistics.mean(k[0] for k in kern), "filter": filt_ms,
                          "reduce": statistics.mean(k[2] for k in kern)},

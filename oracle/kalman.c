@@ -268,6 +268,21 @@ int oracle_loglik_grad(int P, const int64_t* off, const double* t, const double*
     return 0;
 }
 
+/* Threads of the OpenMP loops over parameter vectors (n >= 1). */
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+int oracle_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
+
 /* Continuous-wave projection of one parameter vector onto one pulsar:
    out = {A, B, Omega, Phi0, 1 - n.c (clamped)}. */
 int oracle_cw_project(const double* theta_gw, const double* pos, double* out)

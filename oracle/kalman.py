@@ -50,10 +50,13 @@ def _array_args(data):
     return keep, args
 
 
-def set_threads(n: int | None) -> None:
-    """Number of OpenMP threads the oracle uses (None: leave the default)."""
-    if n is not None:
-        os.environ["OMP_NUM_THREADS"] = str(int(n))
+def set_threads(n: int | None, lib_path: str | None = None) -> int:
+    """Number of OpenMP threads the oracle uses (None: leave it); returns the
+    number now in effect."""
+    lib = _load(lib_path)
+    lib.oracle_set_threads.argtypes = [ctypes.c_int]
+    lib.oracle_set_threads.restype = ctypes.c_int
+    return int(lib.oracle_set_threads(int(n) if n is not None else 0))
 
 
 def loglik(data, theta, lanes: bool = False, lib_path: str | None = None):
