@@ -647,7 +647,7 @@ def run_ours(args):
     flops = FLOPS_PER_LANE_STEP_GRAD_OU if args.noise == "ou" else FLOPS_PER_LANE_STEP_GRAD
     achieved = flops * lane_steps / (filt_ms * 1e-3) / 1e12
     tr = traffic_record("k_filter_grad") if args.noise == "rw" else None
-    peaks, _ = _measured_peaks()
+    peaks, peaks_src = _measured_peaks()
     hbm = peaks.get("hbm_gbs") if peaks else None
     dram_gbs = tr["dram_bytes_per_launch"] / (filt_ms * 1e-3) / 1e9 if tr else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
@@ -655,7 +655,7 @@ def run_ours(args):
                 "traffic": tr["dram_bytes_per_launch"] if tr else None,
                 "dram": {"achieved_gbs": dram_gbs, "peak_gbs": hbm,
                          "frac": (dram_gbs / hbm) if (dram_gbs and hbm) else None,
-                         "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"},
+                         "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peaks_src})"},
                 "kernel": "k_filter_grad", "kernel_ms": filt_ms,
                 "peak_source": "derived: 2 FP64 FMA/clk/SM x 152 SMs x 2.07 GHz",
                 "algorithmic": f"{flops} FP64 flop per lane-step x "
