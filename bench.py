@@ -448,8 +448,23 @@ def gwb_leg(args, dev, local):
         e1.record(stream)
         torch.cuda.synchronize(dev)
         ms.append(e0.elapsed_time(e1))
+    # the same batch with the gradient (reverse-mode adjoint through the joint filter)
+    g = torch.empty((GWB_BATCH, 2 + 3 * P), dtype=torch.float64, device=dev)
+    argus.argus_gwb_loglik_grad(arr, theta, ll, g)
+    torch.cuda.synchronize(dev)
+    gms = []
+    for _ in range(2):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        argus.argus_gwb_loglik_grad(arr, theta, ll, g)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        gms.append(e0.elapsed_time(e1))
+    grad_finite = bool(torch.isfinite(g).all().item())
     arr.close()
     step_ms = statistics.mean(ms)
+    grad_ms = statistics.mean(gms)
     n_toa = int(data.n_toa.sum())
     flops = gwb_flops_per_toa(P) * n_toa * GWB_BATCH
     achieved = flops / (step_ms * 1e-3) / 1e12
@@ -457,6 +472,9 @@ def gwb_leg(args, dev, local):
             "state_dim": 3 * P, "batch": GWB_BATCH, "metric": "loglik evals/s",
             "value": GWB_BATCH / (step_ms * 1e-3), "ms_per_step": step_ms,
             "finite": bool(torch.isfinite(ll).all().item()),
+            "gradient": {"metric": "loglik+grad evals/s", "value": GWB_BATCH / (grad_ms * 1e-3),
+                         "ms_per_step": grad_ms, "over_loglik": grad_ms / step_ms,
+                         "finite": grad_finite},
             "roofline": {"bound": "alu", "kernel": "k_gwb_filter", "kernel_ms": step_ms,
                          "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": achieved / FP64_PEAK_TFLOPS,

@@ -58,6 +58,18 @@ int32_t argus_gwb_dim(const argus_gwb* gwb);
 argus_status argus_gwb_loglik(argus_gwb* gwb, const double* theta, int64_t B, double* loglik,
                               void* stream);
 
+/* The joint log-likelihood and its gradient d loglik / d theta [B][D], by a
+ * reverse-mode adjoint sweep through the joint filter: the state (upper
+ * triangle of the covariance and the mean) is saved every ceil(sqrt(N))
+ * TOAs, each segment is re-run saving the state before every TOA, and the
+ * adjoint steps run backwards through it.  At most 32 pulsars (both the
+ * covariance and its adjoint stay in shared memory; ARGUS_ERR_UNSUPPORTED
+ * beyond).  Device scratch grows to 2 x max(ceil(sqrt N), segments) x
+ * (3P(3P+1)/2 + 3P) doubles per resident block.  Out-of-domain vectors get
+ * loglik = -inf and a zero gradient. */
+argus_status argus_gwb_loglik_grad(argus_gwb* gwb, const double* theta, int64_t B, double* loglik,
+                                   double* grad, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -125,6 +125,8 @@ def load(build_if_missing: bool = False):
     lib.argus_gwb_dim.restype = ctypes.c_int32
     lib.argus_gwb_loglik.argtypes = [vp, dp, ctypes.c_int64, dp, vp]
     lib.argus_gwb_loglik.restype = ctypes.c_int
+    lib.argus_gwb_loglik_grad.argtypes = [vp, dp, ctypes.c_int64, dp, dp, vp]
+    lib.argus_gwb_loglik_grad.restype = ctypes.c_int
     lib.argus_status_string.argtypes = [ctypes.c_int]
     lib.argus_status_string.restype = ctypes.c_char_p
     lib.argus_last_error.argtypes = []
@@ -208,6 +210,18 @@ def argus_gwb_loglik(array: GwbArray, theta, loglik=None, stream=None):
     s = stream if stream is not None else _stream_of(theta, loglik)
     _check(_lib.argus_gwb_loglik(array.handle, _ptr(theta), B, _ptr(loglik), s))
     return loglik
+
+
+def argus_gwb_loglik_grad(array: GwbArray, theta, loglik=None, grad=None, stream=None):
+    theta = _prep(theta, array.dim)
+    B = theta.shape[0]
+    if loglik is None:
+        loglik = _new_like(theta, (B,))
+    if grad is None:
+        grad = _new_like(theta, (B, array.dim))
+    s = stream if stream is not None else _stream_of(theta, loglik, grad)
+    _check(_lib.argus_gwb_loglik_grad(array.handle, _ptr(theta), B, _ptr(loglik), _ptr(grad), s))
+    return loglik, grad
 
 
 class Array:

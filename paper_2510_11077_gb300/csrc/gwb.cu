@@ -41,7 +41,10 @@ namespace argus {
 namespace {
 
 constexpr double kLog2PiGwb = 1.8378770664093454836;
+constexpr double kLn10Gwb = 2.302585092994045684;
 constexpr int kGwbThreads = 256;
+constexpr int kGwbGradMaxPulsars = 32;   // gradient: two 3P x 3P matrices in shared memory
+constexpr int kCo = 9;                   // per-pulsar coefficients (see GwbSmem::co)
 
 struct GwbRec {     // one TOA of the merged, time-ordered stream (32 bytes)
     double dt;      // time since the previous TOA of any pulsar (0 for the first)
@@ -61,175 +64,519 @@ struct GwbArgs {
     const double* theta;    // [B][2 + 3P]
     int64_t B;
     double* loglik;         // [B]
+    double* grad;           // [B][2 + 3P] (gradient kernel)
+    double* ckpt;           // per block: [nseg][ne + n] state at each segment start
+    double* tape;           // per block: [L][ne + n] state before each step of a segment
+    int64_t slot;           // doubles per block in ckpt and in tape
+    int32_t L;              // segment length (TOAs)
+    int32_t nseg;
 };
 
-__host__ __device__ inline size_t gwb_smem_doubles(int P) {
-    const int n = 3 * P;
-    // P, m, c, per-pulsar coefficients (5P), G, per-pulsar parameters (3P), GW coefficients + scalars
-    return size_t(n) * n + 2 * n + 5 * P + size_t(P) * P + 3 * P + 16;
+// Shared memory of a block.  The covariance P is stored whole but only its
+// upper triangle is kept current; the adjoint Pb (gradient) is kept full.
+struct GwbSmem {
+    int P, n, nb, ne;
+    double* Pm;     // [n][n]
+    double* m;      // [n]
+    double* c;      // [n]
+    double* co;     // [P][9]: a, b, Q/sigma^2 (c00, c01, c11), d/dgamma of b and of c00, c01, c11
+    double* G;      // [P][P]
+    double* par;    // [P][4]: sigma^2, gamma_p, EFAC^2, EFAC
+    double* gw;     // GW process: a, b, c00, c01, c11, db, dc00, dc01, dc11 (per unit h_a^2); scalars
+    double* Pb;     // [n][n]   (gradient)
+    double* mb;     // [n]      (gradient)
+    double* u;      // [n]      (gradient)
+    double* v;      // [n]      (gradient)
+    double* acc;    // [P][5]: d/d sigma^2, d/d gamma_p, d/d EFAC, d/d h_a^2 part, d/d gamma_a part
+    uint16_t* pairs;
+    uint8_t* ent;
+};
+// scalar slots of gw[]
+enum { kGwA = 0, kGwHa2 = 9, kGwGa, kGwE, kGwS, kGwRS, kGwG, kGwOk, kGwSb, kGwEb, kGwR0, kGwSlots = 20 };
+
+__host__ __device__ inline size_t gwb_smem_doubles(int P, bool grad) {
+    const size_t n = 3 * size_t(P);
+    size_t d = n * n + 2 * n + kCo * size_t(P) + size_t(P) * P + 4 * size_t(P) + kGwSlots;
+    if (grad) d += n * n + 3 * n + 5 * size_t(P);
+    return d;
 }
 
 // dynamic shared memory of a block: the doubles, the (I, J) pairs of the
 // upper 3x3 blocks (uint16) and the (i, j) pairs of the upper entries (uint8)
-__host__ __device__ inline size_t gwb_smem_bytes(int P) {
+__host__ __device__ inline size_t gwb_smem_bytes(int P, bool grad) {
     const size_t n = 3 * size_t(P);
-    return gwb_smem_doubles(P) * sizeof(double) + size_t(P) * (P + 1) * sizeof(uint16_t) +
+    return gwb_smem_doubles(P, grad) * sizeof(double) + size_t(P) * (P + 1) * sizeof(uint16_t) +
            n * (n + 1) * sizeof(uint8_t);
+}
+
+__device__ GwbSmem gwb_carve(double* base, int P, bool grad) {
+    GwbSmem s;
+    s.P = P; s.n = 3 * P; s.nb = P * (P + 1) / 2; s.ne = s.n * (s.n + 1) / 2;
+    const int n = s.n;
+    double* q = base;
+    s.Pm = q; q += size_t(n) * n;
+    s.m = q; q += n;
+    s.c = q; q += n;
+    s.co = q; q += kCo * P;
+    s.G = q; q += size_t(P) * P;
+    s.par = q; q += 4 * P;
+    s.gw = q; q += kGwSlots;
+    if (grad) {
+        s.Pb = q; q += size_t(n) * n;
+        s.mb = q; q += n;
+        s.u = q; q += n;
+        s.v = q; q += n;
+        s.acc = q; q += 5 * P;
+    } else {
+        s.Pb = s.mb = s.u = s.v = s.acc = nullptr;
+    }
+    s.pairs = reinterpret_cast<uint16_t*>(q);
+    s.ent = reinterpret_cast<uint8_t*>(s.pairs + 2 * s.nb);
+    return s;
+}
+
+__device__ __forceinline__ double psym(const double* M, int n, int i, int j) {
+    return i <= j ? M[i * n + j] : M[j * n + i];
+}
+
+// tables and HD matrix, once per block
+__device__ void gwb_tables(const GwbSmem& s, const GwbArgs& a) {
+    for (int i = threadIdx.x; i < s.P * s.P; i += blockDim.x) s.G[i] = a.G[i];
+    if (threadIdx.x == 0) {
+        int k = 0;
+        for (int I = 0; I < s.P; ++I)
+            for (int J = I; J < s.P; ++J) { s.pairs[2 * k] = uint16_t(I); s.pairs[2 * k + 1] = uint16_t(J); ++k; }
+        k = 0;
+        for (int i = 0; i < s.n; ++i)
+            for (int j = i; j < s.n; ++j) { s.ent[2 * k] = uint8_t(i); s.ent[2 * k + 1] = uint8_t(j); ++k; }
+    }
+}
+
+// parameters of walker th and the prior at the array's earliest TOA; returns
+// false (uniformly) when theta is out of the domain
+__device__ bool gwb_setup(const GwbSmem& s, const GwbArgs& a, const double* th) {
+    const int P = s.P, n = s.n, D = 2 + 3 * P;
+    if (threadIdx.x == 0) {
+        bool ok = true;
+        for (int j = 0; j < D; ++j) ok = ok && isfinite(th[j]);
+        for (int p = 0; p < P; ++p) ok = ok && th[2 + 3 * p + 2] > 0.0;
+        s.gw[kGwHa2] = exp10(2.0 * th[0]);
+        s.gw[kGwGa] = exp10(th[1]);
+        s.gw[kGwOk] = ok ? 1.0 : 0.0;
+    }
+    for (int p = threadIdx.x; p < P; p += blockDim.x) {
+        s.par[4 * p] = exp10(2.0 * th[2 + 3 * p]);
+        s.par[4 * p + 1] = exp10(th[2 + 3 * p + 1]);
+        const double ef = th[2 + 3 * p + 2];
+        s.par[4 * p + 2] = ef * ef;
+        s.par[4 * p + 3] = ef;
+    }
+    __syncthreads();
+    if (s.gw[kGwOk] == 0.0) return false;
+    const double ha2 = s.gw[kGwHa2], ga = s.gw[kGwGa];
+    for (int i = threadIdx.x; i < n * n; i += blockDim.x) {
+        const int r = i / n, col = i - r * n;
+        const int I = r / 3, J = col / 3, uu = r - 3 * I, vv = col - 3 * J;
+        double x = 0.0;
+        if (uu == 2 && vv == 2) x = ha2 * s.G[I * P + J] / (2.0 * ga);
+        else if (I == J && uu < 2 && vv < 2) x = a.p0[3 * I + uu + vv];
+        s.Pm[i] = x;
+    }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s.m[i] = 0.0;
+    __syncthreads();
+    return true;
+}
+
+// 1. transition coefficients over dt (threads 0..P-1 the pulsars, thread P the GW process)
+template <bool kDeriv>
+__device__ void gwb_coef(const GwbSmem& s, double dt) {
+    const double h2 = 0.5 * dt * dt, h3 = dt * dt * dt / 3.0, dt2 = dt * dt;
+    for (int p = threadIdx.x; p <= s.P; p += blockDim.x) {
+        OuCoef oc;
+        const double gam = (p < s.P) ? s.par[4 * p + 1] : s.gw[kGwGa];
+        ou_coef<kDeriv>(gam * dt, dt, h2, h3, dt2, oc);
+        double* o = (p < s.P) ? s.co + kCo * p : s.gw + kGwA;
+        o[0] = oc.a; o[1] = oc.b; o[2] = oc.c00; o[3] = oc.c01; o[4] = oc.c11;
+        if (kDeriv) { o[5] = oc.db; o[6] = oc.dc00; o[7] = oc.dc01; o[8] = oc.dc11; }
+    }
+}
+
+// 2. predict: the mean and every upper 3x3 block, F_I P_IJ F_J^T + Q_IJ
+__device__ void gwb_predict(const GwbSmem& s) {
+    const int P = s.P, n = s.n;
+    const double* gw = s.gw;
+    const double aa = gw[0], ba = gw[1], ha2 = gw[kGwHa2];
+    const double qa00 = ha2 * gw[2], qa01 = ha2 * gw[3], qa11 = ha2 * gw[4];
+    for (int p = threadIdx.x; p < P; p += blockDim.x) {
+        double* mp = s.m + 3 * p;
+        mp[0] = fma(s.co[kCo * p + 1], mp[1], fma(ba, mp[2], mp[0]));
+        mp[1] *= s.co[kCo * p];
+        mp[2] *= aa;
+    }
+    for (int q = threadIdx.x; q < s.nb; q += blockDim.x) {
+        const int I = s.pairs[2 * q], J = s.pairs[2 * q + 1];
+        const double apI = s.co[kCo * I], bpI = s.co[kCo * I + 1];
+        const double apJ = s.co[kCo * J], bpJ = s.co[kCo * J + 1];
+        double X[3][3];
+        for (int u = 0; u < 3; ++u)
+            for (int v = 0; v < 3; ++v)
+                X[u][v] = (I < J || u <= v) ? s.Pm[(3 * I + u) * n + 3 * J + v] : s.Pm[(3 * I + v) * n + 3 * J + u];
+        double Y[3][3];   // F_I X
+        for (int v = 0; v < 3; ++v) {
+            Y[0][v] = fma(bpI, X[1][v], fma(ba, X[2][v], X[0][v]));
+            Y[1][v] = apI * X[1][v];
+            Y[2][v] = aa * X[2][v];
+        }
+        double Z[3][3];   // (F_I X) F_J^T
+        for (int u = 0; u < 3; ++u) {
+            Z[u][0] = fma(bpJ, Y[u][1], fma(ba, Y[u][2], Y[u][0]));
+            Z[u][1] = apJ * Y[u][1];
+            Z[u][2] = aa * Y[u][2];
+        }
+        const double g = s.G[I * P + J];
+        Z[0][0] = fma(g, qa00, Z[0][0]);
+        Z[0][2] = fma(g, qa01, Z[0][2]);
+        Z[2][0] = fma(g, qa01, Z[2][0]);
+        Z[2][2] = fma(g, qa11, Z[2][2]);
+        if (I == J) {
+            const double s2 = s.par[4 * I];
+            Z[0][0] = fma(s2, s.co[kCo * I + 2], Z[0][0]);
+            Z[0][1] = fma(s2, s.co[kCo * I + 3], Z[0][1]);
+            Z[1][0] = fma(s2, s.co[kCo * I + 3], Z[1][0]);
+            Z[1][1] = fma(s2, s.co[kCo * I + 4], Z[1][1]);
+        }
+        for (int u = 0; u < 3; ++u)
+            for (int v = 0; v < 3; ++v)
+                if (I < J || u <= v) s.Pm[(3 * I + u) * n + 3 * J + v] = Z[u][v];
+    }
+}
+
+// 3. innovate on rho of pulsar q: c = P e_i; thread 0 forms e, S, 1/S, e/S
+__device__ void gwb_innovate(const GwbSmem& s, const GwbArgs& a, const GwbRec& rk) {
+    const int n = s.n, i0 = 3 * rk.q;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s.c[i] = psym(s.Pm, n, i, i0);
+    if (threadIdx.x == 0) {
+        const double R = fma(s.par[4 * rk.q + 2], rk.s2, a.equad2[rk.q]);
+        const double e = rk.r - s.m[i0];
+        const double S = s.Pm[i0 * n + i0] + R;
+        const double rS = rcp_nr(S);
+        s.gw[kGwE] = e;
+        s.gw[kGwS] = S;
+        s.gw[kGwRS] = rS;
+        s.gw[kGwG] = e * rS;
+    }
+}
+
+// 4. update (upper triangle) and mean
+__device__ void gwb_update(const GwbSmem& s) {
+    const int n = s.n;
+    const double rS = s.gw[kGwRS], g = s.gw[kGwG];
+    for (int q = threadIdx.x; q < s.ne; q += blockDim.x) {
+        const int r = s.ent[2 * q], col = s.ent[2 * q + 1];
+        s.Pm[r * n + col] = fma(-(s.c[r] * s.c[col]), rS, s.Pm[r * n + col]);
+    }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s.m[i] = fma(s.c[i], g, s.m[i]);
+}
+
+// one forward step; thread 0 accumulates the likelihood when kLL
+template <bool kLL>
+__device__ void gwb_step(const GwbSmem& s, const GwbArgs& a, const GwbRec& rk, double& quad, LogProd& lp) {
+    if (rk.dt > 0.0) {
+        gwb_coef<false>(s, rk.dt);
+        __syncthreads();
+        gwb_predict(s);
+        __syncthreads();
+    }
+    gwb_innovate(s, a, rk);
+    __syncthreads();
+    if (kLL && threadIdx.x == 0) {
+        quad = fma(s.gw[kGwE], s.gw[kGwG], quad);
+        lp.add(s.gw[kGwS]);
+    }
+    gwb_update(s);
+    __syncthreads();
+}
+
+__device__ __forceinline__ double gwb_finish(int64_t N, double quad, const LogProd& lp) {
+    double ll = (N == 0) ? 0.0 : -0.5 * (double(N) * kLog2PiGwb + lp.value() + quad);
+    return (lp.bad || !isfinite(ll)) ? -INFINITY : ll;
 }
 
 __global__ void __launch_bounds__(kGwbThreads) k_gwb_filter(GwbArgs a) {
     extern __shared__ __align__(16) double gsm[];
-    const int P = a.P, n = 3 * P, D = 2 + 3 * P;
-    double* Pm = gsm;                        // [n][n]
-    double* m = Pm + size_t(n) * n;          // [n]
-    double* c = m + n;                       // [n] column of the update
-    double* co = c + n;                      // [P][5]: a_p, b_p, sigma^2 (q00, q01, q11)
-    double* G = co + 5 * P;                  // [P][P]
-    double* par = G + size_t(P) * P;         // [P][3]: sigma^2, gamma_p, EFAC^2
-    double* gw = par + 3 * P;                // a_a, b_a, h_a^2 (q00, q01, q11), h_a^2, gamma_a, e, S, ok
-    uint16_t* pairs = reinterpret_cast<uint16_t*>(gw + 16);   // upper 3x3 blocks (I, J)
-    const int nb = P * (P + 1) / 2;
-    uint8_t* ent = reinterpret_cast<uint8_t*>(pairs + 2 * nb);   // upper entries (i, j), i <= j
-    const int ne = n * (n + 1) / 2;
-    const int tid = threadIdx.x;
-    for (int i = tid; i < P * P; i += blockDim.x) G[i] = a.G[i];
-    if (tid == 0) {
-        int k = 0;
-        for (int I = 0; I < P; ++I)
-            for (int J = I; J < P; ++J) { pairs[2 * k] = uint16_t(I); pairs[2 * k + 1] = uint16_t(J); ++k; }
-        k = 0;
-        for (int i = 0; i < n; ++i)
-            for (int j = i; j < n; ++j) { ent[2 * k] = uint8_t(i); ent[2 * k + 1] = uint8_t(j); ++k; }
-    }
+    const GwbSmem s = gwb_carve(gsm, a.P, false);
+    gwb_tables(s, a);
     for (int64_t b = blockIdx.x; b < a.B; b += gridDim.x) {
-        const double* th = a.theta + b * D;
         __syncthreads();
-        if (tid == 0) {
-            bool ok = true;
-            for (int j = 0; j < D; ++j) ok = ok && isfinite(th[j]);
-            for (int p = 0; p < P; ++p) ok = ok && th[2 + 3 * p + 2] > 0.0;
-            gw[5] = exp10(2.0 * th[0]);
-            gw[6] = exp10(th[1]);
-            gw[9] = ok ? 1.0 : 0.0;
-        }
-        for (int p = tid; p < P; p += blockDim.x) {
-            par[3 * p] = exp10(2.0 * th[2 + 3 * p]);
-            par[3 * p + 1] = exp10(th[2 + 3 * p + 1]);
-            const double ef = th[2 + 3 * p + 2];
-            par[3 * p + 2] = ef * ef;
-        }
-        __syncthreads();
-        if (gw[9] == 0.0) {
-            if (tid == 0) a.loglik[b] = -INFINITY;
+        if (!gwb_setup(s, a, a.theta + b * (2 + 3 * a.P))) {
+            if (threadIdx.x == 0) a.loglik[b] = -INFINITY;
             continue;
         }
-        // prior at the array's earliest TOA
-        const double ha2 = gw[5], ga = gw[6];
-        for (int i = tid; i < n * n; i += blockDim.x) {
-            const int r = i / n, col = i - r * n;
-            const int I = r / 3, J = col / 3, u = r - 3 * I, v = col - 3 * J;
-            double x = 0.0;
-            if (u == 2 && v == 2) x = ha2 * G[I * P + J] / (2.0 * ga);
-            else if (I == J && u < 2 && v < 2) x = a.p0[3 * I + u + v];
-            Pm[i] = x;
-        }
-        for (int i = tid; i < n; i += blockDim.x) m[i] = 0.0;
         double quad = 0.0;
         LogProd lp;
+        for (int64_t k = 0; k < a.N; ++k) gwb_step<true>(s, a, a.rec[k], quad, lp);
+        if (threadIdx.x == 0) a.loglik[b] = gwb_finish(a.N, quad, lp);
+    }
+}
+
+// state (upper triangle of P, then m) to / from a global slot
+__device__ void gwb_save(const GwbSmem& s, double* dst) {
+    for (int q = threadIdx.x; q < s.ne; q += blockDim.x) dst[q] = s.Pm[s.ent[2 * q] * s.n + s.ent[2 * q + 1]];
+    for (int i = threadIdx.x; i < s.n; i += blockDim.x) dst[s.ne + i] = s.m[i];
+}
+
+__device__ void gwb_load(const GwbSmem& s, const double* src) {
+    for (int q = threadIdx.x; q < s.ne; q += blockDim.x) s.Pm[s.ent[2 * q] * s.n + s.ent[2 * q + 1]] = src[q];
+    for (int i = threadIdx.x; i < s.n; i += blockDim.x) s.m[i] = src[s.ne + i];
+}
+
+// Reverse of one forward step k, the state before it in Pm, m.  On entry Pb,
+// mb hold the adjoints of the state after the step; on exit, before it.
+__device__ void gwb_step_adjoint(const GwbSmem& s, const GwbArgs& a, const GwbRec& rk) {
+    const int P = s.P, n = s.n, q = rk.q, i0 = 3 * q;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const double dt = rk.dt;
+    const bool pred = dt > 0.0;
+    double* gw = s.gw;
+    if (pred) {
+        gwb_coef<true>(s, dt);
         __syncthreads();
-        for (int64_t k = 0; k < a.N; ++k) {
-            const GwbRec rk = a.rec[k];
-            const double dt = rk.dt;
-            if (dt > 0.0) {
-                // 1. transition coefficients
-                const double h2 = 0.5 * dt * dt, h3 = dt * dt * dt / 3.0;
-                for (int p = tid; p <= P; p += blockDim.x) {
-                    OuCoef oc;
-                    if (p < P) {
-                        ou_coef<false>(par[3 * p + 1] * dt, dt, h2, h3, 0.0, oc);
-                        const double s2 = par[3 * p];
-                        co[5 * p] = oc.a; co[5 * p + 1] = oc.b;
-                        co[5 * p + 2] = s2 * oc.c00; co[5 * p + 3] = s2 * oc.c01; co[5 * p + 4] = s2 * oc.c11;
-                    } else {
-                        ou_coef<false>(ga * dt, dt, h2, h3, 0.0, oc);
-                        gw[0] = oc.a; gw[1] = oc.b;
-                        gw[2] = ha2 * oc.c00; gw[3] = ha2 * oc.c01; gw[4] = ha2 * oc.c11;
-                    }
-                }
-                __syncthreads();
-                // 2. predict the mean (one thread per pulsar) and each upper block
-                const double aa = gw[0], ba = gw[1], qa00 = gw[2], qa01 = gw[3], qa11 = gw[4];
-                for (int p = tid; p < P; p += blockDim.x) {
-                    double* mp = m + 3 * p;
-                    mp[0] = fma(co[5 * p + 1], mp[1], fma(ba, mp[2], mp[0]));
-                    mp[1] *= co[5 * p];
-                    mp[2] *= aa;
-                }
-                for (int q = tid; q < nb; q += blockDim.x) {
-                    const int I = pairs[2 * q], J = pairs[2 * q + 1];
-                    const double apI = co[5 * I], bpI = co[5 * I + 1];
-                    const double apJ = co[5 * J], bpJ = co[5 * J + 1];
-                    double X[3][3];
-                    for (int u = 0; u < 3; ++u)
-                        for (int v = 0; v < 3; ++v)
-                            X[u][v] = (I < J || u <= v) ? Pm[(3 * I + u) * n + 3 * J + v]
-                                                        : Pm[(3 * I + v) * n + 3 * J + u];
-                    double Y[3][3];   // F_I X
-                    for (int v = 0; v < 3; ++v) {
-                        Y[0][v] = fma(bpI, X[1][v], fma(ba, X[2][v], X[0][v]));
-                        Y[1][v] = apI * X[1][v];
-                        Y[2][v] = aa * X[2][v];
-                    }
-                    double Z[3][3];   // (F_I X) F_J^T
-                    for (int u = 0; u < 3; ++u) {
-                        Z[u][0] = fma(bpJ, Y[u][1], fma(ba, Y[u][2], Y[u][0]));
-                        Z[u][1] = apJ * Y[u][1];
-                        Z[u][2] = aa * Y[u][2];
-                    }
-                    const double g = G[I * P + J];
-                    Z[0][0] = fma(g, qa00, Z[0][0]);
-                    Z[0][2] = fma(g, qa01, Z[0][2]);
-                    Z[2][0] = fma(g, qa01, Z[2][0]);
-                    Z[2][2] = fma(g, qa11, Z[2][2]);
-                    if (I == J) {
-                        Z[0][0] += co[5 * I + 2];
-                        Z[0][1] += co[5 * I + 3];
-                        Z[1][0] += co[5 * I + 3];
-                        Z[1][1] += co[5 * I + 4];
-                    }
-                    for (int u = 0; u < 3; ++u)
-                        for (int v = 0; v < 3; ++v)
-                            if (I < J || u <= v) Pm[(3 * I + u) * n + 3 * J + v] = Z[u][v];
-                }
-                __syncthreads();
+    }
+    // u = P (F^T e_i), and mu_i = (F m)_i
+    const double bq = pred ? s.co[kCo * q + 1] : 0.0, ba = pred ? gw[1] : 0.0;
+    for (int j = tid; j < n; j += blockDim.x)
+        s.u[j] = fma(bq, psym(s.Pm, n, j, i0 + 1), fma(ba, psym(s.Pm, n, j, i0 + 2), psym(s.Pm, n, j, i0)));
+    __syncthreads();
+    // c = F u + Q e_i (the predicted covariance's column i)
+    const double ha2 = gw[kGwHa2];
+    for (int J = tid; J < P; J += blockDim.x) {
+        const double* uJ = s.u + 3 * J;
+        if (pred) {
+            const double aJ = s.co[kCo * J], bJ = s.co[kCo * J + 1], aa = gw[0];
+            const double g = s.G[J * P + q] * ha2;
+            double c0 = fma(bJ, uJ[1], fma(ba, uJ[2], uJ[0])) + g * gw[2];
+            double c1 = aJ * uJ[1];
+            const double c2 = fma(aa, uJ[2], g * gw[3]);
+            if (J == q) {
+                const double s2 = s.par[4 * q];
+                c0 = fma(s2, s.co[kCo * q + 2], c0);
+                c1 = fma(s2, s.co[kCo * q + 3], c1);
             }
-            // 3. innovate on rho of pulsar q
-            const int i0 = 3 * rk.q;
-            for (int i = tid; i < n; i += blockDim.x) c[i] = Pm[min(i, i0) * n + max(i, i0)];
-            if (tid == 0) {
-                const double R = fma(par[3 * rk.q + 2], rk.s2, a.equad2[rk.q]);
-                const double e = rk.r - m[i0];
-                const double S = Pm[i0 * n + i0] + R;
-                const double rS = rcp_nr(S);
-                gw[7] = rS;
-                gw[8] = e * rS;
-                quad = fma(e, gw[8], quad);
-                lp.add(S);
-            }
-            __syncthreads();
-            // 4. update (upper triangle)
-            const double rS = gw[7], g = gw[8];
-            for (int q = tid; q < ne; q += blockDim.x) {
-                const int r = ent[2 * q], col = ent[2 * q + 1];
-                Pm[r * n + col] = fma(-(c[r] * c[col]), rS, Pm[r * n + col]);
-            }
-            for (int i = tid; i < n; i += blockDim.x) m[i] = fma(c[i], g, m[i]);
-            __syncthreads();
+            s.c[3 * J] = c0; s.c[3 * J + 1] = c1; s.c[3 * J + 2] = c2;
+        } else {
+            s.c[3 * J] = uJ[0]; s.c[3 * J + 1] = uJ[1]; s.c[3 * J + 2] = uJ[2];
         }
-        if (tid == 0) {
-            double ll = (a.N == 0) ? 0.0 : -0.5 * (double(a.N) * kLog2PiGwb + lp.value() + quad);
-            if (lp.bad || !isfinite(ll)) ll = -INFINITY;
+    }
+    if (tid == 0) {
+        const double mu = fma(bq, s.m[i0 + 1], fma(ba, s.m[i0 + 2], s.m[i0]));
+        const double R = fma(s.par[4 * q + 2], rk.s2, a.equad2[q]);
+        gw[kGwE] = rk.r - mu;
+        gw[kGwR0] = R;   // this TOA's measurement variance
+    }
+    __syncthreads();
+    if (tid == 0) {
+        const double S = s.c[i0] + gw[kGwR0];
+        const double rS = rcp_nr(S);
+        gw[kGwS] = S; gw[kGwRS] = rS; gw[kGwG] = gw[kGwE] * rS;
+    }
+    // v = Pb c
+    for (int j = tid; j < n; j += blockDim.x) {
+        double acc = 0.0;
+        for (int k = 0; k < n; ++k) acc = fma(s.Pb[j * n + k], s.c[k], acc);
+        s.v[j] = acc;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        const double rS = gw[kGwRS], g = gw[kGwG];
+        double gb = 0.0, cv = 0.0;
+        for (int k = 0; k < n; ++k) { gb = fma(s.mb[k], s.c[k], gb); cv = fma(s.c[k], s.v[k], cv); }
+        const double Sb = rS * rS * cv - gb * g * rS - 0.5 * rS + 0.5 * g * g;
+        gw[kGwSb] = Sb;
+        gw[kGwEb] = gb * rS - g;
+        s.acc[5 * q + 2] += Sb * 2.0 * s.par[4 * q + 3] * rk.s2;     // d/d EFAC_q
+    }
+    __syncthreads();
+    // c-bar, the symmetric M-bar (row and column i of Pb) and mu-bar (in mb)
+    {
+        const double rS = gw[kGwRS], g = gw[kGwG], Sb = gw[kGwSb], eb = gw[kGwEb];
+        for (int j = tid; j < n; j += blockDim.x) {
+            const double cb = fma(s.mb[j], g, -2.0 * rS * s.v[j]);
+            if (j == i0) {
+                s.Pb[j * n + j] += cb + Sb;
+                s.mb[j] -= eb;
+            } else {
+                s.Pb[j * n + i0] = fma(0.5, cb, s.Pb[j * n + i0]);
+                s.Pb[i0 * n + j] = fma(0.5, cb, s.Pb[i0 * n + j]);
+            }
+        }
+    }
+    __syncthreads();
+    if (!pred) return;   // F = I, Q = 0: the adjoints pass through
+    // parameters through F and Q: one warp per pulsar
+    const double aa = gw[0], dba = gw[5], dca00 = gw[6], dca01 = gw[7], dca11 = gw[8];
+    for (int I = warp; I < P; I += nw) {
+        const int rI = 3 * I, yI = rI + 1, aI = rI + 2;
+        double s1 = 0.0, s2 = 0.0, s3 = 0.0, s4 = 0.0, h = 0.0, gd = 0.0;
+        for (int k = lane; k < n; k += 32) {
+            const int J = k / 3, cmp = k - 3 * J;
+            double fpy, fpa;   // (F P)[k, yI], (F P)[k, aI]
+            if (cmp == 0) {
+                const double bJ = s.co[kCo * J + 1];
+                fpy = fma(bJ, psym(s.Pm, n, 3 * J + 1, yI), fma(ba, psym(s.Pm, n, 3 * J + 2, yI), psym(s.Pm, n, 3 * J, yI)));
+                fpa = fma(bJ, psym(s.Pm, n, 3 * J + 1, aI), fma(ba, psym(s.Pm, n, 3 * J + 2, aI), psym(s.Pm, n, 3 * J, aI)));
+            } else if (cmp == 1) {
+                const double aJ = s.co[kCo * J];
+                fpy = aJ * psym(s.Pm, n, k, yI);
+                fpa = aJ * psym(s.Pm, n, k, aI);
+            } else {
+                fpy = aa * psym(s.Pm, n, k, yI);
+                fpa = aa * psym(s.Pm, n, k, aI);
+            }
+            s1 = fma(s.Pb[rI * n + k], fpy, s1);
+            s2 = fma(s.Pb[yI * n + k], fpy, s2);
+            s3 = fma(s.Pb[rI * n + k], fpa, s3);
+            s4 = fma(s.Pb[aI * n + k], fpa, s4);
+        }
+        for (int J = lane; J < P; J += 32) {
+            const double g = s.G[I * P + J];
+            const double X00 = s.Pb[rI * n + 3 * J], X02 = s.Pb[rI * n + 3 * J + 2];
+            const double X20 = s.Pb[aI * n + 3 * J], X22 = s.Pb[aI * n + 3 * J + 2];
+            h = fma(g, fma(X00, gw[2], fma(X02 + X20, gw[3], X22 * gw[4])), h);
+            gd = fma(g, fma(X00, dca00, fma(X02 + X20, dca01, X22 * dca11)), gd);
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            s1 += __shfl_down_sync(0xffffffffu, s1, off);
+            s2 += __shfl_down_sync(0xffffffffu, s2, off);
+            s3 += __shfl_down_sync(0xffffffffu, s3, off);
+            s4 += __shfl_down_sync(0xffffffffu, s4, off);
+            h += __shfl_down_sync(0xffffffffu, h, off);
+            gd += __shfl_down_sync(0xffffffffu, gd, off);
+        }
+        if (lane == 0) {
+            const double* co = s.co + kCo * I;
+            const double bbar_p = fma(2.0, s1, s.mb[rI] * s.m[yI]);
+            const double abar_p = fma(2.0, s2, s.mb[yI] * s.m[yI]);
+            const double bbar_a = fma(2.0, s3, s.mb[rI] * s.m[aI]);
+            const double abar_a = fma(2.0, s4, s.mb[aI] * s.m[aI]);
+            const double M00 = s.Pb[rI * n + rI], M01 = s.Pb[rI * n + yI], M11 = s.Pb[yI * n + yI];
+            const double s2p = s.par[4 * I];
+            double* acc = s.acc + 5 * I;
+            acc[0] += fma(M00, co[2], fma(2.0 * M01, co[3], M11 * co[4]));
+            acc[1] += fma(-dt * co[0], abar_p, fma(bbar_p, co[5],
+                          s2p * fma(M00, co[6], fma(2.0 * M01, co[7], M11 * co[8]))));
+            acc[3] += h;
+            acc[4] += fma(-dt * aa, abar_a, fma(bbar_a, dba, ha2 * gd));
+        }
+    }
+    __syncthreads();
+    // Pb <- F^T Pb F (upper blocks, mirrored) and mb <- F^T mb
+    for (int qq = tid; qq < s.nb; qq += blockDim.x) {
+        const int I = s.pairs[2 * qq], J = s.pairs[2 * qq + 1];
+        const double aI = s.co[kCo * I], bI = s.co[kCo * I + 1], aJ = s.co[kCo * J], bJ = s.co[kCo * J + 1];
+        double X[3][3];
+        for (int u = 0; u < 3; ++u)
+            for (int v = 0; v < 3; ++v) X[u][v] = s.Pb[(3 * I + u) * n + 3 * J + v];
+        double Y[3][3];   // F_I^T X
+        for (int v = 0; v < 3; ++v) {
+            Y[0][v] = X[0][v];
+            Y[1][v] = fma(bI, X[0][v], aI * X[1][v]);
+            Y[2][v] = fma(ba, X[0][v], aa * X[2][v]);
+        }
+        for (int u = 0; u < 3; ++u) {   // (F_I^T X) F_J
+            const double z0 = Y[u][0];
+            const double z1 = fma(bJ, Y[u][0], aJ * Y[u][1]);
+            const double z2 = fma(ba, Y[u][0], aa * Y[u][2]);
+            s.Pb[(3 * I + u) * n + 3 * J] = z0;
+            s.Pb[(3 * I + u) * n + 3 * J + 1] = z1;
+            s.Pb[(3 * I + u) * n + 3 * J + 2] = z2;
+            s.Pb[(3 * J) * n + 3 * I + u] = z0;
+            s.Pb[(3 * J + 1) * n + 3 * I + u] = z1;
+            s.Pb[(3 * J + 2) * n + 3 * I + u] = z2;
+        }
+    }
+    for (int J = tid; J < P; J += blockDim.x) {
+        double* mJ = s.mb + 3 * J;
+        const double m0 = mJ[0];
+        mJ[1] = fma(s.co[kCo * J + 1], m0, s.co[kCo * J] * mJ[1]);
+        mJ[2] = fma(ba, m0, aa * mJ[2]);
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kGwbThreads) k_gwb_grad(GwbArgs a) {
+    extern __shared__ __align__(16) double gsm[];
+    const GwbSmem s = gwb_carve(gsm, a.P, true);
+    const int P = s.P, n = s.n, D = 2 + 3 * P;
+    const int64_t rec_len = s.ne + n;
+    double* ck = a.ckpt + int64_t(blockIdx.x) * a.slot;
+    double* tp = a.tape + int64_t(blockIdx.x) * a.slot;
+    gwb_tables(s, a);
+    for (int64_t b = blockIdx.x; b < a.B; b += gridDim.x) {
+        double* gout = a.grad + b * D;
+        __syncthreads();
+        if (!gwb_setup(s, a, a.theta + b * D)) {
+            for (int j = threadIdx.x; j < D; j += blockDim.x) gout[j] = 0.0;
+            if (threadIdx.x == 0) a.loglik[b] = -INFINITY;
+            continue;
+        }
+        // forward, with the state saved at each segment start
+        double quad = 0.0;
+        LogProd lp;
+        for (int seg = 0; seg < a.nseg; ++seg) {
+            gwb_save(s, ck + seg * rec_len);
+            const int64_t k1 = min(int64_t(seg + 1) * a.L, a.N);
+            for (int64_t k = int64_t(seg) * a.L; k < k1; ++k) gwb_step<true>(s, a, a.rec[k], quad, lp);
+        }
+        if (threadIdx.x == 0) {
+            const double ll = gwb_finish(a.N, quad, lp);
             a.loglik[b] = ll;
+            s.gw[kGwOk] = isfinite(ll) ? 1.0 : 0.0;
+        }
+        for (int i = threadIdx.x; i < n * n; i += blockDim.x) s.Pb[i] = 0.0;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) s.mb[i] = 0.0;
+        for (int i = threadIdx.x; i < 5 * P; i += blockDim.x) s.acc[i] = 0.0;
+        __syncthreads();
+        if (s.gw[kGwOk] == 0.0 || a.N == 0) {
+            for (int j = threadIdx.x; j < D; j += blockDim.x) gout[j] = 0.0;
+            continue;
+        }
+        // reverse, segment by segment: re-run the segment saving the state
+        // before each step, then the adjoint steps in reverse order
+        for (int seg = a.nseg - 1; seg >= 0; --seg) {
+            const int64_t k0 = int64_t(seg) * a.L, k1 = min(k0 + a.L, a.N);
+            gwb_load(s, ck + seg * rec_len);
+            __syncthreads();
+            for (int64_t k = k0; k < k1; ++k) {
+                gwb_save(s, tp + (k - k0) * rec_len);
+                gwb_step<false>(s, a, a.rec[k], quad, lp);
+            }
+            for (int64_t k = k1 - 1; k >= k0; --k) {
+                __syncthreads();
+                gwb_load(s, tp + (k - k0) * rec_len);
+                __syncthreads();
+                gwb_step_adjoint(s, a, a.rec[k]);
+            }
+        }
+        // the stationary prior of the a block: h_a^2 G / (2 gamma_a)
+        const double ha2 = s.gw[kGwHa2], ga = s.gw[kGwGa];
+        for (int I = threadIdx.x; I < P; I += blockDim.x) {
+            double h = 0.0;
+            for (int J = 0; J < P; ++J) h = fma(s.Pb[(3 * I + 2) * n + 3 * J + 2], s.G[I * P + J], h);
+            s.acc[5 * I + 3] += h / (2.0 * ga);
+            s.acc[5 * I + 4] -= h * ha2 / (2.0 * ga * ga);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double hb = 0.0, gb = 0.0;
+            for (int I = 0; I < P; ++I) { hb += s.acc[5 * I + 3]; gb += s.acc[5 * I + 4]; }
+            gout[0] = hb * 2.0 * kLn10Gwb * ha2;
+            gout[1] = gb * kLn10Gwb * ga;
+        }
+        for (int p = threadIdx.x; p < P; p += blockDim.x) {
+            gout[2 + 3 * p] = s.acc[5 * p] * 2.0 * kLn10Gwb * s.par[4 * p];
+            gout[3 + 3 * p] = s.acc[5 * p + 1] * kLn10Gwb * s.par[4 * p + 1];
+            gout[4 + 3 * p] = s.acc[5 * p + 2];
         }
     }
 }
@@ -250,6 +597,10 @@ struct argus_gwb {
     double* d_G = nullptr;
     double* d_stage = nullptr;
     size_t cap_stage = 0;
+    // gradient: per resident block, the segment-start states and one segment's tape
+    double* d_ckpt = nullptr;
+    double* d_tape = nullptr;
+    size_t cap_ckpt = 0;
 };
 
 namespace {
@@ -357,9 +708,10 @@ argus_status argus_gwb_create(const argus_pulsar* psrs, int32_t n_pulsars, int32
         return bail(e, "cudaMemcpy");
     // the kernel's dynamic shared memory limit, set for the largest array any
     // handle may hold (a per-function setting shared by all handles)
-    const size_t smem_max = gwb_smem_bytes(kGwbMaxPulsars);
-    if ((e = cudaFuncSetAttribute(k_gwb_filter, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_max))) !=
-        cudaSuccess)
+    if ((e = cudaFuncSetAttribute(k_gwb_filter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  int(gwb_smem_bytes(kGwbMaxPulsars, false)))) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(k_gwb_grad, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  int(gwb_smem_bytes(kGwbGradMaxPulsars, true)))) != cudaSuccess)
         return bail(e, "cudaFuncSetAttribute");
     if (prev >= 0) cudaSetDevice(prev);
     *out = h;
@@ -377,6 +729,8 @@ void argus_gwb_destroy(argus_gwb* h) {
     cudaFree(h->d_equad2);
     cudaFree(h->d_G);
     cudaFree(h->d_stage);
+    cudaFree(h->d_ckpt);
+    cudaFree(h->d_tape);
     if (prev >= 0) cudaSetDevice(prev);
     delete h;
 }
@@ -422,8 +776,10 @@ argus_status argus_gwb_loglik(argus_gwb* h, const double* theta, int64_t B, doub
         if (!dev_out) ll_d = h->d_stage + size_t(B) * D;
     }
     {
-        GwbArgs a{h->d_rec, h->N, h->P, h->d_p0, h->d_equad2, h->d_G, th_d, B, ll_d};
-        const size_t smem = gwb_smem_bytes(h->P);
+        GwbArgs a{};
+        a.rec = h->d_rec; a.N = h->N; a.P = h->P; a.p0 = h->d_p0; a.equad2 = h->d_equad2; a.G = h->d_G;
+        a.theta = th_d; a.B = B; a.loglik = ll_d;
+        const size_t smem = gwb_smem_bytes(h->P, false);
         const int grid = int(std::min<int64_t>(B, int64_t(h->n_sm) * 8));
         k_gwb_filter<<<grid, kGwbThreads, smem, s>>>(a);
         if ((e = cudaGetLastError()) != cudaSuccess) {
@@ -437,6 +793,101 @@ argus_status argus_gwb_loglik(argus_gwb* h, const double* theta, int64_t B, doub
             }
         }
         if (!dev_in || !dev_out) {
+            if ((e = cudaStreamSynchronize(s)) != cudaSuccess) st = argus_status(gwb_cuda(e, "cudaStreamSynchronize"));
+        }
+    }
+done:
+    if (prev >= 0) cudaSetDevice(prev);
+    return st;
+}
+
+argus_status argus_gwb_loglik_grad(argus_gwb* h, const double* theta, int64_t B, double* loglik,
+                                   double* grad, void* stream) {
+    if (!h) return argus_status(gwb_fail(ARGUS_ERR_INVALID_ARG, "handle is NULL"));
+    if (B < 0) return argus_status(gwb_fail(ARGUS_ERR_INVALID_ARG, "B must be >= 0"));
+    if (B == 0) return ARGUS_OK;
+    if (!theta || !loglik || !grad)
+        return argus_status(gwb_fail(ARGUS_ERR_INVALID_ARG, "theta, loglik or grad is NULL"));
+    if (h->P > kGwbGradMaxPulsars)
+        return argus_status(gwb_fail(ARGUS_ERR_UNSUPPORTED, "the joint filter's gradient holds at most 32 pulsars"));
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice(h->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int D = 2 + 3 * h->P, n = 3 * h->P;
+    const bool dev_in = gwb_is_device_ptr(theta), dev_ll = gwb_is_device_ptr(loglik),
+               dev_g = gwb_is_device_ptr(grad);
+    const double* th_d = theta;
+    double *ll_d = loglik, *g_d = grad;
+    cudaError_t e = cudaSuccess;
+    argus_status st = ARGUS_OK;
+    const size_t smem = gwb_smem_bytes(h->P, true);
+    int per_sm = 1;
+    const int L = std::max(1, int(std::ceil(std::sqrt(double(std::max<int64_t>(h->N, 1))))));
+    const int nseg = int((h->N + L - 1) / L);
+    const size_t slot = size_t(std::max(nseg, L)) * (size_t(n) * (n + 1) / 2 + n);
+    int grid = 1;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gwb_grad, kGwbThreads, smem)) != cudaSuccess) {
+        st = argus_status(gwb_cuda(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor"));
+        goto done;
+    }
+    grid = int(std::min<int64_t>(B, int64_t(h->n_sm) * std::max(per_sm, 1)));
+    if (slot * grid > h->cap_ckpt) {
+        cudaFree(h->d_ckpt);
+        cudaFree(h->d_tape);
+        h->d_ckpt = h->d_tape = nullptr;
+        h->cap_ckpt = 0;
+        if ((e = cudaMalloc(&h->d_ckpt, slot * grid * sizeof(double))) != cudaSuccess ||
+            (e = cudaMalloc(&h->d_tape, slot * grid * sizeof(double))) != cudaSuccess) {
+            st = argus_status(gwb_cuda(e, "cudaMalloc(gradient scratch)"));
+            goto done;
+        }
+        h->cap_ckpt = slot * grid;
+    }
+    if (!dev_in || !dev_ll || !dev_g) {
+        const size_t need = size_t(B) * (2 * D + 1);
+        if (need > h->cap_stage) {
+            cudaFree(h->d_stage);
+            h->d_stage = nullptr;
+            h->cap_stage = 0;
+            if ((e = cudaMalloc(&h->d_stage, need * sizeof(double))) != cudaSuccess) {
+                st = argus_status(gwb_cuda(e, "cudaMalloc(stage)"));
+                goto done;
+            }
+            h->cap_stage = need;
+        }
+        if (!dev_in) {
+            if ((e = cudaMemcpyAsync(h->d_stage, theta, sizeof(double) * B * D, cudaMemcpyHostToDevice, s)) !=
+                cudaSuccess) {
+                st = argus_status(gwb_cuda(e, "cudaMemcpyAsync(theta)"));
+                goto done;
+            }
+            th_d = h->d_stage;
+        }
+        if (!dev_ll) ll_d = h->d_stage + size_t(B) * D;
+        if (!dev_g) g_d = h->d_stage + size_t(B) * (D + 1);
+    }
+    {
+        GwbArgs a{};
+        a.rec = h->d_rec; a.N = h->N; a.P = h->P; a.p0 = h->d_p0; a.equad2 = h->d_equad2; a.G = h->d_G;
+        a.theta = th_d; a.B = B; a.loglik = ll_d; a.grad = g_d;
+        a.ckpt = h->d_ckpt; a.tape = h->d_tape; a.slot = int64_t(slot); a.L = L; a.nseg = nseg;
+        k_gwb_grad<<<grid, kGwbThreads, smem, s>>>(a);
+        if ((e = cudaGetLastError()) != cudaSuccess) {
+            st = argus_status(gwb_cuda(e, "k_gwb_grad"));
+            goto done;
+        }
+        if (!dev_ll &&
+            (e = cudaMemcpyAsync(loglik, ll_d, sizeof(double) * B, cudaMemcpyDeviceToHost, s)) != cudaSuccess) {
+            st = argus_status(gwb_cuda(e, "cudaMemcpyAsync(loglik)"));
+            goto done;
+        }
+        if (!dev_g &&
+            (e = cudaMemcpyAsync(grad, g_d, sizeof(double) * B * D, cudaMemcpyDeviceToHost, s)) != cudaSuccess) {
+            st = argus_status(gwb_cuda(e, "cudaMemcpyAsync(grad)"));
+            goto done;
+        }
+        if (!dev_in || !dev_ll || !dev_g) {
             if ((e = cudaStreamSynchronize(s)) != cudaSuccess) st = argus_status(gwb_cuda(e, "cudaStreamSynchronize"));
         }
     }

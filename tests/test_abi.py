@@ -117,6 +117,7 @@ def test_gwb_create_rejects_too_many_pulsars_and_bad_data(lib):
     assert lib.argus_gwb_create(ps, 2, 0, ctypes.byref(h)) == 1 and h.value is None
     assert lib.argus_gwb_dim(None) == -1
     assert lib.argus_gwb_loglik(None, None, 1, None, None) == 1
+    assert lib.argus_gwb_loglik_grad(None, None, 1, None, None, None) == 1
 
 
 def test_calls_on_null_handle_are_rejected(lib):

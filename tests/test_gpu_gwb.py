@@ -104,3 +104,73 @@ def test_batch_larger_than_the_grid(argus):
     ll = run(argus, arr, theta)
     idx = np.array([0, 1, 1215, 1216, 2999])
     assert ll_err(ll[idx], gwb.loglik(data, theta[idx])) <= LL_TOL
+
+
+G_TOL = 1e-6
+
+
+def g_err(g, ref):
+    g, ref = np.atleast_2d(g), np.atleast_2d(ref)
+    scale = np.maximum(np.abs(ref), 1e-3 * np.abs(ref).max(axis=1, keepdims=True))
+    return np.nan_to_num(np.abs(g - ref) / scale, nan=np.inf).max()
+
+
+@pytest.mark.parametrize("sizes", [[40], [30, 50, 20], [0, 25, 1, 60], [15] * 8])
+def test_gradient_parity_small_arrays(argus, sizes):
+    data = inputs.make_array(np.array(sizes), seed=510 + len(sizes), equad=1e-8)
+    theta = thetas(len(sizes), 5, np.random.default_rng(10 + len(sizes)), lh=(-19.5, -18.3))
+    arr = argus.GwbArray(data)
+    th = torch.from_numpy(theta).cuda()
+    ll, g = argus.argus_gwb_loglik_grad(arr, th)
+    ll, g = ll.cpu().numpy(), g.cpu().numpy()
+    ll_ref, g_ref = gwb.loglik_grad(data, theta)
+    assert ll_err(ll, ll_ref) <= LL_TOL
+    assert ll_err(ll, run(argus, arr, theta)) <= 1e-13
+    assert g_err(g, g_ref) <= G_TOL
+
+
+def test_gradient_with_equal_times(argus):
+    data = inputs.make_array(np.array([40, 35, 25]), seed=511)
+    a, b = data.off[1], data.off[2]
+    data.t[a:a + 10] = data.t[3:13]
+    data.t[a:b] = np.sort(data.t[a:b])
+    data.t[b + 2:b + 5] = data.t[b + 2]
+    theta = thetas(3, 4, np.random.default_rng(12), lh=(-19.5, -18.3))
+    arr = argus.GwbArray(data)
+    ll, g = argus.argus_gwb_loglik_grad(arr, torch.from_numpy(theta).cuda())
+    ll_ref, g_ref = gwb.loglik_grad(data, theta)
+    assert ll_err(ll.cpu().numpy(), ll_ref) <= LL_TOL
+    assert g_err(g.cpu().numpy(), g_ref) <= G_TOL
+
+
+def test_gradient_twenty_pulsars_vs_gpu_finite_differences(argus):
+    """20 pulsars: Richardson central differences of the GPU likelihood."""
+    data = inputs.make_array(np.full(20, 60), seed=512, equad=1e-8)
+    th0 = thetas(20, 1, np.random.default_rng(13), lh=(-19.0, -18.6))[0]
+    arr = argus.GwbArray(data)
+    _, g = argus.argus_gwb_loglik_grad(arr, torch.from_numpy(th0[None, :]).cuda())
+    g = g.cpu().numpy()[0]
+    D = len(th0)
+    rows = []
+    for j in range(D):
+        for h in (1e-4, 5e-5):
+            for sgn in (1, -1):
+                x = th0.copy(); x[j] += sgn * h
+                rows.append(x)
+    ll = run(argus, arr, np.array(rows))
+    fd = np.array([(4 * (ll[4 * j + 2] - ll[4 * j + 3]) / 1e-4 - (ll[4 * j] - ll[4 * j + 1]) / 2e-4) / 3
+                   for j in range(D)])
+    assert g_err(g, fd) <= 1e-5
+
+
+def test_gradient_out_of_domain_and_host_pointers(argus):
+    data = inputs.make_array(np.array([30, 40]), seed=513)
+    theta = thetas(2, 4, np.random.default_rng(14))
+    theta[0, 4] = -1.0
+    arr = argus.GwbArray(data)
+    ll_h, g_h = argus.argus_gwb_loglik_grad(arr, theta)         # numpy (staged)
+    ll_d, g_d = argus.argus_gwb_loglik_grad(arr, torch.from_numpy(theta).cuda())
+    assert np.array_equal(ll_h, ll_d.cpu().numpy()) and np.array_equal(g_h, g_d.cpu().numpy())
+    assert np.isneginf(ll_h[0]) and np.all(g_h[0] == 0.0)
+    ll_ref, g_ref = gwb.loglik_grad(data, theta[1:])
+    assert ll_err(ll_h[1:], ll_ref) <= LL_TOL and g_err(g_h[1:], g_ref) <= G_TOL
