@@ -88,16 +88,20 @@ struct GwbSmem {
     double* u;      // [n]      (gradient)
     double* v;      // [n]      (gradient)
     double* acc;    // [P][5]: d/d sigma^2, d/d gamma_p, d/d EFAC, d/d h_a^2 part, d/d gamma_a part
+    double* part;   // [P][chunks][6]: partial sums of the parameter terms
     uint16_t* pairs;
     uint8_t* ent;
 };
 // scalar slots of gw[]
 enum { kGwA = 0, kGwHa2 = 9, kGwGa, kGwE, kGwS, kGwRS, kGwG, kGwOk, kGwSb, kGwEb, kGwR0, kGwSlots = 20 };
 
+// chunks per pulsar of the adjoint's parameter sums (k ranges of about 8)
+__host__ __device__ inline int gwb_chunks(int P) { return (3 * P + 7) / 8; }
+
 __host__ __device__ inline size_t gwb_smem_doubles(int P, bool grad) {
     const size_t n = 3 * size_t(P);
     size_t d = n * n + 2 * n + kCo * size_t(P) + size_t(P) * P + 4 * size_t(P) + kGwSlots;
-    if (grad) d += n * n + 3 * n + 5 * size_t(P);
+    if (grad) d += n * n + 3 * n + 5 * size_t(P) + 6 * size_t(P) * gwb_chunks(P);
     return d;
 }
 
@@ -127,8 +131,9 @@ __device__ GwbSmem gwb_carve(double* base, int P, bool grad) {
         s.u = q; q += n;
         s.v = q; q += n;
         s.acc = q; q += 5 * P;
+        s.part = q; q += 6 * P * gwb_chunks(P);
     } else {
-        s.Pb = s.mb = s.u = s.v = s.acc = nullptr;
+        s.Pb = s.mb = s.u = s.v = s.acc = s.part = nullptr;
     }
     s.pairs = reinterpret_cast<uint16_t*>(q);
     s.ent = reinterpret_cast<uint8_t*>(s.pairs + 2 * s.nb);
@@ -137,6 +142,13 @@ __device__ GwbSmem gwb_carve(double* base, int P, bool grad) {
 
 __device__ __forceinline__ double psym(const double* M, int n, int i, int j) {
     return i <= j ? M[i * n + j] : M[j * n + i];
+}
+
+// sum over a warp in a fixed order (the same tree on every call)
+__device__ __forceinline__ double warp_sum(double x) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
+    return x;
 }
 
 // tables and HD matrix, once per block
@@ -379,21 +391,25 @@ __device__ void gwb_step_adjoint(const GwbSmem& s, const GwbArgs& a, const GwbRe
         const double rS = rcp_nr(S);
         gw[kGwS] = S; gw[kGwRS] = rS; gw[kGwG] = gw[kGwE] * rS;
     }
-    // v = Pb c
+    // v = Pb c, one thread per row (the fewest FP64 warp instructions)
     for (int j = tid; j < n; j += blockDim.x) {
         double acc = 0.0;
         for (int k = 0; k < n; ++k) acc = fma(s.Pb[j * n + k], s.c[k], acc);
         s.v[j] = acc;
     }
     __syncthreads();
-    if (tid == 0) {
-        const double rS = gw[kGwRS], g = gw[kGwG];
+    if (warp == 0) {
         double gb = 0.0, cv = 0.0;
-        for (int k = 0; k < n; ++k) { gb = fma(s.mb[k], s.c[k], gb); cv = fma(s.c[k], s.v[k], cv); }
-        const double Sb = rS * rS * cv - gb * g * rS - 0.5 * rS + 0.5 * g * g;
-        gw[kGwSb] = Sb;
-        gw[kGwEb] = gb * rS - g;
-        s.acc[5 * q + 2] += Sb * 2.0 * s.par[4 * q + 3] * rk.s2;     // d/d EFAC_q
+        for (int k = lane; k < n; k += 32) { gb = fma(s.mb[k], s.c[k], gb); cv = fma(s.c[k], s.v[k], cv); }
+        gb = warp_sum(gb);
+        cv = warp_sum(cv);
+        if (lane == 0) {
+            const double rS = gw[kGwRS], g = gw[kGwG];
+            const double Sb = rS * rS * cv - gb * g * rS - 0.5 * rS + 0.5 * g * g;
+            gw[kGwSb] = Sb;
+            gw[kGwEb] = gb * rS - g;
+            s.acc[5 * q + 2] += Sb * 2.0 * s.par[4 * q + 3] * rk.s2;     // d/d EFAC_q
+        }
     }
     __syncthreads();
     // c-bar, the symmetric M-bar (row and column i of Pb) and mu-bar (in mb)
@@ -412,12 +428,17 @@ __device__ void gwb_step_adjoint(const GwbSmem& s, const GwbArgs& a, const GwbRe
     }
     __syncthreads();
     if (!pred) return;   // F = I, Q = 0: the adjoints pass through
-    // parameters through F and Q: one warp per pulsar
+    // parameters through F and Q, in two levels: work item (I, chunk) forms
+    // partial sums over its share of k (for F-bar) and of J (for the GW part
+    // of Q-bar); then one thread per pulsar adds its chunks in fixed order
     const double aa = gw[0], dba = gw[5], dca00 = gw[6], dca01 = gw[7], dca11 = gw[8];
-    for (int I = warp; I < P; I += nw) {
+    const int nch = gwb_chunks(P), kc = (n + nch - 1) / nch, jc = (P + nch - 1) / nch;
+    for (int it = tid; it < P * nch; it += blockDim.x) {
+        const int I = it / nch, ch = it - I * nch;
         const int rI = 3 * I, yI = rI + 1, aI = rI + 2;
         double s1 = 0.0, s2 = 0.0, s3 = 0.0, s4 = 0.0, h = 0.0, gd = 0.0;
-        for (int k = lane; k < n; k += 32) {
+        const int k_hi = min(n, (ch + 1) * kc);
+        for (int k = ch * kc; k < k_hi; ++k) {
             const int J = k / 3, cmp = k - 3 * J;
             double fpy, fpa;   // (F P)[k, yI], (F P)[k, aI]
             if (cmp == 0) {
@@ -437,37 +458,38 @@ __device__ void gwb_step_adjoint(const GwbSmem& s, const GwbArgs& a, const GwbRe
             s3 = fma(s.Pb[rI * n + k], fpa, s3);
             s4 = fma(s.Pb[aI * n + k], fpa, s4);
         }
-        for (int J = lane; J < P; J += 32) {
+        const int j_hi = min(P, (ch + 1) * jc);
+        for (int J = ch * jc; J < j_hi; ++J) {
             const double g = s.G[I * P + J];
             const double X00 = s.Pb[rI * n + 3 * J], X02 = s.Pb[rI * n + 3 * J + 2];
             const double X20 = s.Pb[aI * n + 3 * J], X22 = s.Pb[aI * n + 3 * J + 2];
             h = fma(g, fma(X00, gw[2], fma(X02 + X20, gw[3], X22 * gw[4])), h);
             gd = fma(g, fma(X00, dca00, fma(X02 + X20, dca01, X22 * dca11)), gd);
         }
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            s1 += __shfl_down_sync(0xffffffffu, s1, off);
-            s2 += __shfl_down_sync(0xffffffffu, s2, off);
-            s3 += __shfl_down_sync(0xffffffffu, s3, off);
-            s4 += __shfl_down_sync(0xffffffffu, s4, off);
-            h += __shfl_down_sync(0xffffffffu, h, off);
-            gd += __shfl_down_sync(0xffffffffu, gd, off);
+        double* pt = s.part + 6 * (I * nch + ch);
+        pt[0] = s1; pt[1] = s2; pt[2] = s3; pt[3] = s4; pt[4] = h; pt[5] = gd;
+    }
+    __syncthreads();
+    for (int I = tid; I < P; I += blockDim.x) {
+        const int rI = 3 * I, yI = rI + 1, aI = rI + 2;
+        double s1 = 0.0, s2 = 0.0, s3 = 0.0, s4 = 0.0, h = 0.0, gd = 0.0;
+        for (int ch = 0; ch < nch; ++ch) {
+            const double* pt = s.part + 6 * (I * nch + ch);
+            s1 += pt[0]; s2 += pt[1]; s3 += pt[2]; s4 += pt[3]; h += pt[4]; gd += pt[5];
         }
-        if (lane == 0) {
-            const double* co = s.co + kCo * I;
-            const double bbar_p = fma(2.0, s1, s.mb[rI] * s.m[yI]);
-            const double abar_p = fma(2.0, s2, s.mb[yI] * s.m[yI]);
-            const double bbar_a = fma(2.0, s3, s.mb[rI] * s.m[aI]);
-            const double abar_a = fma(2.0, s4, s.mb[aI] * s.m[aI]);
-            const double M00 = s.Pb[rI * n + rI], M01 = s.Pb[rI * n + yI], M11 = s.Pb[yI * n + yI];
-            const double s2p = s.par[4 * I];
-            double* acc = s.acc + 5 * I;
-            acc[0] += fma(M00, co[2], fma(2.0 * M01, co[3], M11 * co[4]));
-            acc[1] += fma(-dt * co[0], abar_p, fma(bbar_p, co[5],
-                          s2p * fma(M00, co[6], fma(2.0 * M01, co[7], M11 * co[8]))));
-            acc[3] += h;
-            acc[4] += fma(-dt * aa, abar_a, fma(bbar_a, dba, ha2 * gd));
-        }
+        const double* co = s.co + kCo * I;
+        const double bbar_p = fma(2.0, s1, s.mb[rI] * s.m[yI]);
+        const double abar_p = fma(2.0, s2, s.mb[yI] * s.m[yI]);
+        const double bbar_a = fma(2.0, s3, s.mb[rI] * s.m[aI]);
+        const double abar_a = fma(2.0, s4, s.mb[aI] * s.m[aI]);
+        const double M00 = s.Pb[rI * n + rI], M01 = s.Pb[rI * n + yI], M11 = s.Pb[yI * n + yI];
+        const double s2p = s.par[4 * I];
+        double* acc = s.acc + 5 * I;
+        acc[0] += fma(M00, co[2], fma(2.0 * M01, co[3], M11 * co[4]));
+        acc[1] += fma(-dt * co[0], abar_p, fma(bbar_p, co[5],
+                      s2p * fma(M00, co[6], fma(2.0 * M01, co[7], M11 * co[8]))));
+        acc[3] += h;
+        acc[4] += fma(-dt * aa, abar_a, fma(bbar_a, dba, ha2 * gd));
     }
     __syncthreads();
     // Pb <- F^T Pb F (upper blocks, mirrored) and mb <- F^T mb
