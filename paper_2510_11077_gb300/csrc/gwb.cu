@@ -206,7 +206,7 @@ __device__ void gwb_coef(const GwbSmem& s, double dt) {
     for (int p = threadIdx.x; p <= s.P; p += blockDim.x) {
         OuCoef oc;
         const double gam = (p < s.P) ? s.par[4 * p + 1] : s.gw[kGwGa];
-        ou_coef<kDeriv>(gam * dt, dt, h2, h3, dt2, oc);
+        ou_coef_warp<kDeriv>(gam * dt, dt, h2, h3, dt2, oc);
         double* o = (p < s.P) ? s.co + kCo * p : s.gw + kGwA;
         o[0] = oc.a; o[1] = oc.b; o[2] = oc.c00; o[3] = oc.c01; o[4] = oc.c11;
         if (kDeriv) { o[5] = oc.db; o[6] = oc.dc00; o[7] = oc.dc01; o[8] = oc.dc11; }

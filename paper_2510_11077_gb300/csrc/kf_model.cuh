@@ -71,16 +71,18 @@ __device__ __forceinline__ double psi4_series(double x) {
     return psi4_horner<N - 2>(x, Psi4Coef<N - 1>::value);
 }
 
+// hsel: the high word that picks the series length (x's own, or a larger
+// one shared by a warp; a longer series is never less accurate)
 template <bool kDeriv>
-__device__ __forceinline__ void ou_coef(double x, double dt, double h2, double h3, double dt2,
-                                        OuCoef& c) {
+__device__ __forceinline__ void ou_coef_sel(double x, int hsel, double dt, double h2, double h3,
+                                            double dt2, OuCoef& c) {
     double p1, p2, phi4, dphi4 = 0.0;
     const int hx = __double2hiint(x);
     if (hx < 0x3FE00000) {                       // x < 2^-1
         double p4;
-        if (hx < 0x3F700000) p4 = psi4_series<5>(x);          // x < 2^-8
-        else if (hx < 0x3F900000) p4 = psi4_series<7>(x);     // x < 2^-6
-        else if (hx < 0x3FC00000) p4 = psi4_series<10>(x);    // x < 2^-3
+        if (hsel < 0x3F700000) p4 = psi4_series<5>(x);          // x < 2^-8
+        else if (hsel < 0x3F900000) p4 = psi4_series<7>(x);     // x < 2^-6
+        else if (hsel < 0x3FC00000) p4 = psi4_series<10>(x);    // x < 2^-3
         else p4 = psi4_series<14>(x);
         const double p3 = fma(-x, p4, 1.0 / 6.0);
         p2 = fma(-x, p3, 0.5);
@@ -110,6 +112,25 @@ __device__ __forceinline__ void ou_coef(double x, double dt, double h2, double h
         c.dc01 = (3.0 * h3) * (p1 * dp1);          // dt^3 psi1 psi1'
         c.dc11 = dt2 * fma(c.a, dp1, -0.5 * p1sq); // dt^2 (a psi1' - psi1^2 / 2)
     }
+}
+
+template <bool kDeriv>
+__device__ __forceinline__ void ou_coef(double x, double dt, double h2, double h3, double dt2,
+                                        OuCoef& c) {
+    ou_coef_sel<kDeriv>(x, __double2hiint(x), dt, h2, h3, dt2, c);
+}
+
+// The same for lanes of one warp with different x (e.g. the pulsars of an
+// array): every lane on the series branch uses the series length of the
+// warp's largest such x, so the warp runs one series instead of several in
+// turn.  All active lanes must call it together.
+template <bool kDeriv>
+__device__ __forceinline__ void ou_coef_warp(double x, double dt, double h2, double h3, double dt2,
+                                             OuCoef& c) {
+    const int hx = __double2hiint(x);
+    const unsigned key = (hx < 0x3FE00000) ? unsigned(hx) : 0u;
+    const int hmax = int(__reduce_max_sync(__activemask(), key));
+    ou_coef_sel<kDeriv>(x, hmax, dt, h2, h3, dt2, c);
 }
 
 template <bool kOU>
