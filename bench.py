@@ -404,10 +404,24 @@ LATENCY_WORKLOAD = "psr1_toa1000"
 
 
 def gwb_flops_per_toa(P: int) -> int:
-    """Algorithmic FP64 flops of one TOA of the joint filter (FMA = 2): the
-    predict of each upper 3x3 block (F_I X: 18, (F_I X) F_J^T: 18, Q: 8), the
-    symmetric rank-1 update of the 3P x 3P covariance (3 per upper entry) and
-    the mean (10 per pulsar)."""
+    """Algorithmic FP64 flops of one TOA of the joint filter in the scaled
+    frame that k_gwb_filter runs (FMA = 2).  The decays are carried in scale
+    factors, so the transition is the identity but for each pulsar's rho row.
+    The predict of an upper 3x3 block then changes only its rho row and
+    column: 12 FMA for (Fh X Fh^T) and 4 for the GW process noise, 32 flops
+    (a diagonal block: 8 + 4 FMA and 3 adds, 25).  Per pulsar the mean
+    predict costs 4.  The update costs 1 FMA per upper entry of the 3P x 3P
+    covariance, n multiplies for c/S and n FMA for the mean.  The textbook
+    unscaled filter takes 44 flops per block and 3 per upper entry
+    (gwb_flops_per_toa_unscaled)."""
+    n = 3 * P
+    return 32 * P * (P - 1) // 2 + 25 * P + 4 * P + n + n * (n + 1) + 2 * n
+
+
+def gwb_flops_per_toa_unscaled(P: int) -> int:
+    """FP64 flops of one TOA of the textbook joint filter: the predict of each
+    upper 3x3 block (F_I X: 18, (F_I X) F_J^T: 18, Q: 8), the symmetric
+    rank-1 update (3 per upper entry) and the mean (10 per pulsar)."""
     n = 3 * P
     return 44 * P * (P + 1) // 2 + 3 * n * (n + 1) // 2 + 10 * P
 
@@ -478,8 +492,10 @@ def gwb_leg(args, dev, local):
             "roofline": {"bound": "alu", "kernel": "k_gwb_filter", "kernel_ms": step_ms,
                          "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": achieved / FP64_PEAK_TFLOPS,
-                         "algorithmic": f"{gwb_flops_per_toa(P)} FP64 flop per TOA per parameter vector x "
-                                        f"{n_toa} TOAs x {GWB_BATCH}"}}
+                         "algorithmic": f"{gwb_flops_per_toa(P)} FP64 flop per TOA per parameter vector "
+                                        f"(scaled frame) x {n_toa} TOAs x {GWB_BATCH}",
+                         "textbook_flop_rate": gwb_flops_per_toa_unscaled(P) * n_toa * GWB_BATCH
+                         / (step_ms * 1e-3) / 1e12}}
 
 
 def latency_leg(args, dev, local):

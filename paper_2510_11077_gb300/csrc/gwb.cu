@@ -20,6 +20,17 @@
 //      P_ij -= (c_i c_j) / S; accumulate -1/2 (ln 2 pi + ln S + e^2 / S).
 // Steps 2-4 are spread over the block's threads with a barrier between them;
 // a TOA at the same time as the previous one skips the predict (F = I, Q = 0).
+//
+// Scaled frame (the likelihood pass).  The decays a_p of y_p and a_a of the
+// GW state are diagonal, so they are carried in scale factors instead of
+// the covariance: P = S Ph S, m = S mh with S = diag(1, s_p, s_a) per pulsar.
+// Since F_I S_I = S'_I Fh_I with S' = diag(1, s_p a_p, s_a a_a) and
+// Fh_I = [[1, b_p s_p, b_a s_a], [0, 1, 0], [0, 0, 1]], the predict becomes
+// Ph <- Fh Ph Fh^T + S'^-1 Q S'^-1 and only the rho rows and columns of each
+// block change (16 FP64 operations per block instead of 28).  The
+// observation picks rho_q, whose scale is 1, so c, S, e and the update keep
+// their form with Ph, mh.  A scale below 2^-200 (a fast decay over a long
+// gap) folds S back into Ph and takes that one predict unscaled.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -79,7 +90,11 @@ struct GwbSmem {
     double* Pm;     // [n][n]
     double* m;      // [n]
     double* c;      // [n]
-    double* co;     // [P][9]: a, b, Q/sigma^2 (c00, c01, c11), d/dgamma of b and of c00, c01, c11
+    double* co;     // [P][9]: a, b, Q/sigma^2 (c00, c01, c11), then d/dgamma of b and of c00, c01, c11
+                    // (gradient) or, scaled frame, b s_p, sigma^2 c00, sigma^2 c01 / s'_p, sigma^2 c11 / s'_p^2
+    double* ct;     // [n]: c / S
+    double* sg;     // [P + 1]: scale factors s_p and s_a (scaled frame)
+    double* sg0;    // [P + 1]: the scale factors before the current predict
     double* G;      // [P][P]
     double* par;    // [P][4]: sigma^2, gamma_p, EFAC^2, EFAC
     double* gw;     // GW process: a, b, c00, c01, c11, db, dc00, dc01, dc11 (per unit h_a^2); scalars
@@ -93,14 +108,15 @@ struct GwbSmem {
     uint8_t* ent;
 };
 // scalar slots of gw[]
-enum { kGwA = 0, kGwHa2 = 9, kGwGa, kGwE, kGwS, kGwRS, kGwG, kGwOk, kGwSb, kGwEb, kGwR0, kGwSlots = 20 };
+enum { kGwA = 0, kGwHa2 = 9, kGwGa, kGwE, kGwS, kGwRS, kGwG, kGwOk, kGwSb, kGwEb, kGwR0, kGwRn, kGwSlots = 20 };
+constexpr double kGwbTiny = 0x1p-200;   // smallest scale factor kept (scaled frame)
 
 // chunks per pulsar of the adjoint's parameter sums (k ranges of about 8)
 __host__ __device__ inline int gwb_chunks(int P) { return (3 * P + 7) / 8; }
 
 __host__ __device__ inline size_t gwb_smem_doubles(int P, bool grad) {
     const size_t n = 3 * size_t(P);
-    size_t d = n * n + 2 * n + kCo * size_t(P) + size_t(P) * P + 4 * size_t(P) + kGwSlots;
+    size_t d = n * n + 3 * n + kCo * size_t(P) + size_t(P) * P + 4 * size_t(P) + 2 * (size_t(P) + 1) + kGwSlots;
     if (grad) d += n * n + 3 * n + 5 * size_t(P) + 6 * size_t(P) * gwb_chunks(P);
     return d;
 }
@@ -122,6 +138,9 @@ __device__ GwbSmem gwb_carve(double* base, int P, bool grad) {
     s.m = q; q += n;
     s.c = q; q += n;
     s.co = q; q += kCo * P;
+    s.ct = q; q += n;
+    s.sg = q; q += P + 1;
+    s.sg0 = q; q += P + 1;
     s.G = q; q += size_t(P) * P;
     s.par = q; q += 4 * P;
     s.gw = q; q += kGwSlots;
@@ -175,7 +194,9 @@ __device__ bool gwb_setup(const GwbSmem& s, const GwbArgs& a, const double* th) 
         s.gw[kGwHa2] = exp10(2.0 * th[0]);
         s.gw[kGwGa] = exp10(th[1]);
         s.gw[kGwOk] = ok ? 1.0 : 0.0;
+        s.gw[kGwRn] = 0.0;
     }
+    for (int p = threadIdx.x; p <= P; p += blockDim.x) s.sg[p] = 1.0;
     for (int p = threadIdx.x; p < P; p += blockDim.x) {
         s.par[4 * p] = exp10(2.0 * th[2 + 3 * p]);
         s.par[4 * p + 1] = exp10(th[2 + 3 * p + 1]);
@@ -230,16 +251,20 @@ __device__ void gwb_predict(const GwbSmem& s) {
         const double apI = s.co[kCo * I], bpI = s.co[kCo * I + 1];
         const double apJ = s.co[kCo * J], bpJ = s.co[kCo * J + 1];
         double X[3][3];
+#pragma unroll
         for (int u = 0; u < 3; ++u)
+#pragma unroll
             for (int v = 0; v < 3; ++v)
                 X[u][v] = (I < J || u <= v) ? s.Pm[(3 * I + u) * n + 3 * J + v] : s.Pm[(3 * I + v) * n + 3 * J + u];
         double Y[3][3];   // F_I X
+#pragma unroll
         for (int v = 0; v < 3; ++v) {
             Y[0][v] = fma(bpI, X[1][v], fma(ba, X[2][v], X[0][v]));
             Y[1][v] = apI * X[1][v];
             Y[2][v] = aa * X[2][v];
         }
         double Z[3][3];   // (F_I X) F_J^T
+#pragma unroll
         for (int u = 0; u < 3; ++u) {
             Z[u][0] = fma(bpJ, Y[u][1], fma(ba, Y[u][2], Y[u][0]));
             Z[u][1] = apJ * Y[u][1];
@@ -257,46 +282,146 @@ __device__ void gwb_predict(const GwbSmem& s) {
             Z[1][0] = fma(s2, s.co[kCo * I + 3], Z[1][0]);
             Z[1][1] = fma(s2, s.co[kCo * I + 4], Z[1][1]);
         }
+#pragma unroll
         for (int u = 0; u < 3; ++u)
+#pragma unroll
             for (int v = 0; v < 3; ++v)
                 if (I < J || u <= v) s.Pm[(3 * I + u) * n + 3 * J + v] = Z[u][v];
     }
 }
 
-// 3. innovate on rho of pulsar q: c = P e_i; thread 0 forms e, S, 1/S, e/S
-__device__ void gwb_innovate(const GwbSmem& s, const GwbArgs& a, const GwbRec& rk) {
-    const int n = s.n, i0 = 3 * rk.q;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) s.c[i] = psym(s.Pm, n, i, i0);
-    if (threadIdx.x == 0) {
-        const double R = fma(s.par[4 * rk.q + 2], rk.s2, a.equad2[rk.q]);
-        const double e = rk.r - s.m[i0];
-        const double S = s.Pm[i0 * n + i0] + R;
-        const double rS = rcp_nr(S);
-        s.gw[kGwE] = e;
-        s.gw[kGwS] = S;
-        s.gw[kGwRS] = rS;
-        s.gw[kGwG] = e * rS;
+// 1'. scaled frame: the coefficients of 1. and those of Fh and S'^-1 Q S'^-1;
+// the scales advance to s' = s a, and a scale below kGwbTiny raises the flag
+__device__ void gwb_coef_scaled(const GwbSmem& s, double dt) {
+    const double h2 = 0.5 * dt * dt, h3 = dt * dt * dt / 3.0, dt2 = dt * dt;
+    for (int p = threadIdx.x; p <= s.P; p += blockDim.x) {
+        OuCoef oc;
+        const bool psr = p < s.P;
+        ou_coef_warp<false>((psr ? s.par[4 * p + 1] : s.gw[kGwGa]) * dt, dt, h2, h3, dt2, oc);
+        const double sg = s.sg[p], sn = sg * oc.a;
+        s.sg0[p] = sg;
+        s.sg[p] = sn;
+        if (!(sn >= kGwbTiny)) s.gw[kGwRn] = 1.0;
+        const double w = rcp_nr(sn), sc = psr ? s.par[4 * p] : s.gw[kGwHa2];
+        double* o = psr ? s.co + kCo * p : s.gw + kGwA;
+        o[0] = oc.a; o[1] = oc.b; o[2] = oc.c00; o[3] = oc.c01; o[4] = oc.c11;
+        o[5] = oc.b * sg;
+        o[6] = sc * oc.c00;
+        o[7] = sc * oc.c01 * w;
+        o[8] = sc * oc.c11 * w * w;
     }
 }
 
-// 4. update (upper triangle) and mean
-__device__ void gwb_update(const GwbSmem& s) {
-    const int n = s.n;
-    const double rS = s.gw[kGwRS], g = s.gw[kGwG];
+// 2'. scaled predict: mh <- Fh mh, Ph <- Fh Ph Fh^T + S'^-1 Q S'^-1 (upper
+// blocks); Fh is the identity but for the rho row (b_p s_p, b_a s_a)
+__device__ void gwb_predict_scaled(const GwbSmem& s) {
+    const int P = s.P, n = s.n;
+    const double al = s.gw[5], qa00 = s.gw[6], qa01 = s.gw[7], qa11 = s.gw[8];
+    for (int p = threadIdx.x; p < P; p += blockDim.x) {
+        double* mp = s.m + 3 * p;
+        mp[0] = fma(s.co[kCo * p + 5], mp[1], fma(al, mp[2], mp[0]));
+    }
+    for (int q = threadIdx.x; q < s.nb; q += blockDim.x) {
+        const int I = s.pairs[2 * q], J = s.pairs[2 * q + 1];
+        const double bI = s.co[kCo * I + 5], bJ = s.co[kCo * J + 5];
+        double* B = s.Pm + (3 * I) * n + 3 * J;
+        const double x00 = B[0], x01 = B[1], x02 = B[2], x11 = B[n + 1], x12 = B[n + 2], x22 = B[2 * n + 2];
+        const double x10 = I < J ? B[n] : x01, x20 = I < J ? B[2 * n] : x02, x21 = I < J ? B[2 * n + 1] : x12;
+        // row 0 of Fh_I X, then column 0 of (Fh_I X) Fh_J^T
+        const double y0 = fma(bI, x10, fma(al, x20, x00));
+        const double y1 = fma(bI, x11, fma(al, x21, x01));
+        const double y2 = fma(bI, x12, fma(al, x22, x02));
+        const double g = s.G[I * P + J];
+        double z00 = fma(g, qa00, fma(bJ, y1, fma(al, y2, y0)));
+        double z01 = y1;
+        const double z02 = fma(g, qa01, y2);
+        double z11 = x11;
+        const double z22 = fma(g, qa11, x22);
+        if (I == J) {
+            const double* co = s.co + kCo * I;
+            z00 += co[6];
+            z01 += co[7];
+            z11 += co[8];
+        } else {
+            B[n] = fma(bJ, x11, fma(al, x12, x10));
+            B[2 * n] = fma(g, qa01, fma(bJ, x21, fma(al, x22, x20)));
+        }
+        B[0] = z00; B[1] = z01; B[2] = z02; B[n + 1] = z11; B[2 * n + 2] = z22;
+    }
+}
+
+// scale of state i: 1 for rho, s_p for y_p, s_a for a_p
+__device__ __forceinline__ double gwb_scale_of(const double* sc, int P, int i) {
+    const int J = i / 3, cmp = i - 3 * J;
+    return cmp == 0 ? 1.0 : sc[cmp == 1 ? J : P];
+}
+
+// P = S Ph S, m = S mh for the scales sc (the upper triangle and the mean)
+__device__ void gwb_fold(const GwbSmem& s, const double* sc) {
+    const int n = s.n, P = s.P;
     for (int q = threadIdx.x; q < s.ne; q += blockDim.x) {
         const int r = s.ent[2 * q], col = s.ent[2 * q + 1];
-        s.Pm[r * n + col] = fma(-(s.c[r] * s.c[col]), rS, s.Pm[r * n + col]);
+        s.Pm[r * n + col] *= gwb_scale_of(sc, P, r) * gwb_scale_of(sc, P, col);
+    }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s.m[i] *= gwb_scale_of(sc, P, i);
+}
+
+// 3. innovate on rho of pulsar q: c = P e_i and c / S (the threads that form
+// c each form 1/S); thread 0 records e, S, 1/S, e/S
+__device__ void gwb_innovate(const GwbSmem& s, const GwbArgs& a, const GwbRec& rk) {
+    const int n = s.n, i0 = 3 * rk.q;
+    if (threadIdx.x < n) {
+        const double R = fma(s.par[4 * rk.q + 2], rk.s2, a.equad2[rk.q]);
+        const double S = s.Pm[i0 * n + i0] + R;
+        const double rS = rcp_nr(S);
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const double ci = psym(s.Pm, n, i, i0);
+            s.c[i] = ci;
+            s.ct[i] = ci * rS;
+        }
+        if (threadIdx.x == 0) {
+            const double e = rk.r - s.m[i0];
+            s.gw[kGwE] = e;
+            s.gw[kGwS] = S;
+            s.gw[kGwRS] = rS;
+            s.gw[kGwG] = e * rS;
+        }
+    }
+}
+
+// 4. update (upper triangle, P_ij -= c_i (c_j / S)) and mean
+__device__ void gwb_update(const GwbSmem& s) {
+    const int n = s.n;
+    const double g = s.gw[kGwG];
+    for (int q = threadIdx.x; q < s.ne; q += blockDim.x) {
+        const int r = s.ent[2 * q], col = s.ent[2 * q + 1];
+        s.Pm[r * n + col] = fma(-s.c[r], s.ct[col], s.Pm[r * n + col]);
     }
     for (int i = threadIdx.x; i < n; i += blockDim.x) s.m[i] = fma(s.c[i], g, s.m[i]);
 }
 
-// one forward step; thread 0 accumulates the likelihood when kLL
-template <bool kLL>
+// one forward step; thread 0 accumulates the likelihood when kLL; kScaled
+// keeps Ph, mh in the scaled frame
+template <bool kLL, bool kScaled = false>
 __device__ void gwb_step(const GwbSmem& s, const GwbArgs& a, const GwbRec& rk, double& quad, LogProd& lp) {
     if (rk.dt > 0.0) {
-        gwb_coef<false>(s, rk.dt);
-        __syncthreads();
-        gwb_predict(s);
+        if (kScaled) {
+            gwb_coef_scaled(s, rk.dt);
+            __syncthreads();
+            if (s.gw[kGwRn] != 0.0) {          // block-uniform and rare: unscale, predict unscaled
+                gwb_fold(s, s.sg0);
+                __syncthreads();
+                gwb_predict(s);
+                for (int p = threadIdx.x; p <= s.P; p += blockDim.x) s.sg[p] = 1.0;
+                if (threadIdx.x == 0) s.gw[kGwRn] = 0.0;
+            } else {
+                gwb_predict_scaled(s);
+            }
+        } else {
+            gwb_coef<false>(s, rk.dt);
+            __syncthreads();
+            gwb_predict(s);
+        }
         __syncthreads();
     }
     gwb_innovate(s, a, rk);
@@ -326,7 +451,7 @@ __global__ void __launch_bounds__(kGwbThreads) k_gwb_filter(GwbArgs a) {
         }
         double quad = 0.0;
         LogProd lp;
-        for (int64_t k = 0; k < a.N; ++k) gwb_step<true>(s, a, a.rec[k], quad, lp);
+        for (int64_t k = 0; k < a.N; ++k) gwb_step<true, true>(s, a, a.rec[k], quad, lp);
         if (threadIdx.x == 0) a.loglik[b] = gwb_finish(a.N, quad, lp);
     }
 }
@@ -545,10 +670,16 @@ __global__ void __launch_bounds__(kGwbThreads) k_gwb_grad(GwbArgs a) {
         // forward, with the state saved at each segment start
         double quad = 0.0;
         LogProd lp;
+        // (in the scaled frame, folded back at each segment start)
         for (int seg = 0; seg < a.nseg; ++seg) {
+            if (seg > 0) {
+                gwb_fold(s, s.sg);
+                __syncthreads();
+                for (int p = threadIdx.x; p <= P; p += blockDim.x) s.sg[p] = 1.0;
+            }
             gwb_save(s, ck + seg * rec_len);
             const int64_t k1 = min(int64_t(seg + 1) * a.L, a.N);
-            for (int64_t k = int64_t(seg) * a.L; k < k1; ++k) gwb_step<true>(s, a, a.rec[k], quad, lp);
+            for (int64_t k = int64_t(seg) * a.L; k < k1; ++k) gwb_step<true, true>(s, a, a.rec[k], quad, lp);
         }
         if (threadIdx.x == 0) {
             const double ll = gwb_finish(a.N, quad, lp);

@@ -174,3 +174,23 @@ def test_gradient_out_of_domain_and_host_pointers(argus):
     assert np.isneginf(ll_h[0]) and np.all(g_h[0] == 0.0)
     ll_ref, g_ref = gwb.loglik_grad(data, theta[1:])
     assert ll_err(ll_h[1:], ll_ref) <= LL_TOL and g_err(g_h[1:], g_ref) <= G_TOL
+
+
+@pytest.mark.parametrize("lg_p,lg_a", [(-5.0, -8.0), (-8.0, -5.0), (-3.0, -3.0), (-5.5, -9.9)])
+def test_fast_decays_fold_the_scaled_frame(argus, lg_p, lg_a):
+    """Decay rates whose products over the TOA gaps fall below 2^-200 (and,
+    at 1e-3 / s, to zero in a single gap): the likelihood kernel folds its
+    scale factors back into the covariance and takes those predicts
+    unscaled; the gradient kernel's checkpoint pass does the same."""
+    data = inputs.make_array(np.array([40, 30, 25]), seed=514, equad=1e-8)
+    theta = thetas(3, 4, np.random.default_rng(15), lh=(-19.5, -18.3))
+    theta[:, 1] = lg_a
+    theta[:, 3::3] = lg_p
+    theta[1, 3] = -8.5                      # one pulsar slow: scales fold independently
+    arr = argus.GwbArray(data)
+    ll = run(argus, arr, theta)
+    ll_ref, g_ref = gwb.loglik_grad(data, theta)
+    assert ll_err(ll, ll_ref) <= LL_TOL
+    ll_g, g = argus.argus_gwb_loglik_grad(arr, torch.from_numpy(theta).cuda())
+    assert ll_err(ll_g.cpu().numpy(), ll_ref) <= LL_TOL
+    assert g_err(g.cpu().numpy(), g_ref) <= G_TOL
