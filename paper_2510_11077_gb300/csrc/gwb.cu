@@ -90,8 +90,9 @@ struct GwbSmem {
     double* Pm;     // [n][n]
     double* m;      // [n]
     double* c;      // [n]
-    double* co;     // [P][9]: a, b, Q/sigma^2 (c00, c01, c11), then d/dgamma of b and of c00, c01, c11
-                    // (gradient) or, scaled frame, b s_p, sigma^2 c00, sigma^2 c01 / s'_p, sigma^2 c11 / s'_p^2
+    double* co;     // [P][9]: a, b, Q/sigma^2 (c00, c01, c11), d/dgamma of b and of c00, c01, c11
+    double* cs;     // [P + 1][5], scaled frame, per pulsar and for the GW process (row P):
+                    // b s, v c00, v c01 / s', v c11 / s'^2, 1 / s' (v = sigma_p^2 or h_a^2, s' = s a)
     double* ct;     // [n]: c / S
     double* sg;     // [P + 1]: scale factors s_p and s_a (scaled frame)
     double* sg0;    // [P + 1]: the scale factors before the current predict
@@ -104,20 +105,30 @@ struct GwbSmem {
     double* v;      // [n]      (gradient)
     double* acc;    // [P][5]: d/d sigma^2, d/d gamma_p, d/d EFAC, d/d h_a^2 part, d/d gamma_a part
     double* part;   // [P][chunks][6]: partial sums of the parameter terms
+    double* sgb;    // [2P]: adjoints of s_p, and pulsar I's share of the adjoint of s_a (gradient)
     uint16_t* pairs;
     uint8_t* ent;
 };
 // scalar slots of gw[]
-enum { kGwA = 0, kGwHa2 = 9, kGwGa, kGwE, kGwS, kGwRS, kGwG, kGwOk, kGwSb, kGwEb, kGwR0, kGwRn, kGwSlots = 20 };
+enum { kGwA = 0, kGwHa2 = 9, kGwGa, kGwE, kGwS, kGwRS, kGwG, kGwOk, kGwSb, kGwEb, kGwR0, kGwRn, kGwRnAny,
+       kGwSlots = 24 };
 constexpr double kGwbTiny = 0x1p-200;   // smallest scale factor kept (scaled frame)
 
 // chunks per pulsar of the adjoint's parameter sums (k ranges of about 8)
 __host__ __device__ inline int gwb_chunks(int P) { return (3 * P + 7) / 8; }
+// chunks per pulsar of the scaled adjoint's sums (J ranges of about 5; never more than gwb_chunks)
+__host__ __device__ inline int gwb_jchunks(int P) { return (P + 4) / 5; }
+// doubles of one saved state: the upper triangle of P, m and the P + 1 scales
+__host__ __device__ inline int64_t gwb_rec_len(int P) {
+    const int64_t n = 3 * int64_t(P);
+    return n * (n + 1) / 2 + n + P + 1;
+}
 
 __host__ __device__ inline size_t gwb_smem_doubles(int P, bool grad) {
     const size_t n = 3 * size_t(P);
-    size_t d = n * n + 3 * n + kCo * size_t(P) + size_t(P) * P + 4 * size_t(P) + 2 * (size_t(P) + 1) + kGwSlots;
-    if (grad) d += n * n + 3 * n + 5 * size_t(P) + 6 * size_t(P) * gwb_chunks(P);
+    size_t d = n * n + 3 * n + kCo * size_t(P) + 5 * (size_t(P) + 1) + size_t(P) * P + 4 * size_t(P) +
+               2 * (size_t(P) + 1) + kGwSlots;
+    if (grad) d += n * n + 3 * n + 5 * size_t(P) + 6 * size_t(P) * gwb_chunks(P) + 2 * size_t(P);
     return d;
 }
 
@@ -138,6 +149,7 @@ __device__ GwbSmem gwb_carve(double* base, int P, bool grad) {
     s.m = q; q += n;
     s.c = q; q += n;
     s.co = q; q += kCo * P;
+    s.cs = q; q += 5 * (P + 1);
     s.ct = q; q += n;
     s.sg = q; q += P + 1;
     s.sg0 = q; q += P + 1;
@@ -151,8 +163,9 @@ __device__ GwbSmem gwb_carve(double* base, int P, bool grad) {
         s.v = q; q += n;
         s.acc = q; q += 5 * P;
         s.part = q; q += 6 * P * gwb_chunks(P);
+        s.sgb = q; q += 2 * P;
     } else {
-        s.Pb = s.mb = s.u = s.v = s.acc = s.part = nullptr;
+        s.Pb = s.mb = s.u = s.v = s.acc = s.part = s.sgb = nullptr;
     }
     s.pairs = reinterpret_cast<uint16_t*>(q);
     s.ent = reinterpret_cast<uint8_t*>(s.pairs + 2 * s.nb);
@@ -195,6 +208,7 @@ __device__ bool gwb_setup(const GwbSmem& s, const GwbArgs& a, const double* th) 
         s.gw[kGwGa] = exp10(th[1]);
         s.gw[kGwOk] = ok ? 1.0 : 0.0;
         s.gw[kGwRn] = 0.0;
+        s.gw[kGwRnAny] = 0.0;
     }
     for (int p = threadIdx.x; p <= P; p += blockDim.x) s.sg[p] = 1.0;
     for (int p = threadIdx.x; p < P; p += blockDim.x) {
@@ -290,25 +304,32 @@ __device__ void gwb_predict(const GwbSmem& s) {
     }
 }
 
-// 1'. scaled frame: the coefficients of 1. and those of Fh and S'^-1 Q S'^-1;
-// the scales advance to s' = s a, and a scale below kGwbTiny raises the flag
+// 1'. scaled frame: the coefficients of 1. (with their gamma-derivatives when
+// kDeriv) and those of Fh and S'^-1 Q S'^-1 (cs).  With kAdvance the scales
+// advance to s' = s a, and a scale below kGwbTiny raises the flag.
+template <bool kDeriv, bool kAdvance>
 __device__ void gwb_coef_scaled(const GwbSmem& s, double dt) {
     const double h2 = 0.5 * dt * dt, h3 = dt * dt * dt / 3.0, dt2 = dt * dt;
     for (int p = threadIdx.x; p <= s.P; p += blockDim.x) {
         OuCoef oc;
         const bool psr = p < s.P;
-        ou_coef_warp<false>((psr ? s.par[4 * p + 1] : s.gw[kGwGa]) * dt, dt, h2, h3, dt2, oc);
+        ou_coef_warp<kDeriv>((psr ? s.par[4 * p + 1] : s.gw[kGwGa]) * dt, dt, h2, h3, dt2, oc);
         const double sg = s.sg[p], sn = sg * oc.a;
-        s.sg0[p] = sg;
-        s.sg[p] = sn;
-        if (!(sn >= kGwbTiny)) s.gw[kGwRn] = 1.0;
+        if (kAdvance) {
+            s.sg0[p] = sg;
+            s.sg[p] = sn;
+            if (!(sn >= kGwbTiny)) s.gw[kGwRn] = 1.0;
+        }
         const double w = rcp_nr(sn), sc = psr ? s.par[4 * p] : s.gw[kGwHa2];
         double* o = psr ? s.co + kCo * p : s.gw + kGwA;
         o[0] = oc.a; o[1] = oc.b; o[2] = oc.c00; o[3] = oc.c01; o[4] = oc.c11;
-        o[5] = oc.b * sg;
-        o[6] = sc * oc.c00;
-        o[7] = sc * oc.c01 * w;
-        o[8] = sc * oc.c11 * w * w;
+        if (kDeriv) { o[5] = oc.db; o[6] = oc.dc00; o[7] = oc.dc01; o[8] = oc.dc11; }
+        double* h = s.cs + 5 * p;
+        h[0] = oc.b * sg;
+        h[1] = sc * oc.c00;
+        h[2] = sc * oc.c01 * w;
+        h[3] = sc * oc.c11 * w * w;
+        h[4] = w;
     }
 }
 
@@ -316,14 +337,15 @@ __device__ void gwb_coef_scaled(const GwbSmem& s, double dt) {
 // blocks); Fh is the identity but for the rho row (b_p s_p, b_a s_a)
 __device__ void gwb_predict_scaled(const GwbSmem& s) {
     const int P = s.P, n = s.n;
-    const double al = s.gw[5], qa00 = s.gw[6], qa01 = s.gw[7], qa11 = s.gw[8];
+    const double* ca = s.cs + 5 * P;
+    const double al = ca[0], qa00 = ca[1], qa01 = ca[2], qa11 = ca[3];
     for (int p = threadIdx.x; p < P; p += blockDim.x) {
         double* mp = s.m + 3 * p;
-        mp[0] = fma(s.co[kCo * p + 5], mp[1], fma(al, mp[2], mp[0]));
+        mp[0] = fma(s.cs[5 * p], mp[1], fma(al, mp[2], mp[0]));
     }
     for (int q = threadIdx.x; q < s.nb; q += blockDim.x) {
         const int I = s.pairs[2 * q], J = s.pairs[2 * q + 1];
-        const double bI = s.co[kCo * I + 5], bJ = s.co[kCo * J + 5];
+        const double bI = s.cs[5 * I], bJ = s.cs[5 * J];
         double* B = s.Pm + (3 * I) * n + 3 * J;
         const double x00 = B[0], x01 = B[1], x02 = B[2], x11 = B[n + 1], x12 = B[n + 2], x22 = B[2 * n + 2];
         const double x10 = I < J ? B[n] : x01, x20 = I < J ? B[2 * n] : x02, x21 = I < J ? B[2 * n + 1] : x12;
@@ -338,10 +360,10 @@ __device__ void gwb_predict_scaled(const GwbSmem& s) {
         double z11 = x11;
         const double z22 = fma(g, qa11, x22);
         if (I == J) {
-            const double* co = s.co + kCo * I;
-            z00 += co[6];
-            z01 += co[7];
-            z11 += co[8];
+            const double* cI = s.cs + 5 * I;
+            z00 += cI[1];
+            z01 += cI[2];
+            z11 += cI[3];
         } else {
             B[n] = fma(bJ, x11, fma(al, x12, x10));
             B[2 * n] = fma(g, qa01, fma(bJ, x21, fma(al, x22, x20)));
@@ -406,14 +428,17 @@ template <bool kLL, bool kScaled = false>
 __device__ void gwb_step(const GwbSmem& s, const GwbArgs& a, const GwbRec& rk, double& quad, LogProd& lp) {
     if (rk.dt > 0.0) {
         if (kScaled) {
-            gwb_coef_scaled(s, rk.dt);
+            gwb_coef_scaled<false, true>(s, rk.dt);
             __syncthreads();
             if (s.gw[kGwRn] != 0.0) {          // block-uniform and rare: unscale, predict unscaled
                 gwb_fold(s, s.sg0);
                 __syncthreads();
                 gwb_predict(s);
                 for (int p = threadIdx.x; p <= s.P; p += blockDim.x) s.sg[p] = 1.0;
-                if (threadIdx.x == 0) s.gw[kGwRn] = 0.0;
+                if (threadIdx.x == 0) {
+                    s.gw[kGwRn] = 0.0;
+                    s.gw[kGwRnAny] = 1.0;
+                }
             } else {
                 gwb_predict_scaled(s);
             }
@@ -460,57 +485,24 @@ __global__ void __launch_bounds__(kGwbThreads) k_gwb_filter(GwbArgs a) {
 __device__ void gwb_save(const GwbSmem& s, double* dst) {
     for (int q = threadIdx.x; q < s.ne; q += blockDim.x) dst[q] = s.Pm[s.ent[2 * q] * s.n + s.ent[2 * q + 1]];
     for (int i = threadIdx.x; i < s.n; i += blockDim.x) dst[s.ne + i] = s.m[i];
+    for (int p = threadIdx.x; p <= s.P; p += blockDim.x) dst[s.ne + s.n + p] = s.sg[p];
 }
 
 __device__ void gwb_load(const GwbSmem& s, const double* src) {
     for (int q = threadIdx.x; q < s.ne; q += blockDim.x) s.Pm[s.ent[2 * q] * s.n + s.ent[2 * q + 1]] = src[q];
     for (int i = threadIdx.x; i < s.n; i += blockDim.x) s.m[i] = src[s.ne + i];
+    for (int p = threadIdx.x; p <= s.P; p += blockDim.x) s.sg[p] = src[s.ne + s.n + p];
 }
 
-// Reverse of one forward step k, the state before it in Pm, m.  On entry Pb,
-// mb hold the adjoints of the state after the step; on exit, before it.
-__device__ void gwb_step_adjoint(const GwbSmem& s, const GwbArgs& a, const GwbRec& rk) {
-    const int P = s.P, n = s.n, q = rk.q, i0 = 3 * q;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-    const double dt = rk.dt;
-    const bool pred = dt > 0.0;
+// Reverse of the observation of TOA rk (either frame).  On entry c holds the
+// predicted covariance's column i = 3q, gw[kGwE] the innovation and
+// gw[kGwR0] the measurement variance; Pb, mb the adjoints after the update.
+// On exit Pb holds M-bar, the symmetric adjoint of the predicted covariance,
+// and mb mu-bar, that of the predicted mean; EFAC_q's term is accumulated.
+__device__ void gwb_adjoint_observation(const GwbSmem& s, const GwbRec& rk) {
+    const int n = s.n, q = rk.q, i0 = 3 * q;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     double* gw = s.gw;
-    if (pred) {
-        gwb_coef<true>(s, dt);
-        __syncthreads();
-    }
-    // u = P (F^T e_i), and mu_i = (F m)_i
-    const double bq = pred ? s.co[kCo * q + 1] : 0.0, ba = pred ? gw[1] : 0.0;
-    for (int j = tid; j < n; j += blockDim.x)
-        s.u[j] = fma(bq, psym(s.Pm, n, j, i0 + 1), fma(ba, psym(s.Pm, n, j, i0 + 2), psym(s.Pm, n, j, i0)));
-    __syncthreads();
-    // c = F u + Q e_i (the predicted covariance's column i)
-    const double ha2 = gw[kGwHa2];
-    for (int J = tid; J < P; J += blockDim.x) {
-        const double* uJ = s.u + 3 * J;
-        if (pred) {
-            const double aJ = s.co[kCo * J], bJ = s.co[kCo * J + 1], aa = gw[0];
-            const double g = s.G[J * P + q] * ha2;
-            double c0 = fma(bJ, uJ[1], fma(ba, uJ[2], uJ[0])) + g * gw[2];
-            double c1 = aJ * uJ[1];
-            const double c2 = fma(aa, uJ[2], g * gw[3]);
-            if (J == q) {
-                const double s2 = s.par[4 * q];
-                c0 = fma(s2, s.co[kCo * q + 2], c0);
-                c1 = fma(s2, s.co[kCo * q + 3], c1);
-            }
-            s.c[3 * J] = c0; s.c[3 * J + 1] = c1; s.c[3 * J + 2] = c2;
-        } else {
-            s.c[3 * J] = uJ[0]; s.c[3 * J + 1] = uJ[1]; s.c[3 * J + 2] = uJ[2];
-        }
-    }
-    if (tid == 0) {
-        const double mu = fma(bq, s.m[i0 + 1], fma(ba, s.m[i0 + 2], s.m[i0]));
-        const double R = fma(s.par[4 * q + 2], rk.s2, a.equad2[q]);
-        gw[kGwE] = rk.r - mu;
-        gw[kGwR0] = R;   // this TOA's measurement variance
-    }
-    __syncthreads();
     if (tid == 0) {
         const double S = s.c[i0] + gw[kGwR0];
         const double rS = rcp_nr(S);
@@ -552,6 +544,53 @@ __device__ void gwb_step_adjoint(const GwbSmem& s, const GwbArgs& a, const GwbRe
         }
     }
     __syncthreads();
+}
+
+// Reverse of one forward step k, the state before it in Pm, m.  On entry Pb,
+// mb hold the adjoints of the state after the step; on exit, before it.
+__device__ void gwb_step_adjoint(const GwbSmem& s, const GwbArgs& a, const GwbRec& rk) {
+    const int P = s.P, n = s.n, q = rk.q, i0 = 3 * q;
+    const int tid = threadIdx.x;
+    const double dt = rk.dt;
+    const bool pred = dt > 0.0;
+    double* gw = s.gw;
+    if (pred) {
+        gwb_coef<true>(s, dt);
+        __syncthreads();
+    }
+    // u = P (F^T e_i), and mu_i = (F m)_i
+    const double bq = pred ? s.co[kCo * q + 1] : 0.0, ba = pred ? gw[1] : 0.0;
+    for (int j = tid; j < n; j += blockDim.x)
+        s.u[j] = fma(bq, psym(s.Pm, n, j, i0 + 1), fma(ba, psym(s.Pm, n, j, i0 + 2), psym(s.Pm, n, j, i0)));
+    __syncthreads();
+    // c = F u + Q e_i (the predicted covariance's column i)
+    const double ha2 = gw[kGwHa2];
+    for (int J = tid; J < P; J += blockDim.x) {
+        const double* uJ = s.u + 3 * J;
+        if (pred) {
+            const double aJ = s.co[kCo * J], bJ = s.co[kCo * J + 1], aa = gw[0];
+            const double g = s.G[J * P + q] * ha2;
+            double c0 = fma(bJ, uJ[1], fma(ba, uJ[2], uJ[0])) + g * gw[2];
+            double c1 = aJ * uJ[1];
+            const double c2 = fma(aa, uJ[2], g * gw[3]);
+            if (J == q) {
+                const double s2 = s.par[4 * q];
+                c0 = fma(s2, s.co[kCo * q + 2], c0);
+                c1 = fma(s2, s.co[kCo * q + 3], c1);
+            }
+            s.c[3 * J] = c0; s.c[3 * J + 1] = c1; s.c[3 * J + 2] = c2;
+        } else {
+            s.c[3 * J] = uJ[0]; s.c[3 * J + 1] = uJ[1]; s.c[3 * J + 2] = uJ[2];
+        }
+    }
+    if (tid == 0) {
+        const double mu = fma(bq, s.m[i0 + 1], fma(ba, s.m[i0 + 2], s.m[i0]));
+        const double R = fma(s.par[4 * q + 2], rk.s2, a.equad2[q]);
+        gw[kGwE] = rk.r - mu;
+        gw[kGwR0] = R;   // this TOA's measurement variance
+    }
+    __syncthreads();
+    gwb_adjoint_observation(s, rk);
     if (!pred) return;   // F = I, Q = 0: the adjoints pass through
     // parameters through F and Q, in two levels: work item (I, chunk) forms
     // partial sums over its share of k (for F-bar) and of J (for the GW part
@@ -651,11 +690,154 @@ __device__ void gwb_step_adjoint(const GwbSmem& s, const GwbArgs& a, const GwbRe
     __syncthreads();
 }
 
+// Reverse of one forward step k in the scaled frame: the state before it
+// (Ph, mh and the scales s) in Pm, m, sg.  On entry Pb, mb and sgb hold the
+// adjoints of Ph, mh and s after the step; on exit, before it.  With M-bar the
+// adjoint of the predicted Ph and mu-bar that of the predicted mh:
+//   Fh-bar = 2 M-bar Fh Ph + mu-bar mh^T, of which b s (rho_I, y_I) and
+//   b_a s_a (rho_I, a_I, every I) are parameters;
+//   the process noise v c / s'^k (k = 0, 1, 2) passes its adjoint to v, c and
+//   s' = s a; s' passes its adjoint to s and a;
+//   Ph-bar = Fh^T M-bar Fh, mh-bar = Fh^T mu-bar.
+// The GW scale s_a is common to all pulsars; its adjoint is carried as P
+// shares (pulsar I's terms), so every sum over pulsars stays in fixed order.
+__device__ void gwb_step_adjoint_scaled(const GwbSmem& s, const GwbArgs& a, const GwbRec& rk) {
+    const int P = s.P, n = s.n, q = rk.q, i0 = 3 * q;
+    const int tid = threadIdx.x;
+    const double dt = rk.dt;
+    const bool pred = dt > 0.0;
+    double* gw = s.gw;
+    if (pred) {
+        gwb_coef_scaled<true, false>(s, dt);
+        __syncthreads();
+    }
+    const double* ca = s.cs + 5 * P;
+    const double bq = pred ? s.cs[5 * q] : 0.0, al = pred ? ca[0] : 0.0;
+    // u = Ph (Fh^T e_i); c = Fh u + Qh e_i, the predicted column i
+    for (int j = tid; j < n; j += blockDim.x)
+        s.u[j] = fma(bq, psym(s.Pm, n, j, i0 + 1), fma(al, psym(s.Pm, n, j, i0 + 2), psym(s.Pm, n, j, i0)));
+    __syncthreads();
+    for (int J = tid; J < P; J += blockDim.x) {
+        const double* uJ = s.u + 3 * J;
+        if (pred) {
+            const double g = s.G[J * P + q];
+            double c0 = fma(g, ca[1], fma(s.cs[5 * J], uJ[1], fma(al, uJ[2], uJ[0])));
+            double c1 = uJ[1];
+            const double c2 = fma(g, ca[2], uJ[2]);
+            if (J == q) {
+                c0 += s.cs[5 * q + 1];
+                c1 += s.cs[5 * q + 2];
+            }
+            s.c[3 * J] = c0; s.c[3 * J + 1] = c1; s.c[3 * J + 2] = c2;
+        } else {
+            s.c[3 * J] = uJ[0]; s.c[3 * J + 1] = uJ[1]; s.c[3 * J + 2] = uJ[2];
+        }
+    }
+    if (tid == 0) {
+        const double mu = fma(bq, s.m[i0 + 1], fma(al, s.m[i0 + 2], s.m[i0]));
+        gw[kGwE] = rk.r - mu;
+        gw[kGwR0] = fma(s.par[4 * q + 2], rk.s2, a.equad2[q]);
+    }
+    __syncthreads();
+    gwb_adjoint_observation(s, rk);
+    if (!pred) return;   // Fh = I, Q = 0, s unchanged: the adjoints pass through
+    // sums over J for each pulsar I, in chunks of J: (M-bar Fh Ph) at (rho_I,
+    // y_I) and (rho_I, a_I), and the GW noise's contractions with G
+    const int nch = gwb_jchunks(P), jc = (P + nch - 1) / nch;
+    for (int it = tid; it < P * nch; it += blockDim.x) {
+        const int I = it / nch, ch = it - I * nch;
+        const int rI = 3 * I, yI = rI + 1, aI = rI + 2;
+        const double* Mr = s.Pb + rI * n;
+        const double* Ma = s.Pb + aI * n;
+        double sB = 0.0, sA = 0.0, t1 = 0.0, t2 = 0.0, t3 = 0.0;
+        const int j_hi = min(P, (ch + 1) * jc);
+        for (int J = ch * jc; J < j_hi; ++J) {
+            const int rJ = 3 * J;
+            const double bJ = s.cs[5 * J];
+            const double py0 = psym(s.Pm, n, rJ, yI), py1 = psym(s.Pm, n, rJ + 1, yI), py2 = psym(s.Pm, n, rJ + 2, yI);
+            const double pa0 = psym(s.Pm, n, rJ, aI), pa1 = psym(s.Pm, n, rJ + 1, aI), pa2 = psym(s.Pm, n, rJ + 2, aI);
+            const double m0 = Mr[rJ], m1 = Mr[rJ + 1], m2 = Mr[rJ + 2];
+            sB = fma(m0, fma(bJ, py1, fma(al, py2, py0)), fma(m1, py1, fma(m2, py2, sB)));
+            sA = fma(m0, fma(bJ, pa1, fma(al, pa2, pa0)), fma(m1, pa1, fma(m2, pa2, sA)));
+            const double g = s.G[I * P + J];
+            t1 = fma(g, m0, t1);
+            t2 = fma(g, m2 + Ma[rJ], t2);
+            t3 = fma(g, Ma[rJ + 2], t3);
+        }
+        double* pt = s.part + 6 * it;
+        pt[0] = sB; pt[1] = sA; pt[2] = t1; pt[3] = t2; pt[4] = t3;
+    }
+    __syncthreads();
+    const double ha2 = gw[kGwHa2], sga = s.sg[P], wa = ca[4];
+    for (int I = tid; I < P; I += blockDim.x) {
+        const int rI = 3 * I, yI = rI + 1, aI = rI + 2;
+        double sB = 0.0, sA = 0.0, t1 = 0.0, t2 = 0.0, t3 = 0.0;
+        for (int ch = 0; ch < nch; ++ch) {
+            const double* pt = s.part + 6 * (I * nch + ch);
+            sB += pt[0]; sA += pt[1]; t1 += pt[2]; t2 += pt[3]; t3 += pt[4];
+        }
+        const double* co = s.co + kCo * I;
+        const double* cI = s.cs + 5 * I;
+        const double w = cI[4], sgI = s.sg[I], s2p = s.par[4 * I];
+        const double bhb = fma(2.0, sB, s.mb[rI] * s.m[yI]);     // adjoint of b_I s_I
+        const double alb = fma(2.0, sA, s.mb[rI] * s.m[aI]);     // pulsar I's share of that of b_a s_a
+        const double M00 = s.Pb[rI * n + rI], q1b = 2.0 * s.Pb[rI * n + yI], M11 = s.Pb[yI * n + yI];
+        // intrinsic noise v c00, v c01 / s', v c11 / s'^2 and the scale s'_I
+        const double sbt = s.sgb[I] - w * fma(q1b, cI[2], 2.0 * M11 * cI[3]);
+        double* acc = s.acc + 5 * I;
+        acc[0] += fma(M00, co[2], w * fma(q1b, co[3], w * M11 * co[4]));
+        acc[1] += fma(s2p, fma(M00, co[6], w * fma(q1b, co[7], w * M11 * co[8])),
+                      sgI * fma(bhb, co[5], -dt * co[0] * sbt));
+        s.sgb[I] = fma(sbt, co[0], bhb * co[1]);
+        // pulsar I's share of the GW terms
+        const double sbat = s.sgb[P + I] - wa * fma(t2, ca[2], 2.0 * t3 * ca[3]);
+        acc[3] += fma(t1, gw[2], wa * fma(t2, gw[3], wa * t3 * gw[4]));
+        acc[4] += fma(ha2, fma(t1, gw[6], wa * fma(t2, gw[7], wa * t3 * gw[8])),
+                      sga * fma(alb, gw[5], -dt * gw[0] * sbat));
+        s.sgb[P + I] = fma(sbat, gw[0], alb * gw[1]);
+    }
+    __syncthreads();
+    // Pb <- Fh^T Pb Fh (upper blocks, mirrored) and mb <- Fh^T mb
+    for (int qq = tid; qq < s.nb; qq += blockDim.x) {
+        const int I = s.pairs[2 * qq], J = s.pairs[2 * qq + 1];
+        const double bI = s.cs[5 * I], bJ = s.cs[5 * J];
+        double X[3][3];
+#pragma unroll
+        for (int u = 0; u < 3; ++u)
+#pragma unroll
+            for (int v = 0; v < 3; ++v) X[u][v] = s.Pb[(3 * I + u) * n + 3 * J + v];
+#pragma unroll
+        for (int v = 0; v < 3; ++v) {   // Fh_I^T X: rows y, a gain b_I s_I, b_a s_a times row rho
+            X[1][v] = fma(bI, X[0][v], X[1][v]);
+            X[2][v] = fma(al, X[0][v], X[2][v]);
+        }
+#pragma unroll
+        for (int u = 0; u < 3; ++u) {   // (Fh_I^T X) Fh_J
+            const double z0 = X[u][0];
+            const double z1 = fma(bJ, z0, X[u][1]);
+            const double z2 = fma(al, z0, X[u][2]);
+            s.Pb[(3 * I + u) * n + 3 * J] = z0;
+            s.Pb[(3 * I + u) * n + 3 * J + 1] = z1;
+            s.Pb[(3 * I + u) * n + 3 * J + 2] = z2;
+            s.Pb[(3 * J) * n + 3 * I + u] = z0;
+            s.Pb[(3 * J + 1) * n + 3 * I + u] = z1;
+            s.Pb[(3 * J + 2) * n + 3 * I + u] = z2;
+        }
+    }
+    for (int J = tid; J < P; J += blockDim.x) {
+        double* mJ = s.mb + 3 * J;
+        const double m0 = mJ[0];
+        mJ[1] = fma(s.cs[5 * J], m0, mJ[1]);
+        mJ[2] = fma(al, m0, mJ[2]);
+    }
+    __syncthreads();
+}
+
 __global__ void __launch_bounds__(kGwbThreads) k_gwb_grad(GwbArgs a) {
     extern __shared__ __align__(16) double gsm[];
     const GwbSmem s = gwb_carve(gsm, a.P, true);
     const int P = s.P, n = s.n, D = 2 + 3 * P;
-    const int64_t rec_len = s.ne + n;
+    const int64_t rec_len = gwb_rec_len(P);
     double* ck = a.ckpt + int64_t(blockIdx.x) * a.slot;
     double* tp = a.tape + int64_t(blockIdx.x) * a.slot;
     gwb_tables(s, a);
@@ -667,19 +849,27 @@ __global__ void __launch_bounds__(kGwbThreads) k_gwb_grad(GwbArgs a) {
             if (threadIdx.x == 0) a.loglik[b] = -INFINITY;
             continue;
         }
-        // forward, with the state saved at each segment start
+        // forward in the scaled frame, with the state saved at each segment
+        // start; a vector whose scales had to be folded back (a fast decay
+        // over a long gap) runs the whole gradient unscaled instead
         double quad = 0.0;
         LogProd lp;
-        // (in the scaled frame, folded back at each segment start)
         for (int seg = 0; seg < a.nseg; ++seg) {
-            if (seg > 0) {
-                gwb_fold(s, s.sg);
-                __syncthreads();
-                for (int p = threadIdx.x; p <= P; p += blockDim.x) s.sg[p] = 1.0;
-            }
             gwb_save(s, ck + seg * rec_len);
             const int64_t k1 = min(int64_t(seg + 1) * a.L, a.N);
             for (int64_t k = int64_t(seg) * a.L; k < k1; ++k) gwb_step<true, true>(s, a, a.rec[k], quad, lp);
+        }
+        const bool scaled = s.gw[kGwRnAny] == 0.0;
+        if (!scaled) {
+            __syncthreads();
+            gwb_setup(s, a, a.theta + b * D);
+            quad = 0.0;
+            lp = LogProd();
+            for (int seg = 0; seg < a.nseg; ++seg) {
+                gwb_save(s, ck + seg * rec_len);
+                const int64_t k1 = min(int64_t(seg + 1) * a.L, a.N);
+                for (int64_t k = int64_t(seg) * a.L; k < k1; ++k) gwb_step<true>(s, a, a.rec[k], quad, lp);
+            }
         }
         if (threadIdx.x == 0) {
             const double ll = gwb_finish(a.N, quad, lp);
@@ -689,6 +879,7 @@ __global__ void __launch_bounds__(kGwbThreads) k_gwb_grad(GwbArgs a) {
         for (int i = threadIdx.x; i < n * n; i += blockDim.x) s.Pb[i] = 0.0;
         for (int i = threadIdx.x; i < n; i += blockDim.x) s.mb[i] = 0.0;
         for (int i = threadIdx.x; i < 5 * P; i += blockDim.x) s.acc[i] = 0.0;
+        for (int i = threadIdx.x; i < 2 * P; i += blockDim.x) s.sgb[i] = 0.0;
         __syncthreads();
         if (s.gw[kGwOk] == 0.0 || a.N == 0) {
             for (int j = threadIdx.x; j < D; j += blockDim.x) gout[j] = 0.0;
@@ -702,13 +893,15 @@ __global__ void __launch_bounds__(kGwbThreads) k_gwb_grad(GwbArgs a) {
             __syncthreads();
             for (int64_t k = k0; k < k1; ++k) {
                 gwb_save(s, tp + (k - k0) * rec_len);
-                gwb_step<false>(s, a, a.rec[k], quad, lp);
+                if (scaled) gwb_step<false, true>(s, a, a.rec[k], quad, lp);
+                else gwb_step<false>(s, a, a.rec[k], quad, lp);
             }
             for (int64_t k = k1 - 1; k >= k0; --k) {
                 __syncthreads();
                 gwb_load(s, tp + (k - k0) * rec_len);
                 __syncthreads();
-                gwb_step_adjoint(s, a, a.rec[k]);
+                if (scaled) gwb_step_adjoint_scaled(s, a, a.rec[k]);
+                else gwb_step_adjoint(s, a, a.rec[k]);
             }
         }
         // the stationary prior of the a block: h_a^2 G / (2 gamma_a)
@@ -967,7 +1160,7 @@ argus_status argus_gwb_loglik_grad(argus_gwb* h, const double* theta, int64_t B,
     cudaGetDevice(&prev);
     cudaSetDevice(h->device);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    const int D = 2 + 3 * h->P, n = 3 * h->P;
+    const int D = 2 + 3 * h->P;
     const bool dev_in = gwb_is_device_ptr(theta), dev_ll = gwb_is_device_ptr(loglik),
                dev_g = gwb_is_device_ptr(grad);
     const double* th_d = theta;
@@ -978,7 +1171,7 @@ argus_status argus_gwb_loglik_grad(argus_gwb* h, const double* theta, int64_t B,
     int per_sm = 1;
     const int L = std::max(1, int(std::ceil(std::sqrt(double(std::max<int64_t>(h->N, 1))))));
     const int nseg = int((h->N + L - 1) / L);
-    const size_t slot = size_t(std::max(nseg, L)) * (size_t(n) * (n + 1) / 2 + n);
+    const size_t slot = size_t(std::max(nseg, L)) * size_t(gwb_rec_len(h->P));
     int grid = 1;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gwb_grad, kGwbThreads, smem)) != cudaSuccess) {
         st = argus_status(gwb_cuda(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor"));
