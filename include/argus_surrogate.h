@@ -71,9 +71,19 @@ argus_status argus_surrogate_set_weights(argus_surrogate* s, const float* params
 argus_status argus_surrogate_get_weights(argus_surrogate* s, float* params);
 
 /* Surrogate log-likelihood and gradient of B parameter vectors:
- * theta [B][47], loglik [B], grad [B][47] or NULL (FP32, device). */
+ * theta [B][47], loglik [B], grad [B][47] or NULL (FP32, device).  By default
+ * one fused kernel evaluates every max_rows rows: each thread block takes 128
+ * rows through all five layers, and in grad mode 1 back through them to the
+ * input, with the activations in shared memory and the weights streamed in
+ * by TMA layer by layer.  Its results equal the layer-by-layer path's up to
+ * the rounding order of a few FP32 operations. */
 argus_status argus_surrogate_eval(argus_surrogate* s, const float* theta, int64_t B, float* loglik,
                                   float* grad, void* stream);
+
+/* Selects how argus_surrogate_eval runs: on = 1 (default) the fused kernel,
+ * on = 0 one tensor-core GEMM launch per layer (the kernels training uses).
+ * For comparison and measurement; both compute the same network. */
+argus_status argus_surrogate_set_fused(argus_surrogate* s, int32_t on);
 
 /* One Adam step on a minibatch of n <= max_rows exact evaluations:
  * theta [n][47], loglik [n], grad [n][47] (FP32, device).  The loss is the

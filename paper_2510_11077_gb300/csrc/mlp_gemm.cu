@@ -125,6 +125,20 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
     for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
 
+// 32 consecutive columns of this warp's TMEM lanes, one wait
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32"
+        " {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+
 __device__ __forceinline__ float gelu_f(float z) {
     return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f));
 }
@@ -292,6 +306,306 @@ cudaError_t launch_one(const CUtensorMap* ta, const CUtensorMap* tb, int M, int 
     return cudaGetLastError();
 }
 
+
+// ---------------------------------------------------------------------------
+// Fused evaluation: one CTA of 8 warps owns 128 rows and runs every layer.
+// Shared memory: the 128 x 256 BF16 activation tile (A operand, four 64-column
+// K-atoms in the 128-byte-swizzled layout a TMA box would give), the weight
+// tile of the current layer (B operand, up to 256 x 256, loaded by TMA while
+// the previous layer's epilogue runs), the biases, the value output's weight
+// row and the rows' quadratic baseline.
+// Stages (each one tcgen05 GEMM into the same 256 TMEM columns):
+//   0..3  h_{l+1} = gelu(h_l W_l^T + b_l); gelu'(z) saved for the backward pass
+//   4     y = h_4 W_4^T + b_4
+//   5..8  (kFusedValueGrad) dz_l = (dz_{l+1} W_l) * gelu'(z_l), then dx = dz_1 W_0,
+//         seeded with dz_4 = W_4[0] * gelu'(z_4) (the value output's one-hot)
+// Warp w reads TMEM lanes 32 (w % 4) .. + 31 (its rows) and columns
+// 128 (w / 4) .. + 127.  Thread 0 issues the copies and the MMAs and alone
+// waits on the mbarriers (bounded); the block follows through __syncthreads.
+constexpr int kFusedThreads = 256;
+constexpr uint32_t kFAtomA = kGemmM * 128u;       // one 64-column K-atom of the activation tile
+constexpr uint32_t kFSmemA = 4u * kFAtomA;        // 64 KB
+constexpr uint32_t kFSmemB = 4u * 256u * 128u;    // 128 KB
+constexpr int kFBiasFloats = 4 * kMlpHidden + kMlpOutPad;
+constexpr int kFTailFloats = kGemmM * kMlpIn + 2 * kGemmM + kFBiasFloats + kMlpHidden;
+constexpr size_t kFusedSmem = 1024 + kFSmemA + kFSmemB + sizeof(float) * kFTailFloats + 64;
+
+struct FusedStage {
+    int map;      // 0..4: maps.w[map]; 5..8: maps.wt[8 - map]
+    int K, N;
+};
+__constant__ FusedStage c_fstage[9] = {{0, kMlpInPad, kMlpHidden}, {1, kMlpHidden, kMlpHidden},
+                                       {2, kMlpHidden, kMlpHidden}, {3, kMlpHidden, kMlpHidden},
+                                       {4, kMlpHidden, kMlpOutPad}, {5, kMlpHidden, kMlpHidden},
+                                       {6, kMlpHidden, kMlpHidden}, {7, kMlpHidden, kMlpHidden},
+                                       {8, kMlpHidden, kMlpInPad}};
+
+__device__ __forceinline__ const CUtensorMap* fused_map(const MlpFusedMaps& m, int i) {
+    return i < kMlpLayers ? &m.w[i] : &m.wt[8 - i];
+}
+
+// 16 consecutive activations of row r, columns c0..c0+15 (c0 a multiple of 16),
+// as BF16 into the swizzled K-major tile: 16-byte chunk j of a row's 128-byte
+// K-atom row sits at chunk position j ^ (r % 8).
+__device__ __forceinline__ void store_act16(uint32_t sA, int r, int c0, const float* d) {
+    uint32_t p[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(d[2 * i], d[2 * i + 1]);
+        p[i] = *reinterpret_cast<const uint32_t*>(&h);
+    }
+    const uint32_t row = sA + uint32_t(c0 >> 6) * kFAtomA + uint32_t(r) * 128u;
+    const uint32_t j0 = uint32_t((c0 & 63) >> 3), sw = uint32_t(r & 7);
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(row + ((j0 ^ sw) << 4)), "r"(p[0]),
+                 "r"(p[1]), "r"(p[2]), "r"(p[3])
+                 : "memory");
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(row + (((j0 + 1u) ^ sw) << 4)),
+                 "r"(p[4]), "r"(p[5]), "r"(p[6]), "r"(p[7])
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// 32 saved gelu'(z) of one row (8 float4), issued early so that their latency
+// overlaps other work
+__device__ __forceinline__ void load_g32(const float* g, float4 (&o)[8]) {
+    const float4* g4 = reinterpret_cast<const float4*>(g);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) o[i] = g4[i];
+}
+
+__global__ void __launch_bounds__(kFusedThreads, 1) k_mlp_fused(const __grid_constant__ MlpFusedMaps maps,
+                                                                const __grid_constant__ MlpFusedArgs a) {
+    extern __shared__ __align__(16) uint8_t smem_raw[];
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_ok;
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    const uint32_t sA = base, sB = base + kFSmemA;
+    float* tail = reinterpret_cast<float*>(smem_raw + (base - raw) + kFSmemA + kFSmemB);
+    float* gbase_s = tail;                        // [128][47]
+    float* base_s = gbase_s + kGemmM * kMlpIn;    // [128]
+    float* y0_s = base_s + kGemmM;                // [128]
+    float* bias_s = y0_s + kGemmM;                // b_0..b_3 [256] each, then b_4 [64]
+    float* w4_s = bias_s + kFBiasFloats;          // W_4[0] [256]
+    const uint32_t bar_load = smem_u32(w4_s + kMlpHidden);
+    const uint32_t bar_mma = bar_load + 8u;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int q = warp & 3, hh = warp >> 2;
+    const int r = 32 * q + lane;                            // this thread's row in the slab
+    const int64_t row0 = int64_t(blockIdx.x) * kGemmM, gr = row0 + r;
+    const bool valid = gr < a.n;
+    const int nst = a.mode == kFusedValueGrad ? 9 : 5;
+
+    auto issue_load = [&](int st, uint32_t bar) {
+        const FusedStage fs = c_fstage[st];
+        const int atoms = fs.K / 64;
+        mbar_expect_tx(bar, uint32_t(atoms) * uint32_t(fs.N) * 128u);
+        for (int at = 0; at < atoms; ++at)
+            tma_load_2d(sB + uint32_t(at) * uint32_t(fs.N) * 128u, fused_map(maps, fs.map), at * 64, 0, bar);
+    };
+
+    if (tid == 0) {
+        mbar_init(bar_load, 1);
+        mbar_init(bar_mma, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_ok = 1;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&s_tmem)),
+                     "r"(256u)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+    if (tid == 0) issue_load(0, bar_load);
+
+    if (hh == 0) {
+        // biases and the value output's weight row, then the standardized input
+        // row: (theta - mean) / std for k < 47, zero padding
+        for (int i = tid; i < kFBiasFloats; i += 128) {
+            const int l = i < 4 * kMlpHidden ? i / kMlpHidden : 4;
+            bias_s[i] = a.bias[l][i - l * kMlpHidden];
+        }
+        for (int i = tid; i < kMlpHidden; i += 128) w4_s[i] = __bfloat162float(a.w4[i]);
+        float d[16];
+#pragma unroll
+        for (int c0 = 0; c0 < kMlpInPad; c0 += 16) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int k = c0 + j;
+                d[j] = (valid && k < kMlpIn) ? (a.theta[gr * kMlpIn + k] - a.xm[k]) / a.xs[k] : 0.0f;
+            }
+            store_act16(sA, r, c0, d);
+        }
+    } else if (a.Hq && valid) {
+        // quadratic baseline: base = -u^T H u / 2, gbase = -H u; four rows of H
+        // at a time (independent sums, each in the order j = 0..46)
+        float u[kMlpIn];
+#pragma unroll
+        for (int j = 0; j < kMlpIn; ++j) u[j] = a.theta[gr * kMlpIn + j];
+        float qd = 0.0f;
+#pragma unroll 1
+        for (int i0 = 0; i0 < kMlpIn; i0 += 4) {
+            float hu[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+            const float* H0 = a.Hq + i0 * kMlpIn;
+#pragma unroll
+            for (int j = 0; j < kMlpIn; ++j)
+#pragma unroll
+                for (int t = 0; t < 4; ++t)
+                    if (i0 + t < kMlpIn) hu[t] = fmaf(H0[t * kMlpIn + j], u[j], hu[t]);
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                if (i0 + t >= kMlpIn) break;
+                gbase_s[r * kMlpIn + i0 + t] = -hu[t];
+                qd = fmaf(a.theta[gr * kMlpIn + i0 + t], hu[t], qd);
+            }
+        }
+        base_s[r] = -0.5f * qd;
+    }
+    fence_async_smem();
+    __syncthreads();
+
+    const uint32_t tlane = tmem + (uint32_t(32 * q) << 16);
+    const int cbeg = 128 * hh;
+    for (int st = 0; st < nst; ++st) {
+        const FusedStage fs = c_fstage[st];
+        // the first 32 saved gelu'(z) this stage's epilogue needs, requested
+        // before the MMA completes
+        const float* gsrc = nullptr;
+        if (st == 4 && a.mode == kFusedValueGrad) gsrc = a.gscr[3] + gr * kMlpHidden;
+        else if (st >= 5 && st < 8) gsrc = a.gscr[7 - st] + gr * kMlpHidden;
+        float4 gbuf[2][8];
+        if (gsrc) load_g32(gsrc + cbeg, gbuf[0]);
+        if (tid == 0) {
+            const uint32_t ph = uint32_t(st & 1);
+            bool ok = mbar_wait(bar_load, ph, a.err, 3);
+            if (ok) {
+                tc_fence_after();
+                const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t(fs.N) >> 3) << 17) |
+                                       ((uint32_t(kGemmM) >> 4) << 24);
+                for (int k = 0; k < fs.K / 16; ++k) {
+                    const uint32_t at = uint32_t(k >> 2), kk = uint32_t(k & 3);
+                    const uint64_t da = smem_desc(sA + at * kFAtomA + kk * 32u);
+                    const uint64_t db = smem_desc(sB + at * uint32_t(fs.N) * 128u + kk * 32u);
+                    tc_mma(tmem, da, db, idesc, k > 0 ? 1u : 0u);
+                }
+                tc_commit(bar_mma);
+                ok = mbar_wait(bar_mma, ph, a.err, 4);
+                if (!ok) mbar_wait(bar_mma, ph, nullptr, 0);   // let MMAs in flight finish (bounded)
+                else if (st + 1 < nst) issue_load(st + 1, bar_load);
+            } else {
+                mbar_wait(bar_load, ph, nullptr, 0);           // let copies in flight land (bounded)
+            }
+            s_ok = ok ? 1 : 0;
+        }
+        __syncthreads();
+        if (!s_ok) break;
+        tc_fence_after();
+        if (st < 4) {
+            // hidden layer: z = acc + b; h = gelu(z) into the tile; gelu'(z) to scratch
+            const float* bias = bias_s + st * kMlpHidden;
+            float* gs = a.gscr[st] + gr * kMlpHidden;
+#pragma unroll 1
+            for (int c0 = cbeg; c0 < cbeg + 128; c0 += 32) {
+                float v[32], g[32];
+                tmem_ld32(tlane + uint32_t(c0), v);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const float z = v[j] + bias[c0 + j];
+                    v[j] = gelu_f(z);
+                    g[j] = gelu_grad_f(z);
+                }
+                float4* g4 = reinterpret_cast<float4*>(gs + c0);
+#pragma unroll
+                for (int i = 0; i < 8; ++i) g4[i] = make_float4(g[4 * i], g[4 * i + 1], g[4 * i + 2], g[4 * i + 3]);
+                store_act16(sA, r, c0, v);
+                store_act16(sA, r, c0 + 16, v + 16);
+            }
+        } else if (st == 4) {
+            // output layer: y = acc + b_4
+            const float* b4 = bias_s + 4 * kMlpHidden;
+            if (hh == 0) {
+                float v[32];
+                tmem_ld32(tlane, v);
+                float v2[16];
+                if (a.mode == kFusedGradHead) tmem_ld16(tlane + 32u, v2);
+                if (valid) {
+                    const float y0 = v[0] + b4[0];
+                    y0_s[r] = y0;
+                    if (a.mode != kFusedValueGrad)
+                        a.loglik[gr] = y0 * a.ys + a.ym + (a.Hq ? base_s[r] : 0.0f);
+                    if (a.mode == kFusedGradHead) {
+                        // output 1 + k is d ll / d x_k
+#pragma unroll
+                        for (int c = 1; c < 48; ++c) {
+                            const float yk = (c < 32 ? v[c] : v2[c - 32]) + b4[c];
+                            const int k = c - 1;
+                            a.grad[gr * kMlpIn + k] = yk * a.ys / a.xs[k] + (a.Hq ? gbase_s[r * kMlpIn + k] : 0.0f);
+                        }
+                    }
+                }
+            }
+            if (a.mode == kFusedValueGrad) {
+                // seed: dz_4 = (one-hot of the value output) W_4 * gelu'(z_4)
+#pragma unroll
+                for (int it = 0; it < 4; ++it) {
+                    const int c0 = cbeg + 32 * it;
+                    if (it < 3) load_g32(gsrc + c0 + 32, gbuf[(it + 1) & 1]);
+                    const float* gg = reinterpret_cast<const float*>(gbuf[it & 1]);
+                    float d[32];
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) d[j] = (valid ? w4_s[c0 + j] : 0.0f) * gg[j];
+                    store_act16(sA, r, c0, d);
+                    store_act16(sA, r, c0 + 16, d + 16);
+                }
+            }
+        } else if (st < 8) {
+            // back through layer 8 - st: dz = acc * gelu'(z)
+#pragma unroll
+            for (int it = 0; it < 4; ++it) {
+                const int c0 = cbeg + 32 * it;
+                if (it < 3) load_g32(gsrc + c0 + 32, gbuf[(it + 1) & 1]);
+                float v[32];
+                tmem_ld32(tlane + uint32_t(c0), v);
+                const float* gg = reinterpret_cast<const float*>(gbuf[it & 1]);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) v[j] = v[j] * gg[j];
+                store_act16(sA, r, c0, v);
+                store_act16(sA, r, c0 + 16, v + 16);
+            }
+        } else if (hh == 0) {
+            // dx = dz_1 W_0: the gradient of the value output in the standardized inputs
+            float v[32], v2[16];
+            tmem_ld32(tlane, v);
+            tmem_ld16(tlane + 32u, v2);
+            if (valid) {
+#pragma unroll
+                for (int k = 0; k < kMlpIn; ++k) {
+                    const float dx = (k < 32 ? v[k] : v2[k - 32]) + 0.0f;
+                    a.grad[gr * kMlpIn + k] = dx * a.ys / a.xs[k] + (a.Hq ? gbase_s[r * kMlpIn + k] : 0.0f);
+                }
+                a.loglik[gr] = y0_s[r] * a.ys + a.ym + (a.Hq ? base_s[r] : 0.0f);
+            }
+        }
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256u)
+                     : "memory");
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_gemm_tc(const CUtensorMap* ta, const CUtensorMap* tb, int M, int N, int K,
@@ -310,6 +624,25 @@ cudaError_t launch_gemm_tc(const CUtensorMap* ta, const CUtensorMap* tb, int M, 
         case kEpiGeluBwd * 1000 + 128: return launch_one<kEpiGeluBwd, 128>(ta, tb, M, N, K, chunks, e, err, s);
     }
     return cudaErrorInvalidValue;
+}
+
+
+cudaError_t launch_mlp_fused(const MlpFusedMaps& maps, const MlpFusedArgs& a, cudaStream_t s) {
+    if (a.n <= 0 || a.mode < kFusedValue || a.mode > kFusedGradHead || !a.theta || !a.loglik ||
+        (a.mode != kFusedValue && !a.grad))
+        return cudaErrorInvalidValue;
+    static bool configured[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 64 && !configured[dev]) {
+        cudaError_t ce = cudaFuncSetAttribute(k_mlp_fused, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              int(kFusedSmem));
+        if (ce != cudaSuccess) return ce;
+        configured[dev] = true;
+    }
+    const unsigned grid = unsigned((a.n + kGemmM - 1) / kGemmM);
+    k_mlp_fused<<<grid, kFusedThreads, kFusedSmem, s>>>(maps, a);
+    return cudaGetLastError();
 }
 
 bool make_tmap_bf16(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols,

@@ -42,6 +42,38 @@ cudaError_t launch_gemm_tc(const CUtensorMap* ta, const CUtensorMap* tb, int M, 
                            int bn, int chunks, int epi, const GemmEpiArgs& e, int* err,
                            cudaStream_t s);
 
+// Fused evaluation of the whole network on one 128-row slab per CTA
+// (forward through the five layers and, in kFusedValueGrad, the value
+// output's gradient back to the input), activations kept in shared memory.
+enum FusedMode : int {
+    kFusedValue = 0,        // loglik only
+    kFusedValueGrad = 1,    // loglik and the back-propagated gradient of the value output
+    kFusedGradHead = 2,     // loglik and the gradient outputs of the network
+};
+
+struct MlpFusedMaps {
+    CUtensorMap w[kMlpLayers];        // W_l [out][in] BF16, box rows = out
+    CUtensorMap wt[kMlpLayers - 1];   // W_l^T [in][out] BF16 for l = 0..3, box rows = in
+};
+
+struct MlpFusedArgs {
+    const float* theta;               // [n][47] raw inputs
+    int64_t n;                        // rows of this launch
+    float xm[kMlpInPad];              // input means (pad 0)
+    float xs[kMlpInPad];              // input std devs (pad 1)
+    float ym, ys;                     // value output mean and std
+    const float* bias[kMlpLayers];    // [out] per layer
+    const __nv_bfloat16* w4;          // W_4 [64][256] BF16 (row 0: the value output's weights)
+    float* gscr[kMlpLayers - 1];      // [>= ceil(n/128)*128][256] scratch: gelu'(z) of layers 1..4
+    const float* Hq;                  // [47][47] quadratic baseline or nullptr
+    float* loglik;                    // [n]
+    float* grad;                      // [n][47] or nullptr (kFusedValue)
+    int mode;
+    int* err;
+};
+
+cudaError_t launch_mlp_fused(const MlpFusedMaps& maps, const MlpFusedArgs& a, cudaStream_t s);
+
 // Make a 2-D BF16 tensor map over a row-major [rows][cols] array with a box of
 // [box_rows][64] and 128-byte swizzle.  Returns false if the driver refuses.
 bool make_tmap_bf16(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols,

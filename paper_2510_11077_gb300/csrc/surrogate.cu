@@ -280,6 +280,8 @@ struct argus_surrogate {
     CUtensorMap tmWT0_b64;   // W_0^T [64][256] with a 64-row box (B operand of dX0 = dZ1 W0)
     int grad_mode = 0;       // 0: gradient head; 1: back-propagated value head
     CUtensorMap tmdY, tmdYT, tmdZ16[2], tmdZT[2];
+    MlpFusedMaps fmaps;      // weights with whole-layer boxes (the fused evaluation kernel)
+    int fused = 1;           // evaluate with the fused kernel (1) or layer by layer (0)
 };
 
 namespace {
@@ -308,6 +310,9 @@ argus_status build_maps(argus_surrogate* s) {
         ok &= make_tmap_bf16(&s->tmHT[l], s->HT[l], kIn[l], R, kIn[l] == 64 ? 64 : 128);
     }
     ok &= make_tmap_bf16(&s->tmWT0_b64, s->W16T[0], kIn[0], kOut[0], 64);
+    for (int l = 0; l < kMlpLayers; ++l) ok &= make_tmap_bf16(&s->fmaps.w[l], s->W16[l], kOut[l], kIn[l], kOut[l]);
+    for (int l = 0; l < kMlpLayers - 1; ++l)
+        ok &= make_tmap_bf16(&s->fmaps.wt[l], s->W16T[l], kIn[l], kOut[l], kIn[l]);
     ok &= make_tmap_bf16(&s->tmdY, s->dY, R, kMlpOutPad, 128);
     ok &= make_tmap_bf16(&s->tmdYT, s->dYT, kMlpOutPad, R, 64);
     for (int i = 0; i < 2; ++i) {
@@ -602,6 +607,28 @@ argus_status argus_surrogate_eval(argus_surrogate* s, const float* theta, int64_
     if (!dev_ptr(theta) || !dev_ptr(loglik) || (grad && !dev_ptr(grad)))
         return sfail(ARGUS_ERR_INVALID_ARG, "argus_surrogate_eval needs device pointers");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (s->fused) {
+        // one launch per max_rows rows: every layer (and the value output's
+        // back-propagation) in one kernel; Z[1..4] hold gelu'(z) as scratch
+        MlpFusedArgs fa{};
+        for (int k = 0; k < kMlpInPad; ++k) { fa.xm[k] = s->norm.xm[k]; fa.xs[k] = s->norm.xs[k]; }
+        fa.ym = s->norm.ym;
+        fa.ys = s->norm.ys;
+        for (int l = 0; l < kMlpLayers; ++l) fa.bias[l] = s->b[l];
+        for (int l = 0; l < kMlpLayers - 1; ++l) fa.gscr[l] = s->Z[l + 1];
+        fa.w4 = s->W16[kMlpLayers - 1];
+        fa.Hq = s->has_baseline ? s->Hq : nullptr;
+        fa.mode = !grad ? kFusedValue : (s->grad_mode == 1 ? kFusedValueGrad : kFusedGradHead);
+        fa.err = s->err;
+        for (int64_t r0 = 0; r0 < B; r0 += s->rows) {
+            fa.n = std::min<int64_t>(s->rows, B - r0);
+            fa.theta = theta + r0 * kMlpIn;
+            fa.loglik = loglik + r0;
+            fa.grad = grad ? grad + r0 * kMlpIn : nullptr;
+            SCK(launch_mlp_fused(s->fmaps, fa, st));
+        }
+        return ARGUS_OK;
+    }
     for (int64_t r0 = 0; r0 < B; r0 += s->rows) {
         const int64_t n = std::min<int64_t>(s->rows, B - r0);
         const int rows = int(((n + 127) / 128) * 128);
@@ -726,6 +753,13 @@ argus_status argus_surrogate_set_grad_mode(argus_surrogate* s, int32_t mode) {
     if (!s) return sfail(ARGUS_ERR_INVALID_ARG, "surrogate handle is NULL");
     if (mode != 0 && mode != 1) return sfail(ARGUS_ERR_INVALID_ARG, "mode must be 0 or 1");
     s->grad_mode = mode;
+    return ARGUS_OK;
+}
+
+argus_status argus_surrogate_set_fused(argus_surrogate* s, int32_t on) {
+    if (!s) return sfail(ARGUS_ERR_INVALID_ARG, "surrogate handle is NULL");
+    if (on != 0 && on != 1) return sfail(ARGUS_ERR_INVALID_ARG, "on must be 0 or 1");
+    s->fused = on;
     return ARGUS_OK;
 }
 

@@ -32,6 +32,7 @@ def _lib():
         lib.argus_surrogate_set_weights.argtypes = [vp, vp]
         lib.argus_surrogate_set_baseline.argtypes = [vp, vp]
         lib.argus_surrogate_set_grad_mode.argtypes = [vp, ctypes.c_int32]
+        lib.argus_surrogate_set_fused.argtypes = [vp, ctypes.c_int32]
         lib.argus_surrogate_get_weights.argtypes = [vp, vp]
         lib.argus_surrogate_eval.argtypes = [vp, vp, ctypes.c_int64, vp, vp, vp]
         lib.argus_surrogate_train_step.argtypes = [vp, vp, vp, vp, ctypes.c_int64, ctypes.c_float,
@@ -93,6 +94,10 @@ class Surrogate:
     def set_grad_mode(self, mode: int):
         """0: gradient outputs of the network; 1: back-propagated value output."""
         _check(_lib().argus_surrogate_set_grad_mode(self.handle, int(mode)))
+
+    def set_fused(self, on: bool):
+        """Evaluate with the fused kernel (True, default) or layer by layer."""
+        _check(_lib().argus_surrogate_set_fused(self.handle, 1 if on else 0))
 
     def set_weights(self, flat):
         flat = np.ascontiguousarray(flat, dtype=np.float32)
