@@ -762,13 +762,24 @@ def run_da_hmc(args):
     for _ in range(reps):
         net.train_step(x, ll, g, 1e-4)
     e[2].record()
+    # the sampler's mode: value output and its back-propagated input gradient
+    net.set_grad_mode(1)
+    for _ in range(5):
+        net.eval(x)
+    e[3].record()
+    for _ in range(reps):
+        net.eval(x)
+    e4 = torch.cuda.Event(enable_timing=True)
+    e4.record()
     torch.cuda.synchronize()
     clk = clocks.stop()
     eval_ms = e[0].elapsed_time(e[1]) / reps
     train_ms = e[1].elapsed_time(e[2]) / reps
+    bp_ms = e[3].elapsed_time(e4) / reps
     layer_macs = 64 * 256 + 3 * 256 * 256 + 256 * 64          # padded shapes
     eval_flop = 2 * layer_macs * 4096
     train_flop = 3 * eval_flop - 2 * 64 * 256 * 4096           # fwd + dX (no dX0) + dW
+    bp_flop = eval_flop + 2 * (3 * 256 * 256 + 256 * 64) * 4096  # fwd + back to the input
     peaks, src = _measured_peaks()
     peak = peaks["bf16_tflops"]
     achieved = eval_flop / (eval_ms * 1e-3) / 1e12
@@ -790,8 +801,10 @@ def run_da_hmc(args):
                                                   "holdout_grad_rel_err_median", "final_loss",
                                                   "data_gen_s", "train_s", "epochs")},
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": None, "kernel": "k_gemm_tc (surrogate eval, 4096 rows)",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "k_mlp_fused (surrogate eval, 4096 rows, forward with gradient head)",
                          "kernel_ms": eval_ms, "peak_source": f"bf16_tflops ({src})",
+                         "backprop_ms": bp_ms, "backprop_tflops": bp_flop / (bp_ms * 1e-3) / 1e12,
                          "train_step_ms": train_ms,
                          "train_tflops": train_flop / (train_ms * 1e-3) / 1e12},
             "clocks": clk, "experiment": res}
