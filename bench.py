@@ -86,8 +86,9 @@ def parse_args():
     ap.add_argument("--autotune", choices=["cache", "off", "force"], default="cache",
                     help="cache: use the tuned-plan cache, tuning on a miss; force: retune")
     ap.add_argument("--tune-batch", type=int, default=4096)
-    ap.add_argument("--mode", choices=["filter", "da-hmc"], default="filter",
-                    help="filter: loglik+grad evals/s (default); da-hmc: surrogate delayed acceptance")
+    ap.add_argument("--mode", choices=["filter", "da-hmc", "surrogate"], default="filter",
+                    help="filter: loglik+grad evals/s (default); da-hmc: surrogate delayed acceptance; "
+                         "surrogate: the surrogate's evaluation alone, fused vs per-layer")
     ap.add_argument("--plan", default="",
                     help="fixed plan, e.g. tape_cache=1,walkers_per_cta=128 (disables autotune)")
     return ap.parse_args()
@@ -812,12 +813,70 @@ def run_da_hmc(args):
     return 0
 
 
+def run_surrogate(args):
+    """The surrogate network's evaluation alone (random seeded weights, the
+    quadratic baseline on), CUDA events over 50 calls after 5 warm-up calls.
+    The sampler's mode (value + back-propagated input gradient) runs first
+    with the fused kernel, so its third launch is the one to profile."""
+    import numpy as np
+    import torch
+
+    from paper_2510_11077_gb300 import surrogate
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    peaks, src = _measured_peaks()
+    modes = [("value backprop", 1, True), ("gradient head", 0, True), ("value", 0, False)]
+    fwd_flop = 2 * (64 * 256 + 3 * 256 * 256 + 256 * 64)
+    bwd_flop = 2 * (3 * 256 * 256 + 256 * 64)
+    out = {}
+    for rows in (4096, 16384):
+        net = surrogate.Surrogate(device=local, max_rows=rows, seed=3)
+        rng = np.random.default_rng(1)
+        net.set_normalizers(np.zeros(47), np.ones(47), 0.0, 1.0)
+        A = rng.standard_normal((47, 47)).astype(np.float32) / 47
+        net.set_baseline(A @ A.T + 0.1 * np.eye(47, dtype=np.float32))
+        x = torch.from_numpy(rng.standard_normal((rows, 47)).astype(np.float32)).to(dev)
+        for name, gm, wg in modes:
+            net.set_grad_mode(gm)
+            for fused in (True, False):
+                net.set_fused(fused)
+                for _ in range(5):
+                    net.eval(x, with_grad=wg)
+                torch.cuda.synchronize(dev)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(50):
+                    net.eval(x, with_grad=wg)
+                e1.record()
+                torch.cuda.synchronize(dev)
+                net.check()
+                us = e0.elapsed_time(e1) / 50 * 1e3
+                flop = rows * (fwd_flop + (bwd_flop if gm == 1 and wg else 0))
+                out[f"{rows} rows, {name}, {'fused' if fused else 'per layer'}"] = {
+                    "us": us, "tflops": flop / (us * 1e-6) / 1e12}
+        net.close()
+    key = "4096 rows, value backprop, fused"
+    line = {"metric": "surrogate evaluation latency (value + back-propagated gradient, 4096 rows)",
+            "value": out[key]["us"], "unit": "us", "n_gpus": 1, "higher_is_better": False,
+            "dtype": "bf16 (fp32 accumulate)", "data": "synthetic",
+            "roofline": {"bound": "tensor", "achieved": out[key]["tflops"], "peak": peaks["bf16_tflops"],
+                         "unit": "TFLOP/s", "frac": out[key]["tflops"] / peaks["bf16_tflops"],
+                         "kernel": "k_mlp_fused", "peak_source": f"bf16_tflops ({src})"},
+            "runs": out}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.mode == "da-hmc":
         return run_da_hmc(args)
+    if args.mode == "surrogate":
+        return run_surrogate(args)
     return run_ours(args)
 
 
