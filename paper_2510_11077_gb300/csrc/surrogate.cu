@@ -67,19 +67,23 @@ struct Norm {
 
 // X0[r][k] = bf16((theta[r][k] - xm_k) / xs_k) for k < 47, 0 otherwise; rows >= n are 0.
 // xt (optional) is the transposed copy [64][pitch].
+// One thread per (row, column): block (64 columns, 4 rows), grid rows / 4.
 __global__ void k_standardize(const float* __restrict__ theta, int64_t n, int rows, Norm nm,
                               __nv_bfloat16* __restrict__ x, __nv_bfloat16* __restrict__ xt,
                               int pitch) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= rows) return;
-    for (int k = 0; k < kMlpInPad; ++k) {
-        float v = 0.0f;
-        if (r < n && k < kMlpIn) v = (theta[int64_t(r) * kMlpIn + k] - nm.xm[k]) / nm.xs[k];
-        const __nv_bfloat16 b = __float2bfloat16_rn(v);
-        x[int64_t(r) * kMlpInPad + k] = b;
-        if (xt) xt[int64_t(k) * pitch + r] = b;
-    }
+    const int k = threadIdx.x;
+    const int r = blockIdx.x * blockDim.y + threadIdx.y;
+    if (r >= rows || k >= kMlpInPad) return;
+    float v = 0.0f;
+    if (r < n && k < kMlpIn) v = (theta[int64_t(r) * kMlpIn + k] - nm.xm[k]) / nm.xs[k];
+    const __nv_bfloat16 b = __float2bfloat16_rn(v);
+    x[int64_t(r) * kMlpInPad + k] = b;
+    if (xt) xt[int64_t(k) * pitch + r] = b;
 }
+
+constexpr int kRowsPerBlock = 4;   // rows per block of the (column, row) kernels
+inline dim3 rc_grid(int rows) { return dim3(unsigned((rows + kRowsPerBlock - 1) / kRowsPerBlock)); }
+inline dim3 rc_block() { return dim3(kMlpInPad, kRowsPerBlock); }
 
 // Standardized targets, weighted squared error per row, and
 // dY = bf16(2 w_j (y - t) / n) (+ its transpose); padding rows and columns get 0.
@@ -88,52 +92,74 @@ __global__ void k_loss(const float* __restrict__ y, const float* __restrict__ ll
                        const float* __restrict__ gbase, int64_t n, int rows, Norm nm,
                        __nv_bfloat16* __restrict__ dy, __nv_bfloat16* __restrict__ dyt, int pitch,
                        float* __restrict__ row_loss) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= rows) return;
-    float acc = 0.0f;
-    for (int j = 0; j < kMlpOutPad; ++j) {
-        float d = 0.0f;
-        if (r < n && j < kMlpOut) {
-            const float b0 = base ? base[r] : 0.0f;
-            const float bj = (gbase && j > 0) ? gbase[int64_t(r) * kMlpIn + (j - 1)] : 0.0f;
-            const float t = (j == 0) ? (ll[r] - b0 - nm.ym) / nm.ys
-                                     : (grad[int64_t(r) * kMlpIn + (j - 1)] - bj) * nm.xs[j - 1] / nm.ys;
-            const float e = y[int64_t(r) * kMlpOutPad + j] - t;
-            acc += nm.w[j] * e * e;
-            d = 2.0f * nm.w[j] * e / float(n);
-        }
+    // one thread per (row, output j): block (64 outputs, 4 rows)
+    __shared__ float term[kRowsPerBlock][kMlpOutPad];
+    const int j = threadIdx.x, ty = threadIdx.y;
+    const int r = blockIdx.x * blockDim.y + ty;
+    const bool live = r < rows;
+    float d = 0.0f, sq = 0.0f;
+    if (live && r < n && j < kMlpOut) {
+        const float b0 = base ? base[r] : 0.0f;
+        const float bj = (gbase && j > 0) ? gbase[int64_t(r) * kMlpIn + (j - 1)] : 0.0f;
+        const float t = (j == 0) ? (ll[r] - b0 - nm.ym) / nm.ys
+                                 : (grad[int64_t(r) * kMlpIn + (j - 1)] - bj) * nm.xs[j - 1] / nm.ys;
+        const float e = y[int64_t(r) * kMlpOutPad + j] - t;
+        sq = nm.w[j] * e * e;
+        d = 2.0f * nm.w[j] * e / float(n);
+    }
+    if (live) {
         const __nv_bfloat16 b = __float2bfloat16_rn(d);
         dy[int64_t(r) * kMlpOutPad + j] = b;
         dyt[int64_t(j) * pitch + r] = b;
     }
-    row_loss[r] = (r < n) ? acc : 0.0f;
+    term[ty][j] = sq;
+    __syncthreads();
+    if (live && j == 0) {   // the row's loss, summed over j in order
+        float acc = 0.0f;
+        for (int jj = 0; jj < kMlpOutPad; ++jj) acc += term[ty][jj];
+        row_loss[r] = (r < n) ? acc : 0.0f;
+    }
 }
 
-// loss = sum_r row_loss[r] / n (fixed order)
-__global__ void k_loss_sum(const float* __restrict__ row_loss, int rows, int64_t n,
-                           float* __restrict__ out) {
-    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+// loss = sum_r row_loss[r] / n in a fixed order: one block of 1024 threads,
+// thread t sums rows t, t + 1024, ..., then a fixed binary tree.
+constexpr int kSumThreads = 1024;
+__global__ void __launch_bounds__(kSumThreads) k_loss_sum(const float* __restrict__ row_loss, int rows,
+                                                          int64_t n, float* __restrict__ out) {
+    __shared__ float part[kSumThreads];
     float s = 0.0f;
-    for (int r = 0; r < rows; ++r) s += row_loss[r];
-    *out = s / float(n);
+    for (int r = threadIdx.x; r < rows; r += kSumThreads) s += row_loss[r];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = kSumThreads / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = part[0] / float(n);
 }
 
-// Column sums (bias gradients), fixed row order: out[c] = sum_r m[r][c].
-__global__ void k_colsum_f32(const float* __restrict__ m, int rows, int cols, float* __restrict__ out) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= cols) return;
-    float s = 0.0f;
-    for (int r = 0; r < rows; ++r) s += m[int64_t(r) * cols + c];
-    out[c] = s;
-}
+// Column sums (bias gradients) in a fixed order: out[c] = sum_r m[r][c].  A
+// block takes 32 columns with 32 row phases (thread (c, p) sums rows p,
+// p + 32, ...); the 32 phase sums are then added in phase order.  Grid cols / 32.
+__device__ __forceinline__ float as_float(float v) { return v; }
+__device__ __forceinline__ float as_float(__nv_bfloat16 v) { return __bfloat162float(v); }
 
-__global__ void k_colsum_bf16(const __nv_bfloat16* __restrict__ m, int rows, int cols,
-                              float* __restrict__ out) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= cols) return;
+template <class T>
+__global__ void __launch_bounds__(1024) k_colsum(const T* __restrict__ m, int rows, int cols,
+                                                 float* __restrict__ out) {
+    __shared__ float part[32][33];
+    const int tx = threadIdx.x & 31, ph = threadIdx.x >> 5;
+    const int c = blockIdx.x * 32 + tx;
     float s = 0.0f;
-    for (int r = 0; r < rows; ++r) s += __bfloat162float(m[int64_t(r) * cols + c]);
-    out[c] = s;
+    if (c < cols)
+        for (int r = ph; r < rows; r += 32) s += as_float(m[int64_t(r) * cols + c]);
+    part[ph][tx] = s;
+    __syncthreads();
+    if (ph == 0 && c < cols) {
+        float t = 0.0f;
+        for (int k = 0; k < 32; ++k) t += part[k][tx];
+        out[c] = t;
+    }
 }
 
 // Adam on one weight matrix W [N][K] (FP32 master) with its gradient as the
@@ -206,19 +232,27 @@ __global__ void k_destandardize_bp(const float* __restrict__ y, const float* __r
 
 // Quadratic baseline of the log-likelihood in the network's input coordinates:
 // base = -1/2 u^T H u, gbase = -H u (H symmetric [47][47]; all zero = no baseline).
+// One thread per (row, i) forms (H u)_i; thread i == 0 then sums q over i in order.
+// Block (64, 4 rows), grid ceil(n / 4).
 __global__ void k_baseline(const float* __restrict__ u, int64_t n, const float* __restrict__ H,
                            float* __restrict__ base, float* __restrict__ gbase) {
-    const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (r >= n) return;
+    __shared__ float hus[4][kMlpInPad];
+    const int i = threadIdx.x, ty = threadIdx.y;
+    const int64_t r = int64_t(blockIdx.x) * blockDim.y + ty;
+    const bool live = r < n;
     const float* ur = u + r * kMlpIn;
-    float q = 0.0f;
-    for (int i = 0; i < kMlpIn; ++i) {
-        float hu = 0.0f;
+    float hu = 0.0f;
+    if (live && i < kMlpIn) {
         for (int j = 0; j < kMlpIn; ++j) hu = fmaf(H[i * kMlpIn + j], ur[j], hu);
         gbase[r * kMlpIn + i] = -hu;
-        q = fmaf(ur[i], hu, q);
     }
-    base[r] = -0.5f * q;
+    hus[ty][i] = hu;
+    __syncthreads();
+    if (live && i == 0) {
+        float q = 0.0f;
+        for (int k = 0; k < kMlpIn; ++k) q = fmaf(ur[k], hus[ty][k], q);
+        base[r] = -0.5f * q;
+    }
 }
 
 // De-standardize: ll = y0 ys + ym, grad_k = y_{1+k} ys / xs_k.
@@ -632,13 +666,13 @@ argus_status argus_surrogate_eval(argus_surrogate* s, const float* theta, int64_
     for (int64_t r0 = 0; r0 < B; r0 += s->rows) {
         const int64_t n = std::min<int64_t>(s->rows, B - r0);
         const int rows = int(((n + 127) / 128) * 128);
-        k_standardize<<<(rows + 127) / 128, 128, 0, st>>>(theta + r0 * kMlpIn, n, rows, s->norm,
+        k_standardize<<<rc_grid(rows), rc_block(), 0, st>>>(theta + r0 * kMlpIn, n, rows, s->norm,
                                                           s->H[0], nullptr, s->rows);
         const bool bp = grad && s->grad_mode == 1;
         argus_status e = forward(s, rows, bp, st);
         if (e) return e;
         if (s->has_baseline)
-            k_baseline<<<unsigned((n + 127) / 128), 128, 0, st>>>(theta + r0 * kMlpIn, n, s->Hq,
+            k_baseline<<<rc_grid(int(n)), rc_block(), 0, st>>>(theta + r0 * kMlpIn, n, s->Hq,
                                                                  s->base, s->gbase);
         if (!bp) {
             k_destandardize<<<unsigned((n + 127) / 128), 128, 0, st>>>(
@@ -671,16 +705,16 @@ argus_status argus_surrogate_train_step(argus_surrogate* s, const float* theta, 
     const int rows = int(((n + 127) / 128) * 128);
     const int ck = (rows % 256 == 0) ? 256 : 128;   // K per split-K chunk over the batch
     const int chunks = rows / ck;
-    k_standardize<<<(rows + 127) / 128, 128, 0, st>>>(theta, n, rows, s->norm, s->H[0], s->HT[0],
+    k_standardize<<<rc_grid(rows), rc_block(), 0, st>>>(theta, n, rows, s->norm, s->H[0], s->HT[0],
                                                       s->rows);
     argus_status e = forward(s, rows, true, st);
     if (e) return e;
     if (s->has_baseline)
-        k_baseline<<<unsigned((n + 127) / 128), 128, 0, st>>>(theta, n, s->Hq, s->base, s->gbase);
-    k_loss<<<(rows + 127) / 128, 128, 0, st>>>(s->Y, loglik, grad, s->has_baseline ? s->base : nullptr,
+        k_baseline<<<rc_grid(int(n)), rc_block(), 0, st>>>(theta, n, s->Hq, s->base, s->gbase);
+    k_loss<<<rc_grid(rows), rc_block(), 0, st>>>(s->Y, loglik, grad, s->has_baseline ? s->base : nullptr,
                                                s->has_baseline ? s->gbase : nullptr, n, rows, s->norm,
                                                s->dY, s->dYT, s->rows, s->row_loss);
-    k_loss_sum<<<1, 32, 0, st>>>(s->row_loss, rows, n, loss);
+    k_loss_sum<<<1, kSumThreads, 0, st>>>(s->row_loss, rows, n, loss);
     // output layer: dW4^T = H4^T dY (split-K over rows), db4 = sum_r dY, dH4 = dY W4 -> dZ4
     {
         GemmEpiArgs g = epi_none();
@@ -690,7 +724,7 @@ argus_status argus_surrogate_train_step(argus_surrogate* s, const float* theta, 
         cudaError_t ce = launch_gemm_tc(&s->tmHT[4], &s->tmdYT, kMlpHidden, kMlpOutPad, ck, 64, chunks,
                                         kEpiF32, g, s->err, st);
         if (ce != cudaSuccess) return scuda(ce, "dW4 GEMM");
-        k_colsum_bf16<<<1, kMlpOutPad, 0, st>>>(s->dY, rows, kMlpOutPad, s->gb[4]);
+        k_colsum<__nv_bfloat16><<<kMlpOutPad / 32, 1024, 0, st>>>(s->dY, rows, kMlpOutPad, s->gb[4]);
         GemmEpiArgs d = epi_none();
         d.zin = s->Z[4];
         d.ldz = kMlpHidden;
@@ -715,7 +749,7 @@ argus_status argus_surrogate_train_step(argus_surrogate* s, const float* theta, 
         cudaError_t ce = launch_gemm_tc(&s->tmdZT[cur], &s->tmHT[l], kMlpHidden, K, ck, K == 64 ? 64 : 128,
                                         chunks, kEpiF32, g, s->err, st);
         if (ce != cudaSuccess) return scuda(ce, "dW GEMM");
-        k_colsum_f32<<<1, kMlpHidden, 0, st>>>(s->dZ32[cur], rows, kMlpHidden, s->gb[l]);
+        k_colsum<float><<<kMlpHidden / 32, 1024, 0, st>>>(s->dZ32[cur], rows, kMlpHidden, s->gb[l]);
         if (l > 0) {
             GemmEpiArgs d = epi_none();
             d.zin = s->Z[l];
