@@ -43,7 +43,7 @@ typedef struct argus_gwb argus_gwb;
 /* Copy the pulsars (argus.h's argus_pulsar, validated the same way) to device
  * `device` and build the handle: the merged, time-ordered TOA stream and the
  * Hellings-Downs matrix of the pulsar positions.  ARGUS_ERR_UNSUPPORTED for
- * more than 48 pulsars or a device that is not sm_103. */
+ * more than 64 pulsars or a device that is not sm_103. */
 argus_status argus_gwb_create(const argus_pulsar* pulsars, int32_t n_pulsars, int32_t device,
                               argus_gwb** out);
 
@@ -62,10 +62,10 @@ argus_status argus_gwb_loglik(argus_gwb* gwb, const double* theta, int64_t B, do
  * reverse-mode adjoint sweep through the joint filter: the state (upper
  * triangle of the covariance and the mean) is saved every ceil(sqrt(N))
  * TOAs, each segment is re-run saving the state before every TOA, and the
- * adjoint steps run backwards through it.  At most 32 pulsars (both the
+ * adjoint steps run backwards through it.  At most 48 pulsars (both the
  * covariance and its adjoint stay in shared memory; ARGUS_ERR_UNSUPPORTED
  * beyond).  Device scratch grows to 2 x max(ceil(sqrt N), segments) x
- * (3P(3P+1)/2 + 3P) doubles per resident block.  Out-of-domain vectors get
+ * (3P(3P+1)/2 + 3P + P + 1) doubles per resident block.  Out-of-domain vectors get
  * loglik = -inf and a zero gradient. */
 argus_status argus_gwb_loglik_grad(argus_gwb* gwb, const double* theta, int64_t B, double* loglik,
                                    double* grad, void* stream);

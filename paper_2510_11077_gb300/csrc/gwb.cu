@@ -54,7 +54,7 @@ namespace {
 constexpr double kLog2PiGwb = 1.8378770664093454836;
 constexpr double kLn10Gwb = 2.302585092994045684;
 constexpr int kGwbThreads = 256;
-constexpr int kGwbGradMaxPulsars = 32;   // gradient: two 3P x 3P matrices in shared memory
+constexpr int kGwbGradMaxPulsars = 48;   // gradient: two packed 3P x 3P triangles in shared memory
 constexpr int kCo = 9;                   // per-pulsar coefficients (see GwbSmem::co)
 
 struct GwbRec {     // one TOA of the merged, time-ordered stream (32 bytes)
@@ -87,8 +87,7 @@ struct GwbArgs {
 // upper triangle is kept current; the adjoint Pb (gradient) is kept full.
 struct GwbSmem {
     int P, n, nb, ne;
-    int ld;         // row stride of Pm and Pb: n rounded up to odd (conflict-free columns)
-    double* Pm;     // [n][n]
+    double* Pm;     // packed upper triangle, n (n + 1) / 2
     double* m;      // [n]
     double* c;      // [n]
     double* co;     // [P][9]: a, b, Q/sigma^2 (c00, c01, c11), d/dgamma of b and of c00, c01, c11
@@ -100,7 +99,7 @@ struct GwbSmem {
     const double* G;   // [P][P] Hellings-Downs, in global memory (read through the read-only cache)
     double* par;    // [P][4]: sigma^2, gamma_p, EFAC^2, EFAC
     double* gw;     // GW process: a, b, c00, c01, c11, db, dc00, dc01, dc11 (per unit h_a^2); scalars
-    double* Pb;     // [n][n]   (gradient)
+    double* Pb;     // packed upper triangle (gradient)
     double* mb;     // [n]      (gradient)
     double* u;      // [n]      (gradient)
     double* v;      // [n]      (gradient)
@@ -116,20 +115,18 @@ enum { kGwA = 0, kGwHa2 = 9, kGwGa, kGwE, kGwS, kGwRS, kGwG, kGwOk, kGwSb, kGwEb
 constexpr double kGwbTiny = 0x1p-200;   // smallest scale factor kept (scaled frame)
 
 // chunks per pulsar of the adjoint's parameter sums (J ranges of about 5)
-__host__ __device__ inline int gwb_jchunks(int P) { return (P + 4) / 5; }
+__host__ __device__ inline int gwb_jchunks(int P) { return (P + 4) / 5 < 8 ? (P + 4) / 5 : 8; }
 // doubles of one saved state: the upper triangle of P, m and the P + 1 scales
 __host__ __device__ inline int64_t gwb_rec_len(int P) {
     const int64_t n = 3 * int64_t(P);
     return n * (n + 1) / 2 + n + P + 1;
 }
 
-__host__ __device__ inline int gwb_ld(int n) { return n | 1; }
-
 __host__ __device__ inline size_t gwb_smem_doubles(int P, bool grad) {
-    const size_t n = 3 * size_t(P), ld = size_t(gwb_ld(int(n)));
-    size_t d = n * ld + 3 * n + kCo * size_t(P) + 5 * (size_t(P) + 1) + 4 * size_t(P) + 2 * (size_t(P) + 1) +
+    const size_t n = 3 * size_t(P), ne = n * (n + 1) / 2;
+    size_t d = ne + 3 * n + kCo * size_t(P) + 5 * (size_t(P) + 1) + 4 * size_t(P) + 2 * (size_t(P) + 1) +
                kGwSlots;
-    if (grad) d += n * ld + 3 * n + 5 * size_t(P) + 6 * size_t(P) * gwb_jchunks(P) + 2 * size_t(P);
+    if (grad) d += ne + 3 * n + 5 * size_t(P) + 6 * size_t(P) * gwb_jchunks(P) + 2 * size_t(P);
     return d;
 }
 
@@ -143,10 +140,10 @@ __host__ __device__ inline size_t gwb_smem_bytes(int P, bool grad) {
 
 __device__ GwbSmem gwb_carve(double* base, int P, bool grad, const double* G) {
     GwbSmem s;
-    s.P = P; s.n = 3 * P; s.nb = P * (P + 1) / 2; s.ne = s.n * (s.n + 1) / 2; s.ld = gwb_ld(s.n);
+    s.P = P; s.n = 3 * P; s.nb = P * (P + 1) / 2; s.ne = s.n * (s.n + 1) / 2;
     const int n = s.n;
     double* q = base;
-    s.Pm = q; q += size_t(n) * s.ld;
+    s.Pm = q; q += s.ne;
     s.m = q; q += n;
     s.c = q; q += n;
     s.co = q; q += kCo * P;
@@ -158,7 +155,7 @@ __device__ GwbSmem gwb_carve(double* base, int P, bool grad, const double* G) {
     s.par = q; q += 4 * P;
     s.gw = q; q += kGwSlots;
     if (grad) {
-        s.Pb = q; q += size_t(n) * s.ld;
+        s.Pb = q; q += s.ne;
         s.mb = q; q += n;
         s.u = q; q += n;
         s.v = q; q += n;
@@ -175,8 +172,14 @@ __device__ GwbSmem gwb_carve(double* base, int P, bool grad, const double* G) {
 
 __device__ __forceinline__ double gwb_G(const GwbSmem& s, int I, int J) { return __ldg(s.G + I * s.P + J); }
 
+// Symmetric matrices (P and its adjoint) are stored as packed upper
+// triangles, row by row: entry (i, j), i <= j, at i n - i (i - 1) / 2 + j - i
+// (the order of the (i, j) pair table and of a saved state).
+__device__ __forceinline__ int pk(int n, int i, int j) { return i * n - ((i * (i - 1)) >> 1) + (j - i); }
+// row i of a packed triangle: prow(M, n, i)[j] is entry (i, j) for j >= i
+__device__ __forceinline__ double* prow(double* M, int n, int i) { return M + (i * n - ((i * (i - 1)) >> 1) - i); }
 __device__ __forceinline__ double psym(const double* M, int n, int i, int j) {
-    return i <= j ? M[i * n + j] : M[j * n + i];
+    return i <= j ? M[pk(n, i, j)] : M[pk(n, j, i)];
 }
 
 // sum over a warp in a fixed order (the same tree on every call)
@@ -204,7 +207,6 @@ __device__ void gwb_tables(const GwbSmem& s, const GwbArgs& a) {
 // false (uniformly) when theta is out of the domain
 __device__ bool gwb_setup(const GwbSmem& s, const GwbArgs& a, const double* th) {
     const int P = s.P, n = s.n, D = 2 + 3 * P;
-    const int ld = s.ld;
     if (threadIdx.x == 0) {
         bool ok = true;
         for (int j = 0; j < D; ++j) ok = ok && isfinite(th[j]);
@@ -226,13 +228,13 @@ __device__ bool gwb_setup(const GwbSmem& s, const GwbArgs& a, const double* th) 
     __syncthreads();
     if (s.gw[kGwOk] == 0.0) return false;
     const double ha2 = s.gw[kGwHa2], ga = s.gw[kGwGa];
-    for (int i = threadIdx.x; i < n * n; i += blockDim.x) {
-        const int r = i / n, col = i - r * n;
+    for (int q = threadIdx.x; q < s.ne; q += blockDim.x) {
+        const int r = s.ent[2 * q], col = s.ent[2 * q + 1];
         const int I = r / 3, J = col / 3, uu = r - 3 * I, vv = col - 3 * J;
         double x = 0.0;
         if (uu == 2 && vv == 2) x = ha2 * gwb_G(s, I, J) / (2.0 * ga);
         else if (I == J && uu < 2 && vv < 2) x = a.p0[3 * I + uu + vv];
-        s.Pm[r * ld + col] = x;
+        s.Pm[q] = x;
     }
     for (int i = threadIdx.x; i < n; i += blockDim.x) s.m[i] = 0.0;
     __syncthreads();
@@ -255,8 +257,7 @@ __device__ void gwb_coef(const GwbSmem& s, double dt) {
 
 // 2. predict: the mean and every upper 3x3 block, F_I P_IJ F_J^T + Q_IJ
 __device__ void gwb_predict(const GwbSmem& s) {
-    const int P = s.P;
-    const int ld = s.ld;
+    const int P = s.P, n = s.n;
     const double* gw = s.gw;
     const double aa = gw[0], ba = gw[1], ha2 = gw[kGwHa2];
     const double qa00 = ha2 * gw[2], qa01 = ha2 * gw[3], qa11 = ha2 * gw[4];
@@ -275,7 +276,7 @@ __device__ void gwb_predict(const GwbSmem& s) {
         for (int u = 0; u < 3; ++u)
 #pragma unroll
             for (int v = 0; v < 3; ++v)
-                X[u][v] = (I < J || u <= v) ? s.Pm[(3 * I + u) * ld + 3 * J + v] : s.Pm[(3 * I + v) * ld + 3 * J + u];
+                X[u][v] = (I < J || u <= v) ? s.Pm[pk(n, 3 * I + u, 3 * J + v)] : s.Pm[pk(n, 3 * I + v, 3 * J + u)];
         double Y[3][3];   // F_I X
 #pragma unroll
         for (int v = 0; v < 3; ++v) {
@@ -306,7 +307,7 @@ __device__ void gwb_predict(const GwbSmem& s) {
         for (int u = 0; u < 3; ++u)
 #pragma unroll
             for (int v = 0; v < 3; ++v)
-                if (I < J || u <= v) s.Pm[(3 * I + u) * ld + 3 * J + v] = Z[u][v];
+                if (I < J || u <= v) s.Pm[pk(n, 3 * I + u, 3 * J + v)] = Z[u][v];
     }
 }
 
@@ -342,8 +343,7 @@ __device__ void gwb_coef_scaled(const GwbSmem& s, double dt) {
 // 2'. scaled predict: mh <- Fh mh, Ph <- Fh Ph Fh^T + S'^-1 Q S'^-1 (upper
 // blocks); Fh is the identity but for the rho row (b_p s_p, b_a s_a)
 __device__ void gwb_predict_scaled(const GwbSmem& s) {
-    const int P = s.P;
-    const int ld = s.ld;
+    const int P = s.P, n = s.n;
     const double* ca = s.cs + 5 * P;
     const double al = ca[0], qa00 = ca[1], qa01 = ca[2], qa11 = ca[3];
     for (int p = threadIdx.x; p < P; p += blockDim.x) {
@@ -353,9 +353,12 @@ __device__ void gwb_predict_scaled(const GwbSmem& s) {
     for (int q = threadIdx.x; q < s.nb; q += blockDim.x) {
         const int I = s.pairs[2 * q], J = s.pairs[2 * q + 1];
         const double bI = s.cs[5 * I], bJ = s.cs[5 * J];
-        double* B = s.Pm + (3 * I) * ld + 3 * J;
-        const double x00 = B[0], x01 = B[1], x02 = B[2], x11 = B[ld + 1], x12 = B[ld + 2], x22 = B[2 * ld + 2];
-        const double x10 = I < J ? B[ld] : x01, x20 = I < J ? B[2 * ld] : x02, x21 = I < J ? B[2 * ld + 1] : x12;
+        // rows 3I, 3I+1, 3I+2 of the block (entry (3I+u, 3J+v) is R_u[v])
+        double* R0 = prow(s.Pm, n, 3 * I) + 3 * J;
+        double* R1 = prow(s.Pm, n, 3 * I + 1) + 3 * J;
+        double* R2 = prow(s.Pm, n, 3 * I + 2) + 3 * J;
+        const double x00 = R0[0], x01 = R0[1], x02 = R0[2], x11 = R1[1], x12 = R1[2], x22 = R2[2];
+        const double x10 = I < J ? R1[0] : x01, x20 = I < J ? R2[0] : x02, x21 = I < J ? R2[1] : x12;
         // row 0 of Fh_I X, then column 0 of (Fh_I X) Fh_J^T
         const double y0 = fma(bI, x10, fma(al, x20, x00));
         const double y1 = fma(bI, x11, fma(al, x21, x01));
@@ -372,10 +375,10 @@ __device__ void gwb_predict_scaled(const GwbSmem& s) {
             z01 += cI[2];
             z11 += cI[3];
         } else {
-            B[ld] = fma(bJ, x11, fma(al, x12, x10));
-            B[2 * ld] = fma(g, qa01, fma(bJ, x21, fma(al, x22, x20)));
+            R1[0] = fma(bJ, x11, fma(al, x12, x10));
+            R2[0] = fma(g, qa01, fma(bJ, x21, fma(al, x22, x20)));
         }
-        B[0] = z00; B[1] = z01; B[2] = z02; B[ld + 1] = z11; B[2 * ld + 2] = z22;
+        R0[0] = z00; R0[1] = z01; R0[2] = z02; R1[1] = z11; R2[2] = z22;
     }
 }
 
@@ -388,10 +391,9 @@ __device__ __forceinline__ double gwb_scale_of(const double* sc, int P, int i) {
 // P = S Ph S, m = S mh for the scales sc (the upper triangle and the mean)
 __device__ void gwb_fold(const GwbSmem& s, const double* sc) {
     const int n = s.n, P = s.P;
-    const int ld = s.ld;
     for (int q = threadIdx.x; q < s.ne; q += blockDim.x) {
         const int r = s.ent[2 * q], col = s.ent[2 * q + 1];
-        s.Pm[r * ld + col] *= gwb_scale_of(sc, P, r) * gwb_scale_of(sc, P, col);
+        s.Pm[q] *= gwb_scale_of(sc, P, r) * gwb_scale_of(sc, P, col);
     }
     for (int i = threadIdx.x; i < n; i += blockDim.x) s.m[i] *= gwb_scale_of(sc, P, i);
 }
@@ -400,13 +402,12 @@ __device__ void gwb_fold(const GwbSmem& s, const double* sc) {
 // c each form 1/S); thread 0 records e, S, 1/S, e/S
 __device__ void gwb_innovate(const GwbSmem& s, const GwbArgs& a, const GwbRec& rk) {
     const int n = s.n, i0 = 3 * rk.q;
-    const int ld = s.ld;
     if (threadIdx.x < n) {
         const double R = fma(s.par[4 * rk.q + 2], rk.s2, a.equad2[rk.q]);
-        const double S = s.Pm[i0 * ld + i0] + R;
+        const double S = s.Pm[pk(n, i0, i0)] + R;
         const double rS = rcp_nr(S);
         for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            const double ci = psym(s.Pm, ld, i, i0);
+            const double ci = psym(s.Pm, n, i, i0);
             s.c[i] = ci;
             s.ct[i] = ci * rS;
         }
@@ -423,11 +424,10 @@ __device__ void gwb_innovate(const GwbSmem& s, const GwbArgs& a, const GwbRec& r
 // 4. update (upper triangle, P_ij -= c_i (c_j / S)) and mean
 __device__ void gwb_update(const GwbSmem& s) {
     const int n = s.n;
-    const int ld = s.ld;
     const double g = s.gw[kGwG];
     for (int q = threadIdx.x; q < s.ne; q += blockDim.x) {
         const int r = s.ent[2 * q], col = s.ent[2 * q + 1];
-        s.Pm[r * ld + col] = fma(-s.c[r], s.ct[col], s.Pm[r * ld + col]);
+        s.Pm[q] = fma(-s.c[r], s.ct[col], s.Pm[q]);
     }
     for (int i = threadIdx.x; i < n; i += blockDim.x) s.m[i] = fma(s.c[i], g, s.m[i]);
 }
@@ -493,13 +493,13 @@ __global__ void __launch_bounds__(kGwbThreads) k_gwb_filter(GwbArgs a) {
 
 // state (upper triangle of P, then m) to / from a global slot
 __device__ void gwb_save(const GwbSmem& s, double* dst) {
-    for (int q = threadIdx.x; q < s.ne; q += blockDim.x) dst[q] = s.Pm[s.ent[2 * q] * s.ld + s.ent[2 * q + 1]];
+    for (int q = threadIdx.x; q < s.ne; q += blockDim.x) dst[q] = s.Pm[q];
     for (int i = threadIdx.x; i < s.n; i += blockDim.x) dst[s.ne + i] = s.m[i];
     for (int p = threadIdx.x; p <= s.P; p += blockDim.x) dst[s.ne + s.n + p] = s.sg[p];
 }
 
 __device__ void gwb_load(const GwbSmem& s, const double* src) {
-    for (int q = threadIdx.x; q < s.ne; q += blockDim.x) s.Pm[s.ent[2 * q] * s.ld + s.ent[2 * q + 1]] = src[q];
+    for (int q = threadIdx.x; q < s.ne; q += blockDim.x) s.Pm[q] = src[q];
     for (int i = threadIdx.x; i < s.n; i += blockDim.x) s.m[i] = src[s.ne + i];
     for (int p = threadIdx.x; p <= s.P; p += blockDim.x) s.sg[p] = src[s.ne + s.n + p];
 }
@@ -511,7 +511,6 @@ __device__ void gwb_load(const GwbSmem& s, const double* src) {
 // and mb mu-bar, that of the predicted mean; EFAC_q's term is accumulated.
 __device__ void gwb_adjoint_observation(const GwbSmem& s, const GwbRec& rk) {
     const int n = s.n, q = rk.q, i0 = 3 * q;
-    const int ld = s.ld;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     double* gw = s.gw;
     if (tid == 0) {
@@ -519,11 +518,17 @@ __device__ void gwb_adjoint_observation(const GwbSmem& s, const GwbRec& rk) {
         const double rS = rcp_nr(S);
         gw[kGwS] = S; gw[kGwRS] = rS; gw[kGwG] = gw[kGwE] * rS;
     }
-    // v = Pb c, one thread per entry reading Pb's column (Pb is kept exactly
-    // symmetric, and a column is conflict-free in shared memory)
+    // v = Pb c, one thread per entry: row j of the symmetric Pb is its packed
+    // column above the diagonal, then its packed row (k in order either way)
     for (int j = tid; j < n; j += blockDim.x) {
         double acc = 0.0;
-        for (int k = 0; k < n; ++k) acc = fma(s.Pb[k * ld + j], s.c[k], acc);
+        int idx = j;                      // packed (0, j)
+        for (int k = 0; k < j; ++k) {
+            acc = fma(s.Pb[idx], s.c[k], acc);
+            idx += n - k - 1;             // packed (k + 1, j)
+        }
+        const double* Rj = prow(s.Pb, n, j);
+        for (int k = j; k < n; ++k) acc = fma(Rj[k], s.c[k], acc);
         s.v[j] = acc;
     }
     __syncthreads();
@@ -547,11 +552,11 @@ __device__ void gwb_adjoint_observation(const GwbSmem& s, const GwbRec& rk) {
         for (int j = tid; j < n; j += blockDim.x) {
             const double cb = fma(s.mb[j], g, -2.0 * rS * s.v[j]);
             if (j == i0) {
-                s.Pb[j * ld + j] += cb + Sb;
+                s.Pb[pk(n, j, j)] += cb + Sb;
                 s.mb[j] -= eb;
-            } else {
-                s.Pb[j * ld + i0] = fma(0.5, cb, s.Pb[j * ld + i0]);
-                s.Pb[i0 * ld + j] = fma(0.5, cb, s.Pb[i0 * ld + j]);
+            } else {   // the one stored entry of the symmetric pair (j, i), (i, j)
+                double& e = s.Pb[j < i0 ? pk(n, j, i0) : pk(n, i0, j)];
+                e = fma(0.5, cb, e);
             }
         }
     }
@@ -562,7 +567,6 @@ __device__ void gwb_adjoint_observation(const GwbSmem& s, const GwbRec& rk) {
 // mb hold the adjoints of the state after the step; on exit, before it.
 __device__ void gwb_step_adjoint(const GwbSmem& s, const GwbArgs& a, const GwbRec& rk) {
     const int P = s.P, n = s.n, q = rk.q, i0 = 3 * q;
-    const int ld = s.ld;
     const int tid = threadIdx.x;
     const double dt = rk.dt;
     const bool pred = dt > 0.0;
@@ -574,7 +578,7 @@ __device__ void gwb_step_adjoint(const GwbSmem& s, const GwbArgs& a, const GwbRe
     // u = P (F^T e_i), and mu_i = (F m)_i
     const double bq = pred ? s.co[kCo * q + 1] : 0.0, ba = pred ? gw[1] : 0.0;
     for (int j = tid; j < n; j += blockDim.x)
-        s.u[j] = fma(bq, psym(s.Pm, ld, j, i0 + 1), fma(ba, psym(s.Pm, ld, j, i0 + 2), psym(s.Pm, ld, j, i0)));
+        s.u[j] = fma(bq, psym(s.Pm, n, j, i0 + 1), fma(ba, psym(s.Pm, n, j, i0 + 2), psym(s.Pm, n, j, i0)));
     __syncthreads();
     // c = F u + Q e_i (the predicted covariance's column i)
     const double ha2 = gw[kGwHa2];
@@ -614,25 +618,25 @@ __device__ void gwb_step_adjoint(const GwbSmem& s, const GwbArgs& a, const GwbRe
     for (int it = tid; it < P * nch; it += blockDim.x) {
         const int I = it / nch, ch = it - I * nch;
         const int rI = 3 * I, yI = rI + 1, aI = rI + 2;
-        const double* Mr = s.Pb + rI * ld;
-        const double* My = s.Pb + yI * ld;
-        const double* Ma = s.Pb + aI * ld;
+        auto Mr = [&](int j) { return psym(s.Pb, n, rI, j); };   // row rho_I of M-bar
+        auto My = [&](int j) { return psym(s.Pb, n, yI, j); };
+        auto Ma = [&](int j) { return psym(s.Pb, n, aI, j); };
         double s1 = 0.0, s2 = 0.0, s3 = 0.0, s4 = 0.0, h = 0.0, gd = 0.0;
         const int j_hi = min(P, (ch + 1) * jc);
         for (int J = ch * jc; J < j_hi; ++J) {
             const int rJ = 3 * J;
             const double aJ = s.co[kCo * J], bJ = s.co[kCo * J + 1];
-            const double py0 = psym(s.Pm, ld, rJ, yI), py1 = psym(s.Pm, ld, rJ + 1, yI), py2 = psym(s.Pm, ld, rJ + 2, yI);
-            const double pa0 = psym(s.Pm, ld, rJ, aI), pa1 = psym(s.Pm, ld, rJ + 1, aI), pa2 = psym(s.Pm, ld, rJ + 2, aI);
+            const double py0 = psym(s.Pm, n, rJ, yI), py1 = psym(s.Pm, n, rJ + 1, yI), py2 = psym(s.Pm, n, rJ + 2, yI);
+            const double pa0 = psym(s.Pm, n, rJ, aI), pa1 = psym(s.Pm, n, rJ + 1, aI), pa2 = psym(s.Pm, n, rJ + 2, aI);
             // (F P)[k, y_I] and (F P)[k, a_I] for k = rho_J, y_J, a_J
             const double fy0 = fma(bJ, py1, fma(ba, py2, py0)), fy1 = aJ * py1, fy2 = aa * py2;
             const double fa0 = fma(bJ, pa1, fma(ba, pa2, pa0)), fa1 = aJ * pa1, fa2 = aa * pa2;
-            s1 = fma(Mr[rJ], fy0, fma(Mr[rJ + 1], fy1, fma(Mr[rJ + 2], fy2, s1)));
-            s2 = fma(My[rJ], fy0, fma(My[rJ + 1], fy1, fma(My[rJ + 2], fy2, s2)));
-            s3 = fma(Mr[rJ], fa0, fma(Mr[rJ + 1], fa1, fma(Mr[rJ + 2], fa2, s3)));
-            s4 = fma(Ma[rJ], fa0, fma(Ma[rJ + 1], fa1, fma(Ma[rJ + 2], fa2, s4)));
+            s1 = fma(Mr(rJ), fy0, fma(Mr(rJ + 1), fy1, fma(Mr(rJ + 2), fy2, s1)));
+            s2 = fma(My(rJ), fy0, fma(My(rJ + 1), fy1, fma(My(rJ + 2), fy2, s2)));
+            s3 = fma(Mr(rJ), fa0, fma(Mr(rJ + 1), fa1, fma(Mr(rJ + 2), fa2, s3)));
+            s4 = fma(Ma(rJ), fa0, fma(Ma(rJ + 1), fa1, fma(Ma(rJ + 2), fa2, s4)));
             const double g = gwb_G(s, I, J);
-            const double X00 = Mr[rJ], X02 = Mr[rJ + 2], X20 = Ma[rJ], X22 = Ma[rJ + 2];
+            const double X00 = Mr(rJ), X02 = Mr(rJ + 2), X20 = Ma(rJ), X22 = Ma(rJ + 2);
             h = fma(g, fma(X00, gw[2], fma(X02 + X20, gw[3], X22 * gw[4])), h);
             gd = fma(g, fma(X00, dca00, fma(X02 + X20, dca01, X22 * dca11)), gd);
         }
@@ -652,7 +656,7 @@ __device__ void gwb_step_adjoint(const GwbSmem& s, const GwbArgs& a, const GwbRe
         const double abar_p = fma(2.0, s2, s.mb[yI] * s.m[yI]);
         const double bbar_a = fma(2.0, s3, s.mb[rI] * s.m[aI]);
         const double abar_a = fma(2.0, s4, s.mb[aI] * s.m[aI]);
-        const double M00 = s.Pb[rI * ld + rI], M01 = s.Pb[rI * ld + yI], M11 = s.Pb[yI * ld + yI];
+        const double M00 = s.Pb[pk(n, rI, rI)], M01 = s.Pb[pk(n, rI, yI)], M11 = s.Pb[pk(n, yI, yI)];
         const double s2p = s.par[4 * I];
         double* acc = s.acc + 5 * I;
         acc[0] += fma(M00, co[2], fma(2.0 * M01, co[3], M11 * co[4]));
@@ -662,13 +666,14 @@ __device__ void gwb_step_adjoint(const GwbSmem& s, const GwbArgs& a, const GwbRe
         acc[4] += fma(-dt * aa, abar_a, fma(bbar_a, dba, ha2 * gd));
     }
     __syncthreads();
-    // Pb <- F^T Pb F (upper blocks, mirrored) and mb <- F^T mb
+    // Pb <- F^T Pb F (upper blocks) and mb <- F^T mb
     for (int qq = tid; qq < s.nb; qq += blockDim.x) {
         const int I = s.pairs[2 * qq], J = s.pairs[2 * qq + 1];
         const double aI = s.co[kCo * I], bI = s.co[kCo * I + 1], aJ = s.co[kCo * J], bJ = s.co[kCo * J + 1];
         double X[3][3];
         for (int u = 0; u < 3; ++u)
-            for (int v = 0; v < 3; ++v) X[u][v] = s.Pb[(3 * I + u) * ld + 3 * J + v];
+            for (int v = 0; v < 3; ++v)
+                X[u][v] = (I < J || u <= v) ? s.Pb[pk(n, 3 * I + u, 3 * J + v)] : s.Pb[pk(n, 3 * I + v, 3 * J + u)];
         double Y[3][3];   // F_I^T X
         for (int v = 0; v < 3; ++v) {
             Y[0][v] = X[0][v];
@@ -679,12 +684,10 @@ __device__ void gwb_step_adjoint(const GwbSmem& s, const GwbArgs& a, const GwbRe
             const double z0 = Y[u][0];
             const double z1 = fma(bJ, Y[u][0], aJ * Y[u][1]);
             const double z2 = fma(ba, Y[u][0], aa * Y[u][2]);
-            s.Pb[(3 * I + u) * ld + 3 * J] = z0;
-            s.Pb[(3 * I + u) * ld + 3 * J + 1] = z1;
-            s.Pb[(3 * I + u) * ld + 3 * J + 2] = z2;
-            s.Pb[(3 * J) * ld + 3 * I + u] = z0;
-            s.Pb[(3 * J + 1) * ld + 3 * I + u] = z1;
-            s.Pb[(3 * J + 2) * ld + 3 * I + u] = z2;
+            double* R = prow(s.Pb, n, 3 * I + u) + 3 * J;   // a diagonal block keeps v >= u
+            if (I < J || u == 0) R[0] = z0;
+            if (I < J || u <= 1) R[1] = z1;
+            R[2] = z2;
         }
     }
     for (int J = tid; J < P; J += blockDim.x) {
@@ -709,7 +712,6 @@ __device__ void gwb_step_adjoint(const GwbSmem& s, const GwbArgs& a, const GwbRe
 // shares (pulsar I's terms), so every sum over pulsars stays in fixed order.
 __device__ void gwb_step_adjoint_scaled(const GwbSmem& s, const GwbArgs& a, const GwbRec& rk) {
     const int P = s.P, n = s.n, q = rk.q, i0 = 3 * q;
-    const int ld = s.ld;
     const int tid = threadIdx.x;
     const double dt = rk.dt;
     const bool pred = dt > 0.0;
@@ -722,7 +724,7 @@ __device__ void gwb_step_adjoint_scaled(const GwbSmem& s, const GwbArgs& a, cons
     const double bq = pred ? s.cs[5 * q] : 0.0, al = pred ? ca[0] : 0.0;
     // u = Ph (Fh^T e_i); c = Fh u + Qh e_i, the predicted column i
     for (int j = tid; j < n; j += blockDim.x)
-        s.u[j] = fma(bq, psym(s.Pm, ld, j, i0 + 1), fma(al, psym(s.Pm, ld, j, i0 + 2), psym(s.Pm, ld, j, i0)));
+        s.u[j] = fma(bq, psym(s.Pm, n, j, i0 + 1), fma(al, psym(s.Pm, n, j, i0 + 2), psym(s.Pm, n, j, i0)));
     __syncthreads();
     for (int J = tid; J < P; J += blockDim.x) {
         const double* uJ = s.u + 3 * J;
@@ -754,22 +756,22 @@ __device__ void gwb_step_adjoint_scaled(const GwbSmem& s, const GwbArgs& a, cons
     for (int it = tid; it < P * nch; it += blockDim.x) {
         const int I = it / nch, ch = it - I * nch;
         const int rI = 3 * I, yI = rI + 1, aI = rI + 2;
-        const double* Mr = s.Pb + rI * ld;
-        const double* Ma = s.Pb + aI * ld;
+        auto Mr = [&](int j) { return psym(s.Pb, n, rI, j); };   // row rho_I of M-bar
+        auto Ma = [&](int j) { return psym(s.Pb, n, aI, j); };
         double sB = 0.0, sA = 0.0, t1 = 0.0, t2 = 0.0, t3 = 0.0;
         const int j_hi = min(P, (ch + 1) * jc);
         for (int J = ch * jc; J < j_hi; ++J) {
             const int rJ = 3 * J;
             const double bJ = s.cs[5 * J];
-            const double py0 = psym(s.Pm, ld, rJ, yI), py1 = psym(s.Pm, ld, rJ + 1, yI), py2 = psym(s.Pm, ld, rJ + 2, yI);
-            const double pa0 = psym(s.Pm, ld, rJ, aI), pa1 = psym(s.Pm, ld, rJ + 1, aI), pa2 = psym(s.Pm, ld, rJ + 2, aI);
-            const double m0 = Mr[rJ], m1 = Mr[rJ + 1], m2 = Mr[rJ + 2];
+            const double py0 = psym(s.Pm, n, rJ, yI), py1 = psym(s.Pm, n, rJ + 1, yI), py2 = psym(s.Pm, n, rJ + 2, yI);
+            const double pa0 = psym(s.Pm, n, rJ, aI), pa1 = psym(s.Pm, n, rJ + 1, aI), pa2 = psym(s.Pm, n, rJ + 2, aI);
+            const double m0 = Mr(rJ), m1 = Mr(rJ + 1), m2 = Mr(rJ + 2);
             sB = fma(m0, fma(bJ, py1, fma(al, py2, py0)), fma(m1, py1, fma(m2, py2, sB)));
             sA = fma(m0, fma(bJ, pa1, fma(al, pa2, pa0)), fma(m1, pa1, fma(m2, pa2, sA)));
             const double g = gwb_G(s, I, J);
             t1 = fma(g, m0, t1);
-            t2 = fma(g, m2 + Ma[rJ], t2);
-            t3 = fma(g, Ma[rJ + 2], t3);
+            t2 = fma(g, m2 + Ma(rJ), t2);
+            t3 = fma(g, Ma(rJ + 2), t3);
         }
         double* pt = s.part + 6 * it;
         pt[0] = sB; pt[1] = sA; pt[2] = t1; pt[3] = t2; pt[4] = t3;
@@ -788,7 +790,7 @@ __device__ void gwb_step_adjoint_scaled(const GwbSmem& s, const GwbArgs& a, cons
         const double w = cI[4], sgI = s.sg[I], s2p = s.par[4 * I];
         const double bhb = fma(2.0, sB, s.mb[rI] * s.m[yI]);     // adjoint of b_I s_I
         const double alb = fma(2.0, sA, s.mb[rI] * s.m[aI]);     // pulsar I's share of that of b_a s_a
-        const double M00 = s.Pb[rI * ld + rI], q1b = 2.0 * s.Pb[rI * ld + yI], M11 = s.Pb[yI * ld + yI];
+        const double M00 = s.Pb[pk(n, rI, rI)], q1b = 2.0 * s.Pb[pk(n, rI, yI)], M11 = s.Pb[pk(n, yI, yI)];
         // intrinsic noise v c00, v c01 / s', v c11 / s'^2 and the scale s'_I
         const double sbt = s.sgb[I] - w * fma(q1b, cI[2], 2.0 * M11 * cI[3]);
         double* acc = s.acc + 5 * I;
@@ -804,7 +806,7 @@ __device__ void gwb_step_adjoint_scaled(const GwbSmem& s, const GwbArgs& a, cons
         s.sgb[P + I] = fma(sbat, gw[0], alb * gw[1]);
     }
     __syncthreads();
-    // Pb <- Fh^T Pb Fh (upper blocks, mirrored) and mb <- Fh^T mb
+    // Pb <- Fh^T Pb Fh (upper blocks) and mb <- Fh^T mb
     for (int qq = tid; qq < s.nb; qq += blockDim.x) {
         const int I = s.pairs[2 * qq], J = s.pairs[2 * qq + 1];
         const double bI = s.cs[5 * I], bJ = s.cs[5 * J];
@@ -812,7 +814,8 @@ __device__ void gwb_step_adjoint_scaled(const GwbSmem& s, const GwbArgs& a, cons
 #pragma unroll
         for (int u = 0; u < 3; ++u)
 #pragma unroll
-            for (int v = 0; v < 3; ++v) X[u][v] = s.Pb[(3 * I + u) * ld + 3 * J + v];
+            for (int v = 0; v < 3; ++v)
+                X[u][v] = (I < J || u <= v) ? s.Pb[pk(n, 3 * I + u, 3 * J + v)] : s.Pb[pk(n, 3 * I + v, 3 * J + u)];
 #pragma unroll
         for (int v = 0; v < 3; ++v) {   // Fh_I^T X: rows y, a gain b_I s_I, b_a s_a times row rho
             X[1][v] = fma(bI, X[0][v], X[1][v]);
@@ -823,12 +826,10 @@ __device__ void gwb_step_adjoint_scaled(const GwbSmem& s, const GwbArgs& a, cons
             const double z0 = X[u][0];
             const double z1 = fma(bJ, z0, X[u][1]);
             const double z2 = fma(al, z0, X[u][2]);
-            s.Pb[(3 * I + u) * ld + 3 * J] = z0;
-            s.Pb[(3 * I + u) * ld + 3 * J + 1] = z1;
-            s.Pb[(3 * I + u) * ld + 3 * J + 2] = z2;
-            s.Pb[(3 * J) * ld + 3 * I + u] = z0;
-            s.Pb[(3 * J + 1) * ld + 3 * I + u] = z1;
-            s.Pb[(3 * J + 2) * ld + 3 * I + u] = z2;
+            double* R = prow(s.Pb, n, 3 * I + u) + 3 * J;   // a diagonal block keeps v >= u
+            if (I < J || u == 0) R[0] = z0;
+            if (I < J || u <= 1) R[1] = z1;
+            R[2] = z2;
         }
     }
     for (int J = tid; J < P; J += blockDim.x) {
@@ -840,11 +841,10 @@ __device__ void gwb_step_adjoint_scaled(const GwbSmem& s, const GwbArgs& a, cons
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(kGwbThreads, 3) k_gwb_grad(GwbArgs a) {
+__global__ void __launch_bounds__(kGwbThreads, 4) k_gwb_grad(GwbArgs a) {
     extern __shared__ __align__(16) double gsm[];
     const GwbSmem s = gwb_carve(gsm, a.P, true, a.G);
     const int P = s.P, n = s.n, D = 2 + 3 * P;
-    const int ld = s.ld;
     const int64_t rec_len = gwb_rec_len(P);
     double* ck = a.ckpt + int64_t(blockIdx.x) * a.slot;
     double* tp = a.tape + int64_t(blockIdx.x) * a.slot;
@@ -884,7 +884,7 @@ __global__ void __launch_bounds__(kGwbThreads, 3) k_gwb_grad(GwbArgs a) {
             a.loglik[b] = ll;
             s.gw[kGwOk] = isfinite(ll) ? 1.0 : 0.0;
         }
-        for (int i = threadIdx.x; i < n * s.ld; i += blockDim.x) s.Pb[i] = 0.0;
+        for (int i = threadIdx.x; i < s.ne; i += blockDim.x) s.Pb[i] = 0.0;
         for (int i = threadIdx.x; i < n; i += blockDim.x) s.mb[i] = 0.0;
         for (int i = threadIdx.x; i < 5 * P; i += blockDim.x) s.acc[i] = 0.0;
         for (int i = threadIdx.x; i < 2 * P; i += blockDim.x) s.sgb[i] = 0.0;
@@ -916,7 +916,7 @@ __global__ void __launch_bounds__(kGwbThreads, 3) k_gwb_grad(GwbArgs a) {
         const double ha2 = s.gw[kGwHa2], ga = s.gw[kGwGa];
         for (int I = threadIdx.x; I < P; I += blockDim.x) {
             double h = 0.0;
-            for (int J = 0; J < P; ++J) h = fma(s.Pb[(3 * I + 2) * ld + 3 * J + 2], gwb_G(s, I, J), h);
+            for (int J = 0; J < P; ++J) h = fma(psym(s.Pb, n, 3 * I + 2, 3 * J + 2), gwb_G(s, I, J), h);
             s.acc[5 * I + 3] += h / (2.0 * ga);
             s.acc[5 * I + 4] -= h * ha2 / (2.0 * ga * ga);
         }
@@ -999,7 +999,7 @@ argus_status argus_gwb_create(const argus_pulsar* psrs, int32_t n_pulsars, int32
     if (!out) return argus_status(gwb_fail(ARGUS_ERR_INVALID_ARG, "out is NULL"));
     if (!psrs || n_pulsars < 1) return argus_status(gwb_fail(ARGUS_ERR_INVALID_ARG, "need at least one pulsar"));
     if (n_pulsars > kGwbMaxPulsars)
-        return argus_status(gwb_fail(ARGUS_ERR_UNSUPPORTED, "the joint filter holds at most 48 pulsars"));
+        return argus_status(gwb_fail(ARGUS_ERR_UNSUPPORTED, "the joint filter holds at most 64 pulsars"));
     if (device < 0) return argus_status(gwb_fail(ARGUS_ERR_INVALID_ARG, "device must be >= 0"));
     int64_t total = 0;
     if (int st = validate_pulsars(psrs, n_pulsars, &total)) return argus_status(st);
@@ -1168,7 +1168,7 @@ argus_status argus_gwb_loglik_grad(argus_gwb* h, const double* theta, int64_t B,
     if (!theta || !loglik || !grad)
         return argus_status(gwb_fail(ARGUS_ERR_INVALID_ARG, "theta, loglik or grad is NULL"));
     if (h->P > kGwbGradMaxPulsars)
-        return argus_status(gwb_fail(ARGUS_ERR_UNSUPPORTED, "the joint filter's gradient holds at most 32 pulsars"));
+        return argus_status(gwb_fail(ARGUS_ERR_UNSUPPORTED, "the joint filter's gradient holds at most 48 pulsars"));
     int prev = -1;
     cudaGetDevice(&prev);
     cudaSetDevice(h->device);

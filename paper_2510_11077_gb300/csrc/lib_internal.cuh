@@ -18,6 +18,6 @@ int validate_pulsars(const argus_pulsar* psrs, int32_t n_pulsars, int64_t* total
 
 // Joint filter with a Hellings-Downs correlated GW background (gwb.cu):
 // pulsars at most kGwbMaxPulsars (the 3P x 3P covariance lives in shared memory).
-constexpr int kGwbMaxPulsars = 48;
+constexpr int kGwbMaxPulsars = 64;
 
 }  // namespace argus

@@ -106,11 +106,11 @@ def test_model_flags_of_array_data():
 
 
 def test_gwb_create_rejects_too_many_pulsars_and_bad_data(lib):
-    data = inputs.make_array(np.full(49, 3), seed=2)
+    data = inputs.make_array(np.full(65, 3), seed=2)
     ps, keep = _pulsars(data)
     h = ctypes.c_void_p()
-    assert lib.argus_gwb_create(ps, 49, 0, ctypes.byref(h)) == 6 and h.value is None
-    assert b"48" in lib.argus_last_error()
+    assert lib.argus_gwb_create(ps, 65, 0, ctypes.byref(h)) == 6 and h.value is None
+    assert b"64" in lib.argus_last_error()
     data = inputs.make_array(np.array([10, 10]), seed=3)
     data.sigma[4] = -1.0
     ps, keep = _pulsars(data)

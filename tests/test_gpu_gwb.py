@@ -77,10 +77,40 @@ def test_twenty_pulsars(argus):
 
 
 def test_largest_supported_array(argus):
-    data = inputs.make_array(np.full(48, 6), seed=503)
-    theta = thetas(48, 3, np.random.default_rng(4))
+    """64 pulsars: the 192-dimensional joint covariance, packed, in shared memory."""
+    data = inputs.make_array(np.full(64, 5), seed=503)
+    theta = thetas(64, 3, np.random.default_rng(4))
     arr = argus.GwbArray(data)
     assert ll_err(run(argus, arr, theta), gwb.loglik(data, theta)) <= LL_TOL
+
+
+def test_gradient_of_the_largest_supported_array(argus):
+    """48 pulsars, the gradient's limit (covariance and adjoint both packed in
+    shared memory); 49 are refused."""
+    data = inputs.make_array(np.full(48, 4), seed=515)
+    th0 = thetas(48, 1, np.random.default_rng(16), lh=(-19.2, -18.6))[0]
+    arr = argus.GwbArray(data)
+    ll, g = argus.argus_gwb_loglik_grad(arr, torch.from_numpy(th0[None, :]).cuda())
+    ll, g = ll.cpu().numpy(), g.cpu().numpy()[0]
+    assert ll_err(ll, gwb.loglik(data, th0[None, :])) <= LL_TOL
+    assert ll_err(ll, run(argus, arr, th0[None, :])) <= 1e-13
+    # Richardson central differences of the GPU likelihood on the background's
+    # parameters and those of the first, a middle and the last pulsar
+    js = [0, 1] + [2 + 3 * p + k for p in (0, 23, 47) for k in range(3)]
+    rows = []
+    for j in js:
+        for h in (1e-4, 5e-5):
+            for sgn in (1, -1):
+                x = th0.copy(); x[j] += sgn * h
+                rows.append(x)
+    lf = run(argus, arr, np.array(rows))
+    fd = np.array([(4 * (lf[4 * i + 2] - lf[4 * i + 3]) / 1e-4 - (lf[4 * i] - lf[4 * i + 1]) / 2e-4) / 3
+                   for i in range(len(js))])
+    assert g_err(g[js], fd) <= 1e-5
+    big = inputs.make_array(np.full(49, 3), seed=516)
+    arr49 = argus.GwbArray(big)
+    with pytest.raises(Exception, match="48 pulsars"):
+        argus.argus_gwb_loglik_grad(arr49, torch.from_numpy(thetas(49, 1, np.random.default_rng(1))).cuda())
 
 
 def test_out_of_domain_and_host_pointers(argus):
