@@ -53,7 +53,8 @@ namespace {
 
 constexpr double kLog2PiGwb = 1.8378770664093454836;
 constexpr double kLn10Gwb = 2.302585092994045684;
-constexpr int kGwbThreads = 256;
+constexpr int kGwbThreads = 256;      // gradient kernel
+constexpr int kGwbFwdThreads = 128;   // likelihood kernel: 8 blocks of 4 warps per SM
 constexpr int kGwbGradMaxPulsars = 48;   // gradient: two packed 3P x 3P triangles in shared memory
 constexpr int kCo = 9;                   // per-pulsar coefficients (see GwbSmem::co)
 
@@ -474,7 +475,7 @@ __device__ __forceinline__ double gwb_finish(int64_t N, double quad, const LogPr
     return (lp.bad || !isfinite(ll)) ? -INFINITY : ll;
 }
 
-__global__ void __launch_bounds__(kGwbThreads) k_gwb_filter(GwbArgs a) {
+__global__ void __launch_bounds__(kGwbFwdThreads) k_gwb_filter(GwbArgs a) {
     extern __shared__ __align__(16) double gsm[];
     const GwbSmem s = gwb_carve(gsm, a.P, false, a.G);
     gwb_tables(s, a);
@@ -1140,7 +1141,7 @@ argus_status argus_gwb_loglik(argus_gwb* h, const double* theta, int64_t B, doub
         a.theta = th_d; a.B = B; a.loglik = ll_d;
         const size_t smem = gwb_smem_bytes(h->P, false);
         const int grid = int(std::min<int64_t>(B, int64_t(h->n_sm) * 8));
-        k_gwb_filter<<<grid, kGwbThreads, smem, s>>>(a);
+        k_gwb_filter<<<grid, kGwbFwdThreads, smem, s>>>(a);
         if ((e = cudaGetLastError()) != cudaSuccess) {
             st = argus_status(gwb_cuda(e, "k_gwb_filter"));
             goto done;
