@@ -80,6 +80,17 @@ argus_status argus_surrogate_get_weights(argus_surrogate* s, float* params);
 argus_status argus_surrogate_eval(argus_surrogate* s, const float* theta, int64_t B, float* loglik,
                                   float* grad, void* stream);
 
+/* argus_surrogate_eval in a sampler's FP64 coordinates, with no conversion
+ * kernels around it: the network's input row is float(z[b] - centre) (z
+ * [B][47], centre [47], FP64), loglik[b] = (double) surrogate loglik + offset
+ * (-inf when not finite), grad [B][47] FP64 = the surrogate gradient
+ * converted to double, or NULL.  Device pointers.  Always the fused kernel;
+ * the same rounding as argus_surrogate_eval on float(z - centre) followed by
+ * the conversions. */
+argus_status argus_surrogate_eval_f64(argus_surrogate* s, const double* z, const double* centre,
+                                      double offset, int64_t B, double* loglik, double* grad,
+                                      void* stream);
+
 /* Selects how argus_surrogate_eval runs: on = 1 (default) the fused kernel,
  * on = 0 one tensor-core GEMM launch per layer (the kernels training uses).
  * For comparison and measurement; both compute the same network. */

@@ -368,6 +368,25 @@ __device__ __forceinline__ void fence_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
+// input k of row gr: theta, or float(z - centre) in the FP64-input mode
+__device__ __forceinline__ float fused_in(const MlpFusedArgs& a, int64_t gr, int k) {
+    return a.z64 ? float(a.z64[gr * kMlpIn + k] - a.zc[k]) : a.theta[gr * kMlpIn + k];
+}
+
+// the outputs of row gr: the loglik and, when the mode has one, gradient k
+__device__ __forceinline__ void fused_out_ll(const MlpFusedArgs& a, int64_t gr, float ll) {
+    if (a.z64) {
+        const double v = double(ll) + a.off;
+        a.ll64[gr] = isfinite(v) ? v : -INFINITY;
+    } else {
+        a.loglik[gr] = ll;
+    }
+}
+__device__ __forceinline__ void fused_out_grad(const MlpFusedArgs& a, int64_t gr, int k, float g) {
+    if (a.z64) a.g64[gr * kMlpIn + k] = double(g);
+    else a.grad[gr * kMlpIn + k] = g;
+}
+
 // 32 saved gelu'(z) of one row (8 float4), issued early so that their latency
 // overlaps other work
 __device__ __forceinline__ void load_g32(const float* g, float4 (&o)[8]) {
@@ -440,7 +459,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_mlp_fused(const __grid_con
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
                 const int k = c0 + j;
-                d[j] = (valid && k < kMlpIn) ? (a.theta[gr * kMlpIn + k] - a.xm[k]) / a.xs[k] : 0.0f;
+                d[j] = (valid && k < kMlpIn) ? (fused_in(a, gr, k) - a.xm[k]) / a.xs[k] : 0.0f;
             }
             store_act16(sA, r, c0, d);
         }
@@ -449,7 +468,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_mlp_fused(const __grid_con
         // at a time (independent sums, each in the order j = 0..46)
         float u[kMlpIn];
 #pragma unroll
-        for (int j = 0; j < kMlpIn; ++j) u[j] = a.theta[gr * kMlpIn + j];
+        for (int j = 0; j < kMlpIn; ++j) u[j] = fused_in(a, gr, j);
         float qd = 0.0f;
 #pragma unroll 1
         for (int i0 = 0; i0 < kMlpIn; i0 += 4) {
@@ -464,7 +483,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_mlp_fused(const __grid_con
             for (int t = 0; t < 4; ++t) {
                 if (i0 + t >= kMlpIn) break;
                 gbase_s[r * kMlpIn + i0 + t] = -hu[t];
-                qd = fmaf(a.theta[gr * kMlpIn + i0 + t], hu[t], qd);
+                qd = fmaf(fused_in(a, gr, i0 + t), hu[t], qd);
             }
         }
         base_s[r] = -0.5f * qd;
@@ -540,14 +559,14 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_mlp_fused(const __grid_con
                     const float y0 = v[0] + b4[0];
                     y0_s[r] = y0;
                     if (a.mode != kFusedValueGrad)
-                        a.loglik[gr] = y0 * a.ys + a.ym + (a.Hq ? base_s[r] : 0.0f);
+                        fused_out_ll(a, gr, y0 * a.ys + a.ym + (a.Hq ? base_s[r] : 0.0f));
                     if (a.mode == kFusedGradHead) {
                         // output 1 + k is d ll / d x_k
 #pragma unroll
                         for (int c = 1; c < 48; ++c) {
                             const float yk = (c < 32 ? v[c] : v2[c - 32]) + b4[c];
                             const int k = c - 1;
-                            a.grad[gr * kMlpIn + k] = yk * a.ys / a.xs[k] + (a.Hq ? gbase_s[r * kMlpIn + k] : 0.0f);
+                            fused_out_grad(a, gr, k, yk * a.ys / a.xs[k] + (a.Hq ? gbase_s[r * kMlpIn + k] : 0.0f));
                         }
                     }
                 }
@@ -589,9 +608,9 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_mlp_fused(const __grid_con
 #pragma unroll
                 for (int k = 0; k < kMlpIn; ++k) {
                     const float dx = (k < 32 ? v[k] : v2[k - 32]) + 0.0f;
-                    a.grad[gr * kMlpIn + k] = dx * a.ys / a.xs[k] + (a.Hq ? gbase_s[r * kMlpIn + k] : 0.0f);
+                    fused_out_grad(a, gr, k, dx * a.ys / a.xs[k] + (a.Hq ? gbase_s[r * kMlpIn + k] : 0.0f));
                 }
-                a.loglik[gr] = y0_s[r] * a.ys + a.ym + (a.Hq ? base_s[r] : 0.0f);
+                fused_out_ll(a, gr, y0_s[r] * a.ys + a.ym + (a.Hq ? base_s[r] : 0.0f));
             }
         }
         fence_async_smem();
@@ -628,8 +647,10 @@ cudaError_t launch_gemm_tc(const CUtensorMap* ta, const CUtensorMap* tb, int M, 
 
 
 cudaError_t launch_mlp_fused(const MlpFusedMaps& maps, const MlpFusedArgs& a, cudaStream_t s) {
-    if (a.n <= 0 || a.mode < kFusedValue || a.mode > kFusedGradHead || !a.theta || !a.loglik ||
-        (a.mode != kFusedValue && !a.grad))
+    const bool f64 = a.z64 != nullptr;
+    if (a.n <= 0 || a.mode < kFusedValue || a.mode > kFusedGradHead ||
+        (f64 ? (!a.zc || !a.ll64 || (a.mode != kFusedValue && !a.g64))
+             : (!a.theta || !a.loglik || (a.mode != kFusedValue && !a.grad))))
         return cudaErrorInvalidValue;
     static bool configured[64] = {};
     int dev = 0;

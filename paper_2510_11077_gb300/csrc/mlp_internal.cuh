@@ -70,6 +70,14 @@ struct MlpFusedArgs {
     float* grad;                      // [n][47] or nullptr (kFusedValue)
     int mode;
     int* err;
+    // FP64 input/output (z64 non-null): the network's input row is
+    // float(z64[r] - zc), and loglik / grad go to ll64 / g64 as doubles, the
+    // loglik plus off and -inf when not finite; theta, loglik, grad unused
+    const double* z64;
+    const double* zc;
+    double off;
+    double* ll64;
+    double* g64;
 };
 
 cudaError_t launch_mlp_fused(const MlpFusedMaps& maps, const MlpFusedArgs& a, cudaStream_t s);

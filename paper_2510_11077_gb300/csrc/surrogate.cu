@@ -366,6 +366,21 @@ argus_status cast_weights(argus_surrogate* s, cudaStream_t st) {
     return ARGUS_OK;
 }
 
+// The fused kernel's arguments that come from the handle (rows and I/O are the caller's).
+MlpFusedArgs fused_args(const argus_surrogate* s, bool with_grad) {
+    MlpFusedArgs fa{};
+    for (int k = 0; k < kMlpInPad; ++k) { fa.xm[k] = s->norm.xm[k]; fa.xs[k] = s->norm.xs[k]; }
+    fa.ym = s->norm.ym;
+    fa.ys = s->norm.ys;
+    for (int l = 0; l < kMlpLayers; ++l) fa.bias[l] = s->b[l];
+    for (int l = 0; l < kMlpLayers - 1; ++l) fa.gscr[l] = s->Z[l + 1];
+    fa.w4 = s->W16[kMlpLayers - 1];
+    fa.Hq = s->has_baseline ? s->Hq : nullptr;
+    fa.mode = !with_grad ? kFusedValue : (s->grad_mode == 1 ? kFusedValueGrad : kFusedGradHead);
+    fa.err = s->err;
+    return fa;
+}
+
 GemmEpiArgs epi_none() {
     GemmEpiArgs e{};
     return e;
@@ -644,16 +659,7 @@ argus_status argus_surrogate_eval(argus_surrogate* s, const float* theta, int64_
     if (s->fused) {
         // one launch per max_rows rows: every layer (and the value output's
         // back-propagation) in one kernel; Z[1..4] hold gelu'(z) as scratch
-        MlpFusedArgs fa{};
-        for (int k = 0; k < kMlpInPad; ++k) { fa.xm[k] = s->norm.xm[k]; fa.xs[k] = s->norm.xs[k]; }
-        fa.ym = s->norm.ym;
-        fa.ys = s->norm.ys;
-        for (int l = 0; l < kMlpLayers; ++l) fa.bias[l] = s->b[l];
-        for (int l = 0; l < kMlpLayers - 1; ++l) fa.gscr[l] = s->Z[l + 1];
-        fa.w4 = s->W16[kMlpLayers - 1];
-        fa.Hq = s->has_baseline ? s->Hq : nullptr;
-        fa.mode = !grad ? kFusedValue : (s->grad_mode == 1 ? kFusedValueGrad : kFusedGradHead);
-        fa.err = s->err;
+        MlpFusedArgs fa = fused_args(s, grad != nullptr);
         for (int64_t r0 = 0; r0 < B; r0 += s->rows) {
             fa.n = std::min<int64_t>(s->rows, B - r0);
             fa.theta = theta + r0 * kMlpIn;
@@ -686,6 +692,31 @@ argus_status argus_surrogate_eval(argus_surrogate* s, const float* theta, int64_
                 s->has_baseline ? s->gbase : nullptr, loglik + r0, grad + r0 * kMlpIn);
         }
         SCK(cudaGetLastError());
+    }
+    return ARGUS_OK;
+}
+
+argus_status argus_surrogate_eval_f64(argus_surrogate* s, const double* z, const double* centre,
+                                      double offset, int64_t B, double* loglik, double* grad,
+                                      void* stream) {
+    if (!s) return sfail(ARGUS_ERR_INVALID_ARG, "surrogate handle is NULL");
+    if (B < 0) return sfail(ARGUS_ERR_INVALID_ARG, "B must be >= 0");
+    if (B == 0) return ARGUS_OK;
+    if (!z || !centre || !loglik) return sfail(ARGUS_ERR_INVALID_ARG, "NULL z, centre or loglik");
+    if (!std::isfinite(offset)) return sfail(ARGUS_ERR_INVALID_ARG, "offset must be finite");
+    DeviceGuardS guard(s->device);
+    if (!dev_ptr(z) || !dev_ptr(centre) || !dev_ptr(loglik) || (grad && !dev_ptr(grad)))
+        return sfail(ARGUS_ERR_INVALID_ARG, "argus_surrogate_eval_f64 needs device pointers");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    MlpFusedArgs fa = fused_args(s, grad != nullptr);
+    fa.zc = centre;
+    fa.off = offset;
+    for (int64_t r0 = 0; r0 < B; r0 += s->rows) {
+        fa.n = std::min<int64_t>(s->rows, B - r0);
+        fa.z64 = z + r0 * kMlpIn;
+        fa.ll64 = loglik + r0;
+        fa.g64 = grad ? grad + r0 * kMlpIn : nullptr;
+        SCK(launch_mlp_fused(s->fmaps, fa, st));
     }
     return ARGUS_OK;
 }

@@ -112,11 +112,9 @@ class SurrogateTarget:
         self.ll_ref = ll_ref
 
     def logp_grad(self, z):
-        u = (z - self.centre).float().contiguous()
-        lp, g = self.net.eval(u)
-        lp = lp.double() + self.ll_ref
-        lp = torch.where(torch.isfinite(lp), lp, torch.full_like(lp, -math.inf))
-        return lp, g.double()
+        # float(z - centre) in, value + ll_ref and its gradient out, all in the
+        # fused kernel (the same rounding as converting around argus_surrogate_eval)
+        return self.net.eval_z(z, self.centre, self.ll_ref)
 
 
 def _sync():

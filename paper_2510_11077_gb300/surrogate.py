@@ -33,6 +33,7 @@ def _lib():
         lib.argus_surrogate_set_baseline.argtypes = [vp, vp]
         lib.argus_surrogate_set_grad_mode.argtypes = [vp, ctypes.c_int32]
         lib.argus_surrogate_set_fused.argtypes = [vp, ctypes.c_int32]
+        lib.argus_surrogate_eval_f64.argtypes = [vp, vp, vp, ctypes.c_double, ctypes.c_int64, vp, vp, vp]
         lib.argus_surrogate_get_weights.argtypes = [vp, vp]
         lib.argus_surrogate_eval.argtypes = [vp, vp, ctypes.c_int64, vp, vp, vp]
         lib.argus_surrogate_train_step.argtypes = [vp, vp, vp, vp, ctypes.c_int64, ctypes.c_float,
@@ -126,6 +127,24 @@ class Surrogate:
         s = stream if stream is not None else torch.cuda.current_stream(theta.device).cuda_stream
         _check(_lib().argus_surrogate_eval(self.handle, theta.data_ptr(), B, loglik.data_ptr(),
                                            grad.data_ptr() if with_grad else None, s))
+        return (loglik, grad) if with_grad else loglik
+
+    def eval_z(self, z, centre, offset=0.0, loglik=None, grad=None, with_grad=True, stream=None):
+        """Surrogate at float(z - centre), FP64 in and out (argus_surrogate_eval_f64):
+        loglik = value + offset (-inf if not finite) and its gradient."""
+        import torch
+        assert z.is_cuda and z.dtype == torch.float64 and z.shape[1] == N_IN
+        assert centre.is_cuda and centre.dtype == torch.float64 and centre.numel() == N_IN
+        z = z.contiguous()
+        centre = centre.contiguous()
+        B = z.shape[0]
+        if loglik is None:
+            loglik = torch.empty(B, dtype=torch.float64, device=z.device)
+        if with_grad and grad is None:
+            grad = torch.empty((B, N_IN), dtype=torch.float64, device=z.device)
+        s = stream if stream is not None else torch.cuda.current_stream(z.device).cuda_stream
+        _check(_lib().argus_surrogate_eval_f64(self.handle, z.data_ptr(), centre.data_ptr(), float(offset), B,
+                                               loglik.data_ptr(), grad.data_ptr() if with_grad else None, s))
         return (loglik, grad) if with_grad else loglik
 
     def train_step(self, theta, loglik, grad, lr, loss_out=None, stream=None):

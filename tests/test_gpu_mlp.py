@@ -198,3 +198,29 @@ def test_fused_eval_matches_layer_by_layer(lib, n, mode, baseline):
     again = [x.cpu().numpy() for x in (r if with_grad else (r,))]
     for a_, b_ in zip(again, out[True]):
         assert np.array_equal(a_, b_)
+
+
+@pytest.mark.parametrize("n", [1, 300, 2500])
+@pytest.mark.parametrize("grad_mode", [0, 1])
+def test_eval_f64_equals_eval_with_conversions(lib, n, grad_mode):
+    """argus_surrogate_eval_f64 does the sampler's conversions inside the fused
+    kernel: it must equal argus_surrogate_eval on float(z - centre) followed by
+    the double conversion, the offset and the -inf of a non-finite value,
+    bit for bit."""
+    s, params, theta, xm, xs, ym, ys = _setup(40 + n, n)
+    rng = np.random.default_rng(n)
+    A = rng.standard_normal((mlp.IN_DIM, mlp.IN_DIM)).astype(np.float32) / mlp.IN_DIM
+    s.set_baseline(A @ A.T + 0.1 * np.eye(mlp.IN_DIM, dtype=np.float32))
+    s.set_grad_mode(grad_mode)
+    centre = torch.from_numpy(rng.standard_normal(mlp.IN_DIM)).cuda()
+    z = torch.from_numpy(theta.astype(np.float64) + rng.standard_normal(theta.shape) * 1e-3).cuda() + centre
+    off = -1234.5678
+    ll_f, g_f = s.eval((z - centre).float().contiguous())
+    ref_ll = ll_f.double() + off
+    ref_ll = torch.where(torch.isfinite(ref_ll), ref_ll, torch.full_like(ref_ll, -np.inf))
+    for _ in range(2):
+        ll, g = s.eval_z(z, centre, off)
+        s.check()
+        assert torch.equal(ll, ref_ll) and torch.equal(g, g_f.double())
+    ll_only = s.eval_z(z, centre, off, with_grad=False)
+    assert torch.equal(ll_only, ref_ll)
