@@ -56,7 +56,15 @@ __device__ __forceinline__ SElem scan_identity() {
     return SElem{1.0, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
 }
 
-__device__ __forceinline__ SElem scan_combine(const SElem& i, const SElem& j) {
+// The combine (i) x (j), restricted to one group of the output's fields:
+// part 0 A, b; part 1 C; part 2 eta; part 3 J (field order of SElem: A00 A01
+// A10 A11 b0 b1 C00 C01 C11 e0 e1 J00 J01 J11).  Every part forms the shared
+// M^-1; scan_combine runs all four, so a split combine is bit for bit the
+// whole one.
+__host__ __device__ constexpr int part_begin(int p) { return p == 0 ? 0 : p == 1 ? 6 : p == 2 ? 9 : p == 3 ? 11 : 14; }
+
+template <int kPart>
+__device__ __forceinline__ void scan_combine_part(const SElem& i, const SElem& j, double* o) {
     // M = I + C_i J_j and X = M^-1
     const double M00 = 1.0 + fma(i.C00, j.J00, i.C01 * j.J01);
     const double M01 = fma(i.C00, j.J01, i.C01 * j.J11);
@@ -65,47 +73,55 @@ __device__ __forceinline__ SElem scan_combine(const SElem& i, const SElem& j) {
     // C_i, J_j are positive semi-definite, so det(I + C_i J_j) >= 1
     const double rdet = rcp_nr(fma(M00, M11, -M01 * M10));
     const double X00 = M11 * rdet, X01 = -M01 * rdet, X10 = -M10 * rdet, X11 = M00 * rdet;
-    // G = A_j X
-    const double G00 = fma(j.A00, X00, j.A01 * X10), G01 = fma(j.A00, X01, j.A01 * X11);
-    const double G10 = fma(j.A10, X00, j.A11 * X10), G11 = fma(j.A10, X01, j.A11 * X11);
-    SElem o;
-    o.A00 = fma(G00, i.A00, G01 * i.A10);
-    o.A01 = fma(G00, i.A01, G01 * i.A11);
-    o.A10 = fma(G10, i.A00, G11 * i.A10);
-    o.A11 = fma(G10, i.A01, G11 * i.A11);
-    const double u0 = i.b0 + fma(i.C00, j.e0, i.C01 * j.e1);
-    const double u1 = i.b1 + fma(i.C01, j.e0, i.C11 * j.e1);
-    o.b0 = fma(G00, u0, fma(G01, u1, j.b0));
-    o.b1 = fma(G10, u0, fma(G11, u1, j.b1));
-    // C = (G C_i) A_j^T + C_j
-    const double H00 = fma(G00, i.C00, G01 * i.C01), H01 = fma(G00, i.C01, G01 * i.C11);
-    const double H10 = fma(G10, i.C00, G11 * i.C01), H11 = fma(G10, i.C01, G11 * i.C11);
-    o.C00 = fma(H00, j.A00, fma(H01, j.A01, j.C00));
-    o.C01 = fma(H00, j.A10, fma(H01, j.A11, j.C01));
-    o.C11 = fma(H10, j.A10, fma(H11, j.A11, j.C11));
-    // Z = X A_i, so A_i^T M^-T = Z^T
-    const double Z00 = fma(X00, i.A00, X01 * i.A10), Z01 = fma(X00, i.A01, X01 * i.A11);
-    const double Z10 = fma(X10, i.A00, X11 * i.A10), Z11 = fma(X10, i.A01, X11 * i.A11);
-    const double v0 = j.e0 - fma(j.J00, i.b0, j.J01 * i.b1);
-    const double v1 = j.e1 - fma(j.J01, i.b0, j.J11 * i.b1);
-    o.e0 = fma(Z00, v0, fma(Z10, v1, i.e0));
-    o.e1 = fma(Z01, v0, fma(Z11, v1, i.e1));
-    // J = Z^T (J_j A_i) + J_i
-    const double W00 = fma(j.J00, i.A00, j.J01 * i.A10), W01 = fma(j.J00, i.A01, j.J01 * i.A11);
-    const double W10 = fma(j.J01, i.A00, j.J11 * i.A10), W11 = fma(j.J01, i.A01, j.J11 * i.A11);
-    o.J00 = fma(Z00, W00, fma(Z10, W10, i.J00));
-    o.J01 = fma(Z00, W01, fma(Z10, W11, i.J01));
-    o.J11 = fma(Z01, W01, fma(Z11, W11, i.J11));
-    return o;
+    if (kPart <= 1) {
+        // G = A_j X
+        const double G00 = fma(j.A00, X00, j.A01 * X10), G01 = fma(j.A00, X01, j.A01 * X11);
+        const double G10 = fma(j.A10, X00, j.A11 * X10), G11 = fma(j.A10, X01, j.A11 * X11);
+        if (kPart == 0) {
+            o[0] = fma(G00, i.A00, G01 * i.A10);
+            o[1] = fma(G00, i.A01, G01 * i.A11);
+            o[2] = fma(G10, i.A00, G11 * i.A10);
+            o[3] = fma(G10, i.A01, G11 * i.A11);
+            const double u0 = i.b0 + fma(i.C00, j.e0, i.C01 * j.e1);
+            const double u1 = i.b1 + fma(i.C01, j.e0, i.C11 * j.e1);
+            o[4] = fma(G00, u0, fma(G01, u1, j.b0));
+            o[5] = fma(G10, u0, fma(G11, u1, j.b1));
+        } else {
+            // C = (G C_i) A_j^T + C_j
+            const double H00 = fma(G00, i.C00, G01 * i.C01), H01 = fma(G00, i.C01, G01 * i.C11);
+            const double H10 = fma(G10, i.C00, G11 * i.C01), H11 = fma(G10, i.C01, G11 * i.C11);
+            o[6] = fma(H00, j.A00, fma(H01, j.A01, j.C00));
+            o[7] = fma(H00, j.A10, fma(H01, j.A11, j.C01));
+            o[8] = fma(H10, j.A10, fma(H11, j.A11, j.C11));
+        }
+    } else {
+        // Z = X A_i, so A_i^T M^-T = Z^T
+        const double Z00 = fma(X00, i.A00, X01 * i.A10), Z01 = fma(X00, i.A01, X01 * i.A11);
+        const double Z10 = fma(X10, i.A00, X11 * i.A10), Z11 = fma(X10, i.A01, X11 * i.A11);
+        if (kPart == 2) {
+            const double v0 = j.e0 - fma(j.J00, i.b0, j.J01 * i.b1);
+            const double v1 = j.e1 - fma(j.J01, i.b0, j.J11 * i.b1);
+            o[9] = fma(Z00, v0, fma(Z10, v1, i.e0));
+            o[10] = fma(Z01, v0, fma(Z11, v1, i.e1));
+        } else {
+            // J = Z^T (J_j A_i) + J_i
+            const double W00 = fma(j.J00, i.A00, j.J01 * i.A10), W01 = fma(j.J00, i.A01, j.J01 * i.A11);
+            const double W10 = fma(j.J01, i.A00, j.J11 * i.A10), W11 = fma(j.J01, i.A01, j.J11 * i.A11);
+            o[11] = fma(Z00, W00, fma(Z10, W10, i.J00));
+            o[12] = fma(Z00, W01, fma(Z10, W11, i.J01));
+            o[13] = fma(Z01, W01, fma(Z11, W11, i.J11));
+        }
+    }
 }
 
-__device__ __forceinline__ SElem shfl_up_elem(const SElem& x, int off) {
-    SElem y;
-    const double* s = &x.A00;
-    double* d = &y.A00;
-#pragma unroll
-    for (int q = 0; q < kScanElem; ++q) d[q] = __shfl_up_sync(0xffffffffu, s[q], off);
-    return y;
+__device__ __forceinline__ SElem scan_combine(const SElem& i, const SElem& j) {
+    SElem o;
+    double* p = &o.A00;
+    scan_combine_part<0>(i, j, p);
+    scan_combine_part<1>(i, j, p);
+    scan_combine_part<2>(i, j, p);
+    scan_combine_part<3>(i, j, p);
+    return o;
 }
 
 __device__ __forceinline__ void store_elem(double* dst, const SElem& x) {
@@ -119,17 +135,6 @@ __device__ __forceinline__ SElem load_elem(const double* src) {
     double* d = &x.A00;
 #pragma unroll
     for (int q = 0; q < kScanElem; ++q) d[q] = src[q];
-    return x;
-}
-
-// warp-inclusive scan (lane i ends with elements 0..i of the warp combined)
-__device__ __forceinline__ SElem warp_scan(SElem x) {
-    const int ln = threadIdx.x & 31;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        const SElem y = shfl_up_elem(x, off);
-        if (ln >= off) x = scan_combine(y, x);
-    }
     return x;
 }
 
@@ -191,42 +196,93 @@ __device__ __forceinline__ PhaseTable scan_table(const ScanArgs& a) {
     return tab;
 }
 
+// Inclusive scan of 32 elements by a block's four warps, for a part whose
+// FP64 units are split between its sub-partitions: a warp's 32-lane FP64
+// instruction runs at a quarter of the SM's rate, so one warp alone spends
+// ~95 of them per combine.  Here every level's 32 combines are shared out by
+// field group (scan_combine_part): warp w forms the common M^-1 and its own
+// fields, ~50 FP64 instructions, and the four warps run on the four
+// sub-partitions at once.  Element i starts in buf[0][i]; the result is in
+// buf[returned index][i].  All kScanThreads threads call it.
+constexpr int kScanThreads = 128;
+
+__device__ __forceinline__ int coop_scan32(double (*buf)[32][kScanElem]) {
+    const int lane = threadIdx.x & 31, part = threadIdx.x >> 5;
+    int cur = 0;
+#pragma unroll 1
+    for (int off = 1; off < 32; off <<= 1) {
+        double* dst = buf[cur ^ 1][lane];
+        const double* xs = buf[cur][lane];
+        if (lane >= off) {
+            const SElem y = load_elem(buf[cur][lane - off]);
+            const SElem x = load_elem(xs);
+            switch (part) {
+                case 0: scan_combine_part<0>(y, x, dst); break;
+                case 1: scan_combine_part<1>(y, x, dst); break;
+                case 2: scan_combine_part<2>(y, x, dst); break;
+                default: scan_combine_part<3>(y, x, dst); break;
+            }
+        } else {
+            for (int f = part_begin(part); f < part_begin(part + 1); ++f) dst[f] = xs[f];
+        }
+        __syncthreads();
+        cur ^= 1;
+    }
+    return cur;
+}
+
 // S1
 template <bool kOU>
-__global__ void __launch_bounds__(32) k_scan_local(ScanArgs a) {
-    const PhaseTable tab = scan_table(a);
-    const ScanItem it = a.items[blockIdx.x];
-    const int p = int(it.lane / a.B);
-    const PulsarDev& ps = a.psr[p];
-    const Lane L = scan_lane(a, it.lane, kOU, ps.equad2);
-    const int k_lo = it.k0 + int(threadIdx.x) * a.E;
-    const int k_hi = min(k_lo + a.E, ps.n);
-    SElem agg = scan_identity();
-    if (k_lo < k_hi) agg = scan_element<kOU>(k_lo, a.rec + (ps.off + k_lo) * kRecDoubles, L, tab, ps);
-    for (int k = k_lo + 1; k < k_hi; ++k)
-        agg = scan_combine(agg, scan_element<kOU>(k, a.rec + (ps.off + k) * kRecDoubles, L, tab, ps));
-    agg = warp_scan(agg);
-    store_elem(a.tpre + (int64_t(blockIdx.x) * 32 + threadIdx.x) * kScanElem, agg);
-    if (threadIdx.x == 31) store_elem(a.bagg + int64_t(blockIdx.x) * kScanElem, agg);
+__global__ void __launch_bounds__(kScanThreads) k_scan_local(ScanArgs a) {
+    __shared__ double buf[2][32][kScanElem];
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x < 32) {
+        const PhaseTable tab = scan_table(a);
+        const ScanItem it = a.items[blockIdx.x];
+        const int p = int(it.lane / a.B);
+        const PulsarDev& ps = a.psr[p];
+        const Lane L = scan_lane(a, it.lane, kOU, ps.equad2);
+        const int k_lo = it.k0 + lane * a.E;
+        const int k_hi = min(k_lo + a.E, ps.n);
+        SElem agg = scan_identity();
+        if (k_lo < k_hi) agg = scan_element<kOU>(k_lo, a.rec + (ps.off + k_lo) * kRecDoubles, L, tab, ps);
+        for (int k = k_lo + 1; k < k_hi; ++k)
+            agg = scan_combine(agg, scan_element<kOU>(k, a.rec + (ps.off + k) * kRecDoubles, L, tab, ps));
+        store_elem(buf[0][lane], agg);
+    }
+    __syncthreads();
+    const int res = coop_scan32(buf);
+    if (threadIdx.x < 32) {
+        const SElem agg = load_elem(buf[res][lane]);
+        store_elem(a.tpre + (int64_t(blockIdx.x) * 32 + lane) * kScanElem, agg);
+        if (lane == 31) store_elem(a.bagg + int64_t(blockIdx.x) * kScanElem, agg);
+    }
 }
 
 // S2
-__global__ void __launch_bounds__(32) k_scan_chunks(ScanArgs a) {
-    const int lane = blockIdx.x;
+__global__ void __launch_bounds__(kScanThreads) k_scan_chunks(ScanArgs a) {
+    __shared__ double buf[2][32][kScanElem];
+    const int lane = blockIdx.x, t = threadIdx.x & 31;
     const int first = a.lane_first[lane], cnt = a.lane_first[lane + 1] - first;
-    if (cnt == 0) return;
+    if (cnt == 0) return;   // the whole block
     const int q = (cnt + 31) / 32;
-    const int c_lo = int(threadIdx.x) * q, c_hi = min(c_lo + q, cnt);
-    SElem agg = scan_identity();
-    if (c_lo < c_hi) agg = load_elem(a.bagg + int64_t(first + c_lo) * kScanElem);
-    for (int c = c_lo + 1; c < c_hi; ++c)
-        agg = scan_combine(agg, load_elem(a.bagg + int64_t(first + c) * kScanElem));
-    const SElem inc = warp_scan(agg);
-    SElem pre = shfl_up_elem(inc, 1);
-    if (threadIdx.x == 0) pre = scan_identity();
-    for (int c = c_lo; c < c_hi; ++c) {
-        store_elem(a.bpre + int64_t(first + c) * kScanElem, pre);
-        pre = scan_combine(pre, load_elem(a.bagg + int64_t(first + c) * kScanElem));
+    const int c_lo = t * q, c_hi = min(c_lo + q, cnt);
+    if (threadIdx.x < 32) {
+        SElem agg = scan_identity();
+        if (c_lo < c_hi) agg = load_elem(a.bagg + int64_t(first + c_lo) * kScanElem);
+        for (int c = c_lo + 1; c < c_hi; ++c)
+            agg = scan_combine(agg, load_elem(a.bagg + int64_t(first + c) * kScanElem));
+        store_elem(buf[0][t], agg);
+    }
+    __syncthreads();
+    const int res = coop_scan32(buf);
+    if (threadIdx.x < 32) {
+        SElem pre = t == 0 ? scan_identity() : load_elem(buf[res][t - 1]);
+        for (int c = c_lo; c < c_hi; ++c) {
+            store_elem(a.bpre + int64_t(first + c) * kScanElem, pre);
+            if (c + 1 < c_hi)   // the prefix after the thread's last chunk is not needed
+                pre = scan_combine(pre, load_elem(a.bagg + int64_t(first + c) * kScanElem));
+        }
     }
 }
 
@@ -297,9 +353,9 @@ void launch_filter_scan(const ScanArgs& a, cudaStream_t s) {
     const bool ou = a.model == kOrnsteinUhlenbeck;
     const int lanes = int(a.B * a.P);
     if (a.n_items > 0) {
-        if (ou) k_scan_local<true><<<a.n_items, 32, smem, s>>>(a);
-        else k_scan_local<false><<<a.n_items, 32, smem, s>>>(a);
-        k_scan_chunks<<<lanes, 32, 0, s>>>(a);
+        if (ou) k_scan_local<true><<<a.n_items, kScanThreads, smem, s>>>(a);
+        else k_scan_local<false><<<a.n_items, kScanThreads, smem, s>>>(a);
+        k_scan_chunks<<<lanes, kScanThreads, 0, s>>>(a);
         if (ou) k_scan_finish<true><<<a.n_items, 32, smem, s>>>(a);
         else k_scan_finish<false><<<a.n_items, 32, smem, s>>>(a);
     }
