@@ -368,7 +368,9 @@ argus_status ensure_scan(argus_array* h, int64_t B) {
     if ((st = grow(&h->d_tpre, &h->cap_tpre, ni * 32 * kScanElem))) return st;
     if ((st = grow(&h->d_bagg, &h->cap_bagg, ni * kScanElem))) return st;
     if ((st = grow(&h->d_bpre, &h->cap_bpre, ni * kScanElem))) return st;
-    if ((st = grow(&h->d_part, &h->cap_part, ni * 2))) return st;
+    // chunk sums [ni][2], then one 8-byte counter per lane (kf_scan.cu's S3
+    // finds the lane's last chunk with it)
+    if ((st = grow(&h->d_part, &h->cap_part, ni * 2 + size_t(lanes)))) return st;
     if (!items.empty())
         CK(cudaMemcpy(h->d_sitems, items.data(), sizeof(ScanItem) * items.size(),
                       cudaMemcpyHostToDevice));

@@ -19,14 +19,18 @@
 // C = filtered covariance at TOA k.
 //
 // Three passes, no block ever waits on another:
-//   S1  one warp per chunk of 32 E TOAs: each thread combines its E elements
-//       in order, the warp scans the 32 partial products (shuffles);
-//   S2  one warp per lane: exclusive scan of the lane's chunk aggregates;
+//   S1  one block of 4 warps per chunk of 32 E TOAs: warp 0's threads
+//       combine their E elements in order, then the 4 warps scan the 32
+//       partial products, each level's combines split by field group;
+//   S2  one such block per lane: exclusive scan of the lane's chunk
+//       aggregates (an empty lane's ll is set to 0 here);
 //   S3  one warp per chunk: each thread's exact filtered state at the TOA
 //       before its own (chunk prefix x thread prefix), then the ordinary
 //       Kalman step of the sequential filter over its E TOAs, accumulating
-//       e^2/S and ln S; warp sums per chunk;
-//   S4  one thread per lane: the chunk sums in fixed order -> ll.
+//       e^2/S and ln S; warp sums per chunk.  The block that completes its
+//       lane last (a per-lane counter) sums the lane's chunks in fixed
+//       order -> ll;
+//   S4  only when every lane is empty: their lls, 0.
 // Work is O(N) per lane and depth O(E + log N).
 #include <cmath>
 #include <cstdint>
@@ -196,6 +200,28 @@ __device__ __forceinline__ PhaseTable scan_table(const ScanArgs& a) {
     return tab;
 }
 
+// Per-lane completion counters, one 8-byte slot per lane after the chunk
+// sums (the handle allocates a.part with n_items * 2 + B P doubles).
+__device__ __forceinline__ unsigned long long* lane_done(const ScanArgs& a) {
+    return reinterpret_cast<unsigned long long*>(a.part + 2 * int64_t(a.n_items));
+}
+
+// ll of a lane from its chunk sums, in chunk order (reads bypass L1: other
+// blocks wrote them)
+__device__ __forceinline__ void lane_total(const ScanArgs& a, int64_t lane) {
+    const int p = int(lane / a.B);
+    const int n = a.psr[p].n;
+    const int first = a.lane_first[lane], last = a.lane_first[lane + 1];
+    double quad = 0.0, logdet = 0.0;
+    for (int c = first; c < last; ++c) {
+        quad += __ldcg(a.part + 2 * int64_t(c));
+        logdet += __ldcg(a.part + 2 * int64_t(c) + 1);
+    }
+    double ll = (n == 0) ? 0.0 : -0.5 * (double(n) * kLog2PiScan + logdet + quad);
+    if (!isfinite(ll)) ll = -INFINITY;
+    a.lane_out[lane] = ll;
+}
+
 // Inclusive scan of 32 elements by a block's four warps, for a part whose
 // FP64 units are split between its sub-partitions: a warp's 32-lane FP64
 // instruction runs at a quarter of the SM's rate, so one warp alone spends
@@ -239,6 +265,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_local(ScanArgs a) {
     if (threadIdx.x < 32) {
         const PhaseTable tab = scan_table(a);
         const ScanItem it = a.items[blockIdx.x];
+        if (threadIdx.x == 0 && it.k0 == 0) lane_done(a)[it.lane] = 0ull;   // before S3 (a later kernel)
         const int p = int(it.lane / a.B);
         const PulsarDev& ps = a.psr[p];
         const Lane L = scan_lane(a, it.lane, kOU, ps.equad2);
@@ -264,7 +291,10 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_chunks(ScanArgs a) {
     __shared__ double buf[2][32][kScanElem];
     const int lane = blockIdx.x, t = threadIdx.x & 31;
     const int first = a.lane_first[lane], cnt = a.lane_first[lane + 1] - first;
-    if (cnt == 0) return;   // the whole block
+    if (cnt == 0) {   // the whole block: an empty lane's ll is 0
+        if (threadIdx.x == 0) a.lane_out[lane] = 0.0;
+        return;
+    }
     const int q = (cnt + 31) / 32;
     const int c_lo = t * q, c_hi = min(c_lo + q, cnt);
     if (threadIdx.x < 32) {
@@ -326,6 +356,14 @@ __global__ void __launch_bounds__(32) k_scan_finish(ScanArgs a) {
     if (threadIdx.x == 0) {
         a.part[2 * int64_t(blockIdx.x)] = quad;
         a.part[2 * int64_t(blockIdx.x) + 1] = logdet;
+        // the block that completes its lane last sums the lane's chunks (no
+        // block waits: the others just leave)
+        __threadfence();
+        const unsigned long long cnt = static_cast<unsigned long long>(a.lane_first[it.lane + 1] - a.lane_first[it.lane]);
+        if (atomicAdd(lane_done(a) + it.lane, 1ull) == cnt - 1) {
+            __threadfence();
+            lane_total(a, it.lane);
+        }
     }
 }
 
@@ -333,17 +371,7 @@ __global__ void __launch_bounds__(32) k_scan_finish(ScanArgs a) {
 __global__ void k_scan_sum(ScanArgs a) {
     const int64_t lane = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (lane >= a.B * a.P) return;
-    const int p = int(lane / a.B);
-    const int n = a.psr[p].n;
-    const int first = a.lane_first[lane], last = a.lane_first[lane + 1];
-    double quad = 0.0, logdet = 0.0;
-    for (int c = first; c < last; ++c) {
-        quad += a.part[2 * int64_t(c)];
-        logdet += a.part[2 * int64_t(c) + 1];
-    }
-    double ll = (n == 0) ? 0.0 : -0.5 * (double(n) * kLog2PiScan + logdet + quad);
-    if (!isfinite(ll)) ll = -INFINITY;
-    a.lane_out[lane] = ll;
+    lane_total(a, lane);
 }
 
 }  // namespace
@@ -358,8 +386,9 @@ void launch_filter_scan(const ScanArgs& a, cudaStream_t s) {
         k_scan_chunks<<<lanes, kScanThreads, 0, s>>>(a);
         if (ou) k_scan_finish<true><<<a.n_items, 32, smem, s>>>(a);
         else k_scan_finish<false><<<a.n_items, 32, smem, s>>>(a);
+    } else {
+        k_scan_sum<<<(lanes + 127) / 128, 128, 0, s>>>(a);   // every lane empty
     }
-    k_scan_sum<<<(lanes + 127) / 128, 128, 0, s>>>(a);
 }
 
 }  // namespace argus
