@@ -10,14 +10,15 @@
 //   2. predict: F is block diagonal (3 x 3 per pulsar,
 //      F_n = [[1, b_p, b_a], [0, a_p, 0], [0, 0, a_a]]), so each 3 x 3 block
 //      of P becomes F_I P_IJ F_J^T + Q_IJ on its own.  P is symmetric and
-//      only its upper triangle is stored: blocks I <= J are computed, the
-//      diagonal blocks read symmetrically.  Q_IJ holds the intrinsic noise
+//      only its upper triangle is stored, packed row by row (up to 64
+//      pulsars fit): blocks I <= J are computed, the diagonal blocks read
+//      symmetrically.  Q_IJ holds the intrinsic noise
 //      (I = J) and h_a^2 G_IJ times the integrated-OU increment covariance of
 //      the GW process in the (rho, a) slots;
 //   3. innovate on rho_q of the TOA's pulsar q: c = P e_{3q}, S = c_{3q} + R,
-//      e = r - m_{3q} (thread 0 forms 1/S once);
+//      e = r - m_{3q}; the threads that form c also form c / S;
 //   4. update: m += c e / S and, over the upper triangle only,
-//      P_ij -= (c_i c_j) / S; accumulate -1/2 (ln 2 pi + ln S + e^2 / S).
+//      P_ij -= c_i (c_j / S); accumulate -1/2 (ln 2 pi + ln S + e^2 / S).
 // Steps 2-4 are spread over the block's threads with a barrier between them;
 // a TOA at the same time as the previous one skips the predict (F = I, Q = 0).
 //
@@ -84,8 +85,8 @@ struct GwbArgs {
     int32_t nseg;
 };
 
-// Shared memory of a block.  The covariance P is stored whole but only its
-// upper triangle is kept current; the adjoint Pb (gradient) is kept full.
+// Shared memory of a block.  The covariance P and, for the gradient, its
+// adjoint Pb are symmetric and stored as packed upper triangles (see pk).
 struct GwbSmem {
     int P, n, nb, ne;
     double* Pm;     // packed upper triangle, n (n + 1) / 2
