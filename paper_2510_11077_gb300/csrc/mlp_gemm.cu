@@ -322,6 +322,9 @@ cudaError_t launch_one(const CUtensorMap* ta, const CUtensorMap* tb, int M, int 
 // Warp w reads TMEM lanes 32 (w % 4) .. + 31 (its rows) and columns
 // 128 (w / 4) .. + 127.  Thread 0 issues the copies and the MMAs and alone
 // waits on the mbarriers (bounded); the block follows through __syncthreads.
+// The prologue standardizes the inputs (from FP32 theta, or from a sampler's
+// FP64 z and centre) and forms the quadratic baseline; the last epilogue
+// writes the outputs in FP32, or in FP64 with an offset.
 constexpr int kFusedThreads = 256;
 constexpr uint32_t kFAtomA = kGemmM * 128u;       // one 64-column K-atom of the activation tile
 constexpr uint32_t kFSmemA = 4u * kFAtomA;        // 64 KB

@@ -1,7 +1,10 @@
 // Surrogate network of the array log-likelihood and its gradient:
 // MLP 47 -> 256 -> 256 -> 256 -> 256 -> 48 (GELU), BF16 weights and
 // activations, FP32 accumulation on the tensor cores (mlp_gemm.cu), FP32
-// master weights and Adam.  C ABI in include/argus_surrogate.h.
+// master weights and Adam.  C ABI in include/argus_surrogate.h.  Evaluation
+// runs the fused kernel (every layer in one launch); training runs one GEMM
+// launch per product, with the small reductions as parallel fixed-order
+// kernels.
 //
 // Layer l computes z = x W_l^T + b_l.  Shapes are padded for the tensor
 // cores: the input has 64 columns (47 used), the output 64 (48 used); padding
