@@ -55,7 +55,7 @@ namespace {
 constexpr double kLog2PiGwb = 1.8378770664093454836;
 constexpr double kLn10Gwb = 2.302585092994045684;
 constexpr int kGwbThreads = 256;      // gradient kernel
-constexpr int kGwbFwdThreads = 128;   // likelihood kernel: 8 blocks of 4 warps per SM
+constexpr int kGwbFwdThreads = 32;    // likelihood kernel: one warp per block
 constexpr int kGwbGradMaxPulsars = 48;   // gradient: two packed 3P x 3P triangles in shared memory
 constexpr int kCo = 9;                   // per-pulsar coefficients (see GwbSmem::co)
 
