@@ -500,11 +500,13 @@ def gwb_leg(args, dev, local):
 
 
 def latency_leg(args, dev, local):
-    """Latency of one loglik evaluation of one parameter vector on the
-    1-pulsar, 1000-TOA array: the sequential filter (one lane, one thread
-    stepping through the TOAs) against the time-parallel filter (plan mode
-    SCAN).  Each call is a CUDA-graph replay; L2 is flushed before each call,
-    outside the events."""
+    """Latency of one evaluation of one parameter vector on the 1-pulsar,
+    1000-TOA array: the sequential filter (one lane, one thread stepping
+    through the TOAs) against the time-parallel filter (plan mode SCAN), for
+    the log-likelihood and for the log-likelihood with its gradient (the
+    sequential adjoint against the time-parallel one).  Each call is a
+    CUDA-graph replay; L2 is flushed before each call, outside the events."""
+    import numpy as np
     import torch
 
     from paper_2510_11077_gb300 import argus, inputs
@@ -512,22 +514,22 @@ def latency_leg(args, dev, local):
     data = inputs.make_workload_array(w.name)
     theta = torch.from_numpy(inputs.make_theta_batch(data, 1, seed=w.seed)).to(dev)
     ll = torch.empty(1, dtype=torch.float64, device=dev)
+    g = torch.empty((1, data.dim), dtype=torch.float64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
     out = {"workload": w.name, "metric": "loglik latency", "unit": "us", "walkers": 1}
-    vals = {}
-    for name, plan in (("sequential", dict(mode=argus.ARGUS_MODE_BATCHED, walkers_per_cta=32)),
-                       ("scan", dict(mode=argus.ARGUS_MODE_SCAN))):
-        arr = argus.Array(data, device=local)
-        arr.set_plan(**plan)
+    plans = (("sequential", dict(mode=argus.ARGUS_MODE_BATCHED, walkers_per_cta=32)),
+             ("scan", dict(mode=argus.ARGUS_MODE_SCAN)))
+
+    def timed(arr, call):
         arr.set_timing(True)
         for _ in range(5):
-            argus.argus_loglik(arr, theta, ll)
+            call()
         torch.cuda.synchronize(dev)
         stages = arr.get_timing()
         arr.set_timing(False)
         for _ in range(3):
-            argus.argus_loglik(arr, theta, ll)     # re-capture without the stage events
+            call()                                  # re-capture without the stage events
         torch.cuda.synchronize(dev)
         reps = 200
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -535,20 +537,37 @@ def latency_leg(args, dev, local):
         for k in range(reps):
             flush.zero_()
             ev[k][0].record(stream)
-            argus.argus_loglik(arr, theta, ll)
+            call()
             ev[k][1].record(stream)
         torch.cuda.synchronize(dev)
         us = sorted(a.elapsed_time(b) * 1e3 for a, b in ev)
+        return {"median_us": us[reps // 2], "p10_us": us[reps // 10], "p90_us": us[9 * reps // 10],
+                "plan": arr.get_plan(),
+                "stage_us": {"project": stages[0] * 1e3, "filter": stages[1] * 1e3,
+                             "reduce": stages[2] * 1e3}}
+
+    vals, grads = {}, {}
+    out["gradient"] = {"metric": "loglik+grad latency", "unit": "us"}
+    for name, plan in plans:
+        arr = argus.Array(data, device=local)
+        arr.set_plan(**plan)
+        out[name] = timed(arr, lambda: argus.argus_loglik(arr, theta, ll))
         vals[name] = float(ll.item())
-        out[name] = {"median_us": us[reps // 2], "p10_us": us[reps // 10], "p90_us": us[9 * reps // 10],
-                     "plan": arr.get_plan(),
-                     "stage_us": {"project": stages[0] * 1e3, "filter": stages[1] * 1e3,
-                                  "reduce": stages[2] * 1e3}}
+        out["gradient"][name] = timed(arr, lambda: argus.argus_loglik_grad(arr, theta, ll, g))
+        grads[name] = g.cpu().numpy()[0].copy()
         arr.close()
     if vals["sequential"] != vals["scan"] and abs(vals["sequential"] - vals["scan"]) > \
             1e-12 * abs(vals["sequential"]):
         raise RuntimeError("scan and sequential filters disagree")
+    gs, gp = grads["sequential"], grads["scan"]
+    scale = np.maximum(np.abs(gs), 1e-3 * np.abs(gs).max())
+    gdiff = float(np.max(np.abs(gp - gs) / scale))
+    if not gdiff <= 1e-8:
+        raise RuntimeError(f"scan and sequential adjoints disagree ({gdiff:.2e})")
     out["speedup"] = out["sequential"]["median_us"] / out["scan"]["median_us"]
+    out["gradient"]["speedup"] = out["gradient"]["sequential"]["median_us"] / \
+        out["gradient"]["scan"]["median_us"]
+    out["gradient"]["max_rel_diff"] = gdiff
     return out
 
 

@@ -93,10 +93,15 @@ typedef struct argus_array argus_array;
  *   2021) and finished by ordinary Kalman steps; O(N) work, O(scan_elems +
  *   log N) depth.  It costs ~10x the sequential filter's FP64 work, so it
  *   pays only while the sequential filter leaves the GPU idle.
- *   argus_loglik_grad in this mode runs the batched adjoint. */
+ *   argus_loglik_grad in this mode runs the time-parallel adjoint: the
+ *   reverse sweep's step is an affine map of the adjoint state, so the
+ *   adjoint at the end of each thread's TOAs is a suffix scan of those maps
+ *   (chunks as above), after which each thread runs the ordinary adjoint
+ *   steps over its own TOAs.  Scratch: 48 B per TOA per lane for the tape
+ *   (144 B with ARGUS_NOISE_OU), plus ~4 KB per chunk. */
 enum { ARGUS_MODE_BATCHED = 0, ARGUS_MODE_PLAIN = 1, ARGUS_MODE_SCAN = 2 };
 typedef struct argus_plan {
-    int32_t mode;             /* ARGUS_MODE_BATCHED | ARGUS_MODE_PLAIN */
+    int32_t mode;             /* ARGUS_MODE_BATCHED, ARGUS_MODE_PLAIN or ARGUS_MODE_SCAN */
     int32_t walkers_per_cta;  /* lanes of one pulsar per thread block: 32, 64, 128 or 256 */
     int32_t ctas_per_sm;      /* resident blocks per SM of the persistent grid, 1..16 */
     int32_t ckpt_stride;      /* adjoint checkpoint stride in TOAs; 0 = ceil(sqrt(N_p)) */

@@ -15,6 +15,7 @@
 
 #include "../../include/argus.h"
 #include "kf_internal.cuh"
+#include "kf_scan_grad.cuh"
 #include "lib_internal.cuh"
 
 using namespace argus;
@@ -176,6 +177,13 @@ struct argus_array {
     int32_t scan_E = 0;
     int32_t n_sitems = 0;
     double* d_phase_tab = nullptr;
+    // time-parallel adjoint (ARGUS_MODE_SCAN with a gradient)
+    double* d_stape = nullptr;     size_t cap_stape = 0;
+    double* d_tsuf = nullptr;      size_t cap_tsuf = 0;
+    double* d_ragg = nullptr;      size_t cap_ragg = 0;
+    double* d_rpre = nullptr;      size_t cap_rpre = 0;
+    double* d_partg = nullptr;     size_t cap_partg = 0;
+    unsigned long long* d_rdone = nullptr; size_t cap_rdone = 0;
     // host staging
     double* d_stage = nullptr;     size_t cap_stage = 0;
     // graphs
@@ -383,9 +391,29 @@ argus_status ensure_scan(argus_array* h, int64_t B) {
     return ARGUS_OK;
 }
 
-// Enqueue one time-parallel loglik evaluation: K1 -> S1..S4 -> K4.
-argus_status enqueue_scan(argus_array* h, const double* theta, int64_t B, double* ll, double* lane,
-                          cudaStream_t s) {
+// Scratch of the time-parallel adjoint for the current chunking (after
+// ensure_scan); reallocation invalidates captured graphs.
+argus_status ensure_scan_grad(argus_array* h, int64_t B) {
+    const size_t ni = std::max<size_t>(size_t(h->n_sitems), 1);
+    const size_t lanes = std::max<size_t>(size_t(B) * h->P, 1);
+    const size_t tape = ni * 32 * size_t(h->scan_E) * size_t(tape_doubles(h->model));
+    void* before[6] = {h->d_stape, h->d_tsuf, h->d_ragg, h->d_rpre, h->d_partg, h->d_rdone};
+    argus_status st;
+    if ((st = grow(&h->d_stape, &h->cap_stape, tape))) return st;
+    if ((st = grow(&h->d_tsuf, &h->cap_tsuf, ni * 32 * kAdjElem))) return st;
+    if ((st = grow(&h->d_ragg, &h->cap_ragg, ni * kAdjElem))) return st;
+    if ((st = grow(&h->d_rpre, &h->cap_rpre, ni * kAdjElem))) return st;
+    if ((st = grow(&h->d_partg, &h->cap_partg, ni * kLaneGrads))) return st;
+    if ((st = grow(&h->d_rdone, &h->cap_rdone, lanes))) return st;
+    void* after[6] = {h->d_stape, h->d_tsuf, h->d_ragg, h->d_rpre, h->d_partg, h->d_rdone};
+    if (memcmp(before, after, sizeof(before)) != 0) drop_graphs(h);
+    return ARGUS_OK;
+}
+
+// Enqueue one time-parallel evaluation: K1 -> S1..S3 (and, with a gradient,
+// G3, R2, R3 in place of S3) -> K4.
+argus_status enqueue_scan(argus_array* h, const double* theta, int64_t B, double* ll, double* grad,
+                          double* lane, cudaStream_t s) {
     if (h->timing) CK(cudaEventRecordWithFlags(h->ev[0], s, cudaEventRecordExternal));
     launch_project(theta, B, h->P, h->flags, h->d_psr, h->d_lc, s);
     if (h->timing) CK(cudaEventRecordWithFlags(h->ev[1], s, cudaEventRecordExternal));
@@ -406,9 +434,21 @@ argus_status enqueue_scan(argus_array* h, const double* theta, int64_t B, double
     a.lane_out = h->d_lane;
     a.phase_table = h->d_phase_tab;
     a.model = h->model;
-    launch_filter_scan(a, s);
+    if (grad) {
+        ScanGradArgs g{};
+        g.s = a;
+        g.tape = h->d_stape;
+        g.tsuf = h->d_tsuf;
+        g.ragg = h->d_ragg;
+        g.rpre = h->d_rpre;
+        g.partg = h->d_partg;
+        g.rdone = h->d_rdone;
+        launch_filter_scan_grad(g, s);
+    } else {
+        launch_filter_scan(a, s);
+    }
     if (h->timing) CK(cudaEventRecordWithFlags(h->ev[2], s, cudaEventRecordExternal));
-    launch_reduce(theta, B, h->P, h->flags, h->d_psr, h->d_lane, ll, nullptr, lane, s);
+    launch_reduce(theta, B, h->P, h->flags, h->d_psr, h->d_lane, ll, grad, lane, s);
     if (h->timing) {
         CK(cudaEventRecordWithFlags(h->ev[3], s, cudaEventRecordExternal));
         h->timed_once = true;
@@ -443,18 +483,19 @@ argus_status enqueue_batched(argus_array* h, const double* theta, int64_t B, dou
 argus_status run_batched(argus_array* h, const double* theta, int64_t B, double* ll, double* grad,
                          double* lane, cudaStream_t s) {
     const int W = h->plan.walkers_per_cta;
-    const bool scan = h->plan.mode == ARGUS_MODE_SCAN && grad == nullptr;
+    const bool scan = h->plan.mode == ARGUS_MODE_SCAN;
     argus_status st;
     if (scan) {
         if ((st = ensure_batch(h, B, W, 1, false))) return st;
         if ((st = ensure_scan(h, B))) return st;
+        if (grad && (st = ensure_scan_grad(h, B))) return st;
     } else {
         if ((st = ensure_items(h, B, W))) return st;
         const int grid = grid_for(h, h->n_items);
         if ((st = ensure_batch(h, B, W, grid, grad != nullptr))) return st;
     }
     auto enqueue = [&](cudaStream_t st_) {
-        return scan ? enqueue_scan(h, theta, B, ll, lane, st_)
+        return scan ? enqueue_scan(h, theta, B, ll, grad, lane, st_)
                     : enqueue_batched(h, theta, B, ll, grad, lane, st_);
     };
     if (!h->plan.use_graph) return enqueue(s);
@@ -644,10 +685,13 @@ argus_status argus_array_create_ex(const argus_pulsar* psrs, int32_t n_pulsars, 
         return st;
     };
     cudaError_t e;
-    if ((e = cudaMalloc(&h->d_rec, rec.size() * sizeof(double))) != cudaSuccess)
-        return cleanup(cuda_fail(e, "cudaMalloc(records)"));
-    if ((e = cudaMemcpy(h->d_rec, rec.data(), rec.size() * sizeof(double), cudaMemcpyHostToDevice)) !=
+    // (one record's room even for an array without TOAs: no kernel reads it then)
+    if ((e = cudaMalloc(&h->d_rec, std::max<size_t>(rec.size(), kRecDoubles) * sizeof(double))) !=
         cudaSuccess)
+        return cleanup(cuda_fail(e, "cudaMalloc(records)"));
+    if (!rec.empty() &&
+        (e = cudaMemcpy(h->d_rec, rec.data(), rec.size() * sizeof(double), cudaMemcpyHostToDevice)) !=
+            cudaSuccess)
         return cleanup(cuda_fail(e, "cudaMemcpy(records)"));
     if ((e = cudaMalloc(&h->d_psr, sizeof(PulsarDev) * n_pulsars)) != cudaSuccess)
         return cleanup(cuda_fail(e, "cudaMalloc(pulsars)"));
@@ -690,6 +734,12 @@ void argus_array_destroy(argus_array* h) {
     cudaFree(h->d_bpre);
     cudaFree(h->d_part);
     cudaFree(h->d_phase_tab);
+    cudaFree(h->d_stape);
+    cudaFree(h->d_tsuf);
+    cudaFree(h->d_ragg);
+    cudaFree(h->d_rpre);
+    cudaFree(h->d_partg);
+    cudaFree(h->d_rdone);
     delete h;
 }
 
