@@ -86,9 +86,12 @@ def parse_args():
     ap.add_argument("--autotune", choices=["cache", "off", "force"], default="cache",
                     help="cache: use the tuned-plan cache, tuning on a miss; force: retune")
     ap.add_argument("--tune-batch", type=int, default=4096)
-    ap.add_argument("--mode", choices=["filter", "da-hmc", "surrogate"], default="filter",
+    ap.add_argument("--mode", choices=["filter", "da-hmc", "surrogate", "latency"], default="filter",
                     help="filter: loglik+grad evals/s (default); da-hmc: surrogate delayed acceptance; "
-                         "surrogate: the surrogate's evaluation alone, fused vs per-layer")
+                         "surrogate: the surrogate's evaluation alone, fused vs per-layer; "
+                         "latency: the single-vector latency leg alone (sequential vs time-parallel)")
+    ap.add_argument("--latency-reps", type=int, default=200,
+                    help="timed calls per path in the latency leg")
     ap.add_argument("--plan", default="",
                     help="fixed plan, e.g. tape_cache=1,walkers_per_cta=128 (disables autotune)")
     return ap.parse_args()
@@ -531,7 +534,7 @@ def latency_leg(args, dev, local):
         for _ in range(3):
             call()                                  # re-capture without the stage events
         torch.cuda.synchronize(dev)
-        reps = 200
+        reps = max(1, getattr(args, "latency_reps", 200))
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(reps)]
         for k in range(reps):
@@ -888,6 +891,26 @@ def run_surrogate(args):
     return 0
 
 
+def run_latency(args):
+    """The latency leg alone: one parameter vector on the 1-pulsar, 1000-TOA
+    array, loglik + gradient through the time-parallel filter (the line's
+    value) against the sequential one, and the loglik alone."""
+    import torch
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    out = latency_leg(args, torch.device("cuda", local), local)
+    g = out["gradient"]
+    line = {"metric": "loglik+grad latency, one parameter vector (1 pulsar x 1000 TOAs)",
+            "value": g["scan"]["median_us"], "unit": "us", "n_gpus": 1, "higher_is_better": False,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": LATENCY_WORKLOAD, "walkers": 1, "plan": "SCAN",
+                       "l2": "flushed before each call"},
+            "latency_1psr": out}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
@@ -896,6 +919,8 @@ def main():
         return run_da_hmc(args)
     if args.mode == "surrogate":
         return run_surrogate(args)
+    if args.mode == "latency":
+        return run_latency(args)
     return run_ours(args)
 
 

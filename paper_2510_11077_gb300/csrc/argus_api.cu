@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/argus.h"
+#include "kf_few.cuh"
 #include "kf_internal.cuh"
 #include "kf_scan_grad.cuh"
 #include "lib_internal.cuh"
@@ -414,8 +415,11 @@ argus_status ensure_scan_grad(argus_array* h, int64_t B) {
 // G3, R2, R3 in place of S3) -> K4.
 argus_status enqueue_scan(argus_array* h, const double* theta, int64_t B, double* ll, double* grad,
                           double* lane, cudaStream_t s) {
+    // a few walkers: K1 and K4 with one block of four warps per walker
+    const bool few = few_walkers(B, h->P);
     if (h->timing) CK(cudaEventRecordWithFlags(h->ev[0], s, cudaEventRecordExternal));
-    launch_project(theta, B, h->P, h->flags, h->d_psr, h->d_lc, s);
+    if (few) launch_project_few(theta, B, h->P, h->flags, h->d_psr, h->d_lc, s);
+    else launch_project(theta, B, h->P, h->flags, h->d_psr, h->d_lc, s);
     if (h->timing) CK(cudaEventRecordWithFlags(h->ev[1], s, cudaEventRecordExternal));
     ScanArgs a{};
     a.rec = h->d_rec;
@@ -448,7 +452,8 @@ argus_status enqueue_scan(argus_array* h, const double* theta, int64_t B, double
         launch_filter_scan(a, s);
     }
     if (h->timing) CK(cudaEventRecordWithFlags(h->ev[2], s, cudaEventRecordExternal));
-    launch_reduce(theta, B, h->P, h->flags, h->d_psr, h->d_lane, ll, grad, lane, s);
+    if (few && grad) launch_reduce_few(theta, B, h->P, h->flags, h->d_psr, h->d_lane, ll, grad, lane, s);
+    else launch_reduce(theta, B, h->P, h->flags, h->d_psr, h->d_lane, ll, grad, lane, s);
     if (h->timing) {
         CK(cudaEventRecordWithFlags(h->ev[3], s, cudaEventRecordExternal));
         h->timed_once = true;
