@@ -140,7 +140,7 @@ struct FilterSmem {
 __device__ __forceinline__ FilterSmem filter_smem() {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     FilterSmem s;
-    s.tab.d = reinterpret_cast<double2*>(smem_raw);
+    s.tab.d = reinterpret_cast<longlong2*>(smem_raw);
     s.tab.f = reinterpret_cast<float4*>(smem_raw + kPhaseTable * sizeof(double2));
     s.rec = reinterpret_cast<double*>(smem_raw + kPhaseTableBytes);
     return s;

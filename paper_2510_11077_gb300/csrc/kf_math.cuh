@@ -10,9 +10,12 @@
 //    sum of two floats, ~48-bit significand), then the angle-addition formula.
 //    Error-free transformations: Knuth's two-sum, Dekker's fast two-sum and
 //    the FMA two-product (as in the double-float arithmetic of Hida, Li &
-//    Bailey 2001).  Only the final hi+lo sums run on the FP64 pipe.
+//    Bailey 2001).  The table node plus the correction is then summed exactly
+//    in 2^-62 fixed point and rounded once to a double, all on the integer
+//    pipe: no FP64 instruction at all.
 //  * rcp_nr: 1/S by the FP64 approximate-reciprocal instruction refined by
-//    two Newton-Raphson steps r <- r + r (1 - S r).
+//    one third-order step r <- r (1 + e + e^2), e = 1 - S r, whose error is
+//    e^3.
 //  * LogProd: sum of ln S_k as a running product kept in [1, 2) with its
 //    binary exponent accumulated in an integer (one log per lane at the end).
 #pragma once
@@ -58,20 +61,6 @@ __device__ __forceinline__ df df_add_f(df a, float b) {          // a + b, b a f
 
 __device__ __forceinline__ df df_neg(df a) { return {-a.hi, -a.lo}; }
 
-// Exact float -> double by re-packing the bits (integer instructions only).
-// Zero and subnormal floats map to a signed zero.
-__device__ __forceinline__ double f2d_bits(float f) {
-    const unsigned u = __float_as_uint(f);
-    const unsigned e = (u >> 23) & 0xffu;
-    unsigned hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u >> 3) & 0xfffffu);
-    unsigned lo = u << 29;
-    hi = e ? hi : (u & 0x80000000u);
-    lo = e ? lo : 0u;
-    return __hiloint2double(int(hi), int(lo));
-}
-
-__device__ __forceinline__ double df_to_double(df a) { return f2d_bits(a.hi) + f2d_bits(a.lo); }
-
 // frac(x) * 2^64 for a finite double x (exact, integer instructions only).
 __device__ __forceinline__ uint64_t frac_cycles_u64(double x) {
     const long long b = __double_as_longlong(x);
@@ -85,23 +74,54 @@ __device__ __forceinline__ uint64_t frac_cycles_u64(double x) {
     return (b < 0) ? (0ull - F) : F;
 }
 
-// Table of sin/cos(2 pi j / 256): FP64 values (for the final sums) and the
-// same values as double-float pairs (for the small corrections).
+// x 2^62 rounded to an integer (half away from zero) for a float |x| < 2;
+// zero and subnormal floats give 0.  Integer instructions only.
+__device__ __forceinline__ long long f2fix62(float x) {
+    const unsigned u = __float_as_uint(x);
+    const int e = int((u >> 23) & 0xffu);
+    const long long m = e ? (long long)((u & 0x7fffffu) | 0x800000u) : 0ll;   // x = m 2^(e - 150)
+    const int sh = e - 88;                                                  // x 2^62 = m 2^sh
+    long long v = 0;
+    if (sh >= 0) v = m << sh;                            // sh <= 38 for |x| < 2
+    else if (sh > -63) v = (m + (1ll << (-sh - 1))) >> (-sh);
+    return (u >> 31) ? -v : v;
+}
+
+// The double nearest to v 2^-62 (ties to even), for |v| <= 2^62 (|value| <= 1).
+// Integer instructions only.
+__device__ __forceinline__ double fix62_to_double(long long v) {
+    const unsigned long long neg = v < 0 ? 1ull : 0ull;
+    const unsigned long long a = neg ? 0ull - static_cast<unsigned long long>(v)
+                                     : static_cast<unsigned long long>(v);
+    const int lz = __clzll(static_cast<long long>(a));
+    const unsigned long long u = a << (lz & 63);          // leading 1 at bit 63
+    unsigned long long m = u >> 11;                       // 53 bits, leading 1 at bit 52
+    const unsigned r = unsigned(u & 0x7ffu);
+    m += (r > 0x400u || (r == 0x400u && (m & 1ull))) ? 1ull : 0ull;
+    // the leading bit of a 2^-62 is 2^(1 - lz); a carry out of m bumps the exponent
+    const unsigned long long bits =
+        (static_cast<unsigned long long>(1024 - lz) << 52) + m - (1ull << 52);
+    return a ? __longlong_as_double(static_cast<long long>(bits | (neg << 63))) : 0.0;
+}
+
+// Table of sin/cos(2 pi j / 256): the nodes in 2^-62 fixed point (exact:
+// every nonzero node is above 2^-6 in magnitude, so its ulp is at least
+// 2^-58) for the final sums, and as double-float pairs for the corrections.
 constexpr int kPhaseTable = 256;
 
 struct PhaseTable {
-    double2* d;   // {sin, cos}
-    float4* f;    // {sin.hi, sin.lo, cos.hi, cos.lo}
+    longlong2* d;   // {sin, cos} 2^62
+    float4* f;      // {sin.hi, sin.lo, cos.hi, cos.lo}
 };
 
-constexpr size_t kPhaseTableBytes = kPhaseTable * (sizeof(double2) + sizeof(float4));
+constexpr size_t kPhaseTableBytes = kPhaseTable * (sizeof(longlong2) + sizeof(float4));
 
 __device__ __forceinline__ void fill_phase_table(PhaseTable tab) {
     for (int j = threadIdx.x; j < kPhaseTable; j += blockDim.x) {
         double s, c;
         sincospi(double(j) / (kPhaseTable / 2), &s, &c);
         const float sh = __double2float_rn(s), ch = __double2float_rn(c);
-        tab.d[j] = make_double2(s, c);
+        tab.d[j] = make_longlong2(__double2ll_rn(s * 0x1p62), __double2ll_rn(c * 0x1p62));
         tab.f[j] = make_float4(sh, __double2float_rn(s - double(sh)), ch,
                                __double2float_rn(c - double(ch)));
     }
@@ -109,7 +129,11 @@ __device__ __forceinline__ void fill_phase_table(PhaseTable tab) {
 
 // sin(2 pi x), cos(2 pi x) for x in cycles.  With x = j/256 + a/(2 pi):
 //   sin = S_j + [S_j (cos a - 1) + C_j sin a],  cos = C_j + [C_j (cos a - 1) - S_j sin a],
-// the brackets (|.| <= 0.013) in double-float, the two sums in FP64.
+// the brackets (|.| <= 0.013) in double-float; each node + bracket summed in
+// 2^-62 fixed point (the bracket's two floats each rounded to 2^-63) and
+// rounded once to a double: within 0.5 ulp + 2^-62 of node + bracket.  (A
+// result below ~2^-40 in magnitude keeps its absolute, not its relative,
+// accuracy.)
 __device__ __forceinline__ void phase_sincos(double x, PhaseTable tab, double& sn, double& cs) {
     const uint64_t F = frac_cycles_u64(x);
     const uint64_t j = (F + (1ull << 55)) >> 56;                 // nearest table node
@@ -134,22 +158,22 @@ __device__ __forceinline__ void phase_sincos(double x, PhaseTable tab, double& s
                             q * q * fmaf(-q, 1.0f / 720.0f, 1.0f / 24.0f));
     const int jj = int(j & (kPhaseTable - 1));
     const float4 t = tab.f[jj];
-    const double2 td = tab.d[jj];
+    const longlong2 td = tab.d[jj];
     const df S = {t.x, t.y}, C = {t.z, t.w};
     const df corr_s = df_add(df_mul(S, cm1), df_mul(C, sa));
     const df corr_c = df_add(df_mul(C, cm1), df_neg(df_mul(S, sa)));
-    sn = (td.x + f2d_bits(corr_s.hi)) + f2d_bits(corr_s.lo);
-    cs = (td.y + f2d_bits(corr_c.hi)) + f2d_bits(corr_c.lo);
+    sn = fix62_to_double(td.x + f2fix62(corr_s.hi) + f2fix62(corr_s.lo));
+    cs = fix62_to_double(td.y + f2fix62(corr_c.hi) + f2fix62(corr_c.lo));
 }
 
-// 1/S for a positive normal S: approximate reciprocal + 2 Newton-Raphson steps.
+// 1/S for a positive normal S: the approximate reciprocal (measured within
+// 2^-19.9) refined by one third-order step, r (1 + e + e^2) with e = 1 - S r:
+// the exact result is (1/S)(1 - e^3), so only the last rounding remains.
 __device__ __forceinline__ double rcp_nr(double S) {
     double r;
     asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(S));
-    double e = fma(-S, r, 1.0);
-    r = fma(r, e, r);
-    e = fma(-S, r, 1.0);
-    return fma(r, e, r);
+    const double e = fma(-S, r, 1.0);
+    return fma(r, fma(e, e, e), r);
 }
 
 // Running sum of ln S_k: mantissa product in [1, 2) and an integer exponent.

@@ -43,7 +43,7 @@
 namespace argus {
 
 __global__ void k_fill_phase_table(double* tab) {
-    fill_phase_table(PhaseTable{reinterpret_cast<double2*>(tab),
+    fill_phase_table(PhaseTable{reinterpret_cast<longlong2*>(tab),
                                 reinterpret_cast<float4*>(tab + 2 * kPhaseTable)});
 }
 
@@ -196,7 +196,7 @@ __device__ __forceinline__ Lane scan_lane(const ScanArgs& a, int lane, bool ou, 
 __device__ __forceinline__ PhaseTable scan_table(const ScanArgs& a) {
     double* t = const_cast<double*>(a.phase_table);   // read only
     PhaseTable tab;
-    tab.d = reinterpret_cast<double2*>(t);
+    tab.d = reinterpret_cast<longlong2*>(t);
     tab.f = reinterpret_cast<float4*>(t + 2 * kPhaseTable);
     return tab;
 }

@@ -12,7 +12,7 @@ namespace {
 using namespace argus;
 
 __global__ void k_phase(const double* x, int64_t n, double* s, double* c, double* rs, double* rc) {
-    __shared__ double2 tabd[kPhaseTable];
+    __shared__ longlong2 tabd[kPhaseTable];
     __shared__ float4 tabf[kPhaseTable];
     const PhaseTable tab{tabd, tabf};
     fill_phase_table(tab);
