@@ -9,7 +9,7 @@ namespace argus {
 constexpr int kNgw = 7;          // continuous-wave parameters at the head of theta
 constexpr int kRecDoubles = 8;   // doubles per staged TOA record
 constexpr int kCkptDoubles = 5;  // (m0, m1, p00, p01, p11) per checkpoint
-constexpr int kTapeDoubles = 6;  // (R/S, K1, 1/S, e, sin, cos) per step of a segment
+constexpr int kTapeDoubles = 6;  // (R/S, K1, e/S, (e/S)^2 - 1/S, sin, cos) per step of a segment
 constexpr int kTapeDoublesOU = 18; // ... plus (m1, p01 + b p11, a p11) before the step, the
                                    // transition a, b, Q / sigma^2 (3) and d/dgamma of b, Q (4)
 constexpr int kMaxStride = 256;  // longest adjoint segment, in TOAs
@@ -102,7 +102,8 @@ struct ScanArgs {
     int32_t model;            // NoiseModel
 };
 void launch_filter_scan(const ScanArgs& a, cudaStream_t s);
-// the sin/cos table of phase_sincos in global memory: 256 double2 then 256 float4
+// the sin/cos table of phase_sincos in global memory: 256 longlong2 (the nodes in
+// 2^-62 fixed point), then 256 float4 (the nodes as float pairs)
 constexpr int kPhaseTableDoubles = 256 * 4;
 void launch_fill_phase_table(double* tab, cudaStream_t s);
 

@@ -41,13 +41,14 @@ __device__ __forceinline__ void kf_step_adjoint(Adjoint& a, const StepOut& so,
     const double t = rec[0], dt = rec[1], h2 = rec[2], h3 = rec[3], s2k = rec[5], dt2 = rec[6];
     const double twodt = rec[7];
     // K0 = M00/S = 1 - w
-    const double w = so.w, K1 = so.K1, gg = so.e * so.rS;
+    const double w = so.w, K1 = so.K1, gg = so.g;
     const double t1 = fma(-a.mu0, w, fma(a.mu1, K1, a.mu0));    // mu0 K0 + mu1 K1
     const double ebar = t1 - gg;                                // dL/de
     const double u = fma(-a.pi00, w, fma(a.pi01, K1, a.pi00));  // pi00 K0 + pi01 K1
     const double v = a.pi11 * K1;
     const double ku = fma(-w, u, fma(v, K1, u));                // K0 u + K1 v
-    const double Sbar = fma(-0.5 * so.rS, fma(-so.e, gg, 1.0), fma(-gg, t1, ku));
+    // dL/dS: its own term -(1 - e^2/S)/(2S) = h2/2, and through g = e/S and K
+    const double Sbar = fma(0.5, so.h2, fma(-gg, t1, ku));
     const double a0 = a.mu0 - ebar;                             // dL/d(predicted m0)
     const double M00b = fma(a.mu0, gg, fma(a.pi00, fma(2.0, w, -1.0), fma(-a.pi01, K1, Sbar)));
     const double M01b = fma(a.mu1, gg, fma(a.pi01, w, -2.0 * v));
@@ -85,8 +86,8 @@ __device__ __forceinline__ void kf_step_adjoint(Adjoint& a, const StepOut& so,
 // One step's tape record, field-major within the step: [field][W].
 template <bool kOU>
 __device__ __forceinline__ void tape_put(double* tk, int W, const StepOut& so) {
-    tk[0 * W] = so.w; tk[1 * W] = so.K1; tk[2 * W] = so.rS;
-    tk[3 * W] = so.e; tk[4 * W] = so.sn; tk[5 * W] = so.cs;
+    tk[0 * W] = so.w; tk[1 * W] = so.K1; tk[2 * W] = so.g;
+    tk[3 * W] = so.h2; tk[4 * W] = so.sn; tk[5 * W] = so.cs;
     if (kOU) {
         tk[6 * W] = so.m1; tk[7 * W] = so.t1; tk[8 * W] = so.ap11;
         tk[9 * W] = so.a; tk[10 * W] = so.b; tk[11 * W] = so.c00; tk[12 * W] = so.c01;
@@ -98,8 +99,8 @@ __device__ __forceinline__ void tape_put(double* tk, int W, const StepOut& so) {
 template <bool kOU>
 __device__ __forceinline__ StepOut tape_get(const double* tk, int W) {
     StepOut so{};
-    so.w = tk[0 * W]; so.K1 = tk[1 * W]; so.rS = tk[2 * W];
-    so.e = tk[3 * W]; so.sn = tk[4 * W]; so.cs = tk[5 * W];
+    so.w = tk[0 * W]; so.K1 = tk[1 * W]; so.g = tk[2 * W];
+    so.h2 = tk[3 * W]; so.sn = tk[4 * W]; so.cs = tk[5 * W];
     if (kOU) {
         so.m1 = tk[6 * W]; so.t1 = tk[7 * W]; so.ap11 = tk[8 * W];
         so.a = tk[9 * W]; so.b = tk[10 * W]; so.c00 = tk[11 * W]; so.c01 = tk[12 * W];
@@ -188,7 +189,7 @@ __global__ void __launch_bounds__(256) k_filter_fwd(FilterArgs a) {
 // Pass 1 runs the filter forward segment by segment (stride TOAs each) and
 // checkpoints the state at the start of every segment.  Pass 2 walks the
 // segments backwards: restore the checkpoint, re-run the segment forward
-// recording (R/S, K1, 1/S, e, sin, cos) per step in the block's tape, then
+// recording (R/S, K1, e/S, (e/S)^2 - 1/S, sin, cos) per step in the block's tape, then
 // run the adjoint steps in reverse.  Checkpoints and tape live in the block's
 // own slot of global scratch ([..][field][W], so a warp's accesses coalesce).
 // With kCache the tape of every segment is written during pass 1 and kept in

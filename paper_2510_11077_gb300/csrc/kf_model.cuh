@@ -149,8 +149,9 @@ __device__ __forceinline__ void load_lane(const FilterArgs& a, int p, int64_t b,
 }
 
 
-struct StepOut {   // what the adjoint needs from the forward step (w = R/S = 1 - K0)
-    double w, K1, rS, e, sn, cs;
+struct StepOut {   // what the adjoint needs from the forward step
+    // w = R/S = 1 - K0, K1 = M01/S, g = e/S, h2 = g^2 - 1/S (= -(1 - e^2/S)/S)
+    double w, K1, g, h2, sn, cs;
     // Ornstein-Uhlenbeck only: m1, p01 + b p11 and a p11 before the step, the
     // transition a, b, Q / sigma^2 and the gamma-derivatives of b and Q / sigma^2
     double m1, t1, ap11;
@@ -202,9 +203,8 @@ __device__ __forceinline__ void kf_step(State& x, const double* __restrict__ rec
     // signal at phase f t + Phi0/(2 pi) cycles
     double sn, cs;
     phase_sincos(fma(L.f, t, L.phc), tab, sn, cs);
-    const double s = fma(L.A, sn, L.B * cs);
-    // innovation
-    const double e = (r - s) - m0;
+    // innovation e = r - (A sin + B cos) - m0
+    const double e = fma(-L.A, sn, fma(-L.B, cs, r - m0));
     const double R = fma(L.efac2, s2k, L.equad2);
     const double S = M00 + R;
     const double rS = rcp_nr(S);
@@ -218,7 +218,7 @@ __device__ __forceinline__ void kf_step(State& x, const double* __restrict__ rec
     x.p01 = M01 * w;
     x.p11 = fma(-K1, M01, M11);
     if (kTape) {
-        so.w = w; so.K1 = K1; so.rS = rS; so.e = e; so.sn = sn; so.cs = cs;
+        so.w = w; so.K1 = K1; so.g = g; so.h2 = fma(g, g, -rS); so.sn = sn; so.cs = cs;
     }
     if (kLL) {
         quad = fma(e, g, quad);

@@ -520,8 +520,8 @@ struct AdjScan {
 template <bool kOU>
 __device__ __forceinline__ AElem adj_element(const StepOut& so, const double* __restrict__ rec) {
     const double a = kOU ? so.a : 1.0, b = kOU ? so.b : rec[1];
-    const double g = so.e * so.rS;
-    const double s0 = -0.5 * so.rS * fma(-so.e, g, 1.0);
+    const double g = so.g;
+    const double s0 = 0.5 * so.h2;
     const double x11 = fma(-b, so.K1, a);
     const double twob = 2.0 * b, b2 = b * b, gw = g * so.w;
     AElem E;
@@ -551,13 +551,13 @@ __device__ __forceinline__ void adj_step(AdjState& a, const StepOut& so, const d
                                          const Lane& L, GradSums& g) {
     const double t = rec[0], dt = rec[1], h2 = rec[2], h3 = rec[3], s2k = rec[5], dt2 = rec[6];
     const double twodt = rec[7];
-    const double w = so.w, K1 = so.K1, gg = so.e * so.rS;
+    const double w = so.w, K1 = so.K1, gg = so.g;
     const double t1 = fma(-a.mu0, w, fma(a.mu1, K1, a.mu0));    // mu0 K0 + mu1 K1, K0 = 1 - w
     const double ebar = t1 - gg;                                // dL/de
     const double u = fma(-a.pi00, w, fma(a.pi01, K1, a.pi00));  // pi00 K0 + pi01 K1
     const double v = a.pi11 * K1;
     const double ku = fma(-w, u, fma(v, K1, u));                // K0 u + K1 v
-    const double Sbar = fma(-0.5 * so.rS, fma(-so.e, gg, 1.0), fma(-gg, t1, ku));
+    const double Sbar = fma(0.5, so.h2, fma(-gg, t1, ku));
     const double a0 = a.mu0 - ebar;                             // dL/d(predicted m0)
     const double M00b = fma(a.mu0, gg, fma(a.pi00, fma(2.0, w, -1.0), fma(-a.pi01, K1, Sbar)));
     const double M01b = fma(a.mu1, gg, fma(a.pi01, w, -2.0 * v));
@@ -592,8 +592,8 @@ __device__ __forceinline__ void adj_step(AdjState& a, const StepOut& so, const d
 // A step's tape record in the chunk's field-major tape: field f at tk[f * st].
 template <bool kOU>
 __device__ __forceinline__ void stape_put(double* tk, int64_t st, const StepOut& so) {
-    tk[0 * st] = so.w; tk[1 * st] = so.K1; tk[2 * st] = so.rS;
-    tk[3 * st] = so.e; tk[4 * st] = so.sn; tk[5 * st] = so.cs;
+    tk[0 * st] = so.w; tk[1 * st] = so.K1; tk[2 * st] = so.g;
+    tk[3 * st] = so.h2; tk[4 * st] = so.sn; tk[5 * st] = so.cs;
     if (kOU) {
         tk[6 * st] = so.m1; tk[7 * st] = so.t1; tk[8 * st] = so.ap11;
         tk[9 * st] = so.a; tk[10 * st] = so.b; tk[11 * st] = so.c00; tk[12 * st] = so.c01;
@@ -605,8 +605,8 @@ __device__ __forceinline__ void stape_put(double* tk, int64_t st, const StepOut&
 template <bool kOU>
 __device__ __forceinline__ StepOut stape_get(const double* tk, int64_t st) {
     StepOut so{};
-    so.w = tk[0 * st]; so.K1 = tk[1 * st]; so.rS = tk[2 * st];
-    so.e = tk[3 * st]; so.sn = tk[4 * st]; so.cs = tk[5 * st];
+    so.w = tk[0 * st]; so.K1 = tk[1 * st]; so.g = tk[2 * st];
+    so.h2 = tk[3 * st]; so.sn = tk[4 * st]; so.cs = tk[5 * st];
     if (kOU) {
         so.m1 = tk[6 * st]; so.t1 = tk[7 * st]; so.ap11 = tk[8 * st];
         so.a = tk[9 * st]; so.b = tk[10 * st]; so.c00 = tk[11 * st]; so.c01 = tk[12 * st];
