@@ -19,13 +19,15 @@
 extern "C" {
 #endif
 
-/* For each phase x[i] (cycles): the table + double-float sin/cos of 2 pi x
- * (sin_out, cos_out) and CUDA's sincospi(2 x) (ref_sin, ref_cos), all [n]. */
+/* For each phase x[i] (cycles): the filter's sin/cos of 2 pi x (table node +
+ * double-float correction, summed in 2^-62 fixed point) (sin_out, cos_out)
+ * and CUDA's sincospi(2 x) (ref_sin, ref_cos), all [n]. */
 argus_status argus_selftest_phase(const double* x, int64_t n, double* sin_out, double* cos_out,
                                   double* ref_sin, double* ref_cos);
 
-/* out[i] = 1 / S[i] by the approximate reciprocal + two Newton-Raphson steps;
- * S[i] must be positive and normal. */
+/* out[i] = 1 / S[i] by the approximate reciprocal refined by one third-order
+ * step r (1 + e + e^2), e = 1 - S r (the filter's 1/S); S[i] must be positive
+ * and normal. */
 argus_status argus_selftest_rcp(const double* S, int64_t n, double* out);
 
 /* *out = sum_i ln S[i] by the running mantissa product; *bad = 1 if some S[i]
