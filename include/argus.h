@@ -112,7 +112,8 @@ typedef struct argus_plan {
                                  lane: 48 B per TOA per resident lane, 144 B with
                                  ARGUS_NOISE_OU) */
     int32_t scan_elems;       /* ARGUS_MODE_SCAN: TOAs per thread, 1..4096; 0 = chosen from the
-                                 batch (about 4 warps per SM) */
+                                 batch (about 4 warps per SM, at most the longest
+                                 pulsar's TOAs / 32) */
     int32_t reserved;         /* must be 0 */
 } argus_plan;
 

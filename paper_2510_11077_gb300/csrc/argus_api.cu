@@ -350,6 +350,10 @@ argus_status ensure_scan(argus_array* h, int64_t B) {
         const int64_t work = B * h->total_toa;
         const int64_t warps = int64_t(std::max(h->n_sm, 1)) * 4;
         E = std::max<int64_t>(1, (work + 32 * warps - 1) / (32 * warps));
+        // no more TOAs per thread than the longest pulsar spreads over one
+        // chunk's 32 threads: a larger E only pads every chunk (and the
+        // adjoint's tape) with idle threads
+        E = std::min<int64_t>(E, std::max<int64_t>(1, (int64_t(h->n_max) + 31) / 32));
         E = std::min<int64_t>(E, 4096);
     }
     if (h->scan_B == B && h->scan_E == E) return ARGUS_OK;

@@ -221,3 +221,18 @@ def test_gradient_out_of_domain_replay_host_buffers_and_determinism(argus):
     assert ll_err(first[0][ok], ll_ref) <= LL_TOL and g_err(first[1][ok], g_ref) <= G_TOL
     ll2 = argus.argus_loglik(arr, th).cpu().numpy()        # the loglik-only path of the same plan
     assert ll_err(ll2, first[0]) <= 1e-12
+
+
+def test_large_batch_chunking_loglik_and_gradient(argus):
+    """1024 walkers on one 1000-TOA pulsar: the automatic chunking is capped
+    at the pulsar's TOAs / 32 per thread (one full chunk per lane); the scan
+    still agrees with the batched filter and its adjoint."""
+    data = inputs.make_array(np.array([1000]), seed=415)
+    theta = inputs.make_theta_batch(data, 1024, seed=11)
+    (ll, g), (ll_s, g_s) = scan_and_sequential(argus, data, theta)
+    assert ll_err(ll, ll_s) <= 1e-12 and g_err(g, g_s) <= G_SEQ_TOL
+    ll_ref, g_ref = kalman.loglik_grad(data, theta[:4])
+    assert ll_err(ll[:4], ll_ref) <= LL_TOL and g_err(g[:4], g_ref) <= G_TOL
+    arr = argus.argus_array_create(data)
+    arr.set_plan(mode=argus.ARGUS_MODE_SCAN)
+    assert ll_err(run_ll(argus, arr, theta), ll_s) <= 1e-12
