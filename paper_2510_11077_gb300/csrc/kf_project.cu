@@ -16,7 +16,8 @@ namespace {
 constexpr double kLn10 = 2.302585092994045684;
 constexpr double kTwoPi = 6.283185307179586477;
 constexpr double kPi = 3.141592653589793238;
-constexpr int kFewThreads = 128;   // one block of four warps per walker (k_project_few, k_reduce_few)
+constexpr int kFewThreads = 128;   // one block of four warps per walker (k_project_few)
+constexpr int kFewReduceThreads = 160;   // k_reduce_few: the four, and a fifth for the walker's ll
 constexpr int kFewTerms = 10;      // a pulsar's terms of the source-parameter gradient sums
 
 // light-travel time over one kiloparsec [s]: 1 pc = (648000 / pi) au,
@@ -220,7 +221,7 @@ __global__ void k_project(const double* __restrict__ theta, int64_t B, int32_t P
 // pulsar finishes its lane with the batched kernels' arithmetic.
 // ---------------------------------------------------------------------------
 // s[0, P): 10^(2 log10 sigma_p); s[P, 2P): 10^log10 gamma_p (Ornstein-Uhlenbeck).
-// Called by all 128 threads of the block.
+// Called by the block's first four warps (a fifth, if any, does nothing here).
 __device__ __forceinline__ void few_trig(const double* th, int P, const Layout& ly, FrameTrig& T,
                                          double* s) {
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
@@ -234,7 +235,7 @@ __device__ __forceinline__ void few_trig(const double* th, int P, const Layout& 
         if (l == 0) sincos(th[5], &T.sa, &T.ca);
     } else if (w == 2) {
         if (l == 0) sincos(th[2], &T.sp, &T.cp);
-    } else {
+    } else if (w == 3) {
         const int n = ly.ou ? 2 * P : P;
         for (int i = l; i < n; i += 32) {
             const int p = i < P ? i : i - P;
@@ -381,9 +382,10 @@ __global__ void k_reduce(const double* __restrict__ theta, int64_t B, int32_t P,
 }
 
 // K4 with the gradient for a few walkers (see k_project_few): the walker's
-// frame and the pulsars' exponentials on four warps at once, each pulsar's
-// terms on its own thread, and the sums over pulsars in pulsar order on one.
-__global__ void __launch_bounds__(kFewThreads) k_reduce_few(const double* __restrict__ theta, int64_t B,
+// frame and the pulsars' exponentials on four warps at once while a fifth
+// sums the walker's log-likelihood, each pulsar's terms on its own thread,
+// and the sums over pulsars in pulsar order on one.
+__global__ void __launch_bounds__(kFewReduceThreads) k_reduce_few(const double* __restrict__ theta, int64_t B,
                                                            int32_t P, int32_t flags,
                                                            const PulsarDev* __restrict__ psr,
                                                            const double* __restrict__ lane_out,
@@ -399,7 +401,7 @@ __global__ void __launch_bounds__(kFewThreads) k_reduce_few(const double* __rest
     const int D = kNgw + nq * P;
     const int64_t lanes = B * P;
     const double* th = theta + b * D;
-    if (threadIdx.x == 0) s_good = walker_ll(th, b, B, P, ly, lane_out, loglik, lane_ll) ? 1 : 0;
+    if (threadIdx.x == 4 * 32) s_good = walker_ll(th, b, B, P, ly, lane_out, loglik, lane_ll) ? 1 : 0;
     few_trig(th, P, ly, T, s_few);
     __syncthreads();
     double* gout = grad + b * D;
@@ -470,8 +472,8 @@ void launch_reduce_few(const double* theta, int64_t B, int32_t P, int32_t flags,
                        const double* lane_out, double* loglik, double* grad, double* lane_ll,
                        cudaStream_t s) {
     const size_t smem = size_t(2 + kFewTerms) * P * sizeof(double);
-    k_reduce_few<<<unsigned(B), kFewThreads, smem, s>>>(theta, B, P, flags, psr, lane_out, loglik, grad,
-                                                        lane_ll);
+    k_reduce_few<<<unsigned(B), kFewReduceThreads, smem, s>>>(theta, B, P, flags, psr, lane_out, loglik,
+                                                              grad, lane_ll);
 }
 
 void launch_reduce(const double* theta, int64_t B, int32_t P, int32_t flags, const PulsarDev* psr,

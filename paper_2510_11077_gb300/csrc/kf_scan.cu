@@ -333,16 +333,21 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_chunks(ScanArgs a) {
 
 // Filtered state at TOA k_lo - 1 for thread t of a chunk whose TOAs start
 // at k_lo > 0: the chunk's prefix x the earlier threads of the chunk (the
-// lane's first chunk has no prefix).
+// lane's first chunk has no prefix).  Only the b and C fields of that
+// combine are formed (parts 0 and 1; A is dead code), bit for bit those of
+// the whole combine.
 __device__ __forceinline__ State prefix_state(const ScanArgs& a, const ScanItem& it, int t) {
-    SElem pre;
     if (t == 0) {
-        pre = load_elem(a.bpre + int64_t(blockIdx.x) * kScanElem);
-    } else {
-        pre = load_elem(a.tpre + (int64_t(blockIdx.x) * 32 + t - 1) * kScanElem);
-        if (it.k0 > 0) pre = scan_combine(load_elem(a.bpre + int64_t(blockIdx.x) * kScanElem), pre);
+        const SElem pre = load_elem(a.bpre + int64_t(blockIdx.x) * kScanElem);
+        return State{pre.b0, pre.b1, pre.C00, pre.C01, pre.C11};
     }
-    return State{pre.b0, pre.b1, pre.C00, pre.C01, pre.C11};
+    const SElem th = load_elem(a.tpre + (int64_t(blockIdx.x) * 32 + t - 1) * kScanElem);
+    if (it.k0 == 0) return State{th.b0, th.b1, th.C00, th.C01, th.C11};
+    const SElem ch = load_elem(a.bpre + int64_t(blockIdx.x) * kScanElem);
+    double o[kScanElem];
+    scan_combine_part<0>(ch, th, o);
+    scan_combine_part<1>(ch, th, o);
+    return State{o[4], o[5], o[6], o[7], o[8]};
 }
 
 // The chunk's (sum e^2/S, sum ln S) by warp sums; the block that completes its
