@@ -218,6 +218,8 @@ def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
         return 0
+    import numpy as np
+
     from oracle import kalman
     from paper_2510_11077_gb300 import inputs
     w = inputs.WORKLOADS[args.workload]
@@ -226,11 +228,15 @@ def run_reference(args):
     cores = os.cpu_count() or 1
     kalman.set_threads(cores)
     per_step = cores * 2
+
+    def sample(i):   # step i's walkers, wrapping around a batch smaller than the sample
+        return theta[(i * per_step + np.arange(per_step)) % len(theta)]
+
     for i in range(args.warmup):
-        kalman.loglik_grad(data, theta[:per_step])
+        kalman.loglik_grad(data, sample(i))
     t0 = time.perf_counter()
     for i in range(args.steps):
-        kalman.loglik_grad(data, theta[i * per_step:(i + 1) * per_step])
+        kalman.loglik_grad(data, sample(i))
     dt = time.perf_counter() - t0
     value = args.steps * per_step / dt
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
