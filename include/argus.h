@@ -36,8 +36,12 @@
  *   pulsar's block (D = 7 + 3P or 7 + 4P).
  * Out-of-domain vectors (a non-finite entry, EFAC <= 0, d_p <= 0, |cos iota| > 1,
  * |sin delta| > 1) and filters that meet a non-positive or non-finite
- * innovation variance give loglik = -inf and a zero gradient for that walker;
- * the call still returns ARGUS_OK.
+ * innovation variance give loglik = -inf and a zero gradient for that walker.
+ * -inf is the per-walker flag a sampler's accept test needs; argus_walker_flags
+ * tells the two causes apart.  An out-of-domain vector is an ordinary
+ * rejection (status ARGUS_OK); a filter failure in a call whose loglik is host
+ * memory (which synchronises anyway) returns ARGUS_ERR_NONFINITE after writing
+ * every output.
  *
  * Pointers: theta, loglik and grad may each be device memory or host memory
  * (pinned or pageable); the library asks CUDA which.  With device pointers a
@@ -61,7 +65,11 @@ typedef enum argus_status {
     ARGUS_ERR_INVALID_ARG = 1,   /* rejected on the host before any launch */
     ARGUS_ERR_CUDA = 2,          /* a CUDA call failed; see argus_last_error() */
     ARGUS_ERR_OOM = 3,           /* device allocation failed */
-    ARGUS_ERR_NONFINITE = 4,     /* reserved: reported through loglik = -inf instead */
+    ARGUS_ERR_NONFINITE = 4,     /* a call with host outputs: some walker's filter met an
+                                    innovation variance S_k that is not a positive normal
+                                    finite number; its loglik is -inf, its gradient 0, and
+                                    the other walkers' results are valid (asynchronous
+                                    device-pointer calls: see argus_walker_flags) */
     ARGUS_ERR_TIMEOUT = 5,       /* a bounded device-side wait gave up */
     ARGUS_ERR_UNSUPPORTED = 6    /* no sm_103a device, or a size beyond a documented limit */
 } argus_status;
@@ -109,7 +117,7 @@ typedef struct argus_plan {
     int32_t tape_cache;       /* adjoint: 0 = re-run each segment from its checkpoint (memory
                                  O(sqrt N) per lane); 1 = also keep every segment's tape in HBM
                                  during the forward pass and skip the re-run (memory O(N) per
-                                 lane: 48 B per TOA per resident lane, 144 B with
+                                 lane: 40 B per TOA per resident lane, 136 B with
                                  ARGUS_NOISE_OU) */
     int32_t scan_elems;       /* ARGUS_MODE_SCAN: TOAs per thread, 1..4096; 0 = chosen from the
                                  batch (about 4 warps per SM, at most the longest
@@ -149,6 +157,9 @@ int32_t argus_array_dim(const argus_array* array);
 /* The handle's model flags (ARGUS_NOISE_* | ARGUS_PULSAR_TERM); -1 for NULL. */
 int32_t argus_array_model(const argus_array* array);
 
+/* The CUDA device ordinal the handle lives on; -1 for NULL. */
+int32_t argus_array_device(const argus_array* array);
+
 /* Replace / read the scheduling plan.  set_plan validates every field and
  * drops captured graphs; get_plan copies the current plan into *plan. */
 argus_status argus_array_set_plan(argus_array* array, const argus_plan* plan);
@@ -183,7 +194,8 @@ argus_status argus_loglik_grad(argus_array* array, const double* theta, int64_t 
  * plus at least one block's checkpoint and tape slot) is rejected with
  * ARGUS_ERR_UNSUPPORTED and a message giving the bytes needed.
  * The first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any stream
+ * device, with that device current, and again after the device's context has
+ * changed, e.g. after a device reset); make that first call before any stream
  * capture.  Every call shares the one array and leaves its contents behind;
  * calls whose work overlaps on the GPU (other streams, other host threads,
  * other handles on the same device) race on it and must be serialised by
@@ -198,6 +210,15 @@ argus_status argus_loglik_grad_noalloc(argus_array* array, const double* theta, 
  * log10 h0] (host, 7 doubles).  s: host array of sum_p N_p doubles in the
  * pulsars' order.  Synchronous.  For simulating or subtracting a source. */
 argus_status argus_cw_signal(argus_array* array, const double* theta_gw, double* s);
+
+/* Per-walker status of a finished call, for asynchronous callers (device
+ * pointers theta [B][D], loglik [B] as the call wrote it, flags [B] int32):
+ * flags[b] = 0 if loglik[b] is finite, 1 if theta_b lies outside the domain
+ * above, 2 if theta_b is in the domain but the filter met an innovation
+ * variance that is not a positive normal finite number (the
+ * ARGUS_ERR_NONFINITE condition).  Enqueued on `stream`. */
+argus_status argus_walker_flags(argus_array* array, const double* theta, int64_t B,
+                                const double* loglik, int32_t* flags, void* stream);
 
 /* Per-(walker, pulsar) terms, for inspection: lane_ll [B][P] doubles (device
  * or host) receives ll_p(theta_b).  Same rules as argus_loglik. */

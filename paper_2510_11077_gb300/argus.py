@@ -107,6 +107,7 @@ def load(build_if_missing: bool = False):
     lib.argus_loglik_grad.argtypes = [vp, dp, ctypes.c_int64, dp, dp, vp]
     lib.argus_loglik_grad.restype = ctypes.c_int
     lib.argus_lane_loglik.argtypes = [vp, dp, ctypes.c_int64, dp, vp]
+    lib.argus_walker_flags.argtypes = [vp, dp, ctypes.c_int64, dp, vp, vp]
     lib.argus_lane_loglik.restype = ctypes.c_int
     lib.argus_loglik_grad_noalloc.argtypes = [vp, dp, ctypes.c_int64, dp, dp, vp]
     lib.argus_loglik_grad_noalloc.restype = ctypes.c_int
@@ -135,8 +136,10 @@ def load(build_if_missing: bool = False):
     return lib
 
 
-def _check(st: int) -> None:
-    if st != 0:
+def _check(st: int, allow_nonfinite: bool = False) -> None:
+    """Raise on a non-OK status.  allow_nonfinite: accept ARGUS_ERR_NONFINITE,
+    whose outputs are all written (the failing walkers hold -inf)."""
+    if st != 0 and not (allow_nonfinite and st == 4):
         raise ArgusError(st, _lib.argus_last_error().decode())
 
 
@@ -315,17 +318,19 @@ def _prep(theta, dim):
     return theta
 
 
-def argus_loglik(array: Array, theta, loglik=None, stream=None):
+def argus_loglik(array: Array, theta, loglik=None, stream=None, strict=False):
+    """strict: raise ArgusError on ARGUS_ERR_NONFINITE (host outputs and a
+    walker whose filter failed) instead of returning its -inf."""
     theta = _prep(theta, array.dim)
     B = theta.shape[0]
     if loglik is None:
         loglik = _new_like(theta, (B,))
     s = stream if stream is not None else _stream_of(theta, loglik)
-    _check(_lib.argus_loglik(array.handle, _ptr(theta), B, _ptr(loglik), s))
+    _check(_lib.argus_loglik(array.handle, _ptr(theta), B, _ptr(loglik), s), not strict)
     return loglik
 
 
-def argus_loglik_grad(array: Array, theta, loglik=None, grad=None, stream=None):
+def argus_loglik_grad(array: Array, theta, loglik=None, grad=None, stream=None, strict=False):
     theta = _prep(theta, array.dim)
     B = theta.shape[0]
     if loglik is None:
@@ -333,8 +338,22 @@ def argus_loglik_grad(array: Array, theta, loglik=None, grad=None, stream=None):
     if grad is None:
         grad = _new_like(theta, (B, array.dim))
     s = stream if stream is not None else _stream_of(theta, loglik, grad)
-    _check(_lib.argus_loglik_grad(array.handle, _ptr(theta), B, _ptr(loglik), _ptr(grad), s))
+    _check(_lib.argus_loglik_grad(array.handle, _ptr(theta), B, _ptr(loglik), _ptr(grad), s),
+           not strict)
     return loglik, grad
+
+
+def argus_walker_flags(array: Array, theta, loglik, flags=None, stream=None):
+    """Per-walker status of a finished call (device tensors): 0 finite, 1 theta
+    out of the domain, 2 the filter met a bad innovation variance."""
+    import torch
+    theta = _prep(theta, array.dim)
+    if flags is None:
+        flags = torch.empty(theta.shape[0], dtype=torch.int32, device=theta.device)
+    s = stream if stream is not None else _stream_of(theta, loglik, flags)
+    _check(_lib.argus_walker_flags(array.handle, _ptr(theta), theta.shape[0], _ptr(loglik),
+                                   _ptr(flags), s))
+    return flags
 
 
 def argus_loglik_grad_noalloc(array: Array, theta, loglik, grad, stream=None):

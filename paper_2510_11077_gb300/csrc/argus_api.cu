@@ -167,6 +167,7 @@ struct argus_array {
     double* d_ckpt = nullptr;      size_t cap_ckpt = 0;
     double* d_tape = nullptr;      size_t cap_tape = 0;
     int* d_counter = nullptr;
+    int* d_any2 = nullptr;         // host-pointer calls: some walker's filter met a bad variance
     // time-parallel filter (ARGUS_MODE_SCAN)
     ScanItem* d_sitems = nullptr;  size_t cap_sitems = 0;
     int32_t* d_lane_first = nullptr; size_t cap_lane_first = 0;
@@ -308,7 +309,8 @@ argus_status ensure_batch(argus_array* h, int64_t B, int W, int grid, bool grad)
     if ((st = grow(&h->d_lc, &h->cap_lc, lanes * kLaneConsts))) return st;
     if ((st = grow(&h->d_lane, &h->cap_lane, lanes * (1 + kLaneGrads)))) return st;
     if (grad) {
-        const size_t ck = size_t(h->nseg_max) * kCkptDoubles * W * grid;
+        // the cached tape needs no checkpoints (K3 writes none with it)
+        const size_t ck = h->plan.tape_cache ? 1 : size_t(h->nseg_max) * kCkptDoubles * W * grid;
         const size_t tp_len = h->plan.tape_cache ? size_t(std::max(h->n_max, 1)) : size_t(h->stride_max);
         const size_t tp = tp_len * tape_doubles(h->model) * W * grid;
         if ((st = grow(&h->d_ckpt, &h->cap_ckpt, std::max<size_t>(ck, 1)))) return st;
@@ -401,7 +403,7 @@ argus_status ensure_scan(argus_array* h, int64_t B) {
 argus_status ensure_scan_grad(argus_array* h, int64_t B) {
     const size_t ni = std::max<size_t>(size_t(h->n_sitems), 1);
     const size_t lanes = std::max<size_t>(size_t(B) * h->P, 1);
-    const size_t tape = ni * 32 * size_t(h->scan_E) * size_t(tape_doubles(h->model));
+    const size_t tape = ni * 32 * size_t(h->scan_E) * size_t(scan_tape_doubles(h->model));
     void* before[6] = {h->d_stape, h->d_tsuf, h->d_ragg, h->d_rpre, h->d_partg, h->d_rdone};
     argus_status st;
     if ((st = grow(&h->d_stape, &h->cap_stape, tape))) return st;
@@ -613,6 +615,15 @@ argus_status evaluate(argus_array* h, const double* theta, int64_t B, double* ll
                           : run_batched(h, th_d, B, ll_d, g_d, lane_d, s);
     if (st) return st;
     if (staged) {
+        // a synchronous call can report the filter's numerical failures as a status
+        int any2 = 0;
+        const bool report = ll != nullptr;
+        if (report) {
+            CK(cudaMemsetAsync(h->d_any2, 0, sizeof(int), s));
+            launch_walker_flags(th_d, B, h->P, h->flags, ll_d, nullptr, h->d_any2, s);
+            CK(cudaGetLastError());
+            CK(cudaMemcpyAsync(&any2, h->d_any2, sizeof(int), cudaMemcpyDeviceToHost, s));
+        }
         if (ll && !dev_ll)
             CK(cudaMemcpyAsync(ll, ll_d, sizeof(double) * B, cudaMemcpyDeviceToHost, s));
         if (grad && !dev_g)
@@ -620,6 +631,11 @@ argus_status evaluate(argus_array* h, const double* theta, int64_t B, double* ll
         if (lane && !dev_l)
             CK(cudaMemcpyAsync(lane, lane_d, sizeof(double) * B * h->P, cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
+        if (any2)
+            return fail(ARGUS_ERR_NONFINITE,
+                        "a walker's filter met an innovation variance that is not a positive normal "
+                        "finite number: its loglik is -inf and its gradient 0; the other walkers' "
+                        "results are valid");
     }
     return ARGUS_OK;
 }
@@ -706,6 +722,8 @@ argus_status argus_array_create_ex(const argus_pulsar* psrs, int32_t n_pulsars, 
         return cleanup(cuda_fail(e, "cudaMalloc(pulsars)"));
     if ((e = cudaMalloc(&h->d_counter, sizeof(int))) != cudaSuccess)
         return cleanup(cuda_fail(e, "cudaMalloc(counter)"));
+    if ((e = cudaMalloc(&h->d_any2, sizeof(int))) != cudaSuccess)
+        return cleanup(cuda_fail(e, "cudaMalloc(status flag)"));
     if ((e = cudaMalloc(&h->d_phase_tab, sizeof(double) * kPhaseTableDoubles)) != cudaSuccess)
         return cleanup(cuda_fail(e, "cudaMalloc(phase table)"));
     launch_fill_phase_table(h->d_phase_tab, nullptr);
@@ -735,6 +753,7 @@ void argus_array_destroy(argus_array* h) {
     cudaFree(h->d_ckpt);
     cudaFree(h->d_tape);
     cudaFree(h->d_counter);
+    cudaFree(h->d_any2);
     cudaFree(h->d_stage);
     cudaFree(h->d_sitems);
     cudaFree(h->d_lane_first);
@@ -753,6 +772,8 @@ void argus_array_destroy(argus_array* h) {
 }
 
 int32_t argus_array_dim(const argus_array* h) { return h ? kNgw + h->nq * h->P : -1; }
+
+int32_t argus_array_device(const argus_array* h) { return h ? h->device : -1; }
 
 int32_t argus_array_model(const argus_array* h) {
     if (!h) return -1;
@@ -786,6 +807,21 @@ argus_status argus_loglik_grad(argus_array* h, const double* theta, int64_t B, d
                                double* grad, void* stream) {
     if (B > 0 && (!loglik || !grad)) return fail(ARGUS_ERR_INVALID_ARG, "loglik or grad is NULL");
     return evaluate(h, theta, B, loglik, grad, nullptr, stream);
+}
+
+argus_status argus_walker_flags(argus_array* h, const double* theta, int64_t B, const double* loglik,
+                                int32_t* flags, void* stream) {
+    if (!h) return fail(ARGUS_ERR_INVALID_ARG, "array handle is NULL");
+    if (B < 0) return fail(ARGUS_ERR_INVALID_ARG, "B must be >= 0");
+    if (B == 0) return ARGUS_OK;
+    if (!theta || !loglik || !flags) return fail(ARGUS_ERR_INVALID_ARG, "NULL theta, loglik or flags");
+    DeviceGuard guard(h->device);
+    if (!is_device_ptr(theta) || !is_device_ptr(loglik) || !is_device_ptr(flags))
+        return fail(ARGUS_ERR_INVALID_ARG, "argus_walker_flags needs device pointers");
+    launch_walker_flags(theta, B, h->P, h->flags, loglik, flags, nullptr,
+                        reinterpret_cast<cudaStream_t>(stream));
+    CK(cudaGetLastError());
+    return ARGUS_OK;
 }
 
 argus_status argus_lane_loglik(argus_array* h, const double* theta, int64_t B, double* lane_ll,
@@ -878,6 +914,7 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 std::mutex g_noalloc_mu;
 void* g_noalloc_addr[kNoAllocMaxDevices] = {};
+void* g_noalloc_ctx[kNoAllocMaxDevices] = {};   // the context each address was looked up in
 
 __global__ void k_noalloc_items(WorkItem* items, int n_items, int64_t tiles, int W) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -887,17 +924,38 @@ __global__ void k_noalloc_items(WorkItem* items, int n_items, int64_t tiles, int
 
 size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
 
-// Device address of the scratch array on the current device; looked up once
-// per device (the array's name in host code is only a host-side stand-in).
+// The current CUDA context (driver entry point, looked up once), or nullptr.
+void* current_context() {
+    using GetCtx = int (*)(void**);
+    static GetCtx fn = []() -> GetCtx {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return nullptr;
+        return reinterpret_cast<GetCtx>(f);
+    }();
+    void* ctx = nullptr;
+    if (!fn || fn(&ctx) != 0) return nullptr;
+    return ctx;
+}
+
+// Device address of the scratch array on the current device (the array's name
+// in host code is only a host-side stand-in).  Looked up once per device, and
+// again if the device's context has changed since (a device reset destroys the
+// primary context, and the module, with the array, loads again elsewhere).
 argus_status noalloc_scratch(int dev, unsigned char** out) {
     if (dev < 0 || dev >= kNoAllocMaxDevices)
         return fail(ARGUS_ERR_UNSUPPORTED, "device ordinal beyond the no-alloc table");
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_addr[dev]) {
+    void* ctx = current_context();
+    if (!g_noalloc_addr[dev] || !ctx || ctx != g_noalloc_ctx[dev]) {
         void* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(no-alloc scratch)");
         g_noalloc_addr[dev] = p;
+        g_noalloc_ctx[dev] = ctx;
     }
     *out = static_cast<unsigned char*>(g_noalloc_addr[dev]);
     return ARGUS_OK;

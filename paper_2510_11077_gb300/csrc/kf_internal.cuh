@@ -9,9 +9,13 @@ namespace argus {
 constexpr int kNgw = 7;          // continuous-wave parameters at the head of theta
 constexpr int kRecDoubles = 8;   // doubles per staged TOA record
 constexpr int kCkptDoubles = 5;  // (m0, m1, p00, p01, p11) per checkpoint
-constexpr int kTapeDoubles = 6;  // (R/S, K1, e/S, (e/S)^2 - 1/S, sin, cos) per step of a segment
-constexpr int kTapeDoublesOU = 18; // ... plus (m1, p01 + b p11, a p11) before the step, the
+constexpr int kTapeDoubles = 5;  // (R/S, K1, e/S, (e/S)^2 - 1/S, phase fraction) per step (K3)
+constexpr int kTapeDoublesOU = 17; // ... plus (m1, p01 + b p11, a p11) before the step, the
                                    // transition a, b, Q / sigma^2 (3) and d/dgamma of b, Q (4)
+// The time-parallel adjoint's tape keeps sin and cos themselves in place of
+// the phase fraction (its steps are latency-bound, not FP64-bound).
+constexpr int kScanTapeDoubles = 6;
+constexpr int kScanTapeDoublesOU = 18;
 constexpr int kMaxStride = 256;  // longest adjoint segment, in TOAs
 constexpr int kLaneConsts = 8;   // A, B, f, Phi0/(2 pi), sigma^2, EFAC^2, EFAC, gamma
 constexpr int kLaneGrads = 7;    // dll/dA, dB, t-weighted sin and cos sums, dsigma^2, EFAC term,
@@ -29,6 +33,9 @@ __host__ __device__ inline int params_per_pulsar(int32_t flags) {
 }
 inline int tape_doubles(int32_t noise_model) {
     return noise_model == kOrnsteinUhlenbeck ? kTapeDoublesOU : kTapeDoubles;
+}
+inline int scan_tape_doubles(int32_t noise_model) {
+    return noise_model == kOrnsteinUhlenbeck ? kScanTapeDoublesOU : kScanTapeDoubles;
 }
 
 // One staged TOA record (8 doubles = 64 bytes, 16-byte aligned):

@@ -83,30 +83,37 @@ __device__ __forceinline__ void kf_step_adjoint(Adjoint& a, const StepOut& so,
     }
 }
 
-// One step's tape record, field-major within the step: [field][W].
+// One step's tape record, field-major within the step: [field][W].  The
+// signal's sin and cos are not stored: the record keeps the phase fraction F
+// (8 bytes, bit pattern in a double slot) and tape_get forms them again with
+// sincos_frac, which runs on the integer and FP32 pipes only -- in the
+// shadow of the FP64 pipe, which bounds this kernel -- and gives the same
+// bits as the forward step.
 template <bool kOU>
 __device__ __forceinline__ void tape_put(double* tk, int W, const StepOut& so) {
     tk[0 * W] = so.w; tk[1 * W] = so.K1; tk[2 * W] = so.g;
-    tk[3 * W] = so.h2; tk[4 * W] = so.sn; tk[5 * W] = so.cs;
+    tk[3 * W] = so.h2; tk[4 * W] = __longlong_as_double(static_cast<long long>(so.F));
     if (kOU) {
-        tk[6 * W] = so.m1; tk[7 * W] = so.t1; tk[8 * W] = so.ap11;
-        tk[9 * W] = so.a; tk[10 * W] = so.b; tk[11 * W] = so.c00; tk[12 * W] = so.c01;
-        tk[13 * W] = so.c11; tk[14 * W] = so.db; tk[15 * W] = so.dc00; tk[16 * W] = so.dc01;
-        tk[17 * W] = so.dc11;
+        tk[5 * W] = so.m1; tk[6 * W] = so.t1; tk[7 * W] = so.ap11;
+        tk[8 * W] = so.a; tk[9 * W] = so.b; tk[10 * W] = so.c00; tk[11 * W] = so.c01;
+        tk[12 * W] = so.c11; tk[13 * W] = so.db; tk[14 * W] = so.dc00; tk[15 * W] = so.dc01;
+        tk[16 * W] = so.dc11;
     }
 }
 
 template <bool kOU>
-__device__ __forceinline__ StepOut tape_get(const double* tk, int W) {
+__device__ __forceinline__ StepOut tape_get(const double* tk, int W, PhaseTable tab) {
     StepOut so{};
     so.w = tk[0 * W]; so.K1 = tk[1 * W]; so.g = tk[2 * W];
-    so.h2 = tk[3 * W]; so.sn = tk[4 * W]; so.cs = tk[5 * W];
+    so.h2 = tk[3 * W];
+    so.F = static_cast<uint64_t>(__double_as_longlong(tk[4 * W]));
     if (kOU) {
-        so.m1 = tk[6 * W]; so.t1 = tk[7 * W]; so.ap11 = tk[8 * W];
-        so.a = tk[9 * W]; so.b = tk[10 * W]; so.c00 = tk[11 * W]; so.c01 = tk[12 * W];
-        so.c11 = tk[13 * W]; so.db = tk[14 * W]; so.dc00 = tk[15 * W]; so.dc01 = tk[16 * W];
-        so.dc11 = tk[17 * W];
+        so.m1 = tk[5 * W]; so.t1 = tk[6 * W]; so.ap11 = tk[7 * W];
+        so.a = tk[8 * W]; so.b = tk[9 * W]; so.c00 = tk[10 * W]; so.c01 = tk[11 * W];
+        so.c11 = tk[12 * W]; so.db = tk[13 * W]; so.dc00 = tk[14 * W]; so.dc01 = tk[15 * W];
+        so.dc11 = tk[16 * W];
     }
+    sincos_frac(so.F, tab, so.sn, so.cs);
     return so;
 }
 
@@ -189,12 +196,13 @@ __global__ void __launch_bounds__(256) k_filter_fwd(FilterArgs a) {
 // Pass 1 runs the filter forward segment by segment (stride TOAs each) and
 // checkpoints the state at the start of every segment.  Pass 2 walks the
 // segments backwards: restore the checkpoint, re-run the segment forward
-// recording (R/S, K1, e/S, (e/S)^2 - 1/S, sin, cos) per step in the block's tape, then
-// run the adjoint steps in reverse.  Checkpoints and tape live in the block's
-// own slot of global scratch ([..][field][W], so a warp's accesses coalesce).
-// With kCache the tape of every segment is written during pass 1 and kept in
-// HBM (the slot holds the whole pulsar), so pass 2 skips the re-run: HBM
-// traffic is traded for FP64 work, which is the scarce resource here.
+// recording (R/S, K1, e/S, (e/S)^2 - 1/S, phase fraction) per step in the
+// block's tape, then run the adjoint steps in reverse.  Checkpoints and tape
+// live in the block's own slot of global scratch ([..][field][W], so a warp's
+// accesses coalesce).  With kCache the tape of every segment is written during
+// pass 1 and kept in HBM (the slot holds the whole pulsar), so pass 2 skips the
+// re-run and pass 1 writes no checkpoints: HBM traffic is traded for FP64
+// work, which is the scarce resource here.
 // ---------------------------------------------------------------------------
 template <bool kCache, bool kOU>
 __global__ void __launch_bounds__(256) k_filter_grad(FilterArgs a) {
@@ -227,8 +235,11 @@ __global__ void __launch_bounds__(256) k_filter_grad(FilterArgs a) {
             stage_records(sm.rec, a.rec + (ps.off + k0) * kRecDoubles, cnt);
             __syncthreads();
             if (active) {
-                double* cp = ck + int64_t(seg) * kCkptDoubles * W;
-                cp[0 * W] = x.m0; cp[1 * W] = x.m1; cp[2 * W] = x.p00; cp[3 * W] = x.p01; cp[4 * W] = x.p11;
+                if (!kCache) {   // the cached tape needs no checkpoints
+                    double* cp = ck + int64_t(seg) * kCkptDoubles * W;
+                    cp[0 * W] = x.m0; cp[1 * W] = x.m1; cp[2 * W] = x.p00; cp[3 * W] = x.p01;
+                    cp[4 * W] = x.p11;
+                }
                 for (int k = 0; k < cnt; ++k) {
                     kf_step<kCache, true, kOU>(x, sm.rec + k * kRecDoubles, L, sm.tab, quad, lp, so);
                     if (kCache) tape_put<kOU>(tp + int64_t(k0 + k) * kTd * W, W, so);
@@ -257,7 +268,7 @@ __global__ void __launch_bounds__(256) k_filter_grad(FilterArgs a) {
                     }
                 }
                 for (int k = cnt - 1; k >= 0; --k) {
-                    const StepOut sk = tape_get<kOU>(ts + int64_t(k) * kTd * W, W);
+                    const StepOut sk = tape_get<kOU>(ts + int64_t(k) * kTd * W, W, sm.tab);
                     kf_step_adjoint<kOU>(adj, sk, sm.rec + k * kRecDoubles, L, g);
                 }
             }

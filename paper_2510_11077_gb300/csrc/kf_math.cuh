@@ -127,15 +127,16 @@ __device__ __forceinline__ void fill_phase_table(PhaseTable tab) {
     }
 }
 
-// sin(2 pi x), cos(2 pi x) for x in cycles.  With x = j/256 + a/(2 pi):
+// sin(2 pi x), cos(2 pi x) for x in cycles, given F = frac(x) 2^64 (so that a
+// caller may keep the 8-byte F and form sin/cos again later, on the integer
+// and FP32 pipes only).  With x = j/256 + a/(2 pi):
 //   sin = S_j + [S_j (cos a - 1) + C_j sin a],  cos = C_j + [C_j (cos a - 1) - S_j sin a],
 // the brackets (|.| <= 0.013) in double-float; each node + bracket summed in
 // 2^-62 fixed point (the bracket's two floats each rounded to 2^-63) and
 // rounded once to a double: within 0.5 ulp + 2^-62 of node + bracket.  (A
 // result below ~2^-40 in magnitude keeps its absolute, not its relative,
 // accuracy.)
-__device__ __forceinline__ void phase_sincos(double x, PhaseTable tab, double& sn, double& cs) {
-    const uint64_t F = frac_cycles_u64(x);
+__device__ __forceinline__ void sincos_frac(uint64_t F, PhaseTable tab, double& sn, double& cs) {
     const uint64_t j = (F + (1ull << 55)) >> 56;                 // nearest table node
     const long long d = static_cast<long long>(F - (j << 56));   // |d| <= 2^55
     // d exactly as a sum of three floats, then to radians: a = 2 pi 2^-64 d
@@ -166,6 +167,11 @@ __device__ __forceinline__ void phase_sincos(double x, PhaseTable tab, double& s
     cs = fix62_to_double(td.y + f2fix62(corr_c.hi) + f2fix62(corr_c.lo));
 }
 
+// The same from the phase itself: F = frac(x) 2^64, then sincos_frac.
+__device__ __forceinline__ void phase_sincos(double x, PhaseTable tab, double& sn, double& cs) {
+    sincos_frac(frac_cycles_u64(x), tab, sn, cs);
+}
+
 // 1/S for a positive normal S: the approximate reciprocal (measured within
 // 2^-19.9) refined by one third-order step, r (1 + e + e^2) with e = 1 - S r:
 // the exact result is (1/S)(1 - e^3), so only the last rounding remains.
@@ -177,6 +183,9 @@ __device__ __forceinline__ double rcp_nr(double S) {
 }
 
 // Running sum of ln S_k: mantissa product in [1, 2) and an integer exponent.
+// S_k's own exponent goes to the integer first and only its mantissa m in
+// [1, 2) is multiplied in, so the product (in [1, 4)) can neither overflow
+// nor underflow for any normal S_k; the rounding is that of pr * S_k.
 struct LogProd {
     double pr = 1.0;
     int ex = 0;
@@ -184,9 +193,10 @@ struct LogProd {
     __device__ __forceinline__ void add(double S) {
         const unsigned hs = unsigned(__double2hiint(S));
         bad |= (hs - 0x00100000u) >= (0x7ff00000u - 0x00100000u) ? 1u : 0u;
-        const double p = pr * S;
+        const double m = __hiloint2double(int((hs & 0x000fffffu) | 0x3ff00000u), __double2loint(S));
+        const double p = pr * m;
         const int hi = __double2hiint(p);
-        ex += ((hi >> 20) & 0x7ff) - 1023;
+        ex += int((hs >> 20) & 0x7ffu) - 1023 + (((hi >> 20) & 0x7ff) - 1023);
         pr = __hiloint2double((hi & 0x800fffff) | 0x3ff00000, __double2loint(p));
     }
     __device__ __forceinline__ double value() const {

@@ -152,6 +152,7 @@ __device__ __forceinline__ void load_lane(const FilterArgs& a, int p, int64_t b,
 struct StepOut {   // what the adjoint needs from the forward step
     // w = R/S = 1 - K0, K1 = M01/S, g = e/S, h2 = g^2 - 1/S (= -(1 - e^2/S)/S)
     double w, K1, g, h2, sn, cs;
+    uint64_t F;    // the phase's fraction in 2^-64 cycles (sin, cos follow from it: sincos_frac)
     // Ornstein-Uhlenbeck only: m1, p01 + b p11 and a p11 before the step, the
     // transition a, b, Q / sigma^2 and the gamma-derivatives of b and Q / sigma^2
     double m1, t1, ap11;
@@ -202,7 +203,8 @@ __device__ __forceinline__ void kf_step(State& x, const double* __restrict__ rec
     }
     // signal at phase f t + Phi0/(2 pi) cycles
     double sn, cs;
-    phase_sincos(fma(L.f, t, L.phc), tab, sn, cs);
+    const uint64_t F = frac_cycles_u64(fma(L.f, t, L.phc));
+    sincos_frac(F, tab, sn, cs);
     // innovation e = r - (A sin + B cos) - m0
     const double e = fma(-L.A, sn, fma(-L.B, cs, r - m0));
     const double R = fma(L.efac2, s2k, L.equad2);
@@ -218,7 +220,7 @@ __device__ __forceinline__ void kf_step(State& x, const double* __restrict__ rec
     x.p01 = M01 * w;
     x.p11 = fma(-K1, M01, M11);
     if (kTape) {
-        so.w = w; so.K1 = K1; so.g = g; so.h2 = fma(g, g, -rS); so.sn = sn; so.cs = cs;
+        so.w = w; so.K1 = K1; so.g = g; so.h2 = fma(g, g, -rS); so.sn = sn; so.cs = cs; so.F = F;
     }
     if (kLL) {
         quad = fma(e, g, quad);

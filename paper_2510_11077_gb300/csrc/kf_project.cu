@@ -8,6 +8,7 @@
 
 #include "kf_internal.cuh"
 #include "kf_few.cuh"
+#include "lib_internal.cuh"
 
 namespace argus {
 
@@ -425,6 +426,23 @@ __global__ void __launch_bounds__(kFewReduceThreads) k_reduce_few(const double* 
     }
 }
 
+// Per-walker status of a finished call: 0 = finite log-likelihood, 1 = theta
+// outside the domain, 2 = theta in the domain but the filter met an innovation
+// variance that is not a positive normal finite number (or the sum is not
+// finite).  Bit 0 of *any2 is set if some walker has status 2.
+__global__ void k_walker_flags(const double* __restrict__ theta, int64_t B, int32_t P, int32_t flags,
+                               const double* __restrict__ loglik, int32_t* __restrict__ out,
+                               int* __restrict__ any2) {
+    const int64_t b = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    const Layout ly(flags);
+    const int D = kNgw + ly.nq * P;
+    int32_t f = 0;
+    if (!isfinite(loglik[b])) f = theta_in_domain(theta + b * D, P, ly) ? 2 : 1;
+    if (out) out[b] = f;
+    if (f == 2 && any2) atomicOr(any2, 1);
+}
+
 // s[off_p + k] = A_p sin(W t_k + Phi0) + B_p cos(W t_k + Phi0); grid (TOA blocks, P)
 __global__ void k_cw_signal(const double* __restrict__ thg, const PulsarDev* __restrict__ psr,
                             const double* __restrict__ rec, double* __restrict__ s) {
@@ -474,6 +492,13 @@ void launch_reduce_few(const double* theta, int64_t B, int32_t P, int32_t flags,
     const size_t smem = size_t(2 + kFewTerms) * P * sizeof(double);
     k_reduce_few<<<unsigned(B), kFewReduceThreads, smem, s>>>(theta, B, P, flags, psr, lane_out, loglik,
                                                               grad, lane_ll);
+}
+
+void launch_walker_flags(const double* theta, int64_t B, int32_t P, int32_t flags, const double* loglik,
+                         int32_t* out, int* any2, cudaStream_t s) {
+    const int threads = 128;
+    const int64_t blocks = (B + threads - 1) / threads;
+    k_walker_flags<<<unsigned(blocks), threads, 0, s>>>(theta, B, P, flags, loglik, out, any2);
 }
 
 void launch_reduce(const double* theta, int64_t B, int32_t P, int32_t flags, const PulsarDev* psr,

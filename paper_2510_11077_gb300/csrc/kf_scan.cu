@@ -629,7 +629,7 @@ __device__ __forceinline__ StepOut stape_get(const double* tk, int64_t st) {
 // of thread t's TOAs and every later thread's.
 template <bool kOU>
 __global__ void __launch_bounds__(kScanThreads) k_scan_finish_grad(ScanGradArgs g) {
-    constexpr int kTd = kOU ? kTapeDoublesOU : kTapeDoubles;
+    constexpr int kTd = kOU ? kScanTapeDoublesOU : kScanTapeDoubles;
     __shared__ double buf[2][32][kAdjElem];
     const ScanArgs& a = g.s;
     const int t = threadIdx.x & 31;
@@ -712,7 +712,7 @@ __global__ void __launch_bounds__(kScanThreads) k_rscan_chunks(ScanGradArgs g) {
 // in chunk order into lane_out rows 1..7.
 template <bool kOU>
 __global__ void __launch_bounds__(32) k_rscan_finish(ScanGradArgs g) {
-    constexpr int kTd = kOU ? kTapeDoublesOU : kTapeDoubles;
+    constexpr int kTd = kOU ? kScanTapeDoublesOU : kScanTapeDoubles;
     const ScanArgs& a = g.s;
     const int t = threadIdx.x;
     const ScanItem it = a.items[blockIdx.x];

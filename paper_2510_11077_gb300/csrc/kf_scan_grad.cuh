@@ -15,7 +15,7 @@ constexpr int kAdjElem = 15;
 struct ScanGradArgs {
     ScanArgs s;                  // the forward scan; s.lane_out is [1 + 7][P][B] here
     double* tape;                // [n_items][tape fields][32 E]: each step's quantities for
-                                 // its adjoint (kTapeDoubles, or kTapeDoublesOU)
+                                 // its adjoint (kScanTapeDoubles, or kScanTapeDoublesOU)
     double* tsuf;                // [n_items * 32][15]: each thread's inclusive suffix map
                                  // within its chunk (its own TOAs and every later thread's)
     double* ragg;                // [n_items][15]: each chunk's composed reverse map

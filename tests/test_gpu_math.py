@@ -78,3 +78,18 @@ def test_log_product_matches_sum_of_logs(lib):
         T = S[:50].copy(); T[17] = badval
         assert lib.argus_selftest_logsum(_p(T), len(T), _p(out), _p(bad)) == 0
         assert bad[0] == 1, badval
+
+
+def test_log_product_has_no_overflow_at_the_ends_of_the_double_range(lib):
+    """Huge and tiny (but normal) innovation variances: S_k's exponent goes to
+    the integer before its mantissa is multiplied in, so the running product
+    stays finite and the sum is right, with no false 'bad' flag."""
+    rng = np.random.default_rng(3)
+    S = np.concatenate([np.array([1.7976931348623157e308, 1.5e308, 2.2250738585072014e-308,
+                                  3e-308, 1e308, 1e-307]),
+                        10.0 ** rng.uniform(-307, 308, 4000)])
+    out = np.empty(1); bad = np.zeros(1, dtype=np.int32)
+    assert lib.argus_selftest_logsum(_p(S), len(S), _p(out), _p(bad)) == 0
+    assert bad[0] == 0
+    ref = math.fsum(np.log(S))
+    assert abs(out[0] - ref) <= 1e-13 * np.sum(np.abs(np.log(S))), (out[0], ref)

@@ -5,9 +5,10 @@ framework that has pre-reserved the GPU's memory for its own pool, or a hot
 sampling loop that must not synchronise on cudaMalloc/cudaFree).  This file
 is collected last so that a run stopping at the first failure has already run
 every other test.  It checks, through the C ABI, that two calls in a row give
-the same results as argus_loglik_grad within the parity tolerances, that the
-second call changes the device's free memory by nothing, and that a batch too
-large for the fixed scratch array is refused.
+the same results as argus_loglik_grad within the parity tolerances, and that
+three of its walkers match the CPU oracle directly, that the second call
+changes the device's free memory by nothing, and that a batch too large for
+the fixed scratch array is refused.
 """
 from __future__ import annotations
 
@@ -64,13 +65,18 @@ def test_noalloc_matches_loglik_grad_twice(argus):
         if call == 1:   # after the first call's one-time set-up, no device memory moves
             assert torch.cuda.mem_get_info()[0] == free_before
         assert _close(ll.cpu().numpy(), g.cpu().numpy(), ll_ref, g_ref), f"call {call}"
+        # three walkers against the oracle itself, not only against the other entry point
+        from oracle import kalman
+        idx = np.array([0, 166, 332])
+        ll_o, g_o = kalman.loglik_grad(data, theta.cpu().numpy()[idx])
+        assert _close(ll.cpu().numpy()[idx], g.cpu().numpy()[idx], ll_o, g_o), f"oracle, call {call}"
 
 
 def test_noalloc_refuses_oversized_batch_and_host_pointers(argus):
     data = inputs.make_array(np.array([300, 400]), seed=302)
     arr = argus.argus_array_create(data)
     lib = argus.load()
-    B = 400_000          # 800k lanes x 112 bytes > 64 MiB
+    B = 400_000          # 800k lanes x 128 bytes (about 102 MB) > 64 MiB
     th = torch.zeros((B, data.dim), dtype=torch.float64, device="cuda")
     ll = torch.empty(B, dtype=torch.float64, device="cuda")
     g = torch.empty((B, data.dim), dtype=torch.float64, device="cuda")
