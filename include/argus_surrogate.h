@@ -43,13 +43,33 @@ typedef struct argus_surrogate argus_surrogate;
 /* Number of FP32 parameters in the flat layout above. */
 int64_t argus_surrogate_param_count(void);
 
-/* Allocate a network on `device` for batches of up to max_rows rows (rounded
- * up to a multiple of 256) with fan-in scaled normal weights drawn from
- * `seed`, zero biases, and identity normalizers.  ARGUS_ERR_UNSUPPORTED if
- * the device is not sm_103. */
-argus_status argus_surrogate_create(int32_t device, int32_t max_rows, uint64_t seed,
+/* The surrogate of one array's log-likelihood (the target path's call: a
+ * network whose inputs are that array's parameter vectors): allocated on the
+ * array's device for batches of up to 4096 rows.  The array must have
+ * D = 47 (20 pulsars, random-walk red noise, no pulsar term), else
+ * ARGUS_ERR_UNSUPPORTED.  weights_path_or_null: a file written by
+ * argus_surrogate_save (weights, normalizers, loss weights and baseline),
+ * or NULL for fan-in scaled normal weights from a fixed seed, zero biases and
+ * identity normalizers.  ARGUS_ERR_INVALID_ARG for an unreadable, foreign,
+ * truncated or non-finite file.  *out is set only on success; the array
+ * handle is not retained. */
+argus_status argus_surrogate_create(const argus_array* array, const char* weights_path_or_null,
                                     argus_surrogate** out);
+
+/* The same with the device, the batch capacity (max_rows, rounded up to a
+ * multiple of 256) and the initial weights' seed given directly.
+ * ARGUS_ERR_UNSUPPORTED if the device is not sm_103. */
+argus_status argus_surrogate_create_ex(int32_t device, int32_t max_rows, uint64_t seed,
+                                       argus_surrogate** out);
 void argus_surrogate_destroy(argus_surrogate* s);
+
+/* Write the network (parameters, normalizers, loss weights and baseline) to
+ * `path` in the format argus_surrogate_create reads: 8 bytes "ARGUSNN1",
+ * int32 version 1, parameter count, input width 47, has_baseline, then FP32
+ * parameters (flat layout), x_mean[47], x_std[47], y_mean, y_std, value
+ * weight, gradient weight, and H[47][47] when has_baseline; little-endian.
+ * Synchronises. */
+argus_status argus_surrogate_save(argus_surrogate* s, const char* path);
 
 /* Host arrays x_mean[47], x_std[47] (> 0); value mean/std (> 0); loss
  * weights of the value output and of each gradient output (>= 0). */
@@ -72,10 +92,10 @@ argus_status argus_surrogate_get_weights(argus_surrogate* s, float* params);
 
 /* Surrogate log-likelihood and gradient of B parameter vectors:
  * theta [B][47], loglik [B], grad [B][47] or NULL (FP32, device).  By default
- * one fused kernel evaluates every max_rows rows: each thread block takes 128
- * rows through all five layers, and in grad mode 1 back through them to the
- * input, with the activations in shared memory and the weights streamed in
- * by TMA layer by layer.  Its results equal the layer-by-layer path's up to
+ * one fused kernel evaluates every max_rows rows: each cluster of thread
+ * blocks (argus_surrogate_set_cluster) takes 128 rows through all five layers,
+ * and in grad mode 1 back through them to the input, with the activations in
+ * shared memory and the weights streamed in by TMA layer by layer.  Its results equal the layer-by-layer path's up to
  * the rounding order of a few FP32 operations. */
 argus_status argus_surrogate_eval(argus_surrogate* s, const float* theta, int64_t B, float* loglik,
                                   float* grad, void* stream);
@@ -96,13 +116,32 @@ argus_status argus_surrogate_eval_f64(argus_surrogate* s, const double* z, const
  * For comparison and measurement; both compute the same network. */
 argus_status argus_surrogate_set_fused(argus_surrogate* s, int32_t on);
 
+/* CTAs of the fused kernel per 128-row slab: 1, 2 or 4 (a thread-block
+ * cluster whose CTAs each compute 1/ctas of every layer's columns and share
+ * the activations through distributed shared memory), or 0 (default) for the
+ * widest whose clusters all run at once -- 4 up to a few thousand rows, 1 for
+ * batches that fill the GPU with single-CTA slabs.  For comparison and
+ * measurement; the results differ only in the rounding order of the
+ * quadratic baseline's sum. */
+argus_status argus_surrogate_set_cluster(argus_surrogate* s, int32_t ctas);
+
 /* One Adam step on a minibatch of n <= max_rows exact evaluations:
- * theta [n][47], loglik [n], grad [n][47] (FP32, device).  The loss is the
- * weighted mean squared error of the standardized outputs; *loss (device
- * FP32) receives its value before the step. */
-argus_status argus_surrogate_train_step(argus_surrogate* s, const float* theta, const float* loglik,
-                                        const float* grad, int64_t n, float lr, float* loss,
-                                        void* stream);
+ * x [n][47] parameter vectors and y [n][1 + 47] their exact log-likelihood
+ * followed by its gradient (FP32, device; the layout the exact filter's
+ * outputs pack into).  The loss is the weighted mean squared error of the
+ * standardized outputs; argus_surrogate_last_loss reads its value before the
+ * step. */
+argus_status argus_surrogate_train_step(argus_surrogate* s, const float* x, const float* y, int64_t n,
+                                        float lr, void* stream);
+
+/* The same with the targets in separate arrays, theta [n][47], loglik [n],
+ * grad [n][47], and the loss written to *loss (device FP32) on the stream. */
+argus_status argus_surrogate_train_step_ex(argus_surrogate* s, const float* theta,
+                                           const float* loglik, const float* grad, int64_t n,
+                                           float lr, float* loss, void* stream);
+
+/* Synchronise and copy the loss of the last argus_surrogate_train_step to *loss (host). */
+argus_status argus_surrogate_last_loss(argus_surrogate* s, float* loss);
 
 /* Which gradient argus_surrogate_eval returns: mode 0 (default) = the 47
  * gradient outputs of the network; mode 1 = the exact input gradient of the

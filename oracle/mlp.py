@@ -92,15 +92,19 @@ def loss_and_dy(y, t, w, rnd: bool = True):
     return loss, _r(dy.astype(y.dtype), rnd)
 
 
-def backward(params, cache, dy, rnd: bool = True):
-    """Gradients [(dW_l, db_l)] of the loss for dY = dL/dy (already rounded)."""
+def backward(params, cache, dy, rnd: bool = True, return_dz: bool = False):
+    """Gradients [(dW_l, db_l)] of the loss for dY = dL/dy (already rounded).
+    return_dz: also return, per layer l, the rounded dL/dz_l it multiplied
+    (dY for l = 4) and the FP32 dL/dz_l it summed for db_l."""
     xs, zs = cache
     dt = dy.dtype
     grads = [None] * len(params)
+    dzs, dz32s = [None] * len(params), [None] * len(params)
     dz = dy
     dz_bf = dy
     for l in reversed(range(len(params))):
         W, _ = params[l]
+        dzs[l], dz32s[l] = dz_bf, dz
         dW = (dz_bf.T @ xs[l]).astype(dt)
         db = dz.sum(axis=0).astype(dt)
         grads[l] = (dW, db)
@@ -108,23 +112,26 @@ def backward(params, cache, dy, rnd: bool = True):
             dx = (dz_bf @ _r(W.astype(dt), rnd)).astype(dt)
             dz = (dx * gelu_grad(zs[l - 1])).astype(dt)
             dz_bf = _r(dz, rnd)
-    return grads
+    return (grads, dzs, dz32s) if return_dz else grads
 
 
-def value_input_grad(params, x, rnd: bool = True):
+def value_input_grad(params, x, rnd: bool = True, return_dz: bool = False):
     """d y_0 / d x: the value output's gradient with respect to the (standardized,
     padded) input, by back-propagating dY = e_0 with the same rounding points as
-    the weight gradients (BF16 operands, FP32 accumulation)."""
+    the weight gradients (BF16 operands, FP32 accumulation).  return_dz: also
+    return the rounded dy_0/dz_l of each layer l = 0..3 (index l)."""
     y, (xs, zs) = forward(params, x, rnd)
     dt = y.dtype
     dz_bf = np.zeros_like(y)
     dz_bf[:, 0] = 1.0
+    dzs = [None] * len(params)
     for l in reversed(range(len(params))):
         W, _ = params[l]
         dx = (dz_bf @ _r(W.astype(dt), rnd)).astype(dt)
         if l == 0:
-            return y, dx
+            return (y, dx, dzs) if return_dz else (y, dx)
         dz_bf = _r((dx * gelu_grad(zs[l - 1])).astype(dt), rnd)
+        dzs[l - 1] = dz_bf
 
 
 class Adam:

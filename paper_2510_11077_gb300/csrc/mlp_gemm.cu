@@ -308,30 +308,50 @@ cudaError_t launch_one(const CUtensorMap* ta, const CUtensorMap* tb, int M, int 
 
 
 // ---------------------------------------------------------------------------
-// Fused evaluation: one CTA of 8 warps owns 128 rows and runs every layer.
+// Fused evaluation: a cluster of kCl CTAs (1, 2 or 4; 8 warps each) owns 128
+// rows and runs every layer; CTA rank c of the cluster computes the output
+// columns [c N / kCl, (c + 1) N / kCl) of every stage, so that a batch of a few
+// thousand rows still spreads over most SMs and each CTA's epilogue (GELU and
+// its derivative, the expensive part) is 1/kCl of a layer.
 // Shared memory: the 128 x 256 BF16 activation tile (A operand, four 64-column
-// K-atoms in the 128-byte-swizzled layout a TMA box would give), the weight
-// tile of the current layer (B operand, up to 256 x 256, loaded by TMA while
-// the previous layer's epilogue runs), the biases, the value output's weight
-// row and the rows' quadratic baseline.
-// Stages (each one tcgen05 GEMM into the same 256 TMEM columns):
+// K-atoms in the 128-byte-swizzled layout a TMA box would give; two copies
+// when kCl > 1, one read by the current stage while the next is filled), this
+// rank's weight slice of the current stage (B operand, N / kCl x K, loaded by
+// TMA while the previous epilogue runs), biases, the value output's weight
+// row, and the rows' quadratic baseline terms.
+// Stages (each one tcgen05 GEMM into the CTA's TMEM accumulator):
 //   0..3  h_{l+1} = gelu(h_l W_l^T + b_l); gelu'(z) saved for the backward pass
 //   4     y = h_4 W_4^T + b_4
 //   5..8  (kFusedValueGrad) dz_l = (dz_{l+1} W_l) * gelu'(z_l), then dx = dz_1 W_0,
 //         seeded with dz_4 = W_4[0] * gelu'(z_4) (the value output's one-hot)
-// Warp w reads TMEM lanes 32 (w % 4) .. + 31 (its rows) and columns
-// 128 (w / 4) .. + 127.  Thread 0 issues the copies and the MMAs and alone
-// waits on the mbarriers (bounded); the block follows through __syncthreads.
+// After its epilogue each rank writes its columns of the next activation tile
+// into every rank's shared memory (distributed shared memory stores), then the
+// cluster meets at a barrier before the next stage's MMA.  Rank c's columns of
+// a hidden layer are one (kCl = 4) or two (kCl = 2) whole K-atoms of the next
+// tile.  gelu'(z) of rank c's columns is saved to, and read back from, global
+// scratch by rank c alone (the backward stage's column i needs layer l's
+// column i).  Warp w reads TMEM lanes 32 (w % 4) .. + 31 (its rows) and half
+// (w / 4) of the rank's columns.  Thread 0 issues the copies and the MMAs and
+// alone waits on the mbarriers (bounded); after a timeout the CTA stops
+// computing but still meets every cluster barrier, so no rank waits forever.
 // The prologue standardizes the inputs (from FP32 theta, or from a sampler's
-// FP64 z and centre) and forms the quadratic baseline; the last epilogue
-// writes the outputs in FP32, or in FP64 with an offset.
+// FP64 z and centre; every rank builds the whole input tile) and forms the
+// quadratic baseline: rank c the terms (H u)_k of the gradient outputs it
+// writes and its share of u^T H u, which rank 0 adds up in rank order.
 constexpr int kFusedThreads = 256;
 constexpr uint32_t kFAtomA = kGemmM * 128u;       // one 64-column K-atom of the activation tile
 constexpr uint32_t kFSmemA = 4u * kFAtomA;        // 64 KB
-constexpr uint32_t kFSmemB = 4u * 256u * 128u;    // 128 KB
 constexpr int kFBiasFloats = 4 * kMlpHidden + kMlpOutPad;
-constexpr int kFTailFloats = kGemmM * kMlpIn + 2 * kGemmM + kFBiasFloats + kMlpHidden;
-constexpr size_t kFusedSmem = 1024 + kFSmemA + kFSmemB + sizeof(float) * kFTailFloats + 64;
+
+template <int kCl>
+struct FusedCfg {
+    static constexpr int kABufs = kCl > 1 ? 2 : 1;
+    static constexpr uint32_t kSmemB = 4u * (256u / kCl) * 128u;          // 4 K-atoms x N/kCl rows
+    static constexpr int kOutCols = kMlpOutPad / kCl;                     // stage 4 and 8 columns
+    static constexpr int kGb = (kMlpIn < kOutCols + 1) ? kMlpIn : kOutCols + 1;   // (H u)_k kept
+    static constexpr int kTailFloats = kGemmM * kGb + kGemmM * (kCl + 2) + kFBiasFloats + kMlpHidden;
+    static constexpr size_t kSmem = 1024 + kABufs * kFSmemA + kSmemB + sizeof(float) * kTailFloats + 64;
+};
 
 struct FusedStage {
     int map;      // 0..4: maps.w[map]; 5..8: maps.wt[8 - map]
@@ -347,28 +367,65 @@ __device__ __forceinline__ const CUtensorMap* fused_map(const MlpFusedMaps& m, i
     return i < kMlpLayers ? &m.w[i] : &m.wt[8 - i];
 }
 
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// the address of the same shared-memory offset in cluster CTA `rank`
+__device__ __forceinline__ uint32_t map_rank(uint32_t addr, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+    return r;
+}
+
+__device__ __forceinline__ void cluster_barrier() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
+                     : "memory");
+}
+
 // 16 consecutive activations of row r, columns c0..c0+15 (c0 a multiple of 16),
-// as BF16 into the swizzled K-major tile: 16-byte chunk j of a row's 128-byte
-// K-atom row sits at chunk position j ^ (r % 8).
-__device__ __forceinline__ void store_act16(uint32_t sA, int r, int c0, const float* d) {
+// as BF16 into the swizzled K-major tile at shared offset `tile` of every rank
+// of the cluster: 16-byte chunk j of a row's 128-byte K-atom row sits at chunk
+// position j ^ (r % 8).
+template <int kCl>
+__device__ __forceinline__ void store_act16(uint32_t tile, int r, int c0, const float* d) {
     uint32_t p[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         const __nv_bfloat162 h = __floats2bfloat162_rn(d[2 * i], d[2 * i + 1]);
         p[i] = *reinterpret_cast<const uint32_t*>(&h);
     }
-    const uint32_t row = sA + uint32_t(c0 >> 6) * kFAtomA + uint32_t(r) * 128u;
+    const uint32_t off = tile + uint32_t(c0 >> 6) * kFAtomA + uint32_t(r) * 128u;
     const uint32_t j0 = uint32_t((c0 & 63) >> 3), sw = uint32_t(r & 7);
-    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(row + ((j0 ^ sw) << 4)), "r"(p[0]),
-                 "r"(p[1]), "r"(p[2]), "r"(p[3])
-                 : "memory");
-    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(row + (((j0 + 1u) ^ sw) << 4)),
-                 "r"(p[4]), "r"(p[5]), "r"(p[6]), "r"(p[7])
-                 : "memory");
+    const uint32_t o0 = off + ((j0 ^ sw) << 4), o1 = off + (((j0 + 1u) ^ sw) << 4);
+    if (kCl == 1) {
+        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(o0), "r"(p[0]), "r"(p[1]),
+                     "r"(p[2]), "r"(p[3])
+                     : "memory");
+        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(o1), "r"(p[4]), "r"(p[5]),
+                     "r"(p[6]), "r"(p[7])
+                     : "memory");
+        return;
+    }
+#pragma unroll
+    for (int k = 0; k < kCl; ++k) {
+        asm volatile("st.shared::cluster.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(map_rank(o0, uint32_t(k))),
+                     "r"(p[0]), "r"(p[1]), "r"(p[2]), "r"(p[3])
+                     : "memory");
+        asm volatile("st.shared::cluster.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(map_rank(o1, uint32_t(k))),
+                     "r"(p[4]), "r"(p[5]), "r"(p[6]), "r"(p[7])
+                     : "memory");
+    }
 }
 
 __device__ __forceinline__ void fence_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_async_cluster() {
+    asm volatile("fence.proxy.async.shared::cluster;" ::: "memory");
 }
 
 // input k of row gr: theta, or float(z - centre) in the FP64-input mode
@@ -390,6 +447,15 @@ __device__ __forceinline__ void fused_out_grad(const MlpFusedArgs& a, int64_t gr
     else a.grad[gr * kMlpIn + k] = g;
 }
 
+// Trace of one row segment (tests only): `cnt` floats, or their BF16 roundings
+// (the values store_act16 writes) with kRound.
+template <bool kRound>
+__device__ __forceinline__ void trace_row(float* t, int cnt, const float* v) {
+#pragma unroll
+    for (int j = 0; j < cnt; ++j)
+        t[j] = kRound ? __bfloat162float(__float2bfloat16_rn(v[j])) : v[j];
+}
+
 // 32 saved gelu'(z) of one row (8 float4), issued early so that their latency
 // overlaps other work
 __device__ __forceinline__ void load_g32(const float* g, float4 (&o)[8]) {
@@ -398,35 +464,68 @@ __device__ __forceinline__ void load_g32(const float* g, float4 (&o)[8]) {
     for (int i = 0; i < 8; ++i) o[i] = g4[i];
 }
 
-__global__ void __launch_bounds__(kFusedThreads, 1) k_mlp_fused(const __grid_constant__ MlpFusedMaps maps,
-                                                                const __grid_constant__ MlpFusedArgs a) {
+// `cnt` (16, 32 or 48) consecutive accumulator columns of this warp's lanes
+template <int kCnt>
+__device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, float (&v)[48]) {
+    if (kCnt == 16) {
+        float t[16];
+        tmem_ld16(taddr, t);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] = t[j];
+    } else {
+        float t[32];
+        tmem_ld32(taddr, t);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) v[j] = t[j];
+        if (kCnt == 48) {
+            float u[16];
+            tmem_ld16(taddr + 32u, u);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) v[32 + j] = u[j];
+        }
+    }
+}
+
+template <int kCl>
+__global__ void __launch_bounds__(kFusedThreads, 1)
+    k_mlp_fused(const __grid_constant__ MlpFusedMaps maps, const __grid_constant__ MlpFusedArgs a) {
+    using Cfg = FusedCfg<kCl>;
+    constexpr int kOut = Cfg::kOutCols;                       // this rank's stage-4/8 columns
+    constexpr int kOutLd = kOut > 32 ? 48 : kOut;             // of them read back (<= 48 used)
     extern __shared__ __align__(16) uint8_t smem_raw[];
     __shared__ uint32_t s_tmem;
     __shared__ int s_ok;
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
-    const uint32_t sA = base, sB = base + kFSmemA;
-    float* tail = reinterpret_cast<float*>(smem_raw + (base - raw) + kFSmemA + kFSmemB);
-    float* gbase_s = tail;                        // [128][47]
-    float* base_s = gbase_s + kGemmM * kMlpIn;    // [128]
-    float* y0_s = base_s + kGemmM;                // [128]
-    float* bias_s = y0_s + kGemmM;                // b_0..b_3 [256] each, then b_4 [64]
-    float* w4_s = bias_s + kFBiasFloats;          // W_4[0] [256]
+    const uint32_t sB = base + Cfg::kABufs * kFSmemA;
+    float* tail = reinterpret_cast<float*>(smem_raw + (base - raw) + Cfg::kABufs * kFSmemA + Cfg::kSmemB);
+    float* gbase_s = tail;                            // [128][kGb]: -(H u)_k, k from k_lo
+    float* qpart_s = gbase_s + kGemmM * Cfg::kGb;     // [kCl][128]: each rank's share of u^T H u
+    float* y0_s = qpart_s + kGemmM * kCl;             // [128]
+    float* spare_s = y0_s + kGemmM;                   // [128]
+    float* bias_s = spare_s + kGemmM;                 // b_0..b_3 [256] each, then b_4 [64]
+    float* w4_s = bias_s + kFBiasFloats;              // W_4[0] [256]
     const uint32_t bar_load = smem_u32(w4_s + kMlpHidden);
     const uint32_t bar_mma = bar_load + 8u;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int q = warp & 3, hh = warp >> 2;
     const int r = 32 * q + lane;                            // this thread's row in the slab
-    const int64_t row0 = int64_t(blockIdx.x) * kGemmM, gr = row0 + r;
+    const uint32_t rank = kCl > 1 ? cluster_rank() : 0u;
+    const int64_t row0 = int64_t(blockIdx.x / kCl) * kGemmM, gr = row0 + r;
     const bool valid = gr < a.n;
     const int nst = a.mode == kFusedValueGrad ? 9 : 5;
+    // gradient outputs of this rank: grad-head columns j = k + 1 and back-propagated
+    // columns k, both within [rank kOut, (rank + 1) kOut)
+    const int k_lo = max(0, int(rank) * kOut - 1), k_hi = min(kMlpIn, int(rank) * kOut + kOut);
 
     auto issue_load = [&](int st, uint32_t bar) {
         const FusedStage fs = c_fstage[st];
         const int atoms = fs.K / 64;
-        mbar_expect_tx(bar, uint32_t(atoms) * uint32_t(fs.N) * 128u);
+        const int nc = fs.N / kCl;
+        mbar_expect_tx(bar, uint32_t(atoms) * uint32_t(nc) * 128u);
         for (int at = 0; at < atoms; ++at)
-            tma_load_2d(sB + uint32_t(at) * uint32_t(fs.N) * 128u, fused_map(maps, fs.map), at * 64, 0, bar);
+            tma_load_2d(sB + uint32_t(at) * uint32_t(nc) * 128u, fused_map(maps, fs.map), at * 64,
+                        int(rank) * nc, bar);
     };
 
     if (tid == 0) {
@@ -438,19 +537,20 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_mlp_fused(const __grid_con
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(&s_tmem)),
-                     "r"(256u)
+                     "r"(uint32_t(256 / kCl))
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     tc_fence_before();
     __syncthreads();
+    if (kCl > 1) cluster_barrier();       // every rank has started before any remote store
     tc_fence_after();
     const uint32_t tmem = s_tmem;
     if (tid == 0) issue_load(0, bar_load);
 
     if (hh == 0) {
         // biases and the value output's weight row, then the standardized input
-        // row: (theta - mean) / std for k < 47, zero padding
+        // row: (theta - mean) / std for k < 47, zero padding (every rank, locally)
         for (int i = tid; i < kFBiasFloats; i += 128) {
             const int l = i < 4 * kMlpHidden ? i / kMlpHidden : 4;
             bias_s[i] = a.bias[l][i - l * kMlpHidden];
@@ -464,168 +564,277 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_mlp_fused(const __grid_con
                 const int k = c0 + j;
                 d[j] = (valid && k < kMlpIn) ? (fused_in(a, gr, k) - a.xm[k]) / a.xs[k] : 0.0f;
             }
-            store_act16(sA, r, c0, d);
+            store_act16<1>(base, r, c0, d);
+            if (a.tr_act && valid && rank == 0) trace_row<true>(a.tr_act + gr * kMlpHidden + c0, 16, d);
         }
     } else if (a.Hq && valid) {
-        // quadratic baseline: base = -u^T H u / 2, gbase = -H u; four rows of H
-        // at a time (independent sums, each in the order j = 0..46)
+        // quadratic baseline: gbase = -(H u)_k for this rank's gradient outputs
+        // (each sum in the order j = 0..46), and the rank's share of u^T H u
         float u[kMlpIn];
 #pragma unroll
         for (int j = 0; j < kMlpIn; ++j) u[j] = fused_in(a, gr, j);
         float qd = 0.0f;
 #pragma unroll 1
-        for (int i0 = 0; i0 < kMlpIn; i0 += 4) {
-            float hu[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-            const float* H0 = a.Hq + i0 * kMlpIn;
+        for (int k = k_lo; k < k_hi; ++k) {
+            const float* Hk = a.Hq + k * kMlpIn;
+            float hu = 0.0f;
 #pragma unroll
-            for (int j = 0; j < kMlpIn; ++j)
-#pragma unroll
-                for (int t = 0; t < 4; ++t)
-                    if (i0 + t < kMlpIn) hu[t] = fmaf(H0[t * kMlpIn + j], u[j], hu[t]);
-#pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                if (i0 + t >= kMlpIn) break;
-                gbase_s[r * kMlpIn + i0 + t] = -hu[t];
-                qd = fmaf(fused_in(a, gr, i0 + t), hu[t], qd);
-            }
+            for (int j = 0; j < kMlpIn; ++j) hu = fmaf(Hk[j], u[j], hu);
+            gbase_s[r * Cfg::kGb + (k - k_lo)] = -hu;
+            if (k >= int(rank) * kOut) qd = fmaf(fused_in(a, gr, k), hu, qd);
         }
-        base_s[r] = -0.5f * qd;
+        const uint32_t qa = smem_u32(qpart_s + rank * kGemmM + r);
+        if (kCl > 1) {
+            asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(map_rank(qa, 0u)), "f"(qd) : "memory");
+        } else {
+            qpart_s[r] = qd;
+        }
     }
     fence_async_smem();
+    tc_fence_before();
     __syncthreads();
+    if (kCl > 1) cluster_barrier();       // the baseline shares have reached rank 0
+    tc_fence_after();
 
     const uint32_t tlane = tmem + (uint32_t(32 * q) << 16);
-    const int cbeg = 128 * hh;
     for (int st = 0; st < nst; ++st) {
         const FusedStage fs = c_fstage[st];
+        const int nc = fs.N / kCl;                       // this rank's columns of the stage
+        const int cg0 = int(rank) * nc;                  // the first of them
+        constexpr int half = 128 / kCl;                  // 256-wide stages: columns per warp half
+        const int cbeg = hh * half;
+        const uint32_t curA = base + uint32_t(Cfg::kABufs > 1 ? (st & 1) : 0) * kFSmemA;
+        const uint32_t nxtA = base + uint32_t(Cfg::kABufs > 1 ? ((st + 1) & 1) : 0) * kFSmemA;
         // the first 32 saved gelu'(z) this stage's epilogue needs, requested
         // before the MMA completes
         const float* gsrc = nullptr;
         if (st == 4 && a.mode == kFusedValueGrad) gsrc = a.gscr[3] + gr * kMlpHidden;
         else if (st >= 5 && st < 8) gsrc = a.gscr[7 - st] + gr * kMlpHidden;
         float4 gbuf[2][8];
-        if (gsrc) load_g32(gsrc + cbeg, gbuf[0]);
+        // the seed (stage 4) and the backward stages cover this rank's 256 / kCl columns
+        const int hbeg = int(rank) * (kMlpHidden / kCl) + cbeg;
+        if (gsrc && s_ok) load_g32(gsrc + hbeg, gbuf[0]);
         if (tid == 0) {
             const uint32_t ph = uint32_t(st & 1);
-            bool ok = mbar_wait(bar_load, ph, a.err, 3);
+            bool ok = s_ok != 0;
+            if (ok) ok = mbar_wait(bar_load, ph, a.err, 3);
             if (ok) {
                 tc_fence_after();
-                const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t(fs.N) >> 3) << 17) |
+                const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t(nc) >> 3) << 17) |
                                        ((uint32_t(kGemmM) >> 4) << 24);
                 for (int k = 0; k < fs.K / 16; ++k) {
                     const uint32_t at = uint32_t(k >> 2), kk = uint32_t(k & 3);
-                    const uint64_t da = smem_desc(sA + at * kFAtomA + kk * 32u);
-                    const uint64_t db = smem_desc(sB + at * uint32_t(fs.N) * 128u + kk * 32u);
+                    const uint64_t da = smem_desc(curA + at * kFAtomA + kk * 32u);
+                    const uint64_t db = smem_desc(sB + at * uint32_t(nc) * 128u + kk * 32u);
                     tc_mma(tmem, da, db, idesc, k > 0 ? 1u : 0u);
                 }
                 tc_commit(bar_mma);
                 ok = mbar_wait(bar_mma, ph, a.err, 4);
                 if (!ok) mbar_wait(bar_mma, ph, nullptr, 0);   // let MMAs in flight finish (bounded)
                 else if (st + 1 < nst) issue_load(st + 1, bar_load);
-            } else {
+            } else if (s_ok) {
                 mbar_wait(bar_load, ph, nullptr, 0);           // let copies in flight land (bounded)
             }
             s_ok = ok ? 1 : 0;
         }
         __syncthreads();
-        if (!s_ok) break;
         tc_fence_after();
-        if (st < 4) {
-            // hidden layer: z = acc + b; h = gelu(z) into the tile; gelu'(z) to scratch
-            const float* bias = bias_s + st * kMlpHidden;
-            float* gs = a.gscr[st] + gr * kMlpHidden;
+        if (s_ok) {
+            if (st < 4) {
+                // hidden layer: z = acc + b; h = gelu(z) into every rank's next tile;
+                // gelu'(z) to scratch
+                const float* bias = bias_s + st * kMlpHidden;
+                float* gs = a.gscr[st] + gr * kMlpHidden;
 #pragma unroll 1
-            for (int c0 = cbeg; c0 < cbeg + 128; c0 += 32) {
-                float v[32], g[32];
-                tmem_ld32(tlane + uint32_t(c0), v);
+                for (int c0 = cbeg; c0 < cbeg + half; c0 += 32) {
+                    const int cg = int(rank) * (kMlpHidden / kCl) + c0;
+                    float v[32], g[32];
+                    tmem_ld32(tlane + uint32_t(c0), v);
+                    if (a.tr_acc && valid)
+                        trace_row<false>(a.tr_acc + st * a.tr_stride + gr * kMlpHidden + cg, 32, v);
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const float z = v[j] + bias[c0 + j];
-                    v[j] = gelu_f(z);
-                    g[j] = gelu_grad_f(z);
+                    for (int j = 0; j < 32; ++j) {
+                        const float z = v[j] + bias[cg + j];
+                        v[j] = gelu_f(z);
+                        g[j] = gelu_grad_f(z);
+                    }
+                    float4* g4 = reinterpret_cast<float4*>(gs + cg);
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) g4[i] = make_float4(g[4 * i], g[4 * i + 1], g[4 * i + 2], g[4 * i + 3]);
+                    store_act16<kCl>(nxtA, r, cg, v);
+                    store_act16<kCl>(nxtA, r, cg + 16, v + 16);
+                    if (a.tr_act && valid)
+                        trace_row<true>(a.tr_act + (st + 1) * a.tr_stride + gr * kMlpHidden + cg, 32, v);
                 }
-                float4* g4 = reinterpret_cast<float4*>(gs + c0);
+            } else if (st == 4) {
+                // output layer: y = acc + b_4 for this rank's columns j = cg0 ..
+                const float* b4 = bias_s + 4 * kMlpHidden;
+                if (hh == 0 && (a.mode == kFusedGradHead || rank == 0 || a.tr_acc)) {
+                    float v[48];
+                    tmem_ld_cols<kOutLd>(tlane, v);
+                    if (a.tr_acc && valid) {
 #pragma unroll
-                for (int i = 0; i < 8; ++i) g4[i] = make_float4(g[4 * i], g[4 * i + 1], g[4 * i + 2], g[4 * i + 3]);
-                store_act16(sA, r, c0, v);
-                store_act16(sA, r, c0 + 16, v + 16);
-            }
-        } else if (st == 4) {
-            // output layer: y = acc + b_4
-            const float* b4 = bias_s + 4 * kMlpHidden;
-            if (hh == 0) {
-                float v[32];
-                tmem_ld32(tlane, v);
-                float v2[16];
-                if (a.mode == kFusedGradHead) tmem_ld16(tlane + 32u, v2);
-                if (valid) {
-                    const float y0 = v[0] + b4[0];
-                    y0_s[r] = y0;
-                    if (a.mode != kFusedValueGrad)
-                        fused_out_ll(a, gr, y0 * a.ys + a.ym + (a.Hq ? base_s[r] : 0.0f));
-                    if (a.mode == kFusedGradHead) {
-                        // output 1 + k is d ll / d x_k
+                        for (int j = 0; j < kOutLd; ++j)
+                            if (cg0 + j < kMlpOut) a.tr_acc[4 * a.tr_stride + gr * kMlpHidden + cg0 + j] = v[j];
+                    }
+                    if (valid && rank == 0) {
+                        const float y0 = v[0] + b4[0];
+                        y0_s[r] = y0;
+                        float base_r = 0.0f;
+                        if (a.Hq) {
+                            float qsum = 0.0f;
+                            for (int c = 0; c < kCl; ++c) qsum += qpart_s[c * kGemmM + r];
+                            base_r = -0.5f * qsum;
+                        }
+                        fused_out_ll(a, gr, y0 * a.ys + a.ym + base_r);
+                    }
+                    if (valid && a.mode == kFusedGradHead) {
+                        // output j = 1 + k is d ll / d x_k
 #pragma unroll
-                        for (int c = 1; c < 48; ++c) {
-                            const float yk = (c < 32 ? v[c] : v2[c - 32]) + b4[c];
-                            const int k = c - 1;
-                            fused_out_grad(a, gr, k, yk * a.ys / a.xs[k] + (a.Hq ? gbase_s[r * kMlpIn + k] : 0.0f));
+                        for (int jj = 0; jj < kOutLd; ++jj) {
+                            const int j = cg0 + jj;
+                            if (j < 1 || j >= kMlpOut) continue;
+                            const int k = j - 1;
+                            const float yk = v[jj] + b4[j];
+                            fused_out_grad(a, gr, k, yk * a.ys / a.xs[k] +
+                                                         (a.Hq ? gbase_s[r * Cfg::kGb + (k - k_lo)] : 0.0f));
                         }
                     }
                 }
-            }
-            if (a.mode == kFusedValueGrad) {
-                // seed: dz_4 = (one-hot of the value output) W_4 * gelu'(z_4)
+                if (a.mode == kFusedValueGrad) {
+                    // seed: dz_4 = (one-hot of the value output) W_4 * gelu'(z_4), for
+                    // this rank's columns of the 256-wide tile
 #pragma unroll
-                for (int it = 0; it < 4; ++it) {
-                    const int c0 = cbeg + 32 * it;
-                    if (it < 3) load_g32(gsrc + c0 + 32, gbuf[(it + 1) & 1]);
+                    for (int it = 0; it < half / 32; ++it) {
+                        const int c0 = hbeg + 32 * it;
+                        if (32 * (it + 1) < half) load_g32(gsrc + c0 + 32, gbuf[(it + 1) & 1]);
+                        const float* gg = reinterpret_cast<const float*>(gbuf[it & 1]);
+                        float d[32];
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) d[j] = (valid ? w4_s[c0 + j] : 0.0f) * gg[j];
+                        store_act16<kCl>(nxtA, r, c0, d);
+                        store_act16<kCl>(nxtA, r, c0 + 16, d + 16);
+                        if (a.tr_act && valid)
+                            trace_row<true>(a.tr_act + 5 * a.tr_stride + gr * kMlpHidden + c0, 32, d);
+                    }
+                }
+            } else if (st < 8) {
+                // back through layer 8 - st: dz = acc * gelu'(z)
+#pragma unroll
+                for (int it = 0; it < half / 32; ++it) {
+                    const int c0 = cbeg + 32 * it, cg = hbeg + 32 * it;
+                    if (32 * (it + 1) < half) load_g32(gsrc + cg + 32, gbuf[(it + 1) & 1]);
+                    float v[32];
+                    tmem_ld32(tlane + uint32_t(c0), v);
+                    if (a.tr_acc && valid)
+                        trace_row<false>(a.tr_acc + st * a.tr_stride + gr * kMlpHidden + cg, 32, v);
                     const float* gg = reinterpret_cast<const float*>(gbuf[it & 1]);
-                    float d[32];
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) d[j] = (valid ? w4_s[c0 + j] : 0.0f) * gg[j];
-                    store_act16(sA, r, c0, d);
-                    store_act16(sA, r, c0 + 16, d + 16);
+                    for (int j = 0; j < 32; ++j) v[j] = v[j] * gg[j];
+                    store_act16<kCl>(nxtA, r, cg, v);
+                    store_act16<kCl>(nxtA, r, cg + 16, v + 16);
+                    if (a.tr_act && valid)
+                        trace_row<true>(a.tr_act + (st + 1) * a.tr_stride + gr * kMlpHidden + cg, 32, v);
                 }
-            }
-        } else if (st < 8) {
-            // back through layer 8 - st: dz = acc * gelu'(z)
+            } else if (hh == 0) {
+                // dx = dz_1 W_0: the gradient of the value output in the standardized
+                // inputs, this rank's columns k = cg0 ..
+                float v[48];
+                tmem_ld_cols<kOutLd>(tlane, v);
+                if (a.tr_acc && valid) {
 #pragma unroll
-            for (int it = 0; it < 4; ++it) {
-                const int c0 = cbeg + 32 * it;
-                if (it < 3) load_g32(gsrc + c0 + 32, gbuf[(it + 1) & 1]);
-                float v[32];
-                tmem_ld32(tlane + uint32_t(c0), v);
-                const float* gg = reinterpret_cast<const float*>(gbuf[it & 1]);
-#pragma unroll
-                for (int j = 0; j < 32; ++j) v[j] = v[j] * gg[j];
-                store_act16(sA, r, c0, v);
-                store_act16(sA, r, c0 + 16, v + 16);
-            }
-        } else if (hh == 0) {
-            // dx = dz_1 W_0: the gradient of the value output in the standardized inputs
-            float v[32], v2[16];
-            tmem_ld32(tlane, v);
-            tmem_ld16(tlane + 32u, v2);
-            if (valid) {
-#pragma unroll
-                for (int k = 0; k < kMlpIn; ++k) {
-                    const float dx = (k < 32 ? v[k] : v2[k - 32]) + 0.0f;
-                    fused_out_grad(a, gr, k, dx * a.ys / a.xs[k] + (a.Hq ? gbase_s[r * kMlpIn + k] : 0.0f));
+                    for (int j = 0; j < kOutLd; ++j)
+                        if (cg0 + j < kMlpIn) a.tr_acc[8 * a.tr_stride + gr * kMlpHidden + cg0 + j] = v[j];
                 }
-                fused_out_ll(a, gr, y0_s[r] * a.ys + a.ym + (a.Hq ? base_s[r] : 0.0f));
+                if (valid) {
+#pragma unroll
+                    for (int jj = 0; jj < kOutLd; ++jj) {
+                        const int k = cg0 + jj;
+                        if (k >= kMlpIn) continue;
+                        fused_out_grad(a, gr, k, v[jj] * a.ys / a.xs[k] +
+                                                     (a.Hq ? gbase_s[r * Cfg::kGb + (k - k_lo)] : 0.0f));
+                    }
+                }
             }
         }
-        fence_async_smem();
+        if (kCl > 1) fence_async_cluster();
+        else fence_async_smem();
         tc_fence_before();
         __syncthreads();
+        if (kCl > 1) cluster_barrier();   // every rank's columns of the next tile are in place
+        tc_fence_after();
     }
     tc_fence_before();
     __syncthreads();
     if (warp == 0) {
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256u)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(uint32_t(256 / kCl))
                      : "memory");
     }
+}
+
+template <int kCl>
+cudaError_t configure_fused(int dev) {
+    static bool configured[64] = {};
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!configured[dev]) {
+        cudaError_t ce = cudaFuncSetAttribute(k_mlp_fused<kCl>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              int(FusedCfg<kCl>::kSmem));
+        if (ce != cudaSuccess) return ce;
+        configured[dev] = true;
+    }
+    return cudaSuccess;
+}
+
+template <int kCl>
+cudaLaunchConfig_t fused_config(unsigned grid, cudaStream_t s, cudaLaunchAttribute* attr) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kFusedThreads);
+    cfg.dynamicSmemBytes = FusedCfg<kCl>::kSmem;
+    cfg.stream = s;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kCl;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cfg;
+}
+
+// How many clusters of kCl fused CTAs the device runs at once (0 if unknown).
+template <int kCl>
+int fused_max_clusters(int dev) {
+    static int cached[64] = {};
+    if (dev < 0 || dev >= 64) return 0;
+    if (!cached[dev]) {
+        if (configure_fused<kCl>(dev) != cudaSuccess) return 0;
+        cudaLaunchAttribute attr[1];
+        cudaLaunchConfig_t cfg = fused_config<kCl>(unsigned(kCl), nullptr, attr);
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, k_mlp_fused<kCl>, &cfg) != cudaSuccess) {
+            cudaGetLastError();
+            n = 0;
+        }
+        cached[dev] = n > 0 ? n : -1;
+    }
+    return cached[dev] > 0 ? cached[dev] : 0;
+}
+
+template <int kCl>
+cudaError_t launch_fused_cl(const MlpFusedMaps& maps, const MlpFusedArgs& a, cudaStream_t s) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaError_t ce = configure_fused<kCl>(dev);
+    if (ce != cudaSuccess) return ce;
+    const unsigned grid = unsigned((a.n + kGemmM - 1) / kGemmM) * kCl;
+    if (kCl == 1) {
+        k_mlp_fused<1><<<grid, kFusedThreads, FusedCfg<1>::kSmem, s>>>(maps, a);
+        return cudaGetLastError();
+    }
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = fused_config<kCl>(grid, s, attr);
+    return cudaLaunchKernelEx(&cfg, k_mlp_fused<kCl>, maps, a);
 }
 
 }  // namespace
@@ -649,24 +858,30 @@ cudaError_t launch_gemm_tc(const CUtensorMap* ta, const CUtensorMap* tb, int M, 
 }
 
 
-cudaError_t launch_mlp_fused(const MlpFusedMaps& maps, const MlpFusedArgs& a, cudaStream_t s) {
+// The widest cluster whose clusters all run at once for n rows (one 128-row
+// slab per cluster); 1 when even two-CTA clusters would need a second wave.
+int fused_cluster_size(int64_t n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int64_t slabs = (n + kGemmM - 1) / kGemmM;
+    if (slabs <= fused_max_clusters<4>(dev)) return 4;
+    if (slabs <= fused_max_clusters<2>(dev)) return 2;
+    return 1;
+}
+
+cudaError_t launch_mlp_fused(const MlpFusedMaps* maps, const MlpFusedArgs& a, cudaStream_t s, int cl) {
     const bool f64 = a.z64 != nullptr;
     if (a.n <= 0 || a.mode < kFusedValue || a.mode > kFusedGradHead ||
         (f64 ? (!a.zc || !a.ll64 || (a.mode != kFusedValue && !a.g64))
              : (!a.theta || !a.loglik || (a.mode != kFusedValue && !a.grad))))
         return cudaErrorInvalidValue;
-    static bool configured[64] = {};
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev < 64 && !configured[dev]) {
-        cudaError_t ce = cudaFuncSetAttribute(k_mlp_fused, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              int(kFusedSmem));
-        if (ce != cudaSuccess) return ce;
-        configured[dev] = true;
+    if (cl == 0) cl = fused_cluster_size(a.n);
+    switch (cl) {
+        case 1: return launch_fused_cl<1>(maps[0], a, s);
+        case 2: return launch_fused_cl<2>(maps[1], a, s);
+        case 4: return launch_fused_cl<4>(maps[2], a, s);
     }
-    const unsigned grid = unsigned((a.n + kGemmM - 1) / kGemmM);
-    k_mlp_fused<<<grid, kFusedThreads, kFusedSmem, s>>>(maps, a);
-    return cudaGetLastError();
+    return cudaErrorInvalidValue;
 }
 
 bool make_tmap_bf16(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols,

@@ -42,9 +42,10 @@ cudaError_t launch_gemm_tc(const CUtensorMap* ta, const CUtensorMap* tb, int M, 
                            int bn, int chunks, int epi, const GemmEpiArgs& e, int* err,
                            cudaStream_t s);
 
-// Fused evaluation of the whole network on one 128-row slab per CTA
-// (forward through the five layers and, in kFusedValueGrad, the value
-// output's gradient back to the input), activations kept in shared memory.
+// Fused evaluation of the whole network on one 128-row slab per cluster of 1,
+// 2 or 4 CTAs (forward through the five layers and, in kFusedValueGrad, the
+// value output's gradient back to the input), activations kept in shared
+// memory; each CTA of a cluster computes its share of every layer's columns.
 enum FusedMode : int {
     kFusedValue = 0,        // loglik only
     kFusedValueGrad = 1,    // loglik and the back-propagated gradient of the value output
@@ -52,8 +53,8 @@ enum FusedMode : int {
 };
 
 struct MlpFusedMaps {
-    CUtensorMap w[kMlpLayers];        // W_l [out][in] BF16, box rows = out
-    CUtensorMap wt[kMlpLayers - 1];   // W_l^T [in][out] BF16 for l = 0..3, box rows = in
+    CUtensorMap w[kMlpLayers];        // W_l [out][in] BF16, box rows = out / cluster size
+    CUtensorMap wt[kMlpLayers - 1];   // W_l^T [in][out] BF16 for l = 0..3, box rows = in / cluster size
 };
 
 struct MlpFusedArgs {
@@ -78,9 +79,19 @@ struct MlpFusedArgs {
     double off;
     double* ll64;
     double* g64;
+    // optional trace of every GEMM stage (tests): tr_act + st * tr_stride + row * 256 gets
+    // the stage's BF16 A operand row (as floats), tr_acc likewise its FP32 accumulator
+    // row before any bias; nullptr = no trace
+    float* tr_act;
+    float* tr_acc;
+    int64_t tr_stride;
 };
 
-cudaError_t launch_mlp_fused(const MlpFusedMaps& maps, const MlpFusedArgs& a, cudaStream_t s);
+// maps[0], [1], [2]: the weight maps for clusters of 1, 2 and 4 CTAs (boxes of
+// N, N / 2 and N / 4 rows); cl = 1, 2 or 4 CTAs per 128-row slab, or 0 for the
+// widest whose clusters all run at once.
+cudaError_t launch_mlp_fused(const MlpFusedMaps* maps, const MlpFusedArgs& a, cudaStream_t s, int cl);
+int fused_cluster_size(int64_t n);
 
 // Make a 2-D BF16 tensor map over a row-major [rows][cols] array with a box of
 // [box_rows][64] and 128-byte swizzle.  Returns false if the driver refuses.

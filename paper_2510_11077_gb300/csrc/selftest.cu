@@ -1,4 +1,5 @@
 // Self-check entry points of the device arithmetic helpers (argus_selftest.h).
+#include <algorithm>
 #include <string>
 
 #include <cuda_runtime.h>
@@ -36,6 +37,32 @@ __global__ void k_logsum(const double* S, int64_t n, double* out, int* bad) {
     for (int64_t i = 0; i < n; ++i) lp.add(S[i]);
     *out = lp.value();
     *bad = int(lp.bad);
+}
+
+// FP64 FMA throughput probe: every thread runs C independent chains
+// a <- a x + y (|x| < 1, so the values stay bounded) for `iters` rounds and
+// stores the sum, so nothing is dead code.  With kRegOps the multiplier and
+// addend are per-thread registers loaded from memory (the compiler cannot
+// treat them as uniform constants); otherwise they are kernel parameters.
+template <int C, bool kRegOps>
+__global__ void __launch_bounds__(256) k_dfma(int64_t iters, double x, double y, double* out) {
+    double a[C];
+#pragma unroll
+    for (int j = 0; j < C; ++j) a[j] = double(threadIdx.x + j);
+    double xr = x, yr = y;
+    if (kRegOps) {
+        xr = out[threadIdx.x] * 0.0 + x;    // out is zeroed before the probe
+        yr = out[threadIdx.x + 256] * 0.0 + y;
+    }
+#pragma unroll 4
+    for (int64_t i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int j = 0; j < C; ++j) a[j] = fma(a[j], xr, yr);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int j = 0; j < C; ++j) s += a[j];
+    out[int64_t(blockIdx.x) * blockDim.x + threadIdx.x] = s;
 }
 
 struct DevBuf {
@@ -109,6 +136,67 @@ argus_status argus_selftest_logsum(const double* S, int64_t n, double* out, int3
     int hb = 0;
     TRY(cudaMemcpy(&hb, dbad, sizeof(int), cudaMemcpyDeviceToHost));
     *bad = hb;
+    return ARGUS_OK;
+}
+
+argus_status argus_selftest_dfma_rate(int64_t iters, int32_t launches, int32_t variant,
+                                      double* dfma_per_s, float* ms) {
+    if (iters < 1 || launches < 1 || variant < 0 || variant > 3 || !dfma_per_s || !ms)
+        return ARGUS_ERR_INVALID_ARG;
+    int dev = 0, n_sm = 0;
+    TRY(cudaGetDevice(&dev));
+    TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+    const int threads = 256;
+    const int chains[4] = {8, 8, 4, 16};
+    // one full wave: as many blocks per SM as the variant's registers allow
+    int per_sm = 0;
+    switch (variant) {
+        case 0: TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dfma<8, false>, threads, 0)); break;
+        case 1: TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dfma<8, true>, threads, 0)); break;
+        case 2: TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dfma<4, false>, threads, 0)); break;
+        default: TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dfma<16, false>, threads, 0)); break;
+    }
+    const int grid = n_sm * std::max(per_sm, 1);
+    DevBuf b;
+    TRY(cudaMalloc(&b.p, size_t(std::max(grid, 2)) * threads * sizeof(double)));
+    TRY(cudaMemset(b.p, 0, size_t(std::max(grid, 2)) * threads * sizeof(double)));
+    double* out = static_cast<double*>(b.p);
+    // the same FMA count for every variant: rounds scale inversely with the chains
+    const int64_t rounds = iters * 8 / chains[variant];
+    auto launch = [&](int64_t r) {
+        switch (variant) {
+            case 0: k_dfma<8, false><<<grid, threads>>>(r, 0.999, 1e-3, out); break;
+            case 1: k_dfma<8, true><<<grid, threads>>>(r, 0.999, 1e-3, out); break;
+            case 2: k_dfma<4, false><<<grid, threads>>>(r, 0.999, 1e-3, out); break;
+            default: k_dfma<16, false><<<grid, threads>>>(r, 0.999, 1e-3, out); break;
+        }
+    };
+    launch(rounds / 8 + 1);   // warm-up
+    TRY(cudaGetLastError());
+    TRY(cudaDeviceSynchronize());
+    TRY(cudaMemset(b.p, 0, size_t(std::max(grid, 2)) * threads * sizeof(double)));
+    cudaEvent_t e0, e1;
+    TRY(cudaEventCreate(&e0));
+    TRY(cudaEventCreate(&e1));
+    const double fmas = double(grid) * threads * double(chains[variant]) * double(rounds);
+    for (int l = 0; l < launches; ++l) {
+        cudaEventRecord(e0);
+        launch(rounds);
+        cudaEventRecord(e1);
+        cudaError_t e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        float t = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+        if (e != cudaSuccess) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return cuda_status(e);
+        }
+        ms[l] = t;
+        dfma_per_s[l] = fmas / (double(t) * 1e-3);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
     return ARGUS_OK;
 }
 

@@ -88,10 +88,11 @@ constexpr int kRowsPerBlock = 4;   // rows per block of the (column, row) kernel
 inline dim3 rc_grid(int rows) { return dim3(unsigned((rows + kRowsPerBlock - 1) / kRowsPerBlock)); }
 inline dim3 rc_block() { return dim3(kMlpInPad, kRowsPerBlock); }
 
-// Standardized targets, weighted squared error per row, and
+// Standardized targets (loglik ll[r ll_stride], gradient grad[r g_stride + k]),
+// weighted squared error per row, and
 // dY = bf16(2 w_j (y - t) / n) (+ its transpose); padding rows and columns get 0.
-__global__ void k_loss(const float* __restrict__ y, const float* __restrict__ ll,
-                       const float* __restrict__ grad, const float* __restrict__ base,
+__global__ void k_loss(const float* __restrict__ y, const float* __restrict__ ll, int ll_stride,
+                       const float* __restrict__ grad, int g_stride, const float* __restrict__ base,
                        const float* __restrict__ gbase, int64_t n, int rows, Norm nm,
                        __nv_bfloat16* __restrict__ dy, __nv_bfloat16* __restrict__ dyt, int pitch,
                        float* __restrict__ row_loss) {
@@ -104,8 +105,8 @@ __global__ void k_loss(const float* __restrict__ y, const float* __restrict__ ll
     if (live && r < n && j < kMlpOut) {
         const float b0 = base ? base[r] : 0.0f;
         const float bj = (gbase && j > 0) ? gbase[int64_t(r) * kMlpIn + (j - 1)] : 0.0f;
-        const float t = (j == 0) ? (ll[r] - b0 - nm.ym) / nm.ys
-                                 : (grad[int64_t(r) * kMlpIn + (j - 1)] - bj) * nm.xs[j - 1] / nm.ys;
+        const float t = (j == 0) ? (ll[int64_t(r) * ll_stride] - b0 - nm.ym) / nm.ys
+                                 : (grad[int64_t(r) * g_stride + (j - 1)] - bj) * nm.xs[j - 1] / nm.ys;
         const float e = y[int64_t(r) * kMlpOutPad + j] - t;
         sq = nm.w[j] * e * e;
         d = 2.0f * nm.w[j] * e / float(n);
@@ -317,8 +318,18 @@ struct argus_surrogate {
     CUtensorMap tmWT0_b64;   // W_0^T [64][256] with a 64-row box (B operand of dX0 = dZ1 W0)
     int grad_mode = 0;       // 0: gradient head; 1: back-propagated value head
     CUtensorMap tmdY, tmdYT, tmdZ16[2], tmdZT[2];
-    MlpFusedMaps fmaps;      // weights with whole-layer boxes (the fused evaluation kernel)
+    MlpFusedMaps fmaps[3];   // weight maps of the fused kernel for clusters of 1, 2 and 4 CTAs
     int fused = 1;           // evaluate with the fused kernel (1) or layer by layer (0)
+    int cluster = 0;         // fused kernel's CTAs per 128-row slab: 1, 2, 4 or 0 (automatic)
+    // tests only (argus_selftest.h): the fused kernel's stage trace, and copies of
+    // each layer's dZ that survive a training step (index l - 1 for dZ_l)
+    float* tr_act = nullptr;
+    float* tr_acc = nullptr;
+    int64_t tr_rows = 0;
+    float* keep_dz32[kMlpLayers - 1] = {};
+    __nv_bfloat16* keep_dz16[kMlpLayers - 1] = {};
+    int last_rows = 0;       // padded rows of the last training step
+    float* loss_dev = nullptr;   // loss of the last argus_surrogate_train_step (packed form)
 };
 
 namespace {
@@ -331,10 +342,22 @@ void free_all(argus_surrogate* s) {
         cudaFree(s->Z[l]);
     }
     cudaFree(s->Y); cudaFree(s->dY); cudaFree(s->dYT); cudaFree(s->row_loss); cudaFree(s->err);
-    cudaFree(s->Hq); cudaFree(s->base); cudaFree(s->gbase);
+    cudaFree(s->Hq); cudaFree(s->base); cudaFree(s->gbase); cudaFree(s->loss_dev);
     for (int i = 0; i < 2; ++i) {
         cudaFree(s->dZ32[i]); cudaFree(s->dZ16[i]); cudaFree(s->dZT[i]);
     }
+    for (int l = 0; l < kMlpLayers - 1; ++l) {
+        cudaFree(s->keep_dz32[l]); cudaFree(s->keep_dz16[l]);
+    }
+}
+
+// Tests: copy dZ_l of the current training step (FP32 and BF16) to the kept buffers.
+argus_status keep_dz(argus_surrogate* s, int l, int cur, int rows, cudaStream_t st) {
+    if (!s->keep_dz32[0]) return ARGUS_OK;
+    const size_t n = size_t(rows) * kMlpHidden;
+    SCK(cudaMemcpyAsync(s->keep_dz32[l - 1], s->dZ32[cur], n * 4, cudaMemcpyDeviceToDevice, st));
+    SCK(cudaMemcpyAsync(s->keep_dz16[l - 1], s->dZ16[cur], n * 2, cudaMemcpyDeviceToDevice, st));
+    return ARGUS_OK;
 }
 
 argus_status build_maps(argus_surrogate* s) {
@@ -347,9 +370,12 @@ argus_status build_maps(argus_surrogate* s) {
         ok &= make_tmap_bf16(&s->tmHT[l], s->HT[l], kIn[l], R, kIn[l] == 64 ? 64 : 128);
     }
     ok &= make_tmap_bf16(&s->tmWT0_b64, s->W16T[0], kIn[0], kOut[0], 64);
-    for (int l = 0; l < kMlpLayers; ++l) ok &= make_tmap_bf16(&s->fmaps.w[l], s->W16[l], kOut[l], kIn[l], kOut[l]);
-    for (int l = 0; l < kMlpLayers - 1; ++l)
-        ok &= make_tmap_bf16(&s->fmaps.wt[l], s->W16T[l], kIn[l], kOut[l], kIn[l]);
+    for (int c = 0; c < 3; ++c) {   // cluster of 1 << c CTAs: each loads 1 / (1 << c) of the rows
+        for (int l = 0; l < kMlpLayers; ++l)
+            ok &= make_tmap_bf16(&s->fmaps[c].w[l], s->W16[l], kOut[l], kIn[l], kOut[l] >> c);
+        for (int l = 0; l < kMlpLayers - 1; ++l)
+            ok &= make_tmap_bf16(&s->fmaps[c].wt[l], s->W16T[l], kIn[l], kOut[l], kIn[l] >> c);
+    }
     ok &= make_tmap_bf16(&s->tmdY, s->dY, R, kMlpOutPad, 128);
     ok &= make_tmap_bf16(&s->tmdYT, s->dYT, kMlpOutPad, R, 64);
     for (int i = 0; i < 2; ++i) {
@@ -381,6 +407,9 @@ MlpFusedArgs fused_args(const argus_surrogate* s, bool with_grad) {
     fa.Hq = s->has_baseline ? s->Hq : nullptr;
     fa.mode = !with_grad ? kFusedValue : (s->grad_mode == 1 ? kFusedValueGrad : kFusedGradHead);
     fa.err = s->err;
+    fa.tr_act = s->tr_act;
+    fa.tr_acc = s->tr_acc;
+    fa.tr_stride = s->tr_rows * kMlpHidden;
     return fa;
 }
 
@@ -470,6 +499,10 @@ bool dev_ptr(const void* p) {
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+argus_status train_step_impl(argus_surrogate* s, const float* theta, const float* loglik,
+                             int ll_stride, const float* grad, int g_stride, int64_t n, float lr,
+                             float* loss, cudaStream_t st);
+
 }  // namespace
 
 extern "C" {
@@ -480,8 +513,8 @@ int64_t argus_surrogate_param_count(void) {
     return n;
 }
 
-argus_status argus_surrogate_create(int32_t device, int32_t max_rows, uint64_t seed,
-                                    argus_surrogate** out) {
+argus_status argus_surrogate_create_ex(int32_t device, int32_t max_rows, uint64_t seed,
+                                       argus_surrogate** out) {
     if (!out) return sfail(ARGUS_ERR_INVALID_ARG, "out is NULL");
     if (max_rows < 1 || max_rows > (1 << 20)) return sfail(ARGUS_ERR_INVALID_ARG, "max_rows out of range");
     int ndev = 0;
@@ -520,6 +553,7 @@ argus_status argus_surrogate_create(int32_t device, int32_t max_rows, uint64_t s
     A(dalloc(&s->base, R));
     A(dalloc(&s->gbase, R * kMlpIn));
     A(dalloc(&s->err, 1));
+    A(dalloc(&s->loss_dev, 1));
     if (!st) {
         // fan-in scaled normal weights from a seeded host generator (Box-Muller on splitmix64)
         std::vector<float> w;
@@ -662,13 +696,19 @@ argus_status argus_surrogate_eval(argus_surrogate* s, const float* theta, int64_
     if (s->fused) {
         // one launch per max_rows rows: every layer (and the value output's
         // back-propagation) in one kernel; Z[1..4] hold gelu'(z) as scratch
+        if (s->tr_act && B > s->tr_rows)
+            return sfail(ARGUS_ERR_INVALID_ARG, "batch larger than the stage trace");
         MlpFusedArgs fa = fused_args(s, grad != nullptr);
         for (int64_t r0 = 0; r0 < B; r0 += s->rows) {
             fa.n = std::min<int64_t>(s->rows, B - r0);
             fa.theta = theta + r0 * kMlpIn;
             fa.loglik = loglik + r0;
             fa.grad = grad ? grad + r0 * kMlpIn : nullptr;
-            SCK(launch_mlp_fused(s->fmaps, fa, st));
+            if (s->tr_act) {
+                fa.tr_act = s->tr_act + r0 * kMlpHidden;
+                fa.tr_acc = s->tr_acc + r0 * kMlpHidden;
+            }
+            SCK(launch_mlp_fused(s->fmaps, fa, st, s->cluster));
         }
         return ARGUS_OK;
     }
@@ -711,6 +751,8 @@ argus_status argus_surrogate_eval_f64(argus_surrogate* s, const double* z, const
     if (!dev_ptr(z) || !dev_ptr(centre) || !dev_ptr(loglik) || (grad && !dev_ptr(grad)))
         return sfail(ARGUS_ERR_INVALID_ARG, "argus_surrogate_eval_f64 needs device pointers");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (s->tr_act && B > s->tr_rows)
+        return sfail(ARGUS_ERR_INVALID_ARG, "batch larger than the stage trace");
     MlpFusedArgs fa = fused_args(s, grad != nullptr);
     fa.zc = centre;
     fa.off = offset;
@@ -719,23 +761,57 @@ argus_status argus_surrogate_eval_f64(argus_surrogate* s, const double* z, const
         fa.z64 = z + r0 * kMlpIn;
         fa.ll64 = loglik + r0;
         fa.g64 = grad ? grad + r0 * kMlpIn : nullptr;
-        SCK(launch_mlp_fused(s->fmaps, fa, st));
+        if (s->tr_act) {
+            fa.tr_act = s->tr_act + r0 * kMlpHidden;
+            fa.tr_acc = s->tr_acc + r0 * kMlpHidden;
+        }
+        SCK(launch_mlp_fused(s->fmaps, fa, st, s->cluster));
     }
     return ARGUS_OK;
 }
 
-argus_status argus_surrogate_train_step(argus_surrogate* s, const float* theta, const float* loglik,
-                                        const float* grad, int64_t n, float lr, float* loss,
-                                        void* stream) {
+argus_status argus_surrogate_train_step_ex(argus_surrogate* s, const float* theta,
+                                           const float* loglik, const float* grad, int64_t n,
+                                           float lr, float* loss, void* stream) {
     if (!s) return sfail(ARGUS_ERR_INVALID_ARG, "surrogate handle is NULL");
-    if (n < 1 || n > s->rows)
-        return sfail(ARGUS_ERR_INVALID_ARG, "n must be in 1..max_rows (rounded up to 256)");
     if (!theta || !loglik || !grad || !loss) return sfail(ARGUS_ERR_INVALID_ARG, "NULL argument");
-    if (!(lr > 0.0f) || !std::isfinite(lr)) return sfail(ARGUS_ERR_INVALID_ARG, "lr must be > 0");
     DeviceGuardS guard(s->device);
     if (!dev_ptr(theta) || !dev_ptr(loglik) || !dev_ptr(grad) || !dev_ptr(loss))
         return sfail(ARGUS_ERR_INVALID_ARG, "argus_surrogate_train_step needs device pointers");
-    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    return train_step_impl(s, theta, loglik, 1, grad, kMlpIn, n, lr, loss,
+                           reinterpret_cast<cudaStream_t>(stream));
+}
+
+argus_status argus_surrogate_train_step(argus_surrogate* s, const float* x, const float* y, int64_t n,
+                                        float lr, void* stream) {
+    if (!s) return sfail(ARGUS_ERR_INVALID_ARG, "surrogate handle is NULL");
+    if (!x || !y) return sfail(ARGUS_ERR_INVALID_ARG, "NULL argument");
+    DeviceGuardS guard(s->device);
+    if (!dev_ptr(x) || !dev_ptr(y))
+        return sfail(ARGUS_ERR_INVALID_ARG, "argus_surrogate_train_step needs device pointers");
+    // y rows are (loglik, gradient[47]): strided views, no copy
+    return train_step_impl(s, x, y, kMlpOut, y + 1, kMlpOut, n, lr, s->loss_dev,
+                           reinterpret_cast<cudaStream_t>(stream));
+}
+
+argus_status argus_surrogate_last_loss(argus_surrogate* s, float* loss) {
+    if (!s || !loss) return sfail(ARGUS_ERR_INVALID_ARG, "NULL argument");
+    DeviceGuardS guard(s->device);
+    SCK(cudaDeviceSynchronize());
+    SCK(cudaMemcpy(loss, s->loss_dev, sizeof(float), cudaMemcpyDeviceToHost));
+    return ARGUS_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+argus_status train_step_impl(argus_surrogate* s, const float* theta, const float* loglik,
+                             int ll_stride, const float* grad, int g_stride, int64_t n, float lr,
+                             float* loss, cudaStream_t st) {
+    if (n < 1 || n > s->rows)
+        return sfail(ARGUS_ERR_INVALID_ARG, "n must be in 1..max_rows (rounded up to 256)");
+    if (!(lr > 0.0f) || !std::isfinite(lr)) return sfail(ARGUS_ERR_INVALID_ARG, "lr must be > 0");
     const int rows = int(((n + 127) / 128) * 128);
     const int ck = (rows % 256 == 0) ? 256 : 128;   // K per split-K chunk over the batch
     const int chunks = rows / ck;
@@ -745,7 +821,8 @@ argus_status argus_surrogate_train_step(argus_surrogate* s, const float* theta, 
     if (e) return e;
     if (s->has_baseline)
         k_baseline<<<rc_grid(int(n)), rc_block(), 0, st>>>(theta, n, s->Hq, s->base, s->gbase);
-    k_loss<<<rc_grid(rows), rc_block(), 0, st>>>(s->Y, loglik, grad, s->has_baseline ? s->base : nullptr,
+    k_loss<<<rc_grid(rows), rc_block(), 0, st>>>(s->Y, loglik, ll_stride, grad, g_stride,
+                                               s->has_baseline ? s->base : nullptr,
                                                s->has_baseline ? s->gbase : nullptr, n, rows, s->norm,
                                                s->dY, s->dYT, s->rows, s->row_loss);
     k_loss_sum<<<1, kSumThreads, 0, st>>>(s->row_loss, rows, n, loss);
@@ -771,6 +848,7 @@ argus_status argus_surrogate_train_step(argus_surrogate* s, const float* theta, 
         ce = launch_gemm_tc(&s->tmdY, &s->tmWT[4], rows, kMlpHidden, kMlpOutPad, 128, 1, kEpiGeluBwd, d,
                             s->err, st);
         if (ce != cudaSuccess) return scuda(ce, "dH4 GEMM");
+        if ((e = keep_dz(s, 4, 0, rows, st))) return e;
     }
     // hidden layers l = 3..0: cur holds dZ_{l+1}
     int cur = 0;
@@ -798,9 +876,11 @@ argus_status argus_surrogate_train_step(argus_surrogate* s, const float* theta, 
                                 kEpiGeluBwd, d, s->err, st);
             if (ce != cudaSuccess) return scuda(ce, "dH GEMM");
             cur ^= 1;
+            if ((e = keep_dz(s, l, cur, rows, st))) return e;
         }
     }
     s->last_chunks = chunks;
+    s->last_rows = rows;
     // Adam
     s->step += 1;
     const float c1 = float(1.0 - std::pow(0.9, s->step));
@@ -817,6 +897,10 @@ argus_status argus_surrogate_train_step(argus_surrogate* s, const float* theta, 
     return ARGUS_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
 argus_status argus_surrogate_set_grad_mode(argus_surrogate* s, int32_t mode) {
     if (!s) return sfail(ARGUS_ERR_INVALID_ARG, "surrogate handle is NULL");
     if (mode != 0 && mode != 1) return sfail(ARGUS_ERR_INVALID_ARG, "mode must be 0 or 1");
@@ -831,6 +915,14 @@ argus_status argus_surrogate_set_fused(argus_surrogate* s, int32_t on) {
     return ARGUS_OK;
 }
 
+argus_status argus_surrogate_set_cluster(argus_surrogate* s, int32_t ctas) {
+    if (!s) return sfail(ARGUS_ERR_INVALID_ARG, "surrogate handle is NULL");
+    if (ctas != 0 && ctas != 1 && ctas != 2 && ctas != 4)
+        return sfail(ARGUS_ERR_INVALID_ARG, "ctas must be 0, 1, 2 or 4");
+    s->cluster = ctas;
+    return ARGUS_OK;
+}
+
 argus_status argus_surrogate_check(argus_surrogate* s) {
     if (!s) return sfail(ARGUS_ERR_INVALID_ARG, "surrogate handle is NULL");
     DeviceGuardS guard(s->device);
@@ -839,6 +931,175 @@ argus_status argus_surrogate_check(argus_surrogate* s) {
 }
 
 const char* argus_surrogate_last_error(void) { return g_sur_error.c_str(); }
+
+// ---------------------------------------------------------------------------
+// The surrogate of one array's log-likelihood, and its weights file.
+// File layout (little-endian): 8 bytes "ARGUSNN1"; int32 version (1), number
+// of parameters, input width (47), has_baseline; FP32 parameters (flat
+// layout), x_mean[47], x_std[47], y_mean, y_std, value weight, gradient
+// weight; FP32 H[47][47] if has_baseline.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr char kMagic[8] = {'A', 'R', 'G', 'U', 'S', 'N', 'N', '1'};
+constexpr int32_t kFileVersion = 1;
+constexpr int32_t kDefaultRows = 4096;
+constexpr uint64_t kDefaultSeed = 20251013ull;
+
+struct FileCloser {
+    FILE* f;
+    ~FileCloser() { if (f) fclose(f); }
+};
+
+}  // namespace
+
+argus_status argus_surrogate_create(const argus_array* array, const char* weights_path_or_null,
+                                    argus_surrogate** out) {
+    if (!array || !out) return sfail(ARGUS_ERR_INVALID_ARG, "NULL array or out");
+    const int32_t dim = argus_array_dim(array);
+    if (dim != kMlpIn)
+        return sfail(ARGUS_ERR_UNSUPPORTED,
+                     "the network takes 47 inputs: a 20-pulsar array with random-walk red noise, "
+                     "no pulsar term (this array has D = " + std::to_string(dim) + ")");
+    std::vector<float> params, tail, H;
+    int32_t has_baseline = 0;
+    if (weights_path_or_null) {
+        FileCloser fc{fopen(weights_path_or_null, "rb")};
+        if (!fc.f) return sfail(ARGUS_ERR_INVALID_ARG, std::string("cannot open ") + weights_path_or_null);
+        char magic[8];
+        int32_t hdr[4];
+        if (fread(magic, 1, 8, fc.f) != 8 || memcmp(magic, kMagic, 8) != 0 ||
+            fread(hdr, sizeof(int32_t), 4, fc.f) != 4)
+            return sfail(ARGUS_ERR_INVALID_ARG, "not an argus surrogate weights file");
+        if (hdr[0] != kFileVersion || hdr[1] != argus_surrogate_param_count() || hdr[2] != kMlpIn ||
+            (hdr[3] != 0 && hdr[3] != 1))
+            return sfail(ARGUS_ERR_INVALID_ARG, "weights file: unsupported version or shape");
+        has_baseline = hdr[3];
+        params.resize(size_t(hdr[1]));
+        tail.resize(2 * kMlpIn + 4);
+        if (fread(params.data(), 4, params.size(), fc.f) != params.size() ||
+            fread(tail.data(), 4, tail.size(), fc.f) != tail.size())
+            return sfail(ARGUS_ERR_INVALID_ARG, "weights file is truncated");
+        if (has_baseline) {
+            H.resize(size_t(kMlpIn) * kMlpIn);
+            if (fread(H.data(), 4, H.size(), fc.f) != H.size())
+                return sfail(ARGUS_ERR_INVALID_ARG, "weights file is truncated");
+        }
+        for (float v : params)
+            if (!std::isfinite(v)) return sfail(ARGUS_ERR_INVALID_ARG, "weights file holds a non-finite weight");
+    }
+    argus_surrogate* s = nullptr;
+    argus_status st = argus_surrogate_create_ex(argus_array_device(array), kDefaultRows, kDefaultSeed, &s);
+    if (st) return st;
+    if (weights_path_or_null) {
+        const float* t = tail.data();
+        if (!st) st = argus_surrogate_set_weights(s, params.data());
+        if (!st) st = argus_surrogate_set_normalizers(s, t, t + kMlpIn, t[2 * kMlpIn], t[2 * kMlpIn + 1],
+                                                      t[2 * kMlpIn + 2], t[2 * kMlpIn + 3]);
+        if (!st && has_baseline) st = argus_surrogate_set_baseline(s, H.data());
+        if (st) {
+            argus_surrogate_destroy(s);
+            return st;
+        }
+    }
+    *out = s;
+    return ARGUS_OK;
+}
+
+argus_status argus_surrogate_save(argus_surrogate* s, const char* path) {
+    if (!s || !path) return sfail(ARGUS_ERR_INVALID_ARG, "NULL argument");
+    std::vector<float> params(static_cast<size_t>(argus_surrogate_param_count()), 0.0f);
+    argus_status st = argus_surrogate_get_weights(s, params.data());
+    if (st) return st;
+    std::vector<float> H;
+    if (s->has_baseline) {
+        DeviceGuardS guard(s->device);
+        H.resize(size_t(kMlpIn) * kMlpIn);
+        SCK(cudaMemcpy(H.data(), s->Hq, H.size() * 4, cudaMemcpyDeviceToHost));
+    }
+    std::vector<float> tail(2 * kMlpIn + 4);
+    for (int k = 0; k < kMlpIn; ++k) {
+        tail[k] = s->norm.xm[k];
+        tail[kMlpIn + k] = s->norm.xs[k];
+    }
+    tail[2 * kMlpIn] = s->norm.ym;
+    tail[2 * kMlpIn + 1] = s->norm.ys;
+    tail[2 * kMlpIn + 2] = s->norm.w[0];
+    tail[2 * kMlpIn + 3] = s->norm.w[1];
+    const int32_t hdr[4] = {kFileVersion, int32_t(params.size()), kMlpIn, s->has_baseline ? 1 : 0};
+    FileCloser fc{fopen(path, "wb")};
+    if (!fc.f) return sfail(ARGUS_ERR_INVALID_ARG, std::string("cannot write ") + path);
+    bool ok = fwrite(kMagic, 1, 8, fc.f) == 8 && fwrite(hdr, 4, 4, fc.f) == 4 &&
+              fwrite(params.data(), 4, params.size(), fc.f) == params.size() &&
+              fwrite(tail.data(), 4, tail.size(), fc.f) == tail.size() &&
+              (H.empty() || fwrite(H.data(), 4, H.size(), fc.f) == H.size());
+    ok = (fclose(fc.f) == 0) && ok;
+    fc.f = nullptr;
+    return ok ? ARGUS_OK : sfail(ARGUS_ERR_CUDA, std::string("write failed: ") + path);
+}
+
+argus_status argus_selftest_surrogate_trace(argus_surrogate* s, float* act, float* acc, int64_t rows) {
+    if (!s) return sfail(ARGUS_ERR_INVALID_ARG, "surrogate handle is NULL");
+    if (!act != !acc || (act && rows < 1)) return sfail(ARGUS_ERR_INVALID_ARG, "bad trace buffers");
+    DeviceGuardS guard(s->device);
+    if (act && (!dev_ptr(act) || !dev_ptr(acc)))
+        return sfail(ARGUS_ERR_INVALID_ARG, "trace buffers must be device memory");
+    s->tr_act = act;
+    s->tr_acc = acc;
+    s->tr_rows = act ? rows : 0;
+    return ARGUS_OK;
+}
+
+argus_status argus_selftest_surrogate_keep(argus_surrogate* s, int32_t on) {
+    if (!s || (on != 0 && on != 1)) return sfail(ARGUS_ERR_INVALID_ARG, "bad argument");
+    DeviceGuardS guard(s->device);
+    SCK(cudaDeviceSynchronize());
+    for (int l = 0; l < kMlpLayers - 1; ++l) {
+        cudaFree(s->keep_dz32[l]); cudaFree(s->keep_dz16[l]);
+        s->keep_dz32[l] = nullptr; s->keep_dz16[l] = nullptr;
+    }
+    if (on) {
+        const size_t n = size_t(s->rows) * kMlpHidden;
+        for (int l = 0; l < kMlpLayers - 1; ++l) {
+            argus_status st = dalloc(&s->keep_dz32[l], n);
+            if (!st) st = dalloc(&s->keep_dz16[l], n);
+            if (st) return st;
+        }
+    }
+    return ARGUS_OK;
+}
+
+argus_status argus_selftest_surrogate_buffer(argus_surrogate* s, int32_t which, int32_t layer,
+                                             void* host, int64_t bytes) {
+    if (!s || !host) return sfail(ARGUS_ERR_INVALID_ARG, "NULL argument");
+    if (s->last_rows < 1) return sfail(ARGUS_ERR_INVALID_ARG, "no training step yet");
+    const size_t R = size_t(s->last_rows);
+    const void* src = nullptr;
+    size_t n = 0;
+    switch (which) {
+        case 0:
+            if (layer < 0 || layer >= kMlpLayers) break;
+            src = s->H[layer]; n = R * kIn[layer] * 2; break;
+        case 1:
+            if (layer < 1 || layer >= kMlpLayers) break;
+            src = s->Z[layer]; n = R * kMlpHidden * 4; break;
+        case 2: src = s->Y; n = R * kMlpOutPad * 4; break;
+        case 3: src = s->dY; n = R * kMlpOutPad * 2; break;
+        case 4:
+            if (layer < 1 || layer >= kMlpLayers) break;
+            src = s->keep_dz32[layer - 1]; n = R * kMlpHidden * 4; break;
+        case 5:
+            if (layer < 1 || layer >= kMlpLayers) break;
+            src = s->keep_dz16[layer - 1]; n = R * kMlpHidden * 2; break;
+        default: break;
+    }
+    if (!src) return sfail(ARGUS_ERR_INVALID_ARG, "no such buffer (or dZ not kept)");
+    if (bytes != int64_t(n)) return sfail(ARGUS_ERR_INVALID_ARG, "byte count does not match");
+    DeviceGuardS guard(s->device);
+    SCK(cudaDeviceSynchronize());
+    SCK(cudaMemcpy(host, src, n, cudaMemcpyDeviceToHost));
+    return ARGUS_OK;
+}
 
 argus_status argus_selftest_surrogate_grads(argus_surrogate* s, float* grads) {
     if (!s || !grads || s->last_chunks < 1) return sfail(ARGUS_ERR_INVALID_ARG, "no training step yet");

@@ -23,8 +23,11 @@ def _lib():
         vp = ctypes.c_void_p
         lib.argus_surrogate_param_count.restype = ctypes.c_int64
         lib.argus_surrogate_param_count.argtypes = []
-        lib.argus_surrogate_create.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64,
-                                               ctypes.POINTER(vp)]
+        lib.argus_surrogate_create_ex.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64,
+                                                  ctypes.POINTER(vp)]
+        lib.argus_surrogate_create.argtypes = [vp, ctypes.c_char_p, ctypes.POINTER(vp)]
+        lib.argus_surrogate_save.argtypes = [vp, ctypes.c_char_p]
+        lib.argus_surrogate_last_loss.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
         lib.argus_surrogate_destroy.argtypes = [vp]
         lib.argus_surrogate_destroy.restype = None
         lib.argus_surrogate_set_normalizers.argtypes = [vp, vp, vp, ctypes.c_float, ctypes.c_float,
@@ -33,11 +36,13 @@ def _lib():
         lib.argus_surrogate_set_baseline.argtypes = [vp, vp]
         lib.argus_surrogate_set_grad_mode.argtypes = [vp, ctypes.c_int32]
         lib.argus_surrogate_set_fused.argtypes = [vp, ctypes.c_int32]
+        lib.argus_surrogate_set_cluster.argtypes = [vp, ctypes.c_int32]
         lib.argus_surrogate_eval_f64.argtypes = [vp, vp, vp, ctypes.c_double, ctypes.c_int64, vp, vp, vp]
         lib.argus_surrogate_get_weights.argtypes = [vp, vp]
         lib.argus_surrogate_eval.argtypes = [vp, vp, ctypes.c_int64, vp, vp, vp]
-        lib.argus_surrogate_train_step.argtypes = [vp, vp, vp, vp, ctypes.c_int64, ctypes.c_float,
-                                                   vp, vp]
+        lib.argus_surrogate_train_step_ex.argtypes = [vp, vp, vp, vp, ctypes.c_int64, ctypes.c_float,
+                                                      vp, vp]
+        lib.argus_surrogate_train_step.argtypes = [vp, vp, vp, ctypes.c_int64, ctypes.c_float, vp]
         lib.argus_surrogate_check.argtypes = [vp]
         lib.argus_surrogate_last_error.restype = ctypes.c_char_p
         lib.argus_selftest_surrogate_grads.argtypes = [vp, vp]
@@ -55,15 +60,30 @@ def param_count() -> int:
 
 
 class Surrogate:
-    """argus_surrogate_create / eval / train_step."""
+    """argus_surrogate_create_ex / eval / train_step (argus_surrogate_create
+    through from_array)."""
 
-    def __init__(self, device: int = 0, max_rows: int = 4096, seed: int = 1):
+    def __init__(self, device: int = 0, max_rows: int = 4096, seed: int = 1, _handle=None):
         lib = _lib()
-        h = ctypes.c_void_p()
-        _check(lib.argus_surrogate_create(device, max_rows, seed, ctypes.byref(h)))
+        h = _handle
+        if h is None:
+            h = ctypes.c_void_p()
+            _check(lib.argus_surrogate_create_ex(device, max_rows, seed, ctypes.byref(h)))
         self.handle = h
         self.device = device
         self.max_rows = max_rows
+
+    @classmethod
+    def from_array(cls, array, weights_path=None):
+        """argus_surrogate_create: the surrogate of `array` (an argus.Array with
+        D = 47), from a file argus_surrogate_save wrote, or freshly initialised."""
+        h = ctypes.c_void_p()
+        path = None if weights_path is None else str(weights_path).encode()
+        _check(_lib().argus_surrogate_create(array.handle, path, ctypes.byref(h)))
+        return cls(device=array.device, max_rows=4096, _handle=h)
+
+    def save(self, path):
+        _check(_lib().argus_surrogate_save(self.handle, str(path).encode()))
 
     def close(self):
         if getattr(self, "handle", None):
@@ -99,6 +119,10 @@ class Surrogate:
     def set_fused(self, on: bool):
         """Evaluate with the fused kernel (True, default) or layer by layer."""
         _check(_lib().argus_surrogate_set_fused(self.handle, 1 if on else 0))
+
+    def set_cluster(self, ctas: int):
+        """CTAs of the fused kernel per 128-row slab: 1, 2, 4, or 0 (automatic)."""
+        _check(_lib().argus_surrogate_set_cluster(self.handle, int(ctas)))
 
     def set_weights(self, flat):
         flat = np.ascontiguousarray(flat, dtype=np.float32)
@@ -148,14 +172,30 @@ class Surrogate:
         return (loglik, grad) if with_grad else loglik
 
     def train_step(self, theta, loglik, grad, lr, loss_out=None, stream=None):
+        """argus_surrogate_train_step_ex: targets in separate arrays; returns the
+        loss (device tensor) before the step."""
         import torch
         n = theta.shape[0]
         if loss_out is None:
             loss_out = torch.empty(1, dtype=torch.float32, device=theta.device)
         s = stream if stream is not None else torch.cuda.current_stream(theta.device).cuda_stream
-        _check(_lib().argus_surrogate_train_step(self.handle, theta.data_ptr(), loglik.data_ptr(),
-                                                 grad.data_ptr(), n, float(lr), loss_out.data_ptr(), s))
+        _check(_lib().argus_surrogate_train_step_ex(self.handle, theta.data_ptr(), loglik.data_ptr(),
+                                                    grad.data_ptr(), n, float(lr), loss_out.data_ptr(),
+                                                    s))
         return loss_out
+
+    def train_step_packed(self, x, y, lr, stream=None):
+        """argus_surrogate_train_step: y [n][48] = (loglik, gradient)."""
+        import torch
+        assert x.is_contiguous() and y.is_contiguous() and y.shape[1] == N_OUT
+        s = stream if stream is not None else torch.cuda.current_stream(x.device).cuda_stream
+        _check(_lib().argus_surrogate_train_step(self.handle, x.data_ptr(), y.data_ptr(), x.shape[0],
+                                                 float(lr), s))
+
+    def last_loss(self) -> float:
+        v = ctypes.c_float()
+        _check(_lib().argus_surrogate_last_loss(self.handle, ctypes.byref(v)))
+        return float(v.value)
 
     def check(self):
         _check(_lib().argus_surrogate_check(self.handle))
