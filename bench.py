@@ -48,7 +48,10 @@ FLOPS_PER_LANE_STEP_GRAD = 120
 # the gradient counted, as above, as 3x the forward.
 FLOPS_PER_LANE_STEP_FWD_OU = 79
 FLOPS_PER_LANE_STEP_GRAD_OU = 3 * FLOPS_PER_LANE_STEP_FWD_OU
+# FP64 instructions (DFMA + DMUL + DADD, thread-level) per lane-step, counted
+# by ncu (profiles/traffic.json, with the source hash they were taken on)
 LOGLIK_WORKLOAD = "psr20_toa500-2000_w4096"
+PSR67_WORKLOAD = "psr67_toa5000_w1024"
 OU_WORKLOAD = "psr20_toa500-2000_w4096"
 L2_FLUSH_BYTES = 256 << 20
 CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -83,6 +86,12 @@ def parse_args():
                     help="skip the Hellings-Downs GW-background leg (20 pulsars, joint filter)")
     ap.add_argument("--gwb-batch", type=int, default=1216,
                     help="parameter vectors of the GW-background leg")
+    ap.add_argument("--no-psr67", action="store_true",
+                    help="skip the 67-pulsar x 5000-TOA x 1024-walker loglik+grad leg")
+    ap.add_argument("--no-da", action="store_true",
+                    help="skip the delayed-acceptance HMC leg (surrogate vs exact HMC, 4096 chains)")
+    ap.add_argument("--no-fp64-probe", action="store_true",
+                    help="skip the measured FP64 FMA-rate leg")
     ap.add_argument("--autotune", choices=["cache", "off", "force"], default="cache",
                     help="cache: use the tuned-plan cache, tuning on a miss; force: retune")
     ap.add_argument("--tune-batch", type=int, default=4096)
@@ -98,10 +107,8 @@ def parse_args():
 
 
 def dist_env():
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return world, rank, local
+    from paper_2510_11077_gb300 import dist as pdist
+    return pdist.env()
 
 
 class ClockSampler:
@@ -161,6 +168,51 @@ def traffic_record(kernel: str):
         return None
     from paper_2510_11077_gb300 import autotune
     return rec if rec.get("source_sha") == autotune.source_hash() else None
+
+
+def fp64_rate(local, iters=65536, launches=3):
+    """Measured FP64 FMA issue rate of this GPU (argus_selftest_dfma_rate:
+    independent FMA chains, 2048 threads per SM; four operand and chain
+    variants, the fastest taken), with nvidia-smi clocks sampled while it
+    runs.  Returns the best variant's median launch in FMA/s and the FLOP/s
+    peak it implies (2 flop per FMA)."""
+    import ctypes
+
+    from paper_2510_11077_gb300 import argus
+    lib = argus.load()
+    lib.argus_selftest_dfma_rate.argtypes = [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                             ctypes.c_void_p, ctypes.c_void_p]
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    clocks = ClockSampler(vis.split(",")[local] if vis else str(local))
+    clocks.start()
+    time.sleep(0.3)
+    names = ["8 chains, parameter operands", "8 chains, register operands", "4 chains",
+             "16 chains"]
+    variants = {}
+    for v, name in enumerate(names):
+        rate = (ctypes.c_double * launches)()
+        ms = (ctypes.c_float * launches)()
+        st = lib.argus_selftest_dfma_rate(iters, launches, v, rate, ms)
+        if st != 0:
+            clocks.stop()
+            raise RuntimeError(f"argus_selftest_dfma_rate failed with status {st}")
+        variants[name] = {"fma_per_s": statistics.median(rate), "launch_ms": list(ms)}
+    clk = clocks.stop()
+    best = max(variants, key=lambda k: variants[k]["fma_per_s"])
+    med = variants[best]["fma_per_s"]
+    n_sm = None
+    try:
+        import torch
+        n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    except Exception:
+        pass
+    out = {"fma_per_s": med, "tflops": 2 * med / 1e12, "best_variant": best, "variants": variants,
+           "clocks": clk,
+           "how": f"{launches} launches per variant, 8 x {iters} FMAs per thread, 2048 threads "
+                  f"per SM (CUDA events, median launch of the fastest variant)"}
+    if clk and n_sm:
+        out["fma_per_clk_per_sm"] = med / (n_sm * clk["sm_mhz"] * 1e6)
+    return out
 
 
 def _oracle_rate(data, theta, threads, seconds):
@@ -255,7 +307,7 @@ def run_reference(args):
     return 0
 
 
-def loglik_only(args, dev, local):
+def loglik_only(args, dev, local, fp64=None):
     """Forward filter alone (K1 -> K2 -> K4) on the 20-pulsar, 4096-walker array:
     loglik evals/s with the forward kernel timed live and its FP64 roofline."""
     import torch
@@ -302,20 +354,16 @@ def loglik_only(args, dev, local):
     torch.cuda.synchronize(dev)
     prior_ms = statistics.mean(a.elapsed_time(b) for a, b in evp)
     lane_steps = w.batch * int(data.n_toa.sum())
-    achieved = FLOPS_PER_LANE_STEP_FWD * lane_steps / (k_ms * 1e-3) / 1e12
     arr.close()
     return {"workload": w.name, "metric": "loglik evals/s", "value": w.batch / (step_ms * 1e-3),
             "ms_per_step": step_ms, "prior_draws_ms_per_step": prior_ms,
             "lane_steps_per_s": lane_steps / (step_ms * 1e-3),
             "plan": res["plan"], "autotune_cached": res["cached"],
-            "roofline": {"bound": "alu", "kernel": "k_filter_fwd", "kernel_ms": k_ms,
-                         "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": achieved / FP64_PEAK_TFLOPS,
-                         "algorithmic": f"{FLOPS_PER_LANE_STEP_FWD} FP64 flop per lane-step x "
-                                        f"{lane_steps} lane-steps per launch"}}
+            "roofline": fp64_roofline("k_filter_fwd", FLOPS_PER_LANE_STEP_FWD, lane_steps, k_ms,
+                                      fp64)}
 
 
-def ou_leg(args, dev, local):
+def ou_leg(args, dev, local, fp64=None):
     """Loglik + gradient with Ornstein-Uhlenbeck red noise (D = 7 + 3P) on the
     20-pulsar, 4096-walker array: evals/s, the adjoint kernel timed live and
     its FP64 roofline."""
@@ -349,18 +397,89 @@ def ou_leg(args, dev, local):
     step_ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
     k_ms = statistics.mean(kern)
     lane_steps = w.batch * int(data.n_toa.sum())
-    achieved = FLOPS_PER_LANE_STEP_GRAD_OU * lane_steps / (k_ms * 1e-3) / 1e12
-    tr = traffic_record("k_filter_grad_ou")
     arr.close()
     return {"workload": w.name + " (Ornstein-Uhlenbeck red noise)", "dim": data.dim,
             "metric": "loglik+grad evals/s", "value": w.batch / (step_ms * 1e-3),
             "ms_per_step": step_ms, "plan": res["plan"], "autotune_cached": res["cached"],
-            "roofline": {"bound": "alu", "kernel": "k_filter_grad<OU>", "kernel_ms": k_ms,
-                         "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": achieved / FP64_PEAK_TFLOPS,
-                         "traffic": tr["dram_bytes_per_launch"] if tr else None,
-                         "algorithmic": f"{FLOPS_PER_LANE_STEP_GRAD_OU} FP64 flop per lane-step x "
-                                        f"{lane_steps} lane-steps per launch"}}
+            "roofline": fp64_roofline("k_filter_grad_ou", FLOPS_PER_LANE_STEP_GRAD_OU, lane_steps,
+                                      k_ms, fp64, traffic=bool(res["plan"].get("tape_cache")))}
+
+
+def psr67_leg(args, dev, local, fp64=None):
+    """Loglik + full gradient (7 GW + 2 noise parameters per pulsar, D = 141)
+    on the 67-pulsar array with 5000 TOAs each and 1024 walkers, through the
+    adjoint kernel with its own autotuned plan: evals/s, the kernel timed live
+    and its FP64 roofline."""
+    import torch
+
+    from paper_2510_11077_gb300 import argus, autotune, inputs
+    w = inputs.WORKLOADS[PSR67_WORKLOAD]
+    data = inputs.make_workload_array(w.name)
+    theta = torch.from_numpy(inputs.make_theta_batch(data, w.batch, seed=w.seed)).to(dev)
+    arr = argus.Array(data, device=local)
+    res = autotune.autotune(arr, theta, data.n_toa, grad=True, batch_for_key=w.batch)
+    ll = torch.empty(w.batch, dtype=torch.float64, device=dev)
+    g = torch.empty((w.batch, data.dim), dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    arr.set_timing(True)
+    for _ in range(3):
+        argus.argus_loglik_grad(arr, theta, ll, g)
+    torch.cuda.synchronize(dev)
+    reps = 10
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(reps)]
+    kern = []
+    for k in range(reps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        argus.argus_loglik_grad(arr, theta, ll, g)
+        ev[k][1].record(stream)
+        kern.append(arr.get_timing()[1])
+    torch.cuda.synchronize(dev)
+    finite = bool(torch.isfinite(ll).all().item() and torch.isfinite(g).all().item())
+    arr.close()
+    step_ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    k_ms = statistics.mean(kern)
+    lane_steps = w.batch * int(data.n_toa.sum())
+    roof = fp64_roofline("k_filter_grad", FLOPS_PER_LANE_STEP_GRAD, lane_steps, k_ms, fp64)
+    return {"workload": w.name, "dim": data.dim, "metric": "loglik+grad evals/s",
+            "value": w.batch / (step_ms * 1e-3), "unit": UNIT, "ms_per_step": step_ms,
+            "lane_steps_per_s": lane_steps / (step_ms * 1e-3), "finite": finite,
+            "plan": res["plan"], "autotune_cached": res["cached"],
+            "l2": "flushed between timed steps (256 MiB write, untimed)", "roofline": roof}
+
+
+def fp64_roofline(kernel, flops_per_lane_step, lane_steps, kernel_ms, fp64=None, traffic=True):
+    """FP64 roofline of one filter launch.  achieved: the algorithmic count
+    (flops_per_lane_step x lane-steps) per event-timed launch; peak: the
+    2 FMA/clk/SM x 152 SMs x 2.07 GHz derived peak; peak_measured and
+    frac_measured: against this run's measured FP64 FMA rate (fp64_rate);
+    fp64_issue_frac: the FP64 instructions the kernel executes per lane-step
+    (ncu count in profiles/traffic.json, taken on the same kernel source) per
+    second, over the measured FMA issue rate -- the FP64 pipe's busy share."""
+    achieved = flops_per_lane_step * lane_steps / (kernel_ms * 1e-3) / 1e12
+    tr = traffic_record(kernel)
+    out = {"bound": "alu", "kernel": kernel, "kernel_ms": kernel_ms, "achieved": achieved,
+           "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+           "peak_source": "derived: 2 FP64 FMA/clk/SM x 152 SMs x 2.07 GHz",
+           "algorithmic": f"{flops_per_lane_step} FP64 flop per lane-step x {lane_steps} "
+                          f"lane-steps per launch",
+           "traffic": (tr["dram_bytes_per_lane_step"] * lane_steps
+                       if tr and traffic and tr.get("dram_bytes_per_lane_step") else None)}
+    if fp64:
+        out["peak_measured"] = fp64["tflops"]
+        out["frac_measured"] = achieved / fp64["tflops"]
+        out["peak_measured_source"] = "argus_selftest_dfma_rate in this run (median launch)"
+    instr = tr.get("fp64_instr_per_lane_step") if tr else None
+    if instr:
+        rate = instr * lane_steps / (kernel_ms * 1e-3)
+        out["fp64_instr_per_lane_step"] = instr
+        out["fp64_instr_per_s"] = rate
+        if fp64:
+            out["fp64_issue_frac"] = rate / fp64["fma_per_s"]
+        out["fp64_issue_frac_derived"] = rate / (FP64_PEAK_TFLOPS * 1e12 / 2)
+    return out
 
 
 def pulsar_term_leg(args, dev, local):
@@ -620,39 +739,37 @@ def run_ours(args):
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    def step():
+    kern = []
+
+    def step(timed):
+        if not timed:
+            argus.argus_loglik_grad(arr, theta, ll, g)
+            return None
+        flush.zero_()                       # evict L2 between timed steps (not timed)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
         argus.argus_loglik_grad(arr, theta, ll, g)
+        e1.record(stream)
+        kern.append(arr.get_timing())
+        return e0, e1
 
     arr.set_timing(True)
-    for _ in range(max(args.warmup, 0)):
-        step()
-    torch.cuda.synchronize(dev)
-
     vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
     gpu_index = vis.split(",")[local] if vis else str(local)
     clocks = ClockSampler(gpu_index) if rank == 0 else None
-    if clocks:
-        clocks.start()
-        time.sleep(0.3)
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize(dev)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    kern = []
-    for k in range(args.steps):
-        flush.zero_()                       # evict L2 between timed steps (not timed)
-        ev[k][0].record(stream)
-        step()
-        ev[k][1].record(stream)
-        kern.append(arr.get_timing())
-    torch.cuda.synchronize(dev)
-    if world > 1:
-        torch.distributed.barrier()
+
+    def start_clocks():
+        if clocks:
+            clocks.start()
+            time.sleep(0.3)
+
+    step_s, total_s = pdist.timed_steps(
+        step, args.steps, args.warmup, sync=lambda: torch.cuda.synchronize(dev),
+        resolve=lambda evs: [a.elapsed_time(b) / 1e3 for a, b in evs], on_start=start_clocks,
+        device=dev)
     clk = clocks.stop() if clocks else None
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = pdist.max_over_ranks(sum(step_ms), device=dev)
-    value = pdist.job_throughput(B * args.steps, world, total_ms / 1e3)
+    total_ms = total_s * 1e3
+    value = pdist.job_throughput(B * args.steps, world, total_s)
     filt_ms = statistics.mean(k[1] for k in kern)
 
     # end to end through the public call with pinned host buffers
@@ -701,28 +818,30 @@ def run_ours(args):
         raise RuntimeError("plain and batched filters disagree")
     arr_p.close()
 
-    loglik_leg = None if args.no_loglik else loglik_only(args, dev, local)
-    ou = None if args.no_ou else ou_leg(args, dev, local)
+    fp64 = None if args.no_fp64_probe else fp64_rate(local)
+    loglik_leg = None if args.no_loglik else loglik_only(args, dev, local, fp64)
+    ou = None if args.no_ou else ou_leg(args, dev, local, fp64)
     pt_leg = None if args.no_pt else pulsar_term_leg(args, dev, local)
     lat = None if args.no_latency else latency_leg(args, dev, local)
     gwb_l = None if args.no_gwb else gwb_leg(args, dev, local)
+    p67 = None if args.no_psr67 else psr67_leg(args, dev, local, fp64)
     lane_steps = B * int(data.n_toa.sum())
     flops = FLOPS_PER_LANE_STEP_GRAD_OU if args.noise == "ou" else FLOPS_PER_LANE_STEP_GRAD
-    achieved = flops * lane_steps / (filt_ms * 1e-3) / 1e12
-    tr = traffic_record("k_filter_grad") if args.noise == "rw" else None
+    kname = "k_filter_grad_ou" if args.noise == "ou" else "k_filter_grad"
+    roofline = fp64_roofline(kname, flops, lane_steps, filt_ms, fp64,
+                             traffic=bool(plan.get("tape_cache")) and not args.pulsar_term)
     peaks, peaks_src = _measured_peaks()
     hbm = peaks.get("hbm_gbs") if peaks else None
-    dram_gbs = tr["dram_bytes_per_launch"] / (filt_ms * 1e-3) / 1e9 if tr else None
-    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS,
-                "traffic": tr["dram_bytes_per_launch"] if tr else None,
-                "dram": {"achieved_gbs": dram_gbs, "peak_gbs": hbm,
-                         "frac": (dram_gbs / hbm) if (dram_gbs and hbm) else None,
-                         "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peaks_src})"},
-                "kernel": "k_filter_grad", "kernel_ms": filt_ms,
-                "peak_source": "derived: 2 FP64 FMA/clk/SM x 152 SMs x 2.07 GHz",
-                "algorithmic": f"{flops} FP64 flop per lane-step x "
-                               f"{lane_steps} lane-steps per launch"}
+    dram_gbs = roofline["traffic"] / (filt_ms * 1e-3) / 1e9 if roofline["traffic"] else None
+    roofline["dram"] = {"achieved_gbs": dram_gbs, "peak_gbs": hbm,
+                        "frac": (dram_gbs / hbm) if (dram_gbs and hbm) else None,
+                        "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peaks_src})"}
+    roofline["headline"] = ("fp64_issue_frac: the FP64 pipe's busy share against the measured FMA "
+                            "rate; frac (the algorithmic count over the derived peak) is kept for "
+                            "the contract's definition")
+    da = None
+    if world == 1 and not args.no_da:
+        da = da_hmc_leg(local)
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(data, theta_np, args.cpu_seconds)
@@ -742,7 +861,8 @@ def run_ours(args):
             "stage_ms": {"project": statistics.mean(k[0] for k in kern), "filter": filt_ms,
                          "reduce": statistics.mean(k[2] for k in kern)},
             "clocks": clk, "cpu_baseline": cpu, "loglik_only": loglik_leg,
-            "ou_red_noise": ou, "pulsar_term": pt_leg, "latency_1psr": lat, "gwb_hd": gwb_l}
+            "ou_red_noise": ou, "pulsar_term": pt_leg, "latency_1psr": lat, "gwb_hd": gwb_l,
+            "psr67_grad": p67, "fp64_peak": fp64, "da_hmc": da}
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -756,22 +876,61 @@ def _measured_peaks():
     return {"bf16_tflops": 1900.0, "hbm_gbs": 6800.0}, "fallback"
 
 
+DA_CONFIG = dict(n_chains=4096, n_train=1_000_000, warmup_iter=200, sample_iter=100, da_iter=400,
+                 n_steps=16, epochs=60, batch=4096, lr=1e-3, value_weight=10.0)
+
+
+def da_hmc_leg(local):
+    """Delayed-acceptance HMC with the surrogate (trained on the GPU on 1e6
+    exact-filter evaluations) against plain exact-filter HMC, both from the
+    same warmed-up state, on the 20-pulsar array with 4096 chains (the
+    configuration of `--mode da-hmc`): min-ESS/s of each, the gain with and
+    without the surrogate's data generation and training, and the posterior
+    agreement (the exact filter is stage 2, so the posterior is unchanged)."""
+    from paper_2510_11077_gb300 import da_experiment
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    clocks = ClockSampler(vis.split(",")[local] if vis else str(local))
+    clocks.start()
+    res = da_experiment.run(device=local, **DA_CONFIG)
+    clk = clocks.stop()
+    h, d = res["hmc"], res["da_hmc"]
+    return {"workload": "psr20_toa500-2000_w4096 TOAs with an injected model source, D = 47",
+            "chains": res["chains"], "leapfrog_steps": res["leapfrog_steps"],
+            "train_rows": res["train_rows"], "epochs": res["epochs"],
+            "exact_hmc": {"min_ess_per_s": h["ess_per_s"], "ess_min": h["ess_min"],
+                          "seconds": h["seconds"], "iters": res["sample_iters"],
+                          "accept": h["accept"], "exact_grad_evals": h["exact_grad_evals"]},
+            "da_hmc": {"min_ess_per_s": d["ess_per_s"], "ess_min": d["ess_min"],
+                       "seconds": d["seconds"], "iters": res["da_iters"],
+                       "accept_stage1": d["accept_stage1"], "accept": d["accept"],
+                       "exact_ll_evals": d["exact_ll_evals"],
+                       "min_ess_per_s_incl_training": d["ess_per_s_incl_training"]},
+            "ess_per_s_gain": res["ess_per_s_gain"],
+            "ess_per_s_gain_incl_training": res["ess_per_s_gain_incl_training"],
+            "ess_per_exact_eval_gain": (d["ess_min"] / max(d["exact_ll_evals"], 1)) /
+                                       (h["ess_min"] / max(h["exact_grad_evals"], 1)),
+            "data_gen_s": res["data_gen_s"], "train_s": res["train_s"],
+            "posterior_mean_z_max": res["posterior_mean_z_max"],
+            "posterior_sd_ratio_range": res["posterior_sd_ratio_range"],
+            "holdout_abs_err_nats_median": res["holdout_abs_err_nats_median"],
+            "clocks": clk, "experiment": res}
+
+
 def run_da_hmc(args):
     """Surrogate-accelerated delayed-acceptance HMC on the 20-pulsar array with
     4096 chains, against plain exact HMC; plus the surrogate network's own
     tensor-core throughput."""
     import torch
 
-    from paper_2510_11077_gb300 import da_experiment, surrogate
+    from paper_2510_11077_gb300 import surrogate
     world, rank, local = dist_env()
     if rank != 0:
         return 0
+    leg = da_hmc_leg(local)
+    res = leg["experiment"]
     clocks = ClockSampler(os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[local]
                           if os.environ.get("CUDA_VISIBLE_DEVICES") else str(local))
     clocks.start()
-    res = da_experiment.run(n_chains=4096, n_train=1_000_000, warmup_iter=200, sample_iter=100,
-                            da_iter=400, n_steps=16, epochs=60, batch=4096, lr=1e-3,
-                            value_weight=10.0, device=local)
     # tensor-core throughput of the surrogate: eval of 4096 rows, and a train step
     dev = torch.device("cuda", local)
     net = surrogate.Surrogate(device=local, max_rows=4096, seed=1)
@@ -820,7 +979,7 @@ def run_da_hmc(args):
             "config": {"workload": "psr20_toa500-2000_w4096 TOAs with an injected model source",
                        "chains": 4096, "surrogate": "MLP 47-4x256-48 GELU, BF16, FP32 accumulate",
                        "train_rows": res["train_rows"]},
-            "da_hmc": res["da_hmc"], "exact_hmc": res["hmc"],
+            "da_hmc": res["da_hmc"], "exact_hmc": res["hmc"], "da_clocks": leg["clocks"],
             "ess_per_s_gain": res["ess_per_s_gain"],
             "ess_per_s_gain_incl_training": res["ess_per_s_gain_incl_training"],
             "posterior_mean_z_max": res["posterior_mean_z_max"],
@@ -867,8 +1026,10 @@ def run_surrogate(args):
         x = torch.from_numpy(rng.standard_normal((rows, 47)).astype(np.float32)).to(dev)
         for name, gm, wg in modes:
             net.set_grad_mode(gm)
-            for fused in (True, False):
+            # fused: automatic cluster size, then 1, 2 and 4 CTAs per slab; then per layer
+            for fused, cl in ((True, 0), (True, 1), (True, 2), (True, 4), (False, 0)):
                 net.set_fused(fused)
+                net.set_cluster(cl)
                 for _ in range(5):
                     net.eval(x, with_grad=wg)
                 torch.cuda.synchronize(dev)
@@ -881,8 +1042,9 @@ def run_surrogate(args):
                 net.check()
                 us = e0.elapsed_time(e1) / 50 * 1e3
                 flop = rows * (fwd_flop + (bwd_flop if gm == 1 and wg else 0))
-                out[f"{rows} rows, {name}, {'fused' if fused else 'per layer'}"] = {
-                    "us": us, "tflops": flop / (us * 1e-6) / 1e12}
+                tag = ("fused" + ("" if cl == 0 else f", cluster {cl}")) if fused else "per layer"
+                out[f"{rows} rows, {name}, {tag}"] = {"us": us, "tflops": flop / (us * 1e-6) / 1e12}
+            net.set_cluster(0)
         net.close()
     key = "4096 rows, value backprop, fused"
     line = {"metric": "surrogate evaluation latency (value + back-propagated gradient, 4096 rows)",

@@ -1,25 +1,60 @@
 """Delayed-acceptance HMC with the trained surrogate against plain exact HMC on
-the 20-pulsar array (reduced sizes): the two posteriors agree within Monte
-Carlo error, and the surrogate reaches useful accuracy."""
+the 20-pulsar array, 4096 chains: the two posteriors agree within Monte Carlo
+error, the surrogate reaches useful accuracy, and the trained network buys
+effective samples -- per exact-filter evaluation and per second."""
 from __future__ import annotations
 
-import numpy as np
+import math
+
 import pytest
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
-def test_da_hmc_matches_exact_hmc_posterior():
+@pytest.fixture(scope="module")
+def res():
     if not torch.cuda.is_available():
         pytest.fail("GPU tests need a CUDA device")
     from paper_2510_11077_gb300 import da_experiment
-    res = da_experiment.run(n_chains=1024, n_train=300_000, warmup_iter=120, sample_iter=60,
-                            da_iter=120, n_steps=12, epochs=30, batch=4096, log=print)
-    print(res)
-    assert res["posterior_mean_z_max"] < 5.0, res
+    # the configuration the bench measures (4096 chains, ~1e6 exact training
+    # rows, 16 leapfrog steps): a smaller training set leaves the surrogate too
+    # rough for the stage-1 acceptance the gain rests on
+    r = da_experiment.run(n_chains=4096, n_train=1_000_000, warmup_iter=200, sample_iter=100,
+                          da_iter=400, n_steps=16, epochs=60, batch=4096, lr=1e-3,
+                          value_weight=10.0, log=print)
+    print({k: v for k, v in r.items() if k not in ("hmc", "da_hmc")})
+    print("hmc", r["hmc"])
+    print("da_hmc", r["da_hmc"])
+    return r
+
+
+def test_da_hmc_matches_exact_hmc_posterior(res):
+    # 47 independent |N(0, 1)| differences exceed 4 with probability 3e-3
+    assert res["posterior_mean_z_max"] < 4.0, res
+    # posterior sd ratio: the relative standard error of an sd estimated from
+    # n effective samples is 1/sqrt(2n); 4 combined errors at the worst ESS
+    tol = 4.0 * math.sqrt(0.5 / res["hmc"]["ess_min"] + 0.5 / res["da_hmc"]["ess_min"])
     lo, hi = res["posterior_sd_ratio_range"]
-    assert 0.8 < lo and hi < 1.25, res
+    assert 1.0 - tol < lo and hi < 1.0 + tol, (res["posterior_sd_ratio_range"], tol)
     # the delayed-acceptance chains move, and stage 2 runs only on stage-1 survivors
-    assert res["da_hmc"]["accept"] > 0.005 and res["da_hmc"]["exact_ll_evals"] > 0
+    assert res["da_hmc"]["accept"] > 0.1 and res["da_hmc"]["exact_ll_evals"] > 0
     assert res["da_hmc"]["exact_ll_evals"] <= res["da_iters"] * res["chains"]
+
+
+def test_surrogate_gains_effective_samples_per_exact_evaluation(res):
+    """Timing-free: min ESS per exact-filter evaluation.  Exact HMC pays one
+    loglik+gradient evaluation per leapfrog step; delayed acceptance pays at
+    most one loglik-only evaluation per iteration (stage-1 survivors only).
+    Counting a cheaper loglik-only call as a full evaluation makes this
+    conservative; the bench measures ~10x, the bound is 4x."""
+    h, d = res["hmc"], res["da_hmc"]
+    per_eval_h = h["ess_min"] / h["exact_grad_evals"]
+    per_eval_d = d["ess_min"] / d["exact_ll_evals"]
+    assert per_eval_d > 4.0 * per_eval_h, (per_eval_d, per_eval_h)
+
+
+def test_surrogate_gains_effective_samples_per_second(res):
+    """Wall clock, sampling phase only (the bench reports the gain with the
+    surrogate's data generation and training counted as well)."""
+    assert res["ess_per_s_gain"] > 4.0, (res["ess_per_s_gain"], res["hmc"], res["da_hmc"])
