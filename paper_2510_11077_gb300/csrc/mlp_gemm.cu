@@ -139,14 +139,15 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
     for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
 }
 
-__device__ __forceinline__ float gelu_f(float z) {
-    return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f));
+// GELU and its derivative from e = erf(z / sqrt 2), so that a caller that needs
+// both evaluates erf once (the same bits as evaluating each on its own)
+__device__ __forceinline__ float erf_gelu(float z) { return erff(z * 0.70710678118654752f); }
+__device__ __forceinline__ float gelu_e(float z, float e) { return 0.5f * z * (1.0f + e); }
+__device__ __forceinline__ float gelu_grad_e(float z, float e) {
+    return 0.5f * (1.0f + e) + z * expf(-0.5f * z * z) * 0.39894228040143268f;
 }
-
-__device__ __forceinline__ float gelu_grad_f(float z) {
-    return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) +
-           z * expf(-0.5f * z * z) * 0.39894228040143268f;
-}
+__device__ __forceinline__ float gelu_f(float z) { return gelu_e(z, erf_gelu(z)); }
+__device__ __forceinline__ float gelu_grad_f(float z) { return gelu_grad_e(z, erf_gelu(z)); }
 
 template <int EPI>
 __device__ __forceinline__ void epilogue(const GemmEpiArgs& e, int row, int col0, int z,
@@ -308,7 +309,7 @@ cudaError_t launch_one(const CUtensorMap* ta, const CUtensorMap* tb, int M, int 
 
 
 // ---------------------------------------------------------------------------
-// Fused evaluation: a cluster of kCl CTAs (1, 2 or 4; 8 warps each) owns 128
+// Fused evaluation: a cluster of kCl CTAs (1, 2 or 4; 8 warps each, 16 with 4) owns 128
 // rows and runs every layer; CTA rank c of the cluster computes the output
 // columns [c N / kCl, (c + 1) N / kCl) of every stage, so that a batch of a few
 // thousand rows still spreads over most SMs and each CTA's epilogue (GELU and
@@ -325,32 +326,53 @@ cudaError_t launch_one(const CUtensorMap* ta, const CUtensorMap* tb, int M, int 
 //   5..8  (kFusedValueGrad) dz_l = (dz_{l+1} W_l) * gelu'(z_l), then dx = dz_1 W_0,
 //         seeded with dz_4 = W_4[0] * gelu'(z_4) (the value output's one-hot)
 // After its epilogue each rank writes its columns of the next activation tile
-// into every rank's shared memory (distributed shared memory stores), then the
-// cluster meets at a barrier before the next stage's MMA.  Rank c's columns of
-// a hidden layer are one (kCl = 4) or two (kCl = 2) whole K-atoms of the next
-// tile.  gelu'(z) of rank c's columns is saved to, and read back from, global
-// scratch by rank c alone (the backward stage's column i needs layer l's
-// column i).  Warp w reads TMEM lanes 32 (w % 4) .. + 31 (its rows) and half
-// (w / 4) of the rank's columns.  Thread 0 issues the copies and the MMAs and
-// alone waits on the mbarriers (bounded); after a timeout the CTA stops
-// computing but still meets every cluster barrier, so no rank waits forever.
+// into its own shared memory, and thread 0 sends them to every other rank
+// with bulk copies (cp.async.bulk, shared::cta -> shared::cluster) that
+// complete on the receiver's mbarrier of that tile; each rank arms its
+// mbarrier with the bytes its peers send and waits on it (bounded) before its
+// next MMA, so no cluster-wide barrier sits between stages.  Rank c's columns of a hidden layer are one (kCl = 4) or two
+// (kCl = 2) whole K-atoms, contiguous in the tile.  The tiles alternate, so a
+// rank writes a tile only after every peer has sent it the next stage's
+// columns, which they do only after their MMA has read that tile.  gelu'(z) of
+// rank c's columns stays with rank c (the backward stage's column i needs
+// layer l's column i): in TMEM behind the accumulator with kCl = 4, else in
+// global scratch.  With kCl = 4 the weight slices are double-buffered and
+// loaded a stage ahead.  Warp w reads TMEM lanes 32 (w % 4) .. + 31 (its rows)
+// and column group w / 4 of the rank's columns (16 columns each with 4-CTA
+// clusters); gelu'(z) is formed only when the value's gradient is
+// back-propagated.  Thread 0 issues the copies and the
+// MMAs and alone waits on the mbarriers (bounded); after a timeout the CTA
+// stops computing but keeps sending and receiving its tile columns, drains
+// its weight copies (bounded), and meets the cluster's one final barrier, so
+// no rank waits forever and none exits while a copy into it is in flight.
 // The prologue standardizes the inputs (from FP32 theta, or from a sampler's
 // FP64 z and centre; every rank builds the whole input tile) and forms the
 // quadratic baseline: rank c the terms (H u)_k of the gradient outputs it
 // writes and its share of u^T H u, which rank 0 adds up in rank order.
-constexpr int kFusedThreads = 256;
 constexpr uint32_t kFAtomA = kGemmM * 128u;       // one 64-column K-atom of the activation tile
 constexpr uint32_t kFSmemA = 4u * kFAtomA;        // 64 KB
 constexpr int kFBiasFloats = 4 * kMlpHidden + kMlpOutPad;
 
 template <int kCl>
 struct FusedCfg {
+    // 16 warps with 4-CTA clusters (a rank's 64 columns: 16 per warp); 8 otherwise
+    static constexpr int kThreads = kCl == 4 ? 512 : 256;
+    static constexpr int kGroups = kThreads / 128;                       // warp groups of 4
+    static constexpr int kGc = (256 / kCl) / kGroups;                     // columns per group, 256-wide stage
     static constexpr int kABufs = kCl > 1 ? 2 : 1;
+    static constexpr int kBBufs = kCl == 4 ? 2 : 1;                      // weights a stage ahead
     static constexpr uint32_t kSmemB = 4u * (256u / kCl) * 128u;          // 4 K-atoms x N/kCl rows
     static constexpr int kOutCols = kMlpOutPad / kCl;                     // stage 4 and 8 columns
     static constexpr int kGb = (kMlpIn < kOutCols + 1) ? kMlpIn : kOutCols + 1;   // (H u)_k kept
     static constexpr int kTailFloats = kGemmM * kGb + kGemmM * (kCl + 2) + kFBiasFloats + kMlpHidden;
-    static constexpr size_t kSmem = 1024 + kABufs * kFSmemA + kSmemB + sizeof(float) * kTailFloats + 64;
+    static constexpr size_t kSmem =
+        1024 + kABufs * kFSmemA + kBBufs * kSmemB + sizeof(float) * kTailFloats + 64;
+    // gelu'(z) of the four hidden layers: kept in TMEM after the accumulator
+    // (columns 64 + 64 l ..) when the rank's 64 columns per layer fit, else in
+    // global scratch
+    static constexpr bool kGInTmem = kCl == 4;
+    static constexpr uint32_t kTmemCols = kGInTmem ? 512u : 256u / kCl;
+    static constexpr uint32_t kRankBytes = (256u / kCl) * 128u * 2u;      // a rank's columns of a tile
 };
 
 struct FusedStage {
@@ -380,16 +402,34 @@ __device__ __forceinline__ uint32_t map_rank(uint32_t addr, uint32_t rank) {
     return r;
 }
 
+// copy `bytes` of this CTA's shared memory to the same offset in cluster CTA
+// `rank`, completing on that CTA's mbarrier (at the same offset as bar)
+__device__ __forceinline__ void bulk_copy_to_rank(uint32_t src, uint32_t bytes, uint32_t bar,
+                                                  uint32_t rank) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            map_rank(src, rank)),
+        "r"(src), "r"(bytes), "r"(map_rank(bar, rank))
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16};\n\t"
+        "tcgen05.wait::st.sync.aligned;" ::"r"(taddr),
+        "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7]),
+        "f"(v[8]), "f"(v[9]), "f"(v[10]), "f"(v[11]), "f"(v[12]), "f"(v[13]), "f"(v[14]), "f"(v[15])
+        : "memory");
+}
+
 __device__ __forceinline__ void cluster_barrier() {
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
                      : "memory");
 }
 
 // 16 consecutive activations of row r, columns c0..c0+15 (c0 a multiple of 16),
-// as BF16 into the swizzled K-major tile at shared offset `tile` of every rank
-// of the cluster: 16-byte chunk j of a row's 128-byte K-atom row sits at chunk
-// position j ^ (r % 8).
-template <int kCl>
+// as BF16 into the swizzled K-major tile at shared address `tile`: 16-byte
+// chunk j of a row's 128-byte K-atom row sits at chunk position j ^ (r % 8).
 __device__ __forceinline__ void store_act16(uint32_t tile, int r, int c0, const float* d) {
     uint32_t p[8];
 #pragma unroll
@@ -399,33 +439,16 @@ __device__ __forceinline__ void store_act16(uint32_t tile, int r, int c0, const 
     }
     const uint32_t off = tile + uint32_t(c0 >> 6) * kFAtomA + uint32_t(r) * 128u;
     const uint32_t j0 = uint32_t((c0 & 63) >> 3), sw = uint32_t(r & 7);
-    const uint32_t o0 = off + ((j0 ^ sw) << 4), o1 = off + (((j0 + 1u) ^ sw) << 4);
-    if (kCl == 1) {
-        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(o0), "r"(p[0]), "r"(p[1]),
-                     "r"(p[2]), "r"(p[3])
-                     : "memory");
-        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(o1), "r"(p[4]), "r"(p[5]),
-                     "r"(p[6]), "r"(p[7])
-                     : "memory");
-        return;
-    }
-#pragma unroll
-    for (int k = 0; k < kCl; ++k) {
-        asm volatile("st.shared::cluster.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(map_rank(o0, uint32_t(k))),
-                     "r"(p[0]), "r"(p[1]), "r"(p[2]), "r"(p[3])
-                     : "memory");
-        asm volatile("st.shared::cluster.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(map_rank(o1, uint32_t(k))),
-                     "r"(p[4]), "r"(p[5]), "r"(p[6]), "r"(p[7])
-                     : "memory");
-    }
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(off + ((j0 ^ sw) << 4)), "r"(p[0]),
+                 "r"(p[1]), "r"(p[2]), "r"(p[3])
+                 : "memory");
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(off + (((j0 + 1u) ^ sw) << 4)),
+                 "r"(p[4]), "r"(p[5]), "r"(p[6]), "r"(p[7])
+                 : "memory");
 }
 
 __device__ __forceinline__ void fence_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-__device__ __forceinline__ void fence_async_cluster() {
-    asm volatile("fence.proxy.async.shared::cluster;" ::: "memory");
 }
 
 // input k of row gr: theta, or float(z - centre) in the FP64-input mode
@@ -456,12 +479,12 @@ __device__ __forceinline__ void trace_row(float* t, int cnt, const float* v) {
         t[j] = kRound ? __bfloat162float(__float2bfloat16_rn(v[j])) : v[j];
 }
 
-// 32 saved gelu'(z) of one row (8 float4), issued early so that their latency
+// 16 saved gelu'(z) of one row (4 float4), issued early so that their latency
 // overlaps other work
-__device__ __forceinline__ void load_g32(const float* g, float4 (&o)[8]) {
+__device__ __forceinline__ void load_g16(const float* g, float4 (&o)[4]) {
     const float4* g4 = reinterpret_cast<const float4*>(g);
 #pragma unroll
-    for (int i = 0; i < 8; ++i) o[i] = g4[i];
+    for (int i = 0; i < 4; ++i) o[i] = g4[i];
 }
 
 // `cnt` (16, 32 or 48) consecutive accumulator columns of this warp's lanes
@@ -487,28 +510,32 @@ __device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, float (&v)[48]) {
 }
 
 template <int kCl>
-__global__ void __launch_bounds__(kFusedThreads, 1)
+__global__ void __launch_bounds__(FusedCfg<kCl>::kThreads, 1)
     k_mlp_fused(const __grid_constant__ MlpFusedMaps maps, const __grid_constant__ MlpFusedArgs a) {
     using Cfg = FusedCfg<kCl>;
     constexpr int kOut = Cfg::kOutCols;                       // this rank's stage-4/8 columns
     constexpr int kOutLd = kOut > 32 ? 48 : kOut;             // of them read back (<= 48 used)
+    constexpr int kBB = Cfg::kBBufs;
     extern __shared__ __align__(16) uint8_t smem_raw[];
     __shared__ uint32_t s_tmem;
     __shared__ int s_ok;
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
-    const uint32_t sB = base + Cfg::kABufs * kFSmemA;
-    float* tail = reinterpret_cast<float*>(smem_raw + (base - raw) + Cfg::kABufs * kFSmemA + Cfg::kSmemB);
+    const uint32_t sB0 = base + Cfg::kABufs * kFSmemA;
+    float* tail = reinterpret_cast<float*>(smem_raw + (base - raw) + Cfg::kABufs * kFSmemA +
+                                           kBB * Cfg::kSmemB);
     float* gbase_s = tail;                            // [128][kGb]: -(H u)_k, k from k_lo
     float* qpart_s = gbase_s + kGemmM * Cfg::kGb;     // [kCl][128]: each rank's share of u^T H u
     float* y0_s = qpart_s + kGemmM * kCl;             // [128]
     float* spare_s = y0_s + kGemmM;                   // [128]
     float* bias_s = spare_s + kGemmM;                 // b_0..b_3 [256] each, then b_4 [64]
     float* w4_s = bias_s + kFBiasFloats;              // W_4[0] [256]
-    const uint32_t bar_load = smem_u32(w4_s + kMlpHidden);
-    const uint32_t bar_mma = bar_load + 8u;
+    // mbarriers: weights (one per B buffer), MMA, and the peers' columns of each A tile
+    const uint32_t bar_load0 = smem_u32(w4_s + kMlpHidden);
+    const uint32_t bar_mma = bar_load0 + 16u;
+    const uint32_t bar_a0 = bar_mma + 8u;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int q = warp & 3, hh = warp >> 2;
+    const int q = warp & 3, grp = warp >> 2;                // TMEM lane quarter, column group
     const int r = 32 * q + lane;                            // this thread's row in the slab
     const uint32_t rank = kCl > 1 ? cluster_rank() : 0u;
     const int64_t row0 = int64_t(blockIdx.x / kCl) * kGemmM, gr = row0 + r;
@@ -517,77 +544,153 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
     // gradient outputs of this rank: grad-head columns j = k + 1 and back-propagated
     // columns k, both within [rank kOut, (rank + 1) kOut)
     const int k_lo = max(0, int(rank) * kOut - 1), k_hi = min(kMlpIn, int(rank) * kOut + kOut);
+    // this rank's columns of a 256-wide tile start at byte own_off of each A tile
+    const uint32_t own_off = rank * Cfg::kRankBytes;
 
-    auto issue_load = [&](int st, uint32_t bar) {
+    auto sB = [&](int st) { return sB0 + uint32_t(kBB > 1 ? (st & 1) : 0) * Cfg::kSmemB; };
+    auto bar_load = [&](int st) { return bar_load0 + uint32_t(kBB > 1 ? (st & 1) : 0) * 8u; };
+    auto issue_load = [&](int st) {
         const FusedStage fs = c_fstage[st];
         const int atoms = fs.K / 64;
         const int nc = fs.N / kCl;
+        const uint32_t bar = bar_load(st);
         mbar_expect_tx(bar, uint32_t(atoms) * uint32_t(nc) * 128u);
         for (int at = 0; at < atoms; ++at)
-            tma_load_2d(sB + uint32_t(at) * uint32_t(nc) * 128u, fused_map(maps, fs.map), at * 64,
+            tma_load_2d(sB(st) + uint32_t(at) * uint32_t(nc) * 128u, fused_map(maps, fs.map), at * 64,
                         int(rank) * nc, bar);
     };
+    // thread 0's record of what is in flight, drained (bounded) before exit
+    int loads_out = 0, loads_done = 0;
 
     if (tid == 0) {
-        mbar_init(bar_load, 1);
+        mbar_init(bar_load0, 1);
+        mbar_init(bar_load0 + 8u, 1);
         mbar_init(bar_mma, 1);
+        mbar_init(bar_a0, 1);
+        mbar_init(bar_a0 + 8u, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_ok = 1;
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(&s_tmem)),
-                     "r"(uint32_t(256 / kCl))
+                     "r"(Cfg::kTmemCols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     tc_fence_before();
     __syncthreads();
-    if (kCl > 1) cluster_barrier();       // every rank has started before any remote store
+    if (kCl > 1) cluster_barrier();       // every rank has started and initialised its barriers
     tc_fence_after();
     const uint32_t tmem = s_tmem;
-    if (tid == 0) issue_load(0, bar_load);
-
-    if (hh == 0) {
-        // biases and the value output's weight row, then the standardized input
-        // row: (theta - mean) / std for k < 47, zero padding (every rank, locally)
-        for (int i = tid; i < kFBiasFloats; i += 128) {
-            const int l = i < 4 * kMlpHidden ? i / kMlpHidden : 4;
-            bias_s[i] = a.bias[l][i - l * kMlpHidden];
+    if (tid == 0) {
+        issue_load(0);
+        ++loads_out;
+        if (kBB > 1 && nst > 1) {
+            issue_load(1);
+            ++loads_out;
         }
-        for (int i = tid; i < kMlpHidden; i += 128) w4_s[i] = __bfloat162float(a.w4[i]);
+    }
+
+    // The prologue stages the slab's input rows and H in a part of the activation
+    // tiles that stage 0 does not read (atoms 1..3 of the single tile, or the
+    // second tile), with row strides of 49 floats so that column reads across a
+    // warp hit distinct banks.
+    constexpr int kLd = kMlpIn + 2;
+    float* u_s = reinterpret_cast<float*>(smem_raw + (base - raw) +
+                                          (Cfg::kABufs > 1 ? kFSmemA : kFAtomA));   // [128][49]
+    float* h_s = u_s + kGemmM * kLd;                                                  // [47][49]
+    constexpr int kNt = Cfg::kThreads;
+    {
+        // every load of the prologue is issued before any store, so that their
+        // latencies overlap (coalesced: the slab's rows are contiguous in memory)
+        constexpr int kNu = (kGemmM * kMlpIn + kNt - 1) / kNt;
+        constexpr int kNh = (kMlpIn * kMlpIn + kNt - 1) / kNt;
+        constexpr int kNb = (kFBiasFloats + kNt - 1) / kNt;
+        float uv[kNu], hv[kNh], bv[kNb];
+        float wv = 0.0f;
+#pragma unroll
+        for (int i = 0; i < kNu; ++i) {
+            const int e = tid + i * kNt, rr = e / kMlpIn;
+            uv[i] = (e < kGemmM * kMlpIn && row0 + rr < a.n) ? fused_in(a, row0 + rr, e - rr * kMlpIn) : 0.0f;
+        }
+#pragma unroll
+        for (int i = 0; i < kNh; ++i) {
+            const int e = tid + i * kNt;
+            hv[i] = (a.Hq && e < kMlpIn * kMlpIn) ? a.Hq[e] : 0.0f;
+        }
+#pragma unroll
+        for (int i = 0; i < kNb; ++i) {
+            const int e = tid + i * kNt;
+            const int l = e < 4 * kMlpHidden ? e / kMlpHidden : 4;
+            bv[i] = e < kFBiasFloats ? a.bias[l][e - l * kMlpHidden] : 0.0f;
+        }
+        if (tid < kMlpHidden) wv = __bfloat162float(a.w4[tid]);
+#pragma unroll
+        for (int i = 0; i < kNu; ++i) {
+            const int e = tid + i * kNt, rr = e / kMlpIn;
+            if (e < kGemmM * kMlpIn) u_s[rr * kLd + (e - rr * kMlpIn)] = uv[i];
+        }
+#pragma unroll
+        for (int i = 0; i < kNh; ++i) {
+            const int e = tid + i * kNt;
+            if (e < kMlpIn * kMlpIn) h_s[(e / kMlpIn) * kLd + e % kMlpIn] = hv[i];
+        }
+#pragma unroll
+        for (int i = 0; i < kNb; ++i) {
+            const int e = tid + i * kNt;
+            if (e < kFBiasFloats) bias_s[e] = bv[i];
+        }
+        if (tid < kMlpHidden) w4_s[tid] = wv;
+    }
+    __syncthreads();
+    if (grp == 0) {
+        // the standardized input row: (theta - mean) / std for k < 47, zero
+        // padding (every rank builds the whole tile, locally)
         float d[16];
 #pragma unroll
         for (int c0 = 0; c0 < kMlpInPad; c0 += 16) {
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
                 const int k = c0 + j;
-                d[j] = (valid && k < kMlpIn) ? (fused_in(a, gr, k) - a.xm[k]) / a.xs[k] : 0.0f;
+                d[j] = (valid && k < kMlpIn) ? (u_s[r * kLd + k] - a.xm[k]) / a.xs[k] : 0.0f;
             }
-            store_act16<1>(base, r, c0, d);
+            store_act16(base, r, c0, d);
             if (a.tr_act && valid && rank == 0) trace_row<true>(a.tr_act + gr * kMlpHidden + c0, 16, d);
         }
-    } else if (a.Hq && valid) {
-        // quadratic baseline: gbase = -(H u)_k for this rank's gradient outputs
-        // (each sum in the order j = 0..46), and the rank's share of u^T H u
-        float u[kMlpIn];
+    }
+    if (a.Hq) {
+        // quadratic baseline: gbase = -(H u)_k for this rank's gradient outputs,
+        // one (row, k) dot product per thread in turn, each sum in the order j = 0..46
+        // (warp group 0 builds the input tile meanwhile)
+        // Four k per task share each u_j load (four independent sums).
+        const int nk = k_hi - k_lo, ng = (nk + 3) / 4;
+        for (int e = tid - 128; grp > 0 && e < kGemmM * ng; e += kNt - 128) {
+            const int rr = e / ng, k0 = k_lo + 4 * (e - rr * ng);
+            const float* uu = u_s + rr * kLd;
+            float hu[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
-        for (int j = 0; j < kMlpIn; ++j) u[j] = fused_in(a, gr, j);
-        float qd = 0.0f;
-#pragma unroll 1
-        for (int k = k_lo; k < k_hi; ++k) {
-            const float* Hk = a.Hq + k * kMlpIn;
-            float hu = 0.0f;
+            for (int j = 0; j < kMlpIn; ++j) {
+                const float uj = uu[j];
 #pragma unroll
-            for (int j = 0; j < kMlpIn; ++j) hu = fmaf(Hk[j], u[j], hu);
-            gbase_s[r * Cfg::kGb + (k - k_lo)] = -hu;
-            if (k >= int(rank) * kOut) qd = fmaf(fused_in(a, gr, k), hu, qd);
+                for (int t = 0; t < 4; ++t) hu[t] = fmaf(h_s[min(k0 + t, kMlpIn - 1) * kLd + j], uj, hu[t]);
+            }
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+                if (k0 + t < k_hi) gbase_s[rr * Cfg::kGb + (k0 + t - k_lo)] = -hu[t];
         }
-        const uint32_t qa = smem_u32(qpart_s + rank * kGemmM + r);
-        if (kCl > 1) {
-            asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(map_rank(qa, 0u)), "f"(qd) : "memory");
-        } else {
-            qpart_s[r] = qd;
+        __syncthreads();
+        if (tid < kGemmM && valid) {
+            // the rank's share of u^T H u, in the order k = rank kOut ..
+            float qd = 0.0f;
+            for (int k = max(k_lo, int(rank) * kOut); k < k_hi; ++k)
+                qd = fmaf(u_s[r * kLd + k], -gbase_s[r * Cfg::kGb + (k - k_lo)], qd);
+            const uint32_t qa = smem_u32(qpart_s + rank * kGemmM + r);
+            if (kCl > 1) {
+                asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(map_rank(qa, 0u)), "f"(qd) : "memory");
+            } else {
+                qpart_s[r] = qd;
+            }
         }
     }
     fence_async_smem();
@@ -597,27 +700,44 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
     tc_fence_after();
 
     const uint32_t tlane = tmem + (uint32_t(32 * q) << 16);
+    const bool need_g = a.mode == kFusedValueGrad;          // gelu'(z) for the back-propagation
+    constexpr int kGc = Cfg::kGc;
     for (int st = 0; st < nst; ++st) {
         const FusedStage fs = c_fstage[st];
         const int nc = fs.N / kCl;                       // this rank's columns of the stage
         const int cg0 = int(rank) * nc;                  // the first of them
-        constexpr int half = 128 / kCl;                  // 256-wide stages: columns per warp half
-        const int cbeg = hh * half;
+        const int cbeg = grp * kGc;                      // this warp group's first local column
         const uint32_t curA = base + uint32_t(Cfg::kABufs > 1 ? (st & 1) : 0) * kFSmemA;
         const uint32_t nxtA = base + uint32_t(Cfg::kABufs > 1 ? ((st + 1) & 1) : 0) * kFSmemA;
-        // the first 32 saved gelu'(z) this stage's epilogue needs, requested
-        // before the MMA completes
-        const float* gsrc = nullptr;
-        if (st == 4 && a.mode == kFusedValueGrad) gsrc = a.gscr[3] + gr * kMlpHidden;
-        else if (st >= 5 && st < 8) gsrc = a.gscr[7 - st] + gr * kMlpHidden;
-        float4 gbuf[2][8];
+        const uint32_t nxtBar = bar_a0 + uint32_t((st + 1) & 1) * 8u;   // the peers' barrier of that tile
         // the seed (stage 4) and the backward stages cover this rank's 256 / kCl columns
         const int hbeg = int(rank) * (kMlpHidden / kCl) + cbeg;
-        if (gsrc && s_ok) load_g32(gsrc + hbeg, gbuf[0]);
+        // the hidden layer whose gelu'(z) this stage needs; from global scratch the
+        // first 16 are requested before the MMA completes
+        int glayer = -1;
+        if (st == 4 && need_g) glayer = 3;
+        else if (st >= 5 && st < 8) glayer = 7 - st;
+        const float* gsrc = (glayer >= 0 && !Cfg::kGInTmem) ? a.gscr[glayer] + gr * kMlpHidden : nullptr;
+        float4 gnext[4];
+        if (gsrc && s_ok) load_g16(gsrc + hbeg, gnext);
         if (tid == 0) {
-            const uint32_t ph = uint32_t(st & 1);
             bool ok = s_ok != 0;
-            if (ok) ok = mbar_wait(bar_load, ph, a.err, 3);
+            if (kBB > 1 && st >= 1 && st + 1 < nst && ok) {
+                issue_load(st + 1);              // into the buffer MMA(st - 1) has finished with
+                ++loads_out;
+            }
+            if (kCl > 1 && st >= 1) {
+                // the peers' columns of this stage's tile (sent after their epilogues)
+                const uint32_t bar = bar_a0 + uint32_t(st & 1) * 8u;
+                const uint32_t par = uint32_t(((st - 1) >> 1) & 1);
+                mbar_expect_tx(bar, uint32_t(kCl - 1) * Cfg::kRankBytes);
+                if (!mbar_wait(bar, par, ok ? a.err : nullptr, 5)) ok = false;
+            }
+            const uint32_t ph = uint32_t(kBB > 1 ? ((st >> 1) & 1) : (st & 1));
+            if (ok) {
+                ok = mbar_wait(bar_load(st), ph, a.err, 3);
+                if (ok) ++loads_done;
+            }
             if (ok) {
                 tc_fence_after();
                 const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t(nc) >> 3) << 17) |
@@ -625,15 +745,16 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
                 for (int k = 0; k < fs.K / 16; ++k) {
                     const uint32_t at = uint32_t(k >> 2), kk = uint32_t(k & 3);
                     const uint64_t da = smem_desc(curA + at * kFAtomA + kk * 32u);
-                    const uint64_t db = smem_desc(sB + at * uint32_t(nc) * 128u + kk * 32u);
+                    const uint64_t db = smem_desc(sB(st) + at * uint32_t(nc) * 128u + kk * 32u);
                     tc_mma(tmem, da, db, idesc, k > 0 ? 1u : 0u);
                 }
                 tc_commit(bar_mma);
-                ok = mbar_wait(bar_mma, ph, a.err, 4);
-                if (!ok) mbar_wait(bar_mma, ph, nullptr, 0);   // let MMAs in flight finish (bounded)
-                else if (st + 1 < nst) issue_load(st + 1, bar_load);
-            } else if (s_ok) {
-                mbar_wait(bar_load, ph, nullptr, 0);           // let copies in flight land (bounded)
+                ok = mbar_wait(bar_mma, uint32_t(st & 1), a.err, 4);
+                if (!ok) mbar_wait(bar_mma, uint32_t(st & 1), nullptr, 0);   // MMAs in flight (bounded)
+                else if (kBB == 1 && st + 1 < nst) {
+                    issue_load(st + 1);
+                    ++loads_out;
+                }
             }
             s_ok = ok ? 1 : 0;
         }
@@ -641,35 +762,42 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
         tc_fence_after();
         if (s_ok) {
             if (st < 4) {
-                // hidden layer: z = acc + b; h = gelu(z) into every rank's next tile;
-                // gelu'(z) to scratch
+                // hidden layer: z = acc + b; h = gelu(z) into this rank's columns of
+                // the next tile; gelu'(z) (back-propagation only) to TMEM or scratch
                 const float* bias = bias_s + st * kMlpHidden;
                 float* gs = a.gscr[st] + gr * kMlpHidden;
 #pragma unroll 1
-                for (int c0 = cbeg; c0 < cbeg + half; c0 += 32) {
+                for (int c0 = cbeg; c0 < cbeg + kGc; c0 += 16) {
                     const int cg = int(rank) * (kMlpHidden / kCl) + c0;
-                    float v[32], g[32];
-                    tmem_ld32(tlane + uint32_t(c0), v);
+                    float v[16], g[16];
+                    tmem_ld16(tlane + uint32_t(c0), v);
                     if (a.tr_acc && valid)
-                        trace_row<false>(a.tr_acc + st * a.tr_stride + gr * kMlpHidden + cg, 32, v);
+                        trace_row<false>(a.tr_acc + st * a.tr_stride + gr * kMlpHidden + cg, 16, v);
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
+                    for (int j = 0; j < 16; ++j) {
                         const float z = v[j] + bias[cg + j];
-                        v[j] = gelu_f(z);
-                        g[j] = gelu_grad_f(z);
+                        const float e = erf_gelu(z);
+                        v[j] = gelu_e(z, e);
+                        if (need_g) g[j] = gelu_grad_e(z, e);
                     }
-                    float4* g4 = reinterpret_cast<float4*>(gs + cg);
+                    if (need_g) {
+                        if (Cfg::kGInTmem) {
+                            tmem_st16(tlane + uint32_t(64 + 64 * st + c0), g);
+                        } else {
+                            float4* g4 = reinterpret_cast<float4*>(gs + cg);
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) g4[i] = make_float4(g[4 * i], g[4 * i + 1], g[4 * i + 2], g[4 * i + 3]);
-                    store_act16<kCl>(nxtA, r, cg, v);
-                    store_act16<kCl>(nxtA, r, cg + 16, v + 16);
+                            for (int i = 0; i < 4; ++i)
+                                g4[i] = make_float4(g[4 * i], g[4 * i + 1], g[4 * i + 2], g[4 * i + 3]);
+                        }
+                    }
+                    store_act16(nxtA, r, cg, v);
                     if (a.tr_act && valid)
-                        trace_row<true>(a.tr_act + (st + 1) * a.tr_stride + gr * kMlpHidden + cg, 32, v);
+                        trace_row<true>(a.tr_act + (st + 1) * a.tr_stride + gr * kMlpHidden + cg, 16, v);
                 }
             } else if (st == 4) {
                 // output layer: y = acc + b_4 for this rank's columns j = cg0 ..
                 const float* b4 = bias_s + 4 * kMlpHidden;
-                if (hh == 0 && (a.mode == kFusedGradHead || rank == 0 || a.tr_acc)) {
+                if (grp == 0 && (a.mode == kFusedGradHead || rank == 0 || a.tr_acc)) {
                     float v[48];
                     tmem_ld_cols<kOutLd>(tlane, v);
                     if (a.tr_acc && valid) {
@@ -701,42 +829,54 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
                         }
                     }
                 }
-                if (a.mode == kFusedValueGrad) {
+                if (need_g) {
                     // seed: dz_4 = (one-hot of the value output) W_4 * gelu'(z_4), for
                     // this rank's columns of the 256-wide tile
+#pragma unroll 1
+                    for (int c = 0; c < kGc; c += 16) {
+                        const int c0 = hbeg + c;
+                        float gg[16];
+                        if (Cfg::kGInTmem) {
+                            tmem_ld16(tlane + uint32_t(64 + 64 * 3 + cbeg + c), gg);
+                        } else {
+                            const float* gn = reinterpret_cast<const float*>(gnext);
 #pragma unroll
-                    for (int it = 0; it < half / 32; ++it) {
-                        const int c0 = hbeg + 32 * it;
-                        if (32 * (it + 1) < half) load_g32(gsrc + c0 + 32, gbuf[(it + 1) & 1]);
-                        const float* gg = reinterpret_cast<const float*>(gbuf[it & 1]);
-                        float d[32];
+                            for (int j = 0; j < 16; ++j) gg[j] = gn[j];
+                            if (c + 16 < kGc) load_g16(gsrc + c0 + 16, gnext);
+                        }
+                        float d[16];
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) d[j] = (valid ? w4_s[c0 + j] : 0.0f) * gg[j];
-                        store_act16<kCl>(nxtA, r, c0, d);
-                        store_act16<kCl>(nxtA, r, c0 + 16, d + 16);
+                        for (int j = 0; j < 16; ++j) d[j] = (valid ? w4_s[c0 + j] : 0.0f) * gg[j];
+                        store_act16(nxtA, r, c0, d);
                         if (a.tr_act && valid)
-                            trace_row<true>(a.tr_act + 5 * a.tr_stride + gr * kMlpHidden + c0, 32, d);
+                            trace_row<true>(a.tr_act + 5 * a.tr_stride + gr * kMlpHidden + c0, 16, d);
                     }
                 }
             } else if (st < 8) {
                 // back through layer 8 - st: dz = acc * gelu'(z)
+#pragma unroll 1
+                for (int c = 0; c < kGc; c += 16) {
+                    const int c0 = cbeg + c, cg = hbeg + c;
+                    float gg[16];
+                    if (Cfg::kGInTmem) {
+                        tmem_ld16(tlane + uint32_t(64 + 64 * glayer + c0), gg);
+                    } else {
+                        const float* gn = reinterpret_cast<const float*>(gnext);
 #pragma unroll
-                for (int it = 0; it < half / 32; ++it) {
-                    const int c0 = cbeg + 32 * it, cg = hbeg + 32 * it;
-                    if (32 * (it + 1) < half) load_g32(gsrc + cg + 32, gbuf[(it + 1) & 1]);
-                    float v[32];
-                    tmem_ld32(tlane + uint32_t(c0), v);
+                        for (int j = 0; j < 16; ++j) gg[j] = gn[j];
+                        if (c + 16 < kGc) load_g16(gsrc + cg + 16, gnext);
+                    }
+                    float v[16];
+                    tmem_ld16(tlane + uint32_t(c0), v);
                     if (a.tr_acc && valid)
-                        trace_row<false>(a.tr_acc + st * a.tr_stride + gr * kMlpHidden + cg, 32, v);
-                    const float* gg = reinterpret_cast<const float*>(gbuf[it & 1]);
+                        trace_row<false>(a.tr_acc + st * a.tr_stride + gr * kMlpHidden + cg, 16, v);
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) v[j] = v[j] * gg[j];
-                    store_act16<kCl>(nxtA, r, cg, v);
-                    store_act16<kCl>(nxtA, r, cg + 16, v + 16);
+                    for (int j = 0; j < 16; ++j) v[j] = v[j] * gg[j];
+                    store_act16(nxtA, r, cg, v);
                     if (a.tr_act && valid)
-                        trace_row<true>(a.tr_act + (st + 1) * a.tr_stride + gr * kMlpHidden + cg, 32, v);
+                        trace_row<true>(a.tr_act + (st + 1) * a.tr_stride + gr * kMlpHidden + cg, 16, v);
                 }
-            } else if (hh == 0) {
+            } else if (grp == 0) {
                 // dx = dz_1 W_0: the gradient of the value output in the standardized
                 // inputs, this rank's columns k = cg0 ..
                 float v[48];
@@ -757,18 +897,34 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
                 }
             }
         }
-        if (kCl > 1) fence_async_cluster();
-        else fence_async_smem();
+        fence_async_smem();                  // this CTA's tile writes, before the async proxy reads them
         tc_fence_before();
         __syncthreads();
-        if (kCl > 1) cluster_barrier();   // every rank's columns of the next tile are in place
         tc_fence_after();
+        // send this rank's columns of the next tile to every other rank (even after a
+        // failure, so that no rank waits for them in vain)
+        if (kCl > 1 && st + 1 < nst) {
+            if (tid == 0) {
+#pragma unroll
+                for (int d = 1; d < kCl; ++d)
+                    bulk_copy_to_rank(nxtA + own_off, Cfg::kRankBytes, nxtBar, (rank + uint32_t(d)) % kCl);
+            }
+        }
+    }
+    // drain (bounded) what thread 0 left in flight after a failure: weight
+    // copies it issued but did not wait for, and the peers' tile copies
+    if (tid == 0) {
+        for (int i = loads_done; i < loads_out; ++i) {
+            const int st = i;             // loads are issued and waited in stage order
+            mbar_wait(bar_load(st), uint32_t(kBB > 1 ? ((st >> 1) & 1) : (st & 1)), nullptr, 0);
+        }
     }
     tc_fence_before();
     __syncthreads();
+    if (kCl > 1) cluster_barrier();       // no rank exits while a copy into it may be in flight
     if (warp == 0) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                     "r"(uint32_t(256 / kCl))
+                     "r"(Cfg::kTmemCols)
                      : "memory");
     }
 }
@@ -790,7 +946,7 @@ template <int kCl>
 cudaLaunchConfig_t fused_config(unsigned grid, cudaStream_t s, cudaLaunchAttribute* attr) {
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(kFusedThreads);
+    cfg.blockDim = dim3(FusedCfg<kCl>::kThreads);
     cfg.dynamicSmemBytes = FusedCfg<kCl>::kSmem;
     cfg.stream = s;
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -829,7 +985,7 @@ cudaError_t launch_fused_cl(const MlpFusedMaps& maps, const MlpFusedArgs& a, cud
     if (ce != cudaSuccess) return ce;
     const unsigned grid = unsigned((a.n + kGemmM - 1) / kGemmM) * kCl;
     if (kCl == 1) {
-        k_mlp_fused<1><<<grid, kFusedThreads, FusedCfg<1>::kSmem, s>>>(maps, a);
+        k_mlp_fused<1><<<grid, FusedCfg<1>::kThreads, FusedCfg<1>::kSmem, s>>>(maps, a);
         return cudaGetLastError();
     }
     cudaLaunchAttribute attr[1];
