@@ -32,6 +32,17 @@
 // observation picks rho_q, whose scale is 1, so c, S, e and the update keep
 // their form with Ph, mh.  A scale below 2^-200 (a fast decay over a long
 // gap) folds S back into Ph and takes that one predict unscaled.
+//
+// Gradient (two kernels).  The likelihood kernel, with one warp per vector,
+// also saves the state every L = ceil(sqrt N) TOAs ("checkpoints") and flags
+// a vector whose scales had to be folded.  The reverse kernel then takes one
+// vector per block of 64 threads (more for large arrays): segment by segment,
+// last first, it re-runs the segment from its checkpoint and writes each
+// step's "tape entry" to global memory -- the state before the step and the
+// step's transition coefficients with their gamma-derivatives -- and then
+// runs the adjoint steps backwards, each reading its entry into one of two
+// shared-memory buffers by cp.async while the step before it computes.  A
+// flagged vector runs the whole gradient unscaled instead.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -54,10 +65,11 @@ namespace {
 
 constexpr double kLog2PiGwb = 1.8378770664093454836;
 constexpr double kLn10Gwb = 2.302585092994045684;
-constexpr int kGwbThreads = 256;      // gradient kernel
 constexpr int kGwbFwdThreads = 32;    // likelihood kernel: one warp per block
-constexpr int kGwbGradMaxPulsars = 48;   // gradient: two packed 3P x 3P triangles in shared memory
+constexpr int kGwbRevMaxThreads = 256;   // reverse kernel: 64, 128 or 256 threads per block
+constexpr int kGwbGradMaxPulsars = 48;   // gradient: the adjoint and a tape entry in shared memory
 constexpr int kCo = 9;                   // per-pulsar coefficients (see GwbSmem::co)
+constexpr int kDotChunks = 4;            // lanes per dot product in the adjoint's parameter sums
 
 struct GwbRec {     // one TOA of the merged, time-ordered stream (32 bytes)
     double dt;      // time since the previous TOA of any pulsar (0 for the first)
@@ -77,98 +89,153 @@ struct GwbArgs {
     const double* theta;    // [B][2 + 3P]
     int64_t B;
     double* loglik;         // [B]
-    double* grad;           // [B][2 + 3P] (gradient kernel)
-    double* ckpt;           // per block: [nseg][ne + n] state at each segment start
-    double* tape;           // per block: [L][ne + n] state before each step of a segment
-    int64_t slot;           // doubles per block in ckpt and in tape
+    double* grad;           // [B][2 + 3P] (reverse kernel)
+    double* ckpt;           // per vector: [nseg][rec_len] state at each segment start, or NULL
+    int32_t* flags;         // per vector: 1 if the likelihood pass folded its scales (with ckpt)
+    double* tape;           // per reverse block: [L][tape_len] tape entries of one segment
+    int64_t ck_slot;        // doubles per vector in ckpt
+    int64_t tape_slot;      // doubles per block in tape
     int32_t L;              // segment length (TOAs)
     int32_t nseg;
+    int32_t nbuf;           // tape-entry buffers in the reverse kernel's shared memory (1 or 2)
 };
 
 // Shared memory of a block.  The covariance P and, for the gradient, its
 // adjoint Pb are symmetric and stored as packed upper triangles (see pk).
+// The state and the step's coefficients sit in one contiguous "entry" in the
+// order of a tape entry: Pm, m, sg, co, gc, cs.
 struct GwbSmem {
     int P, n, nb, ne;
     double* Pm;     // packed upper triangle, n (n + 1) / 2
     double* m;      // [n]
-    double* c;      // [n]
+    double* sg;     // [P + 1]: scale factors s_p and s_a (scaled frame)
     double* co;     // [P][9]: a, b, Q/sigma^2 (c00, c01, c11), d/dgamma of b and of c00, c01, c11
+    double* gc;     // [9]: the same for the GW process (per unit h_a^2)
     double* cs;     // [P + 1][5], scaled frame, per pulsar and for the GW process (row P):
                     // b s, v c00, v c01 / s', v c11 / s'^2, 1 / s' (v = sigma_p^2 or h_a^2, s' = s a)
+    double* c;      // [n]
     double* ct;     // [n]: c / S
-    double* sg;     // [P + 1]: scale factors s_p and s_a (scaled frame)
     double* sg0;    // [P + 1]: the scale factors before the current predict
     const double* G;   // [P][P] Hellings-Downs, in global memory (read through the read-only cache)
     double* par;    // [P][4]: sigma^2, gamma_p, EFAC^2, EFAC
-    double* gw;     // GW process: a, b, c00, c01, c11, db, dc00, dc01, dc11 (per unit h_a^2); scalars
-    double* Pb;     // packed upper triangle (gradient)
-    double* mb;     // [n]      (gradient)
-    double* u;      // [n]      (gradient)
-    double* v;      // [n]      (gradient)
+    double* gw;     // scalar slots (enum below)
+    // reverse kernel only
+    double* E1;     // second tape-entry buffer (== Pm's entry when there is one buffer)
+    double* Pb;     // packed upper triangle: adjoint of Ph
+    double* mb;     // [n]: adjoint of mh
+    double* v;      // [n]
     double* acc;    // [P][5]: d/d sigma^2, d/d gamma_p, d/d EFAC, d/d h_a^2 part, d/d gamma_a part
-    double* part;   // [P][chunks][6]: partial sums of the parameter terms
-    double* sgb;    // [2P]: adjoints of s_p, and pulsar I's share of the adjoint of s_a (gradient)
+    double* sgb;    // [P]: adjoints of the scales s_p
+    double* sbt;    // [P]: this step's adjoint of s'_p from the intrinsic noise
+    double* n1;     // [P]: this step's intrinsic-noise term of d/d gamma_p (before the factor sigma_p^2)
+    double* dd;     // [2P]: this step's Fh-bar dot products, (rho_I, y_I) then (rho_I, a_I)
+    double* red;    // [2 x warps]: block reductions
+    double* u;      // [n]      (unscaled fallback)
+    double* part;   // [P][chunks][6]: partial sums of the parameter terms (unscaled fallback)
     uint16_t* pairs;
-    uint8_t* ent;
 };
 // scalar slots of gw[]
-enum { kGwA = 0, kGwHa2 = 9, kGwGa, kGwE, kGwS, kGwRS, kGwG, kGwOk, kGwSb, kGwEb, kGwR0, kGwRn, kGwRnAny,
-       kGwSlots = 24 };
+// (kGwK..kGwK+10: the GW share update's per-step products, reverse kernel)
+enum { kGwHa2 = 0, kGwGa, kGwE, kGwS, kGwRS, kGwG, kGwOk, kGwSb, kGwEb, kGwR0, kGwRn, kGwRnAny,
+       kGwK = 16, kGwSlots = 32 };
 constexpr double kGwbTiny = 0x1p-200;   // smallest scale factor kept (scaled frame)
 
-// chunks per pulsar of the adjoint's parameter sums (J ranges of about 5)
+// chunks per pulsar of the unscaled adjoint's parameter sums (J ranges of about 5)
 __host__ __device__ inline int gwb_jchunks(int P) { return (P + 4) / 5 < 8 ? (P + 4) / 5 : 8; }
-// doubles of one saved state: the upper triangle of P, m and the P + 1 scales
+// doubles of one saved state (a checkpoint): the upper triangle of P, m and the P + 1 scales
 __host__ __device__ inline int64_t gwb_rec_len(int P) {
     const int64_t n = 3 * int64_t(P);
     return n * (n + 1) / 2 + n + P + 1;
 }
-
-__host__ __device__ inline size_t gwb_smem_doubles(int P, bool grad) {
-    const size_t n = 3 * size_t(P), ne = n * (n + 1) / 2;
-    size_t d = ne + 3 * n + kCo * size_t(P) + 5 * (size_t(P) + 1) + 4 * size_t(P) + 2 * (size_t(P) + 1) +
-               kGwSlots;
-    if (grad) d += ne + 3 * n + 5 * size_t(P) + 6 * size_t(P) * gwb_jchunks(P) + 2 * size_t(P);
-    return d;
+// doubles of one tape entry: a saved state, then co, gc and cs; even, so
+// that entries start on 16-byte boundaries
+__host__ __device__ inline int64_t gwb_tape_len(int P) {
+    const int64_t d = gwb_rec_len(P) + kCo * int64_t(P) + 9 + 5 * (int64_t(P) + 1);
+    return (d + 1) & ~int64_t(1);
 }
 
-// dynamic shared memory of a block: the doubles, the (I, J) pairs of the
-// upper 3x3 blocks (uint16) and the (i, j) pairs of the upper entries (uint8)
-__host__ __device__ inline size_t gwb_smem_bytes(int P, bool grad) {
+// dynamic shared memory of the likelihood kernel: one entry, c, ct, sg0,
+// par, the scalar slots and the (I, J) pairs of the upper 3x3 blocks (uint16)
+__host__ __device__ inline size_t gwb_fwd_smem_bytes(int P) {
     const size_t n = 3 * size_t(P);
-    return gwb_smem_doubles(P, grad) * sizeof(double) + size_t(P) * (P + 1) * sizeof(uint16_t) +
-           n * (n + 1) * sizeof(uint8_t);
+    const size_t d = size_t(gwb_tape_len(P)) + 2 * n + (size_t(P) + 1) + 4 * size_t(P) + kGwSlots;
+    return d * sizeof(double) + size_t(P) * (P + 1) * sizeof(uint16_t);
 }
 
-__device__ GwbSmem gwb_carve(double* base, int P, bool grad, const double* G) {
-    GwbSmem s;
+// doubles of the reverse kernel's arrays after the entry buffers
+__host__ __device__ inline size_t gwb_rev_tail_doubles(int P, int threads) {
+    const size_t n = 3 * size_t(P), ne = n * (n + 1) / 2;
+    return ne + 4 * n + (size_t(P) + 1) + 4 * size_t(P) + kGwSlots + 5 * size_t(P) + 5 * size_t(P) +
+           2 * size_t(threads / 32);
+}
+// the unscaled fallback's u and part: in the second entry buffer when there is one
+__host__ __device__ inline size_t gwb_rev_fallback_doubles(int P) {
+    return 3 * size_t(P) + 6 * size_t(P) * gwb_jchunks(P);
+}
+__host__ __device__ inline size_t gwb_rev_smem_bytes(int P, int nbuf, int threads) {
+    size_t d = size_t(nbuf) * size_t(gwb_tape_len(P)) + gwb_rev_tail_doubles(P, threads);
+    if (nbuf == 1) d += gwb_rev_fallback_doubles(P);
+    return d * sizeof(double) + size_t(P) * (P + 1) * sizeof(uint16_t);
+}
+
+// pointers of an entry at e
+__device__ __forceinline__ void gwb_entry_ptrs(GwbSmem& s, double* e) {
+    const int P = s.P;
+    s.Pm = e;
+    s.m = e + s.ne;
+    s.sg = s.m + s.n;
+    s.co = s.sg + P + 1;
+    s.gc = s.co + kCo * P;
+    s.cs = s.gc + 9;
+}
+
+__device__ GwbSmem gwb_carve_fwd(double* base, int P, const double* G) {
+    GwbSmem s{};
     s.P = P; s.n = 3 * P; s.nb = P * (P + 1) / 2; s.ne = s.n * (s.n + 1) / 2;
-    const int n = s.n;
-    double* q = base;
-    s.Pm = q; q += s.ne;
-    s.m = q; q += n;
-    s.c = q; q += n;
-    s.co = q; q += kCo * P;
-    s.cs = q; q += 5 * (P + 1);
-    s.ct = q; q += n;
-    s.sg = q; q += P + 1;
+    gwb_entry_ptrs(s, base);
+    double* q = base + gwb_tape_len(P);
+    s.c = q; q += s.n;
+    s.ct = q; q += s.n;
     s.sg0 = q; q += P + 1;
-    s.G = G;
     s.par = q; q += 4 * P;
     s.gw = q; q += kGwSlots;
-    if (grad) {
-        s.Pb = q; q += s.ne;
-        s.mb = q; q += n;
-        s.u = q; q += n;
-        s.v = q; q += n;
-        s.acc = q; q += 5 * P;
-        s.part = q; q += 6 * P * gwb_jchunks(P);
-        s.sgb = q; q += 2 * P;
-    } else {
-        s.Pb = s.mb = s.u = s.v = s.acc = s.part = s.sgb = nullptr;
-    }
+    s.G = G;
+    s.E1 = base;
     s.pairs = reinterpret_cast<uint16_t*>(q);
-    s.ent = reinterpret_cast<uint8_t*>(s.pairs + 2 * s.nb);
+    return s;
+}
+
+__device__ GwbSmem gwb_carve_rev(double* base, int P, int nbuf, const double* G) {
+    GwbSmem s{};
+    s.P = P; s.n = 3 * P; s.nb = P * (P + 1) / 2; s.ne = s.n * (s.n + 1) / 2;
+    const int64_t tl = gwb_tape_len(P);
+    const int n = s.n;
+    gwb_entry_ptrs(s, base);
+    s.E1 = base + (nbuf == 2 ? tl : 0);
+    double* q = base + nbuf * tl;
+    s.Pb = q; q += s.ne;
+    s.mb = q; q += n;
+    s.c = q; q += n;
+    s.ct = q; q += n;
+    s.v = q; q += n;
+    s.sg0 = q; q += P + 1;
+    s.par = q; q += 4 * P;
+    s.gw = q; q += kGwSlots;
+    s.acc = q; q += 5 * P;
+    s.sgb = q; q += P;
+    s.sbt = q; q += P;
+    s.n1 = q; q += P;
+    s.dd = q; q += 2 * P;
+    s.red = q; q += 2 * (blockDim.x / 32);
+    if (nbuf == 2) {
+        s.u = s.E1;
+        s.part = s.E1 + n;
+    } else {
+        s.u = q; q += n;
+        s.part = q; q += 6 * P * gwb_jchunks(P);
+    }
+    s.G = G;
+    s.pairs = reinterpret_cast<uint16_t*>(q);
     return s;
 }
 
@@ -191,17 +258,14 @@ __device__ __forceinline__ double warp_sum(double x) {
     return x;
 }
 
-// tables and HD matrix, once per block
-__device__ void gwb_tables(const GwbSmem& s, const GwbArgs& a) {
+// the (I, J) pairs of the upper 3x3 blocks, once per block: the diagonal
+// blocks first, then I < J row by row
+__device__ void gwb_tables(const GwbSmem& s) {
     if (threadIdx.x == 0) {
-        // the diagonal blocks first, so that only the first warp(s) take their extra terms
         int k = 0;
         for (int I = 0; I < s.P; ++I) { s.pairs[2 * k] = uint16_t(I); s.pairs[2 * k + 1] = uint16_t(I); ++k; }
         for (int I = 0; I < s.P; ++I)
             for (int J = I + 1; J < s.P; ++J) { s.pairs[2 * k] = uint16_t(I); s.pairs[2 * k + 1] = uint16_t(J); ++k; }
-        k = 0;
-        for (int i = 0; i < s.n; ++i)
-            for (int j = i; j < s.n; ++j) { s.ent[2 * k] = uint8_t(i); s.ent[2 * k + 1] = uint8_t(j); ++k; }
     }
 }
 
@@ -230,13 +294,16 @@ __device__ bool gwb_setup(const GwbSmem& s, const GwbArgs& a, const double* th) 
     __syncthreads();
     if (s.gw[kGwOk] == 0.0) return false;
     const double ha2 = s.gw[kGwHa2], ga = s.gw[kGwGa];
-    for (int q = threadIdx.x; q < s.ne; q += blockDim.x) {
-        const int r = s.ent[2 * q], col = s.ent[2 * q + 1];
-        const int I = r / 3, J = col / 3, uu = r - 3 * I, vv = col - 3 * J;
-        double x = 0.0;
-        if (uu == 2 && vv == 2) x = ha2 * gwb_G(s, I, J) / (2.0 * ga);
-        else if (I == J && uu < 2 && vv < 2) x = a.p0[3 * I + uu + vv];
-        s.Pm[q] = x;
+    for (int r = threadIdx.x; r < n; r += blockDim.x) {   // one packed row per thread
+        const int I = r / 3, uu = r - 3 * I;
+        double* row = prow(s.Pm, n, r);
+        for (int col = r; col < n; ++col) {
+            const int J = col / 3, vv = col - 3 * J;
+            double x = 0.0;
+            if (uu == 2 && vv == 2) x = ha2 * gwb_G(s, I, J) / (2.0 * ga);
+            else if (I == J && uu < 2 && vv < 2) x = a.p0[3 * I + uu + vv];
+            row[col] = x;
+        }
     }
     for (int i = threadIdx.x; i < n; i += blockDim.x) s.m[i] = 0.0;
     __syncthreads();
@@ -251,7 +318,7 @@ __device__ void gwb_coef(const GwbSmem& s, double dt) {
         OuCoef oc;
         const double gam = (p < s.P) ? s.par[4 * p + 1] : s.gw[kGwGa];
         ou_coef_warp<kDeriv>(gam * dt, dt, h2, h3, dt2, oc);
-        double* o = (p < s.P) ? s.co + kCo * p : s.gw + kGwA;
+        double* o = (p < s.P) ? s.co + kCo * p : s.gc;
         o[0] = oc.a; o[1] = oc.b; o[2] = oc.c00; o[3] = oc.c01; o[4] = oc.c11;
         if (kDeriv) { o[5] = oc.db; o[6] = oc.dc00; o[7] = oc.dc01; o[8] = oc.dc11; }
     }
@@ -260,9 +327,9 @@ __device__ void gwb_coef(const GwbSmem& s, double dt) {
 // 2. predict: the mean and every upper 3x3 block, F_I P_IJ F_J^T + Q_IJ
 __device__ void gwb_predict(const GwbSmem& s) {
     const int P = s.P, n = s.n;
-    const double* gw = s.gw;
-    const double aa = gw[0], ba = gw[1], ha2 = gw[kGwHa2];
-    const double qa00 = ha2 * gw[2], qa01 = ha2 * gw[3], qa11 = ha2 * gw[4];
+    const double* gc = s.gc;
+    const double aa = gc[0], ba = gc[1], ha2 = s.gw[kGwHa2];
+    const double qa00 = ha2 * gc[2], qa01 = ha2 * gc[3], qa11 = ha2 * gc[4];
     for (int p = threadIdx.x; p < P; p += blockDim.x) {
         double* mp = s.m + 3 * p;
         mp[0] = fma(s.co[kCo * p + 1], mp[1], fma(ba, mp[2], mp[0]));
@@ -315,22 +382,25 @@ __device__ void gwb_predict(const GwbSmem& s) {
 
 // 1'. scaled frame: the coefficients of 1. (with their gamma-derivatives when
 // kDeriv) and those of Fh and S'^-1 Q S'^-1 (cs).  With kAdvance the scales
-// advance to s' = s a, and a scale below kGwbTiny raises the flag.
+// advance to s' = s a, and a scale below kGwbTiny raises the flag.  tape_sg,
+// if given, receives the scales before the step (each by the thread that
+// advances it).
 template <bool kDeriv, bool kAdvance>
-__device__ void gwb_coef_scaled(const GwbSmem& s, double dt) {
+__device__ void gwb_coef_scaled(const GwbSmem& s, double dt, double* tape_sg = nullptr) {
     const double h2 = 0.5 * dt * dt, h3 = dt * dt * dt / 3.0, dt2 = dt * dt;
     for (int p = threadIdx.x; p <= s.P; p += blockDim.x) {
         OuCoef oc;
         const bool psr = p < s.P;
         ou_coef_warp<kDeriv>((psr ? s.par[4 * p + 1] : s.gw[kGwGa]) * dt, dt, h2, h3, dt2, oc);
         const double sg = s.sg[p], sn = sg * oc.a;
+        if (tape_sg) tape_sg[p] = sg;
         if (kAdvance) {
             s.sg0[p] = sg;
             s.sg[p] = sn;
             if (!(sn >= kGwbTiny)) s.gw[kGwRn] = 1.0;
         }
         const double w = rcp_nr(sn), sc = psr ? s.par[4 * p] : s.gw[kGwHa2];
-        double* o = psr ? s.co + kCo * p : s.gw + kGwA;
+        double* o = psr ? s.co + kCo * p : s.gc;
         o[0] = oc.a; o[1] = oc.b; o[2] = oc.c00; o[3] = oc.c01; o[4] = oc.c11;
         if (kDeriv) { o[5] = oc.db; o[6] = oc.dc00; o[7] = oc.dc01; o[8] = oc.dc11; }
         double* h = s.cs + 5 * p;
@@ -393,11 +463,29 @@ __device__ __forceinline__ double gwb_scale_of(const double* sc, int P, int i) {
 // P = S Ph S, m = S mh for the scales sc (the upper triangle and the mean)
 __device__ void gwb_fold(const GwbSmem& s, const double* sc) {
     const int n = s.n, P = s.P;
-    for (int q = threadIdx.x; q < s.ne; q += blockDim.x) {
-        const int r = s.ent[2 * q], col = s.ent[2 * q + 1];
-        s.Pm[q] *= gwb_scale_of(sc, P, r) * gwb_scale_of(sc, P, col);
+    for (int r = threadIdx.x; r < n; r += blockDim.x) {   // one packed row per thread
+        const double sr = gwb_scale_of(sc, P, r);
+        double* row = prow(s.Pm, n, r);
+        for (int col = r; col < n; ++col) row[col] *= sr * gwb_scale_of(sc, P, col);
     }
     for (int i = threadIdx.x; i < n; i += blockDim.x) s.m[i] *= gwb_scale_of(sc, P, i);
+}
+
+// 2'' the scaled predict, or (a scale fell below kGwbTiny: block-uniform and
+// rare) unscale and predict unscaled
+__device__ void gwb_predict_scaled_or_fold(const GwbSmem& s) {
+    if (s.gw[kGwRn] != 0.0) {
+        gwb_fold(s, s.sg0);
+        __syncthreads();
+        gwb_predict(s);
+        for (int p = threadIdx.x; p <= s.P; p += blockDim.x) s.sg[p] = 1.0;
+        if (threadIdx.x == 0) {
+            s.gw[kGwRn] = 0.0;
+            s.gw[kGwRnAny] = 1.0;
+        }
+    } else {
+        gwb_predict_scaled(s);
+    }
 }
 
 // 3. innovate on rho of pulsar q: c = P e_i and c / S (the threads that form
@@ -423,15 +511,37 @@ __device__ void gwb_innovate(const GwbSmem& s, const GwbArgs& a, const GwbRec& r
     }
 }
 
-// 4. update (upper triangle, P_ij -= c_i (c_j / S)) and mean
+// 4. update (upper triangle, P_ij -= c_i (c_j / S)) and mean.  Thread t takes
+// packed entries t, t + T, ...; the row r and the offset in the row follow
+// the index along.  Four entries at a time, their loads ahead of their
+// stores, so that the FMAs do not wait on each other.
+__device__ __forceinline__ void gwb_advance(int n, int T, int& r, int& off) {
+    off += T;
+    while (r < n && off >= n - r) { off -= n - r; ++r; }
+}
 __device__ void gwb_update(const GwbSmem& s) {
-    const int n = s.n;
+    const int n = s.n, T = blockDim.x, ne = s.ne;
     const double g = s.gw[kGwG];
-    for (int q = threadIdx.x; q < s.ne; q += blockDim.x) {
-        const int r = s.ent[2 * q], col = s.ent[2 * q + 1];
-        s.Pm[q] = fma(-s.c[r], s.ct[col], s.Pm[q]);
+    int r = 0, off = threadIdx.x;
+    while (r < n && off >= n - r) { off -= n - r; ++r; }
+    int q = threadIdx.x;
+    for (; q + 3 * T < ne; q += 4 * T) {
+        double x[4], ci[4], cj[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            x[u] = s.Pm[q + u * T];
+            ci[u] = s.c[r];
+            cj[u] = s.ct[r + off];
+            gwb_advance(n, T, r, off);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) s.Pm[q + u * T] = fma(-ci[u], cj[u], x[u]);
     }
-    for (int i = threadIdx.x; i < n; i += blockDim.x) s.m[i] = fma(s.c[i], g, s.m[i]);
+    for (; q < ne; q += T) {
+        s.Pm[q] = fma(-s.c[r], s.ct[r + off], s.Pm[q]);
+        gwb_advance(n, T, r, off);
+    }
+    for (int i = threadIdx.x; i < n; i += T) s.m[i] = fma(s.c[i], g, s.m[i]);
 }
 
 // one forward step; thread 0 accumulates the likelihood when kLL; kScaled
@@ -442,18 +552,7 @@ __device__ void gwb_step(const GwbSmem& s, const GwbArgs& a, const GwbRec& rk, d
         if (kScaled) {
             gwb_coef_scaled<false, true>(s, rk.dt);
             __syncthreads();
-            if (s.gw[kGwRn] != 0.0) {          // block-uniform and rare: unscale, predict unscaled
-                gwb_fold(s, s.sg0);
-                __syncthreads();
-                gwb_predict(s);
-                for (int p = threadIdx.x; p <= s.P; p += blockDim.x) s.sg[p] = 1.0;
-                if (threadIdx.x == 0) {
-                    s.gw[kGwRn] = 0.0;
-                    s.gw[kGwRnAny] = 1.0;
-                }
-            } else {
-                gwb_predict_scaled(s);
-            }
+            gwb_predict_scaled_or_fold(s);
         } else {
             gwb_coef<false>(s, rk.dt);
             __syncthreads();
@@ -476,34 +575,46 @@ __device__ __forceinline__ double gwb_finish(int64_t N, double quad, const LogPr
     return (lp.bad || !isfinite(ll)) ? -INFINITY : ll;
 }
 
+// state (upper triangle of P, m, scales) to a global slot; each scale is
+// written by the thread that advances it in the next step
+__device__ void gwb_save(const GwbSmem& s, double* dst) {
+    for (int q = threadIdx.x; q < s.ne + s.n; q += blockDim.x) dst[q] = s.Pm[q];
+    for (int p = threadIdx.x; p <= s.P; p += blockDim.x) dst[s.ne + s.n + p] = s.sg[p];
+}
+
+// Likelihood; with a.ckpt also the state at every segment start (the
+// checkpoints of the gradient) and the fold flag of each vector.
 __global__ void __launch_bounds__(kGwbFwdThreads) k_gwb_filter(GwbArgs a) {
     extern __shared__ __align__(16) double gsm[];
-    const GwbSmem s = gwb_carve(gsm, a.P, false, a.G);
-    gwb_tables(s, a);
+    const GwbSmem s = gwb_carve_fwd(gsm, a.P, a.G);
+    const int64_t rec_len = gwb_rec_len(a.P);
+    gwb_tables(s);
     for (int64_t b = blockIdx.x; b < a.B; b += gridDim.x) {
         __syncthreads();
         if (!gwb_setup(s, a, a.theta + b * (2 + 3 * a.P))) {
-            if (threadIdx.x == 0) a.loglik[b] = -INFINITY;
+            if (threadIdx.x == 0) {
+                a.loglik[b] = -INFINITY;
+                if (a.flags) a.flags[b] = 0;
+            }
             continue;
         }
         double quad = 0.0;
         LogProd lp;
-        for (int64_t k = 0; k < a.N; ++k) gwb_step<true, true>(s, a, a.rec[k], quad, lp);
-        if (threadIdx.x == 0) a.loglik[b] = gwb_finish(a.N, quad, lp);
+        if (a.ckpt) {
+            double* ck = a.ckpt + b * a.ck_slot;
+            for (int seg = 0; seg < a.nseg; ++seg) {
+                gwb_save(s, ck + seg * rec_len);
+                const int64_t k1 = min(int64_t(seg + 1) * a.L, a.N);
+                for (int64_t k = int64_t(seg) * a.L; k < k1; ++k) gwb_step<true, true>(s, a, a.rec[k], quad, lp);
+            }
+        } else {
+            for (int64_t k = 0; k < a.N; ++k) gwb_step<true, true>(s, a, a.rec[k], quad, lp);
+        }
+        if (threadIdx.x == 0) {
+            a.loglik[b] = gwb_finish(a.N, quad, lp);
+            if (a.flags) a.flags[b] = s.gw[kGwRnAny] != 0.0 ? 1 : 0;
+        }
     }
-}
-
-// state (upper triangle of P, then m) to / from a global slot
-__device__ void gwb_save(const GwbSmem& s, double* dst) {
-    for (int q = threadIdx.x; q < s.ne; q += blockDim.x) dst[q] = s.Pm[q];
-    for (int i = threadIdx.x; i < s.n; i += blockDim.x) dst[s.ne + i] = s.m[i];
-    for (int p = threadIdx.x; p <= s.P; p += blockDim.x) dst[s.ne + s.n + p] = s.sg[p];
-}
-
-__device__ void gwb_load(const GwbSmem& s, const double* src) {
-    for (int q = threadIdx.x; q < s.ne; q += blockDim.x) s.Pm[q] = src[q];
-    for (int i = threadIdx.x; i < s.n; i += blockDim.x) s.m[i] = src[s.ne + i];
-    for (int p = threadIdx.x; p <= s.P; p += blockDim.x) s.sg[p] = src[s.ne + s.n + p];
 }
 
 // Reverse of the observation of TOA rk (either frame).  On entry c holds the
@@ -565,20 +676,22 @@ __device__ void gwb_adjoint_observation(const GwbSmem& s, const GwbRec& rk) {
     __syncthreads();
 }
 
-// Reverse of one forward step k, the state before it in Pm, m.  On entry Pb,
-// mb hold the adjoints of the state after the step; on exit, before it.
+// Reverse of one forward step k in the unscaled frame (the fallback for a
+// vector whose scales fold), the state before it in Pm, m.  On entry Pb, mb
+// hold the adjoints of the state after the step; on exit, before it.
 __device__ void gwb_step_adjoint(const GwbSmem& s, const GwbArgs& a, const GwbRec& rk) {
     const int P = s.P, n = s.n, q = rk.q, i0 = 3 * q;
     const int tid = threadIdx.x;
     const double dt = rk.dt;
     const bool pred = dt > 0.0;
     double* gw = s.gw;
+    const double* gc = s.gc;
     if (pred) {
         gwb_coef<true>(s, dt);
         __syncthreads();
     }
     // u = P (F^T e_i), and mu_i = (F m)_i
-    const double bq = pred ? s.co[kCo * q + 1] : 0.0, ba = pred ? gw[1] : 0.0;
+    const double bq = pred ? s.co[kCo * q + 1] : 0.0, ba = pred ? gc[1] : 0.0;
     for (int j = tid; j < n; j += blockDim.x)
         s.u[j] = fma(bq, psym(s.Pm, n, j, i0 + 1), fma(ba, psym(s.Pm, n, j, i0 + 2), psym(s.Pm, n, j, i0)));
     __syncthreads();
@@ -587,11 +700,11 @@ __device__ void gwb_step_adjoint(const GwbSmem& s, const GwbArgs& a, const GwbRe
     for (int J = tid; J < P; J += blockDim.x) {
         const double* uJ = s.u + 3 * J;
         if (pred) {
-            const double aJ = s.co[kCo * J], bJ = s.co[kCo * J + 1], aa = gw[0];
+            const double aJ = s.co[kCo * J], bJ = s.co[kCo * J + 1], aa = gc[0];
             const double g = gwb_G(s, J, q) * ha2;
-            double c0 = fma(bJ, uJ[1], fma(ba, uJ[2], uJ[0])) + g * gw[2];
+            double c0 = fma(bJ, uJ[1], fma(ba, uJ[2], uJ[0])) + g * gc[2];
             double c1 = aJ * uJ[1];
-            const double c2 = fma(aa, uJ[2], g * gw[3]);
+            const double c2 = fma(aa, uJ[2], g * gc[3]);
             if (J == q) {
                 const double s2 = s.par[4 * q];
                 c0 = fma(s2, s.co[kCo * q + 2], c0);
@@ -615,7 +728,7 @@ __device__ void gwb_step_adjoint(const GwbSmem& s, const GwbArgs& a, const GwbRe
     // forms partial sums of (M-bar F P) at (rho_I, y_I), (y_I, y_I),
     // (rho_I, a_I), (a_I, a_I) and of the GW noise's contractions with G;
     // then one thread per pulsar adds its chunks in fixed order
-    const double aa = gw[0], dba = gw[5], dca00 = gw[6], dca01 = gw[7], dca11 = gw[8];
+    const double aa = gc[0], dba = gc[5], dca00 = gc[6], dca01 = gc[7], dca11 = gc[8];
     const int nch = gwb_jchunks(P), jc = (P + nch - 1) / nch;
     for (int it = tid; it < P * nch; it += blockDim.x) {
         const int I = it / nch, ch = it - I * nch;
@@ -639,7 +752,7 @@ __device__ void gwb_step_adjoint(const GwbSmem& s, const GwbArgs& a, const GwbRe
             s4 = fma(Ma(rJ), fa0, fma(Ma(rJ + 1), fa1, fma(Ma(rJ + 2), fa2, s4)));
             const double g = gwb_G(s, I, J);
             const double X00 = Mr(rJ), X02 = Mr(rJ + 2), X20 = Ma(rJ), X22 = Ma(rJ + 2);
-            h = fma(g, fma(X00, gw[2], fma(X02 + X20, gw[3], X22 * gw[4])), h);
+            h = fma(g, fma(X00, gc[2], fma(X02 + X20, gc[3], X22 * gc[4])), h);
             gd = fma(g, fma(X00, dca00, fma(X02 + X20, dca01, X22 * dca11)), gd);
         }
         double* pt = s.part + 6 * it;
@@ -701,123 +814,246 @@ __device__ void gwb_step_adjoint(const GwbSmem& s, const GwbArgs& a, const GwbRe
     __syncthreads();
 }
 
-// Reverse of one forward step k in the scaled frame: the state before it
-// (Ph, mh and the scales s) in Pm, m, sg.  On entry Pb, mb and sgb hold the
-// adjoints of Ph, mh and s after the step; on exit, before it.  With M-bar the
+// ---------------------------------------------------------------------------
+// Reverse kernel: tape entries, the scaled adjoint step, the kernel
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void cp_async16(double* dst_smem, const double* src) {
+    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst_smem));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// all threads: start copying one tape entry (tl doubles, 16-byte aligned) to
+// shared memory; cp_async_wait_all and a barrier make it visible
+__device__ __forceinline__ void gwb_fetch_entry(double* dst, const double* src, int64_t tl) {
+    for (int64_t i = threadIdx.x; i < tl / 2; i += blockDim.x) cp_async16(dst + 2 * i, src + 2 * i);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// One forward step that also writes its tape entry to slot: the state before
+// the step (Ph, mh, scales) and, in the scaled frame, the step's coefficients
+// with their gamma-derivatives.  The unscaled frame's entry holds the state
+// only (its adjoint forms the coefficients itself).
+template <bool kScaled>
+__device__ void gwb_tape_step(const GwbSmem& s, const GwbArgs& a, const GwbRec& rk, double* slot) {
+    const int ne = s.ne, n = s.n, P = s.P;
+    for (int i = threadIdx.x; i < ne + n; i += blockDim.x) slot[i] = s.Pm[i];
+    double* tsg = slot + ne + n;
+    if (rk.dt > 0.0) {
+        if (kScaled) {
+            gwb_coef_scaled<true, true>(s, rk.dt, tsg);
+            __syncthreads();
+            const int ncoef = kCo * P + 9 + 5 * (P + 1);      // co, gc, cs
+            for (int i = threadIdx.x; i < ncoef; i += blockDim.x) tsg[P + 1 + i] = s.co[i];
+            gwb_predict_scaled_or_fold(s);
+        } else {
+            gwb_coef<false>(s, rk.dt);
+            __syncthreads();
+            gwb_predict(s);
+        }
+        __syncthreads();
+    } else if (kScaled) {
+        for (int p = threadIdx.x; p <= P; p += blockDim.x) tsg[p] = s.sg[p];
+    }
+    gwb_innovate(s, a, rk);
+    __syncthreads();
+    gwb_update(s);
+    __syncthreads();
+}
+
+// This thread's shares of the GW scale's adjoint and of the two GW
+// parameters' sums.  Every term is linear in the per-block contractions, so
+// each thread carries its own part through the steps and the parts are added
+// once per vector, in a fixed order.
+struct GwShare {
+    double sg, a3, a4;
+};
+
+// The per-pulsar end of scaled adjoint step rk whose Fh-bar dot products are
+// in dd, on thread I's share: d/d gamma_p through b_p s_p and the adjoint of
+// the scale s_p, and pulsar I's part of the adjoint of b_a s_a (into the GW
+// shares).  E: that step's tape entry.
+__device__ __forceinline__ void gwb_finish_pulsar(const GwbSmem& s, const double* E, double dt, int I,
+                                                  GwShare& sh) {
+    const int P = s.P, rI = 3 * I;
+    const double* mh = E + s.ne;
+    const double* sg = mh + s.n;
+    const double* co = sg + P + 1;
+    const double* gc = co + kCo * P;
+    const double* coI = co + kCo * I;
+    const double mbr = s.mb[rI];
+    const double bhb = fma(2.0, s.dd[I], mbr * mh[rI + 1]);         // adjoint of b_I s_I
+    const double sbt = s.sbt[I];
+    s.acc[5 * I + 1] += fma(s.par[4 * I], s.n1[I], sg[I] * fma(bhb, coI[5], -dt * coI[0] * sbt));
+    s.sgb[I] = fma(sbt, coI[0], bhb * coI[1]);
+    const double alb = fma(2.0, s.dd[P + I], mbr * mh[rI + 2]);     // pulsar I's part of that of b_a s_a
+    sh.a4 = fma(sg[P] * gc[5], alb, sh.a4);
+    sh.sg = fma(gc[1], alb, sh.sg);
+}
+
+// Reverse of forward step rk in the scaled frame.  E holds its tape entry:
+// the state before the step (Ph, mh, the scales s) and the step's
+// coefficients.  On entry Pb, mb and sgb hold the adjoints of Ph, mh and s_p
+// after the step (sh those of s_a); on exit, before it.  With M-bar the
 // adjoint of the predicted Ph and mu-bar that of the predicted mh:
 //   Fh-bar = 2 M-bar Fh Ph + mu-bar mh^T, of which b s (rho_I, y_I) and
 //   b_a s_a (rho_I, a_I, every I) are parameters;
 //   the process noise v c / s'^k (k = 0, 1, 2) passes its adjoint to v, c and
 //   s' = s a; s' passes its adjoint to s and a;
 //   Ph-bar = Fh^T M-bar Fh, mh-bar = Fh^T mu-bar.
-// The GW scale s_a is common to all pulsars; its adjoint is carried as P
-// shares (pulsar I's terms), so every sum over pulsars stays in fixed order.
-__device__ void gwb_step_adjoint_scaled(const GwbSmem& s, const GwbArgs& a, const GwbRec& rk) {
+// Row rho_I of Fh^T M-bar Fh equals that of M-bar Fh, so the two Fh-bar
+// entries of pulsar I are dot products of that row of the new Pb with columns
+// y_I and a_I of Ph.  nxt_src: a tape entry to fetch into nxt_dst meanwhile
+// (NULL: none).  Eprev: the entry of the step reversed before this one, whose
+// per-pulsar ends (gwb_finish_pulsar) run here on the last P threads during
+// the second phase (NULL: none pending).  Five phases, four barriers; on
+// return the fetch has landed, Pb is complete and this step's per-pulsar
+// ends are pending.
+__device__ void gwb_adjoint_scaled(const GwbSmem& s, const GwbArgs& a, const GwbRec& rk, const double* E,
+                                   double* nxt_dst, const double* nxt_src, const double* Eprev, double dt_prev,
+                                   int64_t tl, GwShare& sh) {
     const int P = s.P, n = s.n, q = rk.q, i0 = 3 * q;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31, warp = tid >> 5;
+    const double* Ph = E;
+    const double* mh = E + s.ne;
+    const double* sg = mh + n;
+    const double* co = sg + P + 1;
+    const double* gc = co + kCo * P;
+    const double* cs = gc + 9;
+    const double* ca = cs + 5 * P;
     const double dt = rk.dt;
     const bool pred = dt > 0.0;
     double* gw = s.gw;
-    if (pred) {
-        gwb_coef_scaled<true, false>(s, dt);
-        __syncthreads();
-    }
-    const double* ca = s.cs + 5 * P;
-    const double bq = pred ? s.cs[5 * q] : 0.0, al = pred ? ca[0] : 0.0;
-    // u = Ph (Fh^T e_i); c = Fh u + Qh e_i, the predicted column i
-    for (int j = tid; j < n; j += blockDim.x)
-        s.u[j] = fma(bq, psym(s.Pm, n, j, i0 + 1), fma(al, psym(s.Pm, n, j, i0 + 2), psym(s.Pm, n, j, i0)));
-    __syncthreads();
-    for (int J = tid; J < P; J += blockDim.x) {
-        const double* uJ = s.u + 3 * J;
+    const double bq = pred ? cs[5 * q] : 0.0, al = pred ? ca[0] : 0.0;
+    // 1. c = Fh Ph Fh^T e_i + Qh e_i, the predicted column i = rho_q, three
+    //    entries per thread; the thread of pulsar q forms S, 1/S and e/S
+    for (int J = tid; J < P; J += T) {
+        double uu[3];
+#pragma unroll
+        for (int v = 0; v < 3; ++v) {
+            const int j = 3 * J + v;
+            uu[v] = fma(bq, psym(Ph, n, j, i0 + 1), fma(al, psym(Ph, n, j, i0 + 2), psym(Ph, n, j, i0)));
+        }
+        double c0 = uu[0], c1 = uu[1], c2 = uu[2];
         if (pred) {
             const double g = gwb_G(s, J, q);
-            double c0 = fma(g, ca[1], fma(s.cs[5 * J], uJ[1], fma(al, uJ[2], uJ[0])));
-            double c1 = uJ[1];
-            const double c2 = fma(g, ca[2], uJ[2]);
+            c0 = fma(g, ca[1], fma(cs[5 * J], uu[1], fma(al, uu[2], uu[0])));
+            c2 = fma(g, ca[2], uu[2]);
             if (J == q) {
-                c0 += s.cs[5 * q + 1];
-                c1 += s.cs[5 * q + 2];
+                c0 += cs[5 * q + 1];
+                c1 += cs[5 * q + 2];
             }
-            s.c[3 * J] = c0; s.c[3 * J + 1] = c1; s.c[3 * J + 2] = c2;
-        } else {
-            s.c[3 * J] = uJ[0]; s.c[3 * J + 1] = uJ[1]; s.c[3 * J + 2] = uJ[2];
+        }
+        s.c[3 * J] = c0; s.c[3 * J + 1] = c1; s.c[3 * J + 2] = c2;
+        if (J == q) {
+            const double mu = fma(bq, mh[i0 + 1], fma(al, mh[i0 + 2], mh[i0]));
+            const double S = c0 + fma(s.par[4 * q + 2], rk.s2, a.equad2[q]);
+            const double rS = rcp_nr(S);
+            gw[kGwRS] = rS;
+            gw[kGwG] = (rk.r - mu) * rS;
         }
     }
-    if (tid == 0) {
-        const double mu = fma(bq, s.m[i0 + 1], fma(al, s.m[i0 + 2], s.m[i0]));
-        gw[kGwE] = rk.r - mu;
-        gw[kGwR0] = fma(s.par[4 * q + 2], rk.s2, a.equad2[q]);
-    }
     __syncthreads();
-    gwb_adjoint_observation(s, rk);
-    if (!pred) return;   // Fh = I, Q = 0, s unchanged: the adjoints pass through
-    // sums over J for each pulsar I, in chunks of J: (M-bar Fh Ph) at (rho_I,
-    // y_I) and (rho_I, a_I), and the GW noise's contractions with G
-    const int nch = gwb_jchunks(P), jc = (P + nch - 1) / nch;
-    for (int it = tid; it < P * nch; it += blockDim.x) {
-        const int I = it / nch, ch = it - I * nch;
-        const int rI = 3 * I, yI = rI + 1, aI = rI + 2;
-        auto Mr = [&](int j) { return psym(s.Pb, n, rI, j); };   // row rho_I of M-bar
-        auto Ma = [&](int j) { return psym(s.Pb, n, aI, j); };
-        double sB = 0.0, sA = 0.0, t1 = 0.0, t2 = 0.0, t3 = 0.0;
-        const int j_hi = min(P, (ch + 1) * jc);
-        for (int J = ch * jc; J < j_hi; ++J) {
-            const int rJ = 3 * J;
-            const double bJ = s.cs[5 * J];
-            const double py0 = psym(s.Pm, n, rJ, yI), py1 = psym(s.Pm, n, rJ + 1, yI), py2 = psym(s.Pm, n, rJ + 2, yI);
-            const double pa0 = psym(s.Pm, n, rJ, aI), pa1 = psym(s.Pm, n, rJ + 1, aI), pa2 = psym(s.Pm, n, rJ + 2, aI);
-            const double m0 = Mr(rJ), m1 = Mr(rJ + 1), m2 = Mr(rJ + 2);
-            sB = fma(m0, fma(bJ, py1, fma(al, py2, py0)), fma(m1, py1, fma(m2, py2, sB)));
-            sA = fma(m0, fma(bJ, pa1, fma(al, pa2, pa0)), fma(m1, pa1, fma(m2, pa2, sA)));
-            const double g = gwb_G(s, I, J);
-            t1 = fma(g, m0, t1);
-            t2 = fma(g, m2 + Ma(rJ), t2);
-            t3 = fma(g, Ma(rJ + 2), t3);
+    // the previous step's per-pulsar ends, on the last P threads (its Fh-bar
+    // dot products were written after its last barrier)
+    if (Eprev && tid >= T - P) gwb_finish_pulsar(s, Eprev, dt_prev, tid - (T - P), sh);
+    // 2. v = Pb c, a row per thread (two threads per row when the block has
+    //    twice as many threads as rows), and the block sums mb.c and c.v
+    const int parts = T >= 2 * n ? 2 : 1, half = (n + 1) / 2;
+    double pg = 0.0, pc = 0.0;
+    for (int base = 0; base < parts * n; base += T) {
+        const int it = base + tid, j = it / parts, h = it - j * parts;
+        const bool valid = it < parts * n;
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        if (valid) {
+            const int klo = parts == 2 && h ? half : 0, khi = parts == 2 && !h ? half : n;
+            auto pb = [&](int k) { return k < j ? s.Pb[pk(n, k, j)] : s.Pb[pk(n, j, k)]; };
+            int k = klo;
+            for (; k + 3 < khi; k += 4) {
+                a0 = fma(pb(k), s.c[k], a0);
+                a1 = fma(pb(k + 1), s.c[k + 1], a1);
+                a2 = fma(pb(k + 2), s.c[k + 2], a2);
+                a3 = fma(pb(k + 3), s.c[k + 3], a3);
+            }
+            for (; k < khi; ++k) a0 = fma(pb(k), s.c[k], a0);
         }
-        double* pt = s.part + 6 * it;
-        pt[0] = sB; pt[1] = sA; pt[2] = t1; pt[3] = t2; pt[4] = t3;
-    }
-    __syncthreads();
-    const double ha2 = gw[kGwHa2], sga = s.sg[P], wa = ca[4];
-    for (int I = tid; I < P; I += blockDim.x) {
-        const int rI = 3 * I, yI = rI + 1, aI = rI + 2;
-        double sB = 0.0, sA = 0.0, t1 = 0.0, t2 = 0.0, t3 = 0.0;
-        for (int ch = 0; ch < nch; ++ch) {
-            const double* pt = s.part + 6 * (I * nch + ch);
-            sB += pt[0]; sA += pt[1]; t1 += pt[2]; t2 += pt[3]; t3 += pt[4];
+        double acc = (a0 + a1) + (a2 + a3);
+        if (parts == 2) acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+        if (valid && h == 0) {
+            s.v[j] = acc;
+            pg = fma(s.mb[j], s.c[j], pg);
+            pc = fma(s.c[j], acc, pc);
         }
-        const double* co = s.co + kCo * I;
-        const double* cI = s.cs + 5 * I;
-        const double w = cI[4], sgI = s.sg[I], s2p = s.par[4 * I];
-        const double bhb = fma(2.0, sB, s.mb[rI] * s.m[yI]);     // adjoint of b_I s_I
-        const double alb = fma(2.0, sA, s.mb[rI] * s.m[aI]);     // pulsar I's share of that of b_a s_a
-        const double M00 = s.Pb[pk(n, rI, rI)], q1b = 2.0 * s.Pb[pk(n, rI, yI)], M11 = s.Pb[pk(n, yI, yI)];
-        // intrinsic noise v c00, v c01 / s', v c11 / s'^2 and the scale s'_I
-        const double sbt = s.sgb[I] - w * fma(q1b, cI[2], 2.0 * M11 * cI[3]);
-        double* acc = s.acc + 5 * I;
-        acc[0] += fma(M00, co[2], w * fma(q1b, co[3], w * M11 * co[4]));
-        acc[1] += fma(s2p, fma(M00, co[6], w * fma(q1b, co[7], w * M11 * co[8])),
-                      sgI * fma(bhb, co[5], -dt * co[0] * sbt));
-        s.sgb[I] = fma(sbt, co[0], bhb * co[1]);
-        // pulsar I's share of the GW terms
-        const double sbat = s.sgb[P + I] - wa * fma(t2, ca[2], 2.0 * t3 * ca[3]);
-        acc[3] += fma(t1, gw[2], wa * fma(t2, gw[3], wa * t3 * gw[4]));
-        acc[4] += fma(ha2, fma(t1, gw[6], wa * fma(t2, gw[7], wa * t3 * gw[8])),
-                      sga * fma(alb, gw[5], -dt * gw[0] * sbat));
-        s.sgb[P + I] = fma(sbat, gw[0], alb * gw[1]);
+    }
+    pg = warp_sum(pg);
+    pc = warp_sum(pc);
+    if (lane == 0) {
+        s.red[2 * warp] = pg;
+        s.red[2 * warp + 1] = pc;
     }
     __syncthreads();
-    // Pb <- Fh^T Pb Fh (upper blocks) and mb <- Fh^T mb
-    for (int qq = tid; qq < s.nb; qq += blockDim.x) {
-        const int I = s.pairs[2 * qq], J = s.pairs[2 * qq + 1];
-        const double bI = s.cs[5 * I], bJ = s.cs[5 * J];
+    // the previous step's entry is no longer read: fetch the next one into its buffer
+    if (nxt_src) gwb_fetch_entry(nxt_dst, nxt_src, tl);
+    const double rS = gw[kGwRS], g = gw[kGwG];
+    // 3. M-bar: c-bar and S-bar into row and column i of Pb; mu-bar = mb - e-bar e_i
+    for (int j = tid; j < n; j += T) {
+        const double cb = fma(s.mb[j], g, -2.0 * rS * s.v[j]);
+        if (j == i0) {     // the block sums mb.c, c.v, then S-bar and e-bar
+            double gb = 0.0, cv = 0.0;
+            for (int w = 0; w < T / 32; ++w) {
+                gb += s.red[2 * w];
+                cv += s.red[2 * w + 1];
+            }
+            const double Sb = rS * rS * cv - gb * g * rS - 0.5 * rS + 0.5 * g * g;
+            const double eb = gb * rS - g;
+            s.acc[5 * q + 2] += Sb * 2.0 * s.par[4 * q + 3] * rk.s2;     // d/d EFAC_q
+            s.Pb[pk(n, j, j)] += cb + Sb;
+            s.mb[j] -= eb;
+        } else {   // the one stored entry of the symmetric pair (j, i), (i, j)
+            double& e = s.Pb[j < i0 ? pk(n, j, i0) : pk(n, i0, j)];
+            e = fma(0.5, cb, e);
+        }
+    }
+    if (!pred) {   // Fh = I, Q = 0, scales unchanged: the adjoints pass through
+        cp_async_wait_all();
+        __syncthreads();
+        return;
+    }
+    __syncthreads();
+    if (tid == T - 1) {   // the GW share update's products for this step
+        const double wa = ca[4], ha2 = gw[kGwHa2], sga = sg[P];
+        double* K = gw + kGwK;
+        K[0] = wa * ca[2];
+        K[1] = 2.0 * wa * ca[3];
+        K[2] = gc[2];
+        K[3] = wa * gc[3];
+        K[4] = wa * wa * gc[4];
+        K[5] = ha2 * gc[6];
+        K[6] = ha2 * wa * gc[7];
+        K[7] = ha2 * wa * wa * gc[8];
+        K[8] = -sga * dt * gc[0];
+        K[9] = gc[0];
+    }
+    // 4. Pb <- Fh^T M-bar Fh, block by block, with this thread's parts of the
+    //    Hellings-Downs contractions of M-bar: sum_IJ G_IJ times its (rho_I,
+    //    rho_J), (rho_I, a_J) + (a_I, rho_J) and (a_I, a_J) entries
+    double t1 = 0.0, t2 = 0.0, t3 = 0.0;
+    for (int it = tid; it < s.nb - P; it += T) {           // blocks I < J
+        const int I = s.pairs[2 * (P + it)], J = s.pairs[2 * (P + it) + 1];
+        const double bI = cs[5 * I], bJ = cs[5 * J];
+        double* R[3];
         double X[3][3];
 #pragma unroll
-        for (int u = 0; u < 3; ++u)
+        for (int u = 0; u < 3; ++u) {
+            R[u] = prow(s.Pb, n, 3 * I + u) + 3 * J;
 #pragma unroll
-            for (int v = 0; v < 3; ++v)
-                X[u][v] = (I < J || u <= v) ? s.Pb[pk(n, 3 * I + u, 3 * J + v)] : s.Pb[pk(n, 3 * I + v, 3 * J + u)];
+            for (int v = 0; v < 3; ++v) X[u][v] = R[u][v];
+        }
+        const double g2 = 2.0 * gwb_G(s, I, J);           // the (J, I) block's terms too
+        t1 = fma(g2, X[0][0], t1);
+        t2 = fma(g2, X[0][2] + X[2][0], t2);
+        t3 = fma(g2, X[2][2], t3);
 #pragma unroll
         for (int v = 0; v < 3; ++v) {   // Fh_I^T X: rows y, a gain b_I s_I, b_a s_a times row rho
             X[1][v] = fma(bI, X[0][v], X[1][v]);
@@ -825,117 +1061,212 @@ __device__ void gwb_step_adjoint_scaled(const GwbSmem& s, const GwbArgs& a, cons
         }
 #pragma unroll
         for (int u = 0; u < 3; ++u) {   // (Fh_I^T X) Fh_J
-            const double z0 = X[u][0];
-            const double z1 = fma(bJ, z0, X[u][1]);
-            const double z2 = fma(al, z0, X[u][2]);
-            double* R = prow(s.Pb, n, 3 * I + u) + 3 * J;   // a diagonal block keeps v >= u
-            if (I < J || u == 0) R[0] = z0;
-            if (I < J || u <= 1) R[1] = z1;
-            R[2] = z2;
+            R[u][0] = X[u][0];
+            R[u][1] = fma(bJ, X[u][0], X[u][1]);
+            R[u][2] = fma(al, X[u][0], X[u][2]);
         }
     }
-    for (int J = tid; J < P; J += blockDim.x) {
-        double* mJ = s.mb + 3 * J;
-        const double m0 = mJ[0];
-        mJ[1] = fma(s.cs[5 * J], m0, mJ[1]);
-        mJ[2] = fma(al, m0, mJ[2]);
+    for (int I = T - 1 - tid; I < P; I += T) {              // diagonal blocks, on the last threads
+        const int rI = 3 * I;
+        const double bI = cs[5 * I];
+        double* R0 = prow(s.Pb, n, rI) + rI;
+        double* R1 = prow(s.Pb, n, rI + 1) + rI;
+        double* R2 = prow(s.Pb, n, rI + 2) + rI;
+        const double x00 = R0[0], x01 = R0[1], x02 = R0[2], x11 = R1[1], x12 = R1[2], x22 = R2[2];
+        const double g = gwb_G(s, I, I);
+        t1 = fma(g, x00, t1);
+        t2 = fma(g, x02 + x02, t2);
+        t3 = fma(g, x22, t3);
+        // intrinsic noise sigma^2 c00, sigma^2 c01 / s', sigma^2 c11 / s'^2 and the scale s'_I
+        const double* cI = cs + 5 * I;
+        const double* coI = co + kCo * I;
+        const double w = cI[4], q1b = 2.0 * x01;
+        s.sbt[I] = s.sgb[I] - w * fma(q1b, cI[2], 2.0 * x11 * cI[3]);
+        s.acc[5 * I] += fma(x00, coI[2], w * fma(q1b, coI[3], w * x11 * coI[4]));
+        s.n1[I] = fma(x00, coI[6], w * fma(q1b, coI[7], w * x11 * coI[8]));
+        double X[3][3] = {{x00, x01, x02}, {x01, x11, x12}, {x02, x12, x22}};
+#pragma unroll
+        for (int v = 0; v < 3; ++v) {
+            X[1][v] = fma(bI, X[0][v], X[1][v]);
+            X[2][v] = fma(al, X[0][v], X[2][v]);
+        }
+        R0[0] = X[0][0];
+        R0[1] = fma(bI, X[0][0], X[0][1]);
+        R0[2] = fma(al, X[0][0], X[0][2]);
+        R1[1] = fma(bI, X[1][0], X[1][1]);
+        R1[2] = fma(al, X[1][0], X[1][2]);
+        R2[2] = fma(al, X[2][0], X[2][2]);
+        double* mI = s.mb + rI;                             // mu-bar <- Fh^T mu-bar
+        mI[1] = fma(bI, mI[0], mI[1]);
+        mI[2] = fma(al, mI[0], mI[2]);
     }
+    cp_async_wait_all();
     __syncthreads();
+    // 5. the adjoints of b_I s_I and of b_a s_a: 2 (M-bar Fh Ph) at (rho_I, y_I)
+    //    and (rho_I, a_I) plus the mean's terms; kDotChunks lanes per dot product
+    const int items = 2 * kDotChunks * P, clen = (n + kDotChunks - 1) / kDotChunks;
+    for (int base = 0; base < items; base += T) {
+        if (base + (tid & ~31) >= items) break;             // warp-uniform
+        const int it = base + tid;
+        const bool valid = it < items;
+        const int dp = it / kDotChunks, ch = it % kDotChunks;
+        const int I = dp >> 1, kind = dp & 1, rI = 3 * I;
+        double d = 0.0, d1 = 0.0;
+        if (valid) {
+            const int col = rI + 1 + kind, k1 = min(n, (ch + 1) * clen);
+            int k = ch * clen;
+            for (; k + 1 < k1; k += 2) {
+                d = fma(psym(s.Pb, n, rI, k), psym(Ph, n, k, col), d);
+                d1 = fma(psym(s.Pb, n, rI, k + 1), psym(Ph, n, k + 1, col), d1);
+            }
+            if (k < k1) d = fma(psym(s.Pb, n, rI, k), psym(Ph, n, k, col), d);
+        }
+        d += d1;
+        static_assert(kDotChunks == 4, "the lane sum below adds groups of four lanes");
+        d += __shfl_xor_sync(0xffffffffu, d, 1);
+        d += __shfl_xor_sync(0xffffffffu, d, 2);
+        if (valid && ch == 0) s.dd[kind * P + I] = d;
+    }
+    // GW: h_a^2 c / s'^k and the scale s'_a = s_a a_a, on this thread's parts
+    // (the pulsars' parts of b_a s_a's adjoint follow in gwb_finish_pulsar)
+    const double* K = gw + kGwK;
+    const double sbat = sh.sg - fma(t2, K[0], t3 * K[1]);
+    sh.a3 = fma(t1, K[2], fma(t2, K[3], fma(t3, K[4], sh.a3)));
+    sh.a4 = fma(t1, K[5], fma(t2, K[6], fma(t3, K[7], fma(sbat, K[8], sh.a4))));
+    sh.sg = sbat * K[9];
 }
 
-__global__ void __launch_bounds__(kGwbThreads, 4) k_gwb_grad(GwbArgs a) {
+// Gradient: one vector per block.  The likelihood kernel has written
+// loglik, the checkpoints and the fold flags of this launch's vectors.
+// kMaxT threads at most per block, kMinB blocks per SM: <128, 4> keeps the
+// registers to 128 per thread, so that shared memory alone limits the
+// blocks per SM (4 blocks of 128 threads up to 20 pulsars); <256, 1> gives
+// large arrays, one block per SM, 8 warps.
+template <int kMaxT, int kMinB>
+__global__ void __launch_bounds__(kMaxT, kMinB) k_gwb_reverse(GwbArgs a) {
     extern __shared__ __align__(16) double gsm[];
-    const GwbSmem s = gwb_carve(gsm, a.P, true, a.G);
-    const int P = s.P, n = s.n, D = 2 + 3 * P;
-    const int64_t rec_len = gwb_rec_len(P);
-    double* ck = a.ckpt + int64_t(blockIdx.x) * a.slot;
-    double* tp = a.tape + int64_t(blockIdx.x) * a.slot;
-    gwb_tables(s, a);
+    GwbSmem s = gwb_carve_rev(gsm, a.P, a.nbuf, a.G);
+    const int P = s.P, n = s.n, ne = s.ne, D = 2 + 3 * P;
+    const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t rec_len = gwb_rec_len(P), tl = gwb_tape_len(P);
+    double* tp = a.tape + int64_t(blockIdx.x) * a.tape_slot;
+    double* const Ebuf[2] = {s.Pm, s.E1};
+    gwb_tables(s);
     for (int64_t b = blockIdx.x; b < a.B; b += gridDim.x) {
         double* gout = a.grad + b * D;
+        double* ck = a.ckpt + b * a.ck_slot;
+        const double* th = a.theta + b * D;
         __syncthreads();
-        if (!gwb_setup(s, a, a.theta + b * D)) {
-            for (int j = threadIdx.x; j < D; j += blockDim.x) gout[j] = 0.0;
-            if (threadIdx.x == 0) a.loglik[b] = -INFINITY;
+        if (!gwb_setup(s, a, th) || !isfinite(a.loglik[b]) || a.N == 0) {
+            for (int j = tid; j < D; j += T) gout[j] = 0.0;
             continue;
         }
-        // forward in the scaled frame, with the state saved at each segment
-        // start; a vector whose scales had to be folded back (a fast decay
-        // over a long gap) runs the whole gradient unscaled instead
-        double quad = 0.0;
-        LogProd lp;
-        for (int seg = 0; seg < a.nseg; ++seg) {
-            gwb_save(s, ck + seg * rec_len);
-            const int64_t k1 = min(int64_t(seg + 1) * a.L, a.N);
-            for (int64_t k = int64_t(seg) * a.L; k < k1; ++k) gwb_step<true, true>(s, a, a.rec[k], quad, lp);
-        }
-        const bool scaled = s.gw[kGwRnAny] == 0.0;
-        if (!scaled) {
-            __syncthreads();
-            gwb_setup(s, a, a.theta + b * D);
-            quad = 0.0;
-            lp = LogProd();
-            for (int seg = 0; seg < a.nseg; ++seg) {
-                gwb_save(s, ck + seg * rec_len);
-                const int64_t k1 = min(int64_t(seg + 1) * a.L, a.N);
-                for (int64_t k = int64_t(seg) * a.L; k < k1; ++k) gwb_step<true>(s, a, a.rec[k], quad, lp);
+        bool scaled = a.flags[b] == 0;
+        GwShare sh{0.0, 0.0, 0.0};
+        for (;;) {   // the scaled frame, then (rarely) the unscaled one
+            for (int i = tid; i < ne; i += T) s.Pb[i] = 0.0;
+            for (int i = tid; i < n; i += T) s.mb[i] = 0.0;
+            for (int i = tid; i < 5 * P; i += T) s.acc[i] = 0.0;
+            for (int i = tid; i < P; i += T) s.sgb[i] = 0.0;
+            sh = GwShare{0.0, 0.0, 0.0};
+            if (!scaled) {   // the checkpoints again, unscaled
+                __syncthreads();
+                gwb_setup(s, a, th);
+                double quad = 0.0;
+                LogProd lp;
+                for (int seg = 0; seg < a.nseg; ++seg) {
+                    gwb_save(s, ck + seg * rec_len);
+                    const int64_t k1 = min(int64_t(seg + 1) * a.L, a.N);
+                    for (int64_t k = int64_t(seg) * a.L; k < k1; ++k) gwb_step<false>(s, a, a.rec[k], quad, lp);
+                }
             }
+            bool refold = false;
+            for (int seg = a.nseg - 1; seg >= 0; --seg) {
+                const int64_t k0 = int64_t(seg) * a.L, k1 = min(k0 + a.L, a.N);
+                __syncthreads();
+                for (int64_t i = tid; i < rec_len; i += T) s.Pm[i] = ck[seg * rec_len + i];
+                if (tid == 0) s.gw[kGwRnAny] = 0.0;
+                __syncthreads();
+                // re-run the segment, writing its tape
+                for (int64_t k = k0; k < k1; ++k) {
+                    if (scaled) gwb_tape_step<true>(s, a, a.rec[k], tp + (k - k0) * tl);
+                    else gwb_tape_step<false>(s, a, a.rec[k], tp + (k - k0) * tl);
+                }
+                if (scaled && s.gw[kGwRnAny] != 0.0) {   // a fold the likelihood pass did not flag
+                    refold = true;
+                    break;
+                }
+                // the adjoint steps, last first
+                if (scaled) {
+                    gwb_fetch_entry(Ebuf[(k1 - 1) & 1], tp + (k1 - 1 - k0) * tl, tl);
+                    cp_async_wait_all();
+                    __syncthreads();
+                    for (int64_t k = k1 - 1; k >= k0; --k) {
+                        const bool ahead = a.nbuf == 2 && k > k0;
+                        const bool pend = a.nbuf == 2 && k < k1 - 1 && a.rec[k + 1].dt > 0.0;
+                        gwb_adjoint_scaled(s, a, a.rec[k], Ebuf[k & 1], ahead ? Ebuf[(k - 1) & 1] : nullptr,
+                                           ahead ? tp + (k - 1 - k0) * tl : nullptr,
+                                           pend ? Ebuf[(k + 1) & 1] : nullptr, pend ? a.rec[k + 1].dt : 0.0, tl, sh);
+                        if (a.nbuf == 1 || k == k0) {   // no buffer keeps this entry for the next step
+                            __syncthreads();
+                            if (a.rec[k].dt > 0.0 && tid >= T - P)
+                                gwb_finish_pulsar(s, Ebuf[k & 1], a.rec[k].dt, tid - (T - P), sh);
+                            if (a.nbuf == 1 && k > k0) {
+                                __syncthreads();
+                                gwb_fetch_entry(s.Pm, tp + (k - 1 - k0) * tl, tl);
+                                cp_async_wait_all();
+                                __syncthreads();
+                            }
+                        }
+                    }
+                } else {
+                    for (int64_t k = k1 - 1; k >= k0; --k) {
+                        __syncthreads();
+                        for (int64_t i = tid; i < ne + n; i += T) s.Pm[i] = tp[(k - k0) * tl + i];
+                        __syncthreads();
+                        gwb_step_adjoint(s, a, a.rec[k]);
+                    }
+                }
+            }
+            if (!refold) break;
+            scaled = false;
         }
-        if (threadIdx.x == 0) {
-            const double ll = gwb_finish(a.N, quad, lp);
-            a.loglik[b] = ll;
-            s.gw[kGwOk] = isfinite(ll) ? 1.0 : 0.0;
-        }
-        for (int i = threadIdx.x; i < s.ne; i += blockDim.x) s.Pb[i] = 0.0;
-        for (int i = threadIdx.x; i < n; i += blockDim.x) s.mb[i] = 0.0;
-        for (int i = threadIdx.x; i < 5 * P; i += blockDim.x) s.acc[i] = 0.0;
-        for (int i = threadIdx.x; i < 2 * P; i += blockDim.x) s.sgb[i] = 0.0;
         __syncthreads();
-        if (s.gw[kGwOk] == 0.0 || a.N == 0) {
-            for (int j = threadIdx.x; j < D; j += blockDim.x) gout[j] = 0.0;
-            continue;
-        }
-        // reverse, segment by segment: re-run the segment saving the state
-        // before each step, then the adjoint steps in reverse order
-        for (int seg = a.nseg - 1; seg >= 0; --seg) {
-            const int64_t k0 = int64_t(seg) * a.L, k1 = min(k0 + a.L, a.N);
-            gwb_load(s, ck + seg * rec_len);
-            __syncthreads();
-            for (int64_t k = k0; k < k1; ++k) {
-                gwb_save(s, tp + (k - k0) * rec_len);
-                if (scaled) gwb_step<false, true>(s, a, a.rec[k], quad, lp);
-                else gwb_step<false>(s, a, a.rec[k], quad, lp);
-            }
-            for (int64_t k = k1 - 1; k >= k0; --k) {
-                __syncthreads();
-                gwb_load(s, tp + (k - k0) * rec_len);
-                __syncthreads();
-                if (scaled) gwb_step_adjoint_scaled(s, a, a.rec[k]);
-                else gwb_step_adjoint(s, a, a.rec[k]);
-            }
-        }
         // the stationary prior of the a block: h_a^2 G / (2 gamma_a)
         const double ha2 = s.gw[kGwHa2], ga = s.gw[kGwGa];
-        for (int I = threadIdx.x; I < P; I += blockDim.x) {
+        for (int I = tid; I < P; I += T) {
             double h = 0.0;
             for (int J = 0; J < P; ++J) h = fma(psym(s.Pb, n, 3 * I + 2, 3 * J + 2), gwb_G(s, I, J), h);
             s.acc[5 * I + 3] += h / (2.0 * ga);
             s.acc[5 * I + 4] -= h * ha2 / (2.0 * ga * ga);
         }
+        const double a3 = warp_sum(sh.a3), a4 = warp_sum(sh.a4);
+        if (lane == 0) {
+            s.red[2 * warp] = a3;
+            s.red[2 * warp + 1] = a4;
+        }
         __syncthreads();
-        if (threadIdx.x == 0) {
+        if (tid == 0) {
             double hb = 0.0, gb = 0.0;
             for (int I = 0; I < P; ++I) { hb += s.acc[5 * I + 3]; gb += s.acc[5 * I + 4]; }
+            for (int w = 0; w < T / 32; ++w) { hb += s.red[2 * w]; gb += s.red[2 * w + 1]; }
             gout[0] = hb * 2.0 * kLn10Gwb * ha2;
             gout[1] = gb * kLn10Gwb * ga;
         }
-        for (int p = threadIdx.x; p < P; p += blockDim.x) {
+        for (int p = tid; p < P; p += T) {
             gout[2 + 3 * p] = s.acc[5 * p] * 2.0 * kLn10Gwb * s.par[4 * p];
             gout[3 + 3 * p] = s.acc[5 * p + 1] * kLn10Gwb * s.par[4 * p + 1];
             gout[4 + 3 * p] = s.acc[5 * p + 2];
         }
     }
 }
+
+using GwbRevKernel = void (*)(GwbArgs);
+struct GwbRevCand {
+    GwbRevKernel k;
+    int max_threads;
+};
+const GwbRevCand kGwbRevCands[] = {{k_gwb_reverse<128, 4>, 128}, {k_gwb_reverse<256, 1>, 256}};
 
 }  // namespace
 }  // namespace argus
@@ -953,10 +1284,15 @@ struct argus_gwb {
     double* d_G = nullptr;
     double* d_stage = nullptr;
     size_t cap_stage = 0;
-    // gradient: per resident block, the segment-start states and one segment's tape
+    // gradient: per vector of a launch the segment-start states and the fold
+    // flag; per resident reverse block one segment's tape
     double* d_ckpt = nullptr;
+    int32_t* d_flags = nullptr;
     double* d_tape = nullptr;
-    size_t cap_ckpt = 0;
+    size_t cap_ckpt = 0, cap_flags = 0, cap_tape = 0;
+    // reverse kernel's configuration (rev_threads 0: not chosen yet)
+    GwbRevKernel rev_kernel = nullptr;
+    int rev_threads = 0, rev_nbuf = 0, rev_per_sm = 0;
 };
 
 namespace {
@@ -1062,18 +1398,22 @@ argus_status argus_gwb_create(const argus_pulsar* psrs, int32_t n_pulsars, int32
         (e = cudaMemcpy(h->d_equad2, eq2.data(), sizeof(double) * eq2.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(h->d_G, G.data(), sizeof(double) * G.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
         return bail(e, "cudaMemcpy");
-    // the kernel's dynamic shared memory limit, set for the largest array any
-    // handle may hold (a per-function setting shared by all handles)
+    // the kernels' dynamic shared memory limits, set for the largest array any
+    // handle may hold (a per-function setting shared by all handles), and all
+    // of the unified L1 as shared memory: blocks per SM are set by shared memory
     if ((e = cudaFuncSetAttribute(k_gwb_filter, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  int(gwb_smem_bytes(kGwbMaxPulsars, false)))) != cudaSuccess ||
-        (e = cudaFuncSetAttribute(k_gwb_grad, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  int(gwb_smem_bytes(kGwbGradMaxPulsars, true)))) != cudaSuccess ||
-        // all of the unified L1 as shared memory: blocks per SM are set by shared memory
+                                  int(gwb_fwd_smem_bytes(kGwbMaxPulsars)))) != cudaSuccess ||
         (e = cudaFuncSetAttribute(k_gwb_filter, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                  int(cudaSharedmemCarveoutMaxShared))) != cudaSuccess ||
-        (e = cudaFuncSetAttribute(k_gwb_grad, cudaFuncAttributePreferredSharedMemoryCarveout,
                                   int(cudaSharedmemCarveoutMaxShared))) != cudaSuccess)
         return bail(e, "cudaFuncSetAttribute");
+    for (const GwbRevCand& c : kGwbRevCands) {
+        const size_t most = std::min<size_t>(size_t(prop.sharedMemPerBlockOptin),
+                                             gwb_rev_smem_bytes(kGwbGradMaxPulsars, 1, kGwbRevMaxThreads));
+        if ((e = cudaFuncSetAttribute(c.k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(most))) != cudaSuccess ||
+            (e = cudaFuncSetAttribute(c.k, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                      int(cudaSharedmemCarveoutMaxShared))) != cudaSuccess)
+            return bail(e, "cudaFuncSetAttribute");
+    }
     if (prev >= 0) cudaSetDevice(prev);
     *out = h;
     return ARGUS_OK;
@@ -1091,6 +1431,7 @@ void argus_gwb_destroy(argus_gwb* h) {
     cudaFree(h->d_G);
     cudaFree(h->d_stage);
     cudaFree(h->d_ckpt);
+    cudaFree(h->d_flags);
     cudaFree(h->d_tape);
     if (prev >= 0) cudaSetDevice(prev);
     delete h;
@@ -1140,7 +1481,7 @@ argus_status argus_gwb_loglik(argus_gwb* h, const double* theta, int64_t B, doub
         GwbArgs a{};
         a.rec = h->d_rec; a.N = h->N; a.P = h->P; a.p0 = h->d_p0; a.equad2 = h->d_equad2; a.G = h->d_G;
         a.theta = th_d; a.B = B; a.loglik = ll_d;
-        const size_t smem = gwb_smem_bytes(h->P, false);
+        const size_t smem = gwb_fwd_smem_bytes(h->P);
         const int grid = int(std::min<int64_t>(B, int64_t(h->n_sm) * 8));
         k_gwb_filter<<<grid, kGwbFwdThreads, smem, s>>>(a);
         if ((e = cudaGetLastError()) != cudaSuccess) {
@@ -1175,35 +1516,85 @@ argus_status argus_gwb_loglik_grad(argus_gwb* h, const double* theta, int64_t B,
     cudaGetDevice(&prev);
     cudaSetDevice(h->device);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    const int D = 2 + 3 * h->P;
+    const int P = h->P, D = 2 + 3 * P;
     const bool dev_in = gwb_is_device_ptr(theta), dev_ll = gwb_is_device_ptr(loglik),
                dev_g = gwb_is_device_ptr(grad);
     const double* th_d = theta;
     double *ll_d = loglik, *g_d = grad;
     cudaError_t e = cudaSuccess;
     argus_status st = ARGUS_OK;
-    const size_t smem = gwb_smem_bytes(h->P, true);
-    int per_sm = 1;
     const int L = std::max(1, int(std::ceil(std::sqrt(double(std::max<int64_t>(h->N, 1))))));
     const int nseg = int((h->N + L - 1) / L);
-    const size_t slot = size_t(std::max(nseg, L)) * size_t(gwb_rec_len(h->P));
-    int grid = 1;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gwb_grad, kGwbThreads, smem)) != cudaSuccess) {
-        st = argus_status(gwb_cuda(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor"));
-        goto done;
-    }
-    grid = int(std::min<int64_t>(B, int64_t(h->n_sm) * std::max(per_sm, 1)));
-    if (slot * grid > h->cap_ckpt) {
-        cudaFree(h->d_ckpt);
-        cudaFree(h->d_tape);
-        h->d_ckpt = h->d_tape = nullptr;
-        h->cap_ckpt = 0;
-        if ((e = cudaMalloc(&h->d_ckpt, slot * grid * sizeof(double))) != cudaSuccess ||
-            (e = cudaMalloc(&h->d_tape, slot * grid * sizeof(double))) != cudaSuccess) {
-            st = argus_status(gwb_cuda(e, "cudaMalloc(gradient scratch)"));
+    const int64_t rec_len = gwb_rec_len(P), tl = gwb_tape_len(P);
+    const int64_t ck_slot = std::max<int64_t>(1, int64_t(nseg) * rec_len);
+    const int64_t tape_slot = int64_t(L) * tl;
+    int64_t chunk = 0, resident = 0;
+    // reverse kernel: the most resident warps per SM; then two tape-entry
+    // buffers over one, then fewer threads per block
+    if (h->rev_threads == 0) {
+        int best_w = 0;
+        for (int nbuf = 2; nbuf >= 1; --nbuf)
+            for (const GwbRevCand& c : kGwbRevCands)
+                for (int t = 64; t <= c.max_threads; t *= 2) {
+                    int per_sm = 0;
+                    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, c.k, t, gwb_rev_smem_bytes(P, nbuf, t)) !=
+                        cudaSuccess) {
+                        cudaGetLastError();
+                        per_sm = 0;
+                    }
+                    if (per_sm * t / 32 > best_w) {
+                        best_w = per_sm * t / 32;
+                        h->rev_kernel = c.k;
+                        h->rev_threads = t;
+                        h->rev_nbuf = nbuf;
+                        h->rev_per_sm = per_sm;
+                    }
+                }
+        if (best_w == 0) {
+            st = argus_status(gwb_fail(ARGUS_ERR_UNSUPPORTED, "the gradient kernel does not fit on this device"));
             goto done;
         }
-        h->cap_ckpt = slot * grid;
+    }
+    // vectors per launch pair: every resident reverse block busy, checkpoints
+    // within kGwbCkptBudget bytes where that allows more
+    {
+        constexpr int64_t kGwbCkptBudget = int64_t(4) << 30;
+        resident = int64_t(h->n_sm) * h->rev_per_sm;
+        const int64_t by_mem = kGwbCkptBudget / (ck_slot * int64_t(sizeof(double)));
+        chunk = std::min<int64_t>(B, std::max<int64_t>(resident, by_mem - by_mem % resident));
+    }
+    if (size_t(chunk * ck_slot) > h->cap_ckpt) {
+        cudaFree(h->d_ckpt);
+        h->d_ckpt = nullptr;
+        h->cap_ckpt = 0;
+        if ((e = cudaMalloc(&h->d_ckpt, size_t(chunk * ck_slot) * sizeof(double))) != cudaSuccess) {
+            st = argus_status(gwb_cuda(e, "cudaMalloc(gradient checkpoints)"));
+            goto done;
+        }
+        h->cap_ckpt = size_t(chunk * ck_slot);
+    }
+    if (size_t(chunk) > h->cap_flags) {
+        cudaFree(h->d_flags);
+        h->d_flags = nullptr;
+        h->cap_flags = 0;
+        if ((e = cudaMalloc(&h->d_flags, size_t(chunk) * sizeof(int32_t))) != cudaSuccess) {
+            st = argus_status(gwb_cuda(e, "cudaMalloc(gradient flags)"));
+            goto done;
+        }
+        h->cap_flags = size_t(chunk);
+    }
+    {
+        const size_t need = size_t(std::min(chunk, resident) * tape_slot);
+        if (need > h->cap_tape) {
+            cudaFree(h->d_tape);
+            h->d_tape = nullptr;
+            h->cap_tape = 0;
+            if ((e = cudaMalloc(&h->d_tape, need * sizeof(double))) != cudaSuccess) {
+                st = argus_status(gwb_cuda(e, "cudaMalloc(gradient tape)"));
+                goto done;
+            }
+            h->cap_tape = need;
+        }
     }
     if (!dev_in || !dev_ll || !dev_g) {
         const size_t need = size_t(B) * (2 * D + 1);
@@ -1228,29 +1619,38 @@ argus_status argus_gwb_loglik_grad(argus_gwb* h, const double* theta, int64_t B,
         if (!dev_ll) ll_d = h->d_stage + size_t(B) * D;
         if (!dev_g) g_d = h->d_stage + size_t(B) * (D + 1);
     }
-    {
+    for (int64_t c0 = 0; c0 < B; c0 += chunk) {
+        const int64_t bc = std::min(chunk, B - c0);
         GwbArgs a{};
-        a.rec = h->d_rec; a.N = h->N; a.P = h->P; a.p0 = h->d_p0; a.equad2 = h->d_equad2; a.G = h->d_G;
-        a.theta = th_d; a.B = B; a.loglik = ll_d; a.grad = g_d;
-        a.ckpt = h->d_ckpt; a.tape = h->d_tape; a.slot = int64_t(slot); a.L = L; a.nseg = nseg;
-        k_gwb_grad<<<grid, kGwbThreads, smem, s>>>(a);
+        a.rec = h->d_rec; a.N = h->N; a.P = P; a.p0 = h->d_p0; a.equad2 = h->d_equad2; a.G = h->d_G;
+        a.theta = th_d + c0 * D; a.B = bc; a.loglik = ll_d + c0; a.grad = g_d + c0 * D;
+        a.ckpt = h->d_ckpt; a.flags = h->d_flags; a.tape = h->d_tape;
+        a.ck_slot = ck_slot; a.tape_slot = tape_slot; a.L = L; a.nseg = nseg; a.nbuf = h->rev_nbuf;
+        // the likelihood, the checkpoints and the fold flags; then the reverse sweep
+        k_gwb_filter<<<int(std::min<int64_t>(bc, int64_t(h->n_sm) * 8)), kGwbFwdThreads, gwb_fwd_smem_bytes(P), s>>>(a);
         if ((e = cudaGetLastError()) != cudaSuccess) {
-            st = argus_status(gwb_cuda(e, "k_gwb_grad"));
+            st = argus_status(gwb_cuda(e, "k_gwb_filter"));
             goto done;
         }
-        if (!dev_ll &&
-            (e = cudaMemcpyAsync(loglik, ll_d, sizeof(double) * B, cudaMemcpyDeviceToHost, s)) != cudaSuccess) {
-            st = argus_status(gwb_cuda(e, "cudaMemcpyAsync(loglik)"));
+        h->rev_kernel<<<int(std::min(bc, resident)), h->rev_threads,
+                        gwb_rev_smem_bytes(P, h->rev_nbuf, h->rev_threads), s>>>(a);
+        if ((e = cudaGetLastError()) != cudaSuccess) {
+            st = argus_status(gwb_cuda(e, "k_gwb_reverse"));
             goto done;
         }
-        if (!dev_g &&
-            (e = cudaMemcpyAsync(grad, g_d, sizeof(double) * B * D, cudaMemcpyDeviceToHost, s)) != cudaSuccess) {
-            st = argus_status(gwb_cuda(e, "cudaMemcpyAsync(grad)"));
-            goto done;
-        }
-        if (!dev_in || !dev_ll || !dev_g) {
-            if ((e = cudaStreamSynchronize(s)) != cudaSuccess) st = argus_status(gwb_cuda(e, "cudaStreamSynchronize"));
-        }
+    }
+    if (!dev_ll &&
+        (e = cudaMemcpyAsync(loglik, ll_d, sizeof(double) * B, cudaMemcpyDeviceToHost, s)) != cudaSuccess) {
+        st = argus_status(gwb_cuda(e, "cudaMemcpyAsync(loglik)"));
+        goto done;
+    }
+    if (!dev_g &&
+        (e = cudaMemcpyAsync(grad, g_d, sizeof(double) * B * D, cudaMemcpyDeviceToHost, s)) != cudaSuccess) {
+        st = argus_status(gwb_cuda(e, "cudaMemcpyAsync(grad)"));
+        goto done;
+    }
+    if (!dev_in || !dev_ll || !dev_g) {
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) st = argus_status(gwb_cuda(e, "cudaStreamSynchronize"));
     }
 done:
     if (prev >= 0) cudaSetDevice(prev);
