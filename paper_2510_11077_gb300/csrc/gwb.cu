@@ -71,10 +71,13 @@ constexpr int kGwbGradMaxPulsars = 48;   // gradient: the adjoint and a tape ent
 constexpr int kCo = 9;                   // per-pulsar coefficients (see GwbSmem::co)
 constexpr int kDotChunks = 4;            // lanes per dot product in the adjoint's parameter sums
 
-struct GwbRec {     // one TOA of the merged, time-ordered stream (32 bytes)
+struct GwbRec {     // one TOA of the merged, time-ordered stream (56 bytes)
     double dt;      // time since the previous TOA of any pulsar (0 for the first)
     double r;       // residual, s
     double s2;      // sigma_k^2
+    double h2;      // dt^2 / 2
+    double h3;      // dt^3 / 3
+    double dt2;     // dt^2
     int32_t q;      // pulsar
     int32_t pad;
 };
@@ -312,8 +315,8 @@ __device__ bool gwb_setup(const GwbSmem& s, const GwbArgs& a, const double* th) 
 
 // 1. transition coefficients over dt (threads 0..P-1 the pulsars, thread P the GW process)
 template <bool kDeriv>
-__device__ void gwb_coef(const GwbSmem& s, double dt) {
-    const double h2 = 0.5 * dt * dt, h3 = dt * dt * dt / 3.0, dt2 = dt * dt;
+__device__ void gwb_coef(const GwbSmem& s, const GwbRec& rk) {
+    const double dt = rk.dt, h2 = rk.h2, h3 = rk.h3, dt2 = rk.dt2;
     for (int p = threadIdx.x; p <= s.P; p += blockDim.x) {
         OuCoef oc;
         const double gam = (p < s.P) ? s.par[4 * p + 1] : s.gw[kGwGa];
@@ -386,8 +389,8 @@ __device__ void gwb_predict(const GwbSmem& s) {
 // if given, receives the scales before the step (each by the thread that
 // advances it).
 template <bool kDeriv, bool kAdvance>
-__device__ void gwb_coef_scaled(const GwbSmem& s, double dt, double* tape_sg = nullptr) {
-    const double h2 = 0.5 * dt * dt, h3 = dt * dt * dt / 3.0, dt2 = dt * dt;
+__device__ void gwb_coef_scaled(const GwbSmem& s, const GwbRec& rk, double* tape_sg = nullptr) {
+    const double dt = rk.dt, h2 = rk.h2, h3 = rk.h3, dt2 = rk.dt2;
     for (int p = threadIdx.x; p <= s.P; p += blockDim.x) {
         OuCoef oc;
         const bool psr = p < s.P;
@@ -488,25 +491,35 @@ __device__ void gwb_predict_scaled_or_fold(const GwbSmem& s) {
     }
 }
 
+// first item of a role whose item x runs on thread (o + x) mod T: single-warp
+// roles start on different warps, so that the four sub-partitions' FP64
+// pipes share the serial work of a step
+__device__ __forceinline__ int gwb_role_first(int o) {
+    const int T = blockDim.x;
+    return (int(threadIdx.x) + T - o % T) % T;
+}
+
 // 3. innovate on rho of pulsar q: c = P e_i and c / S (the threads that form
-// c each form 1/S); thread 0 records e, S, 1/S, e/S
+// c each form 1/S; in blocks of 128 threads or more the second half, while
+// the first computes the coefficients); item 0 records e, S, 1/S, e/S
 __device__ void gwb_innovate(const GwbSmem& s, const GwbArgs& a, const GwbRec& rk) {
-    const int n = s.n, i0 = 3 * rk.q;
-    if (threadIdx.x < n) {
+    const int n = s.n, i0 = 3 * rk.q, T = blockDim.x;
+    int i = gwb_role_first(T >= 128 ? T / 2 : 0);
+    if (i < n) {
         const double R = fma(s.par[4 * rk.q + 2], rk.s2, a.equad2[rk.q]);
         const double S = s.Pm[pk(n, i0, i0)] + R;
         const double rS = rcp_nr(S);
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        for (; i < n; i += T) {
             const double ci = psym(s.Pm, n, i, i0);
             s.c[i] = ci;
             s.ct[i] = ci * rS;
-        }
-        if (threadIdx.x == 0) {
-            const double e = rk.r - s.m[i0];
-            s.gw[kGwE] = e;
-            s.gw[kGwS] = S;
-            s.gw[kGwRS] = rS;
-            s.gw[kGwG] = e * rS;
+            if (i == 0) {
+                const double e = rk.r - s.m[i0];
+                s.gw[kGwE] = e;
+                s.gw[kGwS] = S;
+                s.gw[kGwRS] = rS;
+                s.gw[kGwG] = e * rS;
+            }
         }
     }
 }
@@ -550,11 +563,11 @@ template <bool kLL, bool kScaled = false>
 __device__ void gwb_step(const GwbSmem& s, const GwbArgs& a, const GwbRec& rk, double& quad, LogProd& lp) {
     if (rk.dt > 0.0) {
         if (kScaled) {
-            gwb_coef_scaled<false, true>(s, rk.dt);
+            gwb_coef_scaled<false, true>(s, rk);
             __syncthreads();
             gwb_predict_scaled_or_fold(s);
         } else {
-            gwb_coef<false>(s, rk.dt);
+            gwb_coef<false>(s, rk);
             __syncthreads();
             gwb_predict(s);
         }
@@ -687,7 +700,7 @@ __device__ void gwb_step_adjoint(const GwbSmem& s, const GwbArgs& a, const GwbRe
     double* gw = s.gw;
     const double* gc = s.gc;
     if (pred) {
-        gwb_coef<true>(s, dt);
+        gwb_coef<true>(s, rk);
         __syncthreads();
     }
     // u = P (F^T e_i), and mu_i = (F m)_i
@@ -842,13 +855,13 @@ __device__ void gwb_tape_step(const GwbSmem& s, const GwbArgs& a, const GwbRec& 
     double* tsg = slot + ne + n;
     if (rk.dt > 0.0) {
         if (kScaled) {
-            gwb_coef_scaled<true, true>(s, rk.dt, tsg);
+            gwb_coef_scaled<true, true>(s, rk, tsg);
             __syncthreads();
             const int ncoef = kCo * P + 9 + 5 * (P + 1);      // co, gc, cs
             for (int i = threadIdx.x; i < ncoef; i += blockDim.x) tsg[P + 1 + i] = s.co[i];
             gwb_predict_scaled_or_fold(s);
         } else {
-            gwb_coef<false>(s, rk.dt);
+            gwb_coef<false>(s, rk);
             __syncthreads();
             gwb_predict(s);
         }
@@ -906,8 +919,8 @@ __device__ __forceinline__ void gwb_finish_pulsar(const GwbSmem& s, const double
 // entries of pulsar I are dot products of that row of the new Pb with columns
 // y_I and a_I of Ph.  nxt_src: a tape entry to fetch into nxt_dst meanwhile
 // (NULL: none).  Eprev: the entry of the step reversed before this one, whose
-// per-pulsar ends (gwb_finish_pulsar) run here on the last P threads during
-// the second phase (NULL: none pending).  Five phases, four barriers; on
+// per-pulsar ends (gwb_finish_pulsar) run here, during the second phase, on
+// the threads that formed c (NULL: none pending).  Five phases, four barriers; on
 // return the fetch has landed, Pb is complete and this step's per-pulsar
 // ends are pending.
 __device__ void gwb_adjoint_scaled(const GwbSmem& s, const GwbArgs& a, const GwbRec& rk, const double* E,
@@ -928,7 +941,7 @@ __device__ void gwb_adjoint_scaled(const GwbSmem& s, const GwbArgs& a, const Gwb
     const double bq = pred ? cs[5 * q] : 0.0, al = pred ? ca[0] : 0.0;
     // 1. c = Fh Ph Fh^T e_i + Qh e_i, the predicted column i = rho_q, three
     //    entries per thread; the thread of pulsar q forms S, 1/S and e/S
-    for (int J = tid; J < P; J += T) {
+    for (int J = gwb_role_first(32); J < P; J += T) {    // from the second warp on
         double uu[3];
 #pragma unroll
         for (int v = 0; v < 3; ++v) {
@@ -955,56 +968,51 @@ __device__ void gwb_adjoint_scaled(const GwbSmem& s, const GwbArgs& a, const Gwb
         }
     }
     __syncthreads();
-    // the previous step's per-pulsar ends, on the last P threads (its Fh-bar
-    // dot products were written after its last barrier)
-    if (Eprev && tid >= T - P) gwb_finish_pulsar(s, Eprev, dt_prev, tid - (T - P), sh);
+    // the previous step's per-pulsar ends (its Fh-bar dot products were
+    // written after its last barrier)
+    if (Eprev)
+        for (int I = gwb_role_first(32); I < P; I += T) gwb_finish_pulsar(s, Eprev, dt_prev, I, sh);
     // 2. v = Pb c, a row per thread (two threads per row when the block has
-    //    twice as many threads as rows), and the block sums mb.c and c.v
+    //    twice as many threads as rows)
     const int parts = T >= 2 * n ? 2 : 1, half = (n + 1) / 2;
-    double pg = 0.0, pc = 0.0;
     for (int base = 0; base < parts * n; base += T) {
         const int it = base + tid, j = it / parts, h = it - j * parts;
         const bool valid = it < parts * n;
-        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        double a0 = 0.0, a1 = 0.0;
         if (valid) {
             const int klo = parts == 2 && h ? half : 0, khi = parts == 2 && !h ? half : n;
             auto pb = [&](int k) { return k < j ? s.Pb[pk(n, k, j)] : s.Pb[pk(n, j, k)]; };
             int k = klo;
-            for (; k + 3 < khi; k += 4) {
+            for (; k + 1 < khi; k += 2) {
                 a0 = fma(pb(k), s.c[k], a0);
                 a1 = fma(pb(k + 1), s.c[k + 1], a1);
-                a2 = fma(pb(k + 2), s.c[k + 2], a2);
-                a3 = fma(pb(k + 3), s.c[k + 3], a3);
             }
-            for (; k < khi; ++k) a0 = fma(pb(k), s.c[k], a0);
+            if (k < khi) a0 = fma(pb(k), s.c[k], a0);
         }
-        double acc = (a0 + a1) + (a2 + a3);
+        double acc = a0 + a1;
         if (parts == 2) acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-        if (valid && h == 0) {
-            s.v[j] = acc;
-            pg = fma(s.mb[j], s.c[j], pg);
-            pc = fma(s.c[j], acc, pc);
-        }
-    }
-    pg = warp_sum(pg);
-    pc = warp_sum(pc);
-    if (lane == 0) {
-        s.red[2 * warp] = pg;
-        s.red[2 * warp + 1] = pc;
+        if (valid && h == 0) s.v[j] = acc;
     }
     __syncthreads();
     // the previous step's entry is no longer read: fetch the next one into its buffer
     if (nxt_src) gwb_fetch_entry(nxt_dst, nxt_src, tl);
     const double rS = gw[kGwRS], g = gw[kGwG];
-    // 3. M-bar: c-bar and S-bar into row and column i of Pb; mu-bar = mb - e-bar e_i
+    // 3. M-bar: c-bar and S-bar into row and column i of Pb; mu-bar = mb - e-bar e_i.
+    //    The warp of the thread that takes row i forms mb.c and c.v.
+    double gb = 0.0, cv = 0.0;
+    if (warp == (i0 % T) / 32) {
+        for (int k = lane; k < n; k += 32) {
+            gb = fma(s.mb[k], s.c[k], gb);
+            cv = fma(s.c[k], s.v[k], cv);
+        }
+        gb = warp_sum(gb);
+        cv = warp_sum(cv);
+        gb = __shfl_sync(0xffffffffu, gb, 0);
+        cv = __shfl_sync(0xffffffffu, cv, 0);
+    }
     for (int j = tid; j < n; j += T) {
         const double cb = fma(s.mb[j], g, -2.0 * rS * s.v[j]);
-        if (j == i0) {     // the block sums mb.c, c.v, then S-bar and e-bar
-            double gb = 0.0, cv = 0.0;
-            for (int w = 0; w < T / 32; ++w) {
-                gb += s.red[2 * w];
-                cv += s.red[2 * w + 1];
-            }
+        if (j == i0) {     // S-bar and e-bar
             const double Sb = rS * rS * cv - gb * g * rS - 0.5 * rS + 0.5 * g * g;
             const double eb = gb * rS - g;
             s.acc[5 * q + 2] += Sb * 2.0 * s.par[4 * q + 3] * rk.s2;     // d/d EFAC_q
@@ -1038,8 +1046,12 @@ __device__ void gwb_adjoint_scaled(const GwbSmem& s, const GwbArgs& a, const Gwb
     // 4. Pb <- Fh^T M-bar Fh, block by block, with this thread's parts of the
     //    Hellings-Downs contractions of M-bar: sum_IJ G_IJ times its (rho_I,
     //    rho_J), (rho_I, a_J) + (a_I, rho_J) and (a_I, a_J) entries
+    // The off-diagonal blocks on the first 64 threads (all, in smaller
+    // blocks) and the diagonal ones on the threads that form c: only those
+    // carry GW shares
+    const int Tc = T >= 128 ? 64 : T;
     double t1 = 0.0, t2 = 0.0, t3 = 0.0;
-    for (int it = tid; it < s.nb - P; it += T) {           // blocks I < J
+    for (int it = tid < Tc ? tid : s.nb; it < s.nb - P; it += Tc) {   // blocks I < J
         const int I = s.pairs[2 * (P + it)], J = s.pairs[2 * (P + it) + 1];
         const double bI = cs[5 * I], bJ = cs[5 * J];
         double* R[3];
@@ -1066,7 +1078,7 @@ __device__ void gwb_adjoint_scaled(const GwbSmem& s, const GwbArgs& a, const Gwb
             R[u][2] = fma(al, X[u][0], X[u][2]);
         }
     }
-    for (int I = T - 1 - tid; I < P; I += T) {              // diagonal blocks, on the last threads
+    for (int I = gwb_role_first(32); I < P; I += T) {       // diagonal blocks
         const int rI = 3 * I;
         const double bI = cs[5 * I];
         double* R0 = prow(s.Pb, n, rI) + rI;
@@ -1129,11 +1141,13 @@ __device__ void gwb_adjoint_scaled(const GwbSmem& s, const GwbArgs& a, const Gwb
     }
     // GW: h_a^2 c / s'^k and the scale s'_a = s_a a_a, on this thread's parts
     // (the pulsars' parts of b_a s_a's adjoint follow in gwb_finish_pulsar)
-    const double* K = gw + kGwK;
-    const double sbat = sh.sg - fma(t2, K[0], t3 * K[1]);
-    sh.a3 = fma(t1, K[2], fma(t2, K[3], fma(t3, K[4], sh.a3)));
-    sh.a4 = fma(t1, K[5], fma(t2, K[6], fma(t3, K[7], fma(sbat, K[8], sh.a4))));
-    sh.sg = sbat * K[9];
+    if (tid < min(T, max(Tc, 32 + P))) {   // the threads that hold shares
+        const double* K = gw + kGwK;
+        const double sbat = sh.sg - fma(t2, K[0], t3 * K[1]);
+        sh.a3 = fma(t1, K[2], fma(t2, K[3], fma(t3, K[4], sh.a3)));
+        sh.a4 = fma(t1, K[5], fma(t2, K[6], fma(t3, K[7], fma(sbat, K[8], sh.a4))));
+        sh.sg = sbat * K[9];
+    }
 }
 
 // Gradient: one vector per block.  The likelihood kernel has written
@@ -1209,8 +1223,9 @@ __global__ void __launch_bounds__(kMaxT, kMinB) k_gwb_reverse(GwbArgs a) {
                                            pend ? Ebuf[(k + 1) & 1] : nullptr, pend ? a.rec[k + 1].dt : 0.0, tl, sh);
                         if (a.nbuf == 1 || k == k0) {   // no buffer keeps this entry for the next step
                             __syncthreads();
-                            if (a.rec[k].dt > 0.0 && tid >= T - P)
-                                gwb_finish_pulsar(s, Ebuf[k & 1], a.rec[k].dt, tid - (T - P), sh);
+                            if (a.rec[k].dt > 0.0)
+                                for (int I = gwb_role_first(32); I < P; I += T)
+                                    gwb_finish_pulsar(s, Ebuf[k & 1], a.rec[k].dt, I, sh);
                             if (a.nbuf == 1 && k > k0) {
                                 __syncthreads();
                                 gwb_fetch_entry(s.Pm, tp + (k - 1 - k0) * tl, tl);
@@ -1367,7 +1382,9 @@ argus_status argus_gwb_create(const argus_pulsar* psrs, int32_t n_pulsars, int32
         const int64_t g = order[j];
         const argus_pulsar& ps = psrs[psr_of[g]];
         const double t = ps.t[loc[g]];
-        rec[j] = GwbRec{t - t_prev, ps.r[loc[g]], ps.sigma[loc[g]] * ps.sigma[loc[g]], psr_of[g], 0};
+        const double dt = t - t_prev;
+        rec[j] = GwbRec{dt, ps.r[loc[g]], ps.sigma[loc[g]] * ps.sigma[loc[g]], 0.5 * dt * dt, dt * dt * dt / 3.0,
+                        dt * dt, psr_of[g], 0};
         t_prev = t;
     }
     std::vector<double> p0(size_t(3) * n_pulsars), eq2(n_pulsars);
