@@ -69,7 +69,7 @@ constexpr int kGwbFwdThreads = 32;    // likelihood kernel: one warp per block
 constexpr int kGwbRevMaxThreads = 256;   // reverse kernel: 64, 128 or 256 threads per block
 constexpr int kGwbGradMaxPulsars = 48;   // gradient: the adjoint and a tape entry in shared memory
 constexpr int kCo = 9;                   // per-pulsar coefficients (see GwbSmem::co)
-constexpr int kDotChunks = 4;            // lanes per dot product in the adjoint's parameter sums
+constexpr int kDotChunks = 2;            // lanes per dot product in the adjoint's parameter sums
 
 struct GwbRec {     // one TOA of the merged, time-ordered stream (56 bytes)
     double dt;      // time since the previous TOA of any pulsar (0 for the first)
@@ -150,10 +150,14 @@ __host__ __device__ inline int64_t gwb_rec_len(int P) {
     const int64_t n = 3 * int64_t(P);
     return n * (n + 1) / 2 + n + P + 1;
 }
-// doubles of one tape entry: a saved state, then co, gc and cs; even, so
-// that entries start on 16-byte boundaries
+// doubles of one tape entry: a saved state, then co, gc and cs, then the
+// step's predicted column c = M e_i (3P), 1/S and e/S; even, so that entries
+// start on 16-byte boundaries
+__host__ __device__ inline int64_t gwb_tape_c_off(int P) {
+    return gwb_rec_len(P) + kCo * int64_t(P) + 9 + 5 * (int64_t(P) + 1);
+}
 __host__ __device__ inline int64_t gwb_tape_len(int P) {
-    const int64_t d = gwb_rec_len(P) + kCo * int64_t(P) + 9 + 5 * (int64_t(P) + 1);
+    const int64_t d = gwb_tape_c_off(P) + 3 * int64_t(P) + 2;
     return (d + 1) & ~int64_t(1);
 }
 
@@ -844,30 +848,98 @@ __device__ __forceinline__ void gwb_fetch_entry(double* dst, const double* src, 
     asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
-// One forward step that also writes its tape entry to slot: the state before
-// the step (Ph, mh, scales) and, in the scaled frame, the step's coefficients
-// with their gamma-derivatives.  The unscaled frame's entry holds the state
-// only (its adjoint forms the coefficients itself).
-template <bool kScaled>
-__device__ void gwb_tape_step(const GwbSmem& s, const GwbArgs& a, const GwbRec& rk, double* slot) {
-    const int ne = s.ne, n = s.n, P = s.P;
-    for (int i = threadIdx.x; i < ne + n; i += blockDim.x) slot[i] = s.Pm[i];
+// The transition coefficients, with their gamma-derivatives, of steps
+// k0..k1-1 (scaled frame) straight into their tape entries' co and gc fields
+// (tape entry k - k0).  They depend on gamma and dt only, not on the state,
+// so the whole segment's are formed at once, one step per warp; within a
+// step lane p takes pulsar p (p = P: the GW process), so that the lanes
+// choose their series length together as in the likelihood pass.
+__device__ void gwb_segment_coefs(const GwbSmem& s, const GwbArgs& a, int64_t k0, int64_t k1, double* tp,
+                                  int64_t tl) {
+    const int P = s.P, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int64_t off = gwb_rec_len(P);        // co's offset in an entry; gc follows co
+    for (int64_t k = k0 + (threadIdx.x >> 5); k < k1; k += nw) {
+        const GwbRec rk = a.rec[k];
+        if (!(rk.dt > 0.0)) continue;
+        double* co = tp + (k - k0) * tl + off;
+        for (int p = lane; p <= P; p += 32) {
+            OuCoef oc;
+            ou_coef_warp<true>((p < P ? s.par[4 * p + 1] : s.gw[kGwGa]) * rk.dt, rk.dt, rk.h2, rk.h3, rk.dt2, oc);
+            double* o = co + kCo * p;
+            o[0] = oc.a; o[1] = oc.b; o[2] = oc.c00; o[3] = oc.c01; o[4] = oc.c11;
+            o[5] = oc.db; o[6] = oc.dc00; o[7] = oc.dc01; o[8] = oc.dc11;
+        }
+    }
+}
+
+// One forward step in the scaled frame that also writes its tape entry to
+// slot: the state before the step (Ph, mh, scales), the scale-dependent
+// coefficients cs (co and gc are already there, gwb_segment_coefs), the
+// predicted column c, 1/S and e/S.  Thread p forms cs_p and advances s_p
+// from co_p as gwb_coef_scaled does, and keeps a, b and Q / sigma^2 in
+// shared memory for a fold's unscaled predict.
+__device__ void gwb_tape_step_scaled(const GwbSmem& s, const GwbArgs& a, const GwbRec& rk, double* slot) {
+    const int ne = s.ne, n = s.n, P = s.P, T = blockDim.x;
     double* tsg = slot + ne + n;
-    if (rk.dt > 0.0) {
-        if (kScaled) {
-            gwb_coef_scaled<true, true>(s, rk, tsg);
-            __syncthreads();
-            const int ncoef = kCo * P + 9 + 5 * (P + 1);      // co, gc, cs
-            for (int i = threadIdx.x; i < ncoef; i += blockDim.x) tsg[P + 1 + i] = s.co[i];
-            gwb_predict_scaled_or_fold(s);
-        } else {
-            gwb_coef<false>(s, rk);
-            __syncthreads();
-            gwb_predict(s);
+    const double* tco = tsg + P + 1;
+    double* tcs = tsg + P + 1 + kCo * P + 9;
+    const bool pred = rk.dt > 0.0;
+    double oa = 0.0, ob = 0.0, q00 = 0.0, q01 = 0.0, q11 = 0.0;
+    if (pred && int(threadIdx.x) <= P) {        // loads first, under the state's stores
+        const double* o = tco + kCo * threadIdx.x;
+        oa = o[0]; ob = o[1]; q00 = o[2]; q01 = o[3]; q11 = o[4];
+    }
+    for (int i = threadIdx.x; i < ne + n; i += T) slot[i] = s.Pm[i];
+    if (pred) {
+        for (int p = threadIdx.x; p <= P; p += T) {
+            if (p != int(threadIdx.x)) {
+                const double* o = tco + kCo * p;
+                oa = o[0]; ob = o[1]; q00 = o[2]; q01 = o[3]; q11 = o[4];
+            }
+            const double sg = s.sg[p], sn = sg * oa;
+            tsg[p] = sg;
+            s.sg0[p] = sg;
+            s.sg[p] = sn;
+            if (!(sn >= kGwbTiny)) s.gw[kGwRn] = 1.0;
+            const double w = rcp_nr(sn), sc = p < P ? s.par[4 * p] : s.gw[kGwHa2];
+            double* h = s.cs + 5 * p;
+            h[0] = ob * sg;
+            h[1] = sc * q00;
+            h[2] = sc * q01 * w;
+            h[3] = sc * q11 * w * w;
+            h[4] = w;
+            double* th = tcs + 5 * p;
+            th[0] = h[0]; th[1] = h[1]; th[2] = h[2]; th[3] = h[3]; th[4] = h[4];
+            double* o = p < P ? s.co + kCo * p : s.gc;
+            o[0] = oa; o[1] = ob; o[2] = q00; o[3] = q01; o[4] = q11;
         }
         __syncthreads();
-    } else if (kScaled) {
-        for (int p = threadIdx.x; p <= P; p += blockDim.x) tsg[p] = s.sg[p];
+        gwb_predict_scaled_or_fold(s);
+        __syncthreads();
+    } else {
+        for (int p = threadIdx.x; p <= P; p += T) tsg[p] = s.sg[p];
+    }
+    gwb_innovate(s, a, rk);
+    __syncthreads();
+    double* tc = slot + gwb_tape_c_off(P);
+    for (int i = threadIdx.x; i < n; i += T) tc[i] = s.c[i];
+    if (threadIdx.x == 0) {
+        tc[n] = s.gw[kGwRS];
+        tc[n + 1] = s.gw[kGwG];
+    }
+    gwb_update(s);
+    __syncthreads();
+}
+
+// The same in the unscaled frame (the fallback): the entry holds the state
+// only; its adjoint forms the coefficients itself.
+__device__ void gwb_tape_step_unscaled(const GwbSmem& s, const GwbArgs& a, const GwbRec& rk, double* slot) {
+    for (int i = threadIdx.x; i < s.ne + s.n; i += blockDim.x) slot[i] = s.Pm[i];
+    if (rk.dt > 0.0) {
+        gwb_coef<false>(s, rk);
+        __syncthreads();
+        gwb_predict(s);
+        __syncthreads();
     }
     gwb_innovate(s, a, rk);
     __syncthreads();
@@ -920,9 +992,10 @@ __device__ __forceinline__ void gwb_finish_pulsar(const GwbSmem& s, const double
 // y_I and a_I of Ph.  nxt_src: a tape entry to fetch into nxt_dst meanwhile
 // (NULL: none).  Eprev: the entry of the step reversed before this one, whose
 // per-pulsar ends (gwb_finish_pulsar) run here, during the second phase, on
-// the threads that formed c (NULL: none pending).  Five phases, four barriers; on
-// return the fetch has landed, Pb is complete and this step's per-pulsar
-// ends are pending.
+// the threads of the role that starts at thread 32 (NULL: none pending).
+// The forward step left c, 1/S and e/S in the entry.  Four phases and
+// barriers; on return the fetch has landed, Pb is complete and this step's
+// per-pulsar ends are pending.
 __device__ void gwb_adjoint_scaled(const GwbSmem& s, const GwbArgs& a, const GwbRec& rk, const double* E,
                                    double* nxt_dst, const double* nxt_src, const double* Eprev, double dt_prev,
                                    int64_t tl, GwShare& sh) {
@@ -938,35 +1011,10 @@ __device__ void gwb_adjoint_scaled(const GwbSmem& s, const GwbArgs& a, const Gwb
     const double dt = rk.dt;
     const bool pred = dt > 0.0;
     double* gw = s.gw;
-    const double bq = pred ? cs[5 * q] : 0.0, al = pred ? ca[0] : 0.0;
-    // 1. c = Fh Ph Fh^T e_i + Qh e_i, the predicted column i = rho_q, three
-    //    entries per thread; the thread of pulsar q forms S, 1/S and e/S
-    for (int J = gwb_role_first(32); J < P; J += T) {    // from the second warp on
-        double uu[3];
-#pragma unroll
-        for (int v = 0; v < 3; ++v) {
-            const int j = 3 * J + v;
-            uu[v] = fma(bq, psym(Ph, n, j, i0 + 1), fma(al, psym(Ph, n, j, i0 + 2), psym(Ph, n, j, i0)));
-        }
-        double c0 = uu[0], c1 = uu[1], c2 = uu[2];
-        if (pred) {
-            const double g = gwb_G(s, J, q);
-            c0 = fma(g, ca[1], fma(cs[5 * J], uu[1], fma(al, uu[2], uu[0])));
-            c2 = fma(g, ca[2], uu[2]);
-            if (J == q) {
-                c0 += cs[5 * q + 1];
-                c1 += cs[5 * q + 2];
-            }
-        }
-        s.c[3 * J] = c0; s.c[3 * J + 1] = c1; s.c[3 * J + 2] = c2;
-        if (J == q) {
-            const double mu = fma(bq, mh[i0 + 1], fma(al, mh[i0 + 2], mh[i0]));
-            const double S = c0 + fma(s.par[4 * q + 2], rk.s2, a.equad2[q]);
-            const double rS = rcp_nr(S);
-            gw[kGwRS] = rS;
-            gw[kGwG] = (rk.r - mu) * rS;
-        }
-    }
+    const double al = pred ? ca[0] : 0.0;
+    // the predicted column c = M e_i (i = rho_q), 1/S and e/S, from the forward step
+    const double* c = E + gwb_tape_c_off(P);
+    const double rS = c[n], g = c[n + 1];
     __syncthreads();
     // the previous step's per-pulsar ends (its Fh-bar dot products were
     // written after its last barrier)
@@ -981,13 +1029,19 @@ __device__ void gwb_adjoint_scaled(const GwbSmem& s, const GwbArgs& a, const Gwb
         double a0 = 0.0, a1 = 0.0;
         if (valid) {
             const int klo = parts == 2 && h ? half : 0, khi = parts == 2 && !h ? half : n;
-            auto pb = [&](int k) { return k < j ? s.Pb[pk(n, k, j)] : s.Pb[pk(n, j, k)]; };
+            // row j of Pb along k (see the dot products below)
             int k = klo;
+            int ib = k < j ? pk(n, k, j) : pk(n, j, k);
+            auto step = [&](int kk, int& idx) { idx = kk + 1 < j ? idx + n - kk - 1 : kk + 1 == j ? pk(n, j, j) : idx + 1; };
             for (; k + 1 < khi; k += 2) {
-                a0 = fma(pb(k), s.c[k], a0);
-                a1 = fma(pb(k + 1), s.c[k + 1], a1);
+                const double b0 = s.Pb[ib];
+                step(k, ib);
+                const double b1 = s.Pb[ib];
+                step(k + 1, ib);
+                a0 = fma(b0, c[k], a0);
+                a1 = fma(b1, c[k + 1], a1);
             }
-            if (k < khi) a0 = fma(pb(k), s.c[k], a0);
+            if (k < khi) a0 = fma(s.Pb[ib], c[k], a0);
         }
         double acc = a0 + a1;
         if (parts == 2) acc += __shfl_xor_sync(0xffffffffu, acc, 1);
@@ -996,14 +1050,13 @@ __device__ void gwb_adjoint_scaled(const GwbSmem& s, const GwbArgs& a, const Gwb
     __syncthreads();
     // the previous step's entry is no longer read: fetch the next one into its buffer
     if (nxt_src) gwb_fetch_entry(nxt_dst, nxt_src, tl);
-    const double rS = gw[kGwRS], g = gw[kGwG];
     // 3. M-bar: c-bar and S-bar into row and column i of Pb; mu-bar = mb - e-bar e_i.
     //    The warp of the thread that takes row i forms mb.c and c.v.
     double gb = 0.0, cv = 0.0;
     if (warp == (i0 % T) / 32) {
         for (int k = lane; k < n; k += 32) {
-            gb = fma(s.mb[k], s.c[k], gb);
-            cv = fma(s.c[k], s.v[k], cv);
+            gb = fma(s.mb[k], c[k], gb);
+            cv = fma(c[k], s.v[k], cv);
         }
         gb = warp_sum(gb);
         cv = warp_sum(cv);
@@ -1125,18 +1178,27 @@ __device__ void gwb_adjoint_scaled(const GwbSmem& s, const GwbArgs& a, const Gwb
         const int I = dp >> 1, kind = dp & 1, rI = 3 * I;
         double d = 0.0, d1 = 0.0;
         if (valid) {
+            // row rho_I of Pb and column col of Ph along k: packed (k, x) for
+            // k < x steps by n - k - 1, then (x, k) by one
             const int col = rI + 1 + kind, k1 = min(n, (ch + 1) * clen);
             int k = ch * clen;
+            int ib = k < rI ? pk(n, k, rI) : pk(n, rI, k);
+            int ih = k < col ? pk(n, k, col) : pk(n, col, k);
+            auto step = [&](int kk, int x, int& idx) { idx = kk + 1 < x ? idx + n - kk - 1 : kk + 1 == x ? pk(n, x, x) : idx + 1; };
             for (; k + 1 < k1; k += 2) {
-                d = fma(psym(s.Pb, n, rI, k), psym(Ph, n, k, col), d);
-                d1 = fma(psym(s.Pb, n, rI, k + 1), psym(Ph, n, k + 1, col), d1);
+                const double b0 = s.Pb[ib], h0 = Ph[ih];
+                step(k, rI, ib); step(k, col, ih);
+                const double b1 = s.Pb[ib], h1 = Ph[ih];
+                step(k + 1, rI, ib); step(k + 1, col, ih);
+                d = fma(b0, h0, d);
+                d1 = fma(b1, h1, d1);
             }
-            if (k < k1) d = fma(psym(s.Pb, n, rI, k), psym(Ph, n, k, col), d);
+            if (k < k1) d = fma(s.Pb[ib], Ph[ih], d);
         }
         d += d1;
-        static_assert(kDotChunks == 4, "the lane sum below adds groups of four lanes");
-        d += __shfl_xor_sync(0xffffffffu, d, 1);
-        d += __shfl_xor_sync(0xffffffffu, d, 2);
+        static_assert(kDotChunks == 1 || kDotChunks == 2 || kDotChunks == 4, "lane groups within a warp");
+#pragma unroll
+        for (int o = 1; o < kDotChunks; o <<= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
         if (valid && ch == 0) s.dd[kind * P + I] = d;
     }
     // GW: h_a^2 c / s'^k and the scale s'_a = s_a a_a, on this thread's parts
@@ -1200,11 +1262,12 @@ __global__ void __launch_bounds__(kMaxT, kMinB) k_gwb_reverse(GwbArgs a) {
                 __syncthreads();
                 for (int64_t i = tid; i < rec_len; i += T) s.Pm[i] = ck[seg * rec_len + i];
                 if (tid == 0) s.gw[kGwRnAny] = 0.0;
+                if (scaled) gwb_segment_coefs(s, a, k0, k1, tp, tl);
                 __syncthreads();
                 // re-run the segment, writing its tape
                 for (int64_t k = k0; k < k1; ++k) {
-                    if (scaled) gwb_tape_step<true>(s, a, a.rec[k], tp + (k - k0) * tl);
-                    else gwb_tape_step<false>(s, a, a.rec[k], tp + (k - k0) * tl);
+                    if (scaled) gwb_tape_step_scaled(s, a, a.rec[k], tp + (k - k0) * tl);
+                    else gwb_tape_step_unscaled(s, a, a.rec[k], tp + (k - k0) * tl);
                 }
                 if (scaled && s.gw[kGwRnAny] != 0.0) {   // a fold the likelihood pass did not flag
                     refold = true;
