@@ -132,6 +132,7 @@ struct GwbSmem {
     double* sbt;    // [P]: this step's adjoint of s'_p from the intrinsic noise
     double* n1;     // [P]: this step's intrinsic-noise term of d/d gamma_p (before the factor sigma_p^2)
     double* dd;     // [2P]: this step's Fh-bar dot products, (rho_I, y_I) then (rho_I, a_I)
+    double* td;     // [3P]: the diagonal blocks' Hellings-Downs contraction terms
     double* red;    // [2 x warps]: block reductions
     double* u;      // [n]      (unscaled fallback)
     double* part;   // [P][chunks][6]: partial sums of the parameter terms (unscaled fallback)
@@ -172,7 +173,7 @@ __host__ __device__ inline size_t gwb_fwd_smem_bytes(int P) {
 // doubles of the reverse kernel's arrays after the entry buffers
 __host__ __device__ inline size_t gwb_rev_tail_doubles(int P, int threads) {
     const size_t n = 3 * size_t(P), ne = n * (n + 1) / 2;
-    return ne + 4 * n + (size_t(P) + 1) + 4 * size_t(P) + kGwSlots + 5 * size_t(P) + 5 * size_t(P) +
+    return ne + 4 * n + (size_t(P) + 1) + 4 * size_t(P) + kGwSlots + 5 * size_t(P) + 8 * size_t(P) +
            2 * size_t(threads / 32);
 }
 // the unscaled fallback's u and part: in the second entry buffer when there is one
@@ -233,6 +234,7 @@ __device__ GwbSmem gwb_carve_rev(double* base, int P, int nbuf, const double* G)
     s.sbt = q; q += P;
     s.n1 = q; q += P;
     s.dd = q; q += 2 * P;
+    s.td = q; q += 3 * P;
     s.red = q; q += 2 * (blockDim.x / 32);
     if (nbuf == 2) {
         s.u = s.E1;
@@ -1100,8 +1102,8 @@ __device__ void gwb_adjoint_scaled(const GwbSmem& s, const GwbArgs& a, const Gwb
     //    Hellings-Downs contractions of M-bar: sum_IJ G_IJ times its (rho_I,
     //    rho_J), (rho_I, a_J) + (a_I, rho_J) and (a_I, a_J) entries
     // The off-diagonal blocks on the first 64 threads (all, in smaller
-    // blocks) and the diagonal ones on the threads that form c: only those
-    // carry GW shares
+    // blocks): they, the first P threads and the per-pulsar ends' threads
+    // carry the GW shares
     const int Tc = T >= 128 ? 64 : T;
     double t1 = 0.0, t2 = 0.0, t3 = 0.0;
     for (int it = tid < Tc ? tid : s.nb; it < s.nb - P; it += Tc) {   // blocks I < J
@@ -1131,7 +1133,9 @@ __device__ void gwb_adjoint_scaled(const GwbSmem& s, const GwbArgs& a, const Gwb
             R[u][2] = fma(al, X[u][0], X[u][2]);
         }
     }
-    for (int I = gwb_role_first(32); I < P; I += T) {       // diagonal blocks
+    // diagonal blocks: on the third warp of larger blocks (the first two take
+    // the off-diagonal ones); their contraction terms go to thread I's share
+    for (int I = gwb_role_first(T >= 128 ? 64 : 32); I < P; I += T) {
         const int rI = 3 * I;
         const double bI = cs[5 * I];
         double* R0 = prow(s.Pb, n, rI) + rI;
@@ -1139,9 +1143,9 @@ __device__ void gwb_adjoint_scaled(const GwbSmem& s, const GwbArgs& a, const Gwb
         double* R2 = prow(s.Pb, n, rI + 2) + rI;
         const double x00 = R0[0], x01 = R0[1], x02 = R0[2], x11 = R1[1], x12 = R1[2], x22 = R2[2];
         const double g = gwb_G(s, I, I);
-        t1 = fma(g, x00, t1);
-        t2 = fma(g, x02 + x02, t2);
-        t3 = fma(g, x22, t3);
+        s.td[3 * I] = g * x00;
+        s.td[3 * I + 1] = g * (x02 + x02);
+        s.td[3 * I + 2] = g * x22;
         // intrinsic noise sigma^2 c00, sigma^2 c01 / s', sigma^2 c11 / s'^2 and the scale s'_I
         const double* cI = cs + 5 * I;
         const double* coI = co + kCo * I;
@@ -1200,6 +1204,11 @@ __device__ void gwb_adjoint_scaled(const GwbSmem& s, const GwbArgs& a, const Gwb
 #pragma unroll
         for (int o = 1; o < kDotChunks; o <<= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
         if (valid && ch == 0) s.dd[kind * P + I] = d;
+    }
+    for (int I = tid; I < P; I += T) {   // the diagonal blocks' contraction terms
+        t1 += s.td[3 * I];
+        t2 += s.td[3 * I + 1];
+        t3 += s.td[3 * I + 2];
     }
     // GW: h_a^2 c / s'^k and the scale s'_a = s_a a_a, on this thread's parts
     // (the pulsars' parts of b_a s_a's adjoint follow in gwb_finish_pulsar)
