@@ -59,14 +59,20 @@ argus_status argus_gwb_loglik(argus_gwb* gwb, const double* theta, int64_t B, do
                               void* stream);
 
 /* The joint log-likelihood and its gradient d loglik / d theta [B][D], by a
- * reverse-mode adjoint sweep through the joint filter: the state (upper
- * triangle of the covariance and the mean) is saved every ceil(sqrt(N))
- * TOAs, each segment is re-run saving the state before every TOA, and the
- * adjoint steps run backwards through it.  At most 48 pulsars (both the
- * covariance and its adjoint stay in shared memory; ARGUS_ERR_UNSUPPORTED
- * beyond).  Device scratch grows to 2 x max(ceil(sqrt N), segments) x
- * (3P(3P+1)/2 + 3P + P + 1) doubles per resident block.  Out-of-domain vectors get
- * loglik = -inf and a zero gradient. */
+ * reverse-mode adjoint sweep through the joint filter.  The likelihood pass
+ * (the same kernel as argus_gwb_loglik, so loglik is identical) saves the
+ * state (upper triangle of the covariance, mean and scale factors) every
+ * L = ceil(sqrt(N)) TOAs; the reverse pass then takes one thread block per
+ * vector and, segment by segment from the last, re-runs the segment writing
+ * a tape entry per TOA (the state before it, the step's transition
+ * coefficients with their gamma-derivatives and its predicted column) and
+ * runs the adjoint steps backwards through it.  At most 48 pulsars (the
+ * adjoint and two tape entries stay in shared memory; ARGUS_ERR_UNSUPPORTED
+ * beyond).  Device scratch: per vector of a launch the checkpoints,
+ * ceil(N / L) x (3P(3P+1)/2 + 4P + 1) doubles; per resident block one
+ * segment's tape, L x (3P(3P+1)/2 + 21P + 18) doubles at most; vectors are
+ * processed in launches of at most about 4 GB of checkpoints.  Out-of-domain
+ * vectors get loglik = -inf and a zero gradient. */
 argus_status argus_gwb_loglik_grad(argus_gwb* gwb, const double* theta, int64_t B, double* loglik,
                                    double* grad, void* stream);
 

@@ -853,24 +853,26 @@ __device__ __forceinline__ void gwb_fetch_entry(double* dst, const double* src, 
 // The transition coefficients, with their gamma-derivatives, of steps
 // k0..k1-1 (scaled frame) straight into their tape entries' co and gc fields
 // (tape entry k - k0).  They depend on gamma and dt only, not on the state,
-// so the whole segment's are formed at once, one step per warp; within a
-// step lane p takes pulsar p (p = P: the GW process), so that the lanes
-// choose their series length together as in the likelihood pass.
+// so the whole segment's are formed at once: one (step, pulsar) pair per
+// thread (pulsar P: the GW process), all lanes busy.  The lanes of a warp
+// share the longest series any of them needs (ou_coef_warp); a longer
+// series is never less accurate, so these may differ from the likelihood
+// pass's by rounding only.
 __device__ void gwb_segment_coefs(const GwbSmem& s, const GwbArgs& a, int64_t k0, int64_t k1, double* tp,
                                   int64_t tl) {
-    const int P = s.P, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int P = s.P, np = P + 1;
     const int64_t off = gwb_rec_len(P);        // co's offset in an entry; gc follows co
-    for (int64_t k = k0 + (threadIdx.x >> 5); k < k1; k += nw) {
-        const GwbRec rk = a.rec[k];
+    const int64_t items = (k1 - k0) * np;
+    for (int64_t it = threadIdx.x; it < items; it += blockDim.x) {
+        const int64_t j = it / np;
+        const int p = int(it - j * np);
+        const GwbRec& rk = a.rec[k0 + j];
         if (!(rk.dt > 0.0)) continue;
-        double* co = tp + (k - k0) * tl + off;
-        for (int p = lane; p <= P; p += 32) {
-            OuCoef oc;
-            ou_coef_warp<true>((p < P ? s.par[4 * p + 1] : s.gw[kGwGa]) * rk.dt, rk.dt, rk.h2, rk.h3, rk.dt2, oc);
-            double* o = co + kCo * p;
-            o[0] = oc.a; o[1] = oc.b; o[2] = oc.c00; o[3] = oc.c01; o[4] = oc.c11;
-            o[5] = oc.db; o[6] = oc.dc00; o[7] = oc.dc01; o[8] = oc.dc11;
-        }
+        OuCoef oc;
+        ou_coef_warp<true>((p < P ? s.par[4 * p + 1] : s.gw[kGwGa]) * rk.dt, rk.dt, rk.h2, rk.h3, rk.dt2, oc);
+        double* o = tp + j * tl + off + kCo * p;
+        o[0] = oc.a; o[1] = oc.b; o[2] = oc.c00; o[3] = oc.c01; o[4] = oc.c11;
+        o[5] = oc.db; o[6] = oc.dc00; o[7] = oc.dc01; o[8] = oc.dc11;
     }
 }
 
