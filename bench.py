@@ -95,10 +95,11 @@ def parse_args():
     ap.add_argument("--autotune", choices=["cache", "off", "force"], default="cache",
                     help="cache: use the tuned-plan cache, tuning on a miss; force: retune")
     ap.add_argument("--tune-batch", type=int, default=4096)
-    ap.add_argument("--mode", choices=["filter", "da-hmc", "surrogate", "latency"], default="filter",
+    ap.add_argument("--mode", choices=["filter", "da-hmc", "surrogate", "latency", "gwb"], default="filter",
                     help="filter: loglik+grad evals/s (default); da-hmc: surrogate delayed acceptance; "
                          "surrogate: the surrogate's evaluation alone, fused vs per-layer; "
-                         "latency: the single-vector latency leg alone (sequential vs time-parallel)")
+                         "latency: the single-vector latency leg alone (sequential vs time-parallel); "
+                         "gwb: the Hellings-Downs GW-background leg alone (joint filter, --gwb-batch vectors)")
     ap.add_argument("--latency-reps", type=int, default=200,
                     help="timed calls per path in the latency leg")
     ap.add_argument("--plan", default="",
@@ -1079,6 +1080,25 @@ def run_latency(args):
     return 0
 
 
+def run_gwb(args):
+    """The GW-background leg alone: the joint filter's likelihood and its
+    gradient for --gwb-batch parameter vectors on the 20-pulsar array."""
+    import torch
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    out = gwb_leg(args, torch.device("cuda", local), local)
+    g = out["gradient"]
+    line = {"metric": "joint-filter loglik+grad evals/s (Hellings-Downs GW background)",
+            "value": g["value"], "unit": "evals/s", "n_gpus": 1, "higher_is_better": True,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": out["workload"], "batch": out["batch"],
+                       "l2": "flushed before each timed call (256 MiB write, untimed)"},
+            "gwb_hd": out}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
@@ -1089,6 +1109,8 @@ def main():
         return run_surrogate(args)
     if args.mode == "latency":
         return run_latency(args)
+    if args.mode == "gwb":
+        return run_gwb(args)
     return run_ours(args)
 
 

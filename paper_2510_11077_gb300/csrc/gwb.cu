@@ -1055,17 +1055,19 @@ __device__ void gwb_adjoint_scaled(const GwbSmem& s, const GwbArgs& a, const Gwb
     // the previous step's entry is no longer read: fetch the next one into its buffer
     if (nxt_src) gwb_fetch_entry(nxt_dst, nxt_src, tl);
     // 3. M-bar: c-bar and S-bar into row and column i of Pb; mu-bar = mb - e-bar e_i.
-    //    The warp of the thread that takes row i forms mb.c and c.v.
+    //    The warp of the thread that takes row i forms mb.c (lanes 0-15) and
+    //    c.v (lanes 16-31), each half summing its 16 lanes in a fixed tree.
     double gb = 0.0, cv = 0.0;
     if (warp == (i0 % T) / 32) {
-        for (int k = lane; k < n; k += 32) {
-            gb = fma(s.mb[k], c[k], gb);
-            cv = fma(c[k], s.v[k], cv);
-        }
-        gb = warp_sum(gb);
-        cv = warp_sum(cv);
-        gb = __shfl_sync(0xffffffffu, gb, 0);
-        cv = __shfl_sync(0xffffffffu, cv, 0);
+        const bool hv = lane >= 16;
+        const double* x = hv ? c : s.mb;
+        const double* y = hv ? s.v : c;
+        double d = 0.0;
+        for (int k = lane & 15; k < n; k += 16) d = fma(x[k], y[k], d);
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+        gb = __shfl_sync(0xffffffffu, d, 0);
+        cv = __shfl_sync(0xffffffffu, d, 16);
     }
     for (int j = tid; j < n; j += T) {
         const double cb = fma(s.mb[j], g, -2.0 * rS * s.v[j]);
@@ -1086,19 +1088,26 @@ __device__ void gwb_adjoint_scaled(const GwbSmem& s, const GwbArgs& a, const Gwb
         return;
     }
     __syncthreads();
-    if (tid == T - 1) {   // the GW share update's products for this step
-        const double wa = ca[4], ha2 = gw[kGwHa2], sga = sg[P];
-        double* K = gw + kGwK;
-        K[0] = wa * ca[2];
-        K[1] = 2.0 * wa * ca[3];
-        K[2] = gc[2];
-        K[3] = wa * gc[3];
-        K[4] = wa * wa * gc[4];
-        K[5] = ha2 * gc[6];
-        K[6] = ha2 * wa * gc[7];
-        K[7] = ha2 * wa * wa * gc[8];
-        K[8] = -sga * dt * gc[0];
-        K[9] = gc[0];
+    if (tid >= T - 10) {   // the GW share update's products for this step, one per lane:
+        // K_i = ((f0 f1) f2) f3, the factors picked per lane, the products on all ten at once
+        //   K0 = wa ca2, K1 = 2 wa ca3, K2 = gc2, K3 = wa gc3, K4 = wa wa gc4, K5 = ha2 gc6,
+        //   K6 = ha2 wa gc7, K7 = ha2 wa wa gc8, K8 = sga (-dt) gc0, K9 = gc0
+        const int i = tid - (T - 10);
+        const double wa = ca[4];
+        double f0 = wa, f1 = 1.0, f2 = 1.0, f3 = 1.0;
+        switch (i) {
+            case 0: f1 = ca[2]; break;
+            case 1: f0 = 2.0; f1 = wa; f2 = ca[3]; break;
+            case 2: f0 = gc[2]; break;
+            case 3: f1 = gc[3]; break;
+            case 4: f1 = wa; f2 = gc[4]; break;
+            case 5: f0 = gw[kGwHa2]; f1 = gc[6]; break;
+            case 6: f0 = gw[kGwHa2]; f1 = wa; f2 = gc[7]; break;
+            case 7: f0 = gw[kGwHa2]; f1 = wa; f2 = wa; f3 = gc[8]; break;
+            case 8: f0 = sg[P]; f1 = -dt; f2 = gc[0]; break;
+            default: f0 = gc[0]; break;
+        }
+        gw[kGwK + i] = ((f0 * f1) * f2) * f3;
     }
     // 4. Pb <- Fh^T M-bar Fh, block by block, with this thread's parts of the
     //    Hellings-Downs contractions of M-bar: sum_IJ G_IJ times its (rho_I,
