@@ -1047,6 +1047,34 @@ def run_surrogate(args):
                 out[f"{rows} rows, {name}, {tag}"] = {"us": us, "tflops": flop / (us * 1e-6) / 1e12}
             net.set_cluster(0)
         net.close()
+    # one training step (forward with saved activations, loss, back-propagation,
+    # weight gradients, Adam) on 4096-row minibatches of a resident set
+    net = surrogate.Surrogate(device=local, max_rows=4096, seed=3)
+    rng = np.random.default_rng(2)
+    net.set_normalizers(np.zeros(47), np.ones(47), 0.0, 1.0)
+    n_set = 65536
+    xs = torch.from_numpy(rng.standard_normal((n_set, 47)).astype(np.float32)).to(dev)
+    ls = torch.from_numpy(rng.standard_normal(n_set).astype(np.float32)).to(dev)
+    gs = torch.from_numpy(rng.standard_normal((n_set, 47)).astype(np.float32)).to(dev)
+    loss = torch.empty(1, dtype=torch.float32, device=dev)
+    n_steps = n_set // 4096
+    for i in range(5):
+        sl = slice((i % n_steps) * 4096, (i % n_steps + 1) * 4096)
+        net.train_step(xs[sl], ls[sl], gs[sl], 1e-4, loss_out=loss)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for i in range(4 * n_steps):
+        sl = slice((i % n_steps) * 4096, (i % n_steps + 1) * 4096)
+        net.train_step(xs[sl], ls[sl], gs[sl], 1e-4, loss_out=loss)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    net.check()
+    net.close()
+    us = e0.elapsed_time(e1) / (4 * n_steps) * 1e3
+    # forward, the input-side gradients of layers 4..1 and every weight gradient
+    train_flop = 4096 * (fwd_flop + bwd_flop + fwd_flop)
+    out["4096 rows, training step"] = {"us": us, "tflops": train_flop / (us * 1e-6) / 1e12}
     key = "4096 rows, value backprop, fused"
     line = {"metric": "surrogate evaluation latency (value + back-propagated gradient, 4096 rows)",
             "value": out[key]["us"], "unit": "us", "n_gpus": 1, "higher_is_better": False,

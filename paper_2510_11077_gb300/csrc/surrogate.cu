@@ -142,62 +142,102 @@ __global__ void __launch_bounds__(kSumThreads) k_loss_sum(const float* __restric
     if (threadIdx.x == 0) *out = part[0] / float(n);
 }
 
-// Column sums (bias gradients) in a fixed order: out[c] = sum_r m[r][c].  A
-// block takes 32 columns with 32 row phases (thread (c, p) sums rows p,
-// p + 32, ...); the 32 phase sums are then added in phase order.  Grid cols / 32.
+// Column sums (bias gradients) in two fixed-order levels.  k_colsum_part:
+// block (x, ch) takes 32 columns of row chunk ch (rows / kColChunks rows);
+// thread (c, p) sums that chunk's rows p, p + 32, ... of column c and the 32
+// phase sums are added in phase order into part[ch][c].  The optimizer adds
+// the kColChunks chunk sums in chunk order.  Grid (cols / 32, kColChunks).
 __device__ __forceinline__ float as_float(float v) { return v; }
 __device__ __forceinline__ float as_float(__nv_bfloat16 v) { return __bfloat162float(v); }
 
+constexpr int kColChunks = 16;   // rows is a multiple of 128, so every chunk has >= 8 rows
+
 template <class T>
-__global__ void __launch_bounds__(1024) k_colsum(const T* __restrict__ m, int rows, int cols,
-                                                 float* __restrict__ out) {
-    __shared__ float part[32][33];
+__global__ void __launch_bounds__(1024) k_colsum_part(const T* __restrict__ m, int rows, int cols,
+                                                      float* __restrict__ part) {
+    __shared__ float ph_sum[32][33];
     const int tx = threadIdx.x & 31, ph = threadIdx.x >> 5;
     const int c = blockIdx.x * 32 + tx;
+    const int rc = rows / kColChunks, r0 = blockIdx.y * rc;
     float s = 0.0f;
     if (c < cols)
-        for (int r = ph; r < rows; r += 32) s += as_float(m[int64_t(r) * cols + c]);
-    part[ph][tx] = s;
+        for (int r = ph; r < rc; r += 32) s += as_float(m[int64_t(r0 + r) * cols + c]);
+    ph_sum[ph][tx] = s;
     __syncthreads();
     if (ph == 0 && c < cols) {
         float t = 0.0f;
-        for (int k = 0; k < 32; ++k) t += part[k][tx];
-        out[c] = t;
+        for (int k = 0; k < 32; ++k) t += ph_sum[k][tx];
+        part[int64_t(blockIdx.y) * cols + c] = t;
     }
 }
 
-// Adam on one weight matrix W [N][K] (FP32 master) with its gradient as the
-// fixed-order sum of split-K partials; transposed partials for the last layer.
-__global__ void k_adam_w(float* __restrict__ W, float* __restrict__ m, float* __restrict__ v,
-                         const float* __restrict__ part, int chunks, int64_t chunk_stride, int N,
-                         int K, int transposed, float lr, float c1, float c2,
-                         __nv_bfloat16* __restrict__ w16, __nv_bfloat16* __restrict__ w16t) {
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= N * K) return;
-    const int o = idx / K, i = idx % K;
-    const int pidx = transposed ? (i * N + o) : idx;
-    float g = 0.0f;
-    for (int c = 0; c < chunks; ++c) g += part[int64_t(c) * chunk_stride + pidx];
-    const float mm = 0.9f * m[idx] + 0.1f * g;
-    const float vv = 0.999f * v[idx] + 0.001f * g * g;
-    m[idx] = mm;
-    v[idx] = vv;
-    const float w = W[idx] - lr * (mm / c1) / (sqrtf(vv / c2) + 1e-8f);
-    W[idx] = w;
-    const __nv_bfloat16 b = __float2bfloat16_rn(w);
-    w16[idx] = b;
-    w16t[int64_t(i) * N + o] = b;
+// Adam on every weight and bias of the network in one launch, one thread per
+// parameter: weights first (layer by layer, row-major [N][K]), then biases.
+// A weight's gradient is the fixed-order sum of its split-K partials
+// (transposed partials for the last layer); a bias's, the fixed-order sum of
+// its column's chunk sums (k_colsum_part), also kept in gb for inspection.
+// The BF16 copies (and transposes) of the updated weights are written too.
+struct AdamArgs {
+    float* W[kMlpLayers];
+    float* mW[kMlpLayers];
+    float* vW[kMlpLayers];
+    const float* part[kMlpLayers];
+    __nv_bfloat16* w16[kMlpLayers];
+    __nv_bfloat16* w16t[kMlpLayers];
+    float* b[kMlpLayers];
+    float* mb[kMlpLayers];
+    float* vb[kMlpLayers];
+    const float* bpart[kMlpLayers];
+    float* gb[kMlpLayers];
+    int N[kMlpLayers], K[kMlpLayers];   // layer l's outputs and inputs
+    int64_t w_end[kMlpLayers];   // end of layer l's weights in the flat index
+    int64_t b_end[kMlpLayers];   // end of layer l's biases (after all weights)
+    int chunks;                  // split-K chunks of the weight gradients
+    float lr, c1, c2;
+};
+
+__device__ __forceinline__ float adam_update(float& m, float& v, float g, float p, float lr, float c1,
+                                             float c2) {
+    const float mm = 0.9f * m + 0.1f * g;
+    const float vv = 0.999f * v + 0.001f * g * g;
+    m = mm;
+    v = vv;
+    return p - lr * (mm / c1) / (sqrtf(vv / c2) + 1e-8f);
 }
 
-__global__ void k_adam_b(float* __restrict__ b, float* __restrict__ m, float* __restrict__ v,
-                         const float* __restrict__ g, int N, float lr, float c1, float c2) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    const float mm = 0.9f * m[i] + 0.1f * g[i];
-    const float vv = 0.999f * v[i] + 0.001f * g[i] * g[i];
-    m[i] = mm;
-    v[i] = vv;
-    b[i] = b[i] - lr * (mm / c1) / (sqrtf(vv / c2) + 1e-8f);
+__global__ void k_adam_all(AdamArgs a) {
+    const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (idx >= a.b_end[kMlpLayers - 1]) return;
+    if (idx < a.w_end[kMlpLayers - 1]) {
+        int l = 0;
+        while (idx >= a.w_end[l]) ++l;
+        const int N = a.N[l], K = a.K[l];
+        const int64_t j = idx - (l ? a.w_end[l - 1] : 0), stride = int64_t(N) * K;
+        const int o = int(j / K), i = int(j % K);
+        const int64_t pidx = (l == kMlpLayers - 1) ? int64_t(i) * N + o : j;
+        float g = 0.0f;
+        for (int c = 0; c < a.chunks; ++c) g += a.part[l][int64_t(c) * stride + pidx];
+        float m = a.mW[l][j], v = a.vW[l][j];
+        const float w = adam_update(m, v, g, a.W[l][j], a.lr, a.c1, a.c2);
+        a.mW[l][j] = m;
+        a.vW[l][j] = v;
+        a.W[l][j] = w;
+        const __nv_bfloat16 b16 = __float2bfloat16_rn(w);
+        a.w16[l][j] = b16;
+        a.w16t[l][int64_t(i) * N + o] = b16;
+    } else {
+        int l = 0;
+        while (idx >= a.b_end[l]) ++l;
+        const int N = a.N[l];
+        const int i = int(idx - (l ? a.b_end[l - 1] : a.w_end[kMlpLayers - 1]));
+        float g = 0.0f;
+        for (int ch = 0; ch < kColChunks; ++ch) g += a.bpart[l][ch * N + i];
+        a.gb[l][i] = g;
+        float m = a.mb[l][i], v = a.vb[l][i];
+        a.b[l][i] = adam_update(m, v, g, a.b[l][i], a.lr, a.c1, a.c2);
+        a.mb[l][i] = m;
+        a.vb[l][i] = v;
+    }
 }
 
 // BF16 copies (and transposes) of the FP32 master weights.
@@ -293,6 +333,7 @@ struct argus_surrogate {
     float* mb[kMlpLayers] = {};
     float* vb[kMlpLayers] = {};
     float* gb[kMlpLayers] = {};
+    float* bpart[kMlpLayers] = {};   // [kColChunks][out]: the bias gradients' row-chunk sums
     float* part[kMlpLayers] = {};
     __nv_bfloat16* W16[kMlpLayers] = {};
     __nv_bfloat16* W16T[kMlpLayers] = {};
@@ -338,6 +379,7 @@ void free_all(argus_surrogate* s) {
     for (int l = 0; l < kMlpLayers; ++l) {
         cudaFree(s->W[l]); cudaFree(s->b[l]); cudaFree(s->mW[l]); cudaFree(s->vW[l]);
         cudaFree(s->mb[l]); cudaFree(s->vb[l]); cudaFree(s->gb[l]); cudaFree(s->part[l]);
+        cudaFree(s->bpart[l]);
         cudaFree(s->W16[l]); cudaFree(s->W16T[l]); cudaFree(s->H[l]); cudaFree(s->HT[l]);
         cudaFree(s->Z[l]);
     }
@@ -538,6 +580,7 @@ argus_status argus_surrogate_create_ex(int32_t device, int32_t max_rows, uint64_
         A(dalloc(&s->mW[l], nw)); A(dalloc(&s->vW[l], nw));
         A(dalloc(&s->mb[l], kOut[l])); A(dalloc(&s->vb[l], kOut[l])); A(dalloc(&s->gb[l], kOut[l]));
         A(dalloc(&s->part[l], nw * max_chunks));
+        A(dalloc(&s->bpart[l], size_t(kColChunks) * kOut[l]));
         A(dalloc(&s->W16[l], nw)); A(dalloc(&s->W16T[l], nw));
         A(dalloc(&s->H[l], R * kIn[l])); A(dalloc(&s->HT[l], R * kIn[l]));
         A(dalloc(&s->Z[l], R * kMlpHidden));
@@ -835,7 +878,8 @@ argus_status train_step_impl(argus_surrogate* s, const float* theta, const float
         cudaError_t ce = launch_gemm_tc(&s->tmHT[4], &s->tmdYT, kMlpHidden, kMlpOutPad, ck, 64, chunks,
                                         kEpiF32, g, s->err, st);
         if (ce != cudaSuccess) return scuda(ce, "dW4 GEMM");
-        k_colsum<__nv_bfloat16><<<kMlpOutPad / 32, 1024, 0, st>>>(s->dY, rows, kMlpOutPad, s->gb[4]);
+        k_colsum_part<__nv_bfloat16><<<dim3(kMlpOutPad / 32, kColChunks), 1024, 0, st>>>(s->dY, rows, kMlpOutPad,
+                                                                                      s->bpart[4]);
         GemmEpiArgs d = epi_none();
         d.zin = s->Z[4];
         d.ldz = kMlpHidden;
@@ -861,7 +905,8 @@ argus_status train_step_impl(argus_surrogate* s, const float* theta, const float
         cudaError_t ce = launch_gemm_tc(&s->tmdZT[cur], &s->tmHT[l], kMlpHidden, K, ck, K == 64 ? 64 : 128,
                                         chunks, kEpiF32, g, s->err, st);
         if (ce != cudaSuccess) return scuda(ce, "dW GEMM");
-        k_colsum<float><<<kMlpHidden / 32, 1024, 0, st>>>(s->dZ32[cur], rows, kMlpHidden, s->gb[l]);
+        k_colsum_part<float><<<dim3(kMlpHidden / 32, kColChunks), 1024, 0, st>>>(s->dZ32[cur], rows, kMlpHidden,
+                                                                              s->bpart[l]);
         if (l > 0) {
             GemmEpiArgs d = epi_none();
             d.zin = s->Z[l];
@@ -885,14 +930,24 @@ argus_status train_step_impl(argus_surrogate* s, const float* theta, const float
     s->step += 1;
     const float c1 = float(1.0 - std::pow(0.9, s->step));
     const float c2 = float(1.0 - std::pow(0.999, s->step));
+    AdamArgs aa{};
+    int64_t off = 0;
     for (int l = 0; l < kMlpLayers; ++l) {
-        const int N = kOut[l], K = kIn[l];
-        const int64_t stride = int64_t(N) * K;
-        k_adam_w<<<(N * K + 255) / 256, 256, 0, st>>>(s->W[l], s->mW[l], s->vW[l], s->part[l], chunks,
-                                                      stride, N, K, l == kMlpLayers - 1 ? 1 : 0, lr, c1,
-                                                      c2, s->W16[l], s->W16T[l]);
-        k_adam_b<<<(N + 255) / 256, 256, 0, st>>>(s->b[l], s->mb[l], s->vb[l], s->gb[l], N, lr, c1, c2);
+        aa.W[l] = s->W[l]; aa.mW[l] = s->mW[l]; aa.vW[l] = s->vW[l]; aa.part[l] = s->part[l];
+        aa.w16[l] = s->W16[l]; aa.w16t[l] = s->W16T[l];
+        aa.b[l] = s->b[l]; aa.mb[l] = s->mb[l]; aa.vb[l] = s->vb[l]; aa.bpart[l] = s->bpart[l];
+        aa.gb[l] = s->gb[l];
+        aa.N[l] = kOut[l];
+        aa.K[l] = kIn[l];
+        off += int64_t(kOut[l]) * kIn[l];
+        aa.w_end[l] = off;
     }
+    for (int l = 0; l < kMlpLayers; ++l) {
+        off += kOut[l];
+        aa.b_end[l] = off;
+    }
+    aa.chunks = chunks; aa.lr = lr; aa.c1 = c1; aa.c2 = c2;
+    k_adam_all<<<unsigned((off + 255) / 256), 256, 0, st>>>(aa);
     SCK(cudaGetLastError());
     return ARGUS_OK;
 }
