@@ -356,6 +356,8 @@ struct argus_surrogate {
     int last_chunks = 0;   // split-K chunks of the last training step
     // tensor maps
     CUtensorMap tmW[kMlpLayers], tmWT[kMlpLayers], tmH[kMlpLayers], tmHT[kMlpLayers];
+    // the same with 64-row boxes: B operands of the training step's 64-column tiles
+    CUtensorMap tmW64[kMlpLayers], tmWT64[kMlpLayers], tmHT64[kMlpLayers];
     CUtensorMap tmWT0_b64;   // W_0^T [64][256] with a 64-row box (B operand of dX0 = dZ1 W0)
     int grad_mode = 0;       // 0: gradient head; 1: back-propagated value head
     CUtensorMap tmdY, tmdYT, tmdZ16[2], tmdZT[2];
@@ -410,6 +412,9 @@ argus_status build_maps(argus_surrogate* s) {
         ok &= make_tmap_bf16(&s->tmWT[l], s->W16T[l], kIn[l], kOut[l], 128);
         ok &= make_tmap_bf16(&s->tmH[l], s->H[l], R, kIn[l], 128);
         ok &= make_tmap_bf16(&s->tmHT[l], s->HT[l], kIn[l], R, kIn[l] == 64 ? 64 : 128);
+        ok &= make_tmap_bf16(&s->tmW64[l], s->W16[l], kOut[l], kIn[l], 64);
+        ok &= make_tmap_bf16(&s->tmWT64[l], s->W16T[l], kIn[l], kOut[l], 64);
+        ok &= make_tmap_bf16(&s->tmHT64[l], s->HT[l], kIn[l], R, 64);
     }
     ok &= make_tmap_bf16(&s->tmWT0_b64, s->W16T[0], kIn[0], kOut[0], 64);
     for (int c = 0; c < 3; ++c) {   // cluster of 1 << c CTAs: each loads 1 / (1 << c) of the rows
@@ -467,8 +472,7 @@ argus_status forward(argus_surrogate* s, int rows, bool train, cudaStream_t st) 
         GemmEpiArgs e = epi_none();
         e.bias = s->b[l];
         const int N = kOut[l], K = kIn[l];
-        const int bn = N == 64 ? 64 : 128;
-        cudaError_t ce;
+        cudaError_t ce;   // 64-column tiles: 4 x more CTAs than 128-row slabs, each a quarter of the epilogue
         if (l < kMlpLayers - 1) {
             e.out_f32 = train ? s->Z[l + 1] : nullptr;
             e.ldo = N;
@@ -476,11 +480,11 @@ argus_status forward(argus_surrogate* s, int rows, bool train, cudaStream_t st) 
             e.ldb = N;
             e.out_bf16_t = train ? s->HT[l + 1] : nullptr;
             e.ldt = s->rows;
-            ce = launch_gemm_tc(&s->tmH[l], &s->tmW[l], rows, N, K, bn, 1, kEpiGelu, e, s->err, st);
+            ce = launch_gemm_tc(&s->tmH[l], &s->tmW64[l], rows, N, K, 64, 1, kEpiGelu, e, s->err, st);
         } else {
             e.out_f32 = s->Y;
             e.ldo = N;
-            ce = launch_gemm_tc(&s->tmH[l], &s->tmW[l], rows, N, K, bn, 1, kEpiF32, e, s->err, st);
+            ce = launch_gemm_tc(&s->tmH[l], &s->tmW64[l], rows, N, K, 64, 1, kEpiF32, e, s->err, st);
         }
         if (ce != cudaSuccess) return scuda(ce, "forward GEMM");
     }
@@ -497,7 +501,7 @@ argus_status value_input_grad(argus_surrogate* s, int64_t n, int rows, cudaStrea
     d.ldz = kMlpHidden;
     d.out_bf16 = s->dZ16[0];
     d.ldb = kMlpHidden;
-    cudaError_t ce = launch_gemm_tc(&s->tmdY, &s->tmWT[4], rows, kMlpHidden, kMlpOutPad, 128, 1,
+    cudaError_t ce = launch_gemm_tc(&s->tmdY, &s->tmWT64[4], rows, kMlpHidden, kMlpOutPad, 64, 1,
                                     kEpiGeluBwd, d, s->err, st);
     if (ce != cudaSuccess) return scuda(ce, "value backprop GEMM");
     int cur = 0;
@@ -507,7 +511,7 @@ argus_status value_input_grad(argus_surrogate* s, int64_t n, int rows, cudaStrea
         g.ldz = kMlpHidden;
         g.out_bf16 = s->dZ16[cur ^ 1];
         g.ldb = kMlpHidden;
-        ce = launch_gemm_tc(&s->tmdZ16[cur], &s->tmWT[l], rows, kMlpHidden, kMlpHidden, 128, 1,
+        ce = launch_gemm_tc(&s->tmdZ16[cur], &s->tmWT64[l], rows, kMlpHidden, kMlpHidden, 64, 1,
                             kEpiGeluBwd, g, s->err, st);
         if (ce != cudaSuccess) return scuda(ce, "value backprop GEMM");
         cur ^= 1;
@@ -889,7 +893,7 @@ argus_status train_step_impl(argus_surrogate* s, const float* theta, const float
         d.ldb = kMlpHidden;
         d.out_bf16_t = s->dZT[0];
         d.ldt = s->rows;
-        ce = launch_gemm_tc(&s->tmdY, &s->tmWT[4], rows, kMlpHidden, kMlpOutPad, 128, 1, kEpiGeluBwd, d,
+        ce = launch_gemm_tc(&s->tmdY, &s->tmWT64[4], rows, kMlpHidden, kMlpOutPad, 64, 1, kEpiGeluBwd, d,
                             s->err, st);
         if (ce != cudaSuccess) return scuda(ce, "dH4 GEMM");
         if ((e = keep_dz(s, 4, 0, rows, st))) return e;
@@ -902,7 +906,7 @@ argus_status train_step_impl(argus_surrogate* s, const float* theta, const float
         g.out_f32 = s->part[l];
         g.ldo = K;
         g.chunk_stride = int64_t(kMlpHidden) * K;
-        cudaError_t ce = launch_gemm_tc(&s->tmdZT[cur], &s->tmHT[l], kMlpHidden, K, ck, K == 64 ? 64 : 128,
+        cudaError_t ce = launch_gemm_tc(&s->tmdZT[cur], &s->tmHT64[l], kMlpHidden, K, ck, 64,
                                         chunks, kEpiF32, g, s->err, st);
         if (ce != cudaSuccess) return scuda(ce, "dW GEMM");
         k_colsum_part<float><<<dim3(kMlpHidden / 32, kColChunks), 1024, 0, st>>>(s->dZ32[cur], rows, kMlpHidden,
@@ -917,7 +921,7 @@ argus_status train_step_impl(argus_surrogate* s, const float* theta, const float
             d.ldb = kMlpHidden;
             d.out_bf16_t = s->dZT[cur ^ 1];
             d.ldt = s->rows;
-            ce = launch_gemm_tc(&s->tmdZ16[cur], &s->tmWT[l], rows, kMlpHidden, kMlpHidden, 128, 1,
+            ce = launch_gemm_tc(&s->tmdZ16[cur], &s->tmWT64[l], rows, kMlpHidden, kMlpHidden, 64, 1,
                                 kEpiGeluBwd, d, s->err, st);
             if (ce != cudaSuccess) return scuda(ce, "dH GEMM");
             cur ^= 1;
