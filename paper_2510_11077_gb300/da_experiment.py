@@ -194,13 +194,15 @@ def train(net, x, ll, g, centre, ll_ref, epochs, batch, lr, gen, log=None):
         if not bool(torch.isfinite(a).all()):
             raise FloatingPointError(f"non-finite training {name}")
     k = 0
+    loss_buf = torch.empty(1, dtype=torch.float32, device=x.device)
     for ep in range(epochs):
         perm = torch.randperm(n, generator=gen, device=x.device)
+        # the epoch's shuffled copy, so that each minibatch is a contiguous slice
+        up, lp, gp = u[perm], llc[perm], gf[perm]
         for i in range(n // batch):
-            idx = perm[i * batch:(i + 1) * batch]
+            sl = slice(i * batch, (i + 1) * batch)
             lr_k = lr * 0.5 * (1 + math.cos(math.pi * k / steps))    # cosine decay
-            loss = net.train_step(u[idx].contiguous(), llc[idx].contiguous(), gf[idx].contiguous(),
-                                  lr_k)
+            loss = net.train_step(up[sl], lp[sl], gp[sl], lr_k, loss_out=loss_buf)
             k += 1
         losses.append(float(loss.item()))
         if not math.isfinite(losses[-1]):
