@@ -25,10 +25,16 @@ extern "C" {
 argus_status argus_selftest_phase(const double* x, int64_t n, double* sin_out, double* cos_out,
                                   double* ref_sin, double* ref_cos);
 
-/* out[i] = 1 / S[i] by the approximate reciprocal refined by one third-order
- * step r (1 + e + e^2), e = 1 - S r (the filter's 1/S); S[i] must be positive
- * and normal. */
+/* out[i] = 1 / S[i] by the filter kernels' reciprocal: a double-float seed
+ * formed on the FP32 and integer pipes, refined by one FP64 Newton-Raphson
+ * step; S[i] must be normal. */
 argus_status argus_selftest_rcp(const double* S, int64_t n, double* out);
+
+/* out[i] = 1 / S[i] by the short-latency reciprocal of the time-parallel
+ * scan and the joint filter: the FP64 approximate reciprocal refined by one
+ * third-order step r (1 + e + e^2), e = 1 - S r; S[i] must be positive and
+ * normal. */
+argus_status argus_selftest_rcp3(const double* S, int64_t n, double* out);
 
 /* *out = sum_i ln S[i] by the running mantissa product; *bad = 1 if some S[i]
  * is not a positive, normal, finite number. */

@@ -408,7 +408,7 @@ __device__ void gwb_coef_scaled(const GwbSmem& s, const GwbRec& rk, double* tape
             s.sg[p] = sn;
             if (!(sn >= kGwbTiny)) s.gw[kGwRn] = 1.0;
         }
-        const double w = rcp_nr(sn), sc = psr ? s.par[4 * p] : s.gw[kGwHa2];
+        const double w = rcp_nr3(sn), sc = psr ? s.par[4 * p] : s.gw[kGwHa2];
         double* o = psr ? s.co + kCo * p : s.gc;
         o[0] = oc.a; o[1] = oc.b; o[2] = oc.c00; o[3] = oc.c01; o[4] = oc.c11;
         if (kDeriv) { o[5] = oc.db; o[6] = oc.dc00; o[7] = oc.dc01; o[8] = oc.dc11; }
@@ -514,7 +514,7 @@ __device__ void gwb_innovate(const GwbSmem& s, const GwbArgs& a, const GwbRec& r
     if (i < n) {
         const double R = fma(s.par[4 * rk.q + 2], rk.s2, a.equad2[rk.q]);
         const double S = s.Pm[pk(n, i0, i0)] + R;
-        const double rS = rcp_nr(S);
+        const double rS = rcp_nr3(S);
         for (; i < n; i += T) {
             const double ci = psym(s.Pm, n, i, i0);
             s.c[i] = ci;
@@ -647,7 +647,7 @@ __device__ void gwb_adjoint_observation(const GwbSmem& s, const GwbRec& rk) {
     double* gw = s.gw;
     if (tid == 0) {
         const double S = s.c[i0] + gw[kGwR0];
-        const double rS = rcp_nr(S);
+        const double rS = rcp_nr3(S);
         gw[kGwS] = S; gw[kGwRS] = rS; gw[kGwG] = gw[kGwE] * rS;
     }
     // v = Pb c, one thread per entry: row j of the symmetric Pb is its packed
@@ -905,7 +905,7 @@ __device__ void gwb_tape_step_scaled(const GwbSmem& s, const GwbArgs& a, const G
             s.sg0[p] = sg;
             s.sg[p] = sn;
             if (!(sn >= kGwbTiny)) s.gw[kGwRn] = 1.0;
-            const double w = rcp_nr(sn), sc = p < P ? s.par[4 * p] : s.gw[kGwHa2];
+            const double w = rcp_nr3(sn), sc = p < P ? s.par[4 * p] : s.gw[kGwHa2];
             double* h = s.cs + 5 * p;
             h[0] = ob * sg;
             h[1] = sc * q00;

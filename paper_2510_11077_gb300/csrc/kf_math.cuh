@@ -13,9 +13,8 @@
 //    Bailey 2001).  The table node plus the correction is then summed exactly
 //    in 2^-62 fixed point and rounded once to a double, all on the integer
 //    pipe: no FP64 instruction at all.
-//  * rcp_nr: 1/S by the FP64 approximate-reciprocal instruction refined by
-//    one third-order step r <- r (1 + e + e^2), e = 1 - S r, whose error is
-//    e^3.
+//  * rcp_nr: 1/S from a double-float seed formed on the FP32 and integer
+//    pipes, refined by one FP64 Newton-Raphson step (two FMAs).
 //  * LogProd: sum of ln S_k as a running product kept in [1, 2), in
 //    double-float arithmetic on the FP32 pipe, with its binary exponent
 //    accumulated in an integer (one log per lane at the end).
@@ -173,10 +172,48 @@ __device__ __forceinline__ void phase_sincos(double x, PhaseTable tab, double& s
     sincos_frac(frac_cycles_u64(x), tab, sn, cs);
 }
 
-// 1/S for a positive normal S: the approximate reciprocal (measured within
-// 2^-19.9) refined by one third-order step, r (1 + e + e^2) with e = 1 - S r:
-// the exact result is (1/S)(1 - e^3), so only the last rounding remains.
+// 1/S: a seed formed off the FP64 pipe, then one Newton-Raphson step in FP64
+// (two FMAs).  S = m 2^E with m in [1, 2).  The seed is 1/m in double-float
+// arithmetic on the FP32 pipe: the FP32 approximate reciprocal y0 of m's top
+// 24 bits, then one Newton-Raphson step y0 + y0 (1 - m y0), with 1 - m y0
+// formed from the FMA two-product of m's top bits and y0 (1 - m_hi y0 is
+// exact by Sterbenz's lemma) and m's low bits' product; relative error about
+// 2^-44.  The two floats are summed in 2^-62 fixed point and rounded once to
+// a double on the integer pipe, and E goes into the exponent field.  The FP64
+// step r = y (1 + e), e = 1 - S y, then leaves (1/S)(1 - e^2), e^2 < 2^-86:
+// only the last rounding remains.  A seed below the normal range (S above
+// 2^1022) is flushed to zero.  S zero, subnormal, infinite or NaN (never a
+// valid innovation variance; the log-determinant flags it) takes the
+// division.
+// rcp_nr3 below is the short-latency form for the paths that are latency
+// bound (the time-parallel scan, the joint filter's per-pulsar terms).
 __device__ __forceinline__ double rcp_nr(double S) {
+    const unsigned hs = unsigned(__double2hiint(S)), ls = unsigned(__double2loint(S));
+    const int ef = int((hs >> 20) & 0x7ffu);
+    if (ef == 0 || ef == 0x7ff) return 1.0 / S;
+    // m = 1.f: its top 24 bits, and the other 29 rounded to a float
+    const float mh = __uint_as_float(0x3f800000u | ((hs & 0x000fffffu) << 3) | (ls >> 29));
+    const float ml = __uint2float_rn(ls & 0x1fffffffu) * 0x1p-52f;
+    float y0;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y0) : "f"(mh));
+    const float ph = mh * y0;
+    const float pl = fmaf(mh, y0, -ph);                       // mh y0 = ph + pl exactly
+    const float e = fmaf(-ml, y0, (1.0f - ph) - pl);          // 1 - m y0
+    const long long v = f2fix62(y0) + f2fix62(y0 * e);        // y0 + y0 e in 2^-62 fixed point
+    const long long yb = __double_as_longlong(fix62_to_double(v));   // in (0.5, 1]: field 1022 or 1023
+    const int fe = int((yb >> 52) & 0x7ff) - (ef - 1023);     // 2^-E
+    const long long rb = fe > 0 ? (yb & 0x000fffffffffffffll) | (static_cast<long long>(fe) << 52) : 0ll;
+    const double y = __longlong_as_double(rb | (static_cast<long long>(hs >> 31) << 63));
+    const double r = fma(-S, y, 1.0);
+    return fma(y, r, y);
+}
+
+// 1/S with a short dependency chain: the FP64 approximate reciprocal
+// (measured within 2^-19.9) refined by one third-order step r (1 + e + e^2),
+// e = 1 - S r, whose exact result is (1/S)(1 - e^3): three FMAs, for the
+// paths where one thread's chain of steps, not the FP64 issue rate, sets the
+// time.
+__device__ __forceinline__ double rcp_nr3(double S) {
     double r;
     asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(S));
     const double e = fma(-S, r, 1.0);

@@ -170,8 +170,9 @@ struct StepOut {   // what the adjoint needs from the forward step
 // log-determinant is a running mantissa product (LogProd).
 // ---------------------------------------------------------------------------
 // kTape: produce what the adjoint needs; kLL: accumulate the log-likelihood;
-// kOU: Ornstein-Uhlenbeck red noise (else the random walk).
-template <bool kTape, bool kLL, bool kOU>
+// kOU: Ornstein-Uhlenbeck red noise (else the random walk); kShort: the
+// short-latency reciprocal (rcp_nr3) for the latency-bound scan paths.
+template <bool kTape, bool kLL, bool kOU, bool kShort = false>
 __device__ __forceinline__ void kf_step(State& x, const double* __restrict__ rec, const Lane& L,
                                         PhaseTable tab, double& quad, LogProd& lp,
                                         StepOut& so) {
@@ -209,7 +210,7 @@ __device__ __forceinline__ void kf_step(State& x, const double* __restrict__ rec
     const double e = fma(-L.A, sn, fma(-L.B, cs, r - m0));
     const double R = fma(L.efac2, s2k, L.equad2);
     const double S = M00 + R;
-    const double rS = rcp_nr(S);
+    const double rS = kShort ? rcp_nr3(S) : rcp_nr(S);
     const double g = e * rS;
     const double w = R * rS;
     const double K1 = M01 * rS;

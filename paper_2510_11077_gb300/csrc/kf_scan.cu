@@ -76,7 +76,7 @@ __device__ __forceinline__ void scan_combine_part(const SElem& i, const SElem& j
     const double M10 = fma(i.C01, j.J00, i.C11 * j.J01);
     const double M11 = 1.0 + fma(i.C01, j.J01, i.C11 * j.J11);
     // C_i, J_j are positive semi-definite, so det(I + C_i J_j) >= 1
-    const double rdet = rcp_nr(fma(M00, M11, -M01 * M10));
+    const double rdet = rcp_nr3(fma(M00, M11, -M01 * M10));
     const double X00 = M11 * rdet, X01 = -M01 * rdet, X10 = -M10 * rdet, X11 = M00 * rdet;
     if (kPart <= 1) {
         // G = A_j X
@@ -156,7 +156,7 @@ __device__ __forceinline__ SElem scan_element(int k, const double* __restrict__ 
     if (k == 0) {
         // the prior N(0, P0) at the first TOA, updated by it
         const double p00 = ps.p0[0], p01 = ps.p0[1], p11 = ps.p0[2];
-        const double rS = rcp_nr(p00 + R);
+        const double rS = rcp_nr3(p00 + R);
         const double K1 = p01 * rS, w = R * rS;
         E = SElem{0.0, 0.0, 0.0, 0.0, p00 * rS * y, K1 * y, p00 * w, p01 * w, fma(-K1, p01, p11),
                   0.0, 0.0, 0.0, 0.0, 0.0};
@@ -168,7 +168,7 @@ __device__ __forceinline__ SElem scan_element(int k, const double* __restrict__ 
             a = c.a; b = c.b; q00 = c.c00; q01 = c.c01; q11 = c.c11;
         }
         q00 *= L.sig2; q01 *= L.sig2; q11 *= L.sig2;
-        const double rS = rcp_nr(q00 + R);
+        const double rS = rcp_nr3(q00 + R);
         const double K1 = q01 * rS, w = R * rS;
         const double yr = y * rS;
         E.A00 = w; E.A01 = w * b; E.A10 = -K1; E.A11 = fma(-K1, b, a);
@@ -391,7 +391,7 @@ __global__ void __launch_bounds__(32) k_scan_finish(ScanArgs a) {
         if (k_lo > 0) x = prefix_state(a, it, int(threadIdx.x));
         StepOut so;
         for (int k = k_lo; k < k_hi; ++k)
-            kf_step<false, true, kOU>(x, a.rec + (ps.off + k) * kRecDoubles, L, tab, quad, lp, so);
+            kf_step<false, true, kOU, true>(x, a.rec + (ps.off + k) * kRecDoubles, L, tab, quad, lp, so);
     }
     finish_chunk_ll(a, it, quad, lp);
 }
@@ -653,7 +653,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_finish_grad(ScanGradArgs 
             StepOut so;
             for (int k = k_lo; k < k_hi; ++k) {
                 const double* rec = a.rec + (ps.off + k) * kRecDoubles;
-                kf_step<true, true, kOU>(x, rec, L, tab, quad, lp, so);
+                kf_step<true, true, kOU, true>(x, rec, L, tab, quad, lp, so);
                 stape_put<kOU>(tp + (k - k_lo), span, so);
                 const AElem f = adj_element<kOU>(so, rec);
                 psi = (k == k_lo) ? f : adj_combine(f, psi);

@@ -25,10 +25,11 @@ __global__ void k_phase(const double* x, int64_t n, double* s, double* c, double
     }
 }
 
+template <bool kShort>
 __global__ void k_rcp(const double* S, int64_t n, double* out) {
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
          i += int64_t(gridDim.x) * blockDim.x)
-        out[i] = rcp_nr(S[i]);
+        out[i] = kShort ? rcp_nr3(S[i]) : rcp_nr(S[i]);
 }
 
 __global__ void k_logsum(const double* S, int64_t n, double* out, int* bad) {
@@ -83,6 +84,24 @@ argus_status cuda_status(cudaError_t e) {
 
 }  // namespace
 
+namespace {
+template <bool kShort>
+argus_status selftest_rcp(const double* S, int64_t n, double* out) {
+    if (n < 0 || (n > 0 && (!S || !out))) return ARGUS_ERR_INVALID_ARG;
+    if (n == 0) return ARGUS_OK;
+    const size_t bytes = size_t(n) * sizeof(double);
+    DevBuf b;
+    TRY(cudaMalloc(&b.p, 2 * bytes));
+    double* d = static_cast<double*>(b.p);
+    TRY(cudaMemcpy(d, S, bytes, cudaMemcpyHostToDevice));
+    k_rcp<kShort><<<152, 256>>>(d, n, d + n);
+    TRY(cudaGetLastError());
+    TRY(cudaDeviceSynchronize());
+    TRY(cudaMemcpy(out, d + n, bytes, cudaMemcpyDeviceToHost));
+    return ARGUS_OK;
+}
+}  // namespace
+
 extern "C" {
 
 argus_status argus_selftest_phase(const double* x, int64_t n, double* sin_out, double* cos_out,
@@ -105,19 +124,13 @@ argus_status argus_selftest_phase(const double* x, int64_t n, double* sin_out, d
     return ARGUS_OK;
 }
 
+
 argus_status argus_selftest_rcp(const double* S, int64_t n, double* out) {
-    if (n < 0 || (n > 0 && (!S || !out))) return ARGUS_ERR_INVALID_ARG;
-    if (n == 0) return ARGUS_OK;
-    const size_t bytes = size_t(n) * sizeof(double);
-    DevBuf b;
-    TRY(cudaMalloc(&b.p, 2 * bytes));
-    double* d = static_cast<double*>(b.p);
-    TRY(cudaMemcpy(d, S, bytes, cudaMemcpyHostToDevice));
-    k_rcp<<<152, 256>>>(d, n, d + n);
-    TRY(cudaGetLastError());
-    TRY(cudaDeviceSynchronize());
-    TRY(cudaMemcpy(out, d + n, bytes, cudaMemcpyDeviceToHost));
-    return ARGUS_OK;
+    return selftest_rcp<false>(S, n, out);
+}
+
+argus_status argus_selftest_rcp3(const double* S, int64_t n, double* out) {
+    return selftest_rcp<true>(S, n, out);
 }
 
 argus_status argus_selftest_logsum(const double* S, int64_t n, double* out, int32_t* bad) {

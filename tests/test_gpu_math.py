@@ -22,6 +22,7 @@ def lib():
     dp = ctypes.c_void_p
     lib.argus_selftest_phase.argtypes = [dp, ctypes.c_int64, dp, dp, dp, dp]
     lib.argus_selftest_rcp.argtypes = [dp, ctypes.c_int64, dp]
+    lib.argus_selftest_rcp3.argtypes = [dp, ctypes.c_int64, dp]
     lib.argus_selftest_logsum.argtypes = [dp, ctypes.c_int64, dp, dp]
     return lib
 
@@ -55,12 +56,33 @@ def test_phase_sincos_accuracy(lib):
     assert np.all(np.abs(s) <= 1.0 + 1e-15) and np.all(np.abs(c) <= 1.0 + 1e-15)
 
 
-def test_refined_reciprocal_is_within_one_ulp(lib):
+def _rcp_inputs():
     rng = np.random.default_rng(1)
-    S = np.concatenate([10.0 ** rng.uniform(-300, 300, 20000), 1e-14 * rng.uniform(0.5, 4, 20000),
-                        [1.0, 2.0, 3.0, 0.1, 2.2250738585072014e-308 * 4]])
+    return np.concatenate([10.0 ** rng.uniform(-300, 300, 20000), 1e-14 * rng.uniform(0.5, 4, 20000),
+                           1.0 + rng.uniform(0.0, 1.0, 20000),
+                           [1.0, 2.0, 3.0, 0.1, 2.2250738585072014e-308 * 4, np.nextafter(2.0, 1.0)]])
+
+
+def test_refined_reciprocal_is_correctly_rounded(lib):
+    """The filter kernels' 1/S: a double-float seed (about 2^-44) and one FP64
+    Newton step leave (1/S)(1 - e^2), e^2 < 2^-86, so only the last rounding
+    remains: within half an ulp of 1/S, up to that 2^-86."""
+    S = _rcp_inputs()
     out = np.empty_like(S)
     assert lib.argus_selftest_rcp(_p(S), len(S), _p(out)) == 0
+    ref = 1.0 / S
+    ulps = np.abs(out - ref) / np.spacing(np.abs(ref))
+    assert ulps.max() <= 1.0
+    # numpy's division is correctly rounded: the two agree but for ties within 2^-86
+    assert np.mean(out == ref) >= 0.9999, np.mean(out == ref)
+
+
+def test_short_latency_reciprocal_is_within_one_ulp(lib):
+    """The scan's and the joint filter's 1/S: the approximate reciprocal and
+    one third-order step, (1/S)(1 - e^3) with e^3 < 2^-59."""
+    S = _rcp_inputs()
+    out = np.empty_like(S)
+    assert lib.argus_selftest_rcp3(_p(S), len(S), _p(out)) == 0
     ref = 1.0 / S
     ulps = np.abs(out - ref) / np.spacing(np.abs(ref))
     assert ulps.max() <= 1.0
