@@ -87,7 +87,7 @@ __device__ __forceinline__ long long f2fix62(float x) {
     return (u >> 31) ? -v : v;
 }
 
-// The double nearest to v 2^-62 (ties to even), for |v| <= 2^62 (|value| <= 1).
+// The double nearest to v 2^-62 (ties to even), for |v| < 2^63 (|value| < 2).
 // Integer instructions only.
 __device__ __forceinline__ double fix62_to_double(long long v) {
     const unsigned long long neg = v < 0 ? 1ull : 0ull;
