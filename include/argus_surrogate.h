@@ -130,7 +130,9 @@ argus_status argus_surrogate_set_cluster(argus_surrogate* s, int32_t ctas);
  * followed by its gradient (FP32, device; the layout the exact filter's
  * outputs pack into).  The loss is the weighted mean squared error of the
  * standardized outputs; argus_surrogate_last_loss reads its value before the
- * step. */
+ * step.  The step is ordered on `stream`: its weight-gradient products run on
+ * a stream the handle owns, forked from `stream` after the work they read and
+ * joined back into it before the weights change. */
 argus_status argus_surrogate_train_step(argus_surrogate* s, const float* x, const float* y, int64_t n,
                                         float lr, void* stream);
 

@@ -373,6 +373,11 @@ struct argus_surrogate {
     __nv_bfloat16* keep_dz16[kMlpLayers - 1] = {};
     int last_rows = 0;       // padded rows of the last training step
     float* loss_dev = nullptr;   // loss of the last argus_surrogate_train_step (packed form)
+    // training: the weight-gradient GEMMs and bias sums of layer l run on a
+    // side stream, forked after dZ_{l+1} is ready (ev_fork[l]) and joined
+    // through ev_done[l], while the caller's stream goes on down the chain
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork[kMlpLayers] = {}, ev_done[kMlpLayers] = {};
 };
 
 namespace {
@@ -393,6 +398,11 @@ void free_all(argus_surrogate* s) {
     for (int l = 0; l < kMlpLayers - 1; ++l) {
         cudaFree(s->keep_dz32[l]); cudaFree(s->keep_dz16[l]);
     }
+    for (int l = 0; l < kMlpLayers; ++l) {
+        if (s->ev_fork[l]) cudaEventDestroy(s->ev_fork[l]);
+        if (s->ev_done[l]) cudaEventDestroy(s->ev_done[l]);
+    }
+    if (s->side) cudaStreamDestroy(s->side);
 }
 
 // Tests: copy dZ_l of the current training step (FP32 and BF16) to the kept buffers.
@@ -636,6 +646,12 @@ argus_status argus_surrogate_create_ex(int32_t device, int32_t max_rows, uint64_
         }
         if (!st && cudaMemset(s->err, 0, sizeof(int)) != cudaSuccess) st = sfail(ARGUS_ERR_CUDA, "err");
     }
+    if (!st && cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking) != cudaSuccess)
+        st = sfail(ARGUS_ERR_CUDA, "side stream");
+    for (int l = 0; l < kMlpLayers && !st; ++l)
+        if (cudaEventCreateWithFlags(&s->ev_fork[l], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&s->ev_done[l], cudaEventDisableTiming) != cudaSuccess)
+            st = sfail(ARGUS_ERR_CUDA, "training events");
     if (!st) st = build_maps(s);
     if (!st) st = cast_weights(s, nullptr);
     if (!st && cudaDeviceSynchronize() != cudaSuccess) st = sfail(ARGUS_ERR_CUDA, "create sync");
@@ -873,17 +889,25 @@ argus_status train_step_impl(argus_surrogate* s, const float* theta, const float
                                                s->has_baseline ? s->gbase : nullptr, n, rows, s->norm,
                                                s->dY, s->dYT, s->rows, s->row_loss);
     k_loss_sum<<<1, kSumThreads, 0, st>>>(s->row_loss, rows, n, loss);
+    // Layer l's weight gradient (split-K GEMM) and bias sums only read dZ_{l+1}
+    // (dY for l = 4) and H_l, so they run on the side stream while this stream
+    // forms dZ_l; dH_l may overwrite a ping-pong buffer only once the side
+    // stream's reads of it (layer l + 2's) are done, and Adam joins them all.
+    cudaStream_t sd = s->side;
     // output layer: dW4^T = H4^T dY (split-K over rows), db4 = sum_r dY, dH4 = dY W4 -> dZ4
     {
+        SCK(cudaEventRecord(s->ev_fork[4], st));
+        SCK(cudaStreamWaitEvent(sd, s->ev_fork[4], 0));
         GemmEpiArgs g = epi_none();
         g.out_f32 = s->part[4];
         g.ldo = kMlpOutPad;
         g.chunk_stride = int64_t(kMlpHidden) * kMlpOutPad;
         cudaError_t ce = launch_gemm_tc(&s->tmHT[4], &s->tmdYT, kMlpHidden, kMlpOutPad, ck, 64, chunks,
-                                        kEpiF32, g, s->err, st);
+                                        kEpiF32, g, s->err, sd);
         if (ce != cudaSuccess) return scuda(ce, "dW4 GEMM");
-        k_colsum_part<__nv_bfloat16><<<dim3(kMlpOutPad / 32, kColChunks), 1024, 0, st>>>(s->dY, rows, kMlpOutPad,
+        k_colsum_part<__nv_bfloat16><<<dim3(kMlpOutPad / 32, kColChunks), 1024, 0, sd>>>(s->dY, rows, kMlpOutPad,
                                                                                       s->bpart[4]);
+        SCK(cudaEventRecord(s->ev_done[4], sd));
         GemmEpiArgs d = epi_none();
         d.zin = s->Z[4];
         d.ldz = kMlpHidden;
@@ -906,12 +930,17 @@ argus_status train_step_impl(argus_surrogate* s, const float* theta, const float
         g.out_f32 = s->part[l];
         g.ldo = K;
         g.chunk_stride = int64_t(kMlpHidden) * K;
+        SCK(cudaEventRecord(s->ev_fork[l], st));
+        SCK(cudaStreamWaitEvent(sd, s->ev_fork[l], 0));
         cudaError_t ce = launch_gemm_tc(&s->tmdZT[cur], &s->tmHT64[l], kMlpHidden, K, ck, 64,
-                                        chunks, kEpiF32, g, s->err, st);
+                                        chunks, kEpiF32, g, s->err, sd);
         if (ce != cudaSuccess) return scuda(ce, "dW GEMM");
-        k_colsum_part<float><<<dim3(kMlpHidden / 32, kColChunks), 1024, 0, st>>>(s->dZ32[cur], rows, kMlpHidden,
+        k_colsum_part<float><<<dim3(kMlpHidden / 32, kColChunks), 1024, 0, sd>>>(s->dZ32[cur], rows, kMlpHidden,
                                                                               s->bpart[l]);
+        SCK(cudaEventRecord(s->ev_done[l], sd));
         if (l > 0) {
+            // buffer cur ^ 1 last held dZ_{l+2}, which layer l + 1's side work read
+            if (l + 1 < kMlpLayers - 1) SCK(cudaStreamWaitEvent(st, s->ev_done[l + 1], 0));
             GemmEpiArgs d = epi_none();
             d.zin = s->Z[l];
             d.ldz = kMlpHidden;
@@ -928,6 +957,7 @@ argus_status train_step_impl(argus_surrogate* s, const float* theta, const float
             if ((e = keep_dz(s, l, cur, rows, st))) return e;
         }
     }
+    SCK(cudaStreamWaitEvent(st, s->ev_done[0], 0));   // the side stream ran layer 0's work last
     s->last_chunks = chunks;
     s->last_rows = rows;
     // Adam
