@@ -149,9 +149,11 @@ __device__ __forceinline__ float gelu_grad_e(float z, float e) {
 __device__ __forceinline__ float gelu_f(float z) { return gelu_e(z, erf_gelu(z)); }
 __device__ __forceinline__ float gelu_grad_f(float z) { return gelu_grad_e(z, erf_gelu(z)); }
 
+// zpre: for kEpiGeluBwd, the 16 saved pre-activations of these columns when
+// the caller loaded them ahead (else NULL: read here)
 template <int EPI>
 __device__ __forceinline__ void epilogue(const GemmEpiArgs& e, int row, int col0, int z,
-                                         float (&v)[16]) {
+                                         float (&v)[16], const float* zpre = nullptr) {
     if (EPI == kEpiF32) {
         float* o = e.out_f32 + z * e.chunk_stride + int64_t(row) * e.ldo + col0;
         float4* o4 = reinterpret_cast<float4*>(o);
@@ -180,7 +182,7 @@ __device__ __forceinline__ void epilogue(const GemmEpiArgs& e, int row, int col0
             for (int q = 0; q < 4; ++q) o4[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
         }
     } else {   // kEpiGeluBwd
-        const float* zr = e.zin + int64_t(row) * e.ldz + col0;
+        const float* zr = zpre ? zpre : e.zin + int64_t(row) * e.ldz + col0;
 #pragma unroll
         for (int j = 0; j < 16; ++j) d[j] = v[j] * gelu_grad_f(zr[j]);
         if (e.out_f32) {
@@ -203,8 +205,13 @@ __device__ __forceinline__ void epilogue(const GemmEpiArgs& e, int row, int col0
     }
 }
 
+// 256 threads: thread 0 issues the copies and the MMAs; in the epilogue warps
+// w and w + 4 share TMEM lane quadrant w (rows 32w..32w+31), each taking half
+// of the tile's columns.
+constexpr int kGemmThreads = 256;
+
 template <int EPI, int BN>
-__global__ void __launch_bounds__(128, 1) k_gemm_tc(const __grid_constant__ CUtensorMap ta,
+__global__ void __launch_bounds__(kGemmThreads, 1) k_gemm_tc(const __grid_constant__ CUtensorMap ta,
                                                     const __grid_constant__ CUtensorMap tb, int K,
                                                     GemmEpiArgs e, int* err) {
     extern __shared__ __align__(16) uint8_t smem_raw[];
@@ -239,6 +246,22 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(const __grid_constant__ CUte
     tc_fence_after();
     const uint32_t tmem = s_tmem;
 
+    // the epilogue's rows and columns; kEpiGeluBwd with 64-column tiles loads
+    // its saved pre-activations now, under the copies and the MMAs
+    const int quad = warp & 3, half = warp >> 2;
+    const int row = m0 + quad * 32 + (tid & 31);
+    constexpr int kHalf = BN / 2;
+    constexpr bool kPre = EPI == kEpiGeluBwd && BN <= 64;
+    float zp[kPre ? kHalf : 1];
+    if constexpr (kPre) {
+        const float4* z4 = reinterpret_cast<const float4*>(e.zin + int64_t(row) * e.ldz + n0 + half * kHalf);
+#pragma unroll
+        for (int q = 0; q < kHalf / 4; ++q) {
+            const float4 t = z4[q];
+            zp[4 * q] = t.x; zp[4 * q + 1] = t.y; zp[4 * q + 2] = t.z; zp[4 * q + 3] = t.w;
+        }
+    }
+
     bool issued = false;
     if (tid == 0) {
         mbar_expect_tx(bar_load, uint32_t(atoms) * (kGemmM + BN) * 128u);
@@ -267,13 +290,13 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(const __grid_constant__ CUte
     if (s_ok) {
         if (mbar_wait(bar_mma, 0, err, 2)) {
             tc_fence_after();
-            const int row = m0 + tid;
-            const uint32_t lane_base = tmem + (uint32_t(warp * 32) << 16);
-#pragma unroll 1
-            for (int c0 = 0; c0 < BN; c0 += 16) {
+            const uint32_t lane_base = tmem + (uint32_t(quad * 32) << 16);
+#pragma unroll
+            for (int c = 0; c < kHalf; c += 16) {
+                const int c0 = half * kHalf + c;
                 float v[16];
                 tmem_ld16(lane_base + uint32_t(c0), v);
-                epilogue<EPI>(e, row, n0 + c0, blockIdx.z, v);
+                epilogue<EPI>(e, row, n0 + c0, blockIdx.z, v, kPre ? zp + c : nullptr);
             }
         } else if (issued) {
             mbar_wait(bar_mma, 0, nullptr, 0);    // let MMAs in flight finish (bounded)
@@ -303,7 +326,7 @@ cudaError_t launch_one(const CUtensorMap* ta, const CUtensorMap* tb, int M, int 
         configured[dev] = true;
     }
     dim3 grid(M / kGemmM, N / BN, chunks);
-    k_gemm_tc<EPI, BN><<<grid, 128, smem, s>>>(*ta, *tb, K, e, err);
+    k_gemm_tc<EPI, BN><<<grid, kGemmThreads, smem, s>>>(*ta, *tb, K, e, err);
     return cudaGetLastError();
 }
 
