@@ -390,6 +390,41 @@ def test_surrogate_training_fits_a_smooth_function(lib):
     assert losses[-1] < 0.1 * losses[0], (losses[0], losses[-1])
 
 
+def test_training_is_deterministic_on_any_stream(lib):
+    """A training step forks its weight-gradient work onto a stream the handle
+    owns and joins it back; the same seeded steps on the default stream and on
+    a side stream (with other work queued on the default stream meanwhile)
+    give bit-identical weights, and a second run on the default stream too."""
+    from paper_2510_11077_gb300 import surrogate
+    rng = np.random.default_rng(11)
+    n = 2500
+    theta = rng.standard_normal((n, mlp.IN_DIM)).astype(np.float32)
+    ll = rng.standard_normal(n).astype(np.float32)
+    g = rng.standard_normal((n, mlp.IN_DIM)).astype(np.float32)
+    th, l_, g_ = (torch.from_numpy(a).cuda() for a in (theta, ll, g))
+
+    def run(stream):
+        s = surrogate.Surrogate(device=0, max_rows=4096, seed=5)
+        s.set_normalizers(np.zeros(mlp.IN_DIM), np.ones(mlp.IN_DIM), 0.0, 1.0)
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            busy = torch.empty(1 << 24, device="cuda")
+            for i in range(6):
+                busy.normal_()          # unrelated work on the same stream between steps
+                s.train_step(th, l_, g_, lr=1e-3)
+        torch.cuda.synchronize()
+        s.check()
+        w = s.get_weights()
+        s.close()
+        return w
+
+    w0 = run(torch.cuda.default_stream())
+    w1 = run(torch.cuda.Stream())
+    w2 = run(torch.cuda.default_stream())
+    assert np.array_equal(w0, w1)
+    assert np.array_equal(w0, w2)
+
+
 @pytest.mark.parametrize("n", [1, 127, 130, 1000, 2500])
 @pytest.mark.parametrize("mode", ["value", "gradient head", "value backprop"])
 @pytest.mark.parametrize("baseline", [False, True])
