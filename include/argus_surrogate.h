@@ -4,7 +4,7 @@
  *
  * The target path pairs the exact filter with a small network trained on the
  * exact filter's own evaluations and used as the first stage of a
- * delayed-acceptance sampler whose second stage, fallback and judge is the
+ * delayed-acceptance sampler whose second stage, fallback and arbiter is the
  * exact FP64 filter (argus.h).  The paper's own sampler integration
  * (Functionality, "Sampler Integration") calls a likelihood and its gradient
  * at every step; the surrogate supplies a cheap approximation of both.
