@@ -29,7 +29,7 @@ TIE = 0.01
 
 DEFAULT_SPACE = {
     "walkers_per_cta": (32, 64, 128),
-    "ctas_per_sm": (4, 8, 16),
+    "ctas_per_sm": (4, 8, 12, 16),
     "tape_cache": (0, 1),
     "ckpt_stride": (0,),
 }

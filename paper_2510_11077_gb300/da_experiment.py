@@ -50,10 +50,10 @@ class ExactTarget:
 
     def __init__(self, data, device):
         self.arr = argus.Array(data, device=device)      # loglik + grad, graph replay
-        self.arr.set_plan(tape_cache=1, walkers_per_cta=64, ctas_per_sm=8)
+        self.arr.set_plan(tape_cache=1, walkers_per_cta=32, ctas_per_sm=12)
         self.arr_ll = argus.Array(data, device=device)   # loglik of varying batch sizes
         # small tiles balance the stage-1 survivors' uneven batches over the SMs
-        self.arr_ll.set_plan(use_graph=0, walkers_per_cta=32, ctas_per_sm=16)
+        self.arr_ll.set_plan(use_graph=0, walkers_per_cta=32, ctas_per_sm=12)
         lo, hi = prior_box(data.n_pulsars)
         self.lo = torch.tensor(lo, dtype=torch.float64, device=device)
         self.hi = torch.tensor(hi, dtype=torch.float64, device=device)
