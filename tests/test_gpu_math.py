@@ -77,6 +77,24 @@ def test_refined_reciprocal_is_correctly_rounded(lib):
     assert np.mean(out == ref) >= 0.9999, np.mean(out == ref)
 
 
+def test_refined_reciprocal_special_inputs(lib):
+    """Negative normal S is the mirror image; zero, subnormal, infinite and NaN
+    S take the division (1/S exactly); a reciprocal below the normal range
+    (S above 2^1022) flushes to zero, as the approximate instruction does."""
+    S = np.array([-3.0, -1e-14, -2.5e300, 0.0, -0.0, 5e-324, 1e-310, np.inf, -np.inf, np.nan,
+                  2.0 ** 1023, 1.5 * 2.0 ** 1022, 2.0 ** 1022])
+    out = np.empty_like(S)
+    assert lib.argus_selftest_rcp(_p(S), len(S), _p(out)) == 0
+    with np.errstate(divide="ignore", over="ignore"):
+        ref = 1.0 / S
+    neg = S[:3]
+    ulps = np.abs(out[:3] - ref[:3]) / np.spacing(np.abs(ref[:3]))
+    assert ulps.max() <= 1.0 and np.all(np.sign(out[:3]) == np.sign(neg))
+    assert np.array_equal(out[3:10], ref[3:10], equal_nan=True)
+    assert out[10] == 0.0 and out[11] == 0.0
+    assert out[12] == 2.0 ** -1022
+
+
 def test_short_latency_reciprocal_is_within_one_ulp(lib):
     """The scan's and the joint filter's 1/S: the approximate reciprocal and
     one third-order step, (1/S)(1 - e^3) with e^3 < 2^-59."""
