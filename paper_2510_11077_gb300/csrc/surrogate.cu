@@ -894,6 +894,17 @@ argus_status train_step_impl(argus_surrogate* s, const float* theta, const float
     // forms dZ_l; dH_l may overwrite a ping-pong buffer only once the side
     // stream's reads of it (layer l + 2's) are done, and Adam joins them all.
     cudaStream_t sd = s->side;
+    // If a call below fails after the fork, the caller's stream still waits
+    // for whatever the side stream was given, so that no later work on it
+    // overwrites buffers the side stream reads (the normal path joins below).
+    struct SideJoin {
+        cudaStream_t main, side;
+        cudaEvent_t ev;
+        bool pending = true;
+        ~SideJoin() {
+            if (pending && cudaEventRecord(ev, side) == cudaSuccess) cudaStreamWaitEvent(main, ev, 0);
+        }
+    } side_join{st, sd, s->ev_done[0]};
     // output layer: dW4^T = H4^T dY (split-K over rows), db4 = sum_r dY, dH4 = dY W4 -> dZ4
     {
         SCK(cudaEventRecord(s->ev_fork[4], st));
@@ -958,6 +969,7 @@ argus_status train_step_impl(argus_surrogate* s, const float* theta, const float
         }
     }
     SCK(cudaStreamWaitEvent(st, s->ev_done[0], 0));   // the side stream ran layer 0's work last
+    side_join.pending = false;
     s->last_chunks = chunks;
     s->last_rows = rows;
     // Adam
